@@ -1,0 +1,152 @@
+"""Pure-Python brute force: a third, independent reading of the method for tiny
+rooms (a few hundred images, a few hundred samples).
+
+TEST INFRASTRUCTURE ONLY. It does not use oracle.cpp nor the CUDA library.
+Images come from repeated mirroring of the source across the six walls
+(breadth first), not from the lattice formula; the spline is evaluated with
+de Boor's algorithm, not with the basis recursion; the Kaiser window uses its
+own series. Everything is plain Python floats.
+"""
+from __future__ import annotations
+
+import math
+
+
+def mirror_images(dims, max_depth):
+    """Breadth-first mirroring across walls x=0, x=Lx, y=0, y=Ly, z=0, z=Lz.
+
+    Each image is an affine map of the source position, coordinate-wise
+    q_d -> sign_d * q_d + offset_d, reached first at depth rho (its reflection
+    count); hits[w] counts reflections off wall w on that shortest path.
+    Returns a list of (sign[3], offset[3], hits[6]).
+    """
+    start = ((1, 1, 1), (0.0, 0.0, 0.0), (0, 0, 0, 0, 0, 0))
+    seen = {(start[0], start[1])}
+    out = [start]
+    frontier = [start]
+    for _ in range(max_depth):
+        nxt = []
+        for sign, off, hits in frontier:
+            for w in range(6):
+                a, side = divmod(w, 2)
+                s, o = list(sign), list(off)
+                # reflect q -> -q (plane 0) or q -> 2L - q (plane L) applied to s*q + o
+                s[a] = -s[a]
+                o[a] = -o[a] if side == 0 else 2.0 * dims[a] - o[a]
+                key = (tuple(s), tuple(round(v, 9) for v in o))
+                if key in seen:
+                    continue
+                seen.add(key)
+                h = list(hits)
+                h[w] += 1
+                item = (tuple(s), tuple(o), tuple(h))
+                out.append(item)
+                nxt.append(item)
+        frontier = nxt
+    return out
+
+
+def lattice_of(sign, off, dims):
+    """(n, p) of a mirrored image: sign = 1 - 2p, offset = 2 n L."""
+    p = [(1 - s) // 2 for s in sign]
+    n = [int(round(o / (2.0 * L))) for o, L in zip(off, dims)]
+    return n, p
+
+
+def _deboor(ctrl, u):
+    """Clamped uniform cubic B-spline at u in [0, 1] by de Boor's algorithm."""
+    m = len(ctrl)
+    segs = m - 3
+    knots = [0.0] * 4 + [i / segs for i in range(1, segs)] + [1.0] * 4
+    k = min(3 + int(u * segs), m - 1)  # knot span index with knots[k] <= u < knots[k+1]
+    d = [list(ctrl[j + k - 3]) for j in range(4)]
+    for r in range(1, 4):
+        for j in range(3, r - 1, -1):
+            i = j + k - 3
+            den = knots[i + 4 - r] - knots[i]
+            a = 0.0 if den == 0 else (u - knots[i]) / den
+            d[j] = [(1 - a) * d[j - 1][c] + a * d[j][c] for c in range(3)]
+    return d[3]
+
+
+def source(scene, t):
+    tr = scene.traj
+    if scene.traj_kind == 0:
+        nrm = math.sqrt(tr[3] ** 2 + tr[4] ** 2 + tr[5] ** 2)
+        return [tr[i] + tr[6] * t * tr[3 + i] / nrm for i in range(3)]
+    if scene.traj_kind == 1:
+        ang = tr[5] + tr[4] * t / tr[3]
+        return [tr[0] + tr[3] * math.cos(ang), tr[1] + tr[3] * math.sin(ang), tr[2]]
+    ctrl = [tr[3 * i: 3 * i + 3] for i in range(scene.n_ctrl)]
+    return _deboor(ctrl, min(1.0, max(0.0, t / scene.duration)))
+
+
+def _bessel_i0(v):
+    s, term, j = 1.0, 1.0, 1
+    while term > 1e-18 * s:
+        term *= (v / 2.0) ** 2 / (j * j)
+        s += term
+        j += 1
+    return s
+
+
+def _window(scene, u):
+    L = scene.taps
+    if scene.window == 0:
+        return 0.5 + 0.5 * math.cos(2.0 * math.pi * u / L)
+    z = max(0.0, 1.0 - (2.0 * u / L) ** 2)
+    return _bessel_i0(scene.kaiser_beta * math.sqrt(z)) / _bessel_i0(scene.kaiser_beta)
+
+
+def _kernel(scene, u):
+    s = 1.0 if u == 0 else math.sin(math.pi * u) / (math.pi * u)
+    return _window(scene, u) * s
+
+
+def synthesize(scene, x, n_out, mic_index=0):
+    """y[n] = sum over images with |n|_1 <= K of beta/(4 pi d) * windowed-sinc
+    interpolation of x at n - d fs / c, d linearly interpolated between knots.
+    `scene` is a workload scene description (tiers given as knot rates in Hz)."""
+    dims = scene.dims
+    mic = [float(v) for v in scene.mics[mic_index]]
+    tiers = [(r, int(round(scene.fs / rate))) for r, rate in scene.tiers]
+    imgs = []
+    for sign, off, hits in mirror_images(dims, 2 * scene.K + 3):
+        n, _ = lattice_of(sign, off, dims)
+        if sum(abs(v) for v in n) > scene.K:
+            continue
+        beta = 1.0
+        for w in range(6):
+            beta *= scene.beta[w] ** hits[w]
+        rho = sum(hits)
+        step = tiers[-1][1]
+        for max_rho, st in tiers:
+            if rho <= max_rho:
+                step = st
+                break
+        imgs.append((sign, off, beta, step))
+
+    def dist(sign, off, t):
+        q = source(scene, t)
+        return math.sqrt(sum((sign[d] * q[d] + off[d] - mic[d]) ** 2 for d in range(3)))
+
+    half = scene.taps // 2
+    y = []
+    for n in range(n_out):
+        acc = 0.0
+        for sign, off, beta, step in imgs:
+            j0 = (n // step) * step
+            frac = (n - j0) / step
+            d0 = dist(sign, off, j0 / scene.fs)
+            d1 = dist(sign, off, (j0 + step) / scene.fs)
+            d = d0 + frac * (d1 - d0)
+            t = n - d * scene.fs / scene.c
+            m0 = math.floor(t)
+            e = 0.0
+            for k in range(-half, half):
+                m = m0 - k
+                if 0 <= m < len(x):
+                    e += _kernel(scene, t - m) * x[m]
+            acc += beta / (4.0 * math.pi * d) * e
+        y.append(acc)
+    return y

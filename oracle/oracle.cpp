@@ -1,0 +1,454 @@
+// FP64 CPU oracle for moving-source image-source synthesis.
+//
+// TEST INFRASTRUCTURE ONLY. Nothing in the product path may call, link or load
+// this file; only the tests, the smoke check and the benchmark's CPU-baseline
+// leg do. It shares no code, header, table or helper with the CUDA library.
+//
+// What it computes (arXiv 2508.03065, "Fast Algorithm for Moving Sound Source"):
+//   * image set (Sec. II-A, Eq. 1, Allen-Berkley lattice): every lattice triple n
+//     with |n_x|+|n_y|+|n_z| <= K and every parity p in {0,1}^3; image position
+//     r_i(t) = (1-2p) o s(t) + 2 n o L_room; reflection factor
+//     beta_i = prod_d beta_{d,0}^{|n_d-p_d|} beta_{d,1}^{|n_d|};
+//     reflection count rho_i = sum_d |2 n_d - p_d|;
+//   * hierarchical spatio-temporal sampling (Sec. II-C, "Fast Architecture"):
+//     image i is in tier t (by rho_i); its distance d_i is evaluated exactly at
+//     knots n_j = j*N_t and linearly interpolated to every audio sample;
+//   * delay tau_i(n) = d_i(n) fs / c and gain A_i(n) = beta_i / (4 pi d_i(n))
+//     (Sec. II-A, text after Eq. 2; Sec. II-C, text before Eq. 8);
+//   * discrete time-varying fractional delay (Sec. II-B): the ideal delay kernel
+//     sin(pi u)/(pi u), truncated to L taps k = -L/2 .. L/2-1 and windowed
+//     (Hann or Kaiser), applied at read position t = n - tau_i(n):
+//     m0 = floor(t), alpha = t - m0, e_i(n) = sum_k w(alpha+k) sinc(alpha+k) x[m0-k];
+//   * superposition over images (Eq. 2 / Eq. 8): y[n] = sum_i A_i(n) e_i(n).
+// x[m] is zero outside [0, Ns).
+//
+// Every routine is templated on the scalar so that the same code, run in
+// std::complex<double>, gives complex-step derivatives of the loss with respect
+// to trajectory parameters and wall reflection coefficients. Integer decisions
+// (floor, tier, knot index) always use the real part.
+//
+// Parity pins: tests/test_oracle_pins.py (closed forms, library special
+// cases, brute force, invariants). Readings of the paper where it is silent or
+// garbled are listed in the design notes of the repository.
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+using cplx = std::complex<double>;
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+inline double re(double v) { return v; }
+inline double re(const cplx& v) { return v.real(); }
+
+}  // namespace
+
+extern "C" {
+
+// Scene description shared with oracle/api.py through ctypes.
+struct OracleScene {
+  double dims[3];         // room size L_x, L_y, L_z (m)
+  double beta[6];         // reflection coefficients of walls x=0, x=Lx, y=0, y=Ly, z=0, z=Lz
+  double c;               // speed of sound (m/s)
+  double fs;              // sample rate (Hz)
+  double kaiser_beta;     // Kaiser window shape
+  double traj[48];        // trajectory parameters (see source_position)
+  double duration;        // trajectory duration T (s), used by the spline
+  double mic[3];          // microphone position (m)
+  int32_t K;              // image set |n|_1 <= K
+  int32_t n_tiers;        // number of sampling tiers (1..4)
+  int32_t tier_max_rho[4];// tier t holds images with rho <= tier_max_rho[t] (first match)
+  int32_t tier_step[4];   // knot spacing N_t (samples) of tier t
+  int32_t taps;           // L (even)
+  int32_t window;         // 0 = Hann, 1 = Kaiser
+  int32_t traj_kind;      // 0 = line, 1 = circle, 2 = clamped cubic B-spline
+  int32_t n_ctrl;         // number of spline control points
+};
+
+}  // extern "C"
+
+namespace {
+
+struct Image {
+  int n[3];
+  int p[3];
+  int e[6];   // reflections off each wall
+  int rho;    // total reflection count
+  int tier;
+};
+
+// Image enumeration, Sec. II-A (Eq. 1) with the Allen-Berkley lattice.
+std::vector<Image> enumerate_images(const OracleScene& S) {
+  std::vector<Image> out;
+  const int K = S.K;
+  for (int nx = -K; nx <= K; ++nx)
+    for (int ny = -K; ny <= K; ++ny)
+      for (int nz = -K; nz <= K; ++nz) {
+        if (std::abs(nx) + std::abs(ny) + std::abs(nz) > K) continue;
+        for (int pb = 0; pb < 8; ++pb) {
+          Image im;
+          im.n[0] = nx; im.n[1] = ny; im.n[2] = nz;
+          im.p[0] = pb & 1; im.p[1] = (pb >> 1) & 1; im.p[2] = (pb >> 2) & 1;
+          im.rho = 0;
+          for (int d = 0; d < 3; ++d) {
+            im.e[2 * d] = std::abs(im.n[d] - im.p[d]);  // wall at coordinate 0
+            im.e[2 * d + 1] = std::abs(im.n[d]);        // wall at coordinate L_d
+            im.rho += std::abs(2 * im.n[d] - im.p[d]);
+          }
+          im.tier = S.n_tiers - 1;
+          for (int t = 0; t < S.n_tiers; ++t)
+            if (im.rho <= S.tier_max_rho[t]) { im.tier = t; break; }
+          out.push_back(im);
+        }
+      }
+  return out;
+}
+
+template <class T>
+struct Params {
+  T traj[48];
+  T beta[6];
+};
+
+template <class T>
+Params<T> params_from(const OracleScene& S) {
+  Params<T> P;
+  for (int i = 0; i < 48; ++i) P.traj[i] = T(S.traj[i]);
+  for (int i = 0; i < 6; ++i) P.beta[i] = T(S.beta[i]);
+  return P;
+}
+
+// Cox-de Boor recursion for the clamped uniform cubic B-spline basis.
+// Knot vector: four zeros, interior knots k/(n_ctrl-3), four ones.
+double bspline_basis(int i, int deg, double u, const std::vector<double>& kv) {
+  if (deg == 0) {
+    const int last = static_cast<int>(kv.size()) - 1;
+    // the closing interval includes u = 1
+    if (u == kv[last]) return (kv[i] < u && kv[i + 1] == u) ? 1.0 : 0.0;
+    return (kv[i] <= u && u < kv[i + 1]) ? 1.0 : 0.0;
+  }
+  double a = 0.0, b = 0.0;
+  const double d1 = kv[i + deg] - kv[i];
+  const double d2 = kv[i + deg + 1] - kv[i + 1];
+  if (d1 > 0) a = (u - kv[i]) / d1 * bspline_basis(i, deg - 1, u, kv);
+  if (d2 > 0) b = (kv[i + deg + 1] - u) / d2 * bspline_basis(i + 1, deg - 1, u, kv);
+  return a + b;
+}
+
+std::vector<double> clamped_knots(int n_ctrl) {
+  const int segs = n_ctrl - 3;
+  std::vector<double> kv;
+  for (int i = 0; i < 4; ++i) kv.push_back(0.0);
+  for (int i = 1; i < segs; ++i) kv.push_back(static_cast<double>(i) / segs);
+  for (int i = 0; i < 4; ++i) kv.push_back(1.0);
+  return kv;
+}
+
+// Source position s(t), Sec. II-C ("sample a segment of the band-limited
+// trajectory p(n)"). Parameter layout of traj[]:
+//   line:   p0[3], direction[3] (normalised here), speed v      -> p0 + v t dir
+//   circle: centre[3], radius R, speed v, start angle theta0    -> centre + R(cos, sin, 0)(theta0 + v t / R)
+//   spline: control points P_0..P_{n_ctrl-1} (3 each); u = clamp(t / T, 0, 1)
+template <class T>
+void source_position(const OracleScene& S, const Params<T>& P, double t, T out[3]) {
+  if (S.traj_kind == 0) {
+    T nrm = std::sqrt(P.traj[3] * P.traj[3] + P.traj[4] * P.traj[4] + P.traj[5] * P.traj[5]);
+    for (int d = 0; d < 3; ++d) out[d] = P.traj[d] + P.traj[6] * t * P.traj[3 + d] / nrm;
+  } else if (S.traj_kind == 1) {
+    T R = P.traj[3];
+    T ang = P.traj[5] + P.traj[4] * t / R;
+    out[0] = P.traj[0] + R * std::cos(ang);
+    out[1] = P.traj[1] + R * std::sin(ang);
+    out[2] = P.traj[2];
+  } else {
+    double u = t / S.duration;
+    u = std::min(1.0, std::max(0.0, u));
+    const std::vector<double> kv = clamped_knots(S.n_ctrl);
+    for (int d = 0; d < 3; ++d) out[d] = T(0.0);
+    for (int c = 0; c < S.n_ctrl; ++c) {
+      const double B = bspline_basis(c, 3, u, kv);
+      for (int d = 0; d < 3; ++d) out[d] += B * P.traj[3 * c + d];
+    }
+  }
+}
+
+// Euclidean distance from image i to the microphone at time t (Sec. II-A).
+template <class T>
+T image_distance(const OracleScene& S, const Params<T>& P, const Image& im, double t) {
+  T s[3];
+  source_position(S, P, t, s);
+  T acc = T(0.0);
+  for (int d = 0; d < 3; ++d) {
+    const double sigma = 1.0 - 2.0 * im.p[d];
+    T r = sigma * s[d] + 2.0 * im.n[d] * S.dims[d];
+    T diff = r - S.mic[d];
+    acc += diff * diff;
+  }
+  return std::sqrt(acc);
+}
+
+template <class T>
+T image_beta(const Params<T>& P, const Image& im) {
+  T b = T(1.0);
+  for (int w = 0; w < 6; ++w)
+    for (int r = 0; r < im.e[w]; ++r) b *= P.beta[w];
+  return b;
+}
+
+// Window over u in [-L/2, L/2].
+template <class T>
+T window_value(const OracleScene& S, T u) {
+  const double L = S.taps;
+  if (S.window == 0) return 0.5 * (1.0 + std::cos(2.0 * kPi * u / L));
+  // Kaiser: I0(beta sqrt(z)) / I0(beta), z = 1 - (2u/L)^2, with
+  // I0(beta sqrt(z)) = sum_j (beta^2 z / 4)^j / (j!)^2 (power series).
+  const double b = S.kaiser_beta;
+  T z = 1.0 - (2.0 * u / L) * (2.0 * u / L);
+  T term = T(1.0), sum = T(1.0);
+  double term0 = 1.0, sum0 = 1.0;
+  for (int j = 1; j < 80; ++j) {
+    term *= (b * b * z / 4.0) / (double(j) * double(j));
+    sum += term;
+    term0 *= (b * b / 4.0) / (double(j) * double(j));
+    sum0 += term0;
+  }
+  return sum / sum0;
+}
+
+// Ideal fractional-delay kernel sin(pi u)/(pi u) (Sec. II-B).
+template <class T>
+T sinc_value(T u) {
+  if (std::abs(u) == 0.0) return T(1.0);
+  return std::sin(kPi * u) / (kPi * u);
+}
+
+// Tap weight for tap k at fractional read position alpha.
+template <class T>
+T tap_weight(const OracleScene& S, int k, T alpha) {
+  T u = alpha + double(k);
+  return window_value(S, u) * sinc_value(u);
+}
+
+inline double xval(const double* x, long Ns, long m) { return (m >= 0 && m < Ns) ? x[m] : 0.0; }
+
+// Delay tau_i(n) (in samples), gain A_i(n) and distance d_i(n) at output sample
+// n: knots of image i's tier at n_j = j N_t, exact distances there, linear
+// interpolation of the distance in between (Sec. II-C, "Fast Architecture").
+template <class T>
+void delay_gain(const OracleScene& S, const Params<T>& P, const Image& im, long n,
+                T* tau, T* gain, T* dist) {
+  const long N = S.tier_step[im.tier];
+  const long j = n / N;
+  const long nj = j * N;
+  const double s = double(n - nj) / double(N);
+  T dj = image_distance(S, P, im, double(nj) / S.fs);
+  T d = dj;
+  if (s != 0.0) {
+    T dj1 = image_distance(S, P, im, double(nj + N) / S.fs);
+    d = dj + s * (dj1 - dj);
+  }
+  *dist = d;
+  *tau = d * S.fs / S.c;
+  *gain = image_beta(P, im) / (4.0 * kPi * d);
+}
+
+// Contribution A_i(n) e_i(n) of one image to output sample n (Eq. 8).
+template <class T>
+T image_sample(const OracleScene& S, const Params<T>& P, const Image& im,
+               const double* x, long Ns, long n) {
+  T tau, g, d;
+  delay_gain(S, P, im, n, &tau, &g, &d);
+  T t = double(n) - tau;
+  const long m0 = static_cast<long>(std::floor(re(t)));
+  T alpha = t - double(m0);
+  const int half = S.taps / 2;
+  T e = T(0.0);
+  for (int k = -half; k <= half - 1; ++k) e += tap_weight(S, k, alpha) * xval(x, Ns, m0 - k);
+  return g * e;
+}
+
+template <class T>
+T output_sample(const OracleScene& S, const Params<T>& P, const std::vector<Image>& imgs,
+                const double* x, long Ns, long n) {
+  T acc = T(0.0);
+  for (const Image& im : imgs) acc += image_sample(S, P, im, x, Ns, n);
+  return acc;
+}
+
+std::vector<Image> select_images(const OracleScene& S, const int32_t* list, long n_list) {
+  std::vector<Image> all = enumerate_images(S);
+  if (!list) return all;
+  std::vector<Image> sel;
+  sel.reserve(n_list);
+  for (long i = 0; i < n_list; ++i) sel.push_back(all[list[i]]);
+  return sel;
+}
+
+}  // namespace
+
+extern "C" {
+
+long oracle_image_count(int32_t K) {
+  long cnt = 0;
+  for (int nx = -K; nx <= K; ++nx)
+    for (int ny = -K; ny <= K; ++ny)
+      for (int nz = -K; nz <= K; ++nz)
+        if (std::abs(nx) + std::abs(ny) + std::abs(nz) <= K) cnt += 8;
+  return cnt;
+}
+
+// Image table in enumeration order: n[3], p[3], e[6], rho, tier per image,
+// beta_i in FP64.
+void oracle_enumerate(const OracleScene* S, int32_t* n_out, int32_t* p_out, int32_t* e_out,
+                      int32_t* rho_out, int32_t* tier_out, double* beta_out) {
+  std::vector<Image> imgs = enumerate_images(*S);
+  Params<double> P = params_from<double>(*S);
+  for (size_t i = 0; i < imgs.size(); ++i) {
+    for (int d = 0; d < 3; ++d) { n_out[3 * i + d] = imgs[i].n[d]; p_out[3 * i + d] = imgs[i].p[d]; }
+    for (int w = 0; w < 6; ++w) e_out[6 * i + w] = imgs[i].e[w];
+    rho_out[i] = imgs[i].rho;
+    tier_out[i] = imgs[i].tier;
+    beta_out[i] = image_beta(P, imgs[i]);
+  }
+}
+
+void oracle_source_position(const OracleScene* S, const double* t, long n_t, double* out) {
+  Params<double> P = params_from<double>(*S);
+  for (long i = 0; i < n_t; ++i) source_position(*S, P, t[i], out + 3 * i);
+}
+
+// Exact distance of image `idx` (enumeration order) at times t[].
+void oracle_image_distance(const OracleScene* S, long idx, const double* t, long n_t, double* out) {
+  std::vector<Image> imgs = enumerate_images(*S);
+  Params<double> P = params_from<double>(*S);
+  for (long i = 0; i < n_t; ++i) out[i] = image_distance(*S, P, imgs[idx], t[i]);
+}
+
+// Interpolated delay (samples), gain and distance of image `idx` at samples n[].
+void oracle_delay_gain(const OracleScene* S, long idx, const int64_t* n, long n_n,
+                       double* tau, double* gain, double* dist) {
+  std::vector<Image> imgs = enumerate_images(*S);
+  Params<double> P = params_from<double>(*S);
+  for (long i = 0; i < n_n; ++i) delay_gain(*S, P, imgs[idx], n[i], tau + i, gain + i, dist + i);
+}
+
+void oracle_tap_weights(const OracleScene* S, const double* alpha, long n_alpha, double* out) {
+  const int half = S->taps / 2;
+  for (long a = 0; a < n_alpha; ++a)
+    for (int k = -half; k <= half - 1; ++k)
+      out[a * S->taps + (k + half)] = tap_weight(*S, k, alpha[a]);
+}
+
+void oracle_window(const OracleScene* S, const double* u, long n_u, double* out) {
+  for (long i = 0; i < n_u; ++i) out[i] = window_value(*S, u[i]);
+}
+
+// y[idx[q]] for the listed output samples, over the listed images (enumeration
+// indices, in the given order; null = all images in enumeration order).
+void oracle_y_at(const OracleScene* S, const double* x, long Ns, const int64_t* idx, long n_idx,
+                 const int32_t* img_list, long n_img, double* y) {
+  std::vector<Image> imgs = select_images(*S, img_list, n_img);
+  Params<double> P = params_from<double>(*S);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (long q = 0; q < n_idx; ++q) y[q] = output_sample(*S, P, imgs, x, Ns, idx[q]);
+}
+
+// Full output y[0 .. n_out).
+void oracle_synthesize(const OracleScene* S, const double* x, long Ns, long n_out, double* y) {
+  std::vector<Image> imgs = enumerate_images(*S);
+  Params<double> P = params_from<double>(*S);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long n = 0; n < n_out; ++n) y[n] = output_sample(*S, P, imgs, x, Ns, n);
+}
+
+// Adjoint with respect to the source signal: dx = A^T dy, with A the linear map
+// x -> y defined above, written as the plain transpose sum
+// dx[m0_i(n) - k] += dy[n] A_i(n) w(alpha_i(n)+k) sinc(alpha_i(n)+k).
+void oracle_adjoint_x(const OracleScene* S, const double* dy, long n_out, long Ns, double* dx) {
+  std::vector<Image> imgs = enumerate_images(*S);
+  Params<double> P = params_from<double>(*S);
+  int nthr = 1;
+#ifdef _OPENMP
+  nthr = omp_get_max_threads();
+#endif
+  std::vector<std::vector<double>> part(nthr, std::vector<double>(Ns, 0.0));
+#pragma omp parallel
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    std::vector<double>& acc = part[tid];
+#pragma omp for schedule(dynamic, 16)
+    for (long n = 0; n < n_out; ++n) {
+      if (dy[n] == 0.0) continue;
+      for (const Image& im : imgs) {
+        double tau, g, d;
+        delay_gain(*S, P, im, n, &tau, &g, &d);
+        const double t = double(n) - tau;
+        const long m0 = static_cast<long>(std::floor(t));
+        const double alpha = t - double(m0);
+        const int half = S->taps / 2;
+        for (int k = -half; k <= half - 1; ++k) {
+          const long m = m0 - k;
+          if (m >= 0 && m < Ns) acc[m] += dy[n] * g * tap_weight(*S, k, alpha);
+        }
+      }
+    }
+  }
+  for (long m = 0; m < Ns; ++m) {
+    double s = 0.0;
+    for (int t = 0; t < nthr; ++t) s += part[t][m];
+    dx[m] = s;
+  }
+}
+
+// Loss 0.5 * sum_n (y[n] - target[n])^2 over n in [0, n_out).
+double oracle_loss(const OracleScene* S, const double* x, long Ns, long n_out, const double* target) {
+  std::vector<double> y(n_out);
+  oracle_synthesize(S, x, Ns, n_out, y.data());
+  double L = 0.0;
+  for (long n = 0; n < n_out; ++n) L += 0.5 * (y[n] - target[n]) * (y[n] - target[n]);
+  return L;
+}
+
+// Complex-step derivatives of the loss: for each requested parameter q,
+// param_ids[q] < 48 selects traj[param_ids[q]], 48..53 selects beta[param_ids[q]-48];
+// grad[q] = Im(L(theta + i h e_q)) / h.
+void oracle_loss_grad_cs(const OracleScene* S, const double* x, long Ns, long n_out,
+                         const double* target, const int32_t* param_ids, long n_params,
+                         double h, double* grad) {
+  std::vector<Image> imgs = enumerate_images(*S);
+  for (long q = 0; q < n_params; ++q) {
+    Params<cplx> P = params_from<cplx>(*S);
+    const int id = param_ids[q];
+    if (id < 48) P.traj[id] += cplx(0.0, h);
+    else P.beta[id - 48] += cplx(0.0, h);
+    double im_sum = 0.0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : im_sum)
+    for (long n = 0; n < n_out; ++n) {
+      cplx y = output_sample(*S, P, imgs, x, Ns, n);
+      cplx r = y - target[n];
+      im_sum += (0.5 * r * r).imag();
+    }
+    grad[q] = im_sum / h;
+  }
+}
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+}  // extern "C"

@@ -1,0 +1,21 @@
+"""Test helpers: turn a workload SceneSpec into the oracle's plain scene."""
+import numpy as np
+
+from oracle import api as oracle
+from paper_2508_03065_gb300 import workloads as W
+
+
+def oracle_scene(spec: W.SceneSpec, mic: int = 0, **override) -> oracle.Scene:
+    kw = dict(
+        dims=spec.dims, beta=spec.beta, mic=list(np.asarray(spec.mics)[mic]), K=spec.K,
+        fs=spec.fs, c=spec.c, tiers=spec.tier_steps(), taps=spec.taps, window=spec.window,
+        kaiser_beta=spec.kaiser_beta, traj_kind=spec.traj_kind, traj=list(spec.traj),
+        n_ctrl=spec.n_ctrl, duration=spec.duration)
+    kw.update(override)
+    return oracle.Scene(**kw)
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
