@@ -1,0 +1,296 @@
+#!/usr/bin/env python
+"""Benchmark: forward image-source synthesis of the order-20, 48 kHz scene.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+One step = one msrc_synthesize call on the order-20 scene (room 10x8x4 m,
+92 168 images, 4 s of pink noise at 48 kHz, circular trajectory): image
+enumeration and sort, trajectory knots, FP64 delay records, prefilter,
+gather-accumulate and reduction. Metric: image-samples per second
+(images x output samples x microphones / time). Under torchrun every rank
+synthesises its own scene (scene sharding, no collective on the data path);
+`value` is the total over ranks divided by the slowest rank's time.
+
+`--impl reference` times the FP64 CPU oracle (the checker of the GPU path) on
+the host cores, on a bounded sample of output samples of the same scene.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "image-samples/s (forward, order-20 48 kHz)"
+UNIT = "image-samples/s"
+
+# Algorithmic work of the synthesis kernel per image-sample (signal-side Farrow,
+# 2 segments x degree 6): 7 prefiltered values gathered from shared memory.
+Z_BYTES_PER_IMAGE_SAMPLE = 7 * 4
+# FP32 operations per image-sample: Horner 6 FMA (12), accumulate 1 FMA (2),
+# delay interpolation 1 FMA (2), fraction and segment split 4, distance 1 FMA
+# + 1 MUL (3), gain 1 division (1) -> 24.
+FLOPS_PER_IMAGE_SAMPLE = 24
+SM_COUNT = 152
+SMEM_BYTES_PER_CLK_PER_SM = 128
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=48, help="output samples timed for the oracle")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(spec, n_sample: int):
+    import numpy as np
+
+    from oracle import api as oracle
+
+    sc = oracle.Scene(dims=spec.dims, beta=spec.beta, mic=list(spec.mics[0]), K=spec.K, fs=spec.fs,
+                      c=spec.c, tiers=spec.tier_steps(), taps=spec.taps, window=spec.window,
+                      kaiser_beta=spec.kaiser_beta, traj_kind=spec.traj_kind, traj=list(spec.traj),
+                      n_ctrl=spec.n_ctrl, duration=spec.duration)
+    n_out = spec.n_in
+    idx = np.linspace(0, n_out - 1, n_sample).astype(np.int64)
+    x = spec.x.astype(np.float64)
+    n_img = oracle.image_count(spec.K)
+    t0 = time.perf_counter()
+    oracle.y_at(sc, x, idx)
+    dt = time.perf_counter() - t0
+    return {"value": n_img * n_sample / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n_sample} evenly spaced output samples x all {n_img} images of the same scene "
+                      f"(FP64, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2508_03065_gb300 import workloads as W
+
+    spec = W.config2()
+    per_step = max(4, args.cpu_sample // 4)
+    for _ in range(args.warmup):
+        cpu_baseline(spec, 4)
+    times, vals = [], []
+    cores = None
+    for _ in range(args.steps):
+        r = cpu_baseline(spec, per_step)
+        vals.append(r["value"])
+        cores = r["cores"]
+    n_img = W.image_count(spec.K)
+    value = statistics.mean(vals)
+    ms = n_img * spec.n_in / value * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(spec),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: {per_step} evenly spaced output samples x all {n_img} images"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(spec):
+    from paper_2508_03065_gb300 import workloads as W
+
+    return {"workload": spec.name, "images": W.image_count(spec.K), "n_out": spec.n_in, "fs": spec.fs,
+            "taps": spec.taps, "window": "kaiser(8)" if spec.window == 1 else "hann",
+            "tiers": [[r if r < W.RHO_INF else "rest", hz] for r, hz in spec.tiers],
+            "l2": "inputs larger than L2: the delay records (3.2 GB) are rewritten and read every step"}
+
+
+def run_gpu(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2508_03065_gb300 import api
+    from paper_2508_03065_gb300 import workloads as W
+
+    spec = W.config2()
+    if world > 1 and rank > 0:  # an independent scene per rank (own source signal)
+        spec = W.with_signal(spec, W.pink(2 + 1000 * rank, spec.n_in))
+    room = api.Room.from_spec(spec)
+    n_img = room.image_count()[0]
+    n_out = spec.n_in
+    work = n_img * n_out * room.n_mics
+    x = torch.from_numpy(spec.x).cuda()
+    y = torch.empty((room.n_mics, n_out), dtype=torch.float32, device="cuda")
+    ws = api.Workspace("cuda")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(max(args.warmup, 3)):
+        api.synthesize([room], [x], out=[y], workspace=ws)
+    api.profile_enable(True)
+    api.profile_read()
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        api.synthesize([room], [x], out=[y], workspace=ws)
+    stop.record(stream)
+    barrier()
+    clk = clocks.stop()
+    phase_ms, n_calls = api.profile_read()
+    api.profile_enable(False)
+    ms = start.elapsed_time(stop) / args.steps
+    ms = max_over_ranks(ms)
+    value = work * world / (ms * 1e-3)
+
+    # end to end through the host-buffer entry point: pinned host x -> device ->
+    # synthesis -> host y, every step
+    xh = torch.from_numpy(spec.x).pin_memory()
+    yh = torch.empty((room.n_mics, n_out), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        api.synthesize_host([room], [xh], [yh], workspace=ws)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        api.synthesize_host([room], [xh], [yh], workspace=ws)
+        torch.cuda.current_stream().synchronize()
+    barrier()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
+
+    synth_ms = phase_ms[2] / max(n_calls, 1)
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    clk_hz = sm_mhz * 1e6
+    smem_peak = SM_COUNT * SMEM_BYTES_PER_CLK_PER_SM * clk_hz / 1e9  # GB/s
+    achieved = work * Z_BYTES_PER_IMAGE_SAMPLE / (synth_ms * 1e-3) / 1e9
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clk_hz / 1e12
+    fp32 = work * FLOPS_PER_IMAGE_SAMPLE / (synth_ms * 1e-3) / 1e12
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(spec),
+        "phases_ms": {"setup": phase_ms[0] / max(n_calls, 1), "prefilter": phase_ms[1] / max(n_calls, 1),
+                      "synthesis": synth_ms, "reduction": phase_ms[3] / max(n_calls, 1)},
+        "roofline": {"bound": "smem", "kernel": "k_synth", "achieved": achieved, "peak": smem_peak,
+                     "unit": "GB/s", "frac": achieved / smem_peak, "traffic": None,
+                     "peak_source": f"{SM_COUNT} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x median SM clock "
+                                    f"{sm_mhz:.0f} MHz under load",
+                     "fp32_tflops": fp32, "fp32_peak_tflops": fp32_peak, "fp32_frac": fp32 / fp32_peak},
+        "e2e": {"value": work * world / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 4 * spec.n_in, "d2h_bytes_per_step": 4 * n_out * room.n_mics},
+        "gpu_launches": args.steps * launches_per_step(),
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(spec, args.cpu_sample)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def launches_per_step():
+    # enumerate, image table, trajectory knots, delay records, prefilter,
+    # synthesis, reduction + the radix sort's kernels (histogram, exclusive sum,
+    # 5 onesweep passes for a 34-bit key)
+    return 7 + 7
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

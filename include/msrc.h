@@ -1,0 +1,193 @@
+/*
+ * msrc.h - C ABI of the GB300 moving-source image-source synthesis library.
+ *
+ * Method: arXiv 2508.03065, "Fast Algorithm for Moving Sound Source".
+ *   - Every image source of a shoebox room (Sec. II-A, Eq. 1; lattice set
+ *     |n_x|+|n_y|+|n_z| <= max_order times 8 parities) follows the mirrored
+ *     source trajectory.
+ *   - Its distance d_i(t) to the microphone gives the delay tau_i = d_i / c and
+ *     the gain A_i = beta_i / (4 pi d_i) (Sec. II-A, text after Eq. 2).
+ *   - d_i is evaluated exactly at knots whose spacing depends on the image's
+ *     reflection count (dense for low orders, sparse for high orders) and is
+ *     linearly interpolated to audio rate (Sec. II-C, "Fast Architecture").
+ *   - Each image is a discrete time-varying fractional delay realised with a
+ *     Farrow structure (Sec. II-B, Eq. 3-5) approximating an L-tap windowed
+ *     sinc (Hann or Kaiser); the outputs of all images are summed (Eq. 8).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an msrc_status; nothing aborts and no C++ exception
+ *     crosses this boundary. msrc_last_error() gives a thread-local message
+ *     describing the last failure of the calling thread.
+ *   - Device work is asynchronous on the given stream (a cudaStream_t passed
+ *     as void*, NULL = legacy default stream). Device-side errors (a bounded
+ *     wait that timed out, a window clamp) are recorded in the workspace and
+ *     reported by msrc_workspace_errors().
+ *   - Device buffers (signals, outputs, workspace) are owned by the caller; the
+ *     library never allocates device memory and never frees caller memory.
+ *     Rooms are host objects owned by the library between create and destroy.
+ *   - Device pointers must be 16-byte aligned; host arrays are read during the
+ *     call only.
+ *   - Units: metres, seconds, Hz. Wall order everywhere: x=0, x=Lx, y=0, y=Ly,
+ *     z=0, z=Lz.
+ */
+#ifndef MSRC_H
+#define MSRC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MSRC_OK = 0,
+  MSRC_ERR_INVALID_ARG = 1,  /* null pointer, out-of-range value, geometry not valid */
+  MSRC_ERR_UNSUPPORTED = 2,  /* valid request outside what this build handles */
+  MSRC_ERR_WORKSPACE = 3,    /* workspace too small or misaligned */
+  MSRC_ERR_CUDA = 4,         /* a CUDA runtime call failed (message in msrc_last_error) */
+  MSRC_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+  MSRC_ERR_STATE = 6         /* call made on an object in the wrong state */
+} msrc_status;
+
+typedef struct msrc_room* msrc_room_t;
+
+#define MSRC_MAX_TIERS 4
+#define MSRC_MAX_MICS 16
+#define MSRC_MAX_ORDER 60
+#define MSRC_MAX_CTRL 16
+
+/* Room and synthesis parameters (Sec. II-A, II-B, II-C). */
+typedef struct {
+  double dims[3];            /* room size Lx, Ly, Lz (m), each > 0 */
+  double beta[6];            /* pressure reflection coefficient per wall, in [0, 1] */
+  double c;                  /* speed of sound (m/s), > 0 */
+  double fs;                 /* audio sample rate (Hz), > 0 */
+  int32_t max_order;         /* image set |n_x|+|n_y|+|n_z| <= max_order, 0..MSRC_MAX_ORDER */
+  int32_t n_tiers;           /* 1..MSRC_MAX_TIERS sampling tiers */
+  int32_t tier_max_rho[4];   /* an image with reflection count rho = sum_d |2 n_d - p_d| goes to
+                                the first tier t with rho <= tier_max_rho[t], else to the last */
+  double tier_rate_hz[4];    /* knot rate of each tier; fs / rate must be an integer >= 1 */
+  int32_t taps;              /* fractional-delay length L: even, 8..64 */
+  int32_t window;            /* 0 = Hann, 1 = Kaiser */
+  double kaiser_beta;        /* Kaiser shape (used when window == 1), 0..20 */
+} msrc_room_desc;
+
+/* Source trajectory s(t) (Sec. II-C: a band-limited trajectory p(n)). */
+typedef struct {
+  int32_t kind;              /* 0 line, 1 circle, 2 clamped uniform cubic B-spline */
+  int32_t n_ctrl;            /* spline: number of control points, 4..MSRC_MAX_CTRL */
+  double params[48];         /* line:   p0[3], direction[3] (any length > 0), speed v
+                                circle: centre[3], radius R, speed v, start angle theta0
+                                        (s = centre + R (cos, sin, 0)(theta0 + v t / R))
+                                spline: control points P_0..P_{n_ctrl-1}, 3 doubles each */
+  double duration_s;         /* trajectory duration T (> 0); the spline parameter is
+                                u = clamp(t / T, 0, 1) */
+} msrc_traj_desc;
+
+/* Creates a room; validates the description and fits the Farrow coefficients
+ * of the windowed-sinc fractional delay (Sec. II-B, Eq. 3-4) on the host.
+ * *out receives a library-owned handle. No device call is made. */
+msrc_status msrc_create_room(const msrc_room_desc* desc, msrc_room_t* out);
+
+/* Destroys a room handle (NULL is accepted). Device work that used it must have
+ * completed or been enqueued (the library keeps no device state per room). */
+msrc_status msrc_destroy_room(msrc_room_t room);
+
+/* Sets the source trajectory and the static microphone positions
+ * (mics_xyz: n_mics x 3 doubles, host memory, 1 <= n_mics <= MSRC_MAX_MICS).
+ * Validation: microphones strictly inside the room; the trajectory sampled
+ * every millisecond over [0, T] stays strictly inside the room, at least 0.1 m
+ * from every microphone, with speed below c. */
+msrc_status msrc_set_trajectory(msrc_room_t room, const msrc_traj_desc* traj,
+                                const double* mics_xyz, int32_t n_mics);
+
+/* Workspace bytes needed by msrc_synthesize (*fwd_bytes) and by
+ * msrc_synthesize_backward (*bwd_bytes) for these rooms, input lengths
+ * n_in[r] and output lengths n_out[r] (host arrays of n_rooms entries).
+ * Either output pointer may be NULL. */
+msrc_status msrc_workspace_size(const msrc_room_t* rooms, int32_t n_rooms,
+                                const int64_t* n_in, const int64_t* n_out,
+                                size_t* fwd_bytes, size_t* bwd_bytes);
+
+/* Forward synthesis, Eq. 8: for every room r and microphone m,
+ *   y_dev[r][m * n_out[r] + n] = sum_i A_i(n) * (fractional delay of x_dev[r] by tau_i(n))
+ * for n in [0, n_out[r]). x_dev[r]: n_in[r] floats (device); x is zero outside
+ * [0, n_in). y_dev[r]: n_mics x n_out[r] floats (device), fully overwritten.
+ * rooms, x_dev, n_in, y_dev, n_out are host arrays of n_rooms entries; all rooms
+ * must share taps, window and kaiser_beta. n_rooms > 1 runs every scene in the
+ * same launches (one persistent synthesis launch over a work queue).
+ * workspace_dev: >= msrc_workspace_size(...).fwd_bytes, 256-byte aligned.
+ * The result is bitwise reproducible for the same inputs and workspace size. */
+msrc_status msrc_synthesize(const msrc_room_t* rooms, int32_t n_rooms,
+                            const float* const* x_dev, const int64_t* n_in,
+                            float* const* y_dev, const int64_t* n_out,
+                            void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Same computation with HOST signal buffers: x_host[r] is copied to the
+ * workspace, the scene is synthesised and y is copied back into y_host[r]
+ * (n_mics x n_out[r] floats), all enqueued on `stream`. The caller synchronises
+ * the stream before reading y_host; pinned host memory makes the copies
+ * asynchronous. Workspace: msrc_workspace_size(...).fwd_bytes plus the signal
+ * bytes (sum_r 4*(n_in[r] + n_mics*n_out[r]), each rounded up to 256). */
+msrc_status msrc_synthesize_host(const msrc_room_t* rooms, int32_t n_rooms,
+                                 const float* const* x_host, const int64_t* n_in,
+                                 float* const* y_host, const int64_t* n_out,
+                                 void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Extra workspace bytes msrc_synthesize_host needs on top of the forward size. */
+msrc_status msrc_host_io_bytes(const msrc_room_t* rooms, int32_t n_rooms,
+                               const int64_t* n_in, const int64_t* n_out, size_t* bytes);
+
+/* Adjoint of msrc_synthesize (reverse mode), for an upstream gradient
+ * dy_dev[r] (n_mics x n_out[r] floats, device) of a scalar loss:
+ *   dx_dev[r]     (n_in[r] floats, device, nullable): dL/dx
+ *   dparams_dev[r] (48 doubles, device, nullable): dL/d traj.params (spline
+ *                 control points; line p0 and speed; circle centre, radius and speed)
+ *   dbeta_dev[r]  (6 doubles, device, nullable): dL/d beta per wall
+ * Delays are recomputed from the trajectory, not stored. Reductions use a fixed
+ * order, so results are bitwise reproducible. The rooms, signals and lengths must
+ * be those of the forward call whose output dy refers to. */
+msrc_status msrc_synthesize_backward(const msrc_room_t* rooms, int32_t n_rooms,
+                                     const float* const* x_dev, const int64_t* n_in,
+                                     const float* const* dy_dev, const int64_t* n_out,
+                                     float* const* dx_dev, double* const* dparams_dev,
+                                     double* const* dbeta_dev,
+                                     void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Reads (and clears) the device-side error word of a workspace used by the
+ * calls above; synchronises `stream`. *flags receives a bit set:
+ * 1 = a bounded wait gave up, 2 = a shared-memory window had to be clamped. */
+msrc_status msrc_workspace_errors(void* workspace_dev, void* stream, uint32_t* flags);
+
+/* Number of images of a room and, per tier, how many fall in it (host only).
+ * per_tier: MSRC_MAX_TIERS entries, nullable. */
+msrc_status msrc_room_image_count(msrc_room_t room, int64_t* count, int64_t* per_tier);
+
+/* Maximum absolute error, over a dense grid of fractional delays, of the fitted
+ * Farrow polynomials against the exact windowed sinc (host only). */
+msrc_status msrc_room_fit_error(msrc_room_t room, double* max_abs_error);
+
+/* Tuning of the synthesis launch: selects a tile configuration id (0 = default)
+ * for subsequent calls in this process; msrc_tile_configs lists how many exist. */
+msrc_status msrc_set_tile_config(int32_t config_id);
+int32_t msrc_tile_configs(void);
+
+/* Per-phase timing with CUDA events recorded on the launching stream of every
+ * subsequent msrc_synthesize call (at most 256 calls between reads).
+ * msrc_profile_read synchronises on the recorded events and returns, summed
+ * over the calls since the previous read, the milliseconds of the phases
+ * ms[0] setup (image enumeration and sort, trajectory knots, delay records),
+ * ms[1] prefilter, ms[2] synthesis (gather-accumulate), ms[3] reduction;
+ * *n_calls receives the number of calls summed. */
+msrc_status msrc_profile_enable(int32_t on);
+msrc_status msrc_profile_read(double* ms, int32_t* n_calls);
+
+const char* msrc_status_string(msrc_status status);
+const char* msrc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSRC_H */

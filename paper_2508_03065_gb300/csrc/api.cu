@@ -1,0 +1,787 @@
+// Host side of the msrc C ABI: validation, Farrow coefficient fit, workspace
+// planning and launch sequencing. See include/msrc.h for the contract.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "msrc_internal.h"
+
+namespace msrc {
+int tile_config_count();
+int tile_samples(int cfg);
+int tile_block_images(int cfg);
+cudaError_t launch_backward(const KernelArgs& a, const float* const* dy, float* const* dx,
+                            double* const* dparams, double* const* dbeta, cudaStream_t st);
+size_t backward_extra_bytes(const KernelArgs& a);
+}  // namespace msrc
+
+using namespace msrc;
+
+struct msrc_room {
+  msrc_room_desc d;
+  int32_t tier_step[MSRC_MAX_TIERS];
+  int64_t n_images;
+  int64_t tier_count[MSRC_MAX_TIERS];
+  int kL;  // tap template length (16, 32 or 64)
+  float farrow[kFarrowSegs][kFarrowCoef][kMaxTaps];
+  double fit_error;
+  bool has_traj;
+  msrc_traj_desc traj;
+  double mics[MSRC_MAX_MICS][3];
+  int32_t n_mics;
+  double validated_until;  // trajectory checked on [0, validated_until]
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+int g_tile_config = 0;
+
+// Optional per-phase timing with CUDA events recorded on the launching stream.
+// Phases: 0 setup (images, sort, knots, records), 1 prefilter, 2 synthesis, 3 reduction.
+constexpr int kPhases = 4;
+constexpr int kProfSets = 256;
+struct Profiler {
+  bool on = false;
+  cudaEvent_t ev[kProfSets][kPhases + 1];
+  int next = 0, pending = 0;
+} g_prof;
+
+msrc_status fail(msrc_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+msrc_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(MSRC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr double kPiD = 3.14159265358979323846;
+
+// ---------------------------------------------------------------- windowed sinc
+double bessel_i0(double x) {
+  // I0(x) = sum_j ((x/2)^j / j!)^2
+  double sum = 1.0, term = 1.0;
+  for (int j = 1; j < 200; ++j) {
+    term *= (x * 0.5) / j;
+    const double t2 = term * term;
+    sum += t2;
+    if (t2 < 1e-18 * sum) break;
+  }
+  return sum;
+}
+
+double window_fn(const msrc_room_desc& d, double u) {
+  const double L = d.taps;
+  if (d.window == 0) return 0.5 * (1.0 + std::cos(2.0 * kPiD * u / L));
+  const double r = 2.0 * u / L;
+  const double z = std::max(0.0, 1.0 - r * r);
+  return bessel_i0(d.kaiser_beta * std::sqrt(z)) / bessel_i0(d.kaiser_beta);
+}
+
+double kernel_fn(const msrc_room_desc& d, double u) {
+  const double s = (u == 0.0) ? 1.0 : std::sin(kPiD * u) / (kPiD * u);
+  return window_fn(d, u) * s;
+}
+
+// Farrow coefficients (Sec. II-B, Eq. 3-4): for tap k and segment s of the
+// fractional delay alpha in [s/S, (s+1)/S), h(k; alpha) ~ sum_q c[s][q][k] v^q
+// with v = 2 (alpha S - s) - 1. Interpolation at the Chebyshev nodes of v
+// (near-minimax); the error against the exact windowed sinc is measured on a
+// dense grid with the float coefficients the device uses.
+void fit_farrow(msrc_room& R) {
+  const int L = R.d.taps;
+  const int kL = R.kL;
+  const int P = kFarrowCoef;
+  std::memset(R.farrow, 0, sizeof(R.farrow));
+  double worst = 0.0;
+  for (int s = 0; s < kFarrowSegs; ++s)
+    for (int k = -L / 2; k <= L / 2 - 1; ++k) {
+      double V[kFarrowCoef][kFarrowCoef + 1];
+      for (int i = 0; i < P; ++i) {
+        const double v = std::cos(kPiD * (i + 0.5) / P);
+        const double alpha = (s + 0.5 * (v + 1.0)) / kFarrowSegs;
+        double pw = 1.0;
+        for (int q = 0; q < P; ++q) { V[i][q] = pw; pw *= v; }
+        V[i][P] = kernel_fn(R.d, alpha + k);
+      }
+      // Gaussian elimination with partial pivoting
+      for (int col = 0; col < P; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < P; ++r)
+          if (std::fabs(V[r][col]) > std::fabs(V[piv][col])) piv = r;
+        if (piv != col)
+          for (int c = 0; c <= P; ++c) std::swap(V[col][c], V[piv][c]);
+        for (int r = col + 1; r < P; ++r) {
+          const double f = V[r][col] / V[col][col];
+          for (int c = col; c <= P; ++c) V[r][c] -= f * V[col][c];
+        }
+      }
+      double coef[kFarrowCoef];
+      for (int r = P - 1; r >= 0; --r) {
+        double acc = V[r][P];
+        for (int c = r + 1; c < P; ++c) acc -= V[r][c] * coef[c];
+        coef[r] = acc / V[r][r];
+      }
+      for (int q = 0; q < P; ++q) R.farrow[s][q][k + kL / 2] = float(coef[q]);
+      for (int g = 0; g <= 400; ++g) {
+        const double v = -1.0 + 2.0 * g / 400.0;
+        const double alpha = (s + 0.5 * (v + 1.0)) / kFarrowSegs;
+        double e = 0.0;
+        for (int q = P - 1; q >= 0; --q) e = e * v + double(R.farrow[s][q][k + kL / 2]);
+        worst = std::max(worst, std::fabs(e - kernel_fn(R.d, alpha + k)));
+      }
+    }
+  R.fit_error = worst;
+}
+
+// ---------------------------------------------------------------- geometry
+int64_t count_images(int K) {
+  return 8LL * (2 * K + 1) * (2LL * K * K + 2 * K + 3) / 3;
+}
+
+int tier_of(const msrc_room_desc& d, int rho) {
+  for (int t = 0; t < d.n_tiers; ++t)
+    if (rho <= d.tier_max_rho[t]) return t;
+  return d.n_tiers - 1;
+}
+
+void count_tiers(msrc_room& R) {
+  for (int t = 0; t < MSRC_MAX_TIERS; ++t) R.tier_count[t] = 0;
+  const int K = R.d.max_order;
+  for (int nx = -K; nx <= K; ++nx)
+    for (int ny = -K; ny <= K; ++ny)
+      for (int nz = -K; nz <= K; ++nz) {
+        if (std::abs(nx) + std::abs(ny) + std::abs(nz) > K) continue;
+        for (int pb = 0; pb < 8; ++pb) {
+          const int n[3] = {nx, ny, nz};
+          int rho = 0;
+          for (int d = 0; d < 3; ++d) rho += std::abs(2 * n[d] - ((pb >> d) & 1));
+          R.tier_count[tier_of(R.d, rho)]++;
+        }
+      }
+  R.n_images = count_images(K);
+}
+
+void host_source(const msrc_traj_desc& T, double t, double out[3]) {
+  const double* p = T.params;
+  if (T.kind == 0) {
+    const double nrm = std::sqrt(p[3] * p[3] + p[4] * p[4] + p[5] * p[5]);
+    for (int d = 0; d < 3; ++d) out[d] = p[d] + p[6] * t * p[3 + d] / nrm;
+  } else if (T.kind == 1) {
+    const double a = p[5] + p[4] * t / p[3];
+    out[0] = p[0] + p[3] * std::cos(a);
+    out[1] = p[1] + p[3] * std::sin(a);
+    out[2] = p[2];
+  } else {
+    // uniform clamped cubic B-spline via de Boor
+    const int m = T.n_ctrl - 3;
+    double u = std::min(1.0, std::max(0.0, t / T.duration_s));
+    const int span = std::min(int(u * m), m - 1);
+    auto knot = [m](int i) { return std::min(1.0, std::max(0.0, double(i - 3) / m)); };
+    double dd[4][3];
+    for (int j = 0; j < 4; ++j)
+      for (int c = 0; c < 3; ++c) dd[j][c] = p[3 * (span + j) + c];
+    const int k = span + 3;
+    for (int r = 1; r <= 3; ++r)
+      for (int j = 3; j >= r; --j) {
+        const int i = j + k - 3;
+        const double den = knot(i + 4 - r) - knot(i);
+        const double al = den > 0 ? (u - knot(i)) / den : 0.0;
+        for (int c = 0; c < 3; ++c) dd[j][c] = (1 - al) * dd[j - 1][c] + al * dd[j][c];
+      }
+    for (int c = 0; c < 3; ++c) out[c] = dd[3][c];
+  }
+}
+
+msrc_status validate_traj_range(msrc_room& R, double t_end) {
+  if (t_end <= R.validated_until) return MSRC_OK;
+  const double dt = 1e-3;
+  const long steps = long(std::ceil(t_end / dt));
+  double prev[3];
+  host_source(R.traj, 0.0, prev);
+  for (long i = 0; i <= steps; ++i) {
+    const double t = std::min(i * dt, t_end);
+    double s[3];
+    host_source(R.traj, t, s);
+    for (int d = 0; d < 3; ++d)
+      if (!(s[d] > 0.0 && s[d] < R.d.dims[d]))
+        return fail(MSRC_ERR_INVALID_ARG, "trajectory leaves the room at t=%.4f s", t);
+    for (int m = 0; m < R.n_mics; ++m) {
+      double q = 0;
+      for (int d = 0; d < 3; ++d) q += (s[d] - R.mics[m][d]) * (s[d] - R.mics[m][d]);
+      if (std::sqrt(q) < 0.1)
+        return fail(MSRC_ERR_INVALID_ARG, "trajectory within 0.1 m of microphone %d at t=%.4f s", m, t);
+    }
+    if (i > 0) {
+      double q = 0;
+      for (int d = 0; d < 3; ++d) q += (s[d] - prev[d]) * (s[d] - prev[d]);
+      if (std::sqrt(q) >= R.d.c * dt)
+        return fail(MSRC_ERR_INVALID_ARG, "trajectory speed reaches c near t=%.4f s", t);
+    }
+    std::memcpy(prev, s, sizeof(prev));
+  }
+  R.validated_until = t_end;
+  return MSRC_OK;
+}
+
+// ---------------------------------------------------------------- planning
+inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Plan {
+  std::vector<SceneDev> scenes;
+  std::vector<int64_t> prefix[6];
+  int64_t totals[6] = {0, 0, 0, 0, 0, 0};
+  int end_bit = 40;
+  // byte offsets in the workspace
+  size_t off_desc = 0, off_keys_in = 0, off_keys_out = 0, off_vals_in = 0, off_vals_out = 0;
+  size_t off_sort = 0, sort_bytes = 0, off_code = 0, off_gain = 0, off_knots = 0, off_rec = 0;
+  size_t off_z = 0, off_part = 0, fwd_bytes = 0, desc_bytes = 0;
+  int kL = 32;
+  int taps = 32;
+};
+
+msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, const int64_t* n_out,
+                      Plan& P) {
+  if (!rooms || n <= 0 || !n_in || !n_out)
+    return fail(MSRC_ERR_INVALID_ARG, "null rooms/lengths or n_rooms <= 0");
+  const int cfg = g_tile_config;
+  const int T = tile_samples(cfg);
+  const int B = tile_block_images(cfg);
+  P.scenes.resize(n);
+  for (auto& v : P.prefix) v.assign(n + 1, 0);
+  int64_t img_acc = 0, knot_acc = 0, rec_acc = 0, z_acc = 0, part_acc = 0;
+  for (int s = 0; s < n; ++s) {
+    msrc_room* R = rooms[s];
+    if (!R) return fail(MSRC_ERR_INVALID_ARG, "room %d is null", s);
+    if (!R->has_traj) return fail(MSRC_ERR_STATE, "room %d has no trajectory", s);
+    if (n_in[s] <= 0 || n_out[s] <= 0 || n_in[s] > (int64_t(1) << 24) || n_out[s] > (int64_t(1) << 24))
+      return fail(MSRC_ERR_INVALID_ARG, "room %d: lengths must be in [1, 2^24]", s);
+    if (s > 0) {
+      const msrc_room* R0 = rooms[0];
+      if (R->d.taps != R0->d.taps || R->d.window != R0->d.window ||
+          (R->d.window == 1 && R->d.kaiser_beta != R0->d.kaiser_beta))
+        return fail(MSRC_ERR_UNSUPPORTED, "rooms in one call must share taps and window");
+    }
+    SceneDev& S = P.scenes[s];
+    std::memset(&S, 0, sizeof(S));
+    for (int d = 0; d < 3; ++d) S.dims[d] = R->d.dims[d];
+    for (int w = 0; w < 6; ++w) S.beta[w] = R->d.beta[w];
+    S.c = R->d.c;
+    S.fs = R->d.fs;
+    S.duration = R->traj.duration_s;
+    for (int m = 0; m < R->n_mics; ++m)
+      for (int d = 0; d < 3; ++d) S.mics[m][d] = R->mics[m][d];
+    std::memcpy(S.traj, R->traj.params, sizeof(S.traj));
+    S.traj_kind = R->traj.kind;
+    S.n_ctrl = R->traj.n_ctrl;
+    S.K = R->d.max_order;
+    S.n_mics = R->n_mics;
+    S.n_tiers = R->d.n_tiers;
+    S.n_images = int32_t(R->n_images);
+    S.n_in = n_in[s];
+    S.n_out = n_out[s];
+    S.tile = T;
+    S.block_images = B;
+    S.n_tiles = int32_t((n_out[s] + T - 1) / T);
+    S.c_over_fs = float(R->d.c / R->d.fs);
+    int first = 0, blk = 0;
+    int64_t kfirst = 0, rfirst = 0, rbase = 0;
+    int max_step = 1;
+    for (int t = 0; t < S.n_tiers; ++t) {
+      const int N = R->tier_step[t];
+      max_step = std::max(max_step, N);
+      S.tier_max_rho[t] = R->d.tier_max_rho[t];
+      S.tier_step[t] = N;
+      S.tier_count[t] = int32_t(R->tier_count[t]);
+      S.tier_first[t] = first;
+      first += S.tier_count[t];
+      const int J = int((n_out[s] - 1) / N + 1);
+      S.tier_intervals[t] = J;
+      S.tier_blocks[t] = (S.tier_count[t] + B - 1) / B;
+      S.block_first[t] = blk;
+      blk += S.tier_blocks[t];
+      S.knot_base[t] = knot_acc + kfirst;
+      S.knot_units_first[t] = kfirst;
+      kfirst += J + 1;
+      S.rec_units_first[t] = rfirst;
+      rfirst += int64_t(S.tier_count[t]) * ((J + kKnotChunk - 1) / kKnotChunk);
+      S.rec_base[t] = rec_acc + rbase;
+      rbase += int64_t(S.tier_count[t]) * J;
+    }
+    S.rec_units_first[S.n_tiers] = rfirst;
+    S.n_blocks = blk;
+    S.rec_mic_stride = rbase;
+    S.img_base = img_acc;
+    // z rows cover every read position: n - tau with tau in [0, tau_bound]
+    double maxL = 0, diag = 0;
+    for (int d = 0; d < 3; ++d) { maxL = std::max(maxL, R->d.dims[d]); diag += R->d.dims[d] * R->d.dims[d]; }
+    const double dmax = 2.0 * S.K * maxL + 2.0 * std::sqrt(diag) + 1.0;
+    const int64_t tau_bound = int64_t(std::ceil(dmax * R->d.fs / R->d.c)) + 2;
+    const int64_t zlo = -tau_bound - 16;
+    const int64_t zhi = std::max(n_out[s], n_in[s] + R->d.taps) + 16;
+    S.z_m0 = (zlo - 3) / 4 * 4;  // round toward -inf to a multiple of 4 (zlo < 0)
+    S.z_len = ((zhi - S.z_m0) + 3) / 4 * 4;
+    S.z_base = z_acc;
+    S.part_base = part_acc;
+    // trajectory evaluated up to the last knot
+    const double t_last = double(((n_out[s] - 1) / max_step + 1) * max_step) / R->d.fs;
+    msrc_status vs = validate_traj_range(*R, std::max(t_last, R->traj.duration_s));
+    if (vs != MSRC_OK) return vs;
+
+    const int64_t u_enum = S.n_images;
+    const int64_t u_knots = kfirst;
+    const int64_t u_rec = int64_t(S.n_mics) * rfirst;
+    const int64_t u_z = (S.z_len + 255) / 256;
+    const int64_t u_item = int64_t(S.n_mics) * S.n_blocks * S.n_tiles;
+    const int64_t u_red = int64_t(S.n_mics) * S.n_out;
+    const int64_t u[6] = {u_enum, u_knots, u_rec, u_z, u_item, u_red};
+    for (int k = 0; k < 6; ++k) {
+      P.prefix[k][s + 1] = P.prefix[k][s] + u[k];
+      P.totals[k] += u[k];
+    }
+    img_acc += S.n_images;
+    knot_acc += kfirst;
+    rec_acc += int64_t(S.n_mics) * rbase;
+    z_acc += int64_t(kZRows) * S.z_len;
+    part_acc += int64_t(S.n_mics) * S.n_blocks * S.n_out;
+  }
+  P.taps = rooms[0]->d.taps;
+  P.kL = rooms[0]->kL;
+  P.end_bit = 40;
+  while ((int64_t(1) << (P.end_bit - 40)) < n) ++P.end_bit;
+  // workspace layout
+  size_t off = 256;  // error word + work counter
+  P.desc_bytes = (n > 1) ? n * sizeof(SceneDev) + 6 * (n + 1) * sizeof(int64_t) : 0;
+  P.off_desc = off; off = align256(off + P.desc_bytes);
+  const size_t I = size_t(img_acc);
+  P.off_keys_in = off; off = align256(off + 8 * I);
+  P.off_keys_out = off; off = align256(off + 8 * I);
+  P.off_vals_in = off; off = align256(off + 4 * I);
+  P.off_vals_out = off; off = align256(off + 4 * I);
+  P.sort_bytes = sort_temp_bytes(int64_t(I), P.end_bit);
+  P.off_sort = off; off = align256(off + P.sort_bytes);
+  P.off_code = off; off = align256(off + 4 * I);
+  P.off_gain = off; off = align256(off + 4 * I);
+  P.off_knots = off; off = align256(off + 24 * size_t(knot_acc));
+  P.off_rec = off; off = align256(off + 16 * size_t(rec_acc));
+  P.off_z = off; off = align256(off + 4 * size_t(z_acc));
+  P.off_part = off; off = align256(off + 4 * size_t(part_acc));
+  P.fwd_bytes = off;
+  if (I > (size_t(1) << 31)) return fail(MSRC_ERR_UNSUPPORTED, "more than 2^31 images in one call");
+  return MSRC_OK;
+}
+
+void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a) {
+  std::memset(&a, 0, sizeof(a));
+  a.n_scenes = int32_t(P.scenes.size());
+  if (a.n_scenes == 1) a.scene0 = P.scenes[0];
+  for (int k = 0; k < 6; ++k) a.totals[k] = P.totals[k];
+  a.p.err = reinterpret_cast<uint32_t*>(ws);
+  a.p.counter = reinterpret_cast<uint32_t*>(ws + 4);
+  a.p.keys_in = reinterpret_cast<uint64_t*>(ws + P.off_keys_in);
+  a.p.keys_out = reinterpret_cast<uint64_t*>(ws + P.off_keys_out);
+  a.p.vals_in = reinterpret_cast<uint32_t*>(ws + P.off_vals_in);
+  a.p.vals_out = reinterpret_cast<uint32_t*>(ws + P.off_vals_out);
+  a.p.sort_temp = ws + P.off_sort;
+  a.p.sort_temp_bytes = P.sort_bytes;
+  a.p.img_code = reinterpret_cast<uint32_t*>(ws + P.off_code);
+  a.p.img_gain = reinterpret_cast<float*>(ws + P.off_gain);
+  a.p.knot_pos = reinterpret_cast<double*>(ws + P.off_knots);
+  a.p.rec = reinterpret_cast<int4*>(ws + P.off_rec);
+  a.p.z = reinterpret_cast<float*>(ws + P.off_z);
+  a.p.part = reinterpret_cast<float*>(ws + P.off_part);
+  std::memcpy(a.farrow, rooms[0]->farrow, sizeof(a.farrow));
+  a.taps = P.kL;
+  if (a.n_scenes > 1) {
+    char* d = ws + P.off_desc;
+    a.scenes = reinterpret_cast<const SceneDev*>(d);
+    const int64_t* pre = reinterpret_cast<const int64_t*>(d + P.scenes.size() * sizeof(SceneDev));
+    const int n1 = a.n_scenes + 1;
+    a.tab.enum_prefix = pre;
+    a.tab.knots_prefix = pre + n1;
+    a.tab.rec_prefix = pre + 2 * n1;
+    a.tab.z_prefix = pre + 3 * n1;
+    a.tab.item_prefix = pre + 4 * n1;
+    a.tab.red_prefix = pre + 5 * n1;
+  }
+}
+
+msrc_status check_ws(const Plan& P, void* ws, size_t bytes) {
+  if (!ws) return fail(MSRC_ERR_WORKSPACE, "workspace is null");
+  if (reinterpret_cast<uintptr_t>(ws) & 255)
+    return fail(MSRC_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (bytes < P.fwd_bytes)
+    return fail(MSRC_ERR_WORKSPACE, "workspace too small: %zu < %zu bytes", bytes, P.fwd_bytes);
+  return MSRC_OK;
+}
+
+// Uploads scene descriptors and prefix tables of a batched call.
+msrc_status upload_tables(const Plan& P, char* ws, cudaStream_t st, std::vector<char>& blob) {
+  if (P.scenes.size() <= 1) return MSRC_OK;
+  blob.resize(P.desc_bytes);
+  std::memcpy(blob.data(), P.scenes.data(), P.scenes.size() * sizeof(SceneDev));
+  int64_t* pre = reinterpret_cast<int64_t*>(blob.data() + P.scenes.size() * sizeof(SceneDev));
+  const size_t n1 = P.scenes.size() + 1;
+  const int order[6] = {0, 1, 2, 3, 4, 5};
+  for (int k = 0; k < 6; ++k) std::memcpy(pre + k * n1, P.prefix[order[k]].data(), n1 * sizeof(int64_t));
+  cudaError_t e = cudaMemcpyAsync(ws + P.off_desc, blob.data(), P.desc_bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "descriptor upload");
+  return MSRC_OK;
+}
+
+msrc_status run_forward(const msrc_room_t* rooms, int32_t n, const float* const* x_dev,
+                        const int64_t* n_in, float* const* y_dev, const int64_t* n_out,
+                        void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (!x_dev || !y_dev) return fail(MSRC_ERR_INVALID_ARG, "null signal pointer array");
+  Plan P;
+  msrc_status s = make_plan(rooms, n, n_in, n_out, P);
+  if (s != MSRC_OK) return s;
+  s = check_ws(P, ws, ws_bytes);
+  if (s != MSRC_OK) return s;
+  for (int r = 0; r < n; ++r) {
+    if (!x_dev[r] || !y_dev[r]) return fail(MSRC_ERR_INVALID_ARG, "room %d: null x or y", r);
+    if ((reinterpret_cast<uintptr_t>(x_dev[r]) | reinterpret_cast<uintptr_t>(y_dev[r])) & 15)
+      return fail(MSRC_ERR_INVALID_ARG, "room %d: x and y must be 16-byte aligned", r);
+    P.scenes[r].x = x_dev[r];
+    P.scenes[r].y = y_dev[r];
+  }
+  char* w = static_cast<char*>(ws);
+  KernelArgs* a = new (std::nothrow) KernelArgs;
+  if (!a) return fail(MSRC_ERR_INVALID_ARG, "out of host memory");
+  fill_args(P, rooms, w, *a);
+  std::vector<char> blob;
+  cudaError_t e = cudaMemsetAsync(w, 0, 256, st);
+  if (e != cudaSuccess) { delete a; return cuda_fail(e, "workspace header clear"); }
+  s = upload_tables(P, w, st, blob);
+  if (s != MSRC_OK) { delete a; return s; }
+  cudaEvent_t* ev = nullptr;
+  if (g_prof.on) {
+    ev = g_prof.ev[g_prof.next];
+    g_prof.next = (g_prof.next + 1) % kProfSets;
+    g_prof.pending = std::min(g_prof.pending + 1, kProfSets);
+    cudaEventRecord(ev[0], st);
+  }
+  e = launch_setup(*a, st);
+  if (ev) cudaEventRecord(ev[1], st);
+  if (e == cudaSuccess) e = launch_forward(*a, g_tile_config, st, ev ? ev + 2 : nullptr);
+  if (ev) cudaEventRecord(ev[4], st);
+  delete a;
+  if (e != cudaSuccess) return cuda_fail(e, "synthesis launch");
+  return MSRC_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+msrc_status msrc_create_room(const msrc_room_desc* desc, msrc_room_t* out) {
+  if (!desc || !out) return fail(MSRC_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const msrc_room_desc& d = *desc;
+  for (int k = 0; k < 3; ++k)
+    if (!(d.dims[k] > 0.0) || !std::isfinite(d.dims[k]))
+      return fail(MSRC_ERR_INVALID_ARG, "room dimension %d must be positive and finite", k);
+  for (int w = 0; w < 6; ++w)
+    if (!(d.beta[w] >= 0.0 && d.beta[w] <= 1.0))
+      return fail(MSRC_ERR_INVALID_ARG, "reflection coefficient %d must be in [0, 1]", w);
+  if (!(d.c > 0.0) || !std::isfinite(d.c)) return fail(MSRC_ERR_INVALID_ARG, "c must be positive");
+  if (!(d.fs > 0.0) || !std::isfinite(d.fs)) return fail(MSRC_ERR_INVALID_ARG, "fs must be positive");
+  if (d.max_order < 0 || d.max_order > MSRC_MAX_ORDER)
+    return fail(MSRC_ERR_INVALID_ARG, "max_order must be in [0, %d]", MSRC_MAX_ORDER);
+  if (d.n_tiers < 1 || d.n_tiers > MSRC_MAX_TIERS)
+    return fail(MSRC_ERR_INVALID_ARG, "n_tiers must be in [1, %d]", MSRC_MAX_TIERS);
+  if (d.taps < 8 || d.taps > kMaxTaps || (d.taps & 1))
+    return fail(MSRC_ERR_INVALID_ARG, "taps must be even and in [8, %d]", kMaxTaps);
+  if (d.window != 0 && d.window != 1) return fail(MSRC_ERR_INVALID_ARG, "window must be 0 or 1");
+  if (d.window == 1 && !(d.kaiser_beta >= 0.0 && d.kaiser_beta <= 20.0))
+    return fail(MSRC_ERR_INVALID_ARG, "kaiser_beta must be in [0, 20]");
+  msrc_room* R = new (std::nothrow) msrc_room;
+  if (!R) return fail(MSRC_ERR_INVALID_ARG, "out of host memory");
+  std::memset(R, 0, sizeof(*R));
+  R->d = d;
+  for (int t = 0; t < d.n_tiers; ++t) {
+    const double rate = d.tier_rate_hz[t];
+    if (!(rate > 0.0) || rate > d.fs) { delete R; return fail(MSRC_ERR_INVALID_ARG, "tier %d rate must be in (0, fs]", t); }
+    const double ratio = d.fs / rate;
+    const double rr = std::round(ratio);
+    if (std::fabs(ratio - rr) > 1e-9 * ratio || rr < 1 || rr > (1 << 20)) {
+      delete R;
+      return fail(MSRC_ERR_INVALID_ARG, "tier %d: fs / rate must be an integer (got %.6f)", t, ratio);
+    }
+    R->tier_step[t] = int32_t(rr);
+    if (t > 0 && d.tier_max_rho[t] < d.tier_max_rho[t - 1] && t < d.n_tiers - 1) {
+      delete R;
+      return fail(MSRC_ERR_INVALID_ARG, "tier_max_rho must be non-decreasing");
+    }
+  }
+  R->kL = d.taps <= 16 ? 16 : (d.taps <= 32 ? 32 : 64);
+  count_tiers(*R);
+  fit_farrow(*R);
+  if (R->fit_error > 1e-6) {
+    const double err = R->fit_error;
+    delete R;
+    return fail(MSRC_ERR_UNSUPPORTED, "Farrow fit error %.3g exceeds 1e-6 for this window", err);
+  }
+  *out = R;
+  return MSRC_OK;
+}
+
+msrc_status msrc_destroy_room(msrc_room_t room) {
+  delete room;
+  return MSRC_OK;
+}
+
+msrc_status msrc_set_trajectory(msrc_room_t room, const msrc_traj_desc* traj, const double* mics,
+                                int32_t n_mics) {
+  if (!room || !traj || !mics) return fail(MSRC_ERR_INVALID_ARG, "null argument");
+  if (n_mics < 1 || n_mics > MSRC_MAX_MICS)
+    return fail(MSRC_ERR_INVALID_ARG, "n_mics must be in [1, %d]", MSRC_MAX_MICS);
+  if (!(traj->duration_s > 0.0) || !std::isfinite(traj->duration_s))
+    return fail(MSRC_ERR_INVALID_ARG, "duration must be positive");
+  for (int i = 0; i < 48; ++i)
+    if (!std::isfinite(traj->params[i])) return fail(MSRC_ERR_INVALID_ARG, "non-finite trajectory parameter");
+  if (traj->kind == 0) {
+    const double* p = traj->params;
+    if (!(p[3] * p[3] + p[4] * p[4] + p[5] * p[5] > 0.0))
+      return fail(MSRC_ERR_INVALID_ARG, "line direction must be non-zero");
+  } else if (traj->kind == 1) {
+    if (!(traj->params[3] > 0.0)) return fail(MSRC_ERR_INVALID_ARG, "circle radius must be positive");
+  } else if (traj->kind == 2) {
+    if (traj->n_ctrl < 4 || traj->n_ctrl > MSRC_MAX_CTRL)
+      return fail(MSRC_ERR_INVALID_ARG, "spline needs 4..%d control points", MSRC_MAX_CTRL);
+  } else {
+    return fail(MSRC_ERR_INVALID_ARG, "unknown trajectory kind %d", traj->kind);
+  }
+  for (int m = 0; m < n_mics; ++m)
+    for (int d = 0; d < 3; ++d) {
+      const double v = mics[3 * m + d];
+      if (!(v > 0.0 && v < room->d.dims[d]))
+        return fail(MSRC_ERR_INVALID_ARG, "microphone %d is not strictly inside the room", m);
+    }
+  msrc_room saved = *room;
+  room->traj = *traj;
+  room->n_mics = n_mics;
+  for (int m = 0; m < n_mics; ++m)
+    for (int d = 0; d < 3; ++d) room->mics[m][d] = mics[3 * m + d];
+  room->validated_until = -1.0;
+  room->has_traj = true;
+  msrc_status s = validate_traj_range(*room, traj->duration_s);
+  if (s != MSRC_OK) {
+    *room = saved;
+    return s;
+  }
+  return MSRC_OK;
+}
+
+msrc_status msrc_workspace_size(const msrc_room_t* rooms, int32_t n_rooms, const int64_t* n_in,
+                                const int64_t* n_out, size_t* fwd_bytes, size_t* bwd_bytes) {
+  Plan P;
+  msrc_status s = make_plan(rooms, n_rooms, n_in, n_out, P);
+  if (s != MSRC_OK) return s;
+  if (fwd_bytes) *fwd_bytes = P.fwd_bytes;
+  if (bwd_bytes) {
+    KernelArgs* a = new (std::nothrow) KernelArgs;
+    if (!a) return fail(MSRC_ERR_INVALID_ARG, "out of host memory");
+    fill_args(P, rooms, reinterpret_cast<char*>(size_t(0)), *a);
+    *bwd_bytes = P.fwd_bytes + backward_extra_bytes(*a);
+    delete a;
+  }
+  return MSRC_OK;
+}
+
+msrc_status msrc_synthesize(const msrc_room_t* rooms, int32_t n_rooms, const float* const* x_dev,
+                            const int64_t* n_in, float* const* y_dev, const int64_t* n_out,
+                            void* ws, size_t ws_bytes, void* stream) {
+  return run_forward(rooms, n_rooms, x_dev, n_in, y_dev, n_out, ws, ws_bytes,
+                     static_cast<cudaStream_t>(stream));
+}
+
+msrc_status msrc_host_io_bytes(const msrc_room_t* rooms, int32_t n_rooms, const int64_t* n_in,
+                               const int64_t* n_out, size_t* bytes) {
+  if (!rooms || !n_in || !n_out || !bytes || n_rooms <= 0) return fail(MSRC_ERR_INVALID_ARG, "null argument");
+  size_t b = 0;
+  for (int r = 0; r < n_rooms; ++r) {
+    if (!rooms[r]) return fail(MSRC_ERR_INVALID_ARG, "room %d is null", r);
+    b += align256(4 * size_t(n_in[r])) + align256(4 * size_t(n_out[r]) * size_t(rooms[r]->n_mics));
+  }
+  *bytes = b;
+  return MSRC_OK;
+}
+
+msrc_status msrc_synthesize_host(const msrc_room_t* rooms, int32_t n_rooms, const float* const* x_host,
+                                 const int64_t* n_in, float* const* y_host, const int64_t* n_out,
+                                 void* ws, size_t ws_bytes, void* stream) {
+  if (!x_host || !y_host) return fail(MSRC_ERR_INVALID_ARG, "null host signal array");
+  Plan P;
+  msrc_status s = make_plan(rooms, n_rooms, n_in, n_out, P);
+  if (s != MSRC_OK) return s;
+  size_t io = 0;
+  s = msrc_host_io_bytes(rooms, n_rooms, n_in, n_out, &io);
+  if (s != MSRC_OK) return s;
+  if (ws_bytes < P.fwd_bytes + io)
+    return fail(MSRC_ERR_WORKSPACE, "workspace too small for host I/O: %zu < %zu", ws_bytes, P.fwd_bytes + io);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(ws) + P.fwd_bytes;
+  std::vector<const float*> xd(n_rooms);
+  std::vector<float*> yd(n_rooms);
+  size_t off = 0;
+  for (int r = 0; r < n_rooms; ++r) {
+    if (!x_host[r] || !y_host[r]) return fail(MSRC_ERR_INVALID_ARG, "room %d: null host buffer", r);
+    float* xdev = reinterpret_cast<float*>(base + off);
+    off += align256(4 * size_t(n_in[r]));
+    float* ydev = reinterpret_cast<float*>(base + off);
+    off += align256(4 * size_t(n_out[r]) * size_t(rooms[r]->n_mics));
+    cudaError_t e = cudaMemcpyAsync(xdev, x_host[r], 4 * size_t(n_in[r]), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    xd[r] = xdev;
+    yd[r] = ydev;
+  }
+  s = run_forward(rooms, n_rooms, xd.data(), n_in, yd.data(), n_out, ws, P.fwd_bytes, st);
+  if (s != MSRC_OK) return s;
+  for (int r = 0; r < n_rooms; ++r) {
+    cudaError_t e = cudaMemcpyAsync(y_host[r], yd[r], 4 * size_t(n_out[r]) * size_t(rooms[r]->n_mics),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
+  }
+  return MSRC_OK;
+}
+
+msrc_status msrc_synthesize_backward(const msrc_room_t* rooms, int32_t n_rooms, const float* const* x_dev,
+                                     const int64_t* n_in, const float* const* dy_dev, const int64_t* n_out,
+                                     float* const* dx_dev, double* const* dparams_dev,
+                                     double* const* dbeta_dev, void* ws, size_t ws_bytes, void* stream) {
+  if (!x_dev || !dy_dev) return fail(MSRC_ERR_INVALID_ARG, "null signal pointer array");
+  Plan P;
+  msrc_status s = make_plan(rooms, n_rooms, n_in, n_out, P);
+  if (s != MSRC_OK) return s;
+  s = check_ws(P, ws, ws_bytes);
+  if (s != MSRC_OK) return s;
+  for (int r = 0; r < n_rooms; ++r) {
+    if (!x_dev[r] || !dy_dev[r]) return fail(MSRC_ERR_INVALID_ARG, "room %d: null x or dy", r);
+    P.scenes[r].x = x_dev[r];
+    P.scenes[r].y = nullptr;
+  }
+  char* w = static_cast<char*>(ws);
+  KernelArgs* a = new (std::nothrow) KernelArgs;
+  if (!a) return fail(MSRC_ERR_INVALID_ARG, "out of host memory");
+  fill_args(P, rooms, w, *a);
+  const size_t need = P.fwd_bytes + backward_extra_bytes(*a);
+  if (ws_bytes < need) {
+    delete a;
+    return fail(MSRC_ERR_WORKSPACE, "workspace too small for backward: %zu < %zu", ws_bytes, need);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<char> blob;
+  cudaError_t e = cudaMemsetAsync(w, 0, 256, st);
+  if (e != cudaSuccess) { delete a; return cuda_fail(e, "workspace header clear"); }
+  s = upload_tables(P, w, st, blob);
+  if (s != MSRC_OK) { delete a; return s; }
+  e = launch_setup(*a, st);
+  if (e == cudaSuccess) e = launch_backward(*a, dy_dev, dx_dev, dparams_dev, dbeta_dev, st);
+  delete a;
+  if (e == cudaErrorNotSupported) return fail(MSRC_ERR_UNSUPPORTED, "backward not available in this build");
+  if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  return MSRC_OK;
+}
+
+msrc_status msrc_workspace_errors(void* ws, void* stream, uint32_t* flags) {
+  if (!ws || !flags) return fail(MSRC_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, ws, sizeof(v), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return cuda_fail(e, "error word read");
+  *flags = v;
+  return (v & kErrTimeout) ? MSRC_ERR_TIMEOUT : MSRC_OK;
+}
+
+msrc_status msrc_room_image_count(msrc_room_t room, int64_t* count, int64_t* per_tier) {
+  if (!room || !count) return fail(MSRC_ERR_INVALID_ARG, "null argument");
+  *count = room->n_images;
+  if (per_tier)
+    for (int t = 0; t < MSRC_MAX_TIERS; ++t) per_tier[t] = t < room->d.n_tiers ? room->tier_count[t] : 0;
+  return MSRC_OK;
+}
+
+msrc_status msrc_room_fit_error(msrc_room_t room, double* err) {
+  if (!room || !err) return fail(MSRC_ERR_INVALID_ARG, "null argument");
+  *err = room->fit_error;
+  return MSRC_OK;
+}
+
+msrc_status msrc_profile_enable(int32_t on) {
+  if (on && !g_prof.on) {
+    for (int i = 0; i < kProfSets; ++i)
+      for (int k = 0; k <= kPhases; ++k) {
+        cudaError_t e = cudaEventCreate(&g_prof.ev[i][k]);
+        if (e != cudaSuccess) return cuda_fail(e, "event creation");
+      }
+    g_prof.on = true;
+    g_prof.next = g_prof.pending = 0;
+  } else if (!on && g_prof.on) {
+    for (int i = 0; i < kProfSets; ++i)
+      for (int k = 0; k <= kPhases; ++k) cudaEventDestroy(g_prof.ev[i][k]);
+    g_prof.on = false;
+  }
+  return MSRC_OK;
+}
+
+msrc_status msrc_profile_read(double* ms, int32_t* n_calls) {
+  if (!ms || !n_calls) return fail(MSRC_ERR_INVALID_ARG, "null argument");
+  for (int k = 0; k < kPhases; ++k) ms[k] = 0.0;
+  *n_calls = 0;
+  if (!g_prof.on) return fail(MSRC_ERR_STATE, "profiling is not enabled");
+  const int n = g_prof.pending;
+  for (int c = 0; c < n; ++c) {
+    const int i = (g_prof.next - n + c + kProfSets) % kProfSets;
+    cudaError_t e = cudaEventSynchronize(g_prof.ev[i][kPhases]);
+    if (e != cudaSuccess) return cuda_fail(e, "event synchronize");
+    for (int k = 0; k < kPhases; ++k) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, g_prof.ev[i][k], g_prof.ev[i][k + 1]);
+      if (e != cudaSuccess) return cuda_fail(e, "event elapsed time");
+      ms[k] += t;
+    }
+  }
+  *n_calls = n;
+  g_prof.pending = 0;
+  return MSRC_OK;
+}
+
+msrc_status msrc_set_tile_config(int32_t id) {
+  if (id < 0 || id >= tile_config_count()) return fail(MSRC_ERR_INVALID_ARG, "tile config %d out of range", id);
+  g_tile_config = id;
+  return MSRC_OK;
+}
+
+int32_t msrc_tile_configs(void) { return tile_config_count(); }
+
+const char* msrc_status_string(msrc_status s) {
+  switch (s) {
+    case MSRC_OK: return "ok";
+    case MSRC_ERR_INVALID_ARG: return "invalid argument";
+    case MSRC_ERR_UNSUPPORTED: return "unsupported";
+    case MSRC_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case MSRC_ERR_CUDA: return "CUDA error";
+    case MSRC_ERR_TIMEOUT: return "device wait timed out";
+    case MSRC_ERR_STATE: return "invalid state";
+  }
+  return "unknown status";
+}
+
+const char* msrc_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

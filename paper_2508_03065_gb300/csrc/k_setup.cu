@@ -1,0 +1,262 @@
+// Setup kernels of the synthesis path:
+//   k_enumerate    image set of every scene (Sec. II-A, Eq. 1; lattice |n|_1 <= K,
+//                  8 parities) with a sort key (scene, tier, distance)
+//   (radix sort)   images ordered by key
+//   k_image_table  packed image codes and gains beta_i / (4 pi)
+//   k_traj_knots   source position s(t_j) at every knot of every tier, FP64
+//                  (Sec. II-C: trajectory sampled at the tier's spatial rate)
+//   k_records      exact FP64 image distances at the knots, split into an exact
+//                  integer delay and FP32 fraction, stored per interval
+//                  (Sec. II-C: tau_i = d_i / c at the hierarchical knots)
+#include <cub/device/device_radix_sort.cuh>
+
+#include "msrc_internal.h"
+
+namespace msrc {
+namespace {
+
+__device__ __forceinline__ const SceneDev& scene_of(const KernelArgs& a, int s) {
+  return a.n_scenes == 1 ? a.scene0 : a.scenes[s];
+}
+
+// Largest s with prefix[s] <= idx (prefix has n_scenes + 1 entries).
+__device__ __forceinline__ int find_scene(const int64_t* prefix, int n, int64_t idx) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= idx) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int locate(const KernelArgs& a, const int64_t* prefix, int64_t gid,
+                                      int64_t* local) {
+  if (a.n_scenes == 1) { *local = gid; return 0; }
+  int s = find_scene(prefix, a.n_scenes, gid);
+  *local = gid - prefix[s];
+  return s;
+}
+
+// Source position s(t) (FP64). Spline: clamped uniform cubic B-spline by de
+// Boor's algorithm on the knot vector {0,0,0,0, 1/m, ..., (m-1)/m, 1,1,1,1}.
+__device__ void source_position(const SceneDev& S, double t, double out[3]) {
+  const double* p = S.traj;
+  if (S.traj_kind == 0) {
+    const double inv = 1.0 / sqrt(p[3] * p[3] + p[4] * p[4] + p[5] * p[5]);
+    for (int d = 0; d < 3; ++d) out[d] = p[d] + p[6] * t * p[3 + d] * inv;
+  } else if (S.traj_kind == 1) {
+    const double ang = p[5] + p[4] * t / p[3];
+    double sn, cs;
+    sincos(ang, &sn, &cs);
+    out[0] = p[0] + p[3] * cs;
+    out[1] = p[1] + p[3] * sn;
+    out[2] = p[2];
+  } else {
+    const int m = S.n_ctrl - 3;  // segments
+    double u = t / S.duration;
+    u = fmin(1.0, fmax(0.0, u));
+    int span = min(int(u * m), m - 1);  // segment index
+    // knot i of the clamped vector: clamp((i - 3) / m, 0, 1)
+    auto knot = [m](int i) { return fmin(1.0, fmax(0.0, double(i - 3) / double(m))); };
+    double dd[4][3];
+    for (int j = 0; j < 4; ++j)
+      for (int c = 0; c < 3; ++c) dd[j][c] = p[3 * (span + j) + c];
+    const int k = span + 3;
+    for (int r = 1; r <= 3; ++r)
+      for (int j = 3; j >= r; --j) {
+        const int i = j + k - 3;
+        const double den = knot(i + 4 - r) - knot(i);
+        const double al = den > 0.0 ? (u - knot(i)) / den : 0.0;
+        for (int c = 0; c < 3; ++c) dd[j][c] = (1.0 - al) * dd[j - 1][c] + al * dd[j][c];
+      }
+    for (int c = 0; c < 3; ++c) out[c] = dd[3][c];
+  }
+}
+
+__device__ __forceinline__ int tier_of(const SceneDev& S, int rho) {
+  for (int t = 0; t < S.n_tiers; ++t)
+    if (rho <= S.tier_max_rho[t]) return t;
+  return S.n_tiers - 1;
+}
+
+__global__ void k_enumerate(const __grid_constant__ KernelArgs a) {
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= a.totals[0]) return;
+  int64_t local;
+  const int s = locate(a, a.tab.enum_prefix, gid, &local);
+  const SceneDev& S = scene_of(a, s);
+  int li = int(local >> 3);
+  const int pb = int(local & 7);
+  const int K = S.K;
+  // lattice order: n_x ascending, then n_y, then n_z, over |n|_1 <= K
+  int nx = -K;
+  for (; nx <= K; ++nx) {
+    const int r = K - abs(nx);
+    const int cnt = 2 * r * r + 2 * r + 1;
+    if (li < cnt) break;
+    li -= cnt;
+  }
+  const int r = K - abs(nx);
+  int ny = -r;
+  for (; ny <= r; ++ny) {
+    const int cnt = 2 * (r - abs(ny)) + 1;
+    if (li < cnt) break;
+    li -= cnt;
+  }
+  const int nz = -(r - abs(ny)) + li;
+  const int n[3] = {nx, ny, nz};
+  const int p[3] = {pb & 1, (pb >> 1) & 1, (pb >> 2) & 1};
+  int rho = 0;
+  for (int d = 0; d < 3; ++d) rho += abs(2 * n[d] - p[d]);
+  const int tier = tier_of(S, rho);
+  // distance to the first microphone at the middle of the trajectory
+  double sp[3];
+  source_position(S, 0.5 * S.duration, sp);
+  double acc = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double v = (1.0 - 2.0 * p[d]) * sp[d] + 2.0 * n[d] * S.dims[d] - S.mics[0][d];
+    acc += v * v;
+  }
+  const double dist = fmin(sqrt(acc), 4095.0);
+  const uint64_t dq = uint64_t(dist * 1048576.0);
+  a.p.keys_in[gid] = (uint64_t(s) << 40) | (uint64_t(tier) << 32) | dq;
+  a.p.vals_in[gid] = pack_image(nx, ny, nz, pb);
+}
+
+__global__ void k_image_table(const __grid_constant__ KernelArgs a) {
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= a.totals[0]) return;
+  int64_t local;
+  const int s = locate(a, a.tab.enum_prefix, gid, &local);
+  const SceneDev& S = scene_of(a, s);
+  const uint32_t code = a.p.vals_out[gid];
+  int n[3], p[3];
+  unpack_image(code, n, p);
+  // beta_i = prod_d beta_{d,0}^{|n_d - p_d|} beta_{d,1}^{|n_d|} (Allen-Berkley)
+  double b = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    const int e0 = abs(n[d] - p[d]), e1 = abs(n[d]);
+    for (int r = 0; r < e0; ++r) b *= S.beta[2 * d];
+    for (int r = 0; r < e1; ++r) b *= S.beta[2 * d + 1];
+  }
+  a.p.img_code[gid] = code;
+  a.p.img_gain[gid] = float(b / (4.0 * 3.14159265358979323846));
+}
+
+__global__ void k_traj_knots(const __grid_constant__ KernelArgs a) {
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= a.totals[1]) return;
+  int64_t local;
+  const int s = locate(a, a.tab.knots_prefix, gid, &local);
+  const SceneDev& S = scene_of(a, s);
+  int t = 0;
+  while (t + 1 < S.n_tiers && local >= S.knot_units_first[t + 1]) ++t;
+  const int64_t j = local - S.knot_units_first[t];
+  const double time = double(j * S.tier_step[t]) / S.fs;
+  double sp[3];
+  source_position(S, time, sp);
+  double* out = a.p.knot_pos + 3 * (S.knot_base[t] + j);
+  out[0] = sp[0];
+  out[1] = sp[1];
+  out[2] = sp[2];
+}
+
+// One thread: kKnotChunk consecutive intervals of one image for one microphone.
+// The distance is evaluated in FP64 at each knot; the delay tau = d fs / c is
+// split into an exact integer D_j and an FP32 fraction f_j; the record of
+// interval j is {n_j - D_j, f_j, (tau_{j+1} - tau_j) / N_t, d_j}.
+__global__ void k_records(const __grid_constant__ KernelArgs a) {
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= a.totals[2]) return;
+  int64_t local;
+  const int s = locate(a, a.tab.rec_prefix, gid, &local);
+  const SceneDev& S = scene_of(a, s);
+  const int64_t per_mic = S.rec_units_first[S.n_tiers];
+  const int mic = int(local / per_mic);
+  int64_t u = local - int64_t(mic) * per_mic;
+  int t = 0;
+  while (t + 1 < S.n_tiers && u >= S.rec_units_first[t + 1]) ++t;
+  u -= S.rec_units_first[t];
+  const int J = S.tier_intervals[t];
+  const int chunks = (J + kKnotChunk - 1) / kKnotChunk;
+  const int img = int(u / chunks);
+  const int j0 = int(u - int64_t(img) * chunks) * kKnotChunk;
+  const int j1 = min(j0 + kKnotChunk, J);
+  int n[3], p[3];
+  unpack_image(a.p.img_code[S.img_base + S.tier_first[t] + img], n, p);
+  double off[3], sg[3];
+  for (int d = 0; d < 3; ++d) {
+    sg[d] = 1.0 - 2.0 * p[d];
+    off[d] = 2.0 * n[d] * S.dims[d] - S.mics[mic][d];
+  }
+  const double* kp = a.p.knot_pos + 3 * S.knot_base[t];
+  const double fs_c = S.fs / S.c;
+  const int N = S.tier_step[t];
+  int4* out = a.p.rec + S.rec_base[t] + int64_t(mic) * S.rec_mic_stride + int64_t(img) * J;
+  auto tau_at = [&](int j, double* dist) {
+    double acc = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double v = sg[d] * kp[3 * j + d] + off[d];
+      acc += v * v;
+    }
+    *dist = sqrt(acc);
+    return *dist * fs_c;
+  };
+  double dj;
+  double tau = tau_at(j0, &dj);
+  for (int j = j0; j < j1; ++j) {
+    double dn;
+    const double tau_n = tau_at(j + 1, &dn);
+    const double D = floor(tau);
+    int4 r;
+    r.x = int(int64_t(j) * N - int64_t(D));
+    r.y = __float_as_int(float(tau - D));
+    r.z = __float_as_int(float((tau_n - tau) / double(N)));
+    r.w = __float_as_int(float(dj));
+    out[j] = r;
+    tau = tau_n;
+    dj = dn;
+  }
+}
+
+}  // namespace
+
+size_t sort_temp_bytes(int64_t n_items, int end_bit) {
+  size_t bytes = 0;
+  const cudaError_t e = cub::DeviceRadixSort::SortPairs(
+      nullptr, bytes, (const uint64_t*)nullptr, (uint64_t*)nullptr, (const uint32_t*)nullptr,
+      (uint32_t*)nullptr, int(n_items), 0, end_bit);
+  if (e != cudaSuccess) {
+    // no device to query (host-only size estimate): a generous bound
+    cudaGetLastError();
+    bytes = size_t(n_items) * 16 + (size_t(8) << 20);
+  }
+  return bytes;
+}
+
+cudaError_t launch_sort(const KernelArgs& a, int64_t n, int end_bit, cudaStream_t st) {
+  size_t bytes = a.p.sort_temp_bytes;
+  return cub::DeviceRadixSort::SortPairs(a.p.sort_temp, bytes, a.p.keys_in, a.p.keys_out,
+                                         a.p.vals_in, a.p.vals_out, int(n), 0, end_bit, st);
+}
+
+static inline unsigned blocks_for(int64_t n, int threads) {
+  return unsigned((n + threads - 1) / threads);
+}
+
+cudaError_t launch_setup(const KernelArgs& a, cudaStream_t st) {
+  const int T = 256;
+  if (a.totals[0] > 0) {
+    k_enumerate<<<blocks_for(a.totals[0], T), T, 0, st>>>(a);
+    int end_bit = 40;
+    while ((int64_t(1) << (end_bit - 40)) < a.n_scenes) ++end_bit;
+    cudaError_t e = launch_sort(a, a.totals[0], end_bit, st);
+    if (e != cudaSuccess) return e;
+    k_image_table<<<blocks_for(a.totals[0], T), T, 0, st>>>(a);
+  }
+  if (a.totals[1] > 0) k_traj_knots<<<blocks_for(a.totals[1], T), T, 0, st>>>(a);
+  if (a.totals[2] > 0) k_records<<<blocks_for(a.totals[2], T), T, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace msrc

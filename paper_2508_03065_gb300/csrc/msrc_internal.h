@@ -1,0 +1,132 @@
+// Internal structures of the msrc library (host planning + device kernels).
+// Not part of the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "msrc.h"
+
+namespace msrc {
+
+// Signal-side Farrow structure (Sec. II-B, Eq. 5): the tap weight of tap k is a
+// degree-kFarrowDeg polynomial in a local variable v of the fractional delay,
+// piecewise over kFarrowSegs segments of [0, 1). The prefilter produces one
+// signal row per (segment, power): z[s][q][m] = sum_k c[s][q][k] x[m - k].
+constexpr int kFarrowSegs = 2;
+constexpr int kFarrowDeg = 6;
+constexpr int kFarrowCoef = kFarrowDeg + 1;
+constexpr int kZRows = kFarrowSegs * kFarrowCoef;
+constexpr int kMaxTaps = 64;
+constexpr int kMaxScenesInline = 1;
+
+// Error bits of the device error word.
+constexpr uint32_t kErrTimeout = 1u;
+constexpr uint32_t kErrWindowClamp = 2u;
+
+// Per-scene description as the kernels see it. All offsets are in elements of
+// the array they index. Images are stored sorted by (tier, distance at the
+// middle of the trajectory); "block" = kBlockImages consecutive images of one
+// tier; "tile" = consecutive output samples of one synthesis item.
+struct SceneDev {
+  double dims[3];
+  double beta[6];
+  double c, fs, duration;
+  double mics[MSRC_MAX_MICS][3];
+  double traj[48];
+  int32_t traj_kind, n_ctrl;
+  int32_t K, n_mics, n_tiers, n_images;
+  int32_t tier_max_rho[MSRC_MAX_TIERS];
+  int32_t tier_step[MSRC_MAX_TIERS];       // knot spacing N_t (samples)
+  int32_t tier_count[MSRC_MAX_TIERS];      // images in tier
+  int32_t tier_first[MSRC_MAX_TIERS];      // first sorted image of tier
+  int32_t tier_intervals[MSRC_MAX_TIERS];  // J_t intervals per image (knots J_t + 1)
+  int32_t tier_blocks[MSRC_MAX_TIERS];     // blocks of the tier
+  int32_t block_first[MSRC_MAX_TIERS];     // first (scene-local) block of the tier
+  int32_t n_blocks;                        // blocks over all tiers
+  int32_t n_tiles;                         // output tiles
+  int32_t tile;                            // samples per tile
+  int32_t block_images;                    // images per block
+  int64_t img_base;                        // first entry of this scene in the image table
+  int64_t knot_base[MSRC_MAX_TIERS];       // first knot position (double3) per tier
+  int64_t knot_units_first[MSRC_MAX_TIERS];// prefix over tiers of (J_t + 1)
+  int64_t rec_base[MSRC_MAX_TIERS];        // first record of (mic 0, tier) per tier
+  int64_t rec_mic_stride;                  // records per microphone
+  int64_t rec_units_first[MSRC_MAX_TIERS + 1];  // prefix over tiers of knot-kernel units (per mic)
+  int64_t part_base;                       // first partial-sum float
+  int64_t n_in, n_out;
+  int64_t z_base;                          // first float of the z rows
+  int64_t z_len;                           // floats per z row (multiple of 4)
+  int64_t z_m0;                            // sample index of z column 0 (multiple of 4)
+  const float* x;
+  float* y;
+  float c_over_fs;                         // metres per sample of delay
+  float pad_;
+};
+
+// Knot-kernel chunking: one thread computes kKnotChunk consecutive intervals.
+constexpr int kKnotChunk = 8;
+
+// Per-kernel "units" of one scene and the prefix tables that map a global
+// unit index to its scene (batched launches).
+struct LaunchTables {
+  const int64_t* enum_prefix;    // images
+  const int64_t* knots_prefix;   // trajectory knots
+  const int64_t* rec_prefix;     // knot-kernel units
+  const int64_t* z_prefix;       // prefilter units
+  const int64_t* item_prefix;    // synthesis items
+  const int64_t* red_prefix;     // reduction units
+};
+
+struct DevicePtrs {
+  uint32_t* err;                 // device error word
+  uint32_t* counter;             // work-queue head of the persistent synthesis launch
+  uint64_t* keys_in;
+  uint64_t* keys_out;
+  uint32_t* vals_in;
+  uint32_t* vals_out;
+  void* sort_temp;
+  size_t sort_temp_bytes;
+  uint32_t* img_code;            // packed lattice triple and parity
+  float* img_gain;               // beta_i / (4 pi)
+  double* knot_pos;              // s(t_j), 3 doubles per knot
+  int4* rec;                     // interval records {I_j, f_j, slope_j, d_j}
+  float* z;                      // prefiltered rows
+  float* part;                   // partial sums
+};
+
+struct KernelArgs {
+  SceneDev scene0;               // used when n_scenes == 1
+  const SceneDev* scenes;        // used when n_scenes > 1
+  int32_t n_scenes;
+  int64_t totals[6];             // total units per kernel kind (enum, knots, rec, z, item, red)
+  LaunchTables tab;
+  DevicePtrs p;
+  float farrow[kFarrowSegs][kFarrowCoef][kMaxTaps];  // coefficients c[s][q][k + L/2]
+  int32_t taps;
+};
+
+// Image code: n_d + 64 in 7 bits each, parity bits above.
+__host__ __device__ inline uint32_t pack_image(int nx, int ny, int nz, int pbits) {
+  return uint32_t(nx + 64) | (uint32_t(ny + 64) << 7) | (uint32_t(nz + 64) << 14) |
+         (uint32_t(pbits) << 21);
+}
+__host__ __device__ inline void unpack_image(uint32_t code, int n[3], int p[3]) {
+  n[0] = int(code & 127u) - 64;
+  n[1] = int((code >> 7) & 127u) - 64;
+  n[2] = int((code >> 14) & 127u) - 64;
+  p[0] = int((code >> 21) & 1u);
+  p[1] = int((code >> 22) & 1u);
+  p[2] = int((code >> 23) & 1u);
+}
+
+// Launch entry points (defined in the .cu files).
+cudaError_t launch_setup(const KernelArgs& a, cudaStream_t s);
+cudaError_t launch_forward(const KernelArgs& a, int tile_config, cudaStream_t s,
+                           cudaEvent_t* ev /* nullable: [after prefilter, after synthesis] */);
+size_t sort_temp_bytes(int64_t n_items, int end_bit);
+cudaError_t launch_sort(const KernelArgs& a, int64_t n, int end_bit, cudaStream_t s);
+
+}  // namespace msrc

@@ -1,0 +1,184 @@
+"""The C ABI library without a GPU: it loads, exports every symbol declared in
+include/msrc.h, and its host-side logic (validation, Farrow fit, image counts,
+tier plan) behaves. No call here touches a device."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import api as oracle
+from paper_2508_03065_gb300 import _lib
+from paper_2508_03065_gb300 import workloads as W
+from tests.scenes import oracle_scene
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "msrc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(msrc_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.load()
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    bound = {n for n, _, _ in _lib.SIGNATURES}
+    assert set(names) <= bound, set(names) - bound
+
+
+def _desc(**kw):
+    d = _lib.RoomDesc()
+    d.dims[:] = kw.get("dims", [5.0, 4.0, 3.0])
+    d.beta[:] = kw.get("beta", [0.7] * 6)
+    d.c = kw.get("c", 343.0)
+    d.fs = kw.get("fs", 16000.0)
+    d.max_order = kw.get("K", 3)
+    tiers = kw.get("tiers", [(1, 16000.0), (2**31 - 1, 1000.0)])
+    d.n_tiers = len(tiers)
+    rho = [0] * 4
+    rate = [1.0] * 4
+    for t, (r, hz) in enumerate(tiers):
+        rho[t], rate[t] = r, hz
+    d.tier_max_rho[:] = rho
+    d.tier_rate_hz[:] = rate
+    d.taps = kw.get("taps", 32)
+    d.window = kw.get("window", 0)
+    d.kaiser_beta = kw.get("kaiser_beta", 8.0)
+    return d
+
+
+def _create(**kw):
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    st = lib.msrc_create_room(ctypes.byref(_desc(**kw)), ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dims=[0.0, 4.0, 3.0]), dict(beta=[1.2] + [0.7] * 5), dict(c=-1.0), dict(fs=0.0),
+    dict(K=61), dict(K=-1), dict(taps=31), dict(taps=4), dict(taps=66), dict(window=3),
+    dict(tiers=[(1, 16000.0), (2**31 - 1, 700.0)]), dict(tiers=[]),
+    dict(window=1, kaiser_beta=-1.0)])
+def test_create_room_rejects_bad_descriptions(bad):
+    st, h = _create(**bad)
+    assert st == _lib.ERR_INVALID_ARG
+    assert not h.value
+    assert len(_lib.load().msrc_last_error()) > 0
+
+
+def test_null_arguments_are_errors_not_crashes():
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    assert lib.msrc_create_room(None, ctypes.byref(h)) == _lib.ERR_INVALID_ARG
+    assert lib.msrc_set_trajectory(None, None, None, 1) == _lib.ERR_INVALID_ARG
+    assert lib.msrc_workspace_size(None, 1, None, None, None, None) == _lib.ERR_INVALID_ARG
+    assert lib.msrc_synthesize(None, 1, None, None, None, None, None, 0, None) == _lib.ERR_INVALID_ARG
+    assert lib.msrc_destroy_room(None) == _lib.OK
+    assert lib.msrc_status_string(_lib.ERR_WORKSPACE) == b"workspace too small or misaligned"
+
+
+def _traj(kind=0, params=(1.0, 1.0, 1.5, 3.0, 2.0, 0.0, 1.0), duration=1.0, n_ctrl=0):
+    t = _lib.TrajDesc()
+    t.kind, t.n_ctrl, t.duration_s = kind, n_ctrl, duration
+    p = [0.0] * 48
+    p[: len(params)] = params
+    t.params[:] = p
+    return t
+
+
+def _mics(*pts):
+    a = np.ascontiguousarray(np.array(pts, np.float64))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+@pytest.mark.parametrize("traj,mic,why", [
+    (_traj(params=(1.0, 1.0, 1.5, 3.0, 2.0, 0.0, 5.0)), (2.5, 2.0, 1.2), "leaves the room"),
+    (_traj(params=(1.0, 1.0, 1.5, 3.0, 2.0, 0.0, 1.0)), (6.0, 2.0, 1.2), "mic outside"),
+    (_traj(params=(1.0, 1.0, 1.5, 3.0, 2.0, 0.0, 1.0)), (1.5, 1.3, 1.5), "passes the mic"),
+    (_traj(kind=1, params=(2.5, 2.0, 1.5, 1.0, 400.0, 0.0)), (2.5, 2.0, 1.2), "faster than c"),
+    (_traj(kind=2, params=(1,) * 9, n_ctrl=3), (2.5, 2.0, 1.2), "too few control points"),
+    (_traj(kind=7), (2.5, 2.0, 1.2), "unknown kind"),
+    (_traj(duration=0.0), (2.5, 2.0, 1.2), "zero duration"),
+])
+def test_set_trajectory_rejects_invalid_geometry(traj, mic, why):
+    lib = _lib.load()
+    st, h = _create()
+    assert st == _lib.OK
+    arr, p = _mics(mic)
+    assert lib.msrc_set_trajectory(h, ctypes.byref(traj), p, 1) == _lib.ERR_INVALID_ARG, why
+    # a failed call leaves the room without a trajectory
+    sz = ctypes.c_size_t()
+    n = _lib.i64_array([16000])
+    assert lib.msrc_workspace_size(_lib.ptr_array([h.value]), 1, n, n, ctypes.byref(sz), None) == _lib.ERR_STATE
+    lib.msrc_destroy_room(h)
+
+
+def test_workspace_and_signal_checks_without_device():
+    lib = _lib.load()
+    st, h = _create()
+    arr, p = _mics((2.5, 2.0, 1.2))
+    assert lib.msrc_set_trajectory(h, ctypes.byref(_traj()), p, 1) == _lib.OK
+    hs = _lib.ptr_array([h.value])
+    n = _lib.i64_array([16000])
+    fwd = ctypes.c_size_t()
+    assert lib.msrc_workspace_size(hs, 1, n, n, ctypes.byref(fwd), None) == _lib.OK
+    assert fwd.value > 16000 * 4
+    # too-small or misaligned workspace, bad lengths: rejected before any device call
+    xs = _lib.ptr_array([1024])
+    ys = _lib.ptr_array([4096])
+    assert lib.msrc_synthesize(hs, 1, xs, n, ys, n, ctypes.c_void_p(256), 1024, None) == _lib.ERR_WORKSPACE
+    assert lib.msrc_synthesize(hs, 1, xs, n, ys, n, ctypes.c_void_p(257), fwd.value, None) == _lib.ERR_WORKSPACE
+    zero = _lib.i64_array([0])
+    assert lib.msrc_synthesize(hs, 1, xs, zero, ys, n, ctypes.c_void_p(256), fwd.value, None) == _lib.ERR_INVALID_ARG
+    lib.msrc_destroy_room(h)
+
+
+@pytest.mark.parametrize("K,tiers", [(3, [(1, 16000.0), (2**31 - 1, 1000.0)]),
+                                     (6, [(2, 16000.0), (8, 4000.0), (2**31 - 1, 500.0)])])
+def test_image_counts_per_tier_match_oracle(K, tiers):
+    lib = _lib.load()
+    st, h = _create(K=K, tiers=tiers)
+    assert st == _lib.OK
+    cnt = ctypes.c_int64()
+    per = (ctypes.c_int64 * 4)()
+    assert lib.msrc_room_image_count(h, ctypes.byref(cnt), per) == _lib.OK
+    sc = oracle.Scene(dims=(5.0, 4.0, 3.0), beta=(0.7,) * 6, mic=(2.5, 2.0, 1.2), K=K, fs=16000.0,
+                      tiers=[(r, 1) for r, _ in tiers])
+    tab = oracle.enumerate_images(sc)
+    assert cnt.value == W.image_count(K) == tab["tier"].size
+    for t in range(len(tiers)):
+        assert per[t] == int(np.sum(tab["tier"] == t))
+    lib.msrc_destroy_room(h)
+
+
+@pytest.mark.parametrize("taps,window", [(8, 0), (32, 0), (32, 1), (64, 1), (24, 1)])
+def test_farrow_fit_is_accurate(taps, window):
+    lib = _lib.load()
+    st, h = _create(taps=taps, window=window)
+    assert st == _lib.OK
+    e = ctypes.c_double()
+    assert lib.msrc_room_fit_error(h, ctypes.byref(e)) == _lib.OK
+    # polynomial error per tap small enough for the 1e-5 relative output budget
+    assert e.value < 1.5e-7
+    lib.msrc_destroy_room(h)
+
+
+def test_knot_spacing_from_paper_rates():
+    # Sec. III: spatio-temporal rate equal to the 16 kHz audio rate, downsampled
+    # by 3200 (a 5 Hz knot rate); tiers/rates must divide the audio rate.
+    with open(os.path.join(ROOT, "tests", "golden", "paper_rates.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for fs, ratio in rows:
+        fs, ratio = float(fs), int(ratio)
+        st, h = _create(fs=fs, tiers=[(1, fs), (2**31 - 1, fs / ratio)])
+        assert st == _lib.OK
+        _lib.load().msrc_destroy_room(h)
+    st, _ = _create(fs=16000.0, tiers=[(1, 16000.0), (2**31 - 1, 16000.0 / 3200.5)])
+    assert st == _lib.ERR_INVALID_ARG
