@@ -12,9 +12,6 @@
 #include "msrc_internal.h"
 
 namespace msrc {
-int tile_config_count();
-int tile_samples(int cfg);
-int tile_block_images(int cfg);
 cudaError_t launch_backward(const KernelArgs& a, const float* const* dy, float* const* dx,
                             double* const* dparams, double* const* dbeta, cudaStream_t st);
 size_t backward_extra_bytes(const KernelArgs& a);
@@ -245,7 +242,7 @@ struct Plan {
   int end_bit = 40;
   // byte offsets in the workspace
   size_t off_desc = 0, off_keys_in = 0, off_keys_out = 0, off_vals_in = 0, off_vals_out = 0;
-  size_t off_sort = 0, sort_bytes = 0, off_code = 0, off_gain = 0, off_knots = 0, off_rec = 0;
+  size_t off_sort = 0, sort_bytes = 0, off_code = 0, off_gain = 0, off_knots = 0;
   size_t off_z = 0, off_part = 0, fwd_bytes = 0, desc_bytes = 0;
   int kL = 32;
   int taps = 32;
@@ -256,11 +253,11 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   if (!rooms || n <= 0 || !n_in || !n_out)
     return fail(MSRC_ERR_INVALID_ARG, "null rooms/lengths or n_rooms <= 0");
   const int cfg = g_tile_config;
-  const int T = tile_samples(cfg);
-  const int B = tile_block_images(cfg);
+  const TileConfig& tc = tile_config(cfg);
+  const int T = tc.threads * tc.chunks;
   P.scenes.resize(n);
   for (auto& v : P.prefix) v.assign(n + 1, 0);
-  int64_t img_acc = 0, knot_acc = 0, rec_acc = 0, z_acc = 0, part_acc = 0;
+  int64_t img_acc = 0, knot_acc = 0, z_acc = 0, part_acc = 0;
   for (int s = 0; s < n; ++s) {
     msrc_room* R = rooms[s];
     if (!R) return fail(MSRC_ERR_INVALID_ARG, "room %d is null", s);
@@ -292,11 +289,10 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     S.n_in = n_in[s];
     S.n_out = n_out[s];
     S.tile = T;
-    S.block_images = B;
     S.n_tiles = int32_t((n_out[s] + T - 1) / T);
     S.c_over_fs = float(R->d.c / R->d.fs);
     int first = 0, blk = 0;
-    int64_t kfirst = 0, rfirst = 0, rbase = 0;
+    int64_t kfirst = 0;
     int max_step = 1;
     for (int t = 0; t < S.n_tiers; ++t) {
       const int N = R->tier_step[t];
@@ -308,20 +304,21 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
       first += S.tier_count[t];
       const int J = int((n_out[s] - 1) / N + 1);
       S.tier_intervals[t] = J;
+      // images per block: the item's records (one per image and knot interval
+      // touching the tile) must fit the shared record capacity
+      const int rec_per_image = (T - 1) / N + 2;
+      if (rec_per_image > tc.reccap)
+        return fail(MSRC_ERR_UNSUPPORTED, "tile configuration too small for knot spacing %d", N);
+      const int B = std::max(1, std::min(tc.block, tc.reccap / rec_per_image));
+      S.tier_block_images[t] = B;
       S.tier_blocks[t] = (S.tier_count[t] + B - 1) / B;
       S.block_first[t] = blk;
       blk += S.tier_blocks[t];
       S.knot_base[t] = knot_acc + kfirst;
       S.knot_units_first[t] = kfirst;
       kfirst += J + 1;
-      S.rec_units_first[t] = rfirst;
-      rfirst += int64_t(S.tier_count[t]) * ((J + kKnotChunk - 1) / kKnotChunk);
-      S.rec_base[t] = rec_acc + rbase;
-      rbase += int64_t(S.tier_count[t]) * J;
     }
-    S.rec_units_first[S.n_tiers] = rfirst;
     S.n_blocks = blk;
-    S.rec_mic_stride = rbase;
     S.img_base = img_acc;
     // z rows cover every read position: n - tau with tau in [0, tau_bound]
     double maxL = 0, diag = 0;
@@ -341,7 +338,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
 
     const int64_t u_enum = S.n_images;
     const int64_t u_knots = kfirst;
-    const int64_t u_rec = int64_t(S.n_mics) * rfirst;
+    const int64_t u_rec = 0;
     const int64_t u_z = (S.z_len + 255) / 256;
     const int64_t u_item = int64_t(S.n_mics) * S.n_blocks * S.n_tiles;
     const int64_t u_red = int64_t(S.n_mics) * S.n_out;
@@ -352,7 +349,6 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     }
     img_acc += S.n_images;
     knot_acc += kfirst;
-    rec_acc += int64_t(S.n_mics) * rbase;
     z_acc += int64_t(kZRows) * S.z_len;
     part_acc += int64_t(S.n_mics) * S.n_blocks * S.n_out;
   }
@@ -374,7 +370,6 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.off_code = off; off = align256(off + 4 * I);
   P.off_gain = off; off = align256(off + 4 * I);
   P.off_knots = off; off = align256(off + 24 * size_t(knot_acc));
-  P.off_rec = off; off = align256(off + 16 * size_t(rec_acc));
   P.off_z = off; off = align256(off + 4 * size_t(z_acc));
   P.off_part = off; off = align256(off + 4 * size_t(part_acc));
   P.fwd_bytes = off;
@@ -398,7 +393,6 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.img_code = reinterpret_cast<uint32_t*>(ws + P.off_code);
   a.p.img_gain = reinterpret_cast<float*>(ws + P.off_gain);
   a.p.knot_pos = reinterpret_cast<double*>(ws + P.off_knots);
-  a.p.rec = reinterpret_cast<int4*>(ws + P.off_rec);
   a.p.z = reinterpret_cast<float*>(ws + P.off_z);
   a.p.part = reinterpret_cast<float*>(ws + P.off_part);
   std::memcpy(a.farrow, rooms[0]->farrow, sizeof(a.farrow));
@@ -410,7 +404,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
     const int n1 = a.n_scenes + 1;
     a.tab.enum_prefix = pre;
     a.tab.knots_prefix = pre + n1;
-    a.tab.rec_prefix = pre + 2 * n1;
+    a.tab.unused_prefix = pre + 2 * n1;
     a.tab.z_prefix = pre + 3 * n1;
     a.tab.item_prefix = pre + 4 * n1;
     a.tab.red_prefix = pre + 5 * n1;

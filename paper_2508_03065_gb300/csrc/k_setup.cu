@@ -5,29 +5,13 @@
 //   k_image_table  packed image codes and gains beta_i / (4 pi)
 //   k_traj_knots   source position s(t_j) at every knot of every tier, FP64
 //                  (Sec. II-C: trajectory sampled at the tier's spatial rate)
-//   k_records      exact FP64 image distances at the knots, split into an exact
-//                  integer delay and FP32 fraction, stored per interval
-//                  (Sec. II-C: tau_i = d_i / c at the hierarchical knots)
 #include <cub/device/device_radix_sort.cuh>
 
 #include "msrc_internal.h"
+#include "synth_common.cuh"
 
 namespace msrc {
 namespace {
-
-__device__ __forceinline__ const SceneDev& scene_of(const KernelArgs& a, int s) {
-  return a.n_scenes == 1 ? a.scene0 : a.scenes[s];
-}
-
-// Largest s with prefix[s] <= idx (prefix has n_scenes + 1 entries).
-__device__ __forceinline__ int find_scene(const int64_t* prefix, int n, int64_t idx) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= idx) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
 
 __device__ __forceinline__ int locate(const KernelArgs& a, const int64_t* prefix, int64_t gid,
                                       int64_t* local) {
@@ -161,64 +145,6 @@ __global__ void k_traj_knots(const __grid_constant__ KernelArgs a) {
   out[2] = sp[2];
 }
 
-// One thread: kKnotChunk consecutive intervals of one image for one microphone.
-// The distance is evaluated in FP64 at each knot; the delay tau = d fs / c is
-// split into an exact integer D_j and an FP32 fraction f_j; the record of
-// interval j is {n_j - D_j, f_j, (tau_{j+1} - tau_j) / N_t, d_j}.
-__global__ void k_records(const __grid_constant__ KernelArgs a) {
-  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (gid >= a.totals[2]) return;
-  int64_t local;
-  const int s = locate(a, a.tab.rec_prefix, gid, &local);
-  const SceneDev& S = scene_of(a, s);
-  const int64_t per_mic = S.rec_units_first[S.n_tiers];
-  const int mic = int(local / per_mic);
-  int64_t u = local - int64_t(mic) * per_mic;
-  int t = 0;
-  while (t + 1 < S.n_tiers && u >= S.rec_units_first[t + 1]) ++t;
-  u -= S.rec_units_first[t];
-  const int J = S.tier_intervals[t];
-  const int chunks = (J + kKnotChunk - 1) / kKnotChunk;
-  const int img = int(u / chunks);
-  const int j0 = int(u - int64_t(img) * chunks) * kKnotChunk;
-  const int j1 = min(j0 + kKnotChunk, J);
-  int n[3], p[3];
-  unpack_image(a.p.img_code[S.img_base + S.tier_first[t] + img], n, p);
-  double off[3], sg[3];
-  for (int d = 0; d < 3; ++d) {
-    sg[d] = 1.0 - 2.0 * p[d];
-    off[d] = 2.0 * n[d] * S.dims[d] - S.mics[mic][d];
-  }
-  const double* kp = a.p.knot_pos + 3 * S.knot_base[t];
-  const double fs_c = S.fs / S.c;
-  const int N = S.tier_step[t];
-  int4* out = a.p.rec + S.rec_base[t] + int64_t(mic) * S.rec_mic_stride + int64_t(img) * J;
-  auto tau_at = [&](int j, double* dist) {
-    double acc = 0.0;
-    for (int d = 0; d < 3; ++d) {
-      const double v = sg[d] * kp[3 * j + d] + off[d];
-      acc += v * v;
-    }
-    *dist = sqrt(acc);
-    return *dist * fs_c;
-  };
-  double dj;
-  double tau = tau_at(j0, &dj);
-  for (int j = j0; j < j1; ++j) {
-    double dn;
-    const double tau_n = tau_at(j + 1, &dn);
-    const double D = floor(tau);
-    int4 r;
-    r.x = int(int64_t(j) * N - int64_t(D));
-    r.y = __float_as_int(float(tau - D));
-    r.z = __float_as_int(float((tau_n - tau) / double(N)));
-    r.w = __float_as_int(float(dj));
-    out[j] = r;
-    tau = tau_n;
-    dj = dn;
-  }
-}
-
 }  // namespace
 
 size_t sort_temp_bytes(int64_t n_items, int end_bit) {
@@ -255,7 +181,6 @@ cudaError_t launch_setup(const KernelArgs& a, cudaStream_t st) {
     k_image_table<<<blocks_for(a.totals[0], T), T, 0, st>>>(a);
   }
   if (a.totals[1] > 0) k_traj_knots<<<blocks_for(a.totals[1], T), T, 0, st>>>(a);
-  if (a.totals[2] > 0) k_records<<<blocks_for(a.totals[2], T), T, 0, st>>>(a);
   return cudaGetLastError();
 }
 

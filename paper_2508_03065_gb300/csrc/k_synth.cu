@@ -4,34 +4,26 @@
 //                segment s and power q of the tap polynomial,
 //                z[s][q][m] = sum_k c[s][q][k] x[m - k].
 //   k_synth      persistent gather-accumulate over a work queue of
-//                (scene, microphone, image block, output tile) items. Per
-//                image-sample: interpolate the delay from the knot records,
-//                split it into read position m0 and fraction alpha, evaluate
-//                e = sum_q v^q z[seg(alpha)][q][m0] by Horner, and accumulate
-//                (beta_i / (4 pi d_i(n))) e. The z window of the item is staged
-//                in shared memory with cp.async; each item writes one partial
-//                row (no atomics).
+//                (scene, microphone, image block, output tile) items.
+//                Item prologue: the hierarchical delay knots of the block's
+//                images over the tile (Sec. II-C, "Fast Architecture") are
+//                evaluated into shared memory: one FP64 anchor distance per
+//                image, the other knots by an exact FP32 increment of the
+//                squared distance. Then the z window of the item is staged in
+//                shared memory with cp.async. Per image-sample: interpolate the
+//                delay linearly between knots, split it into read position m0
+//                and fraction alpha, evaluate e = sum_q v^q z[seg(alpha)][q][m0]
+//                by Horner and accumulate (beta_i / (4 pi d_i(n))) e. Each item
+//                writes one partial row (no atomics).
 //   k_reduce     y[mic][n] = sum over image blocks of the partial rows, in a
 //                fixed order (bitwise reproducible).
 #include <cstdint>
 
 #include "msrc_internal.h"
+#include "synth_common.cuh"
 
 namespace msrc {
 namespace {
-
-__device__ __forceinline__ const SceneDev& scene_of(const KernelArgs& a, int s) {
-  return a.n_scenes == 1 ? a.scene0 : a.scenes[s];
-}
-
-__device__ __forceinline__ int find_scene(const int64_t* prefix, int n, int64_t idx) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= idx) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
 
 // ------------------------------------------------------------------ prefilter
 constexpr int kPreThreads = 256;
@@ -74,13 +66,6 @@ __global__ void __launch_bounds__(kPreThreads) k_prefilter(const __grid_constant
 }
 
 // ------------------------------------------------------------------ synthesis
-struct TileShape {
-  int threads;   // CTA size
-  int chunks;    // 32-sample chunks per warp (tile = threads * chunks)
-  int wcap;      // shared-memory window capacity (samples)
-  int block;     // images per block
-};
-
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -89,44 +74,32 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-// Delay interpolation and read position of one image-sample.
-// rec = {I_j = n_j - D_j, f_j, slope, d_j}; r = n - n_j.
-struct Tap {
-  int m0;     // read position floor(n - tau)
-  int seg;    // Farrow segment of alpha
-  float v;    // local polynomial variable in [-1, 1]
-  float d;    // interpolated distance
-};
-
-__device__ __forceinline__ Tap delay_split(const int4 rec, int r, float rf, float c_over_fs) {
-  const float fj = __int_as_float(rec.y);
-  const float st = __int_as_float(rec.z);
-  const float dj = __int_as_float(rec.w);
-  // phi = tau(n) - D_j, |phi| small; n - tau = r + I_j - phi
-  const float phi = fmaf(rf, st, fj);
-  // ceil(phi) with the round-to-nearest magic constant 1.5 * 2^23
-  const float q = phi + 12582912.0f;
-  const int kr = __float_as_int(q) - 0x4B400000;
-  const float cf = q - 12582912.0f;
-  const int up = cf < phi ? 1 : 0;
-  const float alpha = (cf - phi) + float(up);  // in [0, 1]
-  Tap t;
-  t.m0 = r + rec.x - (kr + up);
-  const float psi = alpha * float(kFarrowSegs);
-  int seg = int(psi);
-  seg = seg > kFarrowSegs - 1 ? kFarrowSegs - 1 : seg;
-  t.seg = seg;
-  t.v = fmaf(psi - float(seg), 2.0f, -1.0f);
-  t.d = fmaf(rf, st * c_over_fs, dj);
-  return t;
+// One image-sample from shared rows of stride kStride: delay interpolation,
+// read position, Farrow evaluation, gain. Returns g * e.
+template <int kStride>
+__device__ __forceinline__ float image_sample(const float* zs, const int4 rec, int rm, float rf,
+                                              float cfs, float gain, unsigned wmax) {
+  const DelaySplit ds = split_delay(rec, rm, rf, wmax);
+  const float* zp = zs + (ds.hi ? kFarrowCoef * kStride : 0) + ds.col;
+  float e = zp[kFarrowDeg * kStride];
+#pragma unroll
+  for (int qq = kFarrowDeg - 1; qq >= 0; --qq) e = fmaf(e, ds.v, zp[qq * kStride]);
+  const float d = fmaf(rf, __int_as_float(rec.z) * cfs, __int_as_float(rec.w));
+  return __fdividef(gain, d) * e;
 }
 
-template <int kThreads, int kChunks, int kWcap, int kBlock>
+template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock>
 __global__ void __launch_bounds__(kThreads) k_synth(const __grid_constant__ KernelArgs a) {
-  extern __shared__ __align__(16) float zs[];  // kZRows rows of kWcap floats
+  extern __shared__ __align__(16) float smem[];
+  float* zs = smem;                                              // kZRows x kWcap
+  int4* rec_s = reinterpret_cast<int4*>(smem + kZRows * kWcap);  // kRecCap records
+  // prologue scratch aliases the z window (used before the window is staged)
+  float4* u_s = reinterpret_cast<float4*>(smem);
+  float4* anc_s = u_s + kThreads * kChunks + 4;                  // 2 x kBlock
   __shared__ int s_item;
   __shared__ float s_red[2][kThreads / 32];
   constexpr int kTile = kThreads * kChunks;
+  static_assert((kTile + 4) * 4 + 2 * kBlock * 4 <= kZRows * kWcap, "prologue scratch");
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
 
@@ -142,37 +115,11 @@ __global__ void __launch_bounds__(kThreads) k_synth(const __grid_constant__ Kern
       li = item - a.tab.item_prefix[s];
     }
     const SceneDev& S = scene_of(a, s);
-    const int tile = int(li % S.n_tiles);
-    const int64_t mb = li / S.n_tiles;
-    const int mic = int(mb / S.n_blocks);
-    const int blk = int(mb - int64_t(mic) * S.n_blocks);
-    int t = 0;
-    while (t + 1 < S.n_tiers && blk >= S.block_first[t + 1]) ++t;
-    const int blk_t = blk - S.block_first[t];
-    const int img0 = blk_t * kBlock;                         // first image within the tier
-    const int cnt = min(kBlock, S.tier_count[t] - img0);
-    const int N = S.tier_step[t];
-    const int J = S.tier_intervals[t];
-    const int n0 = tile * kTile;
-    const int n_end = int(min(int64_t(n0 + kTile), S.n_out)) - 1;
-    const int4* rec = a.p.rec + S.rec_base[t] + int64_t(mic) * S.rec_mic_stride + int64_t(img0) * J;
-    const float* gain = a.p.img_gain + S.img_base + S.tier_first[t] + img0;
+    const ItemGeom g = item_geometry(S, li, kTile);
 
-    // --- delay range of the item (linear between knots: extremes at knots)
-    const int jf = n0 / N, jl = n_end / N;
-    const int nk = jl - jf + 2;
-    float tmin = 3.0e38f, tmax = -3.0e38f;
-    const int pairs = cnt * nk;
-    for (int pidx = threadIdx.x; pidx < pairs; pidx += kThreads) {
-      const int ib = pidx / nk;
-      const int jj = jf + (pidx - ib * nk);
-      const int jr = jj <= jl ? jj : jl;
-      const int4 R = __ldg(rec + int64_t(ib) * J + jr);
-      float tau = float(jr * N - R.x) + __int_as_float(R.y);
-      if (jj > jl) tau = fmaf(float(N), __int_as_float(R.z), tau);
-      tmin = fminf(tmin, tau);
-      tmax = fmaxf(tmax, tau);
-    }
+    // --- delay knots of the block over the tile (records in shared memory)
+    float tmin, tmax;
+    item_records<kThreads>(a, S, g, rec_s, u_s, anc_s, &tmin, &tmax);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
@@ -187,8 +134,8 @@ __global__ void __launch_bounds__(kThreads) k_synth(const __grid_constant__ Kern
       tmin = fminf(tmin, s_red[0][w]);
       tmax = fmaxf(tmax, s_red[1][w]);
     }
-    const int m_lo = (n0 - int(ceilf(tmax)) - 2) & ~3;
-    const int m_hi = n_end - int(floorf(tmin)) + 2;
+    const int m_lo = (g.n0 - int(ceilf(tmax)) - 2) & ~3;
+    const int m_hi = g.n_end - int(floorf(tmin)) + 2;
     const int width = ((m_hi - m_lo + 1) + 3) & ~3;
     const bool in_smem = width <= kWcap;
 
@@ -210,61 +157,72 @@ __global__ void __launch_bounds__(kThreads) k_synth(const __grid_constant__ Kern
     __syncthreads();
 
     // --- gather-accumulate: warp w owns samples n0 + 32 (w kChunks + c) + lane
-    int jr[kChunks], rr[kChunks];
+    int jc[kChunks], rm[kChunks];
     float rf[kChunks], acc[kChunks];
     bool valid[kChunks];
+    const int nrec = g.nk - 1;
 #pragma unroll
     for (int c = 0; c < kChunks; ++c) {
-      const int n = n0 + 32 * (warp * kChunks + c) + lane;
-      valid[c] = n <= n_end;
-      const int nn = valid[c] ? n : n_end;
-      jr[c] = nn / N;
-      rr[c] = nn - jr[c] * N;
-      rf[c] = float(rr[c]);
+      const int n = g.n0 + 32 * (warp * kChunks + c) + lane;
+      valid[c] = n <= g.n_end;
+      const int nn = valid[c] ? n : g.n_end;
+      const int j = nn / g.N;
+      const int r = nn - j * g.N;
+      jc[c] = j - g.jf;
+      rf[c] = float(r);
+      rm[c] = r - (in_smem ? m_lo : int(S.z_m0));
       acc[c] = 0.0f;
     }
     const float cfs = S.c_over_fs;
+    const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
     if (in_smem) {
       const unsigned wmax = unsigned(width - 1);
-      for (int ib = 0; ib < cnt; ++ib) {
-        const float g = __ldg(gain + ib);
-        const int4* ri = rec + int64_t(ib) * J;
+      int ib = 0;
+      for (; ib + 1 < g.cnt; ib += 2) {
+        const float g0 = __ldg(gain + ib), g1 = __ldg(gain + ib + 1);
+        const int4* r0 = rec_s + ib * nrec;
+        const int4* r1 = r0 + nrec;
 #pragma unroll
         for (int c = 0; c < kChunks; ++c) {
-          const Tap tp = delay_split(__ldg(ri + jr[c]), rr[c], rf[c], cfs);
-          const unsigned col = min(unsigned(tp.m0 - m_lo), wmax);
-          const float* zp = zs + tp.seg * (kFarrowCoef * kWcap) + col;
-          float e = zp[kFarrowDeg * kWcap];
-#pragma unroll
-          for (int q = kFarrowDeg - 1; q >= 0; --q) e = fmaf(e, tp.v, zp[q * kWcap]);
-          acc[c] = fmaf(__fdividef(g, tp.d), e, acc[c]);
+          const float e0 = image_sample<kWcap>(zs, r0[jc[c]], rm[c], rf[c], cfs, g0, wmax);
+          const float e1 = image_sample<kWcap>(zs, r1[jc[c]], rm[c], rf[c], cfs, g1, wmax);
+          acc[c] += e0 + e1;
         }
+      }
+      if (ib < g.cnt) {
+        const float g0 = __ldg(gain + ib);
+        const int4* r0 = rec_s + ib * nrec;
+#pragma unroll
+        for (int c = 0; c < kChunks; ++c)
+          acc[c] += image_sample<kWcap>(zs, r0[jc[c]], rm[c], rf[c], cfs, g0, wmax);
       }
     } else {
       // window wider than shared memory: read the L2-resident rows directly
-      const uint64_t zmax = uint64_t(S.z_len - 1);
-      for (int ib = 0; ib < cnt; ++ib) {
-        const float g = __ldg(gain + ib);
-        const int4* ri = rec + int64_t(ib) * J;
+      const unsigned zmax = unsigned(S.z_len - 1);
+      const int64_t zl = S.z_len;
+      for (int ib = 0; ib < g.cnt; ++ib) {
+        const float g0 = __ldg(gain + ib);
+        const int4* r0 = rec_s + ib * nrec;
 #pragma unroll
         for (int c = 0; c < kChunks; ++c) {
-          const Tap tp = delay_split(__ldg(ri + jr[c]), rr[c], rf[c], cfs);
-          const uint64_t col = min(uint64_t(int64_t(tp.m0) - S.z_m0), zmax);
-          const float* zp = zg + int64_t(tp.seg) * kFarrowCoef * S.z_len + col;
-          float e = __ldg(zp + int64_t(kFarrowDeg) * S.z_len);
+          const int4 R = r0[jc[c]];
+          const DelaySplit ds = split_delay(R, rm[c], rf[c], zmax);
+          const float* zp = zg + (ds.hi ? int64_t(kFarrowCoef) * zl : int64_t(0)) + ds.col;
+          float e = __ldg(zp + int64_t(kFarrowDeg) * zl);
 #pragma unroll
-          for (int q = kFarrowDeg - 1; q >= 0; --q) e = fmaf(e, tp.v, __ldg(zp + int64_t(q) * S.z_len));
-          acc[c] = fmaf(__fdividef(g, tp.d), e, acc[c]);
+          for (int qq = kFarrowDeg - 1; qq >= 0; --qq) e = fmaf(e, ds.v, __ldg(zp + int64_t(qq) * zl));
+          const float d = fmaf(rf[c], __int_as_float(R.z) * cfs, __int_as_float(R.w));
+          acc[c] = fmaf(__fdividef(g0, d), e, acc[c]);
         }
       }
     }
-    float* out = a.p.part + S.part_base + (int64_t(mic) * S.n_blocks + blk) * S.n_out;
+    float* out = a.p.part + S.part_base + (int64_t(g.mic) * S.n_blocks + g.blk) * S.n_out;
 #pragma unroll
     for (int c = 0; c < kChunks; ++c) {
-      const int n = n0 + 32 * (warp * kChunks + c) + lane;
+      const int n = g.n0 + 32 * (warp * kChunks + c) + lane;
       if (valid[c]) out[n] = acc[c];
     }
-    __syncthreads();  // shared window and s_item are reused by the next item
+    __syncthreads();  // shared memory and s_item are reused by the next item
   }
 }
 
@@ -287,10 +245,10 @@ __global__ void k_reduce(const __grid_constant__ KernelArgs a) {
   S.y[int64_t(mic) * S.n_out + n] = acc;
 }
 
-template <int kThreads, int kChunks, int kWcap, int kBlock>
+template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock>
 cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
-  auto kern = k_synth<kThreads, kChunks, kWcap, kBlock>;
-  const size_t smem = size_t(kZRows) * kWcap * sizeof(float);
+  auto kern = k_synth<kThreads, kChunks, kWcap, kRecCap, kBlock>;
+  const size_t smem = size_t(kZRows) * kWcap * sizeof(float) + size_t(kRecCap) * sizeof(int4);
   static int grid = 0;
   if (grid == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -312,19 +270,21 @@ cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-struct TileConfig {
-  int threads, chunks, wcap, block;
-};
+// Tile configurations of the synthesis launch (see TileConfig).
+#define MSRC_TILE_CONFIGS(X)          \
+  X(0, 512, 2, 2816, 4096, 256)       \
+  X(1, 256, 2, 1408, 2048, 256)       \
+  X(2, 256, 3, 1664, 2304, 192)       \
+  X(3, 512, 1, 1536, 2048, 256)
+
 static const TileConfig kConfigs[] = {
-    {256, 3, 1792, 256},
-    {256, 2, 1536, 256},
-    {256, 4, 2048, 128},
-    {512, 2, 3584, 256},
+#define MSRC_ROW(id, th, ch, wc, rc, bl) {th, ch, wc, rc, bl},
+    MSRC_TILE_CONFIGS(MSRC_ROW)
+#undef MSRC_ROW
 };
 
 int tile_config_count() { return int(sizeof(kConfigs) / sizeof(kConfigs[0])); }
-int tile_samples(int cfg) { return kConfigs[cfg].threads * kConfigs[cfg].chunks; }
-int tile_block_images(int cfg) { return kConfigs[cfg].block; }
+const TileConfig& tile_config(int cfg) { return kConfigs[cfg]; }
 
 cudaError_t launch_forward(const KernelArgs& a, int cfg, cudaStream_t st, cudaEvent_t* ev) {
   const int T = 256;
@@ -337,10 +297,11 @@ cudaError_t launch_forward(const KernelArgs& a, int cfg, cudaStream_t st, cudaEv
   if (ev) cudaEventRecord(ev[0], st);
   cudaError_t e = cudaSuccess;
   switch (cfg) {
-    case 1: e = run_synth<256, 2, 1536, 256>(a, st); break;
-    case 2: e = run_synth<256, 4, 2048, 128>(a, st); break;
-    case 3: e = run_synth<512, 2, 3584, 256>(a, st); break;
-    default: e = run_synth<256, 3, 1792, 256>(a, st); break;
+#define MSRC_CASE(id, th, ch, wc, rc, bl) \
+  case id: e = run_synth<th, ch, wc, rc, bl>(a, st); break;
+    MSRC_TILE_CONFIGS(MSRC_CASE)
+#undef MSRC_CASE
+    default: e = cudaErrorInvalidValue; break;
   }
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], st);

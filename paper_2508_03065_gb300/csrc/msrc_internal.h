@@ -48,13 +48,10 @@ struct SceneDev {
   int32_t n_blocks;                        // blocks over all tiers
   int32_t n_tiles;                         // output tiles
   int32_t tile;                            // samples per tile
-  int32_t block_images;                    // images per block
+  int32_t tier_block_images[MSRC_MAX_TIERS];  // images per block of the tier
   int64_t img_base;                        // first entry of this scene in the image table
   int64_t knot_base[MSRC_MAX_TIERS];       // first knot position (double3) per tier
   int64_t knot_units_first[MSRC_MAX_TIERS];// prefix over tiers of (J_t + 1)
-  int64_t rec_base[MSRC_MAX_TIERS];        // first record of (mic 0, tier) per tier
-  int64_t rec_mic_stride;                  // records per microphone
-  int64_t rec_units_first[MSRC_MAX_TIERS + 1];  // prefix over tiers of knot-kernel units (per mic)
   int64_t part_base;                       // first partial-sum float
   int64_t n_in, n_out;
   int64_t z_base;                          // first float of the z rows
@@ -66,15 +63,22 @@ struct SceneDev {
   float pad_;
 };
 
-// Knot-kernel chunking: one thread computes kKnotChunk consecutive intervals.
-constexpr int kKnotChunk = 8;
+// Tile configuration of the synthesis launch: CTA threads, 32-sample chunks per
+// warp (tile = threads * chunks samples), shared z-window capacity (samples),
+// shared record capacity (one record per image and knot interval), maximum
+// images per block.
+struct TileConfig {
+  int threads, chunks, wcap, reccap, block;
+};
+int tile_config_count();
+const TileConfig& tile_config(int cfg);
 
 // Per-kernel "units" of one scene and the prefix tables that map a global
 // unit index to its scene (batched launches).
 struct LaunchTables {
   const int64_t* enum_prefix;    // images
   const int64_t* knots_prefix;   // trajectory knots
-  const int64_t* rec_prefix;     // knot-kernel units
+  const int64_t* unused_prefix;  // (reserved)
   const int64_t* z_prefix;       // prefilter units
   const int64_t* item_prefix;    // synthesis items
   const int64_t* red_prefix;     // reduction units
@@ -92,7 +96,6 @@ struct DevicePtrs {
   uint32_t* img_code;            // packed lattice triple and parity
   float* img_gain;               // beta_i / (4 pi)
   double* knot_pos;              // s(t_j), 3 doubles per knot
-  int4* rec;                     // interval records {I_j, f_j, slope_j, d_j}
   float* z;                      // prefiltered rows
   float* part;                   // partial sums
 };
