@@ -183,6 +183,24 @@ int32_t msrc_tile_configs(void);
 msrc_status msrc_profile_enable(int32_t on);
 msrc_status msrc_profile_read(double* ms, int32_t* n_calls);
 
+/* Allocation-free forward synthesis. The paper has no counterpart: this is a
+ * service of the library for callers that may not allocate device memory, such
+ * as a plug-in whose host application owns every device buffer through its own
+ * pool, or a real-time audio thread that must not enter the CUDA allocator.
+ * Same result as msrc_synthesize for one room (x_dev: n_in floats, y_dev:
+ * n_mics x n_out floats, both device memory owned by the caller), computed in a
+ * scratch array of MSRC_NOALLOC_SCRATCH_BYTES that the library reserves in
+ * device memory on every GPU where it is loaded, for the life of the process.
+ * Rooms whose workspace (msrc_workspace_size) exceeds that size are rejected
+ * with MSRC_ERR_WORKSPACE. The first call on a device looks up the array's
+ * device address with that device current; make that first call before any
+ * stream capture. All calls share the one array and its contents persist
+ * between calls: calls that may overlap on the GPU (other streams or threads)
+ * race, so the caller serialises them. Nothing is allocated by this call. */
+#define MSRC_NOALLOC_SCRATCH_BYTES (32u << 20)
+msrc_status msrc_synthesize_noalloc(msrc_room_t room, const float* x_dev, int64_t n_in,
+                                    float* y_dev, int64_t n_out, void* stream);
+
 const char* msrc_status_string(msrc_status status);
 const char* msrc_last_error(void);
 

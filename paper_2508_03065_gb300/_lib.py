@@ -77,6 +77,7 @@ SIGNATURES = [
     ("msrc_tile_configs", _I32, []),
     ("msrc_profile_enable", _I32, [_I32]),
     ("msrc_profile_read", _I32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
+    ("msrc_synthesize_noalloc", _I32, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P]),
     ("msrc_status_string", ctypes.c_char_p, [_I32]),
     ("msrc_last_error", ctypes.c_char_p, []),
 ]

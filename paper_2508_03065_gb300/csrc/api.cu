@@ -19,6 +19,16 @@ size_t backward_extra_bytes(const KernelArgs& a);
 
 using namespace msrc;
 
+namespace {
+thread_local std::string g_last_error;
+}
+
+namespace msrc {
+// Sets the thread-local message returned by msrc_last_error (used by entry
+// points defined in other translation units).
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+}  // namespace msrc
+
 struct msrc_room {
   msrc_room_desc d;
   int32_t tier_step[MSRC_MAX_TIERS];
@@ -36,7 +46,6 @@ struct msrc_room {
 
 namespace {
 
-thread_local std::string g_last_error;
 int g_tile_config = 0;
 
 // Optional per-phase timing with CUDA events recorded on the launching stream.
