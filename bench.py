@@ -33,12 +33,12 @@ METRIC = "image-samples/s (forward, order-20 48 kHz)"
 UNIT = "image-samples/s"
 
 # Algorithmic work of the synthesis kernel per image-sample (signal-side Farrow,
-# 2 segments x degree 6): 7 prefiltered values gathered from shared memory.
-Z_BYTES_PER_IMAGE_SAMPLE = 7 * 4
-# FP32 operations per image-sample: Horner 6 FMA (12), accumulate 1 FMA (2),
-# delay interpolation 1 FMA (2), fraction and segment split 4, distance 1 FMA
-# + 1 MUL (3), gain 1 division (1) -> 24.
-FLOPS_PER_IMAGE_SAMPLE = 24
+# 2 segments x degree 7): 8 prefiltered values gathered from shared memory.
+Z_BYTES_PER_IMAGE_SAMPLE = 8 * 4
+# FP32 operations per image-sample: Horner 7 FMA (14), accumulate 1 FMA (2),
+# delay interpolation 1 FMA (2), fraction and segment split 5, delay 1 ADD,
+# gain 1 division (1) -> 25.
+FLOPS_PER_IMAGE_SAMPLE = 25
 SM_COUNT = 152
 SMEM_BYTES_PER_CLK_PER_SM = 128
 FP32_LANES_PER_SM = 128
@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--seconds", type=float, default=None,
                     help="shorten the scene (profiling captures); the benchmark default is 4 s")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tile-config", type=int, default=None, help="synthesis tile configuration id")
     return ap.parse_args()
 
 
@@ -197,6 +198,8 @@ def run_gpu(args):
         spec.duration = n / spec.fs
     if world > 1 and rank > 0:  # an independent scene per rank (own source signal)
         spec = W.with_signal(spec, W.pink(2 + 1000 * rank, spec.n_in))
+    if args.tile_config is not None:
+        api.set_tile_config(args.tile_config)
     room = api.Room.from_spec(spec)
     n_img = room.image_count()[0]
     n_out = spec.n_in

@@ -336,8 +336,8 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     const int64_t tau_bound = int64_t(std::ceil(dmax * R->d.fs / R->d.c)) + 2;
     const int64_t zlo = -tau_bound - 16;
     const int64_t zhi = std::max(n_out[s], n_in[s] + R->d.taps) + 16;
-    S.z_m0 = (zlo - 3) / 4 * 4;  // round toward -inf to a multiple of 4 (zlo < 0)
-    S.z_len = ((zhi - S.z_m0) + 3) / 4 * 4;
+    S.z_m0 = zlo;
+    S.z_len = zhi - zlo;
     S.z_base = z_acc;
     S.part_base = part_acc;
     // trajectory evaluated up to the last knot
@@ -358,7 +358,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     }
     img_acc += S.n_images;
     knot_acc += kfirst;
-    z_acc += int64_t(kZRows) * S.z_len;
+    z_acc += int64_t(kZQuadRows) * S.z_len;
     part_acc += int64_t(S.n_mics) * S.n_blocks * S.n_out;
   }
   P.taps = rooms[0]->d.taps;
@@ -379,7 +379,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.off_code = off; off = align256(off + 4 * I);
   P.off_gain = off; off = align256(off + 4 * I);
   P.off_knots = off; off = align256(off + 24 * size_t(knot_acc));
-  P.off_z = off; off = align256(off + 4 * size_t(z_acc));
+  P.off_z = off; off = align256(off + 16 * size_t(z_acc));
   P.off_part = off; off = align256(off + 4 * size_t(part_acc));
   P.fwd_bytes = off;
   if (I > (size_t(1) << 31)) return fail(MSRC_ERR_UNSUPPORTED, "more than 2^31 images in one call");
@@ -402,7 +402,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.img_code = reinterpret_cast<uint32_t*>(ws + P.off_code);
   a.p.img_gain = reinterpret_cast<float*>(ws + P.off_gain);
   a.p.knot_pos = reinterpret_cast<double*>(ws + P.off_knots);
-  a.p.z = reinterpret_cast<float*>(ws + P.off_z);
+  a.p.z = reinterpret_cast<float4*>(ws + P.off_z);
   a.p.part = reinterpret_cast<float*>(ws + P.off_part);
   std::memcpy(a.farrow, rooms[0]->farrow, sizeof(a.farrow));
   a.taps = P.kL;

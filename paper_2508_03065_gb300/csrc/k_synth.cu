@@ -60,9 +60,10 @@ __global__ void __launch_bounds__(kPreThreads) k_prefilter(const __grid_constant
     for (int r = 0; r < kZRows; ++r)
       acc[r] = fmaf(a.farrow[r / kFarrowCoef][r % kFarrowCoef][kk], xv, acc[r]);
   }
-  float* z = a.p.z + S.z_base + col;
+  float4* z = a.p.z + S.z_base + col;
 #pragma unroll
-  for (int r = 0; r < kZRows; ++r) z[int64_t(r) * S.z_len] = acc[r];
+  for (int qr = 0; qr < kZQuadRows; ++qr)
+    z[int64_t(qr) * S.z_len] = make_float4(acc[4 * qr], acc[4 * qr + 1], acc[4 * qr + 2], acc[4 * qr + 3]);
 }
 
 // ------------------------------------------------------------------ synthesis
@@ -74,32 +75,41 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-// One image-sample from shared rows of stride kStride: delay interpolation,
-// read position, Farrow evaluation, gain. Returns g * e.
+// Farrow polynomial of one image-sample from its two quads (Horner in v).
+__device__ __forceinline__ float horner8(const float4 lo, const float4 hi, float v) {
+  float e = fmaf(hi.w, v, hi.z);
+  e = fmaf(e, v, hi.y);
+  e = fmaf(e, v, hi.x);
+  e = fmaf(e, v, lo.w);
+  e = fmaf(e, v, lo.z);
+  e = fmaf(e, v, lo.y);
+  return fmaf(e, v, lo.x);
+}
+
+// acc += (beta_i / (4 pi d_i(n))) e_i(n) for one image-sample read from the
+// staged quads (quad row stride kStride). gain = beta_i / (4 pi) * fs / c, so
+// that the gain is gain / tau with tau the delay in samples.
 template <int kStride>
-__device__ __forceinline__ float image_sample(const float* zs, const int4 rec, int rm, float rf,
-                                              float cfs, float gain, unsigned wmax) {
+__device__ __forceinline__ float image_sample(const float4* zs, const int4 rec, int rm, float rf,
+                                              float gain, unsigned wmax, float acc) {
   const DelaySplit ds = split_delay(rec, rm, rf, wmax);
-  const float* zp = zs + (ds.hi ? kFarrowCoef * kStride : 0) + ds.col;
-  float e = zp[kFarrowDeg * kStride];
-#pragma unroll
-  for (int qq = kFarrowDeg - 1; qq >= 0; --qq) e = fmaf(e, ds.v, zp[qq * kStride]);
-  const float d = fmaf(rf, __int_as_float(rec.z) * cfs, __int_as_float(rec.w));
-  return __fdividef(gain, d) * e;
+  const float4* zp = zs + (ds.hi ? 2 * kStride : 0) + ds.col;
+  const float e = horner8(zp[0], zp[kStride], ds.v);
+  return fmaf(__fdividef(gain, ds.tau), e, acc);
 }
 
 template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock>
 __global__ void __launch_bounds__(kThreads) k_synth(const __grid_constant__ KernelArgs a) {
-  extern __shared__ __align__(16) float smem[];
-  float* zs = smem;                                              // kZRows x kWcap
-  int4* rec_s = reinterpret_cast<int4*>(smem + kZRows * kWcap);  // kRecCap records
+  extern __shared__ __align__(16) float4 smem4[];
+  float4* zs = smem4;                                            // kZQuadRows x kWcap quads
+  int4* rec_s = reinterpret_cast<int4*>(smem4 + kZQuadRows * kWcap);  // kRecCap records
   // prologue scratch aliases the z window (used before the window is staged)
-  float4* u_s = reinterpret_cast<float4*>(smem);
+  float4* u_s = smem4;
   float4* anc_s = u_s + kThreads * kChunks + 4;                  // 2 x kBlock
   __shared__ int s_item;
   __shared__ float s_red[2][kThreads / 32];
   constexpr int kTile = kThreads * kChunks;
-  static_assert((kTile + 4) * 4 + 2 * kBlock * 4 <= kZRows * kWcap, "prologue scratch");
+  static_assert(kTile + 4 + 2 * kBlock <= kZQuadRows * kWcap, "prologue scratch");
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
 
@@ -134,23 +144,23 @@ __global__ void __launch_bounds__(kThreads) k_synth(const __grid_constant__ Kern
       tmin = fminf(tmin, s_red[0][w]);
       tmax = fmaxf(tmax, s_red[1][w]);
     }
-    const int m_lo = (g.n0 - int(ceilf(tmax)) - 2) & ~3;
+    const int m_lo = g.n0 - int(ceilf(tmax)) - 2;
     const int m_hi = g.n_end - int(floorf(tmin)) + 2;
-    const int width = ((m_hi - m_lo + 1) + 3) & ~3;
+    const int width = m_hi - m_lo + 1;
     const bool in_smem = width <= kWcap;
 
-    // --- stage the z window [m_lo, m_lo + width) of all rows
-    const float* zg = a.p.z + S.z_base;
+    // --- stage the z window [m_lo, m_lo + width) of all quad rows
+    const float4* zg = a.p.z + S.z_base;
     if (in_smem) {
       const int64_t lo_c = max(int64_t(m_lo), S.z_m0);
       const int64_t hi_c = min(int64_t(m_lo) + width, S.z_m0 + S.z_len);
       if ((lo_c != m_lo || hi_c != int64_t(m_lo) + width) && threadIdx.x == 0)
         atomicOr(a.p.err, kErrWindowClamp);
-      const int vec = int(hi_c > lo_c ? hi_c - lo_c : int64_t(0)) >> 2;
+      const int cnt_c = int(hi_c > lo_c ? hi_c - lo_c : int64_t(0));
       const int dst0 = int(lo_c - m_lo);
-      for (int i = threadIdx.x; i < kZRows * vec; i += kThreads) {
-        const int r = i / vec, c4 = i - r * vec;
-        cp_async16(zs + r * kWcap + dst0 + 4 * c4, zg + int64_t(r) * S.z_len + (lo_c - S.z_m0) + 4 * c4);
+      for (int i = threadIdx.x; i < kZQuadRows * cnt_c; i += kThreads) {
+        const int r = i / cnt_c, c = i - r * cnt_c;
+        cp_async16(zs + r * kWcap + dst0 + c, zg + int64_t(r) * S.z_len + (lo_c - S.z_m0) + c);
       }
       cp_async_wait_all();
     }
@@ -173,46 +183,41 @@ __global__ void __launch_bounds__(kThreads) k_synth(const __grid_constant__ Kern
       rm[c] = r - (in_smem ? m_lo : int(S.z_m0));
       acc[c] = 0.0f;
     }
-    const float cfs = S.c_over_fs;
+    const float fsc = float(S.fs / S.c);
     const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
     if (in_smem) {
       const unsigned wmax = unsigned(width - 1);
       int ib = 0;
       for (; ib + 1 < g.cnt; ib += 2) {
-        const float g0 = __ldg(gain + ib), g1 = __ldg(gain + ib + 1);
+        const float g0 = __ldg(gain + ib) * fsc, g1 = __ldg(gain + ib + 1) * fsc;
         const int4* r0 = rec_s + ib * nrec;
         const int4* r1 = r0 + nrec;
 #pragma unroll
         for (int c = 0; c < kChunks; ++c) {
-          const float e0 = image_sample<kWcap>(zs, r0[jc[c]], rm[c], rf[c], cfs, g0, wmax);
-          const float e1 = image_sample<kWcap>(zs, r1[jc[c]], rm[c], rf[c], cfs, g1, wmax);
-          acc[c] += e0 + e1;
+          acc[c] = image_sample<kWcap>(zs, r0[jc[c]], rm[c], rf[c], g0, wmax, acc[c]);
+          acc[c] = image_sample<kWcap>(zs, r1[jc[c]], rm[c], rf[c], g1, wmax, acc[c]);
         }
       }
       if (ib < g.cnt) {
-        const float g0 = __ldg(gain + ib);
+        const float g0 = __ldg(gain + ib) * fsc;
         const int4* r0 = rec_s + ib * nrec;
 #pragma unroll
         for (int c = 0; c < kChunks; ++c)
-          acc[c] += image_sample<kWcap>(zs, r0[jc[c]], rm[c], rf[c], cfs, g0, wmax);
+          acc[c] = image_sample<kWcap>(zs, r0[jc[c]], rm[c], rf[c], g0, wmax, acc[c]);
       }
     } else {
-      // window wider than shared memory: read the L2-resident rows directly
+      // window wider than shared memory: read the L2-resident quads directly
       const unsigned zmax = unsigned(S.z_len - 1);
       const int64_t zl = S.z_len;
       for (int ib = 0; ib < g.cnt; ++ib) {
-        const float g0 = __ldg(gain + ib);
+        const float g0 = __ldg(gain + ib) * fsc;
         const int4* r0 = rec_s + ib * nrec;
 #pragma unroll
         for (int c = 0; c < kChunks; ++c) {
-          const int4 R = r0[jc[c]];
-          const DelaySplit ds = split_delay(R, rm[c], rf[c], zmax);
-          const float* zp = zg + (ds.hi ? int64_t(kFarrowCoef) * zl : int64_t(0)) + ds.col;
-          float e = __ldg(zp + int64_t(kFarrowDeg) * zl);
-#pragma unroll
-          for (int qq = kFarrowDeg - 1; qq >= 0; --qq) e = fmaf(e, ds.v, __ldg(zp + int64_t(qq) * zl));
-          const float d = fmaf(rf[c], __int_as_float(R.z) * cfs, __int_as_float(R.w));
-          acc[c] = fmaf(__fdividef(g0, d), e, acc[c]);
+          const DelaySplit ds = split_delay(r0[jc[c]], rm[c], rf[c], zmax);
+          const float4* zp = zg + (ds.hi ? 2 * zl : int64_t(0)) + ds.col;
+          const float e = horner8(__ldg(zp), __ldg(zp + zl), ds.v);
+          acc[c] = fmaf(__fdividef(g0, ds.tau), e, acc[c]);
         }
       }
     }
@@ -248,7 +253,7 @@ __global__ void k_reduce(const __grid_constant__ KernelArgs a) {
 template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock>
 cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
   auto kern = k_synth<kThreads, kChunks, kWcap, kRecCap, kBlock>;
-  const size_t smem = size_t(kZRows) * kWcap * sizeof(float) + size_t(kRecCap) * sizeof(int4);
+  const size_t smem = size_t(kZQuadRows) * kWcap * sizeof(float4) + size_t(kRecCap) * sizeof(int4);
   static int grid = 0;
   if (grid == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -272,10 +277,10 @@ cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
 
 // Tile configurations of the synthesis launch (see TileConfig).
 #define MSRC_TILE_CONFIGS(X)          \
-  X(0, 512, 2, 2816, 4096, 256)       \
-  X(1, 256, 2, 1408, 2048, 256)       \
-  X(2, 256, 3, 1664, 2304, 192)       \
-  X(3, 512, 1, 1536, 2048, 256)
+  X(0, 512, 2, 2688, 3328, 256)       \
+  X(1, 256, 2, 1280, 1664, 256)       \
+  X(2, 384, 2, 2432, 3072, 256)       \
+  X(3, 1024, 1, 2688, 3328, 256)
 
 static const TileConfig kConfigs[] = {
 #define MSRC_ROW(id, th, ch, wc, rc, bl) {th, ch, wc, rc, bl},

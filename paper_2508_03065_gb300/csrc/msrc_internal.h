@@ -14,11 +14,15 @@ namespace msrc {
 // Signal-side Farrow structure (Sec. II-B, Eq. 5): the tap weight of tap k is a
 // degree-kFarrowDeg polynomial in a local variable v of the fractional delay,
 // piecewise over kFarrowSegs segments of [0, 1). The prefilter produces one
-// signal row per (segment, power): z[s][q][m] = sum_k c[s][q][k] x[m - k].
+// signal row per (segment, power): z[s][q][m] = sum_k c[s][q][k] x[m - k],
+// stored as float4 "quads" (powers 4h .. 4h+3 of segment s in quad row 2s + h)
+// so that one image-sample gathers its 8 values with two 16-byte loads.
 constexpr int kFarrowSegs = 2;
-constexpr int kFarrowDeg = 6;
+constexpr int kFarrowDeg = 7;
 constexpr int kFarrowCoef = kFarrowDeg + 1;
 constexpr int kZRows = kFarrowSegs * kFarrowCoef;
+constexpr int kZQuadRows = kZRows / 4;
+static_assert(kFarrowCoef == 8 && kFarrowSegs == 2, "quad layout assumes 2 segments x 8 coefficients");
 constexpr int kMaxTaps = 64;
 constexpr int kMaxScenesInline = 1;
 
@@ -54,9 +58,9 @@ struct SceneDev {
   int64_t knot_units_first[MSRC_MAX_TIERS];// prefix over tiers of (J_t + 1)
   int64_t part_base;                       // first partial-sum float
   int64_t n_in, n_out;
-  int64_t z_base;                          // first float of the z rows
-  int64_t z_len;                           // floats per z row (multiple of 4)
-  int64_t z_m0;                            // sample index of z column 0 (multiple of 4)
+  int64_t z_base;                          // first quad of the z rows
+  int64_t z_len;                           // quads (samples) per quad row
+  int64_t z_m0;                            // sample index of z column 0
   const float* x;
   float* y;
   float c_over_fs;                         // metres per sample of delay
@@ -96,7 +100,7 @@ struct DevicePtrs {
   uint32_t* img_code;            // packed lattice triple and parity
   float* img_gain;               // beta_i / (4 pi)
   double* knot_pos;              // s(t_j), 3 doubles per knot
-  float* z;                      // prefiltered rows
+  float4* z;                     // prefiltered rows (kZQuadRows quad rows per scene)
   float* part;                   // partial sums
 };
 

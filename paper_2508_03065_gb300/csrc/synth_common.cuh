@@ -66,11 +66,12 @@ __device__ __forceinline__ void knot_increment(const float4 A, const float4 U, f
 }
 
 // Records of the item's images over its intervals, in shared memory:
-//   rec_s[ib * (nk - 1) + jj] = {I = n_j - D_a, phi_j = tau_j - D_a,
-//                                (phi_{j+1} - phi_j) / N_t, d_j},  j = jf + jj,
-// where D_a = floor(tau) at the anchor knot jf (FP64) and tau = d fs / c.
-// u_s (nk entries) and anc_s (2 * cnt entries) are scratch. Returns this
-// thread's min / max of tau over its knots (window bounds of the item).
+//   rec_s[ib * (nk - 1) + jj] = {I_j = n_j - D_a, psi_j = -phi_j - 1/2,
+//                                -(phi_{j+1} - phi_j) / N_t, D_a - 1/2},  j = jf + jj,
+// where tau = d fs / c, D_a = floor(tau) at the anchor knot jf (FP64) and
+// phi_j = tau_j - D_a. u_s (nk entries) and anc_s (2 * cnt entries) are
+// scratch. Returns this thread's min / max of tau over its knots (window
+// bounds of the item).
 template <int kThreads>
 __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, int4* rec_s,
                              float4* u_s, float4* anc_s, float* tmin_out, float* tmax_out) {
@@ -112,8 +113,8 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     float phi0, phi1, d0, d1;
     knot_increment(A, u_s[jj], fsc, A2.x, &phi0, &d0);
     knot_increment(A, u_s[jj + 1], fsc, A2.x, &phi1, &d1);
-    rec_s[pidx] = make_int4(__float_as_int(A2.y) + jj * g.N, __float_as_int(phi0),
-                            __float_as_int((phi1 - phi0) * invN), __float_as_int(d0));
+    rec_s[pidx] = make_int4(__float_as_int(A2.y) + jj * g.N, __float_as_int(-phi0 - 0.5f),
+                            __float_as_int((phi0 - phi1) * invN), __float_as_int(A2.z - 0.5f));
     tmin = fminf(tmin, A2.z + fminf(phi0, phi1));
     tmax = fmaxf(tmax, A2.z + fmaxf(phi0, phi1));
   }
@@ -121,30 +122,32 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
   *tmax_out = tmax;
 }
 
-// Interpolated delay of one image-sample split into the read position (column
-// `col` of the window, clamped to [0, wmax]), the Farrow segment `hi` and the
-// local variable v in [-1, 1] of the fraction alpha in [0, 1].
-// rec = {I_j, phi_j, slope_j, d_j}; rm = r - m_lo where r = n - n_j.
-static_assert(kFarrowSegs == 2, "split_delay assumes two Farrow segments");
+// Interpolated delay of one image-sample split into the read position m0
+// (window column `col`, clamped to [0, wmax]), the Farrow segment `hi` of the
+// fraction alpha and its local variable v in [-1, 1], and the delay tau in
+// samples. With y = -phi(n) - 1/2, k = round(y) is floor(-phi) except when phi
+// is an integer, where it may be one less and alpha = 1 instead of 0: the two
+// readings give the same value because the fractional-delay kernel is
+// continuous across alpha = 0 / 1 (h(k; 1) = h(k + 1; 0)).
+// rec = {I_j, psi_j, -slope_j, D_a - 1/2}; rm = r - m_lo where r = n - n_j.
 struct DelaySplit {
   unsigned col;
   bool hi;
   float v;
-  float alpha;
+  float tau;
 };
 
 __device__ __forceinline__ DelaySplit split_delay(const int4 rec, int rm, float rf, unsigned wmax) {
-  const float phi = fmaf(rf, __int_as_float(rec.z), __int_as_float(rec.y));
-  // ceil(phi) via the round-to-nearest magic constant 1.5 * 2^23
-  const float q = phi + 12582912.0f;
-  const int kr = __float_as_int(q) - 0x4B400000;
-  const float cf = q - 12582912.0f;
-  const bool up = cf < phi;
+  const float y = fmaf(rf, __int_as_float(rec.z), __int_as_float(rec.y));
+  const float q = y + 12582912.0f;  // round to nearest integer (1.5 * 2^23)
+  const int k = __float_as_int(q) - 0x4B400000;
+  const float a = y - (q - 12582912.0f);  // alpha - 1/2, in [-1/2, 1/2]
   DelaySplit ds;
-  ds.alpha = (cf - phi) + (up ? 1.0f : 0.0f);  // in [0, 1]
-  ds.col = min(unsigned(rm + rec.x - kr - (up ? 1 : 0)), wmax);
-  ds.hi = ds.alpha >= 0.5f;
-  ds.v = fmaf(ds.alpha, 4.0f, ds.hi ? -3.0f : -1.0f);
+  ds.col = min(unsigned(rm + rec.x + k), wmax);
+  const float v0 = fmaf(a, 4.0f, 1.0f);   // 4 alpha - 1, in [-1, 3]
+  ds.hi = v0 >= 1.0f;
+  ds.v = ds.hi ? v0 - 2.0f : v0;
+  ds.tau = __int_as_float(rec.w) - y;     // tau(n) = D_a + phi(n)
   return ds;
 }
 
