@@ -102,6 +102,11 @@ msrc_status msrc_destroy_room(msrc_room_t room);
 msrc_status msrc_set_trajectory(msrc_room_t room, const msrc_traj_desc* traj,
                                 const double* mics_xyz, int32_t n_mics);
 
+/* Replaces the six wall reflection coefficients of a room (beta: 6 doubles in
+ * [0, 1], host memory); the Farrow fit and the trajectory are kept. Used by
+ * optimisation loops that update the walls between forward calls. */
+msrc_status msrc_set_reflection(msrc_room_t room, const double* beta);
+
 /* Workspace bytes needed by msrc_synthesize (*fwd_bytes) and by
  * msrc_synthesize_backward (*bwd_bytes) for these rooms, input lengths
  * n_in[r] and output lengths n_out[r] (host arrays of n_rooms entries).

@@ -74,6 +74,15 @@ class Room:
                                            m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                            int(m.shape[0])))
         self.n_mics = int(m.shape[0])
+        self.traj_kind, self.n_ctrl, self.duration = int(kind), int(n_ctrl), float(duration)
+        self.mics = m.copy()
+        self.params = np.array(p, np.float64)
+
+    def set_reflection(self, beta) -> None:
+        lib = _lib.load()
+        b = np.ascontiguousarray(np.asarray(beta, np.float64).reshape(6))
+        _lib.check(lib.msrc_set_reflection(self._h, b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        self._desc.beta[:] = [float(v) for v in b]
 
     @property
     def handle(self):
@@ -210,3 +219,66 @@ def profile_read():
     n = ctypes.c_int32()
     _lib.check(_lib.load().msrc_profile_read(ms, ctypes.byref(n)))
     return [float(v) for v in ms], int(n.value)
+
+
+def synthesize_backward(rooms: Sequence[Room], xs: Sequence[torch.Tensor], dys: Sequence[torch.Tensor],
+                        want_dx: bool = True, want_params: bool = True, want_beta: bool = True,
+                        workspace: Optional[Workspace] = None, stream: Optional[torch.cuda.Stream] = None):
+    """Reverse mode of synthesize(): for upstream gradients dys[r] of shape
+    (n_mics, n_out) returns, per room, (dx, dparams, dbeta): dL/dx (float32,
+    n_in), dL/d trajectory parameters (float64, 48, laid out like the
+    trajectory parameters) and dL/d wall reflection coefficients (float64, 6),
+    each None when not requested."""
+    lib = _lib.load()
+    xs = [x.contiguous() for x in xs]
+    dys = [d.contiguous().float() for d in dys]
+    n_in = [int(x.numel()) for x in xs]
+    n_out = [int(d.shape[-1]) for d in dys]
+    dev = xs[0].device
+    dx = [torch.empty(n, dtype=torch.float32, device=dev) for n in n_in] if want_dx else None
+    dp = [torch.zeros(48, dtype=torch.float64, device=dev) for _ in rooms] if want_params else None
+    db = [torch.zeros(6, dtype=torch.float64, device=dev) for _ in rooms] if want_beta else None
+    _, bwd = workspace_size(rooms, n_in, n_out)
+    ws = workspace or _workspace(dev)
+    buf = ws.get(bwd)
+    hs = _lib.ptr_array([r.handle.value for r in rooms])
+    arr = lambda ts: _lib.ptr_array([t.data_ptr() for t in ts]) if ts is not None else None  # noqa: E731
+    _lib.check(lib.msrc_synthesize_backward(hs, len(rooms), arr(xs), _lib.i64_array(n_in), arr(dys),
+                                            _lib.i64_array(n_out), arr(dx), arr(dp), arr(db),
+                                            ctypes.c_void_p(buf.data_ptr()), buf.numel(),
+                                            _stream_handle(stream)))
+    out = []
+    for r in range(len(rooms)):
+        out.append((dx[r] if dx else None, dp[r] if dp else None, db[r] if db else None))
+    return out
+
+
+class MovingSourceSynthesis(torch.autograd.Function):
+    """y = synthesis(x; trajectory parameters, wall coefficients) with gradients
+    for all three. `params` (48) and `beta` (6) are float64 tensors; the room
+    keeps its geometry, tiers, taps and microphones."""
+
+    @staticmethod
+    def forward(ctx, x, params, beta, room: Room):
+        p = params.detach().cpu().numpy().astype(np.float64)
+        room.set_trajectory(room.traj_kind, p, room.duration, room.mics, room.n_ctrl)
+        room.set_reflection(beta.detach().cpu().numpy())
+        y = synthesize([room], [x.detach().float()])[0]
+        ctx.room = room
+        ctx.save_for_backward(x)
+        ctx.params_device, ctx.beta_device = params.device, beta.device
+        return y
+
+    @staticmethod
+    def backward(ctx, dy):
+        (x,) = ctx.saved_tensors
+        need_x, need_p, need_b = ctx.needs_input_grad[:3]
+        dx, dp, db = synthesize_backward([ctx.room], [x.detach().float()], [dy], want_dx=need_x,
+                                         want_params=need_p, want_beta=need_b)[0]
+        return (dx if need_x else None, dp.to(ctx.params_device) if need_p else None,
+                db.to(ctx.beta_device) if need_b else None, None)
+
+
+def synthesize_ad(room: Room, x: torch.Tensor, params: torch.Tensor, beta: torch.Tensor) -> torch.Tensor:
+    """Differentiable forward synthesis of one room (see MovingSourceSynthesis)."""
+    return MovingSourceSynthesis.apply(x, params, beta, room)

@@ -12,9 +12,8 @@
 #include "msrc_internal.h"
 
 namespace msrc {
-cudaError_t launch_backward(const KernelArgs& a, const float* const* dy, float* const* dx,
-                            double* const* dparams, double* const* dbeta, cudaStream_t st);
-size_t backward_extra_bytes(const KernelArgs& a);
+cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st);
+size_t backward_unit_cap();
 }  // namespace msrc
 
 using namespace msrc;
@@ -253,20 +252,27 @@ struct Plan {
   size_t off_desc = 0, off_keys_in = 0, off_keys_out = 0, off_vals_in = 0, off_vals_out = 0;
   size_t off_sort = 0, sort_bytes = 0, off_code = 0, off_gain = 0, off_knots = 0;
   size_t off_z = 0, off_part = 0, fwd_bytes = 0, desc_bytes = 0;
+  // reverse mode
+  bool backward = false;
+  size_t off_dxb = 0, off_kslot = 0, off_bpart = 0, off_gk = 0;
   int kL = 32;
   int taps = 32;
 };
 
+// Workspace layout and per-scene descriptors of one call. Forward mode uses
+// the selected synthesis tile configuration; reverse mode its own (one sample
+// per thread) and adds the gradient buffers.
 msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, const int64_t* n_out,
-                      Plan& P) {
+                      Plan& P, bool backward = false) {
   if (!rooms || n <= 0 || !n_in || !n_out)
     return fail(MSRC_ERR_INVALID_ARG, "null rooms/lengths or n_rooms <= 0");
-  const int cfg = g_tile_config;
-  const TileConfig& tc = tile_config(cfg);
+  P.backward = backward;
+  const TileConfig& tc = backward ? backward_tile_config() : tile_config(g_tile_config);
   const int T = tc.threads * tc.chunks;
   P.scenes.resize(n);
   for (auto& v : P.prefix) v.assign(n + 1, 0);
   int64_t img_acc = 0, knot_acc = 0, z_acc = 0, part_acc = 0;
+  int64_t dxb_acc = 0, kslot_acc = 0, bpart_acc = 0;
   for (int s = 0; s < n; ++s) {
     msrc_room* R = rooms[s];
     if (!R) return fail(MSRC_ERR_INVALID_ARG, "room %d is null", s);
@@ -318,7 +324,8 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
       const int rec_per_image = (T - 1) / N + 2;
       if (rec_per_image > tc.reccap)
         return fail(MSRC_ERR_UNSUPPORTED, "tile configuration too small for knot spacing %d", N);
-      const int B = std::max(1, std::min(tc.block, tc.reccap / rec_per_image));
+      int B = std::max(1, std::min(tc.block, tc.reccap / rec_per_image));
+      if (backward) B = std::max(1, std::min(B, int(backward_unit_cap()) / (rec_per_image + 1)));
       S.tier_block_images[t] = B;
       S.tier_blocks[t] = (S.tier_count[t] + B - 1) / B;
       S.block_first[t] = blk;
@@ -329,6 +336,20 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     }
     S.n_blocks = blk;
     S.img_base = img_acc;
+    if (backward) {
+      int64_t kslot = 0;
+      for (int t = 0; t < S.n_tiers; ++t) {
+        S.kcap[t] = (T - 1) / S.tier_step[t] + 3;
+        S.kslot_first[t] = kslot_acc + kslot;
+        kslot += int64_t(S.tier_blocks[t]) * S.n_tiles * S.kcap[t];
+      }
+      S.kslot_mic_stride = kslot;
+      S.dxb_base = dxb_acc;
+      S.bpart_base = bpart_acc;
+      kslot_acc += int64_t(S.n_mics) * kslot;
+      dxb_acc += int64_t(S.n_mics) * S.n_blocks * S.n_in;
+      bpart_acc += int64_t(S.n_mics) * S.n_blocks * 8;
+    }
     // z rows cover every read position: n - tau with tau in [0, tau_bound]
     double maxL = 0, diag = 0;
     for (int d = 0; d < 3; ++d) { maxL = std::max(maxL, R->d.dims[d]); diag += R->d.dims[d] * R->d.dims[d]; }
@@ -347,9 +368,10 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
 
     const int64_t u_enum = S.n_images;
     const int64_t u_knots = kfirst;
-    const int64_t u_rec = 0;
+    const int64_t u_rec = backward ? S.n_in : 0;  // reverse mode: dx samples
     const int64_t u_z = (S.z_len + 255) / 256;
-    const int64_t u_item = int64_t(S.n_mics) * S.n_blocks * S.n_tiles;
+    const int64_t u_item = backward ? int64_t(S.n_mics) * S.n_blocks
+                                    : int64_t(S.n_mics) * S.n_blocks * S.n_tiles;
     const int64_t u_red = int64_t(S.n_mics) * S.n_out;
     const int64_t u[6] = {u_enum, u_knots, u_rec, u_z, u_item, u_red};
     for (int k = 0; k < 6; ++k) {
@@ -380,7 +402,14 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.off_gain = off; off = align256(off + 4 * I);
   P.off_knots = off; off = align256(off + 24 * size_t(knot_acc));
   P.off_z = off; off = align256(off + 16 * size_t(z_acc));
-  P.off_part = off; off = align256(off + 4 * size_t(part_acc));
+  if (!backward) {
+    P.off_part = off; off = align256(off + 4 * size_t(part_acc));
+  } else {
+    P.off_dxb = off; off = align256(off + 4 * size_t(dxb_acc));
+    P.off_kslot = off; off = align256(off + 12 * size_t(kslot_acc));
+    P.off_bpart = off; off = align256(off + 4 * size_t(bpart_acc));
+    P.off_gk = off; off = align256(off + 24 * size_t(knot_acc));
+  }
   P.fwd_bytes = off;
   if (I > (size_t(1) << 31)) return fail(MSRC_ERR_UNSUPPORTED, "more than 2^31 images in one call");
   return MSRC_OK;
@@ -404,6 +433,12 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.knot_pos = reinterpret_cast<double*>(ws + P.off_knots);
   a.p.z = reinterpret_cast<float4*>(ws + P.off_z);
   a.p.part = reinterpret_cast<float*>(ws + P.off_part);
+  if (P.backward) {
+    a.p.dxb = reinterpret_cast<float*>(ws + P.off_dxb);
+    a.p.kslot = reinterpret_cast<float*>(ws + P.off_kslot);
+    a.p.bpart = reinterpret_cast<float*>(ws + P.off_bpart);
+    a.p.gk = reinterpret_cast<double*>(ws + P.off_gk);
+  }
   std::memcpy(a.farrow, rooms[0]->farrow, sizeof(a.farrow));
   a.taps = P.kL;
   if (a.n_scenes > 1) {
@@ -413,7 +448,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
     const int n1 = a.n_scenes + 1;
     a.tab.enum_prefix = pre;
     a.tab.knots_prefix = pre + n1;
-    a.tab.unused_prefix = pre + 2 * n1;
+    a.tab.dx_prefix = pre + 2 * n1;
     a.tab.z_prefix = pre + 3 * n1;
     a.tab.item_prefix = pre + 4 * n1;
     a.tab.red_prefix = pre + 5 * n1;
@@ -588,6 +623,15 @@ msrc_status msrc_set_trajectory(msrc_room_t room, const msrc_traj_desc* traj, co
   return MSRC_OK;
 }
 
+msrc_status msrc_set_reflection(msrc_room_t room, const double* beta) {
+  if (!room || !beta) return fail(MSRC_ERR_INVALID_ARG, "null argument");
+  for (int w = 0; w < 6; ++w)
+    if (!(beta[w] >= 0.0 && beta[w] <= 1.0))
+      return fail(MSRC_ERR_INVALID_ARG, "reflection coefficient %d must be in [0, 1]", w);
+  for (int w = 0; w < 6; ++w) room->d.beta[w] = beta[w];
+  return MSRC_OK;
+}
+
 msrc_status msrc_workspace_size(const msrc_room_t* rooms, int32_t n_rooms, const int64_t* n_in,
                                 const int64_t* n_out, size_t* fwd_bytes, size_t* bwd_bytes) {
   Plan P;
@@ -595,11 +639,10 @@ msrc_status msrc_workspace_size(const msrc_room_t* rooms, int32_t n_rooms, const
   if (s != MSRC_OK) return s;
   if (fwd_bytes) *fwd_bytes = P.fwd_bytes;
   if (bwd_bytes) {
-    KernelArgs* a = new (std::nothrow) KernelArgs;
-    if (!a) return fail(MSRC_ERR_INVALID_ARG, "out of host memory");
-    fill_args(P, rooms, reinterpret_cast<char*>(size_t(0)), *a);
-    *bwd_bytes = P.fwd_bytes + backward_extra_bytes(*a);
-    delete a;
+    Plan B;
+    s = make_plan(rooms, n_rooms, n_in, n_out, B, true);
+    if (s != MSRC_OK) return s;
+    *bwd_bytes = B.fwd_bytes;
   }
   return MSRC_OK;
 }
@@ -667,24 +710,22 @@ msrc_status msrc_synthesize_backward(const msrc_room_t* rooms, int32_t n_rooms, 
                                      double* const* dbeta_dev, void* ws, size_t ws_bytes, void* stream) {
   if (!x_dev || !dy_dev) return fail(MSRC_ERR_INVALID_ARG, "null signal pointer array");
   Plan P;
-  msrc_status s = make_plan(rooms, n_rooms, n_in, n_out, P);
+  msrc_status s = make_plan(rooms, n_rooms, n_in, n_out, P, true);
   if (s != MSRC_OK) return s;
   s = check_ws(P, ws, ws_bytes);
   if (s != MSRC_OK) return s;
   for (int r = 0; r < n_rooms; ++r) {
     if (!x_dev[r] || !dy_dev[r]) return fail(MSRC_ERR_INVALID_ARG, "room %d: null x or dy", r);
     P.scenes[r].x = x_dev[r];
-    P.scenes[r].y = nullptr;
+    P.scenes[r].dy = dy_dev[r];
+    P.scenes[r].dx = dx_dev ? dx_dev[r] : nullptr;
+    P.scenes[r].dparams = dparams_dev ? dparams_dev[r] : nullptr;
+    P.scenes[r].dbeta = dbeta_dev ? dbeta_dev[r] : nullptr;
   }
   char* w = static_cast<char*>(ws);
   KernelArgs* a = new (std::nothrow) KernelArgs;
   if (!a) return fail(MSRC_ERR_INVALID_ARG, "out of host memory");
   fill_args(P, rooms, w, *a);
-  const size_t need = P.fwd_bytes + backward_extra_bytes(*a);
-  if (ws_bytes < need) {
-    delete a;
-    return fail(MSRC_ERR_WORKSPACE, "workspace too small for backward: %zu < %zu", ws_bytes, need);
-  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   std::vector<char> blob;
   cudaError_t e = cudaMemsetAsync(w, 0, 256, st);
@@ -692,9 +733,8 @@ msrc_status msrc_synthesize_backward(const msrc_room_t* rooms, int32_t n_rooms, 
   s = upload_tables(P, w, st, blob);
   if (s != MSRC_OK) { delete a; return s; }
   e = launch_setup(*a, st);
-  if (e == cudaSuccess) e = launch_backward(*a, dy_dev, dx_dev, dparams_dev, dbeta_dev, st);
+  if (e == cudaSuccess) e = launch_backward_kernels(*a, st);
   delete a;
-  if (e == cudaErrorNotSupported) return fail(MSRC_ERR_UNSUPPORTED, "backward not available in this build");
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
   return MSRC_OK;
 }

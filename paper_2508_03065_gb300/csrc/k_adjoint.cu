@@ -1,13 +1,501 @@
-// Adjoint (reverse-mode) kernels of the synthesis path.
+// Reverse mode of the synthesis (adjoint of Eq. 8 with the Farrow structure of
+// Eq. 5 and the hierarchical knots of Sec. II-C).
+//
+// With e_i(n) = sum_q v^q z[seg][q][m0], g_i(n) = beta_i / (4 pi d_i(n)) and
+// y = sum_i g_i e_i, for an upstream gradient dy:
+//   dx[m]       = sum_{s,q,k} c[s][q][k] w[s][q][m + k],
+//                 w[s][q][m] = sum over image-samples with (seg, m0) = (s, m) of dy g v^q
+//   dL/dd_i(n)  = -dy g (fs/c) (4 de/dv + e / tau)         (tau = d fs / c)
+//   dL/dd_{i,j} = sum_n dL/dd_i(n) * (linear-interpolation weight of knot j)
+//   dL/ds(t_j)  = sum_i dL/dd_{i,j} (sigma_i o Delta_{i,j}) / d_{i,j}
+//   dL/dbeta_w  = sum_i (dbeta_i/dbeta_w) sum_n dy e / (4 pi d)
+// then the trajectory parameters through ds(t_j)/dparams.
+//
+// k_adjoint: persistent over (scene, microphone, image block) items. The CTA
+// walks the block's output tiles in order; per tile it recomputes the knots
+// (delays are recomputed, never stored), stages the z window, and for every
+// image lets each thread handle one output sample: the knot and reflection
+// gradients accumulate in registers (a lane's knots are the same for every
+// image), and dy g v^q is scattered into a shared w window. Within one image
+// no two samples share a (segment, column) bin, so images are separated by a
+// barrier and no atomics are used. Each tile's window is correlated with the
+// Farrow coefficients and added, in tile order, to the CTA's own dx row.
+// Windows wider than shared memory are processed in several column passes.
+// k_dx_final / k_knot_final / k_param_final / k_beta_final: fixed-order sums.
+#include <cstdint>
+
 #include "msrc_internal.h"
+#include "synth_common.cuh"
 
 namespace msrc {
+namespace {
 
-size_t backward_extra_bytes(const KernelArgs&) { return 0; }
+constexpr int kBwThreads = 512;   // one output sample per thread
+constexpr int kBwTile = kBwThreads;
+constexpr int kBwWcap = 1024;     // shared z / w window (samples)
+constexpr int kBwRecCap = 1024;   // records (image x interval)
+constexpr int kBwUnitCap = 1152;  // unit vectors (image x knot)
+constexpr int kBwBlock = 128;     // images per block at most
 
-cudaError_t launch_backward(const KernelArgs&, const float* const*, float* const*, double* const*,
-                            double* const*, cudaStream_t) {
-  return cudaErrorNotSupported;
+constexpr size_t kBwSmem = size_t(2 * kZQuadRows * kBwWcap) * sizeof(float4) +
+                           size_t(kBwRecCap) * sizeof(int4) + size_t(kBwUnitCap) * sizeof(float4) +
+                           size_t(2 * kBwBlock) * sizeof(float4) + size_t(6 * kBwTile) * sizeof(float);
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// dbeta_i / dbeta_w of beta_i = prod_w beta_w^{e_w} (FP64; handles beta_w = 0).
+__device__ void beta_weights(const SceneDev& S, uint32_t code, double out[6]) {
+  int n[3], p[3];
+  unpack_image(code, n, p);
+  int e[6];
+  for (int d = 0; d < 3; ++d) {
+    e[2 * d] = abs(n[d] - p[d]);
+    e[2 * d + 1] = abs(n[d]);
+  }
+  for (int w = 0; w < 6; ++w) {
+    if (e[w] == 0) { out[w] = 0.0; continue; }
+    double v = double(e[w]);
+    for (int r = 0; r < e[w] - 1; ++r) v *= S.beta[w];
+    for (int o = 0; o < 6; ++o)
+      if (o != w)
+        for (int r = 0; r < e[o]; ++r) v *= S.beta[o];
+    out[w] = v;
+  }
+}
+
+template <int kL>
+__global__ void __launch_bounds__(kBwThreads, 1) k_adjoint(const __grid_constant__ KernelArgs a) {
+  extern __shared__ __align__(16) float4 sm[];
+  float4* zs = sm;                                        // kZQuadRows x kBwWcap
+  float4* ws = zs + kZQuadRows * kBwWcap;                 // kZQuadRows x kBwWcap
+  int4* rec_s = reinterpret_cast<int4*>(ws + kZQuadRows * kBwWcap);
+  float4* unit_s = reinterpret_cast<float4*>(rec_s + kBwRecCap);
+  float4* bw_s = unit_s + kBwUnitCap;                     // 2 per image
+  float* kv_s = reinterpret_cast<float*>(bw_s + 2 * kBwBlock);  // 6 per sample
+  // prologue scratch aliases the w window
+  float4* u_s = ws;
+  float4* anc_s = ws + kBwTile + 4;
+  __shared__ int s_item;
+  __shared__ float s_red[2][kBwThreads / 32];
+  __shared__ float s_beta[kBwThreads / 32][6];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_item = int(atomicAdd(a.p.counter, 1u));
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= a.totals[4]) break;
+    int s = 0;
+    int64_t li = item;
+    if (a.n_scenes > 1) {
+      s = find_scene(a.tab.item_prefix, a.n_scenes, item);
+      li = item - a.tab.item_prefix[s];
+    }
+    const SceneDev& S = scene_of(a, s);
+    const int mic = int(li / S.n_blocks);
+    const int blk = int(li - int64_t(mic) * S.n_blocks);
+    const float fsc = float(S.fs / S.c);
+    float* dxrow = a.p.dxb + S.dxb_base + (int64_t(mic) * S.n_blocks + blk) * S.n_in;
+    for (int64_t i = threadIdx.x; i < S.n_in; i += kBwThreads) dxrow[i] = 0.0f;
+
+    // per-image gain and reflection-coefficient derivatives (fixed for the item)
+    ItemGeom g0 = item_geometry(S, int64_t(mic) * S.n_blocks * S.n_tiles + int64_t(blk) * S.n_tiles, kBwTile);
+    {
+      const uint32_t* codes = a.p.img_code + S.img_base + S.tier_first[g0.t] + g0.img0;
+      const float* gain = a.p.img_gain + S.img_base + S.tier_first[g0.t] + g0.img0;
+      for (int ib = threadIdx.x; ib < g0.cnt; ib += kBwThreads) {
+        double D[6];
+        beta_weights(S, codes[ib], D);
+        const float hb = float(1.0 / (4.0 * 3.14159265358979323846));
+        bw_s[2 * ib] = make_float4(float(D[0]) * hb, float(D[1]) * hb, float(D[2]) * hb, float(D[3]) * hb);
+        bw_s[2 * ib + 1] = make_float4(float(D[4]) * hb, float(D[5]) * hb, gain[ib] * fsc, 0.0f);
+      }
+    }
+    float bacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+
+    for (int tile = 0; tile < S.n_tiles; ++tile) {
+      const ItemGeom g = item_geometry(S, (int64_t(mic) * S.n_blocks + blk) * S.n_tiles + tile, kBwTile);
+      float tmin, tmax;
+      item_records<kBwThreads>(a, S, g, rec_s, u_s, anc_s, &tmin, &tmax);
+      // unit vectors (sigma o Delta) / d of every image at every knot of the tile
+      const int nrec = g.nk - 1;
+      for (int pidx = threadIdx.x; pidx < g.cnt * g.nk; pidx += kBwThreads) {
+        const int ib = pidx / g.nk, jj = pidx - ib * g.nk;
+        const float4 A = anc_s[2 * ib];
+        const float4 U = u_s[jj];
+        float phi, d;
+        knot_increment(A, U, fsc, 0.0f, &phi, &d);
+        const float inv = 1.0f / d;
+        unit_s[pidx] = make_float4((A.x + U.x) * inv, (A.y + U.y) * inv, (A.z + U.z) * inv, 0.0f);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+        tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+      }
+      if (lane == 0) { s_red[0][warp] = tmin; s_red[1][warp] = tmax; }
+      __syncthreads();
+      tmin = s_red[0][0];
+      tmax = s_red[1][0];
+      for (int w = 1; w < kBwThreads / 32; ++w) {
+        tmin = fminf(tmin, s_red[0][w]);
+        tmax = fmaxf(tmax, s_red[1][w]);
+      }
+      const int m_lo = g.n0 - int(ceilf(tmax)) - 2;
+      const int width = g.n_end - int(floorf(tmin)) + 2 - m_lo + 1;
+
+      // this thread's output sample
+      const int n = g.n0 + threadIdx.x;
+      const bool valid = n <= g.n_end;
+      const int nn = valid ? n : g.n_end;
+      const int j = nn / g.N;
+      const int r = nn - j * g.N;
+      const int jc = j - g.jf;
+      const float rf = float(r);
+      const float sN = rf / float(g.N);
+      const float dyv = valid ? __ldg(S.dy + int64_t(mic) * S.n_out + n) : 0.0f;
+      float v0x = 0.f, v0y = 0.f, v0z = 0.f, v1x = 0.f, v1y = 0.f, v1z = 0.f;
+      const float4* zg = a.p.z + S.z_base;
+
+      for (int p0 = 0; p0 < width; p0 += kBwWcap) {
+        const int pass_lo = m_lo + p0;
+        const int pw = min(kBwWcap, width - p0);
+        __syncthreads();  // previous users of zs / ws (prologue scratch, last pass) are done
+        {
+          const int64_t lo_c = max(int64_t(pass_lo), S.z_m0);
+          const int64_t hi_c = min(int64_t(pass_lo) + pw, S.z_m0 + S.z_len);
+          const int cnt_c = int(hi_c > lo_c ? hi_c - lo_c : int64_t(0));
+          const int dst0 = int(lo_c - pass_lo);
+          if (cnt_c != pw && threadIdx.x == 0) atomicOr(a.p.err, kErrWindowClamp);
+          for (int i = threadIdx.x; i < kZQuadRows * cnt_c; i += kBwThreads) {
+            const int rr = i / cnt_c, c = i - rr * cnt_c;
+            cp_async16(zs + rr * kBwWcap + dst0 + c, zg + int64_t(rr) * S.z_len + (lo_c - S.z_m0) + c);
+          }
+          for (int i = threadIdx.x; i < kZQuadRows * kBwWcap; i += kBwThreads)
+            ws[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+          cp_async_wait_all();
+        }
+        __syncthreads();
+        const int rm = r - pass_lo;
+        for (int ib = 0; ib < g.cnt; ++ib) {
+          const int4 rec = rec_s[ib * nrec + jc];
+          const float y = fmaf(rf, __int_as_float(rec.z), __int_as_float(rec.y));
+          const float q = y + 12582912.0f;
+          const int k = __float_as_int(q) - 0x4B400000;
+          const float al = y - (q - 12582912.0f);
+          const int col = rm + rec.x + k;
+          if (valid && unsigned(col) < unsigned(pw)) {
+            const float vv0 = fmaf(al, 4.0f, 1.0f);
+            const bool hi = vv0 >= 1.0f;
+            const float v = hi ? vv0 - 2.0f : vv0;
+            const float tau = __int_as_float(rec.w) - y;
+            const int base = (hi ? 2 * kBwWcap : 0) + col;
+            const float4 lo4 = zs[base], hi4 = zs[base + kBwWcap];
+            // e = P(v) and dP/dv together (Horner)
+            float pe = hi4.w, pd = 0.0f;
+            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, hi4.z);
+            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, hi4.y);
+            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, hi4.x);
+            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, lo4.w);
+            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, lo4.z);
+            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, lo4.y);
+            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, lo4.x);
+            const float rt = 1.0f / tau;
+            const float4 B0 = bw_s[2 * ib], B1 = bw_s[2 * ib + 1];
+            const float val = dyv * B1.z * rt;                       // dy g
+            const float ad = -val * fsc * fmaf(4.0f, pd, pe * rt);   // dL/dd_i(n)
+            const float4 U0 = unit_s[ib * g.nk + jc];
+            const float4 U1 = unit_s[ib * g.nk + jc + 1];
+            const float w1 = ad * sN, w0 = ad - w1;
+            v0x = fmaf(w0, U0.x, v0x); v0y = fmaf(w0, U0.y, v0y); v0z = fmaf(w0, U0.z, v0z);
+            v1x = fmaf(w1, U1.x, v1x); v1y = fmaf(w1, U1.y, v1y); v1z = fmaf(w1, U1.z, v1z);
+            const float hbv = dyv * pe * rt * fsc;                   // dy e / d (4 pi in B)
+            bacc[0] = fmaf(hbv, B0.x, bacc[0]); bacc[1] = fmaf(hbv, B0.y, bacc[1]);
+            bacc[2] = fmaf(hbv, B0.z, bacc[2]); bacc[3] = fmaf(hbv, B0.w, bacc[3]);
+            bacc[4] = fmaf(hbv, B1.x, bacc[4]); bacc[5] = fmaf(hbv, B1.y, bacc[5]);
+            // w[seg][q][m0] += dy g v^q
+            const float p1 = val * v, p2 = p1 * v, p3 = p2 * v, p4 = p3 * v, p5 = p4 * v, p6 = p5 * v,
+                        p7 = p6 * v;
+            float4 wa = ws[base], wb = ws[base + kBwWcap];
+            wa.x += val; wa.y += p1; wa.z += p2; wa.w += p3;
+            wb.x += p4; wb.y += p5; wb.z += p6; wb.w += p7;
+            ws[base] = wa;
+            ws[base + kBwWcap] = wb;
+          }
+          __syncthreads();  // the next image may write the same bins
+        }
+        // dx[m'] += sum_{row, k} c[row][k] w[row][m' + k], 4 consecutive m' per thread
+        const int n_outv = pw + kL - 1;
+        for (int o4 = threadIdx.x; 4 * o4 < n_outv; o4 += kBwThreads) {
+          const int mp0 = pass_lo - kL / 2 + 1 + 4 * o4;  // first m' of this thread
+          float acc4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int t = 0; t < kL + 3; ++t) {
+            // window column of m = mp0 - kL/2 + t; it feeds output mp0 + o through
+            // tap index kk = k + kL/2 = t - o
+            const int cc = mp0 - pass_lo - kL / 2 + t;
+            if (cc < 0 || cc >= pw) continue;
+            float wv[16];
+#pragma unroll
+            for (int qr = 0; qr < kZQuadRows; ++qr) {
+              const float4 w4 = ws[qr * kBwWcap + cc];
+              wv[4 * qr] = w4.x; wv[4 * qr + 1] = w4.y; wv[4 * qr + 2] = w4.z; wv[4 * qr + 3] = w4.w;
+            }
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+              const int kk = t - o;  // k + kL/2
+              if (kk < 0 || kk >= kL) continue;
+#pragma unroll
+              for (int row = 0; row < kZRows; ++row)
+                acc4[o] = fmaf(a.farrow[row / kFarrowCoef][row % kFarrowCoef][kk], wv[row], acc4[o]);
+            }
+          }
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            const int mp = mp0 + o;
+            if (4 * o4 + o < n_outv && mp >= 0 && mp < S.n_in) dxrow[mp] += acc4[o];
+          }
+        }
+      }
+      // knot gradients of this tile: per-sample vectors, then fixed-order sums
+      kv_s[6 * threadIdx.x + 0] = v0x; kv_s[6 * threadIdx.x + 1] = v0y; kv_s[6 * threadIdx.x + 2] = v0z;
+      kv_s[6 * threadIdx.x + 3] = v1x; kv_s[6 * threadIdx.x + 4] = v1y; kv_s[6 * threadIdx.x + 5] = v1z;
+      __syncthreads();
+      float* slot = a.p.kslot + 3 * (S.kslot_first[g.t] + int64_t(mic) * S.kslot_mic_stride +
+                                     (int64_t(blk - S.block_first[g.t]) * S.n_tiles + tile) * S.kcap[g.t]);
+      for (int jj = threadIdx.x; jj < g.nk; jj += kBwThreads) {
+        const int jk = g.jf + jj;
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        // V0 of samples in interval jk, V1 of samples in interval jk - 1
+        const int a0 = max(jk * g.N, g.n0), a1 = min((jk + 1) * g.N - 1, g.n_end);
+        for (int nn2 = a0; nn2 <= a1; ++nn2) {
+          const float* v = kv_s + 6 * (nn2 - g.n0);
+          sx += v[0]; sy += v[1]; sz += v[2];
+        }
+        const int b0 = max((jk - 1) * g.N, g.n0), b1 = min(jk * g.N - 1, g.n_end);
+        for (int nn2 = b0; nn2 <= b1; ++nn2) {
+          const float* v = kv_s + 6 * (nn2 - g.n0);
+          sx += v[3]; sy += v[4]; sz += v[5];
+        }
+        slot[3 * jj] = sx; slot[3 * jj + 1] = sy; slot[3 * jj + 2] = sz;
+      }
+      __syncthreads();
+    }
+    // reflection-coefficient partials of the item (fixed-order block sum)
+#pragma unroll
+    for (int w = 0; w < 6; ++w) {
+      float v = bacc[w];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) s_beta[warp][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      float v = 0.f;
+      for (int w = 0; w < kBwThreads / 32; ++w) v += s_beta[w][threadIdx.x];
+      a.p.bpart[S.bpart_base + (int64_t(mic) * S.n_blocks + blk) * 8 + threadIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// dx[m] = sum over microphones and blocks of the dx rows (fixed order).
+__global__ void k_dx_final(const __grid_constant__ KernelArgs a) {
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= a.totals[2]) return;
+  int s = 0;
+  int64_t m = gid;
+  if (a.n_scenes > 1) {
+    s = find_scene(a.tab.dx_prefix, a.n_scenes, gid);
+    m = gid - a.tab.dx_prefix[s];
+  }
+  const SceneDev& S = scene_of(a, s);
+  if (!S.dx) return;
+  const float* p = a.p.dxb + S.dxb_base + m;
+  const int rows = S.n_mics * S.n_blocks;
+  float acc = 0.f;
+  for (int rr = 0; rr < rows; ++rr) acc += p[int64_t(rr) * S.n_in];
+  S.dx[m] = acc;
+}
+
+// dL/ds(t_j) per tier knot: sum over microphones, blocks of the tier and the
+// (at most two) tiles whose knot range holds j.
+__global__ void k_knot_final(const __grid_constant__ KernelArgs a) {
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= a.totals[1]) return;
+  int s = 0;
+  int64_t local = gid;
+  if (a.n_scenes > 1) {
+    s = find_scene(a.tab.knots_prefix, a.n_scenes, gid);
+    local = gid - a.tab.knots_prefix[s];
+  }
+  const SceneDev& S = scene_of(a, s);
+  int t = 0;
+  while (t + 1 < S.n_tiers && local >= S.knot_units_first[t + 1]) ++t;
+  const int j = int(local - S.knot_units_first[t]);
+  const int N = S.tier_step[t];
+  double gx = 0.0, gy = 0.0, gz = 0.0;
+  if (S.tier_count[t] > 0) {
+    const int kt = int((int64_t(j) * N) / S.tile);
+    for (int mic = 0; mic < S.n_mics; ++mic)
+      for (int b = 0; b < S.tier_blocks[t]; ++b)
+        for (int tile = max(kt - 1, 0); tile <= min(kt, S.n_tiles - 1); ++tile) {
+          const int n0 = tile * S.tile;
+          const int n_end = int(min(int64_t(n0 + S.tile), S.n_out)) - 1;
+          const int jf = n0 / N, nk = n_end / N - jf + 2;
+          if (j < jf || j >= jf + nk) continue;
+          const float* slot = a.p.kslot + 3 * (S.kslot_first[t] + int64_t(mic) * S.kslot_mic_stride +
+                                               (int64_t(b) * S.n_tiles + tile) * S.kcap[t] + (j - jf));
+          gx += slot[0];
+          gy += slot[1];
+          gz += slot[2];
+        }
+  }
+  double* out = a.p.gk + 3 * (S.knot_base[t] + j);
+  out[0] = gx;
+  out[1] = gy;
+  out[2] = gz;
+}
+
+// ds(t)/dparams[p] of the trajectory (3 components).
+__device__ void source_jacobian(const SceneDev& S, double t, int p, double J[3]) {
+  J[0] = J[1] = J[2] = 0.0;
+  const double* q = S.traj;
+  if (S.traj_kind == 0) {
+    const double nrm = sqrt(q[3] * q[3] + q[4] * q[4] + q[5] * q[5]);
+    const double u[3] = {q[3] / nrm, q[4] / nrm, q[5] / nrm};
+    if (p < 3) {
+      J[p] = 1.0;
+    } else if (p < 6) {
+      const int c = p - 3;
+      for (int d = 0; d < 3; ++d) J[d] = q[6] * t * ((d == c ? 1.0 : 0.0) - u[d] * u[c]) / nrm;
+    } else if (p == 6) {
+      for (int d = 0; d < 3; ++d) J[d] = t * u[d];
+    }
+  } else if (S.traj_kind == 1) {
+    const double R = q[3], v = q[4];
+    const double th = q[5] + v * t / R;
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    if (p < 3) J[p] = 1.0;
+    else if (p == 3) { J[0] = cs + sn * v * t / R; J[1] = sn - cs * v * t / R; }
+    else if (p == 4) { J[0] = -t * sn; J[1] = t * cs; }
+    else if (p == 5) { J[0] = -R * sn; J[1] = R * cs; }
+  } else {
+    const int c = p / 3, d = p - 3 * c;
+    if (c >= S.n_ctrl) return;
+    const int m = S.n_ctrl - 3;
+    double u = fmin(1.0, fmax(0.0, t / S.duration));
+    const int span = min(int(u * m), m - 1);
+    if (c < span || c > span + 3) return;
+    auto knot = [m](int i) { return fmin(1.0, fmax(0.0, double(i - 3) / double(m))); };
+    // the four non-zero cubic basis functions on the span (triangular scheme)
+    const int K = span + 3;
+    double Nb[4], left[4], right[4];
+    Nb[0] = 1.0;
+    for (int jdeg = 1; jdeg <= 3; ++jdeg) {
+      left[jdeg] = u - knot(K + 1 - jdeg);
+      right[jdeg] = knot(K + jdeg) - u;
+      double saved = 0.0;
+      for (int rr = 0; rr < jdeg; ++rr) {
+        const double den = right[rr + 1] + left[jdeg - rr];
+        const double tmp = den != 0.0 ? Nb[rr] / den : 0.0;
+        Nb[rr] = saved + right[rr + 1] * tmp;
+        saved = left[jdeg - rr] * tmp;
+      }
+      Nb[jdeg] = saved;
+    }
+    J[d] = Nb[c - span];
+  }
+}
+
+// dL/dparams[p] = sum over tiers and knots of J_p(t_j) . dL/ds(t_j)  (one CTA per (scene, p)).
+__global__ void k_param_final(const __grid_constant__ KernelArgs a) {
+  const int s = blockIdx.x / 48, p = blockIdx.x % 48;
+  const SceneDev& S = scene_of(a, s);
+  __shared__ double red[256];
+  double acc = 0.0;
+  const bool used = (S.traj_kind == 0 && p < 7) || (S.traj_kind == 1 && p < 6) ||
+                    (S.traj_kind == 2 && p < 3 * S.n_ctrl);
+  if (S.dparams && used) {
+    for (int t = 0; t < S.n_tiers; ++t) {
+      if (S.tier_count[t] == 0) continue;
+      const int J = S.tier_intervals[t];
+      for (int j = threadIdx.x; j <= J; j += blockDim.x) {
+        double Jp[3];
+        source_jacobian(S, double(int64_t(j) * S.tier_step[t]) / S.fs, p, Jp);
+        const double* gk = a.p.gk + 3 * (S.knot_base[t] + j);
+        acc += Jp[0] * gk[0] + Jp[1] * gk[1] + Jp[2] * gk[2];
+      }
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && S.dparams) S.dparams[p] = red[0];
+}
+
+// dL/dbeta_w: sum of the item partials in item order (one CTA per scene).
+__global__ void k_beta_final(const __grid_constant__ KernelArgs a) {
+  const SceneDev& S = scene_of(a, blockIdx.x);
+  if (!S.dbeta || threadIdx.x >= 6) return;
+  double acc = 0.0;
+  const int rows = S.n_mics * S.n_blocks;
+  for (int rr = 0; rr < rows; ++rr) acc += a.p.bpart[S.bpart_base + int64_t(rr) * 8 + threadIdx.x];
+  S.dbeta[threadIdx.x] = acc;
+}
+
+}  // namespace
+
+static const TileConfig kBwConfig = {kBwThreads, 1, kBwWcap, kBwRecCap, kBwBlock};
+const TileConfig& backward_tile_config() { return kBwConfig; }
+size_t backward_unit_cap() { return kBwUnitCap; }
+
+cudaError_t launch_prefilter(const KernelArgs& a, cudaStream_t st);
+
+template <int kL>
+static cudaError_t run_adjoint(const KernelArgs& a, cudaStream_t st) {
+  static int grid = 0;
+  if (grid == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_adjoint<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBwSmem));
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint<kL>, kBwThreads, kBwSmem);
+    if (e != cudaSuccess) return e;
+    grid = sms * (occ > 0 ? occ : 1);
+  }
+  const int64_t items = a.totals[4];
+  const int g = int(items < grid ? items : grid);
+  cudaError_t e = cudaMemsetAsync(a.p.counter, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  if (g > 0) k_adjoint<kL><<<g, kBwThreads, kBwSmem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
+  cudaError_t e = launch_prefilter(a, st);
+  if (e != cudaSuccess) return e;
+  if (a.taps <= 16) e = run_adjoint<16>(a, st);
+  else if (a.taps <= 32) e = run_adjoint<32>(a, st);
+  else e = run_adjoint<64>(a, st);
+  if (e != cudaSuccess) return e;
+  const int T = 256;
+  if (a.totals[2] > 0) k_dx_final<<<unsigned((a.totals[2] + T - 1) / T), T, 0, st>>>(a);
+  if (a.totals[1] > 0) k_knot_final<<<unsigned((a.totals[1] + T - 1) / T), T, 0, st>>>(a);
+  k_param_final<<<unsigned(a.n_scenes * 48), 256, 0, st>>>(a);
+  k_beta_final<<<unsigned(a.n_scenes), 32, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace msrc

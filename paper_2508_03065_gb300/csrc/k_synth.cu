@@ -291,14 +291,20 @@ static const TileConfig kConfigs[] = {
 int tile_config_count() { return int(sizeof(kConfigs) / sizeof(kConfigs[0])); }
 const TileConfig& tile_config(int cfg) { return kConfigs[cfg]; }
 
-cudaError_t launch_forward(const KernelArgs& a, int cfg, cudaStream_t st, cudaEvent_t* ev) {
-  const int T = 256;
+cudaError_t launch_prefilter(const KernelArgs& a, cudaStream_t st) {
   if (a.totals[3] > 0) {
     const unsigned g = unsigned(a.totals[3]);
     if (a.taps <= 16) k_prefilter<16><<<g, kPreThreads, 0, st>>>(a);
     else if (a.taps <= 32) k_prefilter<32><<<g, kPreThreads, 0, st>>>(a);
     else k_prefilter<64><<<g, kPreThreads, 0, st>>>(a);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward(const KernelArgs& a, int cfg, cudaStream_t st, cudaEvent_t* ev) {
+  const int T = 256;
+  cudaError_t pe = launch_prefilter(a, st);
+  if (pe != cudaSuccess) return pe;
   if (ev) cudaEventRecord(ev[0], st);
   cudaError_t e = cudaSuccess;
   switch (cfg) {

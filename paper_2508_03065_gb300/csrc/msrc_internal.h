@@ -63,6 +63,16 @@ struct SceneDev {
   int64_t z_m0;                            // sample index of z column 0
   const float* x;
   float* y;
+  // reverse mode (msrc_synthesize_backward)
+  const float* dy;                         // [n_mics][n_out]
+  float* dx;                               // [n_in] or null
+  double* dparams;                         // [48] or null
+  double* dbeta;                           // [6] or null
+  int64_t dxb_base;                        // first float of the per-(mic, block) dx rows
+  int64_t kslot_first[MSRC_MAX_TIERS];     // first knot-gradient slot of tier t (mic 0)
+  int64_t kslot_mic_stride;                // slots per microphone
+  int32_t kcap[MSRC_MAX_TIERS];            // knot slots per (block, tile) item of tier t
+  int64_t bpart_base;                      // first float of the per-(mic, block) beta partials
   float c_over_fs;                         // metres per sample of delay
   float pad_;
 };
@@ -82,7 +92,7 @@ const TileConfig& tile_config(int cfg);
 struct LaunchTables {
   const int64_t* enum_prefix;    // images
   const int64_t* knots_prefix;   // trajectory knots
-  const int64_t* unused_prefix;  // (reserved)
+  const int64_t* dx_prefix;      // input samples (reverse mode)
   const int64_t* z_prefix;       // prefilter units
   const int64_t* item_prefix;    // synthesis items
   const int64_t* red_prefix;     // reduction units
@@ -102,6 +112,11 @@ struct DevicePtrs {
   double* knot_pos;              // s(t_j), 3 doubles per knot
   float4* z;                     // prefiltered rows (kZQuadRows quad rows per scene)
   float* part;                   // partial sums
+  // reverse mode
+  float* dxb;                    // dx rows per (scene, mic, block)
+  float* kslot;                  // knot-gradient slots (3 floats each)
+  float* bpart;                  // beta partials (8 floats per (scene, mic, block))
+  double* gk;                    // dL/ds(t_j) per tier knot (3 doubles, indexed like knot_pos)
 };
 
 struct KernelArgs {
@@ -131,6 +146,8 @@ __host__ __device__ inline void unpack_image(uint32_t code, int n[3], int p[3]) 
 
 // Launch entry points (defined in the .cu files).
 cudaError_t launch_setup(const KernelArgs& a, cudaStream_t s);
+// Reverse-mode tile configuration (threads = tile samples, one per thread).
+const TileConfig& backward_tile_config();
 cudaError_t launch_forward(const KernelArgs& a, int tile_config, cudaStream_t s,
                            cudaEvent_t* ev /* nullable: [after prefilter, after synthesis] */);
 size_t sort_temp_bytes(int64_t n_items, int end_bit);
