@@ -56,6 +56,8 @@ def parse():
                     help="shorten the scene (profiling captures); the benchmark default is 4 s")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tile-config", type=int, default=None, help="synthesis tile configuration id")
+    ap.add_argument("--batched-scenes", type=int, default=256,
+                    help="scenes of the batched comparison (0 disables it)")
     return ap.parse_args()
 
 
@@ -281,6 +283,8 @@ def run_gpu(args):
         "gpu_launches": args.steps * launches_per_step(),
         "clocks": clk,
     }
+    if world == 1 and args.batched_scenes > 0 and args.seconds is None:
+        line["batched"] = run_batched(args, torch, api, W)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, args.cpu_sample)
     if rank == 0:
@@ -288,6 +292,49 @@ def run_gpu(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_batched(args, torch, api, W):
+    """256 scenes with uneven durations (1-8 s at 16 kHz), rooms and orders
+    (6-12): one batched call (graph replay of the persistent launch) against
+    the same scenes synthesised one call at a time by the same library."""
+    specs = [W.config3_scene(s) for s in range(args.batched_scenes)]
+    rooms = [api.Room.from_spec(sp) for sp in specs]
+    xs = [torch.from_numpy(sp.x).cuda() for sp in specs]
+    stream = torch.cuda.Stream()
+    batch = api.Batch(rooms, xs, stream=stream)
+    work = batch.work()
+    for _ in range(2):
+        batch.run(True)
+    stream.synchronize()
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        batch.run(True)
+    e1.record(stream)
+    stream.synchronize()
+    t_batched = e0.elapsed_time(e1) / reps
+    del batch
+    torch.cuda.empty_cache()
+    ws = api.Workspace("cuda")
+    ys = [torch.empty((r.n_mics, sp.n_in), device="cuda") for r, sp in zip(rooms, specs)]
+    with torch.cuda.stream(stream):
+        for r, x, y in zip(rooms, xs, ys):
+            api.synthesize([r], [x], out=[y], workspace=ws, stream=stream)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            for r, x, y in zip(rooms, xs, ys):
+                api.synthesize([r], [x], out=[y], workspace=ws, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+    t_single = e0.elapsed_time(e1) / reps
+    return {"scenes": len(specs), "image_samples": work, "batched_ms": t_batched, "single_loop_ms": t_single,
+            "batched_value": work / (t_batched * 1e-3), "single_value": work / (t_single * 1e-3),
+            "speedup": t_single / t_batched, "unit": UNIT,
+            "how": "one persistent synthesis launch over all scenes, CUDA-graph replay, vs one msrc_synthesize "
+                   "call per scene on the same stream (same kernels and tile configuration)"}
 
 
 def launches_per_step():

@@ -160,6 +160,38 @@ msrc_status msrc_synthesize_backward(const msrc_room_t* rooms, int32_t n_rooms,
                                      double* const* dbeta_dev,
                                      void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* Batched synthesis with a reusable plan. msrc_batch_create plans the call
+ * (scene descriptors, work queue of (scene, microphone, image block, output
+ * tile) items, workspace layout) and uploads the descriptors into the
+ * workspace once, synchronising `stream`; the rooms' current trajectories,
+ * walls and the signal / output pointers are bound at this point (re-create
+ * the batch after changing them). msrc_batch_run enqueues only kernels on
+ * `stream` (image enumeration and sort, knots, prefilter, one persistent
+ * synthesis launch over all scenes, reduction); with use_graph != 0 the
+ * first run captures them into a CUDA graph (the stream must not be the
+ * legacy default stream) and later runs replay it. Arguments as for
+ * msrc_synthesize; the workspace must stay allocated until the batch is
+ * destroyed. The selected tile configuration is frozen at creation. */
+typedef struct msrc_batch* msrc_batch_t;
+msrc_status msrc_batch_create(const msrc_room_t* rooms, int32_t n_rooms,
+                              const float* const* x_dev, const int64_t* n_in,
+                              float* const* y_dev, const int64_t* n_out,
+                              void* workspace_dev, size_t workspace_bytes, void* stream,
+                              msrc_batch_t* out);
+msrc_status msrc_batch_run(msrc_batch_t batch, int32_t use_graph, void* stream);
+msrc_status msrc_batch_destroy(msrc_batch_t batch);
+
+/* Autotuner of the synthesis launch: runs the given call (arguments as for
+ * msrc_synthesize) once per tile configuration whose workspace fits, `reps`
+ * times each after one warm-up, timed with CUDA events on `stream`; writes the
+ * mean milliseconds per configuration into ms_per_config (msrc_tile_configs()
+ * entries, -1 when skipped), selects the fastest for later calls and returns
+ * its id in *best. Synchronises `stream`. */
+msrc_status msrc_autotune(const msrc_room_t* rooms, int32_t n_rooms, const float* const* x_dev,
+                          const int64_t* n_in, float* const* y_dev, const int64_t* n_out,
+                          void* workspace_dev, size_t workspace_bytes, void* stream, int32_t reps,
+                          double* ms_per_config, int32_t* best);
+
 /* Reads (and clears) the device-side error word of a workspace used by the
  * calls above; synchronises `stream`. *flags receives a bit set:
  * 1 = a bounded wait gave up, 2 = a shared-memory window had to be clamped. */

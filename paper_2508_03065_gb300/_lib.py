@@ -79,6 +79,13 @@ SIGNATURES = [
     ("msrc_profile_enable", _I32, [_I32]),
     ("msrc_profile_read", _I32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     ("msrc_synthesize_noalloc", _I32, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P]),
+    ("msrc_batch_create", _I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P), _I64P, ctypes.POINTER(_P),
+                                 _I64P, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    ("msrc_batch_run", _I32, [_P, _I32, _P]),
+    ("msrc_batch_destroy", _I32, [_P]),
+    ("msrc_autotune", _I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P), _I64P, ctypes.POINTER(_P), _I64P,
+                             _P, ctypes.c_size_t, _P, _I32, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(_I32)]),
     ("msrc_status_string", ctypes.c_char_p, [_I32]),
     ("msrc_last_error", ctypes.c_char_p, []),
 ]

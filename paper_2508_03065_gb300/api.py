@@ -282,3 +282,97 @@ class MovingSourceSynthesis(torch.autograd.Function):
 def synthesize_ad(room: Room, x: torch.Tensor, params: torch.Tensor, beta: torch.Tensor) -> torch.Tensor:
     """Differentiable forward synthesis of one room (see MovingSourceSynthesis)."""
     return MovingSourceSynthesis.apply(x, params, beta, room)
+
+
+class Batch:
+    """A planned batched synthesis (msrc_batch_*): descriptors uploaded once,
+    kernels only per run, optionally replayed from a captured CUDA graph.
+    Signals and outputs are bound at creation."""
+
+    def __init__(self, rooms: Sequence[Room], xs: Sequence[torch.Tensor], n_out: Optional[Sequence[int]] = None,
+                 stream: Optional[torch.cuda.Stream] = None):
+        lib = _lib.load()
+        self.rooms = list(rooms)
+        self.xs = [x.contiguous() for x in xs]
+        self.n_in = [int(x.numel()) for x in self.xs]
+        self.n_out = list(self.n_in) if n_out is None else [int(v) for v in n_out]
+        dev = self.xs[0].device
+        self.ys = [torch.empty((r.n_mics, no), dtype=torch.float32, device=dev)
+                   for r, no in zip(self.rooms, self.n_out)]
+        fwd, _ = workspace_size(self.rooms, self.n_in, self.n_out)
+        self.ws = torch.empty(fwd, dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        self.stream.wait_stream(torch.cuda.current_stream(dev))
+        h = ctypes.c_void_p()
+        hs = _lib.ptr_array([r.handle.value for r in self.rooms])
+        _lib.check(lib.msrc_batch_create(hs, len(self.rooms), _lib.ptr_array([x.data_ptr() for x in self.xs]),
+                                         _lib.i64_array(self.n_in), _lib.ptr_array([y.data_ptr() for y in self.ys]),
+                                         _lib.i64_array(self.n_out), ctypes.c_void_p(self.ws.data_ptr()),
+                                         self.ws.numel(), _stream_handle(self.stream), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, use_graph: bool = True) -> List[torch.Tensor]:
+        _lib.check(_lib.load().msrc_batch_run(self._h, 1 if use_graph else 0, _stream_handle(self.stream)))
+        return self.ys
+
+    def work(self) -> int:
+        """Image-samples per run (images x output samples x microphones)."""
+        return sum(r.image_count()[0] * no * r.n_mics for r, no in zip(self.rooms, self.n_out))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib._lib is not None:
+            _lib._lib.msrc_batch_destroy(h)
+            self._h = None
+
+
+def autotune(rooms: Sequence[Room], xs: Sequence[torch.Tensor], n_out: Optional[Sequence[int]] = None,
+             reps: int = 3, cache_path: Optional[str] = None, stream: Optional[torch.cuda.Stream] = None) -> int:
+    """Selects the fastest synthesis tile configuration for this workload and
+    caches the choice in a JSON file (MSRC_AUTOTUNE_CACHE, else
+    ~/.cache/msrc_autotune.json) keyed by GPU and workload shape."""
+    import json
+    import os
+
+    lib = _lib.load()
+    xs = [x.contiguous() for x in xs]
+    n_in = [int(x.numel()) for x in xs]
+    n_out = list(n_in) if n_out is None else [int(v) for v in n_out]
+    dev = xs[0].device
+    key = json.dumps([torch.cuda.get_device_name(dev), len(rooms),
+                      sum(r.image_count()[0] for r in rooms), sum(n_out), sum(n_in),
+                      sorted({int(r._desc.taps) for r in rooms})])
+    path = cache_path or os.environ.get("MSRC_AUTOTUNE_CACHE") or os.path.expanduser("~/.cache/msrc_autotune.json")
+    cache = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if key in cache:
+        set_tile_config(int(cache[key]["best"]))
+        return int(cache[key]["best"])
+    ys = [torch.empty((r.n_mics, no), dtype=torch.float32, device=dev) for r, no in zip(rooms, n_out)]
+    need = 0
+    saved = None
+    for c in range(tile_configs()):
+        set_tile_config(c)
+        need = max(need, workspace_size(rooms, n_in, n_out)[0])
+    ws = _workspace(dev).get(need)
+    ms = (ctypes.c_double * tile_configs())()
+    best = ctypes.c_int32()
+    hs = _lib.ptr_array([r.handle.value for r in rooms])
+    _lib.check(lib.msrc_autotune(hs, len(rooms), _lib.ptr_array([x.data_ptr() for x in xs]), _lib.i64_array(n_in),
+                                 _lib.ptr_array([y.data_ptr() for y in ys]), _lib.i64_array(n_out),
+                                 ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream), int(reps), ms,
+                                 ctypes.byref(best)))
+    cache[key] = {"best": int(best.value), "ms": [float(v) for v in ms]}
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1)
+    except OSError:
+        pass
+    del saved
+    return int(best.value)

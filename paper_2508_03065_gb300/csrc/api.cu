@@ -739,6 +739,137 @@ msrc_status msrc_synthesize_backward(const msrc_room_t* rooms, int32_t n_rooms, 
   return MSRC_OK;
 }
 
+}  // extern "C"
+
+struct msrc_batch {
+  Plan P;
+  KernelArgs* a = nullptr;
+  int cfg = 0;
+  char* ws = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+cudaError_t enqueue_forward(const KernelArgs& a, char* ws, int cfg, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(ws, 0, 256, st);
+  if (e == cudaSuccess) e = launch_setup(a, st);
+  if (e == cudaSuccess) e = launch_forward(a, cfg, st, nullptr);
+  return e;
+}
+}  // namespace
+
+extern "C" {
+
+msrc_status msrc_batch_create(const msrc_room_t* rooms, int32_t n, const float* const* x_dev,
+                              const int64_t* n_in, float* const* y_dev, const int64_t* n_out, void* ws,
+                              size_t ws_bytes, void* stream, msrc_batch_t* out) {
+  if (!out || !x_dev || !y_dev) return fail(MSRC_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  msrc_batch* b = new (std::nothrow) msrc_batch;
+  if (!b) return fail(MSRC_ERR_INVALID_ARG, "out of host memory");
+  msrc_status s = make_plan(rooms, n, n_in, n_out, b->P);
+  if (s == MSRC_OK) s = check_ws(b->P, ws, ws_bytes);
+  if (s != MSRC_OK) { delete b; return s; }
+  for (int r = 0; r < n; ++r) {
+    if (!x_dev[r] || !y_dev[r]) { delete b; return fail(MSRC_ERR_INVALID_ARG, "room %d: null x or y", r); }
+    b->P.scenes[r].x = x_dev[r];
+    b->P.scenes[r].y = y_dev[r];
+  }
+  b->a = new (std::nothrow) KernelArgs;
+  if (!b->a) { delete b; return fail(MSRC_ERR_INVALID_ARG, "out of host memory"); }
+  b->ws = static_cast<char*>(ws);
+  b->cfg = g_tile_config;
+  fill_args(b->P, rooms, b->ws, *b->a);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<char> blob;
+  s = upload_tables(b->P, b->ws, st, blob);
+  if (s == MSRC_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_fail(e, "descriptor upload");
+  }
+  if (s != MSRC_OK) { delete b->a; delete b; return s; }
+  *out = b;
+  return MSRC_OK;
+}
+
+msrc_status msrc_batch_run(msrc_batch_t b, int32_t use_graph, void* stream) {
+  if (!b) return fail(MSRC_ERR_INVALID_ARG, "null batch");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!use_graph) {
+    cudaError_t e = enqueue_forward(*b->a, b->ws, b->cfg, st);
+    return e == cudaSuccess ? MSRC_OK : cuda_fail(e, "batch launch");
+  }
+  if (!b->exec) {
+    if (st == nullptr) return fail(MSRC_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+    // warm-up outside the capture: first launches set kernel attributes
+    cudaError_t e = enqueue_forward(*b->a, b->ws, b->cfg, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture begin");
+    cudaError_t le = enqueue_forward(*b->a, b->ws, b->cfg, st);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(st, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(le != cudaSuccess ? le : e, "graph capture");
+    }
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); b->exec = nullptr; return cuda_fail(e, "graph instantiate"); }
+    b->graph = g;
+  }
+  cudaError_t e = cudaGraphLaunch(b->exec, st);
+  return e == cudaSuccess ? MSRC_OK : cuda_fail(e, "graph launch");
+}
+
+msrc_status msrc_batch_destroy(msrc_batch_t b) {
+  if (!b) return MSRC_OK;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  delete b->a;
+  delete b;
+  return MSRC_OK;
+}
+
+msrc_status msrc_autotune(const msrc_room_t* rooms, int32_t n, const float* const* x_dev, const int64_t* n_in,
+                          float* const* y_dev, const int64_t* n_out, void* ws, size_t ws_bytes, void* stream,
+                          int32_t reps, double* ms, int32_t* best) {
+  if (!ms || !best || reps < 1) return fail(MSRC_ERR_INVALID_ARG, "null output or reps < 1");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int saved = g_tile_config;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(MSRC_ERR_CUDA, "event creation");
+  int pick = -1;
+  double best_ms = 0.0;
+  msrc_status result = MSRC_OK;
+  for (int c = 0; c < tile_config_count(); ++c) {
+    ms[c] = -1.0;
+    g_tile_config = c;
+    Plan P;
+    if (make_plan(rooms, n, n_in, n_out, P) != MSRC_OK || P.fwd_bytes > ws_bytes) continue;
+    msrc_status s = msrc_synthesize(rooms, n, x_dev, n_in, y_dev, n_out, ws, ws_bytes, stream);
+    if (s != MSRC_OK) { result = s; break; }
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && s == MSRC_OK; ++r)
+      s = msrc_synthesize(rooms, n, x_dev, n_in, y_dev, n_out, ws, ws_bytes, stream);
+    cudaEventRecord(e1, st);
+    if (s != MSRC_OK) { result = s; break; }
+    if (cudaEventSynchronize(e1) != cudaSuccess) { result = fail(MSRC_ERR_CUDA, "event synchronize"); break; }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    ms[c] = double(t) / reps;
+    if (pick < 0 || ms[c] < best_ms) { pick = c; best_ms = ms[c]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g_tile_config = pick >= 0 ? pick : saved;
+  *best = g_tile_config;
+  if (result != MSRC_OK) return result;
+  if (pick < 0) return fail(MSRC_ERR_WORKSPACE, "no tile configuration fits the workspace");
+  return MSRC_OK;
+}
+
 msrc_status msrc_workspace_errors(void* ws, void* stream, uint32_t* flags) {
   if (!ws || !flags) return fail(MSRC_ERR_INVALID_ARG, "null argument");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
