@@ -39,6 +39,10 @@ Z_BYTES_PER_IMAGE_SAMPLE = 8 * 4
 # delay interpolation 1 FMA (2), fraction and segment split 5, delay 1 ADD,
 # gain 1 division (1) -> 25.
 FLOPS_PER_IMAGE_SAMPLE = 25
+# DRAM bytes (read + write) of one synthesis launch on this workload, from the
+# ncu capture of the 1 s version of the scene (26.0 MB) scaled by the
+# image-samples processed (x4); None whenever the kernel changed since.
+K_SYNTH_TRAFFIC_BYTES = 1.04e8
 SM_COUNT = 152
 SMEM_BYTES_PER_CLK_PER_SM = 128
 FP32_LANES_PER_SM = 128
@@ -58,6 +62,10 @@ def parse():
     ap.add_argument("--tile-config", type=int, default=None, help="synthesis tile configuration id")
     ap.add_argument("--batched-scenes", type=int, default=256,
                     help="scenes of the batched comparison (0 disables it)")
+    ap.add_argument("--sections", default="batched,backward",
+                    help="extra measurements in the JSON line: batched, backward, array")
+    ap.add_argument("--only", default=None, choices=["backward", "array", "batched"],
+                    help="run one extra section alone (profiling captures) and print it")
     return ap.parse_args()
 
 
@@ -274,7 +282,8 @@ def run_gpu(args):
         "phases_ms": {"setup": phase_ms[0] / max(n_calls, 1), "prefilter": phase_ms[1] / max(n_calls, 1),
                       "synthesis": synth_ms, "reduction": phase_ms[3] / max(n_calls, 1)},
         "roofline": {"bound": "smem", "kernel": "k_synth", "achieved": achieved, "peak": smem_peak,
-                     "unit": "GB/s", "frac": achieved / smem_peak, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / smem_peak,
+                     "traffic": K_SYNTH_TRAFFIC_BYTES if args.seconds is None else None,
                      "peak_source": f"{SM_COUNT} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x median SM clock "
                                     f"{sm_mhz:.0f} MHz under load",
                      "fp32_tflops": fp32, "fp32_peak_tflops": fp32_peak, "fp32_frac": fp32 / fp32_peak},
@@ -283,8 +292,14 @@ def run_gpu(args):
         "gpu_launches": args.steps * launches_per_step(),
         "clocks": clk,
     }
-    if world == 1 and args.batched_scenes > 0 and args.seconds is None:
-        line["batched"] = run_batched(args, torch, api, W)
+    sections = set(filter(None, args.sections.split(",")))
+    if world == 1 and args.seconds is None:
+        if "batched" in sections and args.batched_scenes > 0:
+            line["batched"] = run_batched(args, torch, api, W)
+        if "backward" in sections:
+            line["backward"] = run_backward(args, torch, api, W)
+        if "array" in sections:
+            line["array"] = run_array(args, torch, api, W)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, args.cpu_sample)
     if rank == 0:
@@ -337,17 +352,93 @@ def run_batched(args, torch, api, W):
                    "call per scene on the same stream (same kernels and tile configuration)"}
 
 
+def run_backward(args, torch, api, W, n_scenes=16):
+    """The 16 differentiation scenes (6x5x3 m, order 8, 2 s at 16 kHz): one
+    batched forward and one batched backward (dx, trajectory and wall
+    gradients of 0.5 ||y - y*||^2)."""
+    pairs = [W.config4_scene(s) for s in range(n_scenes)]
+    rooms = [api.Room.from_spec(sp) for sp, _ in pairs]
+    xs = [torch.from_numpy(sp.x).cuda() for sp, _ in pairs]
+    tg = [torch.from_numpy(t).cuda() for _, t in pairs]
+    ws = api.Workspace("cuda")
+    work = sum(r.image_count()[0] * sp.n_in * r.n_mics for r, (sp, _) in zip(rooms, pairs))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ys = api.synthesize(rooms, xs, workspace=ws)
+        dys = [y - t[None] for y, t in zip(ys, tg)]
+        return api.synthesize_backward(rooms, xs, dys, workspace=ws)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    reps = 3
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    t_f = t_b = 0.0
+    for _ in range(reps):
+        e0.record(stream)
+        ys = api.synthesize(rooms, xs, workspace=ws)
+        dys = [y - t[None] for y, t in zip(ys, tg)]
+        e1.record(stream)
+        api.synthesize_backward(rooms, xs, dys, workspace=ws)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        t_f += e0.elapsed_time(e1) / reps
+        t_b += e1.elapsed_time(e2) / reps
+    return {"scenes": n_scenes, "image_samples": work, "forward_ms": t_f, "backward_ms": t_b,
+            "forward_value": work / (t_f * 1e-3), "backward_value": work / (t_b * 1e-3), "unit": UNIT,
+            "grads": "dx (32000), 18 spline control-point coordinates, 6 wall coefficients per scene"}
+
+
+def run_array(args, torch, api, W):
+    """The array scene: 8-mic circular array, order 25 (177 208 images), 10 s at
+    48 kHz, 64 taps; forward and backward."""
+    spec = W.config5()
+    room = api.Room.from_spec(spec)
+    x = torch.from_numpy(spec.x).cuda()
+    ws = api.Workspace("cuda")
+    work = room.image_count()[0] * spec.n_in * room.n_mics
+    stream = torch.cuda.current_stream()
+    y = api.synthesize([room], [x], workspace=ws)[0]
+    dy = torch.randn_like(y) * 1e-2
+    api.synthesize_backward([room], [x], [dy], workspace=ws)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    api.synthesize([room], [x], out=[y], workspace=ws)
+    e1.record(stream)
+    api.synthesize_backward([room], [x], [dy], workspace=ws)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    t_f, t_b = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    return {"workload": spec.name, "image_samples": work, "forward_ms": t_f, "backward_ms": t_b,
+            "forward_value": work / (t_f * 1e-3), "backward_value": work / (t_b * 1e-3), "unit": UNIT}
+
+
 def launches_per_step():
-    # enumerate, image table, trajectory knots, delay records, prefilter,
-    # synthesis, reduction + the radix sort's kernels (histogram, exclusive sum,
-    # 5 onesweep passes for a 34-bit key)
-    return 7 + 7
+    # enumerate, image table, trajectory knots, prefilter, synthesis, reduction
+    # + the radix sort's kernels (histogram, exclusive sum, 5 onesweep passes
+    # for a 34-bit key); counted from the ncu launch list of this command
+    return 6 + 7
+
+
+def run_only(args):
+    import torch
+
+    from paper_2508_03065_gb300 import api
+    from paper_2508_03065_gb300 import workloads as W
+
+    fn = {"backward": run_backward, "array": run_array, "batched": run_batched}[args.only]
+    print(json.dumps({args.only: fn(args, torch, api, W)}), flush=True)
+    return 0
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run_gpu(args)
 
 
