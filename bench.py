@@ -42,7 +42,7 @@ FLOPS_PER_IMAGE_SAMPLE = 25
 # DRAM bytes (read + write) of one synthesis launch on this workload, from the
 # ncu capture of the 1 s version of the scene (26.0 MB) scaled by the
 # image-samples processed (x4); None whenever the kernel changed since.
-K_SYNTH_TRAFFIC_BYTES = 1.04e8
+K_SYNTH_TRAFFIC_BYTES = None
 SM_COUNT = 152
 SMEM_BYTES_PER_CLK_PER_SM = 128
 FP32_LANES_PER_SM = 128

@@ -37,9 +37,11 @@ constexpr int kBwRecCap = 1024;   // records (image x interval)
 constexpr int kBwUnitCap = 1152;  // unit vectors (image x knot)
 constexpr int kBwBlock = 128;     // images per block at most
 
+constexpr int kBwSegCap = 33;     // knot intervals touched by one warp's 32 samples
 constexpr size_t kBwSmem = size_t(2 * kZQuadRows * kBwWcap) * sizeof(float4) +
                            size_t(kBwRecCap) * sizeof(int4) + size_t(kBwUnitCap) * sizeof(float4) +
-                           size_t(2 * kBwBlock) * sizeof(float4) + size_t(6 * kBwTile) * sizeof(float);
+                           size_t(2 * kBwBlock) * sizeof(float4) +
+                           size_t(6 * kBwSegCap * (kBwThreads / 32)) * sizeof(float);
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adjoint(const __grid_constant
   int4* rec_s = reinterpret_cast<int4*>(ws + kZQuadRows * kBwWcap);
   float4* unit_s = reinterpret_cast<float4*>(rec_s + kBwRecCap);
   float4* bw_s = unit_s + kBwUnitCap;                     // 2 per image
-  float* kv_s = reinterpret_cast<float*>(bw_s + 2 * kBwBlock);  // 6 per sample
+  float* seg_s = reinterpret_cast<float*>(bw_s + 2 * kBwBlock);  // [warp][interval][6]
   // prologue scratch aliases the w window
   float4* u_s = ws;
   float4* anc_s = ws + kBwTile + 4;
@@ -263,25 +265,45 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adjoint(const __grid_constant
           }
         }
       }
-      // knot gradients of this tile: per-sample vectors, then fixed-order sums
-      kv_s[6 * threadIdx.x + 0] = v0x; kv_s[6 * threadIdx.x + 1] = v0y; kv_s[6 * threadIdx.x + 2] = v0z;
-      kv_s[6 * threadIdx.x + 3] = v1x; kv_s[6 * threadIdx.x + 4] = v1y; kv_s[6 * threadIdx.x + 5] = v1z;
+      // knot gradients of this tile: a warp-segmented inclusive scan over the
+      // lanes' intervals (non-decreasing along the lanes), the segment tails
+      // stored per (warp, interval), then per knot a sum over warps in order
+      {
+        float vals[6] = {v0x, v0y, v0z, v1x, v1y, v1z};
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int kd = __shfl_up_sync(0xffffffffu, jc, d);
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            const float t = __shfl_up_sync(0xffffffffu, vals[c], d);
+            if (lane >= d && kd == jc) vals[c] += t;
+          }
+        }
+        const int jn = __shfl_down_sync(0xffffffffu, jc, 1);
+        const int jw = __shfl_sync(0xffffffffu, jc, 0);
+        if (lane == 31 || jn != jc) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) seg_s[(warp * kBwSegCap + (jc - jw)) * 6 + c] = vals[c];
+        }
+      }
       __syncthreads();
       float* slot = a.p.kslot + 3 * (S.kslot_first[g.t] + int64_t(mic) * S.kslot_mic_stride +
                                      (int64_t(blk - S.block_first[g.t]) * S.n_tiles + tile) * S.kcap[g.t]);
       for (int jj = threadIdx.x; jj < g.nk; jj += kBwThreads) {
-        const int jk = g.jf + jj;
         float sx = 0.f, sy = 0.f, sz = 0.f;
-        // V0 of samples in interval jk, V1 of samples in interval jk - 1
-        const int a0 = max(jk * g.N, g.n0), a1 = min((jk + 1) * g.N - 1, g.n_end);
-        for (int nn2 = a0; nn2 <= a1; ++nn2) {
-          const float* v = kv_s + 6 * (nn2 - g.n0);
-          sx += v[0]; sy += v[1]; sz += v[2];
-        }
-        const int b0 = max((jk - 1) * g.N, g.n0), b1 = min(jk * g.N - 1, g.n_end);
-        for (int nn2 = b0; nn2 <= b1; ++nn2) {
-          const float* v = kv_s + 6 * (nn2 - g.n0);
-          sx += v[3]; sy += v[4]; sz += v[5];
+        for (int w = 0; w < kBwThreads / 32; ++w) {
+          const int na = g.n0 + 32 * w;
+          if (na > g.n_end) break;
+          const int first = na / g.N - g.jf;
+          const int last = min(na + 31, g.n_end) / g.N - g.jf;
+          if (jj >= first && jj <= last) {  // V0 of interval jj
+            const float* v = seg_s + (w * kBwSegCap + (jj - first)) * 6;
+            sx += v[0]; sy += v[1]; sz += v[2];
+          }
+          if (jj - 1 >= first && jj - 1 <= last) {  // V1 of interval jj - 1
+            const float* v = seg_s + (w * kBwSegCap + (jj - 1 - first)) * 6;
+            sx += v[3]; sy += v[4]; sz += v[5];
+          }
         }
         slot[3 * jj] = sx; slot[3 * jj + 1] = sy; slot[3 * jj + 2] = sz;
       }

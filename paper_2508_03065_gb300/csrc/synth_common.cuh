@@ -51,6 +51,14 @@ __device__ __forceinline__ ItemGeom item_geometry(const SceneDev& S, int64_t li,
   return g;
 }
 
+// sqrt(q) for q > 0 in FP64 from an FP32 reciprocal-square-root seed and one
+// Newton step: the seed has relative error ~1e-7, the step squares it (~1e-14).
+__device__ __forceinline__ double fast_sqrt(double q) {
+  const float r = rsqrtf(float(q));
+  const double d0 = double(float(q) * r);
+  return fma(fma(-d0, d0, q), 0.5 * double(r), d0);
+}
+
 // Knot j of an image relative to its anchor knot a: with Delta the FP64
 // image-to-microphone vector at the anchor, w = sigma o Delta_a (FP32),
 // u = s(t_j) - s(t_a) and q = |Delta_j|^2 - |Delta_a|^2 = 2 w.u + |u|^2 exactly,
@@ -93,7 +101,7 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     const double D0 = s0 * sa0 + 2.0 * n[0] * S.dims[0] - mic[0];
     const double D1 = s1 * sa1 + 2.0 * n[1] * S.dims[1] - mic[1];
     const double D2 = s2 * sa2 + 2.0 * n[2] * S.dims[2] - mic[2];
-    const double da = sqrt(D0 * D0 + D1 * D1 + D2 * D2);
+    const double da = fast_sqrt(fma(D0, D0, fma(D1, D1, D2 * D2)));
     const double tau = da * fs_c;
     const double Dfl = floor(tau);
     anc_s[2 * ib] = make_float4(float(s0 * D0), float(s1 * D1), float(s2 * D2), float(da));
