@@ -198,7 +198,7 @@ def run_gpu(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2508_03065_gb300 import api
+    from paper_2508_03065_gb300 import api, multigpu
     from paper_2508_03065_gb300 import workloads as W
 
     spec = W.config2()
@@ -227,9 +227,7 @@ def run_gpu(args):
     def max_over_ranks(v):
         if dist is None:
             return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return multigpu.job_throughput(0.0, v)[1]
 
     for _ in range(max(args.warmup, 3)):
         api.synthesize([room], [x], out=[y], workspace=ws)
