@@ -33,12 +33,12 @@ METRIC = "image-samples/s (forward, order-20 48 kHz)"
 UNIT = "image-samples/s"
 
 # Algorithmic work of the synthesis kernel per image-sample (signal-side Farrow,
-# 2 segments x degree 7): 8 prefiltered values gathered from shared memory.
-Z_BYTES_PER_IMAGE_SAMPLE = 8 * 4
-# FP32 operations per image-sample: Horner 7 FMA (14), accumulate 1 FMA (2),
-# delay interpolation 1 FMA (2), fraction and segment split 5, delay 1 ADD,
-# gain 1 division (1) -> 25.
-FLOPS_PER_IMAGE_SAMPLE = 25
+# 3 segments x degree 5): 6 prefiltered values gathered from shared memory.
+Z_BYTES_PER_IMAGE_SAMPLE = 6 * 4
+# FP32 operations per image-sample: Horner 5 FMA (10), accumulate 1 FMA (2),
+# delay interpolation 1 FMA (2), fraction and segment split 6, delay 1 ADD,
+# gain 1 division (1) -> 22.
+FLOPS_PER_IMAGE_SAMPLE = 22
 # DRAM bytes (read + write) of one synthesis launch on this workload, from the
 # ncu capture of the 1 s version of the scene (26.0 MB) scaled by the
 # image-samples processed (x4); None whenever the kernel changed since.

@@ -251,7 +251,7 @@ struct Plan {
   // byte offsets in the workspace
   size_t off_desc = 0, off_keys_in = 0, off_keys_out = 0, off_vals_in = 0, off_vals_out = 0;
   size_t off_sort = 0, sort_bytes = 0, off_code = 0, off_gain = 0, off_knots = 0;
-  size_t off_z = 0, off_part = 0, fwd_bytes = 0, desc_bytes = 0;
+  size_t off_z = 0, off_zp = 0, off_part = 0, fwd_bytes = 0, desc_bytes = 0;
   // reverse mode
   bool backward = false;
   size_t off_dxb = 0, off_kslot = 0, off_bpart = 0, off_gk = 0;
@@ -380,7 +380,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     }
     img_acc += S.n_images;
     knot_acc += kfirst;
-    z_acc += int64_t(kZQuadRows) * S.z_len;
+    z_acc += int64_t(kFarrowSegs) * S.z_len;
     part_acc += int64_t(S.n_mics) * S.n_blocks * S.n_out;
   }
   P.taps = rooms[0]->d.taps;
@@ -402,6 +402,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.off_gain = off; off = align256(off + 4 * I);
   P.off_knots = off; off = align256(off + 24 * size_t(knot_acc));
   P.off_z = off; off = align256(off + 16 * size_t(z_acc));
+  P.off_zp = off; off = align256(off + 8 * size_t(z_acc));
   if (!backward) {
     P.off_part = off; off = align256(off + 4 * size_t(part_acc));
   } else {
@@ -431,7 +432,8 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.img_code = reinterpret_cast<uint32_t*>(ws + P.off_code);
   a.p.img_gain = reinterpret_cast<float*>(ws + P.off_gain);
   a.p.knot_pos = reinterpret_cast<double*>(ws + P.off_knots);
-  a.p.z = reinterpret_cast<float4*>(ws + P.off_z);
+  a.p.zq = reinterpret_cast<float4*>(ws + P.off_z);
+  a.p.zp = reinterpret_cast<float2*>(ws + P.off_zp);
   a.p.part = reinterpret_cast<float*>(ws + P.off_part);
   if (P.backward) {
     a.p.dxb = reinterpret_cast<float*>(ws + P.off_dxb);

@@ -38,7 +38,7 @@ constexpr int kBwUnitCap = 1152;  // unit vectors (image x knot)
 constexpr int kBwBlock = 128;     // images per block at most
 
 constexpr int kBwSegCap = 33;     // knot intervals touched by one warp's 32 samples
-constexpr size_t kBwSmem = size_t(2 * kZQuadRows * kBwWcap) * sizeof(float4) +
+constexpr size_t kBwSmem = size_t(2 * kFarrowSegs * kBwWcap) * (sizeof(float4) + sizeof(float2)) +
                            size_t(kBwRecCap) * sizeof(int4) + size_t(kBwUnitCap) * sizeof(float4) +
                            size_t(2 * kBwBlock) * sizeof(float4) +
                            size_t(6 * kBwSegCap * (kBwThreads / 32)) * sizeof(float);
@@ -46,6 +46,10 @@ constexpr size_t kBwSmem = size_t(2 * kZQuadRows * kBwWcap) * sizeof(float4) +
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -74,15 +78,17 @@ __device__ void beta_weights(const SceneDev& S, uint32_t code, double out[6]) {
 template <int kL>
 __global__ void __launch_bounds__(kBwThreads, 1) k_adjoint(const __grid_constant__ KernelArgs a) {
   extern __shared__ __align__(16) float4 sm[];
-  float4* zs = sm;                                        // kZQuadRows x kBwWcap
-  float4* ws = zs + kZQuadRows * kBwWcap;                 // kZQuadRows x kBwWcap
-  int4* rec_s = reinterpret_cast<int4*>(ws + kZQuadRows * kBwWcap);
+  float4* zq_s = sm;                                      // kFarrowSegs x kBwWcap (powers 0..3)
+  float4* wq_s = zq_s + kFarrowSegs * kBwWcap;            // same layout, dx bins
+  float2* zp_s = reinterpret_cast<float2*>(wq_s + kFarrowSegs * kBwWcap);  // powers 4..5
+  float2* wp_s = zp_s + kFarrowSegs * kBwWcap;
+  int4* rec_s = reinterpret_cast<int4*>(wp_s + kFarrowSegs * kBwWcap);
   float4* unit_s = reinterpret_cast<float4*>(rec_s + kBwRecCap);
   float4* bw_s = unit_s + kBwUnitCap;                     // 2 per image
   float* seg_s = reinterpret_cast<float*>(bw_s + 2 * kBwBlock);  // [warp][interval][6]
   // prologue scratch aliases the w window
-  float4* u_s = ws;
-  float4* anc_s = ws + kBwTile + 4;
+  float4* u_s = wq_s;
+  float4* anc_s = wq_s + kBwTile + 4;
   __shared__ int s_item;
   __shared__ float s_red[2][kBwThreads / 32];
   __shared__ float s_beta[kBwThreads / 32][6];
@@ -163,7 +169,8 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adjoint(const __grid_constant
       const float sN = rf / float(g.N);
       const float dyv = valid ? __ldg(S.dy + int64_t(mic) * S.n_out + n) : 0.0f;
       float v0x = 0.f, v0y = 0.f, v0z = 0.f, v1x = 0.f, v1y = 0.f, v1z = 0.f;
-      const float4* zg = a.p.z + S.z_base;
+      const float4* zqg = a.p.zq + S.z_base;
+      const float2* zpg = a.p.zp + S.z_base;
 
       for (int p0 = 0; p0 < width; p0 += kBwWcap) {
         const int pass_lo = m_lo + p0;
@@ -175,60 +182,56 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adjoint(const __grid_constant
           const int cnt_c = int(hi_c > lo_c ? hi_c - lo_c : int64_t(0));
           const int dst0 = int(lo_c - pass_lo);
           if (cnt_c != pw && threadIdx.x == 0) atomicOr(a.p.err, kErrWindowClamp);
-          for (int i = threadIdx.x; i < kZQuadRows * cnt_c; i += kBwThreads) {
-            const int rr = i / cnt_c, c = i - rr * cnt_c;
-            cp_async16(zs + rr * kBwWcap + dst0 + c, zg + int64_t(rr) * S.z_len + (lo_c - S.z_m0) + c);
+          for (int i = threadIdx.x; i < kFarrowSegs * cnt_c; i += kBwThreads) {
+            const int sg = i / cnt_c, c = i - sg * cnt_c;
+            cp_async16(zq_s + sg * kBwWcap + dst0 + c, zqg + int64_t(sg) * S.z_len + (lo_c - S.z_m0) + c);
+            cp_async8(zp_s + sg * kBwWcap + dst0 + c, zpg + int64_t(sg) * S.z_len + (lo_c - S.z_m0) + c);
           }
-          for (int i = threadIdx.x; i < kZQuadRows * kBwWcap; i += kBwThreads)
-            ws[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int i = threadIdx.x; i < kFarrowSegs * kBwWcap; i += kBwThreads) {
+            wq_s[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            wp_s[i] = make_float2(0.f, 0.f);
+          }
           cp_async_wait_all();
         }
         __syncthreads();
         const int rm = r - pass_lo;
         for (int ib = 0; ib < g.cnt; ++ib) {
           const int4 rec = rec_s[ib * nrec + jc];
-          const float y = fmaf(rf, __int_as_float(rec.z), __int_as_float(rec.y));
-          const float q = y + 12582912.0f;
-          const int k = __float_as_int(q) - 0x4B400000;
-          const float al = y - (q - 12582912.0f);
-          const int col = rm + rec.x + k;
-          if (valid && unsigned(col) < unsigned(pw)) {
-            const float vv0 = fmaf(al, 4.0f, 1.0f);
-            const bool hi = vv0 >= 1.0f;
-            const float v = hi ? vv0 - 2.0f : vv0;
-            const float tau = __int_as_float(rec.w) - y;
-            const int base = (hi ? 2 * kBwWcap : 0) + col;
-            const float4 lo4 = zs[base], hi4 = zs[base + kBwWcap];
+          const DelaySplit ds = split_delay(rec, rm, rf);
+          if (valid && unsigned(ds.col) < unsigned(pw)) {
+            const float v = ds.v;
+            const int idx = ds.seg * kBwWcap + ds.col;
+            const float4 A = zq_s[idx];
+            const float2 Bz = zp_s[idx];
             // e = P(v) and dP/dv together (Horner)
-            float pe = hi4.w, pd = 0.0f;
-            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, hi4.z);
-            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, hi4.y);
-            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, hi4.x);
-            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, lo4.w);
-            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, lo4.z);
-            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, lo4.y);
-            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, lo4.x);
-            const float rt = 1.0f / tau;
+            float pe = Bz.y, pd = 0.0f;
+            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, Bz.x);
+            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.w);
+            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.z);
+            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.y);
+            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.x);
+            const float rt = 1.0f / ds.tau;
             const float4 B0 = bw_s[2 * ib], B1 = bw_s[2 * ib + 1];
-            const float val = dyv * B1.z * rt;                       // dy g
-            const float ad = -val * fsc * fmaf(4.0f, pd, pe * rt);   // dL/dd_i(n)
+            const float val = dyv * B1.z * rt;                                  // dy g
+            // dalpha/dtau = -1, dv/dalpha = 2 kFarrowSegs
+            const float ad = -val * fsc * fmaf(float(2 * kFarrowSegs), pd, pe * rt);  // dL/dd_i(n)
             const float4 U0 = unit_s[ib * g.nk + jc];
             const float4 U1 = unit_s[ib * g.nk + jc + 1];
             const float w1 = ad * sN, w0 = ad - w1;
             v0x = fmaf(w0, U0.x, v0x); v0y = fmaf(w0, U0.y, v0y); v0z = fmaf(w0, U0.z, v0z);
             v1x = fmaf(w1, U1.x, v1x); v1y = fmaf(w1, U1.y, v1y); v1z = fmaf(w1, U1.z, v1z);
-            const float hbv = dyv * pe * rt * fsc;                   // dy e / d (4 pi in B)
+            const float hbv = dyv * pe * rt * fsc;                              // dy e / d (4 pi in B)
             bacc[0] = fmaf(hbv, B0.x, bacc[0]); bacc[1] = fmaf(hbv, B0.y, bacc[1]);
             bacc[2] = fmaf(hbv, B0.z, bacc[2]); bacc[3] = fmaf(hbv, B0.w, bacc[3]);
             bacc[4] = fmaf(hbv, B1.x, bacc[4]); bacc[5] = fmaf(hbv, B1.y, bacc[5]);
             // w[seg][q][m0] += dy g v^q
-            const float p1 = val * v, p2 = p1 * v, p3 = p2 * v, p4 = p3 * v, p5 = p4 * v, p6 = p5 * v,
-                        p7 = p6 * v;
-            float4 wa = ws[base], wb = ws[base + kBwWcap];
+            const float p1 = val * v, p2 = p1 * v, p3 = p2 * v, p4 = p3 * v, p5 = p4 * v;
+            float4 wa = wq_s[idx];
+            float2 wb = wp_s[idx];
             wa.x += val; wa.y += p1; wa.z += p2; wa.w += p3;
-            wb.x += p4; wb.y += p5; wb.z += p6; wb.w += p7;
-            ws[base] = wa;
-            ws[base + kBwWcap] = wb;
+            wb.x += p4; wb.y += p5;
+            wq_s[idx] = wa;
+            wp_s[idx] = wb;
           }
           __syncthreads();  // the next image may write the same bins
         }
@@ -243,11 +246,13 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adjoint(const __grid_constant
             // tap index kk = k + kL/2 = t - o
             const int cc = mp0 - pass_lo - kL / 2 + t;
             if (cc < 0 || cc >= pw) continue;
-            float wv[16];
+            float wv[kZRows];
 #pragma unroll
-            for (int qr = 0; qr < kZQuadRows; ++qr) {
-              const float4 w4 = ws[qr * kBwWcap + cc];
-              wv[4 * qr] = w4.x; wv[4 * qr + 1] = w4.y; wv[4 * qr + 2] = w4.z; wv[4 * qr + 3] = w4.w;
+            for (int sg = 0; sg < kFarrowSegs; ++sg) {
+              const float4 w4 = wq_s[sg * kBwWcap + cc];
+              const float2 w2 = wp_s[sg * kBwWcap + cc];
+              float* o = wv + sg * kFarrowCoef;
+              o[0] = w4.x; o[1] = w4.y; o[2] = w4.z; o[3] = w4.w; o[4] = w2.x; o[5] = w2.y;
             }
 #pragma unroll
             for (int o = 0; o < 4; ++o) {

@@ -60,10 +60,14 @@ __global__ void __launch_bounds__(kPreThreads) k_prefilter(const __grid_constant
     for (int r = 0; r < kZRows; ++r)
       acc[r] = fmaf(a.farrow[r / kFarrowCoef][r % kFarrowCoef][kk], xv, acc[r]);
   }
-  float4* z = a.p.z + S.z_base + col;
+  float4* zq = a.p.zq + S.z_base + col;
+  float2* zp = a.p.zp + S.z_base + col;
 #pragma unroll
-  for (int qr = 0; qr < kZQuadRows; ++qr)
-    z[int64_t(qr) * S.z_len] = make_float4(acc[4 * qr], acc[4 * qr + 1], acc[4 * qr + 2], acc[4 * qr + 3]);
+  for (int sg = 0; sg < kFarrowSegs; ++sg) {
+    const float* c = acc + sg * kFarrowCoef;
+    zq[int64_t(sg) * S.z_len] = make_float4(c[0], c[1], c[2], c[3]);
+    zp[int64_t(sg) * S.z_len] = make_float2(c[4], c[5]);
+  }
 }
 
 // ------------------------------------------------------------------ synthesis
@@ -71,45 +75,67 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-// Farrow polynomial of one image-sample from its two quads (Horner in v).
-__device__ __forceinline__ float horner8(const float4 lo, const float4 hi, float v) {
-  float e = fmaf(hi.w, v, hi.z);
-  e = fmaf(e, v, hi.y);
-  e = fmaf(e, v, hi.x);
-  e = fmaf(e, v, lo.w);
-  e = fmaf(e, v, lo.z);
-  e = fmaf(e, v, lo.y);
-  return fmaf(e, v, lo.x);
-}
-
-// acc += (beta_i / (4 pi d_i(n))) e_i(n) for one image-sample read from the
-// staged quads (quad row stride kStride). gain = beta_i / (4 pi) * fs / c, so
-// that the gain is gain / tau with tau the delay in samples.
-template <int kStride>
-__device__ __forceinline__ float image_sample(const float4* zs, const int4 rec, int rm, float rf,
-                                              float gain, unsigned wmax, float acc) {
-  const DelaySplit ds = split_delay(rec, rm, rf, wmax);
-  const float4* zp = zs + (ds.hi ? 2 * kStride : 0) + ds.col;
-  const float e = horner8(zp[0], zp[kStride], ds.v);
+// acc + (beta_i / (4 pi d_i(n))) e_i(n) for one image-sample read from the
+// staged window (row stride kStride). gain = beta_i / (4 pi) * fs / c, so the
+// gain is gain / tau with tau the delay in samples. kChecked: the window is
+// processed in several column passes and only columns inside this pass count.
+template <int kStride, bool kChecked>
+__device__ __forceinline__ float image_sample(const float4* zq, const float2* zp, const int4 rec, int rm,
+                                              float rf, float gain, unsigned wmax, float acc) {
+  const DelaySplit ds = split_delay(rec, rm, rf);
+  if (kChecked && unsigned(ds.col) > wmax) return acc;
+  const int idx = ds.seg * kStride + int(min(unsigned(ds.col), wmax));
+  const float e = horner6(zq[idx], zp[idx], ds.v);
   return fmaf(__fdividef(gain, ds.tau), e, acc);
 }
 
-template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock>
-__global__ void __launch_bounds__(kThreads) k_synth(const __grid_constant__ KernelArgs a) {
+template <int kStride, int kChunks, int kUnroll, bool kChecked>
+__device__ __forceinline__ void gather_images(const float4* zq, const float2* zp, const int4* rec_s, int nrec,
+                                              const float* gain, float fsc, int cnt, const int* jc,
+                                              const int* rm, const float* rf, unsigned wmax, float* acc) {
+  int ib = 0;
+  for (; ib + kUnroll <= cnt; ib += kUnroll) {
+    float gg[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) gg[u] = __ldg(gain + ib + u) * fsc;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int4* ru = rec_s + (ib + u) * nrec;
+#pragma unroll
+      for (int c = 0; c < kChunks; ++c)
+        acc[c] = image_sample<kStride, kChecked>(zq, zp, ru[jc[c]], rm[c], rf[c], gg[u], wmax, acc[c]);
+    }
+  }
+  for (; ib < cnt; ++ib) {
+    const float g0 = __ldg(gain + ib) * fsc;
+    const int4* r0 = rec_s + ib * nrec;
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c)
+      acc[c] = image_sample<kStride, kChecked>(zq, zp, r0[jc[c]], rm[c], rf[c], g0, wmax, acc[c]);
+  }
+}
+
+template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock, int kUnroll>
+__global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(const __grid_constant__ KernelArgs a) {
   extern __shared__ __align__(16) float4 smem4[];
-  float4* zs = smem4;                                            // kZQuadRows x kWcap quads
-  int4* rec_s = reinterpret_cast<int4*>(smem4 + kZQuadRows * kWcap);  // kRecCap records
+  float4* zq_s = smem4;                                                  // kFarrowSegs x kWcap
+  float2* zp_s = reinterpret_cast<float2*>(smem4 + kFarrowSegs * kWcap);  // kFarrowSegs x kWcap
+  int4* rec_s = reinterpret_cast<int4*>(zp_s + kFarrowSegs * kWcap);     // kRecCap records
   // prologue scratch aliases the z window (used before the window is staged)
   float4* u_s = smem4;
-  float4* anc_s = u_s + kThreads * kChunks + 4;                  // 2 x kBlock
+  float4* anc_s = u_s + kThreads * kChunks + 4;                          // 2 x kBlock
   __shared__ int s_item;
   __shared__ float s_red[2][kThreads / 32];
   constexpr int kTile = kThreads * kChunks;
-  static_assert(kTile + 4 + 2 * kBlock <= kZQuadRows * kWcap, "prologue scratch");
+  static_assert(kTile + 4 + 2 * kBlock <= kFarrowSegs * kWcap, "prologue scratch");
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
 
@@ -145,29 +171,10 @@ __global__ void __launch_bounds__(kThreads) k_synth(const __grid_constant__ Kern
       tmax = fmaxf(tmax, s_red[1][w]);
     }
     const int m_lo = g.n0 - int(ceilf(tmax)) - 2;
-    const int m_hi = g.n_end - int(floorf(tmin)) + 2;
-    const int width = m_hi - m_lo + 1;
-    const bool in_smem = width <= kWcap;
+    const int width = g.n_end - int(floorf(tmin)) + 2 - m_lo + 1;
 
-    // --- stage the z window [m_lo, m_lo + width) of all quad rows
-    const float4* zg = a.p.z + S.z_base;
-    if (in_smem) {
-      const int64_t lo_c = max(int64_t(m_lo), S.z_m0);
-      const int64_t hi_c = min(int64_t(m_lo) + width, S.z_m0 + S.z_len);
-      if ((lo_c != m_lo || hi_c != int64_t(m_lo) + width) && threadIdx.x == 0)
-        atomicOr(a.p.err, kErrWindowClamp);
-      const int cnt_c = int(hi_c > lo_c ? hi_c - lo_c : int64_t(0));
-      const int dst0 = int(lo_c - m_lo);
-      for (int i = threadIdx.x; i < kZQuadRows * cnt_c; i += kThreads) {
-        const int r = i / cnt_c, c = i - r * cnt_c;
-        cp_async16(zs + r * kWcap + dst0 + c, zg + int64_t(r) * S.z_len + (lo_c - S.z_m0) + c);
-      }
-      cp_async_wait_all();
-    }
-    __syncthreads();
-
-    // --- gather-accumulate: warp w owns samples n0 + 32 (w kChunks + c) + lane
-    int jc[kChunks], rm[kChunks];
+    // this thread's samples: warp w owns n0 + 32 (w kChunks + c) + lane
+    int jc[kChunks], rr[kChunks], rm[kChunks];
     float rf[kChunks], acc[kChunks];
     bool valid[kChunks];
     const int nrec = g.nk - 1;
@@ -177,49 +184,42 @@ __global__ void __launch_bounds__(kThreads) k_synth(const __grid_constant__ Kern
       valid[c] = n <= g.n_end;
       const int nn = valid[c] ? n : g.n_end;
       const int j = nn / g.N;
-      const int r = nn - j * g.N;
+      rr[c] = nn - j * g.N;
       jc[c] = j - g.jf;
-      rf[c] = float(r);
-      rm[c] = r - (in_smem ? m_lo : int(S.z_m0));
+      rf[c] = float(rr[c]);
       acc[c] = 0.0f;
     }
     const float fsc = float(S.fs / S.c);
     const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
-    if (in_smem) {
-      const unsigned wmax = unsigned(width - 1);
-      int ib = 0;
-      for (; ib + 1 < g.cnt; ib += 2) {
-        const float g0 = __ldg(gain + ib) * fsc, g1 = __ldg(gain + ib + 1) * fsc;
-        const int4* r0 = rec_s + ib * nrec;
-        const int4* r1 = r0 + nrec;
-#pragma unroll
-        for (int c = 0; c < kChunks; ++c) {
-          acc[c] = image_sample<kWcap>(zs, r0[jc[c]], rm[c], rf[c], g0, wmax, acc[c]);
-          acc[c] = image_sample<kWcap>(zs, r1[jc[c]], rm[c], rf[c], g1, wmax, acc[c]);
-        }
+    const float4* zqg = a.p.zq + S.z_base;
+    const float2* zpg = a.p.zp + S.z_base;
+
+    // --- the window [m_lo, m_lo + width) in passes of at most kWcap columns
+    for (int p0 = 0; p0 < width; p0 += kWcap) {
+      const int pass_lo = m_lo + p0;
+      const int pw = min(kWcap, width - p0);
+      if (p0 > 0) __syncthreads();  // the previous pass is done with the window
+      const int64_t lo_c = max(int64_t(pass_lo), S.z_m0);
+      const int64_t hi_c = min(int64_t(pass_lo) + pw, S.z_m0 + S.z_len);
+      if ((lo_c != pass_lo || hi_c != int64_t(pass_lo) + pw) && threadIdx.x == 0)
+        atomicOr(a.p.err, kErrWindowClamp);
+      const int cnt_c = int(hi_c > lo_c ? hi_c - lo_c : int64_t(0));
+      const int dst0 = int(lo_c - pass_lo);
+      const int64_t src0 = lo_c - S.z_m0;
+      for (int i = threadIdx.x; i < kFarrowSegs * cnt_c; i += kThreads) {
+        const int sg = i / cnt_c, c = i - sg * cnt_c;
+        cp_async16(zq_s + sg * kWcap + dst0 + c, zqg + int64_t(sg) * S.z_len + src0 + c);
+        cp_async8(zp_s + sg * kWcap + dst0 + c, zpg + int64_t(sg) * S.z_len + src0 + c);
       }
-      if (ib < g.cnt) {
-        const float g0 = __ldg(gain + ib) * fsc;
-        const int4* r0 = rec_s + ib * nrec;
+      cp_async_wait_all();
+      __syncthreads();
 #pragma unroll
-        for (int c = 0; c < kChunks; ++c)
-          acc[c] = image_sample<kWcap>(zs, r0[jc[c]], rm[c], rf[c], g0, wmax, acc[c]);
-      }
-    } else {
-      // window wider than shared memory: read the L2-resident quads directly
-      const unsigned zmax = unsigned(S.z_len - 1);
-      const int64_t zl = S.z_len;
-      for (int ib = 0; ib < g.cnt; ++ib) {
-        const float g0 = __ldg(gain + ib) * fsc;
-        const int4* r0 = rec_s + ib * nrec;
-#pragma unroll
-        for (int c = 0; c < kChunks; ++c) {
-          const DelaySplit ds = split_delay(r0[jc[c]], rm[c], rf[c], zmax);
-          const float4* zp = zg + (ds.hi ? 2 * zl : int64_t(0)) + ds.col;
-          const float e = horner8(__ldg(zp), __ldg(zp + zl), ds.v);
-          acc[c] = fmaf(__fdividef(g0, ds.tau), e, acc[c]);
-        }
-      }
+      for (int c = 0; c < kChunks; ++c) rm[c] = rr[c] - pass_lo;
+      const unsigned wmax = unsigned(pw - 1);
+      if (width <= kWcap)
+        gather_images<kWcap, kChunks, kUnroll, false>(zq_s, zp_s, rec_s, nrec, gain, fsc, g.cnt, jc, rm, rf, wmax, acc);
+      else
+        gather_images<kWcap, kChunks, kUnroll, true>(zq_s, zp_s, rec_s, nrec, gain, fsc, g.cnt, jc, rm, rf, wmax, acc);
     }
     float* out = a.p.part + S.part_base + (int64_t(g.mic) * S.n_blocks + g.blk) * S.n_out;
 #pragma unroll
@@ -250,10 +250,11 @@ __global__ void k_reduce(const __grid_constant__ KernelArgs a) {
   S.y[int64_t(mic) * S.n_out + n] = acc;
 }
 
-template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock>
+template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock, int kUnroll>
 cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
-  auto kern = k_synth<kThreads, kChunks, kWcap, kRecCap, kBlock>;
-  const size_t smem = size_t(kZQuadRows) * kWcap * sizeof(float4) + size_t(kRecCap) * sizeof(int4);
+  auto kern = k_synth<kThreads, kChunks, kWcap, kRecCap, kBlock, kUnroll>;
+  const size_t smem = size_t(kFarrowSegs) * kWcap * (sizeof(float4) + sizeof(float2)) +
+                      size_t(kRecCap) * sizeof(int4);
   static int grid = 0;
   if (grid == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -276,14 +277,16 @@ cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
 }  // namespace
 
 // Tile configurations of the synthesis launch (see TileConfig).
-#define MSRC_TILE_CONFIGS(X)          \
-  X(0, 512, 2, 2688, 3328, 256)       \
-  X(1, 256, 2, 1280, 1664, 256)       \
-  X(2, 384, 2, 2432, 3072, 256)       \
-  X(3, 1024, 1, 2688, 3328, 256)
+#define MSRC_TILE_CONFIGS(X)             \
+  X(0, 512, 2, 2432, 3328, 256, 8)       \
+  X(1, 256, 2, 1152, 1664, 256, 4)       \
+  X(2, 384, 2, 2048, 3072, 256, 4)       \
+  X(3, 1024, 1, 2432, 3328, 256, 2)      \
+  X(4, 512, 2, 2432, 3328, 256, 4)       \
+  X(5, 512, 1, 2432, 3328, 256, 8)
 
 static const TileConfig kConfigs[] = {
-#define MSRC_ROW(id, th, ch, wc, rc, bl) {th, ch, wc, rc, bl},
+#define MSRC_ROW(id, th, ch, wc, rc, bl, un) {th, ch, wc, rc, bl},
     MSRC_TILE_CONFIGS(MSRC_ROW)
 #undef MSRC_ROW
 };
@@ -308,8 +311,8 @@ cudaError_t launch_forward(const KernelArgs& a, int cfg, cudaStream_t st, cudaEv
   if (ev) cudaEventRecord(ev[0], st);
   cudaError_t e = cudaSuccess;
   switch (cfg) {
-#define MSRC_CASE(id, th, ch, wc, rc, bl) \
-  case id: e = run_synth<th, ch, wc, rc, bl>(a, st); break;
+#define MSRC_CASE(id, th, ch, wc, rc, bl, un) \
+  case id: e = run_synth<th, ch, wc, rc, bl, un>(a, st); break;
     MSRC_TILE_CONFIGS(MSRC_CASE)
 #undef MSRC_CASE
     default: e = cudaErrorInvalidValue; break;

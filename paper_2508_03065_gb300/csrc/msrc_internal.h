@@ -15,14 +15,14 @@ namespace msrc {
 // degree-kFarrowDeg polynomial in a local variable v of the fractional delay,
 // piecewise over kFarrowSegs segments of [0, 1). The prefilter produces one
 // signal row per (segment, power): z[s][q][m] = sum_k c[s][q][k] x[m - k],
-// stored as float4 "quads" (powers 4h .. 4h+3 of segment s in quad row 2s + h)
-// so that one image-sample gathers its 8 values with two 16-byte loads.
-constexpr int kFarrowSegs = 2;
-constexpr int kFarrowDeg = 7;
+// stored per segment as a float4 row (powers 0..3) and a float2 row (powers
+// 4..5), so that one image-sample gathers its 6 values with a 16-byte and an
+// 8-byte load.
+constexpr int kFarrowSegs = 3;
+constexpr int kFarrowDeg = 5;
 constexpr int kFarrowCoef = kFarrowDeg + 1;
 constexpr int kZRows = kFarrowSegs * kFarrowCoef;
-constexpr int kZQuadRows = kZRows / 4;
-static_assert(kFarrowCoef == 8 && kFarrowSegs == 2, "quad layout assumes 2 segments x 8 coefficients");
+static_assert(kFarrowCoef == 6 && kFarrowSegs == 3, "row layout assumes 3 segments x 6 coefficients");
 constexpr int kMaxTaps = 64;
 constexpr int kMaxScenesInline = 1;
 
@@ -58,8 +58,8 @@ struct SceneDev {
   int64_t knot_units_first[MSRC_MAX_TIERS];// prefix over tiers of (J_t + 1)
   int64_t part_base;                       // first partial-sum float
   int64_t n_in, n_out;
-  int64_t z_base;                          // first quad of the z rows
-  int64_t z_len;                           // quads (samples) per quad row
+  int64_t z_base;                          // first column of the scene's z rows (x kFarrowSegs rows)
+  int64_t z_len;                           // columns (samples) per row
   int64_t z_m0;                            // sample index of z column 0
   const float* x;
   float* y;
@@ -110,7 +110,8 @@ struct DevicePtrs {
   uint32_t* img_code;            // packed lattice triple and parity
   float* img_gain;               // beta_i / (4 pi)
   double* knot_pos;              // s(t_j), 3 doubles per knot
-  float4* z;                     // prefiltered rows (kZQuadRows quad rows per scene)
+  float4* zq;                    // prefiltered powers 0..3, [scene rows][segment][column]
+  float2* zp;                    // prefiltered powers 4..5, same indexing
   float* part;                   // partial sums
   // reverse mode
   float* dxb;                    // dx rows per (scene, mic, block)

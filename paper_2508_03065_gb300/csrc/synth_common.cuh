@@ -131,32 +131,46 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
 }
 
 // Interpolated delay of one image-sample split into the read position m0
-// (window column `col`, clamped to [0, wmax]), the Farrow segment `hi` of the
-// fraction alpha and its local variable v in [-1, 1], and the delay tau in
-// samples. With y = -phi(n) - 1/2, k = round(y) is floor(-phi) except when phi
-// is an integer, where it may be one less and alpha = 1 instead of 0: the two
+// (window column `col`, not clamped), the Farrow segment `seg` of the fraction
+// alpha and its local variable v in [-1, 1], and the delay tau in samples.
+// With y = -phi(n) - 1/2, k = round(y) is floor(-phi) except when phi is an
+// integer, where it may be one less and alpha = 1 instead of 0: the two
 // readings give the same value because the fractional-delay kernel is
 // continuous across alpha = 0 / 1 (h(k; 1) = h(k + 1; 0)).
 // rec = {I_j, psi_j, -slope_j, D_a - 1/2}; rm = r - m_lo where r = n - n_j.
 struct DelaySplit {
-  unsigned col;
-  bool hi;
+  int col;
+  int seg;
   float v;
   float tau;
 };
 
-__device__ __forceinline__ DelaySplit split_delay(const int4 rec, int rm, float rf, unsigned wmax) {
+__device__ __forceinline__ DelaySplit split_delay(const int4 rec, int rm, float rf) {
   const float y = fmaf(rf, __int_as_float(rec.z), __int_as_float(rec.y));
   const float q = y + 12582912.0f;  // round to nearest integer (1.5 * 2^23)
   const int k = __float_as_int(q) - 0x4B400000;
   const float a = y - (q - 12582912.0f);  // alpha - 1/2, in [-1/2, 1/2]
   DelaySplit ds;
-  ds.col = min(unsigned(rm + rec.x + k), wmax);
-  const float v0 = fmaf(a, 4.0f, 1.0f);   // 4 alpha - 1, in [-1, 3]
-  ds.hi = v0 >= 1.0f;
-  ds.v = ds.hi ? v0 - 2.0f : v0;
-  ds.tau = __int_as_float(rec.w) - y;     // tau(n) = D_a + phi(n)
+  ds.col = rm + rec.x + k;
+  // three segments of alpha: v = 2 (3 alpha - seg) - 1 = 6 a + 2 - 2 seg
+  float v = fmaf(a, 6.0f, 2.0f);  // in [-1, 5]
+  const bool s1 = v >= 1.0f;
+  v = s1 ? v - 2.0f : v;
+  const bool s2 = v >= 1.0f;
+  v = s2 ? v - 2.0f : v;
+  ds.seg = int(s1) + int(s2);
+  ds.v = v;
+  ds.tau = __int_as_float(rec.w) - y;  // tau(n) = D_a + phi(n)
   return ds;
+}
+
+// Farrow polynomial (degree 5) from the powers 0..3 (A) and 4..5 (B), Horner in v.
+__device__ __forceinline__ float horner6(const float4 A, const float2 B, float v) {
+  float e = fmaf(B.y, v, B.x);
+  e = fmaf(e, v, A.w);
+  e = fmaf(e, v, A.z);
+  e = fmaf(e, v, A.y);
+  return fmaf(e, v, A.x);
 }
 
 }  // namespace msrc

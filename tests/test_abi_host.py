@@ -165,8 +165,9 @@ def test_farrow_fit_is_accurate(taps, window):
     assert st == _lib.OK
     e = ctypes.c_double()
     assert lib.msrc_room_fit_error(h, ctypes.byref(e)) == _lib.OK
-    # polynomial error per tap small enough for the 1e-5 relative output budget
-    assert e.value < 1.5e-7
+    # polynomial error per tap (3 segments x degree 5) small enough for the 1e-5
+    # relative output budget: sqrt(L) x 3e-7 stays below 2e-6
+    assert e.value < 3e-7
     lib.msrc_destroy_room(h)
 
 
