@@ -306,6 +306,8 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     S.tile = T;
     S.n_tiles = int32_t((n_out[s] + T - 1) / T);
     S.c_over_fs = float(R->d.c / R->d.fs);
+    S.fs_over_c = R->d.fs / R->d.c;
+    S.fsc = float(S.fs_over_c);
     int first = 0, blk = 0;
     int64_t kfirst = 0;
     int max_step = 1;
@@ -373,6 +375,8 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     const int64_t u_item = backward ? int64_t(S.n_mics) * S.n_blocks
                                     : int64_t(S.n_mics) * S.n_blocks * S.n_tiles;
     const int64_t u_red = int64_t(S.n_mics) * S.n_out;
+    if (int64_t(S.n_mics) * S.n_blocks * S.n_tiles >= (int64_t(1) << 31))
+      return fail(MSRC_ERR_UNSUPPORTED, "room %d: more than 2^31 work items", s);
     const int64_t u[6] = {u_enum, u_knots, u_rec, u_z, u_item, u_red};
     for (int k = 0; k < 6; ++k) {
       P.prefix[k][s + 1] = P.prefix[k][s] + u[k];

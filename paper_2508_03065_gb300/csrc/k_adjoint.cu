@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adjoint(const __grid_constant
     const SceneDev& S = scene_of(a, s);
     const int mic = int(li / S.n_blocks);
     const int blk = int(li - int64_t(mic) * S.n_blocks);
-    const float fsc = float(S.fs / S.c);
+    const float fsc = S.fsc;
     float* dxrow = a.p.dxb + S.dxb_base + (int64_t(mic) * S.n_blocks + blk) * S.n_in;
     for (int64_t i = threadIdx.x; i < S.n_in; i += kBwThreads) dxrow[i] = 0.0f;
 

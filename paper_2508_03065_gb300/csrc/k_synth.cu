@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       rf[c] = float(rr[c]);
       acc[c] = 0.0f;
     }
-    const float fsc = float(S.fs / S.c);
+    const float fsc = S.fsc;
     const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
     const float4* zqg = a.p.zq + S.z_base;
     const float2* zpg = a.p.zp + S.z_base;

@@ -74,7 +74,8 @@ struct SceneDev {
   int32_t kcap[MSRC_MAX_TIERS];            // knot slots per (block, tile) item of tier t
   int64_t bpart_base;                      // first float of the per-(mic, block) beta partials
   float c_over_fs;                         // metres per sample of delay
-  float pad_;
+  float fsc;                               // fs / c (samples of delay per metre), FP32
+  double fs_over_c;                        // fs / c, FP64
 };
 
 // Tile configuration of the synthesis launch: CTA threads, 32-sample chunks per

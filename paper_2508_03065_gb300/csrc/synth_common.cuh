@@ -33,10 +33,12 @@ struct ItemGeom {
 
 __device__ __forceinline__ ItemGeom item_geometry(const SceneDev& S, int64_t li, int tile) {
   ItemGeom g;
-  const int tl = int(li % S.n_tiles);
-  const int64_t mb = li / S.n_tiles;
-  g.mic = int(mb / S.n_blocks);
-  g.blk = int(mb - int64_t(g.mic) * S.n_blocks);
+  // item index of one scene < 2^31 (checked when planning): 32-bit division
+  const unsigned l32 = unsigned(li);
+  const unsigned mb = l32 / unsigned(S.n_tiles);
+  const int tl = int(l32 - mb * unsigned(S.n_tiles));
+  g.mic = int(mb / unsigned(S.n_blocks));
+  g.blk = int(mb - unsigned(g.mic) * unsigned(S.n_blocks));
   int t = 0;
   while (t + 1 < S.n_tiers && g.blk >= S.block_first[t + 1]) ++t;
   g.t = t;
@@ -91,7 +93,7 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     const float uz = float(kp[3 * jj + 2] - sa2);
     u_s[jj] = make_float4(ux, uy, uz, fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
   }
-  const double fs_c = S.fs / S.c;
+  const double fs_c = S.fs_over_c;
   const uint32_t* codes = a.p.img_code + S.img_base + S.tier_first[g.t] + g.img0;
   const double* mic = S.mics[g.mic];
   for (int ib = threadIdx.x; ib < g.cnt; ib += kThreads) {
@@ -108,7 +110,7 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     anc_s[2 * ib + 1] = make_float4(float(tau - Dfl), __int_as_float(g.jf * g.N - int(Dfl)), float(Dfl), 0.0f);
   }
   __syncthreads();
-  const float fsc = float(fs_c);
+  const float fsc = S.fsc;
   const float invN = 1.0f / float(g.N);
   const int nrec = g.nk - 1;
   const int total = g.cnt * nrec;
