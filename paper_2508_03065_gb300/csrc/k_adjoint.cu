@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adjoint(const __grid_constant
         beta_weights(S, codes[ib], D);
         const float hb = float(1.0 / (4.0 * 3.14159265358979323846));
         bw_s[2 * ib] = make_float4(float(D[0]) * hb, float(D[1]) * hb, float(D[2]) * hb, float(D[3]) * hb);
-        bw_s[2 * ib + 1] = make_float4(float(D[4]) * hb, float(D[5]) * hb, gain[ib] * fsc, 0.0f);
+        bw_s[2 * ib + 1] = make_float4(float(D[4]) * hb, float(D[5]) * hb, gain[ib], 0.0f);
       }
     }
     float bacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adjoint(const __grid_constant
         __syncthreads();
         const int rm = r - pass_lo;
         for (int ib = 0; ib < g.cnt; ++ib) {
-          const int4 rec = rec_s[ib * nrec + jc];
+          const int4 rec = rec_s[jc * g.cnt + ib];
           const DelaySplit ds = split_delay(rec, rm, rf);
           if (valid && unsigned(ds.col) < unsigned(pw)) {
             const float v = ds.v;

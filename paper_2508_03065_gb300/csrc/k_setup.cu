@@ -2,7 +2,7 @@
 //   k_enumerate    image set of every scene (Sec. II-A, Eq. 1; lattice |n|_1 <= K,
 //                  8 parities) with a sort key (scene, tier, distance)
 //   (radix sort)   images ordered by key
-//   k_image_table  packed image codes and gains beta_i / (4 pi)
+//   k_image_table  packed image codes and gains beta_i / (4 pi) * fs / c
 //   k_traj_knots   source position s(t_j) at every knot of every tier, FP64
 //                  (Sec. II-C: trajectory sampled at the tier's spatial rate)
 #include <cub/device/device_radix_sort.cuh>
@@ -124,7 +124,7 @@ __global__ void k_image_table(const __grid_constant__ KernelArgs a) {
     for (int r = 0; r < e1; ++r) b *= S.beta[2 * d + 1];
   }
   a.p.img_code[gid] = code;
-  a.p.img_gain[gid] = float(b / (4.0 * 3.14159265358979323846));
+  a.p.img_gain[gid] = float(b / (4.0 * 3.14159265358979323846) * S.fs_over_c);
 }
 
 __global__ void k_traj_knots(const __grid_constant__ KernelArgs a) {

@@ -84,8 +84,8 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // acc + (beta_i / (4 pi d_i(n))) e_i(n) for one image-sample read from the
-// staged window (row stride kStride). gain = beta_i / (4 pi) * fs / c, so the
-// gain is gain / tau with tau the delay in samples. kChecked: the window is
+// staged window (row stride kStride). gain = beta_i / (4 pi) * fs / c (the
+// image table stores it so), so the gain is gain / tau with tau in samples. kChecked: the window is
 // processed in several column passes and only columns inside this pass count.
 template <int kStride, bool kChecked>
 __device__ __forceinline__ float image_sample(const float4* zq, const float2* zp, const int4 rec, int rm,
@@ -98,28 +98,29 @@ __device__ __forceinline__ float image_sample(const float4* zq, const float2* zp
 }
 
 template <int kStride, int kChunks, int kUnroll, bool kChecked>
-__device__ __forceinline__ void gather_images(const float4* zq, const float2* zp, const int4* rec_s, int nrec,
-                                              const float* gain, float fsc, int cnt, const int* jc,
-                                              const int* rm, const float* rf, unsigned wmax, float* acc) {
+__device__ __forceinline__ void gather_images(const float4* zq, const float2* zp, const int4* rec_s,
+                                              const float* gain, int cnt, const int* jc, const int* rm,
+                                              const float* rf, unsigned wmax, float* acc) {
+  // records of chunk c: row jc[c] of the interval-major table, one entry per image
+  const int4* row[kChunks];
+#pragma unroll
+  for (int c = 0; c < kChunks; ++c) row[c] = rec_s + jc[c] * cnt;
   int ib = 0;
   for (; ib + kUnroll <= cnt; ib += kUnroll) {
     float gg[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) gg[u] = __ldg(gain + ib + u) * fsc;
+    for (int u = 0; u < kUnroll; ++u) gg[u] = __ldg(gain + ib + u);
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const int4* ru = rec_s + (ib + u) * nrec;
+    for (int u = 0; u < kUnroll; ++u)
 #pragma unroll
       for (int c = 0; c < kChunks; ++c)
-        acc[c] = image_sample<kStride, kChecked>(zq, zp, ru[jc[c]], rm[c], rf[c], gg[u], wmax, acc[c]);
-    }
+        acc[c] = image_sample<kStride, kChecked>(zq, zp, row[c][ib + u], rm[c], rf[c], gg[u], wmax, acc[c]);
   }
   for (; ib < cnt; ++ib) {
-    const float g0 = __ldg(gain + ib) * fsc;
-    const int4* r0 = rec_s + ib * nrec;
+    const float g0 = __ldg(gain + ib);
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)
-      acc[c] = image_sample<kStride, kChecked>(zq, zp, r0[jc[c]], rm[c], rf[c], g0, wmax, acc[c]);
+      acc[c] = image_sample<kStride, kChecked>(zq, zp, row[c][ib], rm[c], rf[c], g0, wmax, acc[c]);
   }
 }
 
@@ -177,7 +178,6 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
     int jc[kChunks], rr[kChunks], rm[kChunks];
     float rf[kChunks], acc[kChunks];
     bool valid[kChunks];
-    const int nrec = g.nk - 1;
 #pragma unroll
     for (int c = 0; c < kChunks; ++c) {
       const int n = g.n0 + 32 * (warp * kChunks + c) + lane;
@@ -189,7 +189,6 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       rf[c] = float(rr[c]);
       acc[c] = 0.0f;
     }
-    const float fsc = S.fsc;
     const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
     const float4* zqg = a.p.zq + S.z_base;
     const float2* zpg = a.p.zp + S.z_base;
@@ -217,9 +216,9 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       for (int c = 0; c < kChunks; ++c) rm[c] = rr[c] - pass_lo;
       const unsigned wmax = unsigned(pw - 1);
       if (width <= kWcap)
-        gather_images<kWcap, kChunks, kUnroll, false>(zq_s, zp_s, rec_s, nrec, gain, fsc, g.cnt, jc, rm, rf, wmax, acc);
+        gather_images<kWcap, kChunks, kUnroll, false>(zq_s, zp_s, rec_s, gain, g.cnt, jc, rm, rf, wmax, acc);
       else
-        gather_images<kWcap, kChunks, kUnroll, true>(zq_s, zp_s, rec_s, nrec, gain, fsc, g.cnt, jc, rm, rf, wmax, acc);
+        gather_images<kWcap, kChunks, kUnroll, true>(zq_s, zp_s, rec_s, gain, g.cnt, jc, rm, rf, wmax, acc);
     }
     float* out = a.p.part + S.part_base + (int64_t(g.mic) * S.n_blocks + g.blk) * S.n_out;
 #pragma unroll

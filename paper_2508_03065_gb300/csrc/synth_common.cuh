@@ -75,8 +75,9 @@ __device__ __forceinline__ void knot_increment(const float4 A, const float4 U, f
   *d = A.w + dd;
 }
 
-// Records of the item's images over its intervals, in shared memory:
-//   rec_s[ib * (nk - 1) + jj] = {I_j = n_j - D_a, psi_j = -phi_j - 1/2,
+// Records of the item's images over its intervals, in shared memory
+// (interval-major, so that consecutive images of one interval are adjacent):
+//   rec_s[jj * cnt + ib] = {I_j = n_j - D_a, psi_j = -phi_j - 1/2,
 //                                -(phi_{j+1} - phi_j) / N_t, D_a - 1/2},  j = jf + jj,
 // where tau = d fs / c, D_a = floor(tau) at the anchor knot jf (FP64) and
 // phi_j = tau_j - D_a. u_s (nk entries) and anc_s (2 * cnt entries) are
@@ -123,7 +124,7 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     float phi0, phi1, d0, d1;
     knot_increment(A, u_s[jj], fsc, A2.x, &phi0, &d0);
     knot_increment(A, u_s[jj + 1], fsc, A2.x, &phi1, &d1);
-    rec_s[pidx] = make_int4(__float_as_int(A2.y) + jj * g.N, __float_as_int(-phi0 - 0.5f),
+    rec_s[jj * g.cnt + ib] = make_int4(__float_as_int(A2.y) + jj * g.N, __float_as_int(-phi0 - 0.5f),
                             __float_as_int((phi0 - phi1) * invN), __float_as_int(A2.z - 0.5f));
     tmin = fminf(tmin, A2.z + fminf(phi0, phi1));
     tmax = fmaxf(tmax, A2.z + fmaxf(phi0, phi1));
