@@ -152,7 +152,10 @@ msrc_status msrc_host_io_bytes(const msrc_room_t* rooms, int32_t n_rooms,
  *   dbeta_dev[r]  (6 doubles, device, nullable): dL/d beta per wall
  * Delays are recomputed from the trajectory, not stored. Reductions use a fixed
  * order, so results are bitwise reproducible. The rooms, signals and lengths must
- * be those of the forward call whose output dy refers to. */
+ * be those of the forward call whose output dy refers to. The source speed must
+ * stay below c/2 on the output range (1 ms grid), else MSRC_ERR_UNSUPPORTED:
+ * the dx scatter relies on consecutive samples of one image reading different
+ * (Farrow segment, column) bins. */
 msrc_status msrc_synthesize_backward(const msrc_room_t* rooms, int32_t n_rooms,
                                      const float* const* x_dev, const int64_t* n_in,
                                      const float* const* dy_dev, const int64_t* n_out,

@@ -41,6 +41,7 @@ struct msrc_room {
   double mics[MSRC_MAX_MICS][3];
   int32_t n_mics;
   double validated_until;  // trajectory checked on [0, validated_until]
+  double max_speed;        // largest speed seen on that range (m/s, 1 ms steps)
 };
 
 namespace {
@@ -214,6 +215,7 @@ msrc_status validate_traj_range(msrc_room& R, double t_end) {
   const double dt = 1e-3;
   const long steps = long(std::ceil(t_end / dt));
   double prev[3];
+  double vmax = 0.0;
   host_source(R.traj, 0.0, prev);
   for (long i = 0; i <= steps; ++i) {
     const double t = std::min(i * dt, t_end);
@@ -233,10 +235,12 @@ msrc_status validate_traj_range(msrc_room& R, double t_end) {
       for (int d = 0; d < 3; ++d) q += (s[d] - prev[d]) * (s[d] - prev[d]);
       if (std::sqrt(q) >= R.d.c * dt)
         return fail(MSRC_ERR_INVALID_ARG, "trajectory speed reaches c near t=%.4f s", t);
+      vmax = std::max(vmax, std::sqrt(q) / dt);
     }
     std::memcpy(prev, s, sizeof(prev));
   }
   R.validated_until = t_end;
+  R.max_speed = vmax;
   return MSRC_OK;
 }
 
@@ -350,7 +354,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
       S.bpart_base = bpart_acc;
       kslot_acc += int64_t(S.n_mics) * kslot;
       dxb_acc += int64_t(S.n_mics) * S.n_blocks * S.n_in;
-      bpart_acc += int64_t(S.n_mics) * S.n_blocks * 8;
+      bpart_acc += int64_t(S.n_mics) * S.n_blocks * S.n_tiles * 8;
     }
     // z rows cover every read position: n - tau with tau in [0, tau_bound]
     double maxL = 0, diag = 0;
@@ -367,14 +371,20 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     const double t_last = double(((n_out[s] - 1) / max_step + 1) * max_step) / R->d.fs;
     msrc_status vs = validate_traj_range(*R, std::max(t_last, R->traj.duration_s));
     if (vs != MSRC_OK) return vs;
+    // reverse mode scatters one image's samples into shared (segment, column)
+    // bins without atomics: below c/2 the read position advances by more than
+    // 1/2 sample per output sample, so no two samples of an image share a bin
+    if (backward && !(R->max_speed < 0.5 * R->d.c))
+      return fail(MSRC_ERR_UNSUPPORTED, "room %d: reverse mode needs source speed below c/2", s);
 
     const int64_t u_enum = S.n_images;
     const int64_t u_knots = kfirst;
     const int64_t u_rec = backward ? S.n_in : 0;  // reverse mode: dx samples
     const int64_t u_z = (S.z_len + 255) / 256;
-    const int64_t u_item = backward ? int64_t(S.n_mics) * S.n_blocks
-                                    : int64_t(S.n_mics) * S.n_blocks * S.n_tiles;
-    const int64_t u_red = int64_t(S.n_mics) * S.n_out;
+    // work items: (microphone, image block, tile); reverse mode adds the dx
+    // items (microphone, image block) in the reduction slot
+    const int64_t u_item = int64_t(S.n_mics) * S.n_blocks * S.n_tiles;
+    const int64_t u_red = backward ? int64_t(S.n_mics) * S.n_blocks : int64_t(S.n_mics) * S.n_out;
     if (int64_t(S.n_mics) * S.n_blocks * S.n_tiles >= (int64_t(1) << 31))
       return fail(MSRC_ERR_UNSUPPORTED, "room %d: more than 2^31 work items", s);
     const int64_t u[6] = {u_enum, u_knots, u_rec, u_z, u_item, u_red};
@@ -620,6 +630,7 @@ msrc_status msrc_set_trajectory(msrc_room_t room, const msrc_traj_desc* traj, co
   for (int m = 0; m < n_mics; ++m)
     for (int d = 0; d < 3; ++d) room->mics[m][d] = mics[3 * m + d];
   room->validated_until = -1.0;
+  room->max_speed = 0.0;
   room->has_traj = true;
   msrc_status s = validate_traj_range(*room, traj->duration_s);
   if (s != MSRC_OK) {

@@ -5,22 +5,24 @@
 // y = sum_i g_i e_i, for an upstream gradient dy:
 //   dx[m]       = sum_{s,q,k} c[s][q][k] w[s][q][m + k],
 //                 w[s][q][m] = sum over image-samples with (seg, m0) = (s, m) of dy g v^q
-//   dL/dd_i(n)  = -dy g (fs/c) (4 de/dv + e / tau)         (tau = d fs / c)
+//   dL/dd_i(n)  = -dy g (fs/c) (2S de/dv + e / tau)        (tau = d fs / c, S segments)
 //   dL/dd_{i,j} = sum_n dL/dd_i(n) * (linear-interpolation weight of knot j)
 //   dL/ds(t_j)  = sum_i dL/dd_{i,j} (sigma_i o Delta_{i,j}) / d_{i,j}
 //   dL/dbeta_w  = sum_i (dbeta_i/dbeta_w) sum_n dy e / (4 pi d)
 // then the trajectory parameters through ds(t_j)/dparams.
 //
-// k_adjoint: persistent over (scene, microphone, image block) items. The CTA
-// walks the block's output tiles in order; per tile it recomputes the knots
-// (delays are recomputed, never stored), stages the z window, and for every
-// image lets each thread handle one output sample: the knot and reflection
-// gradients accumulate in registers (a lane's knots are the same for every
-// image), and dy g v^q is scattered into a shared w window. Within one image
-// no two samples share a (segment, column) bin, so images are separated by a
-// barrier and no atomics are used. Each tile's window is correlated with the
-// Farrow coefficients and added, in tile order, to the CTA's own dx row.
-// Windows wider than shared memory are processed in several column passes.
+// k_adj_grad: persistent over (scene, mic, image block, tile) items, shaped
+//   like the forward synthesis: per image-sample e and de/dv from the staged z
+//   window, the knot gradients (a lane's knots are the same for every image)
+//   and the wall gradients accumulate in registers; no barriers in the image
+//   loop. Per item: a warp-segmented scan folds the lanes' knot vectors into
+//   knot slots; the wall partials are reduced in a fixed order.
+// k_adj_dx: persistent over (scene, mic, image block) items; walks the tiles in
+//   order, two output samples per thread. dy g v^q is scattered into a shared w
+//   window; within one image no two samples share a (segment, column) bin, so
+//   images are separated by a barrier and no atomics are used. Each tile's
+//   window is correlated with the Farrow coefficients and added, in tile
+//   order, to the CTA's own dx row. Wide windows run in several column passes.
 // k_dx_final / k_knot_final / k_param_final / k_beta_final: fixed-order sums.
 #include <cstdint>
 
@@ -30,18 +32,22 @@
 namespace msrc {
 namespace {
 
-constexpr int kBwThreads = 512;   // one output sample per thread
-constexpr int kBwTile = kBwThreads;
-constexpr int kBwWcap = 1024;     // shared z / w window (samples)
-constexpr int kBwRecCap = 1024;   // records (image x interval)
-constexpr int kBwUnitCap = 1152;  // unit vectors (image x knot)
-constexpr int kBwBlock = 128;     // images per block at most
+constexpr int kBwThreads = 512;
+constexpr int kBwChunks = 2;                    // output samples per thread per tile
+constexpr int kBwTile = kBwThreads * kBwChunks;
+constexpr int kBwRecCap = 3328;                 // records (image x interval)
+constexpr int kBwUnitCap = 3584;                // unit vectors (image x knot)
+constexpr int kBwBlock = 256;                   // images per block at most
+constexpr int kGradWcap = 1536;                 // shared z window of the gradient kernel
+constexpr int kDxWcap = 1792;                   // shared w window of the dx kernel
+constexpr int kSegCap = 33;                     // knot intervals touched by 32 consecutive samples
 
-constexpr int kBwSegCap = 33;     // knot intervals touched by one warp's 32 samples
-constexpr size_t kBwSmem = size_t(2 * kFarrowSegs * kBwWcap) * (sizeof(float4) + sizeof(float2)) +
-                           size_t(kBwRecCap) * sizeof(int4) + size_t(kBwUnitCap) * sizeof(float4) +
-                           size_t(2 * kBwBlock) * sizeof(float4) +
-                           size_t(6 * kBwSegCap * (kBwThreads / 32)) * sizeof(float);
+constexpr size_t kGradSmem = size_t(kFarrowSegs) * kGradWcap * (sizeof(float4) + sizeof(float2)) +
+                             size_t(kBwRecCap) * sizeof(int4) + size_t(kBwUnitCap) * sizeof(float4) +
+                             size_t(2 * kBwBlock) * sizeof(float4);
+constexpr size_t kDxSmem = size_t(kFarrowSegs) * kDxWcap * (sizeof(float4) + sizeof(float2)) +
+                           size_t(kBwRecCap) * sizeof(int4);
+static_assert(kGradSmem <= 232448 && kDxSmem <= 232448, "shared memory per CTA");
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -75,29 +81,54 @@ __device__ void beta_weights(const SceneDev& S, uint32_t code, double out[6]) {
   }
 }
 
-template <int kL>
-__global__ void __launch_bounds__(kBwThreads, 1) k_adjoint(const __grid_constant__ KernelArgs a) {
+__device__ __forceinline__ int next_item(const KernelArgs& a, int* s_item) {
+  if (threadIdx.x == 0) *s_item = int(atomicAdd(a.p.counter, 1u));
+  __syncthreads();
+  return *s_item;
+}
+
+// Item delay range -> window [m_lo, m_lo + width).
+template <int kThreads>
+__device__ __forceinline__ void window_of(float tmin, float tmax, const ItemGeom& g, float (*s_red)[kThreads / 32],
+                                          int* m_lo, int* width) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+    tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+  }
+  if (lane == 0) { s_red[0][warp] = tmin; s_red[1][warp] = tmax; }
+  __syncthreads();
+  tmin = s_red[0][0];
+  tmax = s_red[1][0];
+  for (int w = 1; w < kThreads / 32; ++w) {
+    tmin = fminf(tmin, s_red[0][w]);
+    tmax = fmaxf(tmax, s_red[1][w]);
+  }
+  *m_lo = g.n0 - int(ceilf(tmax)) - 2;
+  *width = g.n_end - int(floorf(tmin)) + 2 - *m_lo + 1;
+}
+
+// ------------------------------------------------------------------ gradients
+__global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constant__ KernelArgs a) {
   extern __shared__ __align__(16) float4 sm[];
-  float4* zq_s = sm;                                      // kFarrowSegs x kBwWcap (powers 0..3)
-  float4* wq_s = zq_s + kFarrowSegs * kBwWcap;            // same layout, dx bins
-  float2* zp_s = reinterpret_cast<float2*>(wq_s + kFarrowSegs * kBwWcap);  // powers 4..5
-  float2* wp_s = zp_s + kFarrowSegs * kBwWcap;
-  int4* rec_s = reinterpret_cast<int4*>(wp_s + kFarrowSegs * kBwWcap);
-  float4* unit_s = reinterpret_cast<float4*>(rec_s + kBwRecCap);
-  float4* bw_s = unit_s + kBwUnitCap;                     // 2 per image
-  float* seg_s = reinterpret_cast<float*>(bw_s + 2 * kBwBlock);  // [warp][interval][6]
-  // prologue scratch aliases the w window
-  float4* u_s = wq_s;
-  float4* anc_s = wq_s + kBwTile + 4;
+  float4* zq_s = sm;                                                    // kFarrowSegs x kGradWcap
+  float2* zp_s = reinterpret_cast<float2*>(zq_s + kFarrowSegs * kGradWcap);
+  int4* rec_s = reinterpret_cast<int4*>(zp_s + kFarrowSegs * kGradWcap);
+  float4* unit_s = reinterpret_cast<float4*>(rec_s + kBwRecCap);       // [image][knot]
+  float4* bw_s = unit_s + kBwUnitCap;                                   // 2 per image
+  float4* u_s = sm;                                                     // prologue scratch
+  float4* anc_s = sm + kBwTile + 4;
+  float* seg_s = reinterpret_cast<float*>(sm);                          // knot scan scratch (after the loop)
+  static_assert(kBwTile + 4 + 2 * kBwBlock <= kFarrowSegs * kGradWcap, "prologue scratch");
+  static_assert(6 * kSegCap * (kBwTile / 32) <= 4 * kFarrowSegs * kGradWcap, "scan scratch");
   __shared__ int s_item;
   __shared__ float s_red[2][kBwThreads / 32];
   __shared__ float s_beta[kBwThreads / 32][6];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   for (;;) {
-    if (threadIdx.x == 0) s_item = int(atomicAdd(a.p.counter, 1u));
-    __syncthreads();
-    const int64_t item = s_item;
+    const int64_t item = next_item(a, &s_item);
     if (item >= a.totals[4]) break;
     int s = 0;
     int64_t li = item;
@@ -106,126 +137,243 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adjoint(const __grid_constant
       li = item - a.tab.item_prefix[s];
     }
     const SceneDev& S = scene_of(a, s);
-    const int mic = int(li / S.n_blocks);
-    const int blk = int(li - int64_t(mic) * S.n_blocks);
+    const ItemGeom g = item_geometry(S, li, kBwTile);
     const float fsc = S.fsc;
-    float* dxrow = a.p.dxb + S.dxb_base + (int64_t(mic) * S.n_blocks + blk) * S.n_in;
-    for (int64_t i = threadIdx.x; i < S.n_in; i += kBwThreads) dxrow[i] = 0.0f;
 
-    // per-image gain and reflection-coefficient derivatives (fixed for the item)
-    ItemGeom g0 = item_geometry(S, int64_t(mic) * S.n_blocks * S.n_tiles + int64_t(blk) * S.n_tiles, kBwTile);
+    float tmin, tmax;
+    item_records<kBwThreads>(a, S, g, rec_s, u_s, anc_s, &tmin, &tmax);
+    // unit vectors (sigma o Delta) / d of every image at every knot of the tile
+    for (int pidx = threadIdx.x; pidx < g.cnt * g.nk; pidx += kBwThreads) {
+      const int ib = pidx / g.nk, jj = pidx - ib * g.nk;
+      const float4 A = anc_s[2 * ib];
+      const float4 U = u_s[jj];
+      float phi, d;
+      knot_increment(A, U, fsc, 0.0f, &phi, &d);
+      const float inv = 1.0f / d;
+      unit_s[pidx] = make_float4((A.x + U.x) * inv, (A.y + U.y) * inv, (A.z + U.z) * inv, 0.0f);
+    }
+    // gains and dbeta_i/dbeta_w / (4 pi) of the block's images
     {
-      const uint32_t* codes = a.p.img_code + S.img_base + S.tier_first[g0.t] + g0.img0;
-      const float* gain = a.p.img_gain + S.img_base + S.tier_first[g0.t] + g0.img0;
-      for (int ib = threadIdx.x; ib < g0.cnt; ib += kBwThreads) {
+      const uint32_t* codes = a.p.img_code + S.img_base + S.tier_first[g.t] + g.img0;
+      const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
+      const float hb = float(1.0 / (4.0 * 3.14159265358979323846));
+      for (int ib = threadIdx.x; ib < g.cnt; ib += kBwThreads) {
         double D[6];
         beta_weights(S, codes[ib], D);
-        const float hb = float(1.0 / (4.0 * 3.14159265358979323846));
         bw_s[2 * ib] = make_float4(float(D[0]) * hb, float(D[1]) * hb, float(D[2]) * hb, float(D[3]) * hb);
         bw_s[2 * ib + 1] = make_float4(float(D[4]) * hb, float(D[5]) * hb, gain[ib], 0.0f);
       }
     }
+    int m_lo, width;
+    window_of<kBwThreads>(tmin, tmax, g, s_red, &m_lo, &width);
+
+    int jc[kBwChunks], rr[kBwChunks];
+    float rf[kBwChunks], sN[kBwChunks], dyv[kBwChunks];
+    float V[kBwChunks][6];
+    bool valid[kBwChunks];
+#pragma unroll
+    for (int c = 0; c < kBwChunks; ++c) {
+      const int n = g.n0 + 32 * (warp * kBwChunks + c) + lane;
+      valid[c] = n <= g.n_end;
+      const int nn = valid[c] ? n : g.n_end;
+      const int j = nn / g.N;
+      rr[c] = nn - j * g.N;
+      jc[c] = j - g.jf;
+      rf[c] = float(rr[c]);
+      sN[c] = rf[c] / float(g.N);
+      dyv[c] = valid[c] ? __ldg(S.dy + int64_t(g.mic) * S.n_out + n) : 0.0f;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) V[c][k] = 0.0f;
+    }
     float bacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float4* zqg = a.p.zq + S.z_base;
+    const float2* zpg = a.p.zp + S.z_base;
+
+    for (int p0 = 0; p0 < width; p0 += kGradWcap) {
+      const int pass_lo = m_lo + p0;
+      const int pw = min(kGradWcap, width - p0);
+      __syncthreads();  // prologue scratch / previous pass done
+      const int64_t lo_c = max(int64_t(pass_lo), S.z_m0);
+      const int64_t hi_c = min(int64_t(pass_lo) + pw, S.z_m0 + S.z_len);
+      const int cnt_c = int(hi_c > lo_c ? hi_c - lo_c : int64_t(0));
+      if (cnt_c != pw && threadIdx.x == 0) atomicOr(a.p.err, kErrWindowClamp);
+      const int dst0 = int(lo_c - pass_lo);
+      for (int i = threadIdx.x; i < kFarrowSegs * cnt_c; i += kBwThreads) {
+        const int sg = i / cnt_c, c = i - sg * cnt_c;
+        cp_async16(zq_s + sg * kGradWcap + dst0 + c, zqg + int64_t(sg) * S.z_len + (lo_c - S.z_m0) + c);
+        cp_async8(zp_s + sg * kGradWcap + dst0 + c, zpg + int64_t(sg) * S.z_len + (lo_c - S.z_m0) + c);
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      for (int ib = 0; ib < g.cnt; ++ib) {
+        const float4 B0 = bw_s[2 * ib], B1 = bw_s[2 * ib + 1];
+#pragma unroll
+        for (int c = 0; c < kBwChunks; ++c) {
+          const DelaySplit ds = split_delay(rec_s[jc[c] * g.cnt + ib], rr[c] - pass_lo, rf[c]);
+          if (!valid[c] || unsigned(ds.col) >= unsigned(pw)) continue;
+          const int idx = ds.seg * kGradWcap + ds.col;
+          const float4 A = zq_s[idx];
+          const float2 Bz = zp_s[idx];
+          const float v = ds.v;
+          float pe = Bz.y, pd = 0.0f;  // e = P(v) and dP/dv together (Horner)
+          pd = fmaf(pd, v, pe); pe = fmaf(pe, v, Bz.x);
+          pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.w);
+          pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.z);
+          pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.y);
+          pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.x);
+          const float rt = __fdividef(1.0f, ds.tau);
+          const float val = dyv[c] * B1.z * rt;                                        // dy g
+          const float ad = -val * fsc * fmaf(float(2 * kFarrowSegs), pd, pe * rt);    // dL/dd_i(n)
+          const float4 U0 = unit_s[ib * g.nk + jc[c]];
+          const float4 U1 = unit_s[ib * g.nk + jc[c] + 1];
+          const float w1 = ad * sN[c], w0 = ad - w1;
+          V[c][0] = fmaf(w0, U0.x, V[c][0]); V[c][1] = fmaf(w0, U0.y, V[c][1]); V[c][2] = fmaf(w0, U0.z, V[c][2]);
+          V[c][3] = fmaf(w1, U1.x, V[c][3]); V[c][4] = fmaf(w1, U1.y, V[c][4]); V[c][5] = fmaf(w1, U1.z, V[c][5]);
+          const float hbv = dyv[c] * pe * rt * fsc;                                    // dy e / d (4 pi in B)
+          bacc[0] = fmaf(hbv, B0.x, bacc[0]); bacc[1] = fmaf(hbv, B0.y, bacc[1]);
+          bacc[2] = fmaf(hbv, B0.z, bacc[2]); bacc[3] = fmaf(hbv, B0.w, bacc[3]);
+          bacc[4] = fmaf(hbv, B1.x, bacc[4]); bacc[5] = fmaf(hbv, B1.y, bacc[5]);
+        }
+      }
+    }
+    __syncthreads();  // the z window is reused as scan scratch
+    // knot slots of the item: per chunk a warp-segmented scan over the lanes'
+    // intervals, segment tails stored per (chunk, interval), then per knot a
+    // sum over the chunks in sample order
+#pragma unroll
+    for (int c = 0; c < kBwChunks; ++c) {
+      float vals[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) vals[k] = V[c][k];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int kd = __shfl_up_sync(0xffffffffu, jc[c], d);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const float t = __shfl_up_sync(0xffffffffu, vals[k], d);
+          if (lane >= d && kd == jc[c]) vals[k] += t;
+        }
+      }
+      const int jn = __shfl_down_sync(0xffffffffu, jc[c], 1);
+      const int jw = __shfl_sync(0xffffffffu, jc[c], 0);
+      if (lane == 31 || jn != jc[c]) {
+        const int chunk = warp * kBwChunks + c;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) seg_s[(chunk * kSegCap + (jc[c] - jw)) * 6 + k] = vals[k];
+      }
+    }
+    __syncthreads();
+    {
+      float* slot = a.p.kslot + 3 * (S.kslot_first[g.t] + int64_t(g.mic) * S.kslot_mic_stride +
+                                     (int64_t(g.blk - S.block_first[g.t]) * S.n_tiles + (g.n0 / kBwTile)) *
+                                         S.kcap[g.t]);
+      constexpr int kChunksPerTile = kBwTile / 32;
+      for (int jj = threadIdx.x; jj < g.nk; jj += kBwThreads) {
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        for (int ch = 0; ch < kChunksPerTile; ++ch) {
+          const int na = g.n0 + 32 * ch;
+          if (na > g.n_end) break;
+          const int first = na / g.N - g.jf;
+          const int last = min(na + 31, g.n_end) / g.N - g.jf;
+          if (jj >= first && jj <= last) {  // V0 of interval jj
+            const float* v = seg_s + (ch * kSegCap + (jj - first)) * 6;
+            sx += v[0]; sy += v[1]; sz += v[2];
+          }
+          if (jj - 1 >= first && jj - 1 <= last) {  // V1 of interval jj - 1
+            const float* v = seg_s + (ch * kSegCap + (jj - 1 - first)) * 6;
+            sx += v[3]; sy += v[4]; sz += v[5];
+          }
+        }
+        slot[3 * jj] = sx; slot[3 * jj + 1] = sy; slot[3 * jj + 2] = sz;
+      }
+    }
+    // wall partials of the item (fixed-order block sum)
+#pragma unroll
+    for (int w = 0; w < 6; ++w) {
+      float v = bacc[w];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) s_beta[warp][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      float v = 0.f;
+      for (int w = 0; w < kBwThreads / 32; ++w) v += s_beta[w][threadIdx.x];
+      a.p.bpart[S.bpart_base + li * 8 + threadIdx.x] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ dx
+template <int kL>
+__global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant__ KernelArgs a) {
+  extern __shared__ __align__(16) float4 sm[];
+  float4* wq_s = sm;                                                    // kFarrowSegs x kDxWcap (powers 0..3)
+  float2* wp_s = reinterpret_cast<float2*>(wq_s + kFarrowSegs * kDxWcap);  // powers 4..5
+  int4* rec_s = reinterpret_cast<int4*>(wp_s + kFarrowSegs * kDxWcap);
+  float4* u_s = sm;                                                     // prologue scratch
+  float4* anc_s = sm + kBwTile + 4;
+  static_assert(kBwTile + 4 + 2 * kBwBlock <= kFarrowSegs * kDxWcap, "prologue scratch");
+  __shared__ int s_item;
+  __shared__ float s_red[2][kBwThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  for (;;) {
+    const int64_t item = next_item(a, &s_item);
+    if (item >= a.totals[5]) break;
+    int s = 0;
+    int64_t li = item;
+    if (a.n_scenes > 1) {
+      s = find_scene(a.tab.red_prefix, a.n_scenes, item);
+      li = item - a.tab.red_prefix[s];
+    }
+    const SceneDev& S = scene_of(a, s);
+    const int mic = int(li / S.n_blocks);
+    const int blk = int(li - int64_t(mic) * S.n_blocks);
+    float* dxrow = a.p.dxb + S.dxb_base + (int64_t(mic) * S.n_blocks + blk) * S.n_in;
+    for (int64_t i = threadIdx.x; i < S.n_in; i += kBwThreads) dxrow[i] = 0.0f;
 
     for (int tile = 0; tile < S.n_tiles; ++tile) {
+      __syncthreads();  // the prologue scratch aliases the w window of the previous tile
       const ItemGeom g = item_geometry(S, (int64_t(mic) * S.n_blocks + blk) * S.n_tiles + tile, kBwTile);
+      const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
       float tmin, tmax;
       item_records<kBwThreads>(a, S, g, rec_s, u_s, anc_s, &tmin, &tmax);
-      // unit vectors (sigma o Delta) / d of every image at every knot of the tile
-      const int nrec = g.nk - 1;
-      for (int pidx = threadIdx.x; pidx < g.cnt * g.nk; pidx += kBwThreads) {
-        const int ib = pidx / g.nk, jj = pidx - ib * g.nk;
-        const float4 A = anc_s[2 * ib];
-        const float4 U = u_s[jj];
-        float phi, d;
-        knot_increment(A, U, fsc, 0.0f, &phi, &d);
-        const float inv = 1.0f / d;
-        unit_s[pidx] = make_float4((A.x + U.x) * inv, (A.y + U.y) * inv, (A.z + U.z) * inv, 0.0f);
-      }
+      int m_lo, width;
+      window_of<kBwThreads>(tmin, tmax, g, s_red, &m_lo, &width);
+      int jc[kBwChunks], rr[kBwChunks];
+      float rf[kBwChunks], dyv[kBwChunks];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
-        tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+      for (int c = 0; c < kBwChunks; ++c) {
+        const int n = g.n0 + 32 * (warp * kBwChunks + c) + lane;
+        const bool valid = n <= g.n_end;
+        const int nn = valid ? n : g.n_end;
+        const int j = nn / g.N;
+        rr[c] = nn - j * g.N;
+        jc[c] = j - g.jf;
+        rf[c] = float(rr[c]);
+        dyv[c] = valid ? __ldg(S.dy + int64_t(mic) * S.n_out + n) : 0.0f;  // 0 disables the sample
       }
-      if (lane == 0) { s_red[0][warp] = tmin; s_red[1][warp] = tmax; }
-      __syncthreads();
-      tmin = s_red[0][0];
-      tmax = s_red[1][0];
-      for (int w = 1; w < kBwThreads / 32; ++w) {
-        tmin = fminf(tmin, s_red[0][w]);
-        tmax = fmaxf(tmax, s_red[1][w]);
-      }
-      const int m_lo = g.n0 - int(ceilf(tmax)) - 2;
-      const int width = g.n_end - int(floorf(tmin)) + 2 - m_lo + 1;
-
-      // this thread's output sample
-      const int n = g.n0 + threadIdx.x;
-      const bool valid = n <= g.n_end;
-      const int nn = valid ? n : g.n_end;
-      const int j = nn / g.N;
-      const int r = nn - j * g.N;
-      const int jc = j - g.jf;
-      const float rf = float(r);
-      const float sN = rf / float(g.N);
-      const float dyv = valid ? __ldg(S.dy + int64_t(mic) * S.n_out + n) : 0.0f;
-      float v0x = 0.f, v0y = 0.f, v0z = 0.f, v1x = 0.f, v1y = 0.f, v1z = 0.f;
-      const float4* zqg = a.p.zq + S.z_base;
-      const float2* zpg = a.p.zp + S.z_base;
-
-      for (int p0 = 0; p0 < width; p0 += kBwWcap) {
+      for (int p0 = 0; p0 < width; p0 += kDxWcap) {
         const int pass_lo = m_lo + p0;
-        const int pw = min(kBwWcap, width - p0);
-        __syncthreads();  // previous users of zs / ws (prologue scratch, last pass) are done
-        {
-          const int64_t lo_c = max(int64_t(pass_lo), S.z_m0);
-          const int64_t hi_c = min(int64_t(pass_lo) + pw, S.z_m0 + S.z_len);
-          const int cnt_c = int(hi_c > lo_c ? hi_c - lo_c : int64_t(0));
-          const int dst0 = int(lo_c - pass_lo);
-          if (cnt_c != pw && threadIdx.x == 0) atomicOr(a.p.err, kErrWindowClamp);
-          for (int i = threadIdx.x; i < kFarrowSegs * cnt_c; i += kBwThreads) {
-            const int sg = i / cnt_c, c = i - sg * cnt_c;
-            cp_async16(zq_s + sg * kBwWcap + dst0 + c, zqg + int64_t(sg) * S.z_len + (lo_c - S.z_m0) + c);
-            cp_async8(zp_s + sg * kBwWcap + dst0 + c, zpg + int64_t(sg) * S.z_len + (lo_c - S.z_m0) + c);
-          }
-          for (int i = threadIdx.x; i < kFarrowSegs * kBwWcap; i += kBwThreads) {
-            wq_s[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            wp_s[i] = make_float2(0.f, 0.f);
-          }
-          cp_async_wait_all();
+        const int pw = min(kDxWcap, width - p0);
+        __syncthreads();  // prologue scratch / previous pass done with the window
+        for (int i = threadIdx.x; i < kFarrowSegs * kDxWcap; i += kBwThreads) {
+          wq_s[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+          wp_s[i] = make_float2(0.f, 0.f);
         }
         __syncthreads();
-        const int rm = r - pass_lo;
         for (int ib = 0; ib < g.cnt; ++ib) {
-          const int4 rec = rec_s[jc * g.cnt + ib];
-          const DelaySplit ds = split_delay(rec, rm, rf);
-          if (valid && unsigned(ds.col) < unsigned(pw)) {
+          const float gi = __ldg(gain + ib);
+#pragma unroll
+          for (int c = 0; c < kBwChunks; ++c) {
+            const DelaySplit ds = split_delay(rec_s[jc[c] * g.cnt + ib], rr[c] - pass_lo, rf[c]);
+            if (dyv[c] == 0.0f || unsigned(ds.col) >= unsigned(pw)) continue;
+            const float val = dyv[c] * __fdividef(gi, ds.tau);  // dy g
             const float v = ds.v;
-            const int idx = ds.seg * kBwWcap + ds.col;
-            const float4 A = zq_s[idx];
-            const float2 Bz = zp_s[idx];
-            // e = P(v) and dP/dv together (Horner)
-            float pe = Bz.y, pd = 0.0f;
-            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, Bz.x);
-            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.w);
-            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.z);
-            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.y);
-            pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.x);
-            const float rt = 1.0f / ds.tau;
-            const float4 B0 = bw_s[2 * ib], B1 = bw_s[2 * ib + 1];
-            const float val = dyv * B1.z * rt;                                  // dy g
-            // dalpha/dtau = -1, dv/dalpha = 2 kFarrowSegs
-            const float ad = -val * fsc * fmaf(float(2 * kFarrowSegs), pd, pe * rt);  // dL/dd_i(n)
-            const float4 U0 = unit_s[ib * g.nk + jc];
-            const float4 U1 = unit_s[ib * g.nk + jc + 1];
-            const float w1 = ad * sN, w0 = ad - w1;
-            v0x = fmaf(w0, U0.x, v0x); v0y = fmaf(w0, U0.y, v0y); v0z = fmaf(w0, U0.z, v0z);
-            v1x = fmaf(w1, U1.x, v1x); v1y = fmaf(w1, U1.y, v1y); v1z = fmaf(w1, U1.z, v1z);
-            const float hbv = dyv * pe * rt * fsc;                              // dy e / d (4 pi in B)
-            bacc[0] = fmaf(hbv, B0.x, bacc[0]); bacc[1] = fmaf(hbv, B0.y, bacc[1]);
-            bacc[2] = fmaf(hbv, B0.z, bacc[2]); bacc[3] = fmaf(hbv, B0.w, bacc[3]);
-            bacc[4] = fmaf(hbv, B1.x, bacc[4]); bacc[5] = fmaf(hbv, B1.y, bacc[5]);
-            // w[seg][q][m0] += dy g v^q
             const float p1 = val * v, p2 = p1 * v, p3 = p2 * v, p4 = p3 * v, p5 = p4 * v;
+            const int idx = ds.seg * kDxWcap + ds.col;
             float4 wa = wq_s[idx];
             float2 wb = wp_s[idx];
             wa.x += val; wa.y += p1; wa.z += p2; wa.w += p3;
@@ -238,25 +386,25 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adjoint(const __grid_constant
         // dx[m'] += sum_{row, k} c[row][k] w[row][m' + k], 4 consecutive m' per thread
         const int n_outv = pw + kL - 1;
         for (int o4 = threadIdx.x; 4 * o4 < n_outv; o4 += kBwThreads) {
-          const int mp0 = pass_lo - kL / 2 + 1 + 4 * o4;  // first m' of this thread
+          const int mp0 = pass_lo - kL / 2 + 1 + 4 * o4;
           float acc4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
           for (int t = 0; t < kL + 3; ++t) {
-            // window column of m = mp0 - kL/2 + t; it feeds output mp0 + o through
+            // window column of m = mp0 - kL/2 + t feeds output mp0 + o through
             // tap index kk = k + kL/2 = t - o
             const int cc = mp0 - pass_lo - kL / 2 + t;
             if (cc < 0 || cc >= pw) continue;
             float wv[kZRows];
 #pragma unroll
             for (int sg = 0; sg < kFarrowSegs; ++sg) {
-              const float4 w4 = wq_s[sg * kBwWcap + cc];
-              const float2 w2 = wp_s[sg * kBwWcap + cc];
+              const float4 w4 = wq_s[sg * kDxWcap + cc];
+              const float2 w2 = wp_s[sg * kDxWcap + cc];
               float* o = wv + sg * kFarrowCoef;
               o[0] = w4.x; o[1] = w4.y; o[2] = w4.z; o[3] = w4.w; o[4] = w2.x; o[5] = w2.y;
             }
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
-              const int kk = t - o;  // k + kL/2
+              const int kk = t - o;
               if (kk < 0 || kk >= kL) continue;
 #pragma unroll
               for (int row = 0; row < kZRows; ++row)
@@ -270,63 +418,6 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adjoint(const __grid_constant
           }
         }
       }
-      // knot gradients of this tile: a warp-segmented inclusive scan over the
-      // lanes' intervals (non-decreasing along the lanes), the segment tails
-      // stored per (warp, interval), then per knot a sum over warps in order
-      {
-        float vals[6] = {v0x, v0y, v0z, v1x, v1y, v1z};
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const int kd = __shfl_up_sync(0xffffffffu, jc, d);
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            const float t = __shfl_up_sync(0xffffffffu, vals[c], d);
-            if (lane >= d && kd == jc) vals[c] += t;
-          }
-        }
-        const int jn = __shfl_down_sync(0xffffffffu, jc, 1);
-        const int jw = __shfl_sync(0xffffffffu, jc, 0);
-        if (lane == 31 || jn != jc) {
-#pragma unroll
-          for (int c = 0; c < 6; ++c) seg_s[(warp * kBwSegCap + (jc - jw)) * 6 + c] = vals[c];
-        }
-      }
-      __syncthreads();
-      float* slot = a.p.kslot + 3 * (S.kslot_first[g.t] + int64_t(mic) * S.kslot_mic_stride +
-                                     (int64_t(blk - S.block_first[g.t]) * S.n_tiles + tile) * S.kcap[g.t]);
-      for (int jj = threadIdx.x; jj < g.nk; jj += kBwThreads) {
-        float sx = 0.f, sy = 0.f, sz = 0.f;
-        for (int w = 0; w < kBwThreads / 32; ++w) {
-          const int na = g.n0 + 32 * w;
-          if (na > g.n_end) break;
-          const int first = na / g.N - g.jf;
-          const int last = min(na + 31, g.n_end) / g.N - g.jf;
-          if (jj >= first && jj <= last) {  // V0 of interval jj
-            const float* v = seg_s + (w * kBwSegCap + (jj - first)) * 6;
-            sx += v[0]; sy += v[1]; sz += v[2];
-          }
-          if (jj - 1 >= first && jj - 1 <= last) {  // V1 of interval jj - 1
-            const float* v = seg_s + (w * kBwSegCap + (jj - 1 - first)) * 6;
-            sx += v[3]; sy += v[4]; sz += v[5];
-          }
-        }
-        slot[3 * jj] = sx; slot[3 * jj + 1] = sy; slot[3 * jj + 2] = sz;
-      }
-      __syncthreads();
-    }
-    // reflection-coefficient partials of the item (fixed-order block sum)
-#pragma unroll
-    for (int w = 0; w < 6; ++w) {
-      float v = bacc[w];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) s_beta[warp][w] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 6) {
-      float v = 0.f;
-      for (int w = 0; w < kBwThreads / 32; ++w) v += s_beta[w][threadIdx.x];
-      a.p.bpart[S.bpart_base + (int64_t(mic) * S.n_blocks + blk) * 8 + threadIdx.x] = v;
     }
     __syncthreads();
   }
@@ -369,10 +460,13 @@ __global__ void k_knot_final(const __grid_constant__ KernelArgs a) {
   const int N = S.tier_step[t];
   double gx = 0.0, gy = 0.0, gz = 0.0;
   if (S.tier_count[t] > 0) {
-    const int kt = int((int64_t(j) * N) / S.tile);
+    // samples weighting knot j: intervals j - 1 and j, n in [(j-1) N, (j+1) N)
+    const int64_t s_lo = max(int64_t(j - 1) * N, int64_t(0));
+    const int64_t s_hi = min(int64_t(j + 1) * N - 1, S.n_out - 1);
+    const int tile_lo = int(s_lo / S.tile), tile_hi = int(s_hi / S.tile);
     for (int mic = 0; mic < S.n_mics; ++mic)
       for (int b = 0; b < S.tier_blocks[t]; ++b)
-        for (int tile = max(kt - 1, 0); tile <= min(kt, S.n_tiles - 1); ++tile) {
+        for (int tile = tile_lo; tile <= tile_hi; ++tile) {
           const int n0 = tile * S.tile;
           const int n_end = int(min(int64_t(n0 + S.tile), S.n_out)) - 1;
           const int jf = n0 / N, nk = n_end / N - jf + 2;
@@ -476,46 +570,48 @@ __global__ void k_beta_final(const __grid_constant__ KernelArgs a) {
   const SceneDev& S = scene_of(a, blockIdx.x);
   if (!S.dbeta || threadIdx.x >= 6) return;
   double acc = 0.0;
-  const int rows = S.n_mics * S.n_blocks;
-  for (int rr = 0; rr < rows; ++rr) acc += a.p.bpart[S.bpart_base + int64_t(rr) * 8 + threadIdx.x];
+  const int64_t rows = int64_t(S.n_mics) * S.n_blocks * S.n_tiles;
+  for (int64_t rr = 0; rr < rows; ++rr) acc += a.p.bpart[S.bpart_base + rr * 8 + threadIdx.x];
   S.dbeta[threadIdx.x] = acc;
+}
+
+template <typename K>
+cudaError_t persistent_launch(K kern, size_t smem, int64_t items, const KernelArgs& a, cudaStream_t st,
+                              int* grid) {
+  if (*grid == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBwThreads, smem);
+    if (e != cudaSuccess) return e;
+    *grid = sms * (occ > 0 ? occ : 1);
+  }
+  const int g = int(items < *grid ? items : *grid);
+  cudaError_t e = cudaMemsetAsync(a.p.counter, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  if (g > 0) kern<<<g, kBwThreads, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
-static const TileConfig kBwConfig = {kBwThreads, 1, kBwWcap, kBwRecCap, kBwBlock};
+static const TileConfig kBwConfig = {kBwThreads, kBwChunks, kGradWcap, kBwRecCap, kBwBlock};
 const TileConfig& backward_tile_config() { return kBwConfig; }
 size_t backward_unit_cap() { return kBwUnitCap; }
 
 cudaError_t launch_prefilter(const KernelArgs& a, cudaStream_t st);
 
-template <int kL>
-static cudaError_t run_adjoint(const KernelArgs& a, cudaStream_t st) {
-  static int grid = 0;
-  if (grid == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_adjoint<kL>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBwSmem));
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint<kL>, kBwThreads, kBwSmem);
-    if (e != cudaSuccess) return e;
-    grid = sms * (occ > 0 ? occ : 1);
-  }
-  const int64_t items = a.totals[4];
-  const int g = int(items < grid ? items : grid);
-  cudaError_t e = cudaMemsetAsync(a.p.counter, 0, sizeof(uint32_t), st);
-  if (e != cudaSuccess) return e;
-  if (g > 0) k_adjoint<kL><<<g, kBwThreads, kBwSmem, st>>>(a);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
   cudaError_t e = launch_prefilter(a, st);
   if (e != cudaSuccess) return e;
-  if (a.taps <= 16) e = run_adjoint<16>(a, st);
-  else if (a.taps <= 32) e = run_adjoint<32>(a, st);
-  else e = run_adjoint<64>(a, st);
+  static int g_grad = 0, g_dx16 = 0, g_dx32 = 0, g_dx64 = 0;
+  e = persistent_launch(k_adj_grad, kGradSmem, a.totals[4], a, st, &g_grad);
+  if (e != cudaSuccess) return e;
+  if (a.taps <= 16) e = persistent_launch(k_adj_dx<16>, kDxSmem, a.totals[5], a, st, &g_dx16);
+  else if (a.taps <= 32) e = persistent_launch(k_adj_dx<32>, kDxSmem, a.totals[5], a, st, &g_dx32);
+  else e = persistent_launch(k_adj_dx<64>, kDxSmem, a.totals[5], a, st, &g_dx64);
   if (e != cudaSuccess) return e;
   const int T = 256;
   if (a.totals[2] > 0) k_dx_final<<<unsigned((a.totals[2] + T - 1) / T), T, 0, st>>>(a);

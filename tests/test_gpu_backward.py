@@ -71,6 +71,12 @@ def test_dot_product_identity_on_gpu():
     (dict(seed=66, K=2, seconds=0.03, window=W.HANN, traj_kind=W.SPLINE), [0, 1, 2, 4, 7, 11]),
     (dict(seed=67, K=2, seconds=0.03, window=W.HANN, traj_kind=W.CIRCLE), [0, 1, 3, 4, 5]),
     (dict(seed=68, K=2, seconds=0.03, window=W.HANN, traj_kind=W.LINE), [0, 1, 2, 3, 6]),
+    # knot spacings that do not divide the 1024-sample tile: a knot's samples
+    # fall in two or more tiles (spacing 12, and 1600 > one tile)
+    (dict(seed=69, K=2, seconds=0.1, window=W.KAISER, taps=32, traj_kind=W.SPLINE,
+          tiers=[(1, 16000.0), (W.RHO_INF, 16000.0 / 12)]), [0, 3, 5, 8, 10]),
+    (dict(seed=70, K=2, seconds=0.25, window=W.HANN, taps=16, traj_kind=W.CIRCLE,
+          tiers=[(0, 16000.0), (W.RHO_INF, 10.0)]), [0, 1, 3, 4, 5]),
 ])
 def test_param_and_beta_gradients_match_complex_step(kw, ids):
     spec = W.small_scene(**kw)
