@@ -14,6 +14,7 @@
 namespace msrc {
 cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st);
 size_t backward_unit_cap();
+int backward_group_images();
 }  // namespace msrc
 
 using namespace msrc;
@@ -258,7 +259,8 @@ struct Plan {
   size_t off_z = 0, off_zp = 0, off_part = 0, fwd_bytes = 0, desc_bytes = 0;
   // reverse mode
   bool backward = false;
-  size_t off_dxb = 0, off_kslot = 0, off_bpart = 0, off_gk = 0;
+  int64_t dxb_floats = 0;
+  size_t off_dxb = 0, off_kslot = 0, off_bpart = 0, off_gk = 0, off_ppart = 0, off_bwt = 0;
   int kL = 32;
   int taps = 32;
 };
@@ -343,6 +345,15 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     S.n_blocks = blk;
     S.img_base = img_acc;
     if (backward) {
+      int groups = 0;
+      for (int t = 0; t < S.n_tiers; ++t) {
+        // dx items take groups of blocks of one tier (about the same number
+        // of images each), so one Farrow correlation serves the whole group
+        S.group_blocks[t] = std::max(1, backward_group_images() / S.tier_block_images[t]);
+        S.group_first[t] = groups;
+        groups += (S.tier_blocks[t] + S.group_blocks[t] - 1) / S.group_blocks[t];
+      }
+      S.n_groups = groups;
       int64_t kslot = 0;
       for (int t = 0; t < S.n_tiers; ++t) {
         S.kcap[t] = (T - 1) / S.tier_step[t] + 3;
@@ -350,10 +361,23 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
         kslot += int64_t(S.tier_blocks[t]) * S.n_tiles * S.kcap[t];
       }
       S.kslot_mic_stride = kslot;
+      // dx items split the tiles into ranges; a range writes dx columns within
+      // [first sample - tau_max - L, last sample + L], so ranges two apart
+      // never share a column once a range spans tau_max + 2L samples: ranges
+      // of equal parity share one dx row per (mic, group)
+      {
+        double mL = 0, dg = 0;
+        for (int d = 0; d < 3; ++d) { mL = std::max(mL, R->d.dims[d]); dg += R->d.dims[d] * R->d.dims[d]; }
+        const double dm = 2.0 * S.K * mL + 2.0 * std::sqrt(dg) + 1.0;
+        const int64_t tb = int64_t(std::ceil(dm * R->d.fs / R->d.c)) + 2;
+        S.range_tiles = int32_t(std::max<int64_t>(1, (tb + 2 * R->d.taps + 16 + T - 1) / T));
+        S.n_ranges = (S.n_tiles + S.range_tiles - 1) / S.range_tiles;
+        S.dx_rows = S.n_ranges > 1 ? 2 : 1;
+      }
       S.dxb_base = dxb_acc;
       S.bpart_base = bpart_acc;
       kslot_acc += int64_t(S.n_mics) * kslot;
-      dxb_acc += int64_t(S.n_mics) * S.n_blocks * S.n_in;
+      dxb_acc += int64_t(S.n_mics) * S.n_groups * S.dx_rows * S.n_in;
       bpart_acc += int64_t(S.n_mics) * S.n_blocks * S.n_tiles * 8;
     }
     // z rows cover every read position: n - tau with tau in [0, tau_bound]
@@ -384,7 +408,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     // work items: (microphone, image block, tile); reverse mode adds the dx
     // items (microphone, image block) in the reduction slot
     const int64_t u_item = int64_t(S.n_mics) * S.n_blocks * S.n_tiles;
-    const int64_t u_red = backward ? int64_t(S.n_mics) * S.n_blocks : int64_t(S.n_mics) * S.n_out;
+    const int64_t u_red = backward ? int64_t(S.n_mics) * S.n_groups * S.n_ranges : int64_t(S.n_mics) * S.n_out;
     if (int64_t(S.n_mics) * S.n_blocks * S.n_tiles >= (int64_t(1) << 31))
       return fail(MSRC_ERR_UNSUPPORTED, "room %d: more than 2^31 work items", s);
     const int64_t u[6] = {u_enum, u_knots, u_rec, u_z, u_item, u_red};
@@ -421,9 +445,12 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     P.off_part = off; off = align256(off + 4 * size_t(part_acc));
   } else {
     P.off_dxb = off; off = align256(off + 4 * size_t(dxb_acc));
+    P.dxb_floats = dxb_acc;
     P.off_kslot = off; off = align256(off + 12 * size_t(kslot_acc));
     P.off_bpart = off; off = align256(off + 4 * size_t(bpart_acc));
     P.off_gk = off; off = align256(off + 24 * size_t(knot_acc));
+    P.off_ppart = off; off = align256(off + 8 * size_t(n) * kParamPartialsPerScene);
+    P.off_bwt = off; off = align256(off + 32 * I);
   }
   P.fwd_bytes = off;
   if (I > (size_t(1) << 31)) return fail(MSRC_ERR_UNSUPPORTED, "more than 2^31 images in one call");
@@ -451,9 +478,12 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.part = reinterpret_cast<float*>(ws + P.off_part);
   if (P.backward) {
     a.p.dxb = reinterpret_cast<float*>(ws + P.off_dxb);
+    a.p.dxb_floats = P.dxb_floats;
     a.p.kslot = reinterpret_cast<float*>(ws + P.off_kslot);
     a.p.bpart = reinterpret_cast<float*>(ws + P.off_bpart);
     a.p.gk = reinterpret_cast<double*>(ws + P.off_gk);
+    a.p.ppart = reinterpret_cast<double*>(ws + P.off_ppart);
+    a.p.bwt = reinterpret_cast<float4*>(ws + P.off_bwt);
   }
   std::memcpy(a.farrow, rooms[0]->farrow, sizeof(a.farrow));
   a.taps = P.kL;

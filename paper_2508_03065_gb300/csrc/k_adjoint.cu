@@ -17,13 +17,19 @@
 //   and the wall gradients accumulate in registers; no barriers in the image
 //   loop. Per item: a warp-segmented scan folds the lanes' knot vectors into
 //   knot slots; the wall partials are reduced in a fixed order.
-// k_adj_dx: persistent over (scene, mic, image block) items; walks the tiles in
-//   order, two output samples per thread. dy g v^q is scattered into a shared w
-//   window; within one image no two samples share a (segment, column) bin, so
-//   images are separated by a barrier and no atomics are used. Each tile's
-//   window is correlated with the Farrow coefficients and added, in tile
-//   order, to the CTA's own dx row. Wide windows run in several column passes.
-// k_dx_final / k_knot_final / k_param_final / k_beta_final: fixed-order sums.
+// k_adj_dx: persistent over (scene, mic, block group, tile range) items, a
+//   group being consecutive image blocks of one tier (about 256 images), a
+//   range spanning more than the largest delay; walks the range's tiles in
+//   order, two output samples per thread. dy g v^q of every image of the group
+//   is scattered into one shared w window; within one image no two samples
+//   share a (segment, column) bin, so images are separated by a barrier and no
+//   atomics are used. Each tile's window is correlated once with the Farrow
+//   coefficients and added, in tile order, to the dx row of the range's parity
+//   (ranges two apart write disjoint columns). The window
+//   is the union of the blocks' delay ranges (a first sweep over the blocks'
+//   records); wide windows run in several column passes.
+// k_dx_final / k_knot_final / k_param_partial + k_param_final / k_beta_final:
+// fixed-order sums.
 #include <cstdint>
 
 #include "msrc_internal.h"
@@ -45,8 +51,9 @@ constexpr int kSegCap = 33;                     // knot intervals touched by 32 
 constexpr size_t kGradSmem = size_t(kFarrowSegs) * kGradWcap * (sizeof(float4) + sizeof(float2)) +
                              size_t(kBwRecCap) * sizeof(int4) + size_t(kBwUnitCap) * sizeof(float4) +
                              size_t(2 * kBwBlock) * sizeof(float4);
+constexpr int kDxGroupImages = 256;             // images per dx item (block group), about
 constexpr size_t kDxSmem = size_t(kFarrowSegs) * kDxWcap * (sizeof(float4) + sizeof(float2)) +
-                           size_t(kBwRecCap) * sizeof(int4);
+                           size_t(kBwRecCap) * sizeof(int4) + size_t(kBwTile + 4 + 2 * kBwBlock) * sizeof(float4);
 static_assert(kGradSmem <= 232448 && kDxSmem <= 232448, "shared memory per CTA");
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -79,6 +86,25 @@ __device__ void beta_weights(const SceneDev& S, uint32_t code, double out[6]) {
         for (int r = 0; r < e[o]; ++r) v *= S.beta[o];
     out[w] = v;
   }
+}
+
+// Per image of the sorted table: dbeta_i/dbeta_w / (4 pi) and the gain.
+__global__ void k_beta_table(const __grid_constant__ KernelArgs a) {
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= a.totals[0]) return;
+  int s = 0;
+  int64_t i = gid;
+  if (a.n_scenes > 1) {
+    s = find_scene(a.tab.enum_prefix, a.n_scenes, gid);
+    i = gid - a.tab.enum_prefix[s];
+  }
+  const SceneDev& S = scene_of(a, s);
+  double D[6];
+  beta_weights(S, a.p.img_code[S.img_base + i], D);
+  const double hb = 1.0 / (4.0 * 3.14159265358979323846);
+  float4* o = a.p.bwt + 2 * (S.img_base + i);
+  o[0] = make_float4(float(D[0] * hb), float(D[1] * hb), float(D[2] * hb), float(D[3] * hb));
+  o[1] = make_float4(float(D[4] * hb), float(D[5] * hb), a.p.img_gain[S.img_base + i], 0.0f);
 }
 
 __device__ __forceinline__ int next_item(const KernelArgs& a, int* s_item) {
@@ -149,20 +175,13 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
       const float4 U = u_s[jj];
       float phi, d;
       knot_increment(A, U, fsc, 0.0f, &phi, &d);
-      const float inv = 1.0f / d;
+      const float inv = __fdividef(1.0f, d);
       unit_s[pidx] = make_float4((A.x + U.x) * inv, (A.y + U.y) * inv, (A.z + U.z) * inv, 0.0f);
     }
     // gains and dbeta_i/dbeta_w / (4 pi) of the block's images
     {
-      const uint32_t* codes = a.p.img_code + S.img_base + S.tier_first[g.t] + g.img0;
-      const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
-      const float hb = float(1.0 / (4.0 * 3.14159265358979323846));
-      for (int ib = threadIdx.x; ib < g.cnt; ib += kBwThreads) {
-        double D[6];
-        beta_weights(S, codes[ib], D);
-        bw_s[2 * ib] = make_float4(float(D[0]) * hb, float(D[1]) * hb, float(D[2]) * hb, float(D[3]) * hb);
-        bw_s[2 * ib + 1] = make_float4(float(D[4]) * hb, float(D[5]) * hb, gain[ib], 0.0f);
-      }
+      const float4* bwt = a.p.bwt + 2 * (S.img_base + S.tier_first[g.t] + g.img0);
+      for (int i = threadIdx.x; i < 2 * g.cnt; i += kBwThreads) bw_s[i] = bwt[i];
     }
     int m_lo, width;
     window_of<kBwThreads>(tmin, tmax, g, s_red, &m_lo, &width);
@@ -270,7 +289,10 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
       constexpr int kChunksPerTile = kBwTile / 32;
       for (int jj = threadIdx.x; jj < g.nk; jj += kBwThreads) {
         float sx = 0.f, sy = 0.f, sz = 0.f;
-        for (int ch = 0; ch < kChunksPerTile; ++ch) {
+        // chunks holding samples of intervals jj - 1 and jj (in sample order)
+        const int c_lo = max(0, ((g.jf + jj - 1) * g.N - g.n0) >> 5);
+        const int c_hi = min(kChunksPerTile - 1, ((g.jf + jj + 1) * g.N - 1 - g.n0) >> 5);
+        for (int ch = c_lo; ch <= c_hi; ++ch) {
           const int na = g.n0 + 32 * ch;
           if (na > g.n_end) break;
           const int first = na / g.N - g.jf;
@@ -309,12 +331,11 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
 template <int kL>
 __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant__ KernelArgs a) {
   extern __shared__ __align__(16) float4 sm[];
-  float4* wq_s = sm;                                                    // kFarrowSegs x kDxWcap (powers 0..3)
+  float4* wq_s = sm;                                                       // kFarrowSegs x kDxWcap (powers 0..3)
   float2* wp_s = reinterpret_cast<float2*>(wq_s + kFarrowSegs * kDxWcap);  // powers 4..5
   int4* rec_s = reinterpret_cast<int4*>(wp_s + kFarrowSegs * kDxWcap);
-  float4* u_s = sm;                                                     // prologue scratch
-  float4* anc_s = sm + kBwTile + 4;
-  static_assert(kBwTile + 4 + 2 * kBwBlock <= kFarrowSegs * kDxWcap, "prologue scratch");
+  float4* u_s = reinterpret_cast<float4*>(rec_s + kBwRecCap);             // record scratch
+  float4* anc_s = u_s + kBwTile + 4;
   __shared__ int s_item;
   __shared__ float s_red[2][kBwThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -329,59 +350,84 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
       li = item - a.tab.red_prefix[s];
     }
     const SceneDev& S = scene_of(a, s);
-    const int mic = int(li / S.n_blocks);
-    const int blk = int(li - int64_t(mic) * S.n_blocks);
-    float* dxrow = a.p.dxb + S.dxb_base + (int64_t(mic) * S.n_blocks + blk) * S.n_in;
-    for (int64_t i = threadIdx.x; i < S.n_in; i += kBwThreads) dxrow[i] = 0.0f;
+    const int range = int(li % S.n_ranges);
+    const int64_t mg = li / S.n_ranges;
+    const int mic = int(mg / S.n_groups);
+    const int grp = int(mg - int64_t(mic) * S.n_groups);
+    int t = 0;
+    while (t + 1 < S.n_tiers && grp >= S.group_first[t + 1]) ++t;
+    const int b0 = S.block_first[t] + (grp - S.group_first[t]) * S.group_blocks[t];
+    const int b1 = min(b0 + S.group_blocks[t], S.block_first[t] + S.tier_blocks[t]);
+    const int64_t item0 = int64_t(mic) * S.n_blocks;
+    // rows are zeroed before the launch; ranges of one parity write disjoint columns
+    float* dxrow = a.p.dxb + S.dxb_base + (mg * S.dx_rows + range % S.dx_rows) * S.n_in;
+    const int tile_end = min(S.n_tiles, (range + 1) * S.range_tiles);
 
-    for (int tile = 0; tile < S.n_tiles; ++tile) {
-      __syncthreads();  // the prologue scratch aliases the w window of the previous tile
-      const ItemGeom g = item_geometry(S, (int64_t(mic) * S.n_blocks + blk) * S.n_tiles + tile, kBwTile);
-      const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
-      float tmin, tmax;
-      item_records<kBwThreads>(a, S, g, rec_s, u_s, anc_s, &tmin, &tmax);
+    for (int tile = range * S.range_tiles; tile < tile_end; ++tile) {
+      // the group's delay range over the tile: union of its blocks' records
+      float tmin = 3.0e38f, tmax = -3.0e38f;
+      for (int b = b0; b < b1; ++b) {
+        __syncthreads();  // records of the previous block / tile are no longer read
+        const ItemGeom g = item_geometry(S, (item0 + b) * S.n_tiles + tile, kBwTile);
+        float lo, hi;
+        item_records<kBwThreads>(a, S, g, rec_s, u_s, anc_s, &lo, &hi);
+        tmin = fminf(tmin, lo);
+        tmax = fmaxf(tmax, hi);
+      }
+      const ItemGeom g0 = item_geometry(S, (item0 + b0) * S.n_tiles + tile, kBwTile);
       int m_lo, width;
-      window_of<kBwThreads>(tmin, tmax, g, s_red, &m_lo, &width);
+      window_of<kBwThreads>(tmin, tmax, g0, s_red, &m_lo, &width);
+      // every block of the group has the tier's knot spacing and the same tile
       int jc[kBwChunks], rr[kBwChunks];
       float rf[kBwChunks], dyv[kBwChunks];
 #pragma unroll
       for (int c = 0; c < kBwChunks; ++c) {
-        const int n = g.n0 + 32 * (warp * kBwChunks + c) + lane;
-        const bool valid = n <= g.n_end;
-        const int nn = valid ? n : g.n_end;
-        const int j = nn / g.N;
-        rr[c] = nn - j * g.N;
-        jc[c] = j - g.jf;
+        const int n = g0.n0 + 32 * (warp * kBwChunks + c) + lane;
+        const bool valid = n <= g0.n_end;
+        const int nn = valid ? n : g0.n_end;
+        const int j = nn / g0.N;
+        rr[c] = nn - j * g0.N;
+        jc[c] = j - g0.jf;
         rf[c] = float(rr[c]);
         dyv[c] = valid ? __ldg(S.dy + int64_t(mic) * S.n_out + n) : 0.0f;  // 0 disables the sample
       }
+      const bool reuse = (b1 - b0 == 1);  // a single block keeps its records
       for (int p0 = 0; p0 < width; p0 += kDxWcap) {
         const int pass_lo = m_lo + p0;
         const int pw = min(kDxWcap, width - p0);
-        __syncthreads();  // prologue scratch / previous pass done with the window
+        __syncthreads();  // the previous pass's correlation is done with the window
         for (int i = threadIdx.x; i < kFarrowSegs * kDxWcap; i += kBwThreads) {
           wq_s[i] = make_float4(0.f, 0.f, 0.f, 0.f);
           wp_s[i] = make_float2(0.f, 0.f);
         }
-        __syncthreads();
-        for (int ib = 0; ib < g.cnt; ++ib) {
-          const float gi = __ldg(gain + ib);
-#pragma unroll
-          for (int c = 0; c < kBwChunks; ++c) {
-            const DelaySplit ds = split_delay(rec_s[jc[c] * g.cnt + ib], rr[c] - pass_lo, rf[c]);
-            if (dyv[c] == 0.0f || unsigned(ds.col) >= unsigned(pw)) continue;
-            const float val = dyv[c] * __fdividef(gi, ds.tau);  // dy g
-            const float v = ds.v;
-            const float p1 = val * v, p2 = p1 * v, p3 = p2 * v, p4 = p3 * v, p5 = p4 * v;
-            const int idx = ds.seg * kDxWcap + ds.col;
-            float4 wa = wq_s[idx];
-            float2 wb = wp_s[idx];
-            wa.x += val; wa.y += p1; wa.z += p2; wa.w += p3;
-            wb.x += p4; wb.y += p5;
-            wq_s[idx] = wa;
-            wp_s[idx] = wb;
+        for (int b = b0; b < b1; ++b) {
+          const ItemGeom g = item_geometry(S, (item0 + b) * S.n_tiles + tile, kBwTile);
+          if (!reuse) {
+            float lo, hi;
+            __syncthreads();  // the previous block's records are no longer read
+            item_records<kBwThreads>(a, S, g, rec_s, u_s, anc_s, &lo, &hi);
           }
-          __syncthreads();  // the next image may write the same bins
+          __syncthreads();  // records and the zeroed window are complete
+          const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
+          for (int ib = 0; ib < g.cnt; ++ib) {
+            const float gi = __ldg(gain + ib);
+#pragma unroll
+            for (int c = 0; c < kBwChunks; ++c) {
+              const DelaySplit ds = split_delay(rec_s[jc[c] * g.cnt + ib], rr[c] - pass_lo, rf[c]);
+              if (dyv[c] == 0.0f || unsigned(ds.col) >= unsigned(pw)) continue;
+              const float val = dyv[c] * __fdividef(gi, ds.tau);  // dy g
+              const float v = ds.v;
+              const float p1 = val * v, p2 = p1 * v, p3 = p2 * v, p4 = p3 * v, p5 = p4 * v;
+              const int idx = ds.seg * kDxWcap + ds.col;
+              float4 wa = wq_s[idx];
+              float2 wb = wp_s[idx];
+              wa.x += val; wa.y += p1; wa.z += p2; wa.w += p3;
+              wb.x += p4; wb.y += p5;
+              wq_s[idx] = wa;
+              wp_s[idx] = wb;
+            }
+            __syncthreads();  // the next image may write the same bins
+          }
         }
         // dx[m'] += sum_{row, k} c[row][k] w[row][m' + k], 4 consecutive m' per thread
         const int n_outv = pw + kL - 1;
@@ -389,10 +435,10 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
           const int mp0 = pass_lo - kL / 2 + 1 + 4 * o4;
           float acc4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-          for (int t = 0; t < kL + 3; ++t) {
-            // window column of m = mp0 - kL/2 + t feeds output mp0 + o through
-            // tap index kk = k + kL/2 = t - o
-            const int cc = mp0 - pass_lo - kL / 2 + t;
+          for (int tt = 0; tt < kL + 3; ++tt) {
+            // window column of m = mp0 - kL/2 + tt feeds output mp0 + o through
+            // tap index kk = k + kL/2 = tt - o
+            const int cc = mp0 - pass_lo - kL / 2 + tt;
             if (cc < 0 || cc >= pw) continue;
             float wv[kZRows];
 #pragma unroll
@@ -404,7 +450,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
             }
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
-              const int kk = t - o;
+              const int kk = tt - o;
               if (kk < 0 || kk >= kL) continue;
 #pragma unroll
               for (int row = 0; row < kZRows; ++row)
@@ -418,12 +464,13 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
           }
         }
       }
+      __syncthreads();  // the correlation is done before the next tile's records
     }
     __syncthreads();
   }
 }
 
-// dx[m] = sum over microphones and blocks of the dx rows (fixed order).
+// dx[m] = sum over microphones and block groups of the dx rows (fixed order).
 __global__ void k_dx_final(const __grid_constant__ KernelArgs a) {
   const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (gid >= a.totals[2]) return;
@@ -436,7 +483,7 @@ __global__ void k_dx_final(const __grid_constant__ KernelArgs a) {
   const SceneDev& S = scene_of(a, s);
   if (!S.dx) return;
   const float* p = a.p.dxb + S.dxb_base + m;
-  const int rows = S.n_mics * S.n_blocks;
+  const int rows = S.n_mics * S.n_groups * S.dx_rows;
   float acc = 0.f;
   for (int rr = 0; rr < rows; ++rr) acc += p[int64_t(rr) * S.n_in];
   S.dx[m] = acc;
@@ -484,39 +531,40 @@ __global__ void k_knot_final(const __grid_constant__ KernelArgs a) {
   out[2] = gz;
 }
 
-// ds(t)/dparams[p] of the trajectory (3 components).
-__device__ void source_jacobian(const SceneDev& S, double t, int p, double J[3]) {
-  J[0] = J[1] = J[2] = 0.0;
+// Adds J(t)^T g to every trajectory parameter, J = ds(t)/dparams (3 x 48):
+// row[p * kParamThreads] += sum_d J[d][p] g[d].
+constexpr int kParamThreads = 256;
+constexpr int kParamChunks = 32;  // CTAs per scene of the parameter reduction
+static_assert(kParamChunks * 48 == kParamPartialsPerScene, "parameter partials per scene");
+
+__device__ void add_source_jacobian(const SceneDev& S, double t, const double g[3], double* row) {
   const double* q = S.traj;
-  if (S.traj_kind == 0) {
+  constexpr int st = kParamThreads;
+  if (S.traj_kind == 0) {  // s = p0 + v t u, u = dir / |dir|
     const double nrm = sqrt(q[3] * q[3] + q[4] * q[4] + q[5] * q[5]);
     const double u[3] = {q[3] / nrm, q[4] / nrm, q[5] / nrm};
-    if (p < 3) {
-      J[p] = 1.0;
-    } else if (p < 6) {
-      const int c = p - 3;
-      for (int d = 0; d < 3; ++d) J[d] = q[6] * t * ((d == c ? 1.0 : 0.0) - u[d] * u[c]) / nrm;
-    } else if (p == 6) {
-      for (int d = 0; d < 3; ++d) J[d] = t * u[d];
+    const double ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
+    const double f = q[6] * t / nrm;
+    for (int d = 0; d < 3; ++d) {
+      row[d * st] += g[d];
+      row[(3 + d) * st] += f * (g[d] - u[d] * ug);
     }
-  } else if (S.traj_kind == 1) {
+    row[6 * st] += t * ug;
+  } else if (S.traj_kind == 1) {  // s = c + R (cos th, sin th, 0), th = th0 + v t / R
     const double R = q[3], v = q[4];
-    const double th = q[5] + v * t / R;
     double sn, cs;
-    sincos(th, &sn, &cs);
-    if (p < 3) J[p] = 1.0;
-    else if (p == 3) { J[0] = cs + sn * v * t / R; J[1] = sn - cs * v * t / R; }
-    else if (p == 4) { J[0] = -t * sn; J[1] = t * cs; }
-    else if (p == 5) { J[0] = -R * sn; J[1] = R * cs; }
-  } else {
-    const int c = p / 3, d = p - 3 * c;
-    if (c >= S.n_ctrl) return;
+    sincos(q[5] + v * t / R, &sn, &cs);
+    const double w = v * t / R;
+    for (int d = 0; d < 3; ++d) row[d * st] += g[d];
+    row[3 * st] += (cs + sn * w) * g[0] + (sn - cs * w) * g[1];
+    row[4 * st] += t * (cs * g[1] - sn * g[0]);
+    row[5 * st] += R * (cs * g[1] - sn * g[0]);
+  } else {  // clamped uniform cubic B-spline: s = sum_c N_c(u) P_c
     const int m = S.n_ctrl - 3;
-    double u = fmin(1.0, fmax(0.0, t / S.duration));
+    const double u = fmin(1.0, fmax(0.0, t / S.duration));
     const int span = min(int(u * m), m - 1);
-    if (c < span || c > span + 3) return;
     auto knot = [m](int i) { return fmin(1.0, fmax(0.0, double(i - 3) / double(m))); };
-    // the four non-zero cubic basis functions on the span (triangular scheme)
+    // the four non-zero basis functions on the span (triangular scheme)
     const int K = span + 3;
     double Nb[4], left[4], right[4];
     Nb[0] = 1.0;
@@ -532,37 +580,51 @@ __device__ void source_jacobian(const SceneDev& S, double t, int p, double J[3])
       }
       Nb[jdeg] = saved;
     }
-    J[d] = Nb[c - span];
+    for (int r = 0; r < 4; ++r)
+      for (int d = 0; d < 3; ++d) row[(3 * (span + r) + d) * st] += Nb[r] * g[d];
   }
 }
 
-// dL/dparams[p] = sum over tiers and knots of J_p(t_j) . dL/ds(t_j)  (one CTA per (scene, p)).
-__global__ void k_param_final(const __grid_constant__ KernelArgs a) {
-  const int s = blockIdx.x / 48, p = blockIdx.x % 48;
+// Partial dL/dparams of one chunk of a scene's knots (all tiers, flattened):
+// every thread sums J(t_j)^T dL/ds(t_j) over a contiguous knot range into its
+// own shared column, then the columns are summed in thread order.
+__global__ void __launch_bounds__(kParamThreads) k_param_partial(const __grid_constant__ KernelArgs a) {
+  const int s = blockIdx.x / kParamChunks, chunk = blockIdx.x % kParamChunks;
   const SceneDev& S = scene_of(a, s);
-  __shared__ double red[256];
-  double acc = 0.0;
-  const bool used = (S.traj_kind == 0 && p < 7) || (S.traj_kind == 1 && p < 6) ||
-                    (S.traj_kind == 2 && p < 3 * S.n_ctrl);
-  if (S.dparams && used) {
-    for (int t = 0; t < S.n_tiers; ++t) {
+  extern __shared__ double rows[];  // [48][kParamThreads]
+  for (int p = 0; p < 48; ++p) rows[p * kParamThreads + threadIdx.x] = 0.0;
+  const int last = S.n_tiers - 1;
+  const int64_t total = S.knot_units_first[last] + S.tier_intervals[last] + 1;
+  const int64_t per_cta = (total + kParamChunks - 1) / kParamChunks;
+  const int64_t per_thr = (per_cta + kParamThreads - 1) / kParamThreads;
+  const int64_t lo = min(total, chunk * per_cta + threadIdx.x * per_thr);
+  const int64_t hi = min(min(total, (chunk + 1) * per_cta), lo + per_thr);
+  if (S.dparams) {
+    int t = 0;
+    for (int64_t k = lo; k < hi; ++k) {
+      while (t + 1 < S.n_tiers && k >= S.knot_units_first[t + 1]) ++t;
       if (S.tier_count[t] == 0) continue;
-      const int J = S.tier_intervals[t];
-      for (int j = threadIdx.x; j <= J; j += blockDim.x) {
-        double Jp[3];
-        source_jacobian(S, double(int64_t(j) * S.tier_step[t]) / S.fs, p, Jp);
-        const double* gk = a.p.gk + 3 * (S.knot_base[t] + j);
-        acc += Jp[0] * gk[0] + Jp[1] * gk[1] + Jp[2] * gk[2];
-      }
+      const int64_t j = k - S.knot_units_first[t];
+      const double* gk = a.p.gk + 3 * (S.knot_base[t] + j);
+      const double g[3] = {gk[0], gk[1], gk[2]};
+      add_source_jacobian(S, double(j * S.tier_step[t]) / S.fs, g, rows + threadIdx.x);
     }
   }
-  red[threadIdx.x] = acc;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.x < 48) {
+    double acc = 0.0;
+    for (int r = 0; r < kParamThreads; ++r) acc += rows[threadIdx.x * kParamThreads + r];
+    a.p.ppart[(int64_t(s) * kParamChunks + chunk) * 48 + threadIdx.x] = acc;
   }
-  if (threadIdx.x == 0 && S.dparams) S.dparams[p] = red[0];
+}
+
+// dL/dparams[p]: sum of the chunk partials in chunk order (one CTA per scene).
+__global__ void k_param_final(const __grid_constant__ KernelArgs a) {
+  const SceneDev& S = scene_of(a, blockIdx.x);
+  if (!S.dparams || threadIdx.x >= 48) return;
+  double acc = 0.0;
+  for (int c = 0; c < kParamChunks; ++c) acc += a.p.ppart[(int64_t(blockIdx.x) * kParamChunks + c) * 48 + threadIdx.x];
+  S.dparams[threadIdx.x] = acc;
 }
 
 // dL/dbeta_w: sum of the item partials in item order (one CTA per scene).
@@ -600,6 +662,7 @@ cudaError_t persistent_launch(K kern, size_t smem, int64_t items, const KernelAr
 static const TileConfig kBwConfig = {kBwThreads, kBwChunks, kGradWcap, kBwRecCap, kBwBlock};
 const TileConfig& backward_tile_config() { return kBwConfig; }
 size_t backward_unit_cap() { return kBwUnitCap; }
+int backward_group_images() { return kDxGroupImages; }
 
 cudaError_t launch_prefilter(const KernelArgs& a, cudaStream_t st);
 
@@ -607,7 +670,10 @@ cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
   cudaError_t e = launch_prefilter(a, st);
   if (e != cudaSuccess) return e;
   static int g_grad = 0, g_dx16 = 0, g_dx32 = 0, g_dx64 = 0;
+  if (a.totals[0] > 0) k_beta_table<<<unsigned((a.totals[0] + 255) / 256), 256, 0, st>>>(a);
   e = persistent_launch(k_adj_grad, kGradSmem, a.totals[4], a, st, &g_grad);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(a.p.dxb, 0, sizeof(float) * size_t(a.p.dxb_floats), st);
   if (e != cudaSuccess) return e;
   if (a.taps <= 16) e = persistent_launch(k_adj_dx<16>, kDxSmem, a.totals[5], a, st, &g_dx16);
   else if (a.taps <= 32) e = persistent_launch(k_adj_dx<32>, kDxSmem, a.totals[5], a, st, &g_dx32);
@@ -616,7 +682,17 @@ cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
   const int T = 256;
   if (a.totals[2] > 0) k_dx_final<<<unsigned((a.totals[2] + T - 1) / T), T, 0, st>>>(a);
   if (a.totals[1] > 0) k_knot_final<<<unsigned((a.totals[1] + T - 1) / T), T, 0, st>>>(a);
-  k_param_final<<<unsigned(a.n_scenes * 48), 256, 0, st>>>(a);
+  {
+    constexpr size_t smem = 48 * kParamThreads * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+      e = cudaFuncSetAttribute(k_param_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k_param_partial<<<unsigned(a.n_scenes * kParamChunks), kParamThreads, smem, st>>>(a);
+    k_param_final<<<unsigned(a.n_scenes), 64, 0, st>>>(a);
+  }
   k_beta_final<<<unsigned(a.n_scenes), 32, 0, st>>>(a);
   return cudaGetLastError();
 }

@@ -68,7 +68,13 @@ struct SceneDev {
   float* dx;                               // [n_in] or null
   double* dparams;                         // [48] or null
   double* dbeta;                           // [6] or null
-  int64_t dxb_base;                        // first float of the per-(mic, block) dx rows
+  int64_t dxb_base;                        // first float of the per-(mic, block group) dx rows
+  int32_t n_groups;                        // dx block groups over all tiers
+  int32_t group_first[MSRC_MAX_TIERS];     // first group of tier t
+  int32_t group_blocks[MSRC_MAX_TIERS];    // blocks per group of tier t
+  int32_t range_tiles;                     // tiles per dx item (tile range)
+  int32_t n_ranges;                        // tile ranges
+  int32_t dx_rows;                         // dx rows per (mic, group): one per range parity
   int64_t kslot_first[MSRC_MAX_TIERS];     // first knot-gradient slot of tier t (mic 0)
   int64_t kslot_mic_stride;                // slots per microphone
   int32_t kcap[MSRC_MAX_TIERS];            // knot slots per (block, tile) item of tier t
@@ -115,11 +121,15 @@ struct DevicePtrs {
   float2* zp;                    // prefiltered powers 4..5, same indexing
   float* part;                   // partial sums
   // reverse mode
-  float* dxb;                    // dx rows per (scene, mic, block)
+  float* dxb;                    // dx rows per (scene, mic, block group, range parity)
+  int64_t dxb_floats;            // floats of all dx rows (zeroed before the dx launch)
   float* kslot;                  // knot-gradient slots (3 floats each)
   float* bpart;                  // beta partials (8 floats per (scene, mic, block))
   double* gk;                    // dL/ds(t_j) per tier knot (3 doubles, indexed like knot_pos)
+  double* ppart;                 // trajectory-parameter partials (48 doubles per (scene, knot chunk))
+  float4* bwt;                   // per image: dbeta_i/dbeta_w / (4 pi) for walls 0..3 | walls 4..5, gain, 0
 };
+constexpr int kParamPartialsPerScene = 32 * 48;
 
 struct KernelArgs {
   SceneDev scene0;               // used when n_scenes == 1
