@@ -179,13 +179,28 @@ def run_reference(args):
     return 0
 
 
-def workload_config(spec):
+def workload_config(spec, tier_counts=None):
     from paper_2508_03065_gb300 import workloads as W
 
     return {"workload": spec.name, "images": W.image_count(spec.K), "n_out": spec.n_in, "fs": spec.fs,
             "taps": spec.taps, "window": "kaiser(8)" if spec.window == 1 else "hann",
             "tiers": [[r if r < W.RHO_INF else "rest", hz] for r, hz in spec.tiers],
-            "l2": "inputs larger than L2: the delay records (3.2 GB) are rewritten and read every step"}
+            "l2": "every step writes and reads the per-(block, tile) partial sums "
+                  + (f"({partial_bytes(spec, tier_counts) / 1e6:.0f} MB, " if tier_counts else "(")
+                  + "larger than the 129 MB L2)"}
+
+
+def partial_bytes(spec, tier_counts):
+    """Bytes of the synthesis partial sums of one step: one float per
+    (microphone, image block, output sample); blocks per tier from the record
+    capacity of the default tile configuration (3328 records of 1024 samples,
+    at most 256 images)."""
+    T, reccap, bmax = 1024, 3328, 256
+    blocks = 0
+    for (rho, n_step), cnt in zip(spec.tier_steps(), tier_counts):
+        B = max(1, min(bmax, reccap // ((T - 1) // n_step + 2)))
+        blocks += (cnt + B - 1) // B
+    return 4 * blocks * spec.n_in * len(spec.mics)
 
 
 def run_gpu(args):
@@ -276,15 +291,20 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(spec),
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(spec, room.image_count()[1]),
         "phases_ms": {"setup": phase_ms[0] / max(n_calls, 1), "prefilter": phase_ms[1] / max(n_calls, 1),
                       "synthesis": synth_ms, "reduction": phase_ms[3] / max(n_calls, 1)},
-        "roofline": {"bound": "smem", "kernel": "k_synth", "achieved": achieved, "peak": smem_peak,
-                     "unit": "GB/s", "frac": achieved / smem_peak,
+        "roofline": {"bound": "alu", "kernel": "k_synth", "achieved": fp32, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": fp32 / fp32_peak,
                      "traffic": K_SYNTH_TRAFFIC_BYTES if args.seconds is None else None,
-                     "peak_source": f"{SM_COUNT} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x median SM clock "
-                                    f"{sm_mhz:.0f} MHz under load",
-                     "fp32_tflops": fp32, "fp32_peak_tflops": fp32_peak, "fp32_frac": fp32 / fp32_peak},
+                     "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x median SM "
+                                    f"clock {sm_mhz:.0f} MHz under load (derived, not measured)",
+                     "flops_per_image_sample": FLOPS_PER_IMAGE_SAMPLE,
+                     "smem": {"achieved_gbs": achieved, "peak_gbs": smem_peak, "frac": achieved / smem_peak,
+                              "bytes_per_image_sample": Z_BYTES_PER_IMAGE_SAMPLE,
+                              "peak_source": f"{SM_COUNT} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x "
+                                             f"{sm_mhz:.0f} MHz"}},
         "e2e": {"value": work * world / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * spec.n_in, "d2h_bytes_per_step": 4 * n_out * room.n_mics},
         "gpu_launches": args.steps * launches_per_step(),

@@ -155,14 +155,13 @@ __device__ __forceinline__ DelaySplit split_delay(const int4 rec, int rm, float 
   const float a = y - (q - 12582912.0f);  // alpha - 1/2, in [-1/2, 1/2]
   DelaySplit ds;
   ds.col = rm + rec.x + k;
-  // three segments of alpha: v = 2 (3 alpha - seg) - 1 = 6 a + 2 - 2 seg
-  float v = fmaf(a, 6.0f, 2.0f);  // in [-1, 5]
-  const bool s1 = v >= 1.0f;
-  v = s1 ? v - 2.0f : v;
-  const bool s2 = v >= 1.0f;
-  v = s2 ? v - 2.0f : v;
-  ds.seg = int(s1) + int(s2);
-  ds.v = v;
+  // three segments of alpha: seg = round(3 a + 1) in {0, 1, 2} (the same
+  // rounding constant, one FMA), v = 2 (3 alpha - seg) - 1 = 6 a + 2 - 2 seg
+  // in [-1, 1]; at a segment boundary either neighbour is taken (the
+  // segment polynomials agree there to the fit error)
+  const float q2 = fmaf(a, 3.0f, 12582913.0f);
+  ds.seg = __float_as_int(q2) - 0x4B400000;
+  ds.v = fmaf(q2 - 12582912.0f, -2.0f, fmaf(a, 6.0f, 2.0f));
   ds.tau = __int_as_float(rec.w) - y;  // tau(n) = D_a + phi(n)
   return ds;
 }
