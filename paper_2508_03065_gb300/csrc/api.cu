@@ -485,7 +485,10 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
     a.p.ppart = reinterpret_cast<double*>(ws + P.off_ppart);
     a.p.bwt = reinterpret_cast<float4*>(ws + P.off_bwt);
   }
-  std::memcpy(a.farrow, rooms[0]->farrow, sizeof(a.farrow));
+  // device tables: coefficients of the powers of w = v / 2 (c_q 2^q, exact)
+  for (int sg = 0; sg < kFarrowSegs; ++sg)
+    for (int q = 0; q < kFarrowCoef; ++q)
+      for (int k = 0; k < kMaxTaps; ++k) a.farrow[sg][q][k] = std::ldexp(rooms[0]->farrow[sg][q][k], q);
   a.taps = P.kL;
   if (a.n_scenes > 1) {
     char* d = ws + P.off_desc;

@@ -1,11 +1,12 @@
 // Reverse mode of the synthesis (adjoint of Eq. 8 with the Farrow structure of
 // Eq. 5 and the hierarchical knots of Sec. II-C).
 //
-// With e_i(n) = sum_q v^q z[seg][q][m0], g_i(n) = beta_i / (4 pi d_i(n)) and
+// With e_i(n) = sum_q w^q z[seg][q][m0], g_i(n) = beta_i / (4 pi d_i(n)) and
 // y = sum_i g_i e_i, for an upstream gradient dy:
-//   dx[m]       = sum_{s,q,k} c[s][q][k] w[s][q][m + k],
-//                 w[s][q][m] = sum over image-samples with (seg, m0) = (s, m) of dy g v^q
-//   dL/dd_i(n)  = -dy g (fs/c) (2S de/dv + e / tau)        (tau = d fs / c, S segments)
+//   dx[m]       = sum_{s,q,k} c[s][q][k] W[s][q][m + k],
+//                 W[s][q][m] = sum over image-samples with (seg, m0) = (s, m) of dy g w^q
+//   dL/dd_i(n)  = -dy g (fs/c) (S de/dw + e / tau)         (tau = d fs / c, S segments,
+//                 w = S alpha - seg - 1/2 the local variable of the Farrow tables)
 //   dL/dd_{i,j} = sum_n dL/dd_i(n) * (linear-interpolation weight of knot j)
 //   dL/ds(t_j)  = sum_i dL/dd_{i,j} (sigma_i o Delta_{i,j}) / d_{i,j}
 //   dL/dbeta_w  = sum_i (dbeta_i/dbeta_w) sum_n dy e / (4 pi d)
@@ -20,7 +21,7 @@
 // k_adj_dx: persistent over (scene, mic, block group, tile range) items, a
 //   group being consecutive image blocks of one tier (about 256 images), a
 //   range spanning more than the largest delay; walks the range's tiles in
-//   order, two output samples per thread. dy g v^q of every image of the group
+//   order, two output samples per thread. dy g w^q of every image of the group
 //   is scattered into one shared w window; within one image no two samples
 //   share a (segment, column) bin, so images are separated by a barrier and no
 //   atomics are used. Each tile's window is correlated once with the Farrow
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
           pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.x);
           const float rt = __fdividef(1.0f, ds.tau);
           const float val = dyv[c] * B1.z * rt;                                        // dy g
-          const float ad = -val * fsc * fmaf(float(2 * kFarrowSegs), pd, pe * rt);    // dL/dd_i(n)
+          const float ad = -val * fsc * fmaf(float(kFarrowSegs), pd, pe * rt);        // dL/dd_i(n)
           const float4 U0 = unit_s[ib * g.nk + jc[c]];
           const float4 U1 = unit_s[ib * g.nk + jc[c] + 1];
           const float w1 = ad * sN[c], w0 = ad - w1;

@@ -12,7 +12,7 @@
 //                squared distance. Then the z window of the item is staged in
 //                shared memory with cp.async. Per image-sample: interpolate the
 //                delay linearly between knots, split it into read position m0
-//                and fraction alpha, evaluate e = sum_q v^q z[seg(alpha)][q][m0]
+//                and fraction alpha, evaluate e = sum_q w^q z[seg(alpha)][q][m0]
 //                by Horner and accumulate (beta_i / (4 pi d_i(n))) e. Each item
 //                writes one partial row (no atomics).
 //   k_reduce     y[mic][n] = sum over image blocks of the partial rows, in a
@@ -87,20 +87,34 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // staged window (row stride kStride). gain = beta_i / (4 pi) * fs / c (the
 // image table stores it so), so the gain is gain / tau with tau in samples. kChecked: the window is
 // processed in several column passes and only columns inside this pass count.
+// One image-sample: kChecked skips read positions outside the pass's columns
+// (windows wider than one pass); otherwise every position lies inside the
+// window by construction and the index is only clamped to the window arrays.
 template <int kStride, bool kChecked>
 __device__ __forceinline__ float image_sample(const float4* zq, const float2* zp, const int4 rec, int rm,
-                                              float rf, float gain, unsigned wmax, float acc) {
-  const DelaySplit ds = split_delay(rec, rm, rf);
-  if (kChecked && unsigned(ds.col) > wmax) return acc;
-  const int idx = ds.seg * kStride + int(min(unsigned(ds.col), wmax));
-  const float e = horner6(zq[idx], zp[idx], ds.v);
-  return fmaf(__fdividef(gain, ds.tau), e, acc);
+                                              unsigned rmc, float rf, float gain, unsigned wmax, float acc) {
+  float w, tau;
+  unsigned idx;
+  if (kChecked) {
+    const DelaySplit ds = split_delay(rec, rm, rf);
+    if (unsigned(ds.col) > wmax) return acc;
+    idx = unsigned(ds.seg * kStride + ds.col);
+    w = ds.v;
+    tau = ds.tau;
+  } else {
+    idx = min(split_index<kStride>(rec, rmc, rf, &w, &tau), unsigned(kFarrowSegs * kStride - 1));
+  }
+  const float e = horner6(zq[idx], zp[idx], w);
+  return fmaf(__fdividef(gain, tau), e, acc);
 }
 
 template <int kStride, int kChunks, int kUnroll, bool kChecked>
 __device__ __forceinline__ void gather_images(const float4* zq, const float2* zp, const int4* rec_s,
                                               const float* gain, int cnt, const int* jc, const int* rm,
                                               const float* rf, unsigned wmax, float* acc) {
+  unsigned rmc[kChunks];
+#pragma unroll
+  for (int c = 0; c < kChunks; ++c) rmc[c] = fold_rounding(rm[c], kStride);
   // records of chunk c: row jc[c] of the interval-major table, one entry per image
   const int4* row[kChunks];
 #pragma unroll
@@ -114,13 +128,13 @@ __device__ __forceinline__ void gather_images(const float4* zq, const float2* zp
     for (int u = 0; u < kUnroll; ++u)
 #pragma unroll
       for (int c = 0; c < kChunks; ++c)
-        acc[c] = image_sample<kStride, kChecked>(zq, zp, row[c][ib + u], rm[c], rf[c], gg[u], wmax, acc[c]);
+        acc[c] = image_sample<kStride, kChecked>(zq, zp, row[c][ib + u], rm[c], rmc[c], rf[c], gg[u], wmax, acc[c]);
   }
   for (; ib < cnt; ++ib) {
     const float g0 = __ldg(gain + ib);
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)
-      acc[c] = image_sample<kStride, kChecked>(zq, zp, row[c][ib], rm[c], rf[c], g0, wmax, acc[c]);
+      acc[c] = image_sample<kStride, kChecked>(zq, zp, row[c][ib], rm[c], rmc[c], rf[c], g0, wmax, acc[c]);
   }
 }
 

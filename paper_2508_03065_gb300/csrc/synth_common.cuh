@@ -135,38 +135,60 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
 
 // Interpolated delay of one image-sample split into the read position m0
 // (window column `col`, not clamped), the Farrow segment `seg` of the fraction
-// alpha and its local variable v in [-1, 1], and the delay tau in samples.
+// alpha, its local variable and the delay tau in samples.
 // With y = -phi(n) - 1/2, k = round(y) is floor(-phi) except when phi is an
 // integer, where it may be one less and alpha = 1 instead of 0: the two
 // readings give the same value because the fractional-delay kernel is
 // continuous across alpha = 0 / 1 (h(k; 1) = h(k + 1; 0)).
+// Segments: a = alpha - 1/2 in [-1/2, 1/2]; seg = round(3 a + 1) in {0, 1, 2}
+// (the same rounding constant, one FMA) and the local variable is
+// w = 3 a + 1 - seg in [-1/2, 1/2], i.e. half the v = 2 (S alpha - seg) - 1
+// of the fit: the device tables hold the coefficients of the powers of w
+// (c_q 2^q, an exact rescaling). At a segment boundary either neighbour is
+// taken (the segment polynomials agree there to the fit error).
 // rec = {I_j, psi_j, -slope_j, D_a - 1/2}; rm = r - m_lo where r = n - n_j.
+constexpr float kRound = 12582912.0f;     // 1.5 * 2^23: x + kRound rounds x to an integer
+constexpr int kRoundBits = 0x4B400000;    // bit pattern of kRound
+
 struct DelaySplit {
   int col;
   int seg;
-  float v;
+  float v;    // w in [-1/2, 1/2]
   float tau;
 };
 
 __device__ __forceinline__ DelaySplit split_delay(const int4 rec, int rm, float rf) {
   const float y = fmaf(rf, __int_as_float(rec.z), __int_as_float(rec.y));
-  const float q = y + 12582912.0f;  // round to nearest integer (1.5 * 2^23)
-  const int k = __float_as_int(q) - 0x4B400000;
-  const float a = y - (q - 12582912.0f);  // alpha - 1/2, in [-1/2, 1/2]
+  const float q = y + kRound;
+  const float a = y - (q - kRound);
+  const float q2 = fmaf(a, 3.0f, kRound + 1.0f);
   DelaySplit ds;
-  ds.col = rm + rec.x + k;
-  // three segments of alpha: seg = round(3 a + 1) in {0, 1, 2} (the same
-  // rounding constant, one FMA), v = 2 (3 alpha - seg) - 1 = 6 a + 2 - 2 seg
-  // in [-1, 1]; at a segment boundary either neighbour is taken (the
-  // segment polynomials agree there to the fit error)
-  const float q2 = fmaf(a, 3.0f, 12582913.0f);
-  ds.seg = __float_as_int(q2) - 0x4B400000;
-  ds.v = fmaf(q2 - 12582912.0f, -2.0f, fmaf(a, 6.0f, 2.0f));
-  ds.tau = __int_as_float(rec.w) - y;  // tau(n) = D_a + phi(n)
+  ds.col = rm + rec.x + (__float_as_int(q) - kRoundBits);
+  ds.seg = __float_as_int(q2) - kRoundBits;
+  ds.v = fmaf(a, 3.0f, (kRound + 1.0f) - q2);  // (kRound + 1) - q2 = 1 - seg exactly
+  ds.tau = __int_as_float(rec.w) - y;          // tau(n) = D_a + phi(n)
   return ds;
 }
 
-// Farrow polynomial (degree 5) from the powers 0..3 (A) and 4..5 (B), Horner in v.
+// The same split for a gather from a window of kStride columns per segment:
+// idx = seg * kStride + col with the rounding offsets folded into rmc, where
+// rmc = rm - kRoundBits * (1 + kStride) (mod 2^32, once per window pass).
+template <int kStride>
+__device__ __forceinline__ unsigned split_index(const int4 rec, unsigned rmc, float rf, float* w, float* tau) {
+  const float y = fmaf(rf, __int_as_float(rec.z), __int_as_float(rec.y));
+  const float q = y + kRound;
+  const float a = y - (q - kRound);
+  const float q2 = fmaf(a, 3.0f, kRound + 1.0f);
+  *w = fmaf(a, 3.0f, (kRound + 1.0f) - q2);
+  *tau = __int_as_float(rec.w) - y;
+  return unsigned(__float_as_int(q2)) * unsigned(kStride) +
+         (unsigned(__float_as_int(q)) + unsigned(rec.x) + rmc);
+}
+__device__ __forceinline__ unsigned fold_rounding(int rm, int stride) {
+  return unsigned(rm) - unsigned(kRoundBits) * (1u + unsigned(stride));
+}
+
+// Farrow polynomial (degree 5) from the powers 0..3 (A) and 4..5 (B), Horner in w.
 __device__ __forceinline__ float horner6(const float4 A, const float2 B, float v) {
   float e = fmaf(B.y, v, B.x);
   e = fmaf(e, v, A.w);
