@@ -35,8 +35,10 @@ struct msrc_room {
   int64_t n_images;
   int64_t tier_count[MSRC_MAX_TIERS];
   int kL;  // tap template length (16, 32 or 64)
-  float farrow[kFarrowSegs][kFarrowCoef][kMaxTaps];
-  double fit_error;
+  float farrow[kFarrowSegs][kFarrowCoef][kMaxTaps];    // synthesis and dx (degree 4)
+  float farrow_g[kFarrowSegs][kGradCoef][kMaxTaps];    // gradient kernel (degree 5)
+  double fit_error;                                    // of the synthesis table
+  double fit_error_g;
   bool has_traj;
   msrc_traj_desc traj;
   double mics[MSRC_MAX_MICS][3];
@@ -103,18 +105,19 @@ double kernel_fn(const msrc_room_desc& d, double u) {
 
 // Farrow coefficients (Sec. II-B, Eq. 3-4): for tap k and segment s of the
 // fractional delay alpha in [s/S, (s+1)/S), h(k; alpha) ~ sum_q c[s][q][k] v^q
-// with v = 2 (alpha S - s) - 1. Interpolation at the Chebyshev nodes of v
-// (near-minimax); the error against the exact windowed sinc is measured on a
-// dense grid with the float coefficients the device uses.
-void fit_farrow(msrc_room& R) {
+// with v = 2 (alpha S - s) - 1, q < P. Interpolation at the Chebyshev nodes of
+// v (near-minimax); returns the error against the exact windowed sinc measured
+// on a dense grid with the float coefficients the device uses. out is
+// [kFarrowSegs][P][kMaxTaps].
+double fit_farrow(const msrc_room& R, int P, float* out) {
   const int L = R.d.taps;
   const int kL = R.kL;
-  const int P = kFarrowCoef;
-  std::memset(R.farrow, 0, sizeof(R.farrow));
+  std::memset(out, 0, sizeof(float) * kFarrowSegs * P * kMaxTaps);
+  auto C = [&](int s, int q, int kk) -> float& { return out[(s * P + q) * kMaxTaps + kk]; };
   double worst = 0.0;
   for (int s = 0; s < kFarrowSegs; ++s)
     for (int k = -L / 2; k <= L / 2 - 1; ++k) {
-      double V[kFarrowCoef][kFarrowCoef + 1];
+      double V[kGradCoef][kGradCoef + 1];
       for (int i = 0; i < P; ++i) {
         const double v = std::cos(kPiD * (i + 0.5) / P);
         const double alpha = (s + 0.5 * (v + 1.0)) / kFarrowSegs;
@@ -134,22 +137,22 @@ void fit_farrow(msrc_room& R) {
           for (int c = col; c <= P; ++c) V[r][c] -= f * V[col][c];
         }
       }
-      double coef[kFarrowCoef];
+      double coef[kGradCoef];
       for (int r = P - 1; r >= 0; --r) {
         double acc = V[r][P];
         for (int c = r + 1; c < P; ++c) acc -= V[r][c] * coef[c];
         coef[r] = acc / V[r][r];
       }
-      for (int q = 0; q < P; ++q) R.farrow[s][q][k + kL / 2] = float(coef[q]);
+      for (int q = 0; q < P; ++q) C(s, q, k + kL / 2) = float(coef[q]);
       for (int g = 0; g <= 400; ++g) {
         const double v = -1.0 + 2.0 * g / 400.0;
         const double alpha = (s + 0.5 * (v + 1.0)) / kFarrowSegs;
         double e = 0.0;
-        for (int q = P - 1; q >= 0; --q) e = e * v + double(R.farrow[s][q][k + kL / 2]);
+        for (int q = P - 1; q >= 0; --q) e = e * v + double(C(s, q, k + kL / 2));
         worst = std::max(worst, std::fabs(e - kernel_fn(R.d, alpha + k)));
       }
     }
-  R.fit_error = worst;
+  return worst;
 }
 
 // ---------------------------------------------------------------- geometry
@@ -440,7 +443,9 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.off_gain = off; off = align256(off + 4 * I);
   P.off_knots = off; off = align256(off + 24 * size_t(knot_acc));
   P.off_z = off; off = align256(off + 16 * size_t(z_acc));
-  P.off_zp = off; off = align256(off + 8 * size_t(z_acc));
+  // forward: power 4 of the degree-4 rows; reverse mode: powers 4..5 of the
+  // degree-5 rows the gradient kernel reads (zq holds powers 0..3 either way)
+  P.off_zp = off; off = align256(off + (backward ? 8 : 4) * size_t(z_acc));
   if (!backward) {
     P.off_part = off; off = align256(off + 4 * size_t(part_acc));
   } else {
@@ -474,7 +479,8 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.img_gain = reinterpret_cast<float*>(ws + P.off_gain);
   a.p.knot_pos = reinterpret_cast<double*>(ws + P.off_knots);
   a.p.zq = reinterpret_cast<float4*>(ws + P.off_z);
-  a.p.zp = reinterpret_cast<float2*>(ws + P.off_zp);
+  a.p.zp = P.backward ? nullptr : reinterpret_cast<float*>(ws + P.off_zp);
+  a.p.zg = P.backward ? reinterpret_cast<float2*>(ws + P.off_zp) : nullptr;
   a.p.part = reinterpret_cast<float*>(ws + P.off_part);
   if (P.backward) {
     a.p.dxb = reinterpret_cast<float*>(ws + P.off_dxb);
@@ -489,6 +495,9 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   for (int sg = 0; sg < kFarrowSegs; ++sg)
     for (int q = 0; q < kFarrowCoef; ++q)
       for (int k = 0; k < kMaxTaps; ++k) a.farrow[sg][q][k] = std::ldexp(rooms[0]->farrow[sg][q][k], q);
+  for (int sg = 0; sg < kFarrowSegs; ++sg)
+    for (int q = 0; q < kGradCoef; ++q)
+      for (int k = 0; k < kMaxTaps; ++k) a.farrow_g[sg][q][k] = std::ldexp(rooms[0]->farrow_g[sg][q][k], q);
   a.taps = P.kL;
   if (a.n_scenes > 1) {
     char* d = ws + P.off_desc;
@@ -615,11 +624,15 @@ msrc_status msrc_create_room(const msrc_room_desc* desc, msrc_room_t* out) {
   }
   R->kL = d.taps <= 16 ? 16 : (d.taps <= 32 ? 32 : 64);
   count_tiers(*R);
-  fit_farrow(*R);
-  if (R->fit_error > 1e-6) {
+  R->fit_error = fit_farrow(*R, kFarrowCoef, &R->farrow[0][0][0]);
+  R->fit_error_g = fit_farrow(*R, kGradCoef, &R->farrow_g[0][0][0]);
+  // worst error of one tap weight; the output error is several times smaller
+  // (errors of different taps and images do not align): 4e-6 keeps it well
+  // inside the 1e-5 relative budget for every window the description admits
+  if (R->fit_error > 4e-6) {
     const double err = R->fit_error;
     delete R;
-    return fail(MSRC_ERR_UNSUPPORTED, "Farrow fit error %.3g exceeds 1e-6 for this window", err);
+    return fail(MSRC_ERR_UNSUPPORTED, "Farrow fit error %.3g exceeds 4e-6 for this window", err);
   }
   *out = R;
   return MSRC_OK;

@@ -45,16 +45,18 @@ constexpr int kBwTile = kBwThreads * kBwChunks;
 constexpr int kBwRecCap = 3328;                 // records (image x interval)
 constexpr int kBwUnitCap = 3584;                // unit vectors (image x knot)
 constexpr int kBwBlock = 256;                   // images per block at most
-constexpr int kGradWcap = 1536;                 // shared z window of the gradient kernel
+constexpr int kGradWcap = 1408;                 // shared z window of the gradient kernel
 constexpr int kDxWcap = 1792;                   // shared w window of the dx kernel
 constexpr int kSegCap = 33;                     // knot intervals touched by 32 consecutive samples
 
 constexpr size_t kGradSmem = size_t(kFarrowSegs) * kGradWcap * (sizeof(float4) + sizeof(float2)) +
-                             size_t(kBwRecCap) * sizeof(int4) + size_t(kBwUnitCap) * sizeof(float4) +
-                             size_t(2 * kBwBlock) * sizeof(float4);
+                             size_t(kBwRecCap) * sizeof(float2) + size_t(kBwBlock) * sizeof(int4) +
+                             size_t(kBwUnitCap) * sizeof(float4) + size_t(2 * kBwBlock) * sizeof(float4);
 constexpr int kDxGroupImages = 256;             // images per dx item (block group), about
-constexpr size_t kDxSmem = size_t(kFarrowSegs) * kDxWcap * (sizeof(float4) + sizeof(float2)) +
-                           size_t(kBwRecCap) * sizeof(int4) + size_t(kBwTile + 4 + 2 * kBwBlock) * sizeof(float4);
+constexpr size_t kDxSmem = size_t(kFarrowSegs) * kDxWcap * (sizeof(float4) + sizeof(float)) +
+                           size_t(kBwRecCap) * sizeof(float2) + size_t(kBwBlock) * sizeof(int4) +
+                           size_t(kBwTile + 4 + 2 * kBwBlock) * sizeof(float4);
+static_assert(kBwRecCap % 2 == 0, "16-byte alignment of the image records");
 static_assert(kGradSmem <= 232448 && kDxSmem <= 232448, "shared memory per CTA");
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -140,9 +142,10 @@ __device__ __forceinline__ void window_of(float tmin, float tmax, const ItemGeom
 __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constant__ KernelArgs a) {
   extern __shared__ __align__(16) float4 sm[];
   float4* zq_s = sm;                                                    // kFarrowSegs x kGradWcap
-  float2* zp_s = reinterpret_cast<float2*>(zq_s + kFarrowSegs * kGradWcap);
-  int4* rec_s = reinterpret_cast<int4*>(zp_s + kFarrowSegs * kGradWcap);
-  float4* unit_s = reinterpret_cast<float4*>(rec_s + kBwRecCap);       // [image][knot]
+  float2* zp_s = reinterpret_cast<float2*>(zq_s + kFarrowSegs * kGradWcap);  // powers 4..5
+  float2* rec_s = zp_s + kFarrowSegs * kGradWcap;
+  int4* img_s = reinterpret_cast<int4*>(rec_s + kBwRecCap);
+  float4* unit_s = reinterpret_cast<float4*>(img_s + kBwBlock);        // [image][knot]
   float4* bw_s = unit_s + kBwUnitCap;                                   // 2 per image
   float4* u_s = sm;                                                     // prologue scratch
   float4* anc_s = sm + kBwTile + 4;
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     const float fsc = S.fsc;
 
     float tmin, tmax;
-    item_records<kBwThreads>(a, S, g, rec_s, u_s, anc_s, &tmin, &tmax);
+    item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, anc_s, &tmin, &tmax);
     // unit vectors (sigma o Delta) / d of every image at every knot of the tile
     for (int pidx = threadIdx.x; pidx < g.cnt * g.nk; pidx += kBwThreads) {
       const int ib = pidx / g.nk, jj = pidx - ib * g.nk;
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     }
     float bacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const float4* zqg = a.p.zq + S.z_base;
-    const float2* zpg = a.p.zp + S.z_base;
+    const float2* zpg = a.p.zg + S.z_base;
 
     for (int p0 = 0; p0 < width; p0 += kGradWcap) {
       const int pass_lo = m_lo + p0;
@@ -225,17 +228,21 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
       }
       cp_async_wait_all();
       __syncthreads();
+      int rmj[kBwChunks];
+#pragma unroll
+      for (int c = 0; c < kBwChunks; ++c) rmj[c] = rr[c] - pass_lo + jc[c] * g.N;
       for (int ib = 0; ib < g.cnt; ++ib) {
         const float4 B0 = bw_s[2 * ib], B1 = bw_s[2 * ib + 1];
+        const int4 im = img_s[ib];
 #pragma unroll
         for (int c = 0; c < kBwChunks; ++c) {
-          const DelaySplit ds = split_delay(rec_s[jc[c] * g.cnt + ib], rr[c] - pass_lo, rf[c]);
+          const DelaySplit ds = split_delay(rec_s[jc[c] * g.cnt + ib], rmj[c] + im.x, rf[c], __int_as_float(im.y));
           if (!valid[c] || unsigned(ds.col) >= unsigned(pw)) continue;
           const int idx = ds.seg * kGradWcap + ds.col;
           const float4 A = zq_s[idx];
           const float2 Bz = zp_s[idx];
-          const float v = ds.v;
-          float pe = Bz.y, pd = 0.0f;  // e = P(v) and dP/dv together (Horner)
+          const float v = ds.w;
+          float pe = Bz.y, pd = 0.0f;  // e = P(w) and dP/dw together (Horner, degree 5)
           pd = fmaf(pd, v, pe); pe = fmaf(pe, v, Bz.x);
           pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.w);
           pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.z);
@@ -333,9 +340,10 @@ template <int kL>
 __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant__ KernelArgs a) {
   extern __shared__ __align__(16) float4 sm[];
   float4* wq_s = sm;                                                       // kFarrowSegs x kDxWcap (powers 0..3)
-  float2* wp_s = reinterpret_cast<float2*>(wq_s + kFarrowSegs * kDxWcap);  // powers 4..5
-  int4* rec_s = reinterpret_cast<int4*>(wp_s + kFarrowSegs * kDxWcap);
-  float4* u_s = reinterpret_cast<float4*>(rec_s + kBwRecCap);             // record scratch
+  float* wp_s = reinterpret_cast<float*>(wq_s + kFarrowSegs * kDxWcap);    // power 4
+  float2* rec_s = reinterpret_cast<float2*>(wp_s + kFarrowSegs * kDxWcap);
+  int4* img_s = reinterpret_cast<int4*>(rec_s + kBwRecCap);
+  float4* u_s = reinterpret_cast<float4*>(img_s + kBwBlock);              // record scratch
   float4* anc_s = u_s + kBwTile + 4;
   __shared__ int s_item;
   __shared__ float s_red[2][kBwThreads / 32];
@@ -371,7 +379,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
         __syncthreads();  // records of the previous block / tile are no longer read
         const ItemGeom g = item_geometry(S, (item0 + b) * S.n_tiles + tile, kBwTile);
         float lo, hi;
-        item_records<kBwThreads>(a, S, g, rec_s, u_s, anc_s, &lo, &hi);
+        item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, anc_s, &lo, &hi);
         tmin = fminf(tmin, lo);
         tmax = fmaxf(tmax, hi);
       }
@@ -399,33 +407,34 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
         __syncthreads();  // the previous pass's correlation is done with the window
         for (int i = threadIdx.x; i < kFarrowSegs * kDxWcap; i += kBwThreads) {
           wq_s[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-          wp_s[i] = make_float2(0.f, 0.f);
+          wp_s[i] = 0.f;
         }
+        int rmj[kBwChunks];
+#pragma unroll
+        for (int c = 0; c < kBwChunks; ++c) rmj[c] = rr[c] - pass_lo + jc[c] * g0.N;
         for (int b = b0; b < b1; ++b) {
           const ItemGeom g = item_geometry(S, (item0 + b) * S.n_tiles + tile, kBwTile);
           if (!reuse) {
             float lo, hi;
             __syncthreads();  // the previous block's records are no longer read
-            item_records<kBwThreads>(a, S, g, rec_s, u_s, anc_s, &lo, &hi);
+            item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, anc_s, &lo, &hi);
           }
           __syncthreads();  // records and the zeroed window are complete
-          const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
           for (int ib = 0; ib < g.cnt; ++ib) {
-            const float gi = __ldg(gain + ib);
+            const int4 im = img_s[ib];
+            const float gi = __int_as_float(im.z);
 #pragma unroll
             for (int c = 0; c < kBwChunks; ++c) {
-              const DelaySplit ds = split_delay(rec_s[jc[c] * g.cnt + ib], rr[c] - pass_lo, rf[c]);
+              const DelaySplit ds = split_delay(rec_s[jc[c] * g.cnt + ib], rmj[c] + im.x, rf[c], __int_as_float(im.y));
               if (dyv[c] == 0.0f || unsigned(ds.col) >= unsigned(pw)) continue;
               const float val = dyv[c] * __fdividef(gi, ds.tau);  // dy g
-              const float v = ds.v;
-              const float p1 = val * v, p2 = p1 * v, p3 = p2 * v, p4 = p3 * v, p5 = p4 * v;
+              const float v = ds.w;
+              const float p1 = val * v, p2 = p1 * v, p3 = p2 * v, p4 = p3 * v;
               const int idx = ds.seg * kDxWcap + ds.col;
               float4 wa = wq_s[idx];
-              float2 wb = wp_s[idx];
               wa.x += val; wa.y += p1; wa.z += p2; wa.w += p3;
-              wb.x += p4; wb.y += p5;
               wq_s[idx] = wa;
-              wp_s[idx] = wb;
+              wp_s[idx] += p4;
             }
             __syncthreads();  // the next image may write the same bins
           }
@@ -445,9 +454,8 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
 #pragma unroll
             for (int sg = 0; sg < kFarrowSegs; ++sg) {
               const float4 w4 = wq_s[sg * kDxWcap + cc];
-              const float2 w2 = wp_s[sg * kDxWcap + cc];
               float* o = wv + sg * kFarrowCoef;
-              o[0] = w4.x; o[1] = w4.y; o[2] = w4.z; o[3] = w4.w; o[4] = w2.x; o[5] = w2.y;
+              o[0] = w4.x; o[1] = w4.y; o[2] = w4.z; o[3] = w4.w; o[4] = wp_s[sg * kDxWcap + cc];
             }
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
@@ -665,10 +673,10 @@ const TileConfig& backward_tile_config() { return kBwConfig; }
 size_t backward_unit_cap() { return kBwUnitCap; }
 int backward_group_images() { return kDxGroupImages; }
 
-cudaError_t launch_prefilter(const KernelArgs& a, cudaStream_t st);
+cudaError_t launch_prefilter(const KernelArgs& a, cudaStream_t st, bool gradient_rows);
 
 cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
-  cudaError_t e = launch_prefilter(a, st);
+  cudaError_t e = launch_prefilter(a, st, true);
   if (e != cudaSuccess) return e;
   static int g_grad = 0, g_dx16 = 0, g_dx32 = 0, g_dx64 = 0;
   if (a.totals[0] > 0) k_beta_table<<<unsigned((a.totals[0] + 255) / 256), 256, 0, st>>>(a);

@@ -28,8 +28,12 @@ namespace {
 // ------------------------------------------------------------------ prefilter
 constexpr int kPreThreads = 256;
 
-template <int kL>
+// kCoef = kFarrowCoef: the synthesis rows (degree 4, zq + zp); kCoef =
+// kGradCoef: the gradient kernel's rows (degree 5, zq + zg).
+template <int kL, int kCoef>
 __global__ void __launch_bounds__(kPreThreads) k_prefilter(const __grid_constant__ KernelArgs a) {
+  static_assert(kCoef == kFarrowCoef || kCoef == kGradCoef, "row sets");
+  constexpr int kRows = kFarrowSegs * kCoef;
   __shared__ float xs[kPreThreads + kL];
   int s = 0;
   int64_t blk = blockIdx.x;
@@ -50,23 +54,26 @@ __global__ void __launch_bounds__(kPreThreads) k_prefilter(const __grid_constant
   const int64_t col = blk * kPreThreads + threadIdx.x;
   if (col >= S.z_len) return;
   // xs index of x[m - k] is (threadIdx.x - k) + kL/2 - 1
-  float acc[kZRows];
+  float acc[kRows];
 #pragma unroll
-  for (int r = 0; r < kZRows; ++r) acc[r] = 0.0f;
+  for (int r = 0; r < kRows; ++r) acc[r] = 0.0f;
 #pragma unroll
   for (int kk = 0; kk < kL; ++kk) {  // kk = k + kL/2
     const float xv = xs[threadIdx.x - kk + kL - 1];
 #pragma unroll
-    for (int r = 0; r < kZRows; ++r)
-      acc[r] = fmaf(a.farrow[r / kFarrowCoef][r % kFarrowCoef][kk], xv, acc[r]);
+    for (int r = 0; r < kRows; ++r) {
+      const float c = kCoef == kFarrowCoef ? a.farrow[r / kCoef][r % kCoef][kk]
+                                           : a.farrow_g[r / kCoef][r % kCoef][kk];
+      acc[r] = fmaf(c, xv, acc[r]);
+    }
   }
   float4* zq = a.p.zq + S.z_base + col;
-  float2* zp = a.p.zp + S.z_base + col;
 #pragma unroll
   for (int sg = 0; sg < kFarrowSegs; ++sg) {
-    const float* c = acc + sg * kFarrowCoef;
+    const float* c = acc + sg * kCoef;
     zq[int64_t(sg) * S.z_len] = make_float4(c[0], c[1], c[2], c[3]);
-    zp[int64_t(sg) * S.z_len] = make_float2(c[4], c[5]);
+    if constexpr (kCoef == kFarrowCoef) a.p.zp[S.z_base + col + int64_t(sg) * S.z_len] = c[4];
+    else a.p.zg[S.z_base + col + int64_t(sg) * S.z_len] = make_float2(c[4], c[kCoef - 1]);
   }
 }
 
@@ -75,66 +82,67 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 // acc + (beta_i / (4 pi d_i(n))) e_i(n) for one image-sample read from the
-// staged window (row stride kStride). gain = beta_i / (4 pi) * fs / c (the
-// image table stores it so), so the gain is gain / tau with tau in samples. kChecked: the window is
-// processed in several column passes and only columns inside this pass count.
-// One image-sample: kChecked skips read positions outside the pass's columns
-// (windows wider than one pass); otherwise every position lies inside the
-// window by construction and the index is only clamped to the window arrays.
+// staged window (kStride columns per segment). The gain of the image record is
+// beta_i / (4 pi) * fs / c, so the gain at n is gain / tau with tau in samples.
+// kChecked: the window is processed in several column passes and only columns
+// inside this pass count; otherwise every read position lies inside the window
+// by construction and the index is only clamped to the window arrays.
 template <int kStride, bool kChecked>
-__device__ __forceinline__ float image_sample(const float4* zq, const float2* zp, const int4 rec, int rm,
-                                              unsigned rmc, float rf, float gain, unsigned wmax, float acc) {
+__device__ __forceinline__ float image_sample(const float4* zq, const float* zp, const float2 rec, const int4 im,
+                                              int rmj, unsigned rmc, float rf, unsigned wmax, float acc) {
+  const float Dp = __int_as_float(im.y);
   float w, tau;
   unsigned idx;
   if (kChecked) {
-    const DelaySplit ds = split_delay(rec, rm, rf);
+    const DelaySplit ds = split_delay(rec, rmj + im.x, rf, Dp);
     if (unsigned(ds.col) > wmax) return acc;
     idx = unsigned(ds.seg * kStride + ds.col);
-    w = ds.v;
+    w = ds.w;
     tau = ds.tau;
   } else {
-    idx = min(split_index<kStride>(rec, rmc, rf, &w, &tau), unsigned(kFarrowSegs * kStride - 1));
+    idx = min(split_index<kStride>(rec, im.x, rmc, rf, Dp, &w, &tau), unsigned(kFarrowSegs * kStride - 1));
   }
-  const float e = horner6(zq[idx], zp[idx], w);
-  return fmaf(__fdividef(gain, tau), e, acc);
+  const float e = horner5(zq[idx], zp[idx], w);
+  return fmaf(__fdividef(__int_as_float(im.z), tau), e, acc);
 }
 
+// All images of the block for this thread's kChunks samples; rmj[c] =
+// r - m_lo + jj N_t of chunk c (its interval jj = jc[c]).
 template <int kStride, int kChunks, int kUnroll, bool kChecked>
-__device__ __forceinline__ void gather_images(const float4* zq, const float2* zp, const int4* rec_s,
-                                              const float* gain, int cnt, const int* jc, const int* rm,
+__device__ __forceinline__ void gather_images(const float4* zq, const float* zp, const float2* rec_s,
+                                              const int4* img_s, int cnt, const int* jc, const int* rmj,
                                               const float* rf, unsigned wmax, float* acc) {
   unsigned rmc[kChunks];
+  const float2* row[kChunks];  // records of chunk c: row jc[c] of the interval-major table
 #pragma unroll
-  for (int c = 0; c < kChunks; ++c) rmc[c] = fold_rounding(rm[c], kStride);
-  // records of chunk c: row jc[c] of the interval-major table, one entry per image
-  const int4* row[kChunks];
-#pragma unroll
-  for (int c = 0; c < kChunks; ++c) row[c] = rec_s + jc[c] * cnt;
+  for (int c = 0; c < kChunks; ++c) {
+    rmc[c] = fold_rounding(rmj[c]);
+    row[c] = rec_s + jc[c] * cnt;
+  }
   int ib = 0;
   for (; ib + kUnroll <= cnt; ib += kUnroll) {
-    float gg[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) gg[u] = __ldg(gain + ib + u);
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
+    for (int u = 0; u < kUnroll; ++u) {
+      const int4 im = img_s[ib + u];
 #pragma unroll
       for (int c = 0; c < kChunks; ++c)
-        acc[c] = image_sample<kStride, kChecked>(zq, zp, row[c][ib + u], rm[c], rmc[c], rf[c], gg[u], wmax, acc[c]);
+        acc[c] = image_sample<kStride, kChecked>(zq, zp, row[c][ib + u], im, rmj[c], rmc[c], rf[c], wmax, acc[c]);
+    }
   }
   for (; ib < cnt; ++ib) {
-    const float g0 = __ldg(gain + ib);
+    const int4 im = img_s[ib];
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)
-      acc[c] = image_sample<kStride, kChecked>(zq, zp, row[c][ib], rm[c], rmc[c], rf[c], g0, wmax, acc[c]);
+      acc[c] = image_sample<kStride, kChecked>(zq, zp, row[c][ib], im, rmj[c], rmc[c], rf[c], wmax, acc[c]);
   }
 }
 
@@ -142,8 +150,10 @@ template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock, int kUn
 __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(const __grid_constant__ KernelArgs a) {
   extern __shared__ __align__(16) float4 smem4[];
   float4* zq_s = smem4;                                                  // kFarrowSegs x kWcap
-  float2* zp_s = reinterpret_cast<float2*>(smem4 + kFarrowSegs * kWcap);  // kFarrowSegs x kWcap
-  int4* rec_s = reinterpret_cast<int4*>(zp_s + kFarrowSegs * kWcap);     // kRecCap records
+  float* zp_s = reinterpret_cast<float*>(smem4 + kFarrowSegs * kWcap);    // kFarrowSegs x kWcap
+  float2* rec_s = reinterpret_cast<float2*>(zp_s + kFarrowSegs * kWcap);  // kRecCap interval records
+  int4* img_s = reinterpret_cast<int4*>(rec_s + kRecCap);                 // kBlock image records
+  static_assert(kRecCap % 2 == 0, "16-byte alignment of the image records");
   // prologue scratch aliases the z window (used before the window is staged)
   float4* u_s = smem4;
   float4* anc_s = u_s + kThreads * kChunks + 4;                          // 2 x kBlock
@@ -170,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
 
     // --- delay knots of the block over the tile (records in shared memory)
     float tmin, tmax;
-    item_records<kThreads>(a, S, g, rec_s, u_s, anc_s, &tmin, &tmax);
+    item_records<kThreads>(a, S, g, rec_s, img_s, u_s, anc_s, &tmin, &tmax);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
@@ -189,7 +199,7 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
     const int width = g.n_end - int(floorf(tmin)) + 2 - m_lo + 1;
 
     // this thread's samples: warp w owns n0 + 32 (w kChunks + c) + lane
-    int jc[kChunks], rr[kChunks], rm[kChunks];
+    int jc[kChunks], rr[kChunks], rmj[kChunks];
     float rf[kChunks], acc[kChunks];
     bool valid[kChunks];
 #pragma unroll
@@ -203,9 +213,8 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       rf[c] = float(rr[c]);
       acc[c] = 0.0f;
     }
-    const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
     const float4* zqg = a.p.zq + S.z_base;
-    const float2* zpg = a.p.zp + S.z_base;
+    const float* zpg = a.p.zp + S.z_base;
 
     // --- the window [m_lo, m_lo + width) in passes of at most kWcap columns
     for (int p0 = 0; p0 < width; p0 += kWcap) {
@@ -222,17 +231,17 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       for (int i = threadIdx.x; i < kFarrowSegs * cnt_c; i += kThreads) {
         const int sg = i / cnt_c, c = i - sg * cnt_c;
         cp_async16(zq_s + sg * kWcap + dst0 + c, zqg + int64_t(sg) * S.z_len + src0 + c);
-        cp_async8(zp_s + sg * kWcap + dst0 + c, zpg + int64_t(sg) * S.z_len + src0 + c);
+        cp_async4(zp_s + sg * kWcap + dst0 + c, zpg + int64_t(sg) * S.z_len + src0 + c);
       }
       cp_async_wait_all();
       __syncthreads();
 #pragma unroll
-      for (int c = 0; c < kChunks; ++c) rm[c] = rr[c] - pass_lo;
+      for (int c = 0; c < kChunks; ++c) rmj[c] = rr[c] - pass_lo + jc[c] * g.N;
       const unsigned wmax = unsigned(pw - 1);
       if (width <= kWcap)
-        gather_images<kWcap, kChunks, kUnroll, false>(zq_s, zp_s, rec_s, gain, g.cnt, jc, rm, rf, wmax, acc);
+        gather_images<kWcap, kChunks, kUnroll, false>(zq_s, zp_s, rec_s, img_s, g.cnt, jc, rmj, rf, wmax, acc);
       else
-        gather_images<kWcap, kChunks, kUnroll, true>(zq_s, zp_s, rec_s, gain, g.cnt, jc, rm, rf, wmax, acc);
+        gather_images<kWcap, kChunks, kUnroll, true>(zq_s, zp_s, rec_s, img_s, g.cnt, jc, rmj, rf, wmax, acc);
     }
     float* out = a.p.part + S.part_base + (int64_t(g.mic) * S.n_blocks + g.blk) * S.n_out;
 #pragma unroll
@@ -266,8 +275,8 @@ __global__ void k_reduce(const __grid_constant__ KernelArgs a) {
 template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock, int kUnroll>
 cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
   auto kern = k_synth<kThreads, kChunks, kWcap, kRecCap, kBlock, kUnroll>;
-  const size_t smem = size_t(kFarrowSegs) * kWcap * (sizeof(float4) + sizeof(float2)) +
-                      size_t(kRecCap) * sizeof(int4);
+  const size_t smem = size_t(kFarrowSegs) * kWcap * (sizeof(float4) + sizeof(float)) +
+                      size_t(kRecCap) * sizeof(float2) + size_t(kBlock) * sizeof(int4);
   static int grid = 0;
   if (grid == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -291,12 +300,12 @@ cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
 
 // Tile configurations of the synthesis launch (see TileConfig).
 #define MSRC_TILE_CONFIGS(X)             \
-  X(0, 512, 2, 2432, 3328, 256, 8)       \
+  X(0, 512, 2, 2432, 4096, 256, 8)       \
   X(1, 256, 2, 1152, 1664, 256, 4)       \
   X(2, 384, 2, 2048, 3072, 256, 4)       \
-  X(3, 1024, 1, 2432, 3328, 256, 2)      \
-  X(4, 512, 2, 2432, 3328, 256, 4)       \
-  X(5, 512, 1, 2432, 3328, 256, 8)
+  X(3, 1024, 1, 2432, 4096, 256, 2)      \
+  X(4, 512, 2, 2432, 4096, 256, 4)       \
+  X(5, 512, 1, 2432, 4096, 256, 8)
 
 static const TileConfig kConfigs[] = {
 #define MSRC_ROW(id, th, ch, wc, rc, bl, un) {th, ch, wc, rc, bl},
@@ -307,19 +316,25 @@ static const TileConfig kConfigs[] = {
 int tile_config_count() { return int(sizeof(kConfigs) / sizeof(kConfigs[0])); }
 const TileConfig& tile_config(int cfg) { return kConfigs[cfg]; }
 
-cudaError_t launch_prefilter(const KernelArgs& a, cudaStream_t st) {
+cudaError_t launch_prefilter(const KernelArgs& a, cudaStream_t st, bool gradient_rows) {
   if (a.totals[3] > 0) {
     const unsigned g = unsigned(a.totals[3]);
-    if (a.taps <= 16) k_prefilter<16><<<g, kPreThreads, 0, st>>>(a);
-    else if (a.taps <= 32) k_prefilter<32><<<g, kPreThreads, 0, st>>>(a);
-    else k_prefilter<64><<<g, kPreThreads, 0, st>>>(a);
+    if (gradient_rows) {
+      if (a.taps <= 16) k_prefilter<16, kGradCoef><<<g, kPreThreads, 0, st>>>(a);
+      else if (a.taps <= 32) k_prefilter<32, kGradCoef><<<g, kPreThreads, 0, st>>>(a);
+      else k_prefilter<64, kGradCoef><<<g, kPreThreads, 0, st>>>(a);
+    } else {
+      if (a.taps <= 16) k_prefilter<16, kFarrowCoef><<<g, kPreThreads, 0, st>>>(a);
+      else if (a.taps <= 32) k_prefilter<32, kFarrowCoef><<<g, kPreThreads, 0, st>>>(a);
+      else k_prefilter<64, kFarrowCoef><<<g, kPreThreads, 0, st>>>(a);
+    }
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_forward(const KernelArgs& a, int cfg, cudaStream_t st, cudaEvent_t* ev) {
   const int T = 256;
-  cudaError_t pe = launch_prefilter(a, st);
+  cudaError_t pe = launch_prefilter(a, st, false);
   if (pe != cudaSuccess) return pe;
   if (ev) cudaEventRecord(ev[0], st);
   cudaError_t e = cudaSuccess;

@@ -12,17 +12,22 @@
 namespace msrc {
 
 // Signal-side Farrow structure (Sec. II-B, Eq. 5): the tap weight of tap k is a
-// degree-kFarrowDeg polynomial in a local variable v of the fractional delay,
+// degree-kFarrowDeg polynomial in a local variable of the fractional delay,
 // piecewise over kFarrowSegs segments of [0, 1). The prefilter produces one
 // signal row per (segment, power): z[s][q][m] = sum_k c[s][q][k] x[m - k],
-// stored per segment as a float4 row (powers 0..3) and a float2 row (powers
-// 4..5), so that one image-sample gathers its 6 values with a 16-byte and an
-// 8-byte load.
-constexpr int kFarrowSegs = 3;
-constexpr int kFarrowDeg = 5;
+// stored per segment as a float4 row (powers 0..3) and a float row (power 4),
+// so that one image-sample gathers its 5 values with a 16-byte and a 4-byte
+// load (5 shared-memory wavefronts per warp).
+constexpr int kFarrowSegs = 4;
+constexpr int kFarrowDeg = 4;
 constexpr int kFarrowCoef = kFarrowDeg + 1;
 constexpr int kZRows = kFarrowSegs * kFarrowCoef;
-static_assert(kFarrowCoef == 6 && kFarrowSegs == 3, "row layout assumes 3 segments x 6 coefficients");
+static_assert(kFarrowCoef == 5 && kFarrowSegs == 4, "row layout assumes 4 segments x 5 coefficients");
+// The gradient kernel needs de/dalpha, whose error grows with the degree of
+// the fit's derivative; it reads its own rows of a degree-5 fit on the same
+// segments (float4 row for powers 0..3, float2 row for powers 4..5).
+constexpr int kGradCoef = 6;
+constexpr int kGradRows = kFarrowSegs * kGradCoef;
 constexpr int kMaxTaps = 64;
 constexpr int kMaxScenesInline = 1;
 
@@ -118,7 +123,8 @@ struct DevicePtrs {
   float* img_gain;               // beta_i / (4 pi)
   double* knot_pos;              // s(t_j), 3 doubles per knot
   float4* zq;                    // prefiltered powers 0..3, [scene rows][segment][column]
-  float2* zp;                    // prefiltered powers 4..5, same indexing
+  float* zp;                     // prefiltered power 4, same indexing
+  float2* zg;                    // reverse mode: powers 4..5 of the degree-5 rows (zq holds 0..3)
   float* part;                   // partial sums
   // reverse mode
   float* dxb;                    // dx rows per (scene, mic, block group, range parity)
@@ -138,7 +144,8 @@ struct KernelArgs {
   int64_t totals[6];             // total units per kernel kind (enum, knots, rec, z, item, red)
   LaunchTables tab;
   DevicePtrs p;
-  float farrow[kFarrowSegs][kFarrowCoef][kMaxTaps];  // coefficients c[s][q][k + L/2]
+  float farrow[kFarrowSegs][kFarrowCoef][kMaxTaps];  // coefficients c[s][q][k + L/2] of the powers of w
+  float farrow_g[kFarrowSegs][kGradCoef][kMaxTaps];  // degree-5 coefficients (gradient kernel)
   int32_t taps;
 };
 

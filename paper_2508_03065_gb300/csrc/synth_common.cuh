@@ -75,17 +75,21 @@ __device__ __forceinline__ void knot_increment(const float4 A, const float4 U, f
   *d = A.w + dd;
 }
 
-// Records of the item's images over its intervals, in shared memory
-// (interval-major, so that consecutive images of one interval are adjacent):
-//   rec_s[jj * cnt + ib] = {I_j = n_j - D_a, psi_j = -phi_j - 1/2,
-//                                -(phi_{j+1} - phi_j) / N_t, D_a - 1/2},  j = jf + jj,
-// where tau = d fs / c, D_a = floor(tau) at the anchor knot jf (FP64) and
-// phi_j = tau_j - D_a. u_s (nk entries) and anc_s (2 * cnt entries) are
-// scratch. Returns this thread's min / max of tau over its knots (window
-// bounds of the item).
+// Records of the item's images over its intervals, in shared memory.
+// With tau = d fs / c, D_a = floor(tau) at the anchor knot jf (FP64) and
+// phi_j = tau_j - D_a, the delay between knots j and j + 1 is
+// tau(n) = D_a + phi_j + (phi_{j+1} - phi_j) r / N_t (r = n - n_j). Stored:
+//   rec_s[jj * cnt + ib] = {Psi_j = -S phi_j - 1/2, sigma_j = -S (phi_{j+1} - phi_j) / N_t}
+//                          (float2, interval-major so that consecutive images of one
+//                          interval are adjacent; j = jf + jj; S = kFarrowSegs),
+//   img_s[ib]            = {I = n_jf - D_a, D_a - 1/(2S) (float), gain (float), 0}
+// so that Y(n) = Psi_j + sigma_j r = S (n - tau(n) - n_j + I + jj N_t) - 1/2 up to
+// the integer read position, and tau(n) = (D_a - 1/(2S)) - Y / S.
+// u_s (nk entries) and anc_s (2 * cnt entries) are scratch. Returns this
+// thread's min / max of tau over its knots (window bounds of the item).
 template <int kThreads>
-__device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, int4* rec_s,
-                             float4* u_s, float4* anc_s, float* tmin_out, float* tmax_out) {
+__device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
+                             int4* img_s, float4* u_s, float4* anc_s, float* tmin_out, float* tmax_out) {
   const double* kp = a.p.knot_pos + 3 * (S.knot_base[g.t] + g.jf);
   const double sa0 = kp[0], sa1 = kp[1], sa2 = kp[2];
   for (int jj = threadIdx.x; jj < g.nk; jj += kThreads) {
@@ -96,6 +100,7 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
   }
   const double fs_c = S.fs_over_c;
   const uint32_t* codes = a.p.img_code + S.img_base + S.tier_first[g.t] + g.img0;
+  const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
   const double* mic = S.mics[g.mic];
   for (int ib = threadIdx.x; ib < g.cnt; ib += kThreads) {
     int n[3], p[3];
@@ -108,11 +113,13 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     const double tau = da * fs_c;
     const double Dfl = floor(tau);
     anc_s[2 * ib] = make_float4(float(s0 * D0), float(s1 * D1), float(s2 * D2), float(da));
-    anc_s[2 * ib + 1] = make_float4(float(tau - Dfl), __int_as_float(g.jf * g.N - int(Dfl)), float(Dfl), 0.0f);
+    anc_s[2 * ib + 1] = make_float4(float(tau - Dfl), float(Dfl), 0.0f, 0.0f);
+    img_s[ib] = make_int4(g.jf * g.N - int(Dfl), __float_as_int(float(Dfl) - 0.5f / kFarrowSegs),
+                          __float_as_int(__ldg(gain + ib)), 0);
   }
   __syncthreads();
   const float fsc = S.fsc;
-  const float invN = 1.0f / float(g.N);
+  const float sN = float(kFarrowSegs) / float(g.N);
   const int nrec = g.nk - 1;
   const int total = g.cnt * nrec;
   float tmin = 3.0e38f, tmax = -3.0e38f;
@@ -124,10 +131,9 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     float phi0, phi1, d0, d1;
     knot_increment(A, u_s[jj], fsc, A2.x, &phi0, &d0);
     knot_increment(A, u_s[jj + 1], fsc, A2.x, &phi1, &d1);
-    rec_s[jj * g.cnt + ib] = make_int4(__float_as_int(A2.y) + jj * g.N, __float_as_int(-phi0 - 0.5f),
-                            __float_as_int((phi0 - phi1) * invN), __float_as_int(A2.z - 0.5f));
-    tmin = fminf(tmin, A2.z + fminf(phi0, phi1));
-    tmax = fmaxf(tmax, A2.z + fmaxf(phi0, phi1));
+    rec_s[jj * g.cnt + ib] = make_float2(fmaf(-float(kFarrowSegs), phi0, -0.5f), (phi0 - phi1) * sN);
+    tmin = fminf(tmin, A2.y + fminf(phi0, phi1));
+    tmax = fmaxf(tmax, A2.y + fmaxf(phi0, phi1));
   }
   *tmin_out = tmin;
   *tmax_out = tmax;
@@ -135,66 +141,63 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
 
 // Interpolated delay of one image-sample split into the read position m0
 // (window column `col`, not clamped), the Farrow segment `seg` of the fraction
-// alpha, its local variable and the delay tau in samples.
-// With y = -phi(n) - 1/2, k = round(y) is floor(-phi) except when phi is an
-// integer, where it may be one less and alpha = 1 instead of 0: the two
-// readings give the same value because the fractional-delay kernel is
-// continuous across alpha = 0 / 1 (h(k; 1) = h(k + 1; 0)).
-// Segments: a = alpha - 1/2 in [-1/2, 1/2]; seg = round(3 a + 1) in {0, 1, 2}
-// (the same rounding constant, one FMA) and the local variable is
-// w = 3 a + 1 - seg in [-1/2, 1/2], i.e. half the v = 2 (S alpha - seg) - 1
-// of the fit: the device tables hold the coefficients of the powers of w
-// (c_q 2^q, an exact rescaling). At a segment boundary either neighbour is
-// taken (the segment polynomials agree there to the fit error).
-// rec = {I_j, psi_j, -slope_j, D_a - 1/2}; rm = r - m_lo where r = n - n_j.
+// alpha, its local variable w and the delay tau in samples.
+// With p = n - tau(n) the read position, Y = S p - 1/2 (relative to an integer
+// offset), one rounding R = round(Y) gives m0 = floor(R / S) and seg = R mod S
+// (S = 4, shifts and masks), and w = Y - R = S alpha - seg - 1/2 in [-1/2, 1/2]
+// is half the v = 2 (S alpha - seg) - 1 of the fit: the device tables hold the
+// coefficients of the powers of w (c_q 2^q, an exact rescaling). At a segment
+// boundary either neighbour is taken, and alpha = 1 reads as alpha = 0 at
+// m0 + 1: the pieces agree there to the fit error (the fractional-delay kernel
+// is continuous, h(k; 1) = h(k + 1; 0)).
+// rec = {Psi_j, sigma_j}; rmI = r - m_lo + I + jj N_t (r = n - n_j); Dp = img.y.
 constexpr float kRound = 12582912.0f;     // 1.5 * 2^23: x + kRound rounds x to an integer
 constexpr int kRoundBits = 0x4B400000;    // bit pattern of kRound
+static_assert(kFarrowSegs == 4, "the segment split uses R mod 4 and R / 4");
+static_assert((kRoundBits & 3) == 0, "kRound bits divisible by the segment count");
 
 struct DelaySplit {
   int col;
   int seg;
-  float v;    // w in [-1/2, 1/2]
+  float w;
   float tau;
 };
 
-__device__ __forceinline__ DelaySplit split_delay(const int4 rec, int rm, float rf) {
-  const float y = fmaf(rf, __int_as_float(rec.z), __int_as_float(rec.y));
-  const float q = y + kRound;
-  const float a = y - (q - kRound);
-  const float q2 = fmaf(a, 3.0f, kRound + 1.0f);
+__device__ __forceinline__ DelaySplit split_delay(const float2 rec, int rmI, float rf, float Dp) {
+  const float Y = fmaf(rf, rec.y, rec.x);
+  const float q = Y + kRound;
+  const int b = __float_as_int(q);
   DelaySplit ds;
-  ds.col = rm + rec.x + (__float_as_int(q) - kRoundBits);
-  ds.seg = __float_as_int(q2) - kRoundBits;
-  ds.v = fmaf(a, 3.0f, (kRound + 1.0f) - q2);  // (kRound + 1) - q2 = 1 - seg exactly
-  ds.tau = __int_as_float(rec.w) - y;          // tau(n) = D_a + phi(n)
+  ds.col = rmI + ((b >> 2) - (kRoundBits >> 2));
+  ds.seg = b & 3;
+  ds.w = Y - (q - kRound);
+  ds.tau = fmaf(Y, -1.0f / kFarrowSegs, Dp);
   return ds;
 }
 
 // The same split for a gather from a window of kStride columns per segment:
-// idx = seg * kStride + col with the rounding offsets folded into rmc, where
-// rmc = rm - kRoundBits * (1 + kStride) (mod 2^32, once per window pass).
+// returns seg * kStride + col (mod 2^32) with rmc = r - m_lo + jj N_t -
+// kRoundBits / 4 (once per chunk and window pass) and I = img.x.
 template <int kStride>
-__device__ __forceinline__ unsigned split_index(const int4 rec, unsigned rmc, float rf, float* w, float* tau) {
-  const float y = fmaf(rf, __int_as_float(rec.z), __int_as_float(rec.y));
-  const float q = y + kRound;
-  const float a = y - (q - kRound);
-  const float q2 = fmaf(a, 3.0f, kRound + 1.0f);
-  *w = fmaf(a, 3.0f, (kRound + 1.0f) - q2);
-  *tau = __int_as_float(rec.w) - y;
-  return unsigned(__float_as_int(q2)) * unsigned(kStride) +
-         (unsigned(__float_as_int(q)) + unsigned(rec.x) + rmc);
+__device__ __forceinline__ unsigned split_index(const float2 rec, int I, unsigned rmc, float rf, float Dp,
+                                                float* w, float* tau) {
+  const float Y = fmaf(rf, rec.y, rec.x);
+  const float q = Y + kRound;
+  const unsigned b = unsigned(__float_as_int(q));
+  *w = Y - (q - kRound);
+  *tau = fmaf(Y, -1.0f / kFarrowSegs, Dp);
+  return (b & 3u) * unsigned(kStride) + ((b >> 2) + unsigned(I) + rmc);
 }
-__device__ __forceinline__ unsigned fold_rounding(int rm, int stride) {
-  return unsigned(rm) - unsigned(kRoundBits) * (1u + unsigned(stride));
+__device__ __forceinline__ unsigned fold_rounding(int r_minus_mlo_plus_jjN) {
+  return unsigned(r_minus_mlo_plus_jjN) - unsigned(kRoundBits >> 2);
 }
 
-// Farrow polynomial (degree 5) from the powers 0..3 (A) and 4..5 (B), Horner in w.
-__device__ __forceinline__ float horner6(const float4 A, const float2 B, float v) {
-  float e = fmaf(B.y, v, B.x);
-  e = fmaf(e, v, A.w);
-  e = fmaf(e, v, A.z);
-  e = fmaf(e, v, A.y);
-  return fmaf(e, v, A.x);
+// Farrow polynomial (degree 4) from the powers 0..3 (A) and 4 (B), Horner in w.
+__device__ __forceinline__ float horner5(const float4 A, const float B, float w) {
+  float e = fmaf(B, w, A.w);
+  e = fmaf(e, w, A.z);
+  e = fmaf(e, w, A.y);
+  return fmaf(e, w, A.x);
 }
 
 }  // namespace msrc

