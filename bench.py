@@ -33,16 +33,16 @@ METRIC = "image-samples/s (forward, order-20 48 kHz)"
 UNIT = "image-samples/s"
 
 # Algorithmic work of the synthesis kernel per image-sample (signal-side Farrow,
-# 3 segments x degree 5): 6 prefiltered values gathered from shared memory.
-Z_BYTES_PER_IMAGE_SAMPLE = 6 * 4
-# FP32 operations per image-sample: Horner 5 FMA (10), accumulate 1 FMA (2),
-# delay interpolation 1 FMA (2), fraction and segment split 6, delay 1 ADD,
-# gain 1 division (1) -> 22.
-FLOPS_PER_IMAGE_SAMPLE = 22
-# DRAM bytes (read + write) of one synthesis launch on this workload, from the
-# ncu capture of the 1 s version of the scene (26.0 MB) scaled by the
-# image-samples processed (x4); None whenever the kernel changed since.
-K_SYNTH_TRAFFIC_BYTES = None
+# 4 segments x degree 4): 5 prefiltered values gathered from shared memory.
+Z_BYTES_PER_IMAGE_SAMPLE = 5 * 4
+# FP32 operations per image-sample: delay interpolation 1 FMA (2), rounding and
+# local variable 3 adds (3), delay for the gain 1 FMA (2), gain 1 division (1),
+# Farrow polynomial 4 FMA (8), accumulate 1 FMA (2) -> 18.
+FLOPS_PER_IMAGE_SAMPLE = 18
+# DRAM bytes (read + write) of one synthesis launch on this workload, from one
+# ncu capture of the full-size launch (26.84 MB read + 240.60 MB written, the
+# partial rows); None whenever the kernel changed since.
+K_SYNTH_TRAFFIC_BYTES = 26838016 + 240595712
 SM_COUNT = 152
 SMEM_BYTES_PER_CLK_PER_SM = 128
 FP32_LANES_PER_SM = 128
