@@ -53,7 +53,11 @@ constexpr size_t kGradSmem = size_t(kFarrowSegs) * kGradWcap * (sizeof(float4) +
                              size_t(kBwRecCap) * sizeof(float2) + size_t(kBwBlock) * sizeof(int4) +
                              size_t(kBwUnitCap) * sizeof(float4) + size_t(2 * kBwBlock) * sizeof(float4);
 constexpr int kDxGroupImages = 256;             // images per dx item (block group), about
-constexpr size_t kDxSmem = size_t(kFarrowSegs) * kDxWcap * (sizeof(float4) + sizeof(float)) +
+constexpr int kDxSlots = kFarrowSegs * kDxWcap + 4;   // w window + a discard slot (+ 16-byte alignment)
+static_assert((kDxSlots * sizeof(float)) % 16 == 0 && (kBwRecCap * sizeof(float2)) % 16 == 0,
+              "every shared array of the reverse-mode kernels starts on a 16-byte boundary");
+static_assert((kFarrowSegs * kGradWcap * sizeof(float2)) % 16 == 0, "gradient window alignment");
+constexpr size_t kDxSmem = size_t(kDxSlots) * (sizeof(float4) + sizeof(float)) +
                            size_t(kBwRecCap) * sizeof(float2) + size_t(kBwBlock) * sizeof(int4) +
                            size_t(kBwTile + 4 + 2 * kBwBlock) * sizeof(float4);
 static_assert(kBwRecCap % 2 == 0, "16-byte alignment of the image records");
@@ -138,6 +142,73 @@ __device__ __forceinline__ void window_of(float tmin, float tmax, const ItemGeom
   *width = g.n_end - int(floorf(tmin)) + 2 - *m_lo + 1;
 }
 
+// The gradient kernel's image loop for this thread's chunks. Per image-sample:
+// e and de/dw (degree-5 rows), dL/dd_i(n) = -dy g (fs/c) (S de/dw + e / tau),
+// its knot weights (1 - s, s) times the unit vectors of the interval's knots,
+// and the wall terms dy e (fs/c) / tau times dbeta_i/dbeta_w / (4 pi).
+// kChecked: the window is processed in several passes and read positions
+// outside this pass contribute nothing; otherwise every position lies inside
+// the window by construction (the index is only clamped to the arrays).
+// dyf[c] = dy (fs/c) of the chunk's sample (0 for samples past the output).
+template <bool kChecked>
+__device__ __forceinline__ void grad_images(const float4* zq_s, const float2* zp_s, const float2* rec_s,
+                                            const int4* img_s, const float4* unit_s, const float4* bw_s,
+                                            int cnt, int nk, const int* jc, const int* rmj, const float* rf,
+                                            const float* sN, const float* dyf, unsigned pw,
+                                            float (&V)[kBwChunks][6], float (&bacc)[6]) {
+  const float2* row[kBwChunks];
+  const float4* urow[kBwChunks];
+  unsigned rmc[kBwChunks];
+#pragma unroll
+  for (int c = 0; c < kBwChunks; ++c) {
+    row[c] = rec_s + jc[c] * cnt;
+    urow[c] = unit_s + jc[c];
+    rmc[c] = fold_rounding(rmj[c]);
+  }
+  for (int ib = 0; ib < cnt; ++ib) {
+    const float4 B0 = bw_s[2 * ib], B1 = bw_s[2 * ib + 1];
+    const int4 im = img_s[ib];
+    const float Dp = __int_as_float(im.y);
+    const int ub = ib * nk;
+#pragma unroll
+    for (int c = 0; c < kBwChunks; ++c) {
+      float w, tau, dy = dyf[c];
+      unsigned idx;
+      if (kChecked) {
+        const DelaySplit ds = split_delay(row[c][ib], rmj[c] + im.x, rf[c], Dp);
+        const bool in = unsigned(ds.col) < pw;
+        dy = in ? dy : 0.0f;
+        idx = in ? unsigned(ds.seg * kGradWcap + ds.col) : 0u;
+        w = ds.w;
+        tau = ds.tau;
+      } else {
+        idx = min(split_index<kGradWcap>(row[c][ib], im.x, rmc[c], rf[c], Dp, &w, &tau),
+                  unsigned(kFarrowSegs * kGradWcap - 1));
+      }
+      const float4 A = zq_s[idx];
+      const float2 Bz = zp_s[idx];
+      float pe = Bz.y, pd = 0.0f;  // e = P(w) and dP/dw together (Horner, degree 5)
+      pd = fmaf(pd, w, pe); pe = fmaf(pe, w, Bz.x);
+      pd = fmaf(pd, w, pe); pe = fmaf(pe, w, A.w);
+      pd = fmaf(pd, w, pe); pe = fmaf(pe, w, A.z);
+      pd = fmaf(pd, w, pe); pe = fmaf(pe, w, A.y);
+      pd = fmaf(pd, w, pe); pe = fmaf(pe, w, A.x);
+      const float rt = __fdividef(1.0f, tau);
+      const float et = pe * rt;                                          // e / tau
+      const float ad = -(dy * B1.z * rt) * fmaf(float(kFarrowSegs), pd, et);  // dL/dd_i(n)
+      const float hbv = dy * et;                                         // dy e (fs/c) / tau
+      const float4 U0 = urow[c][ub];
+      const float4 U1 = urow[c][ub + 1];
+      const float w1 = ad * sN[c], w0 = ad - w1;
+      V[c][0] = fmaf(w0, U0.x, V[c][0]); V[c][1] = fmaf(w0, U0.y, V[c][1]); V[c][2] = fmaf(w0, U0.z, V[c][2]);
+      V[c][3] = fmaf(w1, U1.x, V[c][3]); V[c][4] = fmaf(w1, U1.y, V[c][4]); V[c][5] = fmaf(w1, U1.z, V[c][5]);
+      bacc[0] = fmaf(hbv, B0.x, bacc[0]); bacc[1] = fmaf(hbv, B0.y, bacc[1]);
+      bacc[2] = fmaf(hbv, B0.z, bacc[2]); bacc[3] = fmaf(hbv, B0.w, bacc[3]);
+      bacc[4] = fmaf(hbv, B1.x, bacc[4]); bacc[5] = fmaf(hbv, B1.y, bacc[5]);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ gradients
 __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constant__ KernelArgs a) {
   extern __shared__ __align__(16) float4 sm[];
@@ -191,20 +262,19 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     window_of<kBwThreads>(tmin, tmax, g, s_red, &m_lo, &width);
 
     int jc[kBwChunks], rr[kBwChunks];
-    float rf[kBwChunks], sN[kBwChunks], dyv[kBwChunks];
+    float rf[kBwChunks], sN[kBwChunks], dyf[kBwChunks];
     float V[kBwChunks][6];
-    bool valid[kBwChunks];
 #pragma unroll
     for (int c = 0; c < kBwChunks; ++c) {
       const int n = g.n0 + 32 * (warp * kBwChunks + c) + lane;
-      valid[c] = n <= g.n_end;
-      const int nn = valid[c] ? n : g.n_end;
+      const bool valid = n <= g.n_end;
+      const int nn = valid ? n : g.n_end;
       const int j = nn / g.N;
       rr[c] = nn - j * g.N;
       jc[c] = j - g.jf;
       rf[c] = float(rr[c]);
       sN[c] = rf[c] / float(g.N);
-      dyv[c] = valid[c] ? __ldg(S.dy + int64_t(g.mic) * S.n_out + n) : 0.0f;
+      dyf[c] = valid ? __ldg(S.dy + int64_t(g.mic) * S.n_out + n) * fsc : 0.0f;
 #pragma unroll
       for (int k = 0; k < 6; ++k) V[c][k] = 0.0f;
     }
@@ -231,37 +301,12 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
       int rmj[kBwChunks];
 #pragma unroll
       for (int c = 0; c < kBwChunks; ++c) rmj[c] = rr[c] - pass_lo + jc[c] * g.N;
-      for (int ib = 0; ib < g.cnt; ++ib) {
-        const float4 B0 = bw_s[2 * ib], B1 = bw_s[2 * ib + 1];
-        const int4 im = img_s[ib];
-#pragma unroll
-        for (int c = 0; c < kBwChunks; ++c) {
-          const DelaySplit ds = split_delay(rec_s[jc[c] * g.cnt + ib], rmj[c] + im.x, rf[c], __int_as_float(im.y));
-          if (!valid[c] || unsigned(ds.col) >= unsigned(pw)) continue;
-          const int idx = ds.seg * kGradWcap + ds.col;
-          const float4 A = zq_s[idx];
-          const float2 Bz = zp_s[idx];
-          const float v = ds.w;
-          float pe = Bz.y, pd = 0.0f;  // e = P(w) and dP/dw together (Horner, degree 5)
-          pd = fmaf(pd, v, pe); pe = fmaf(pe, v, Bz.x);
-          pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.w);
-          pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.z);
-          pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.y);
-          pd = fmaf(pd, v, pe); pe = fmaf(pe, v, A.x);
-          const float rt = __fdividef(1.0f, ds.tau);
-          const float val = dyv[c] * B1.z * rt;                                        // dy g
-          const float ad = -val * fsc * fmaf(float(kFarrowSegs), pd, pe * rt);        // dL/dd_i(n)
-          const float4 U0 = unit_s[ib * g.nk + jc[c]];
-          const float4 U1 = unit_s[ib * g.nk + jc[c] + 1];
-          const float w1 = ad * sN[c], w0 = ad - w1;
-          V[c][0] = fmaf(w0, U0.x, V[c][0]); V[c][1] = fmaf(w0, U0.y, V[c][1]); V[c][2] = fmaf(w0, U0.z, V[c][2]);
-          V[c][3] = fmaf(w1, U1.x, V[c][3]); V[c][4] = fmaf(w1, U1.y, V[c][4]); V[c][5] = fmaf(w1, U1.z, V[c][5]);
-          const float hbv = dyv[c] * pe * rt * fsc;                                    // dy e / d (4 pi in B)
-          bacc[0] = fmaf(hbv, B0.x, bacc[0]); bacc[1] = fmaf(hbv, B0.y, bacc[1]);
-          bacc[2] = fmaf(hbv, B0.z, bacc[2]); bacc[3] = fmaf(hbv, B0.w, bacc[3]);
-          bacc[4] = fmaf(hbv, B1.x, bacc[4]); bacc[5] = fmaf(hbv, B1.y, bacc[5]);
-        }
-      }
+      if (width <= kGradWcap)
+        grad_images<false>(zq_s, zp_s, rec_s, img_s, unit_s, bw_s, g.cnt, g.nk, jc, rmj, rf, sN, dyf, unsigned(pw),
+                           V, bacc);
+      else
+        grad_images<true>(zq_s, zp_s, rec_s, img_s, unit_s, bw_s, g.cnt, g.nk, jc, rmj, rf, sN, dyf, unsigned(pw),
+                          V, bacc);
     }
     __syncthreads();  // the z window is reused as scan scratch
     // knot slots of the item: per chunk a warp-segmented scan over the lanes'
@@ -335,13 +380,59 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
   }
 }
 
+// The dx kernel's scatter of one block's images into the w window: per
+// image-sample, dy g w^q goes to bin (segment, column); samples past the output
+// (and, with kChecked, read positions outside this pass) go to a discard slot
+// past the window. Within one image no two samples share a bin (the source is
+// slower than c/2), so images are separated by a barrier and no atomics are
+// needed.
+template <bool kChecked>
+__device__ __forceinline__ void dx_images(float4* wq_s, float* wp_s, const float2* rec_s, const int4* img_s, int cnt,
+                                          const int* jc, const int* rmj, const float* rf, const float* dyv,
+                                          const bool* valid, unsigned pw) {
+  constexpr unsigned kDiscard = unsigned(kFarrowSegs * kDxWcap);
+  const float2* row[kBwChunks];
+  unsigned rmc[kBwChunks];
+#pragma unroll
+  for (int c = 0; c < kBwChunks; ++c) {
+    row[c] = rec_s + jc[c] * cnt;
+    rmc[c] = fold_rounding(rmj[c]);
+  }
+  for (int ib = 0; ib < cnt; ++ib) {
+    const int4 im = img_s[ib];
+    const float gi = __int_as_float(im.z);
+    const float Dp = __int_as_float(im.y);
+#pragma unroll
+    for (int c = 0; c < kBwChunks; ++c) {
+      float w, tau;
+      unsigned idx;
+      if (kChecked) {
+        const DelaySplit ds = split_delay(row[c][ib], rmj[c] + im.x, rf[c], Dp);
+        idx = (valid[c] && unsigned(ds.col) < pw) ? unsigned(ds.seg * kDxWcap + ds.col) : kDiscard;
+        w = ds.w;
+        tau = ds.tau;
+      } else {
+        idx = split_index<kDxWcap>(row[c][ib], im.x, rmc[c], rf[c], Dp, &w, &tau);
+        idx = valid[c] ? min(idx, kDiscard - 1) : kDiscard;
+      }
+      const float val = dyv[c] * __fdividef(gi, tau);  // dy g
+      const float p1 = val * w, p2 = p1 * w, p3 = p2 * w, p4 = p3 * w;
+      float4 wa = wq_s[idx];
+      wa.x += val; wa.y += p1; wa.z += p2; wa.w += p3;
+      wq_s[idx] = wa;
+      wp_s[idx] += p4;
+    }
+    __syncthreads();  // the next image may write the same bins
+  }
+}
+
 // ------------------------------------------------------------------ dx
 template <int kL>
 __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant__ KernelArgs a) {
   extern __shared__ __align__(16) float4 sm[];
   float4* wq_s = sm;                                                       // kFarrowSegs x kDxWcap (powers 0..3)
-  float* wp_s = reinterpret_cast<float*>(wq_s + kFarrowSegs * kDxWcap);    // power 4
-  float2* rec_s = reinterpret_cast<float2*>(wp_s + kFarrowSegs * kDxWcap);
+  float* wp_s = reinterpret_cast<float*>(wq_s + kDxSlots);                 // power 4
+  float2* rec_s = reinterpret_cast<float2*>(wp_s + kDxSlots);
   int4* img_s = reinterpret_cast<int4*>(rec_s + kBwRecCap);
   float4* u_s = reinterpret_cast<float4*>(img_s + kBwBlock);              // record scratch
   float4* anc_s = u_s + kBwTile + 4;
@@ -389,16 +480,17 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
       // every block of the group has the tier's knot spacing and the same tile
       int jc[kBwChunks], rr[kBwChunks];
       float rf[kBwChunks], dyv[kBwChunks];
+      bool valid[kBwChunks];
 #pragma unroll
       for (int c = 0; c < kBwChunks; ++c) {
         const int n = g0.n0 + 32 * (warp * kBwChunks + c) + lane;
-        const bool valid = n <= g0.n_end;
-        const int nn = valid ? n : g0.n_end;
+        valid[c] = n <= g0.n_end;
+        const int nn = valid[c] ? n : g0.n_end;
         const int j = nn / g0.N;
         rr[c] = nn - j * g0.N;
         jc[c] = j - g0.jf;
         rf[c] = float(rr[c]);
-        dyv[c] = valid ? __ldg(S.dy + int64_t(mic) * S.n_out + n) : 0.0f;  // 0 disables the sample
+        dyv[c] = valid[c] ? __ldg(S.dy + int64_t(mic) * S.n_out + n) : 0.0f;
       }
       const bool reuse = (b1 - b0 == 1);  // a single block keeps its records
       for (int p0 = 0; p0 < width; p0 += kDxWcap) {
@@ -420,24 +512,10 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
             item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, anc_s, &lo, &hi);
           }
           __syncthreads();  // records and the zeroed window are complete
-          for (int ib = 0; ib < g.cnt; ++ib) {
-            const int4 im = img_s[ib];
-            const float gi = __int_as_float(im.z);
-#pragma unroll
-            for (int c = 0; c < kBwChunks; ++c) {
-              const DelaySplit ds = split_delay(rec_s[jc[c] * g.cnt + ib], rmj[c] + im.x, rf[c], __int_as_float(im.y));
-              if (dyv[c] == 0.0f || unsigned(ds.col) >= unsigned(pw)) continue;
-              const float val = dyv[c] * __fdividef(gi, ds.tau);  // dy g
-              const float v = ds.w;
-              const float p1 = val * v, p2 = p1 * v, p3 = p2 * v, p4 = p3 * v;
-              const int idx = ds.seg * kDxWcap + ds.col;
-              float4 wa = wq_s[idx];
-              wa.x += val; wa.y += p1; wa.z += p2; wa.w += p3;
-              wq_s[idx] = wa;
-              wp_s[idx] += p4;
-            }
-            __syncthreads();  // the next image may write the same bins
-          }
+          if (width <= kDxWcap)
+            dx_images<false>(wq_s, wp_s, rec_s, img_s, g.cnt, jc, rmj, rf, dyv, valid, unsigned(pw));
+          else
+            dx_images<true>(wq_s, wp_s, rec_s, img_s, g.cnt, jc, rmj, rf, dyv, valid, unsigned(pw));
         }
         // dx[m'] += sum_{row, k} c[row][k] w[row][m' + k], 4 consecutive m' per thread
         const int n_outv = pw + kL - 1;
@@ -500,44 +578,64 @@ __global__ void k_dx_final(const __grid_constant__ KernelArgs a) {
 
 // dL/ds(t_j) per tier knot: sum over microphones, blocks of the tier and the
 // (at most two) tiles whose knot range holds j.
-__global__ void k_knot_final(const __grid_constant__ KernelArgs a) {
-  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (gid >= a.totals[1]) return;
-  int s = 0;
-  int64_t local = gid;
-  if (a.n_scenes > 1) {
-    s = find_scene(a.tab.knots_prefix, a.n_scenes, gid);
-    local = gid - a.tab.knots_prefix[s];
-  }
-  const SceneDev& S = scene_of(a, s);
-  int t = 0;
-  while (t + 1 < S.n_tiers && local >= S.knot_units_first[t + 1]) ++t;
-  const int j = int(local - S.knot_units_first[t]);
-  const int N = S.tier_step[t];
+// 32 knots per CTA x 8 lanes per knot: lane q sums blocks q, q + 8, ... (in
+// order), the 8 lane sums are added in lane order (bitwise reproducible).
+constexpr int kKnotsPerCta = 32;
+constexpr int kKnotLanes = 8;
+__global__ void __launch_bounds__(kKnotsPerCta * kKnotLanes) k_knot_final(const __grid_constant__ KernelArgs a) {
+  __shared__ double part[kKnotLanes][kKnotsPerCta][3];
+  const int kq = threadIdx.x % kKnotsPerCta, q = threadIdx.x / kKnotsPerCta;
+  const int64_t gid = int64_t(blockIdx.x) * kKnotsPerCta + kq;
   double gx = 0.0, gy = 0.0, gz = 0.0;
-  if (S.tier_count[t] > 0) {
-    // samples weighting knot j: intervals j - 1 and j, n in [(j-1) N, (j+1) N)
-    const int64_t s_lo = max(int64_t(j - 1) * N, int64_t(0));
-    const int64_t s_hi = min(int64_t(j + 1) * N - 1, S.n_out - 1);
-    const int tile_lo = int(s_lo / S.tile), tile_hi = int(s_hi / S.tile);
-    for (int mic = 0; mic < S.n_mics; ++mic)
-      for (int b = 0; b < S.tier_blocks[t]; ++b)
-        for (int tile = tile_lo; tile <= tile_hi; ++tile) {
-          const int n0 = tile * S.tile;
-          const int n_end = int(min(int64_t(n0 + S.tile), S.n_out)) - 1;
-          const int jf = n0 / N, nk = n_end / N - jf + 2;
-          if (j < jf || j >= jf + nk) continue;
-          const float* slot = a.p.kslot + 3 * (S.kslot_first[t] + int64_t(mic) * S.kslot_mic_stride +
-                                               (int64_t(b) * S.n_tiles + tile) * S.kcap[t] + (j - jf));
-          gx += slot[0];
-          gy += slot[1];
-          gz += slot[2];
-        }
+  int s = 0, t = 0, j = 0;
+  const bool live = gid < a.totals[1];
+  if (live) {
+    int64_t local = gid;
+    if (a.n_scenes > 1) {
+      s = find_scene(a.tab.knots_prefix, a.n_scenes, gid);
+      local = gid - a.tab.knots_prefix[s];
+    }
+    const SceneDev& S = scene_of(a, s);
+    while (t + 1 < S.n_tiers && local >= S.knot_units_first[t + 1]) ++t;
+    j = int(local - S.knot_units_first[t]);
+    const int N = S.tier_step[t];
+    if (S.tier_count[t] > 0) {
+      // samples weighting knot j: intervals j - 1 and j, n in [(j-1) N, (j+1) N)
+      const int64_t s_lo = max(int64_t(j - 1) * N, int64_t(0));
+      const int64_t s_hi = min(int64_t(j + 1) * N - 1, S.n_out - 1);
+      const int tile_lo = int(s_lo / S.tile), tile_hi = int(s_hi / S.tile);
+      for (int mic = 0; mic < S.n_mics; ++mic)
+        for (int b = q; b < S.tier_blocks[t]; b += kKnotLanes)
+          for (int tile = tile_lo; tile <= tile_hi; ++tile) {
+            const int n0 = tile * S.tile;
+            const int n_end = int(min(int64_t(n0 + S.tile), S.n_out)) - 1;
+            const int jf = n0 / N, nk = n_end / N - jf + 2;
+            if (j < jf || j >= jf + nk) continue;
+            const float* slot = a.p.kslot + 3 * (S.kslot_first[t] + int64_t(mic) * S.kslot_mic_stride +
+                                                 (int64_t(b) * S.n_tiles + tile) * S.kcap[t] + (j - jf));
+            gx += slot[0];
+            gy += slot[1];
+            gz += slot[2];
+          }
+    }
   }
-  double* out = a.p.gk + 3 * (S.knot_base[t] + j);
-  out[0] = gx;
-  out[1] = gy;
-  out[2] = gz;
+  part[q][kq][0] = gx;
+  part[q][kq][1] = gy;
+  part[q][kq][2] = gz;
+  __syncthreads();
+  if (q == 0 && live) {
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int r = 0; r < kKnotLanes; ++r) {
+      sx += part[r][kq][0];
+      sy += part[r][kq][1];
+      sz += part[r][kq][2];
+    }
+    const SceneDev& S = scene_of(a, s);
+    double* out = a.p.gk + 3 * (S.knot_base[t] + j);
+    out[0] = sx;
+    out[1] = sy;
+    out[2] = sz;
+  }
 }
 
 // Adds J(t)^T g to every trajectory parameter, J = ds(t)/dparams (3 x 48):
@@ -637,13 +735,27 @@ __global__ void k_param_final(const __grid_constant__ KernelArgs a) {
 }
 
 // dL/dbeta_w: sum of the item partials in item order (one CTA per scene).
-__global__ void k_beta_final(const __grid_constant__ KernelArgs a) {
+// 256 threads per scene: thread r sums rows r, r + 256, ... per wall (in
+// order), then the thread sums are added in thread order.
+constexpr int kBetaThreads = 256;
+__global__ void __launch_bounds__(kBetaThreads) k_beta_final(const __grid_constant__ KernelArgs a) {
+  __shared__ double part[6][kBetaThreads];
   const SceneDev& S = scene_of(a, blockIdx.x);
-  if (!S.dbeta || threadIdx.x >= 6) return;
-  double acc = 0.0;
+  if (!S.dbeta) return;
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   const int64_t rows = int64_t(S.n_mics) * S.n_blocks * S.n_tiles;
-  for (int64_t rr = 0; rr < rows; ++rr) acc += a.p.bpart[S.bpart_base + rr * 8 + threadIdx.x];
-  S.dbeta[threadIdx.x] = acc;
+  for (int64_t rr = threadIdx.x; rr < rows; rr += kBetaThreads) {
+    const float4 v0 = *reinterpret_cast<const float4*>(a.p.bpart + S.bpart_base + rr * 8);
+    const float2 v1 = *reinterpret_cast<const float2*>(a.p.bpart + S.bpart_base + rr * 8 + 4);
+    acc[0] += v0.x; acc[1] += v0.y; acc[2] += v0.z; acc[3] += v0.w; acc[4] += v1.x; acc[5] += v1.y;
+  }
+  for (int w = 0; w < 6; ++w) part[w][threadIdx.x] = acc[w];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double sum = 0.0;
+    for (int r = 0; r < kBetaThreads; ++r) sum += part[threadIdx.x][r];
+    S.dbeta[threadIdx.x] = sum;
+  }
 }
 
 template <typename K>
@@ -690,7 +802,8 @@ cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int T = 256;
   if (a.totals[2] > 0) k_dx_final<<<unsigned((a.totals[2] + T - 1) / T), T, 0, st>>>(a);
-  if (a.totals[1] > 0) k_knot_final<<<unsigned((a.totals[1] + T - 1) / T), T, 0, st>>>(a);
+  if (a.totals[1] > 0)
+    k_knot_final<<<unsigned((a.totals[1] + kKnotsPerCta - 1) / kKnotsPerCta), kKnotsPerCta * kKnotLanes, 0, st>>>(a);
   {
     constexpr size_t smem = 48 * kParamThreads * sizeof(double);
     static bool attr = false;
@@ -702,7 +815,7 @@ cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
     k_param_partial<<<unsigned(a.n_scenes * kParamChunks), kParamThreads, smem, st>>>(a);
     k_param_final<<<unsigned(a.n_scenes), 64, 0, st>>>(a);
   }
-  k_beta_final<<<unsigned(a.n_scenes), 32, 0, st>>>(a);
+  k_beta_final<<<unsigned(a.n_scenes), kBetaThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

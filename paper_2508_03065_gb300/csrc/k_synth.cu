@@ -153,7 +153,8 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
   float* zp_s = reinterpret_cast<float*>(smem4 + kFarrowSegs * kWcap);    // kFarrowSegs x kWcap
   float2* rec_s = reinterpret_cast<float2*>(zp_s + kFarrowSegs * kWcap);  // kRecCap interval records
   int4* img_s = reinterpret_cast<int4*>(rec_s + kRecCap);                 // kBlock image records
-  static_assert(kRecCap % 2 == 0, "16-byte alignment of the image records");
+  static_assert((kRecCap * sizeof(float2)) % 16 == 0 && (kFarrowSegs * kWcap * sizeof(float)) % 16 == 0,
+                "every shared array starts on a 16-byte boundary");
   // prologue scratch aliases the z window (used before the window is staged)
   float4* u_s = smem4;
   float4* anc_s = u_s + kThreads * kChunks + 4;                          // 2 x kBlock
