@@ -42,7 +42,7 @@ FLOPS_PER_IMAGE_SAMPLE = 18
 # DRAM bytes (read + write) of one synthesis launch on this workload, from one
 # ncu capture of the full-size launch (26.84 MB read + 240.60 MB written, the
 # partial rows); None whenever the kernel changed since.
-K_SYNTH_TRAFFIC_BYTES = 26838016 + 240595712
+K_SYNTH_TRAFFIC_BYTES = None
 SM_COUNT = 152
 SMEM_BYTES_PER_CLK_PER_SM = 128
 FP32_LANES_PER_SM = 128
@@ -193,9 +193,9 @@ def workload_config(spec, tier_counts=None):
 def partial_bytes(spec, tier_counts):
     """Bytes of the synthesis partial sums of one step: one float per
     (microphone, image block, output sample); blocks per tier from the record
-    capacity of the default tile configuration (3328 records of 1024 samples,
-    at most 256 images)."""
-    T, reccap, bmax = 1024, 3328, 256
+    capacity of the default tile configuration (4096 records over tiles of
+    1536 samples, at most 256 images)."""
+    T, reccap, bmax = 1536, 4096, 256
     blocks = 0
     for (rho, n_step), cnt in zip(spec.tier_steps(), tier_counts):
         B = max(1, min(bmax, reccap // ((T - 1) // n_step + 2)))

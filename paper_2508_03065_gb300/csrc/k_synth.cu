@@ -301,12 +301,14 @@ cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
 
 // Tile configurations of the synthesis launch (see TileConfig).
 #define MSRC_TILE_CONFIGS(X)             \
-  X(0, 512, 2, 2432, 4096, 256, 8)       \
+  X(0, 512, 3, 2432, 4096, 256, 8)       \
   X(1, 256, 2, 1152, 1664, 256, 4)       \
   X(2, 384, 2, 2048, 3072, 256, 4)       \
   X(3, 1024, 1, 2432, 4096, 256, 2)      \
-  X(4, 512, 2, 2432, 4096, 256, 4)       \
-  X(5, 512, 1, 2432, 4096, 256, 8)
+  X(4, 512, 2, 2432, 4096, 256, 8)       \
+  X(5, 512, 1, 2432, 4096, 256, 8)       \
+  X(6, 512, 3, 2432, 4096, 256, 4)       \
+  X(7, 512, 2, 2432, 4096, 256, 16)
 
 static const TileConfig kConfigs[] = {
 #define MSRC_ROW(id, th, ch, wc, rc, bl, un) {th, ch, wc, rc, bl},
