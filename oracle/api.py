@@ -54,6 +54,8 @@ class _Scene(ctypes.Structure):
         ("window", ctypes.c_int32),
         ("traj_kind", ctypes.c_int32),
         ("n_ctrl", ctypes.c_int32),
+        ("farrow_order", ctypes.c_int32),
+        ("farrow", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -95,6 +97,8 @@ class Scene:
     traj_kind: 0 line (traj = p0[3], direction[3], speed), 1 circle
     (traj = centre[3], radius, speed, start angle), 2 clamped cubic B-spline
     (traj = control points, 3 per point; n_ctrl points; u = clamp(t/duration)).
+    window: 0 Hann, 1 Kaiser(kaiser_beta), 2 a Farrow polynomial per tap with
+    coefficients `farrow` (taps x (order + 1), e.g. from oracle.gls.design).
     tiers: list of (max_rho, knot_step_samples); an image goes to the first
     tier whose max_rho >= its reflection count, else to the last tier.
     """
@@ -113,6 +117,7 @@ class Scene:
     traj: Sequence[float] = field(default_factory=list)
     n_ctrl: int = 0
     duration: float = 1.0
+    farrow: Optional[np.ndarray] = None
 
     def to_c(self) -> _Scene:
         s = _Scene()
@@ -139,6 +144,13 @@ class Scene:
         s.window = int(self.window)
         s.traj_kind = int(self.traj_kind)
         s.n_ctrl = int(self.n_ctrl)
+        if self.window == 2:
+            c = np.ascontiguousarray(self.farrow, dtype=np.float64)
+            if c.ndim != 2 or c.shape[0] != self.taps:
+                raise ValueError("farrow must be taps x (order + 1)")
+            s.farrow_order = c.shape[1] - 1
+            s.farrow = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            s._keep = c  # the table must outlive the call
         return s
 
 

@@ -17,7 +17,9 @@
 //     (Sec. II-A, text after Eq. 2; Sec. II-C, text before Eq. 8);
 //   * discrete time-varying fractional delay (Sec. II-B): the ideal delay kernel
 //     sin(pi u)/(pi u), truncated to L taps k = -L/2 .. L/2-1 and windowed
-//     (Hann or Kaiser), applied at read position t = n - tau_i(n):
+//     (Hann or Kaiser) -- or a Farrow polynomial per tap (Eq. 3) whose
+//     coefficients come from a least-squares design -- applied at read
+//     position t = n - tau_i(n):
 //     m0 = floor(t), alpha = t - m0, e_i(n) = sum_k w(alpha+k) sinc(alpha+k) x[m0-k];
 //   * superposition over images (Eq. 2 / Eq. 8): y[n] = sum_i A_i(n) e_i(n).
 // x[m] is zero outside [0, Ns).
@@ -68,9 +70,11 @@ struct OracleScene {
   int32_t tier_max_rho[4];// tier t holds images with rho <= tier_max_rho[t] (first match)
   int32_t tier_step[4];   // knot spacing N_t (samples) of tier t
   int32_t taps;           // L (even)
-  int32_t window;         // 0 = Hann, 1 = Kaiser
+  int32_t window;         // 0 = Hann, 1 = Kaiser, 2 = Farrow polynomial given in `farrow`
   int32_t traj_kind;      // 0 = line, 1 = circle, 2 = clamped cubic B-spline
   int32_t n_ctrl;         // number of spline control points
+  int32_t farrow_order;   // window 2: polynomial order M
+  const double* farrow;   // window 2: c[(k + L/2) * (M + 1) + q], tap weight sum_q c alpha^q
 };
 
 }  // extern "C"
@@ -230,9 +234,18 @@ T sinc_value(T u) {
   return std::sin(kPi * u) / (kPi * u);
 }
 
-// Tap weight for tap k at fractional read position alpha.
+// Tap weight for tap k at fractional read position alpha: the windowed ideal
+// kernel, or (window 2) the Farrow polynomial of Eq. 3, h(k; alpha) =
+// sum_q c_q(k) alpha^q, with coefficients designed outside (oracle/gls.py).
 template <class T>
 T tap_weight(const OracleScene& S, int k, T alpha) {
+  if (S.window == 2) {
+    const int P = S.farrow_order + 1;
+    const double* c = S.farrow + (k + S.taps / 2) * P;
+    T h = T(c[P - 1]);
+    for (int q = P - 2; q >= 0; --q) h = h * alpha + c[q];
+    return h;
+  }
   T u = alpha + double(k);
   return window_value(S, u) * sinc_value(u);
 }
