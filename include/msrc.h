@@ -69,8 +69,16 @@ typedef struct {
                                 the first tier t with rho <= tier_max_rho[t], else to the last */
   double tier_rate_hz[4];    /* knot rate of each tier; fs / rate must be an integer >= 1 */
   int32_t taps;              /* fractional-delay length L: even, 8..64 */
-  int32_t window;            /* 0 = Hann, 1 = Kaiser */
+  int32_t window;            /* tap weights h(k; alpha), k = -L/2 .. L/2-1:
+                                0 = Hann-windowed sinc, 1 = Kaiser-windowed sinc,
+                                2 = least-squares Farrow design (Sec. II-B, Eq. 3-4):
+                                    h(k; alpha) = sum_{q<=M} c_q(k) alpha^q minimising the
+                                    integral over alpha in [0,1] and w in [0,pi] of
+                                    V(w) |sum_k h(k; alpha) e^{-jwk} - e^{jw alpha}|^2,
+                                    V = 1 up to passband*pi and 1e-3 above */
   double kaiser_beta;        /* Kaiser shape (used when window == 1), 0..20 */
+  int32_t farrow_order;      /* window 2: polynomial order M, 1..4 */
+  double passband;           /* window 2: passband edge as a fraction of pi, 0.05..0.98 */
 } msrc_room_desc;
 
 /* Source trajectory s(t) (Sec. II-C: a band-limited trajectory p(n)). */

@@ -31,6 +31,8 @@ class RoomDesc(ctypes.Structure):
         ("taps", ctypes.c_int32),
         ("window", ctypes.c_int32),
         ("kaiser_beta", ctypes.c_double),
+        ("farrow_order", ctypes.c_int32),
+        ("passband", ctypes.c_double),
     ]
 
 

@@ -26,7 +26,9 @@ class Room:
     """A shoebox room with its image-source settings, trajectory and microphones."""
 
     def __init__(self, dims, beta, fs, max_order, tiers, taps=32, window=0, kaiser_beta=8.0,
-                 c=343.0):
+                 c=343.0, farrow_order=4, passband=0.9):
+        """window: 0 Hann- or 1 Kaiser-windowed sinc taps, 2 a least-squares
+        Farrow design of order `farrow_order` fitted up to `passband` * pi."""
         lib = _lib.load()
         d = _lib.RoomDesc()
         d.dims[:] = [float(v) for v in dims]
@@ -45,6 +47,8 @@ class Room:
         d.taps = int(taps)
         d.window = int(window)
         d.kaiser_beta = float(kaiser_beta)
+        d.farrow_order = int(farrow_order)
+        d.passband = float(passband)
         self._desc = d
         h = ctypes.c_void_p()
         _lib.check(lib.msrc_create_room(ctypes.byref(d), ctypes.byref(h)))
@@ -55,7 +59,7 @@ class Room:
     @classmethod
     def from_spec(cls, spec) -> "Room":
         room = cls(spec.dims, spec.beta, spec.fs, spec.K, spec.tiers, spec.taps, spec.window,
-                   spec.kaiser_beta, spec.c)
+                   spec.kaiser_beta, spec.c, spec.farrow_order, spec.passband)
         room.set_trajectory(spec.traj_kind, spec.traj, spec.duration, spec.mics, spec.n_ctrl)
         return room
 

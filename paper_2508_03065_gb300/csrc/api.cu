@@ -35,6 +35,7 @@ struct msrc_room {
   int64_t n_images;
   int64_t tier_count[MSRC_MAX_TIERS];
   int kL;  // tap template length (16, 32 or 64)
+  double gls[kMaxTaps * (kFarrowDeg + 1)];              // window 2: c[k + L/2][q] of the design
   float farrow[kFarrowSegs][kFarrowCoef][kMaxTaps];    // synthesis and dx (degree 4)
   float farrow_g[kFarrowSegs][kGradCoef][kMaxTaps];    // gradient kernel (degree 5)
   double fit_error;                                    // of the synthesis table
@@ -103,6 +104,117 @@ double kernel_fn(const msrc_room_desc& d, double u) {
   return window_fn(d, u) * s;
 }
 
+// ---------------------------------------------------------------- least-squares Farrow design
+// Gauss-Legendre nodes and weights on [0, 1] (Newton on the three-term
+// recurrence of the Legendre polynomials).
+void gauss_legendre01(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(kPiD * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int j = 2; j <= n; ++j) {
+        const double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = 0.5 * (1.0 - z);
+    w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Solves A X = B in place (A n x n, B n x m, row-major) by Gaussian
+// elimination with partial pivoting; false when A is singular.
+bool solve_dense(int n, int m, std::vector<double>& A, std::vector<double>& B) {
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(A[r * n + col]) > std::fabs(A[piv * n + col])) piv = r;
+    if (A[piv * n + col] == 0.0) return false;
+    if (piv != col) {
+      for (int c = 0; c < n; ++c) std::swap(A[col * n + c], A[piv * n + c]);
+      for (int c = 0; c < m; ++c) std::swap(B[col * m + c], B[piv * m + c]);
+    }
+    for (int r = col + 1; r < n; ++r) {
+      const double f = A[r * n + col] / A[col * n + col];
+      if (f == 0.0) continue;
+      for (int c = col; c < n; ++c) A[r * n + c] -= f * A[col * n + c];
+      for (int c = 0; c < m; ++c) B[r * m + c] -= f * B[col * m + c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r)
+    for (int c = 0; c < m; ++c) {
+      double acc = B[r * m + c];
+      for (int k = r + 1; k < n; ++k) acc -= A[r * n + k] * B[k * m + c];
+      B[r * m + c] = acc / A[r * n + r];
+    }
+  return true;
+}
+
+// Least-squares Farrow design (Sec. II-B, Eq. 3-4, the complex-domain fit of
+// the frequency response): c[k + L/2][q], q <= M, minimising the integral over
+// alpha in [0, 1] and w in [0, pi] of V(w) |sum_k h(k; alpha) e^{-jwk} - e^{jw alpha}|^2
+// (V = 1 up to wp, kStopWeight above). Normal equations: the Gram matrix
+// factors as A (x) T with A[q][q'] = 1/(q + q' + 1) (the alpha integral) and
+// T[k][k'] = integral of V(w) cos(w (k - k')) dw, the right-hand side is
+// b[k][q] = integral over alpha of alpha^q * integral of V(w) cos(w (alpha + k)) dw,
+// so C = T^{-1} B A^{-1}.
+constexpr double kStopWeight = 1e-3;
+bool gls_design(int L, int M, double passband, double* c /* L x (M + 1) */) {
+  const double wp = passband * kPiD, lam = kStopWeight;
+  const int P = M + 1;
+  // integral of V(w) cos(w u) dw over [0, pi]
+  auto vcos = [&](double u) {
+    if (u == 0.0) return (1.0 - lam) * wp + lam * kPiD;
+    return ((1.0 - lam) * std::sin(wp * u) + lam * std::sin(kPiD * u)) / u;
+  };
+  std::vector<double> T(size_t(L) * L), B(size_t(L) * P, 0.0), A(size_t(P) * P);
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < L; ++j) {
+      const int m = i - j;
+      T[size_t(i) * L + j] = m == 0 ? vcos(0.0) : (1.0 - lam) * std::sin(wp * m) / m;  // sin(pi m) = 0
+    }
+  constexpr int kNodes = 64;
+  double xa[kNodes], wa[kNodes];
+  gauss_legendre01(kNodes, xa, wa);
+  for (int i = 0; i < L; ++i) {
+    const int k = i - L / 2;
+    for (int g = 0; g < kNodes; ++g) {
+      const double v = wa[g] * vcos(xa[g] + k);
+      double pw = 1.0;
+      for (int q = 0; q < P; ++q) { B[size_t(i) * P + q] += v * pw; pw *= xa[g]; }
+    }
+  }
+  if (!solve_dense(L, P, T, B)) return false;  // B <- T^{-1} B
+  for (int q = 0; q < P; ++q)
+    for (int r = 0; r < P; ++r) A[size_t(q) * P + r] = 1.0 / (q + r + 1.0);
+  // C = B A^{-1}: solve A C^T = B^T (A symmetric)
+  std::vector<double> Bt(size_t(P) * L);
+  for (int i = 0; i < L; ++i)
+    for (int q = 0; q < P; ++q) Bt[size_t(q) * L + i] = B[size_t(i) * P + q];
+  if (!solve_dense(P, L, A, Bt)) return false;
+  for (int i = 0; i < L; ++i)
+    for (int q = 0; q < P; ++q) c[size_t(i) * P + q] = Bt[size_t(q) * L + i];
+  return true;
+}
+
+// Tap weight h(k; alpha) of the room's fractional-delay filter: the windowed
+// ideal kernel (Hann, Kaiser) or the least-squares Farrow polynomial.
+double tap_fn(const msrc_room& R, int k, double alpha) {
+  if (R.d.window == 2) {
+    const int P = R.d.farrow_order + 1;
+    const double* c = R.gls + size_t(k + R.d.taps / 2) * P;
+    double h = c[P - 1];
+    for (int q = P - 2; q >= 0; --q) h = h * alpha + c[q];
+    return h;
+  }
+  return kernel_fn(R.d, alpha + k);
+}
+
 // Farrow coefficients (Sec. II-B, Eq. 3-4): for tap k and segment s of the
 // fractional delay alpha in [s/S, (s+1)/S), h(k; alpha) ~ sum_q c[s][q][k] v^q
 // with v = 2 (alpha S - s) - 1, q < P. Interpolation at the Chebyshev nodes of
@@ -123,7 +235,7 @@ double fit_farrow(const msrc_room& R, int P, float* out) {
         const double alpha = (s + 0.5 * (v + 1.0)) / kFarrowSegs;
         double pw = 1.0;
         for (int q = 0; q < P; ++q) { V[i][q] = pw; pw *= v; }
-        V[i][P] = kernel_fn(R.d, alpha + k);
+        V[i][P] = tap_fn(R, k, alpha);
       }
       // Gaussian elimination with partial pivoting
       for (int col = 0; col < P; ++col) {
@@ -149,7 +261,7 @@ double fit_farrow(const msrc_room& R, int P, float* out) {
         const double alpha = (s + 0.5 * (v + 1.0)) / kFarrowSegs;
         double e = 0.0;
         for (int q = P - 1; q >= 0; --q) e = e * v + double(C(s, q, k + kL / 2));
-        worst = std::max(worst, std::fabs(e - kernel_fn(R.d, alpha + k)));
+        worst = std::max(worst, std::fabs(e - tap_fn(R, k, alpha)));
       }
     }
   return worst;
@@ -291,7 +403,8 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     if (s > 0) {
       const msrc_room* R0 = rooms[0];
       if (R->d.taps != R0->d.taps || R->d.window != R0->d.window ||
-          (R->d.window == 1 && R->d.kaiser_beta != R0->d.kaiser_beta))
+          (R->d.window == 1 && R->d.kaiser_beta != R0->d.kaiser_beta) ||
+          (R->d.window == 2 && (R->d.farrow_order != R0->d.farrow_order || R->d.passband != R0->d.passband)))
         return fail(MSRC_ERR_UNSUPPORTED, "rooms in one call must share taps and window");
     }
     SceneDev& S = P.scenes[s];
@@ -600,9 +713,13 @@ msrc_status msrc_create_room(const msrc_room_desc* desc, msrc_room_t* out) {
     return fail(MSRC_ERR_INVALID_ARG, "n_tiers must be in [1, %d]", MSRC_MAX_TIERS);
   if (d.taps < 8 || d.taps > kMaxTaps || (d.taps & 1))
     return fail(MSRC_ERR_INVALID_ARG, "taps must be even and in [8, %d]", kMaxTaps);
-  if (d.window != 0 && d.window != 1) return fail(MSRC_ERR_INVALID_ARG, "window must be 0 or 1");
+  if (d.window < 0 || d.window > 2) return fail(MSRC_ERR_INVALID_ARG, "window must be 0, 1 or 2");
   if (d.window == 1 && !(d.kaiser_beta >= 0.0 && d.kaiser_beta <= 20.0))
     return fail(MSRC_ERR_INVALID_ARG, "kaiser_beta must be in [0, 20]");
+  if (d.window == 2 && (d.farrow_order < 1 || d.farrow_order > kFarrowDeg))
+    return fail(MSRC_ERR_INVALID_ARG, "farrow_order must be in [1, %d]", kFarrowDeg);
+  if (d.window == 2 && !(d.passband >= 0.05 && d.passband <= 0.98))
+    return fail(MSRC_ERR_INVALID_ARG, "passband must be in [0.05, 0.98]");
   msrc_room* R = new (std::nothrow) msrc_room;
   if (!R) return fail(MSRC_ERR_INVALID_ARG, "out of host memory");
   std::memset(R, 0, sizeof(*R));
@@ -623,6 +740,10 @@ msrc_status msrc_create_room(const msrc_room_desc* desc, msrc_room_t* out) {
     }
   }
   R->kL = d.taps <= 16 ? 16 : (d.taps <= 32 ? 32 : 64);
+  if (d.window == 2 && !gls_design(d.taps, d.farrow_order, d.passband, R->gls)) {
+    delete R;
+    return fail(MSRC_ERR_UNSUPPORTED, "least-squares Farrow design failed (singular normal equations)");
+  }
   count_tiers(*R);
   R->fit_error = fit_farrow(*R, kFarrowCoef, &R->farrow[0][0][0]);
   R->fit_error_g = fit_farrow(*R, kGradCoef, &R->farrow_g[0][0][0]);

@@ -17,7 +17,7 @@ from typing import List, Sequence, Tuple
 import numpy as np
 
 LINE, CIRCLE, SPLINE = 0, 1, 2
-HANN, KAISER = 0, 1
+HANN, KAISER, FARROW_LS = 0, 1, 2
 RHO_INF = 2**31 - 1
 
 
@@ -32,6 +32,8 @@ class SceneSpec:
     taps: int = 32
     window: int = HANN
     kaiser_beta: float = 8.0
+    farrow_order: int = 4                   # window FARROW_LS: polynomial order
+    passband: float = 0.9                   # window FARROW_LS: passband edge / pi
     c: float = 343.0
     traj_kind: int = LINE
     traj: List[float] = field(default_factory=list)
@@ -228,7 +230,8 @@ def config5() -> SceneSpec:
 
 def small_scene(seed: int = 0, K: int = 4, fs: float = 16000.0, seconds: float = 0.25,
                 traj_kind: int = SPLINE, window: int = HANN, taps: int = 32,
-                tiers=None, n_mics: int = 1, vmax: float = 2.0) -> SceneSpec:
+                tiers=None, n_mics: int = 1, vmax: float = 2.0, farrow_order: int = 4,
+                passband: float = 0.9) -> SceneSpec:
     """A small random scene (parity tests at sizes the oracle finishes quickly)."""
     rng = np.random.default_rng(10_000 + seed)
     dims = tuple(float(v) for v in rng.uniform([3, 3, 2.5], [7, 6, 4]))
@@ -259,6 +262,7 @@ def small_scene(seed: int = 0, K: int = 4, fs: float = 16000.0, seconds: float =
     mics = mic[None, :] + np.array([[0.05 * i, -0.03 * i, 0.02 * i] for i in range(n_mics)])
     return SceneSpec(
         dims=dims, beta=beta, mics=mics, K=K, fs=fs, tiers=tiers, taps=taps, window=window,
+        farrow_order=farrow_order, passband=passband,
         traj_kind=traj_kind, traj=traj, n_ctrl=n_ctrl, duration=T,
         x=(rng.standard_normal(n) * 0.1).astype(np.float32), name=f"small scene {seed}")
 

@@ -51,6 +51,8 @@ def _desc(**kw):
     d.taps = kw.get("taps", 32)
     d.window = kw.get("window", 0)
     d.kaiser_beta = kw.get("kaiser_beta", 8.0)
+    d.farrow_order = kw.get("farrow_order", 4)
+    d.passband = kw.get("passband", 0.9)
     return d
 
 
@@ -65,7 +67,8 @@ def _create(**kw):
     dict(dims=[0.0, 4.0, 3.0]), dict(beta=[1.2] + [0.7] * 5), dict(c=-1.0), dict(fs=0.0),
     dict(K=61), dict(K=-1), dict(taps=31), dict(taps=4), dict(taps=66), dict(window=3),
     dict(tiers=[(1, 16000.0), (2**31 - 1, 700.0)]), dict(tiers=[]),
-    dict(window=1, kaiser_beta=-1.0)])
+    dict(window=1, kaiser_beta=-1.0), dict(window=2, farrow_order=0), dict(window=2, farrow_order=5),
+    dict(window=2, passband=0.01), dict(window=2, passband=0.99)])
 def test_create_room_rejects_bad_descriptions(bad):
     st, h = _create(**bad)
     assert st == _lib.ERR_INVALID_ARG
@@ -170,6 +173,20 @@ def test_farrow_fit_is_accurate(taps, window):
     # output error is ~3e-7 relative (errors of different taps do not align),
     # well inside the 1e-5 budget
     assert e.value < (2e-6 if taps < 16 else 1e-6)
+    lib.msrc_destroy_room(h)
+
+
+@pytest.mark.parametrize("taps,order,passband", [(8, 1, 0.5), (16, 3, 0.8), (32, 4, 0.9), (64, 2, 0.95)])
+def test_least_squares_design_is_held_exactly(taps, order, passband):
+    # a least-squares Farrow design of order <= 4 is itself a polynomial of
+    # degree <= 4 on every segment: the device table holds it up to float
+    # rounding
+    lib = _lib.load()
+    st, h = _create(taps=taps, window=2, farrow_order=order, passband=passband)
+    assert st == _lib.OK
+    e = ctypes.c_double()
+    assert lib.msrc_room_fit_error(h, ctypes.byref(e)) == _lib.OK
+    assert e.value < 1e-7
     lib.msrc_destroy_room(h)
 
 

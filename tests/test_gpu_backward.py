@@ -37,6 +37,7 @@ def _bwd(spec, dy, **kw):
     dict(seed=61, K=3, window=W.KAISER, taps=32, traj_kind=W.CIRCLE),
     dict(seed=62, K=3, window=W.HANN, taps=64, traj_kind=W.LINE, seconds=0.08),
     dict(seed=63, K=4, window=W.KAISER, taps=16, tiers=[(0, 16000.0), (3, 2000.0), (W.RHO_INF, 400.0)]),
+    dict(seed=71, K=3, window=W.FARROW_LS, taps=32, farrow_order=4, passband=0.9),
 ])
 def test_dx_matches_oracle_transpose(kw):
     spec = W.small_scene(**kw)
@@ -77,6 +78,8 @@ def test_dot_product_identity_on_gpu():
           tiers=[(1, 16000.0), (W.RHO_INF, 16000.0 / 12)]), [0, 3, 5, 8, 10]),
     (dict(seed=70, K=2, seconds=0.25, window=W.HANN, taps=16, traj_kind=W.CIRCLE,
           tiers=[(0, 16000.0), (W.RHO_INF, 10.0)]), [0, 1, 3, 4, 5]),
+    (dict(seed=72, K=2, seconds=0.03, window=W.FARROW_LS, taps=16, farrow_order=3, passband=0.8,
+          traj_kind=W.SPLINE), [0, 2, 4, 9]),
 ])
 def test_param_and_beta_gradients_match_complex_step(kw, ids):
     spec = W.small_scene(**kw)

@@ -48,6 +48,10 @@ def test_config1_full_parity():
     dict(seed=4, K=3, traj_kind=W.SPLINE, window=W.HANN, taps=8),
     dict(seed=5, K=6, traj_kind=W.SPLINE, window=W.HANN, taps=32, tiers=[(W.RHO_INF, 16000.0)]),
     dict(seed=6, K=4, traj_kind=W.SPLINE, window=W.KAISER, taps=24, tiers=[(0, 16000.0), (3, 2000.0), (W.RHO_INF, 400.0)]),
+    # least-squares Farrow designs (the oracle designs its own table)
+    dict(seed=8, K=4, traj_kind=W.SPLINE, window=W.FARROW_LS, taps=32, farrow_order=4, passband=0.9),
+    dict(seed=9, K=3, traj_kind=W.CIRCLE, window=W.FARROW_LS, taps=8, farrow_order=1, passband=0.5),
+    dict(seed=10, K=3, traj_kind=W.LINE, window=W.FARROW_LS, taps=64, farrow_order=3, passband=0.95),
 ])
 def test_small_scene_parity(kw):
     spec = W.small_scene(**kw)
