@@ -56,6 +56,10 @@ class _Scene(ctypes.Structure):
         ("n_ctrl", ctypes.c_int32),
         ("farrow_order", ctypes.c_int32),
         ("farrow", ctypes.POINTER(ctypes.c_double)),
+        ("arr_kind", ctypes.c_int32),
+        ("arr_n_ctrl", ctypes.c_int32),
+        ("arr_traj", ctypes.c_double * 48),
+        ("arr_duration", ctypes.c_double),
     ]
 
 
@@ -99,6 +103,9 @@ class Scene:
     (traj = control points, 3 per point; n_ctrl points; u = clamp(t/duration)).
     window: 0 Hann, 1 Kaiser(kaiser_beta), 2 a Farrow polynomial per tap with
     coefficients `farrow` (taps x (order + 1), e.g. from oracle.gls.design).
+    arr_kind: -1 static microphone; else the microphone moves as
+    mic + a(t) - a(0) with a(t) a trajectory of that kind (arr_traj,
+    arr_n_ctrl, arr_duration as for the source).
     tiers: list of (max_rho, knot_step_samples); an image goes to the first
     tier whose max_rho >= its reflection count, else to the last tier.
     """
@@ -118,6 +125,10 @@ class Scene:
     n_ctrl: int = 0
     duration: float = 1.0
     farrow: Optional[np.ndarray] = None
+    arr_kind: int = -1
+    arr_traj: Sequence[float] = field(default_factory=list)
+    arr_n_ctrl: int = 0
+    arr_duration: float = 1.0
 
     def to_c(self) -> _Scene:
         s = _Scene()
@@ -144,6 +155,12 @@ class Scene:
         s.window = int(self.window)
         s.traj_kind = int(self.traj_kind)
         s.n_ctrl = int(self.n_ctrl)
+        s.arr_kind = int(self.arr_kind)
+        s.arr_n_ctrl = int(self.arr_n_ctrl)
+        at = [0.0] * 48
+        at[: len(self.arr_traj)] = [float(v) for v in self.arr_traj]
+        s.arr_traj[:] = at
+        s.arr_duration = float(self.arr_duration)
         if self.window == 2:
             c = np.ascontiguousarray(self.farrow, dtype=np.float64)
             if c.ndim != 2 or c.shape[0] != self.taps:

@@ -69,16 +69,30 @@ def _deboor(ctrl, u):
     return d[3]
 
 
-def source(scene, t):
-    tr = scene.traj
-    if scene.traj_kind == 0:
+def _path(kind, tr, n_ctrl, duration, t):
+    if kind == 0:
         nrm = math.sqrt(tr[3] ** 2 + tr[4] ** 2 + tr[5] ** 2)
         return [tr[i] + tr[6] * t * tr[3 + i] / nrm for i in range(3)]
-    if scene.traj_kind == 1:
+    if kind == 1:
         ang = tr[5] + tr[4] * t / tr[3]
         return [tr[0] + tr[3] * math.cos(ang), tr[1] + tr[3] * math.sin(ang), tr[2]]
-    ctrl = [tr[3 * i: 3 * i + 3] for i in range(scene.n_ctrl)]
-    return _deboor(ctrl, min(1.0, max(0.0, t / scene.duration)))
+    ctrl = [tr[3 * i: 3 * i + 3] for i in range(n_ctrl)]
+    return _deboor(ctrl, min(1.0, max(0.0, t / duration)))
+
+
+def source(scene, t):
+    return _path(scene.traj_kind, scene.traj, scene.n_ctrl, scene.duration, t)
+
+
+def mic_at(scene, mic, t):
+    """Microphone position at time t: static, or moved with the array by
+    a(t) - a(0) when the scene has an array trajectory."""
+    kind = getattr(scene, "arr_kind", -1)
+    if kind < 0:
+        return list(mic)
+    a0 = _path(kind, scene.arr_traj, scene.arr_n_ctrl, scene.arr_duration, 0.0)
+    at = _path(kind, scene.arr_traj, scene.arr_n_ctrl, scene.arr_duration, t)
+    return [mic[d] + at[d] - a0[d] for d in range(3)]
 
 
 def _bessel_i0(v):
@@ -128,7 +142,8 @@ def synthesize(scene, x, n_out, mic_index=0):
 
     def dist(sign, off, t):
         q = source(scene, t)
-        return math.sqrt(sum((sign[d] * q[d] + off[d] - mic[d]) ** 2 for d in range(3)))
+        m = mic_at(scene, mic, t)
+        return math.sqrt(sum((sign[d] * q[d] + off[d] - m[d]) ** 2 for d in range(3)))
 
     half = scene.taps // 2
     y = []

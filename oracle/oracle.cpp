@@ -75,6 +75,10 @@ struct OracleScene {
   int32_t n_ctrl;         // number of spline control points
   int32_t farrow_order;   // window 2: polynomial order M
   const double* farrow;   // window 2: c[(k + L/2) * (M + 1) + q], tap weight sum_q c alpha^q
+  int32_t arr_kind;       // microphone motion: -1 static; else a trajectory a(t) (kinds as the
+  int32_t arr_n_ctrl;     //   source's) and the microphone sits at mic + a(t) - a(0)
+  double arr_traj[48];
+  double arr_duration;
 };
 
 }  // extern "C"
@@ -184,16 +188,51 @@ void source_position(const OracleScene& S, const Params<T>& P, double t, T out[3
   }
 }
 
+// Point of a trajectory of the source's kinds (line, circle, clamped cubic
+// B-spline) with real parameters, by the same formulas as source_position.
+void trajectory_point(int kind, const double* p, int n_ctrl, double duration, double t, double out[3]) {
+  if (kind == 0) {
+    const double nrm = std::sqrt(p[3] * p[3] + p[4] * p[4] + p[5] * p[5]);
+    for (int d = 0; d < 3; ++d) out[d] = p[d] + p[6] * t * p[3 + d] / nrm;
+  } else if (kind == 1) {
+    const double ang = p[5] + p[4] * t / p[3];
+    out[0] = p[0] + p[3] * std::cos(ang);
+    out[1] = p[1] + p[3] * std::sin(ang);
+    out[2] = p[2];
+  } else {
+    double u = std::min(1.0, std::max(0.0, t / duration));
+    const std::vector<double> kv = clamped_knots(n_ctrl);
+    for (int d = 0; d < 3; ++d) out[d] = 0.0;
+    for (int c = 0; c < n_ctrl; ++c) {
+      const double B = bspline_basis(c, 3, u, kv);
+      for (int d = 0; d < 3; ++d) out[d] += B * p[3 * c + d];
+    }
+  }
+}
+
+// Microphone position at time t: static, or carried by the array motion a(t)
+// as mic + a(t) - a(0).
+void mic_position(const OracleScene& S, double t, double out[3]) {
+  for (int d = 0; d < 3; ++d) out[d] = S.mic[d];
+  if (S.arr_kind < 0) return;
+  double a0[3], at[3];
+  trajectory_point(S.arr_kind, S.arr_traj, S.arr_n_ctrl, S.arr_duration, 0.0, a0);
+  trajectory_point(S.arr_kind, S.arr_traj, S.arr_n_ctrl, S.arr_duration, t, at);
+  for (int d = 0; d < 3; ++d) out[d] += at[d] - a0[d];
+}
+
 // Euclidean distance from image i to the microphone at time t (Sec. II-A).
 template <class T>
 T image_distance(const OracleScene& S, const Params<T>& P, const Image& im, double t) {
   T s[3];
   source_position(S, P, t, s);
+  double m[3];
+  mic_position(S, t, m);
   T acc = T(0.0);
   for (int d = 0; d < 3; ++d) {
     const double sigma = 1.0 - 2.0 * im.p[d];
     T r = sigma * s[d] + 2.0 * im.n[d] * S.dims[d];
-    T diff = r - S.mic[d];
+    T diff = r - m[d];
     acc += diff * diff;
   }
   return std::sqrt(acc);
