@@ -110,6 +110,18 @@ msrc_status msrc_destroy_room(msrc_room_t room);
 msrc_status msrc_set_trajectory(msrc_room_t room, const msrc_traj_desc* traj,
                                 const double* mics_xyz, int32_t n_mics);
 
+/* Moves the microphones rigidly with an array trajectory a(t) (same kinds and
+ * parameters as the source's msrc_traj_desc): microphone m sits at
+ * mics_xyz[m] + a(t) - a(0), mics_xyz as given to msrc_set_trajectory (their
+ * positions at t = 0). Image distances use the microphone position at each knot
+ * time (Sec. II-A distance |r_i(t) - mic|, with a moving receiver). traj = NULL
+ * makes the array static again. Validation (1 ms grid, up to the source
+ * duration): every microphone strictly inside the room and at least 0.1 m from
+ * the source, source speed plus array speed below c (below c/2 for
+ * msrc_synthesize_backward). On failure the room keeps its previous state.
+ * Reverse mode differentiates with respect to the source trajectory only. */
+msrc_status msrc_set_array_trajectory(msrc_room_t room, const msrc_traj_desc* traj);
+
 /* Replaces the six wall reflection coefficients of a room (beta: 6 doubles in
  * [0, 1], host memory); the Farrow fit and the trajectory are kept. Used by
  * optimisation loops that update the walls between forward calls. */

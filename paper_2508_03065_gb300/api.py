@@ -61,6 +61,8 @@ class Room:
         room = cls(spec.dims, spec.beta, spec.fs, spec.K, spec.tiers, spec.taps, spec.window,
                    spec.kaiser_beta, spec.c, spec.farrow_order, spec.passband)
         room.set_trajectory(spec.traj_kind, spec.traj, spec.duration, spec.mics, spec.n_ctrl)
+        if getattr(spec, "arr_kind", -1) >= 0:
+            room.set_array_trajectory(spec.arr_kind, spec.arr_traj, spec.arr_duration, spec.arr_n_ctrl)
         return room
 
     def set_trajectory(self, kind: int, params: Sequence[float], duration: float, mics,
@@ -81,6 +83,24 @@ class Room:
         self.traj_kind, self.n_ctrl, self.duration = int(kind), int(n_ctrl), float(duration)
         self.mics = m.copy()
         self.params = np.array(p, np.float64)
+
+    def set_array_trajectory(self, kind: Optional[int], params: Sequence[float] = (), duration: float = 1.0,
+                             n_ctrl: int = 0) -> None:
+        """Moves the microphones rigidly along a trajectory a(t): microphone m
+        sits at its set_trajectory position + a(t) - a(0). kind=None makes
+        the array static again."""
+        lib = _lib.load()
+        if kind is None:
+            _lib.check(lib.msrc_set_array_trajectory(self._h, None))
+            return
+        t = _lib.TrajDesc()
+        t.kind = int(kind)
+        t.n_ctrl = int(n_ctrl)
+        p = [0.0] * 48
+        p[: len(params)] = [float(v) for v in params]
+        t.params[:] = p
+        t.duration_s = float(duration)
+        _lib.check(lib.msrc_set_array_trajectory(self._h, ctypes.byref(t)))
 
     def set_reflection(self, beta) -> None:
         lib = _lib.load()

@@ -44,6 +44,8 @@ struct msrc_room {
   msrc_traj_desc traj;
   double mics[MSRC_MAX_MICS][3];
   int32_t n_mics;
+  bool arr_moving;          // microphones carried by `arr`: m + a(t) - a(0)
+  msrc_traj_desc arr;
   double validated_until;  // trajectory checked on [0, validated_until]
   double max_speed;        // largest speed seen on that range (m/s, 1 ms steps)
 };
@@ -326,34 +328,54 @@ void host_source(const msrc_traj_desc& T, double t, double out[3]) {
   }
 }
 
+// Checks the source path and the microphones on a 1 ms grid up to t_end: the
+// source strictly inside the room, every microphone (carried by the array
+// motion when there is one) strictly inside and at least 0.1 m from the
+// source, and the source speed plus the array speed (a bound on the rate of
+// change of every image distance) below c. Records that largest rate.
 msrc_status validate_traj_range(msrc_room& R, double t_end) {
   if (t_end <= R.validated_until) return MSRC_OK;
   const double dt = 1e-3;
   const long steps = long(std::ceil(t_end / dt));
-  double prev[3];
+  double prev[3], aprev[3] = {0.0, 0.0, 0.0}, a0[3] = {0.0, 0.0, 0.0};
   double vmax = 0.0;
   host_source(R.traj, 0.0, prev);
+  if (R.arr_moving) {
+    host_source(R.arr, 0.0, a0);
+    std::memcpy(aprev, a0, sizeof(a0));
+  }
   for (long i = 0; i <= steps; ++i) {
     const double t = std::min(i * dt, t_end);
-    double s[3];
+    double s[3], a[3] = {0.0, 0.0, 0.0};
     host_source(R.traj, t, s);
+    if (R.arr_moving) host_source(R.arr, t, a);
     for (int d = 0; d < 3; ++d)
       if (!(s[d] > 0.0 && s[d] < R.d.dims[d]))
         return fail(MSRC_ERR_INVALID_ARG, "trajectory leaves the room at t=%.4f s", t);
     for (int m = 0; m < R.n_mics; ++m) {
       double q = 0;
-      for (int d = 0; d < 3; ++d) q += (s[d] - R.mics[m][d]) * (s[d] - R.mics[m][d]);
+      for (int d = 0; d < 3; ++d) {
+        const double md = R.mics[m][d] + (R.arr_moving ? a[d] - a0[d] : 0.0);
+        if (!(md > 0.0 && md < R.d.dims[d]))
+          return fail(MSRC_ERR_INVALID_ARG, "microphone %d leaves the room at t=%.4f s", m, t);
+        q += (s[d] - md) * (s[d] - md);
+      }
       if (std::sqrt(q) < 0.1)
         return fail(MSRC_ERR_INVALID_ARG, "trajectory within 0.1 m of microphone %d at t=%.4f s", m, t);
     }
     if (i > 0) {
-      double q = 0;
-      for (int d = 0; d < 3; ++d) q += (s[d] - prev[d]) * (s[d] - prev[d]);
-      if (std::sqrt(q) >= R.d.c * dt)
-        return fail(MSRC_ERR_INVALID_ARG, "trajectory speed reaches c near t=%.4f s", t);
-      vmax = std::max(vmax, std::sqrt(q) / dt);
+      double q = 0, qa = 0;
+      for (int d = 0; d < 3; ++d) {
+        q += (s[d] - prev[d]) * (s[d] - prev[d]);
+        qa += (a[d] - aprev[d]) * (a[d] - aprev[d]);
+      }
+      const double v = (std::sqrt(q) + std::sqrt(qa)) / dt;
+      if (v >= R.d.c)
+        return fail(MSRC_ERR_INVALID_ARG, "source plus array speed reaches c near t=%.4f s", t);
+      vmax = std::max(vmax, v);
     }
     std::memcpy(prev, s, sizeof(prev));
+    std::memcpy(aprev, a, sizeof(aprev));
   }
   R.validated_until = t_end;
   R.max_speed = vmax;
@@ -371,7 +393,7 @@ struct Plan {
   // byte offsets in the workspace
   size_t off_desc = 0, off_keys_in = 0, off_keys_out = 0, off_vals_in = 0, off_vals_out = 0;
   size_t off_sort = 0, sort_bytes = 0, off_code = 0, off_gain = 0, off_knots = 0;
-  size_t off_z = 0, off_zp = 0, off_part = 0, fwd_bytes = 0, desc_bytes = 0;
+  size_t off_z = 0, off_zp = 0, off_part = 0, fwd_bytes = 0, desc_bytes = 0, off_arr = 0;
   // reverse mode
   bool backward = false;
   int64_t dxb_floats = 0;
@@ -394,6 +416,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   for (auto& v : P.prefix) v.assign(n + 1, 0);
   int64_t img_acc = 0, knot_acc = 0, z_acc = 0, part_acc = 0;
   int64_t dxb_acc = 0, kslot_acc = 0, bpart_acc = 0;
+  bool any_moving = false;
   for (int s = 0; s < n; ++s) {
     msrc_room* R = rooms[s];
     if (!R) return fail(MSRC_ERR_INVALID_ARG, "room %d is null", s);
@@ -419,6 +442,14 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     std::memcpy(S.traj, R->traj.params, sizeof(S.traj));
     S.traj_kind = R->traj.kind;
     S.n_ctrl = R->traj.n_ctrl;
+    if (R->arr_moving) {
+      S.arr_moving = 1;
+      std::memcpy(S.arr_params, R->arr.params, sizeof(S.arr_params));
+      S.arr_kind = R->arr.kind;
+      S.arr_n_ctrl = R->arr.n_ctrl;
+      S.arr_duration = R->arr.duration_s;
+      any_moving = true;
+    }
     S.K = R->d.max_order;
     S.n_mics = R->n_mics;
     S.n_tiers = R->d.n_tiers;
@@ -555,6 +586,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.off_code = off; off = align256(off + 4 * I);
   P.off_gain = off; off = align256(off + 4 * I);
   P.off_knots = off; off = align256(off + 24 * size_t(knot_acc));
+  P.off_arr = off; off = align256(off + (any_moving ? 24 * size_t(knot_acc) : 0));
   P.off_z = off; off = align256(off + 16 * size_t(z_acc));
   // forward: power 4 of the degree-4 rows; reverse mode: powers 4..5 of the
   // degree-5 rows the gradient kernel reads (zq holds powers 0..3 either way)
@@ -591,6 +623,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.img_code = reinterpret_cast<uint32_t*>(ws + P.off_code);
   a.p.img_gain = reinterpret_cast<float*>(ws + P.off_gain);
   a.p.knot_pos = reinterpret_cast<double*>(ws + P.off_knots);
+  a.p.arr_pos = reinterpret_cast<double*>(ws + P.off_arr);
   a.p.zq = reinterpret_cast<float4*>(ws + P.off_z);
   a.p.zp = P.backward ? nullptr : reinterpret_cast<float*>(ws + P.off_zp);
   a.p.zg = P.backward ? reinterpret_cast<float2*>(ws + P.off_zp) : nullptr;
@@ -764,11 +797,8 @@ msrc_status msrc_destroy_room(msrc_room_t room) {
   return MSRC_OK;
 }
 
-msrc_status msrc_set_trajectory(msrc_room_t room, const msrc_traj_desc* traj, const double* mics,
-                                int32_t n_mics) {
-  if (!room || !traj || !mics) return fail(MSRC_ERR_INVALID_ARG, "null argument");
-  if (n_mics < 1 || n_mics > MSRC_MAX_MICS)
-    return fail(MSRC_ERR_INVALID_ARG, "n_mics must be in [1, %d]", MSRC_MAX_MICS);
+namespace {
+msrc_status check_traj_params(const msrc_traj_desc* traj) {
   if (!(traj->duration_s > 0.0) || !std::isfinite(traj->duration_s))
     return fail(MSRC_ERR_INVALID_ARG, "duration must be positive");
   for (int i = 0; i < 48; ++i)
@@ -785,6 +815,17 @@ msrc_status msrc_set_trajectory(msrc_room_t room, const msrc_traj_desc* traj, co
   } else {
     return fail(MSRC_ERR_INVALID_ARG, "unknown trajectory kind %d", traj->kind);
   }
+  return MSRC_OK;
+}
+}  // namespace
+
+msrc_status msrc_set_trajectory(msrc_room_t room, const msrc_traj_desc* traj, const double* mics,
+                                int32_t n_mics) {
+  if (!room || !traj || !mics) return fail(MSRC_ERR_INVALID_ARG, "null argument");
+  if (n_mics < 1 || n_mics > MSRC_MAX_MICS)
+    return fail(MSRC_ERR_INVALID_ARG, "n_mics must be in [1, %d]", MSRC_MAX_MICS);
+  const msrc_status ps = check_traj_params(traj);
+  if (ps != MSRC_OK) return ps;
   for (int m = 0; m < n_mics; ++m)
     for (int d = 0; d < 3; ++d) {
       const double v = mics[3 * m + d];
@@ -803,6 +844,29 @@ msrc_status msrc_set_trajectory(msrc_room_t room, const msrc_traj_desc* traj, co
   if (s != MSRC_OK) {
     *room = saved;
     return s;
+  }
+  return MSRC_OK;
+}
+
+msrc_status msrc_set_array_trajectory(msrc_room_t room, const msrc_traj_desc* traj) {
+  if (!room) return fail(MSRC_ERR_INVALID_ARG, "null room");
+  msrc_room saved = *room;
+  if (!traj) {
+    room->arr_moving = false;
+  } else {
+    const msrc_status ps = check_traj_params(traj);
+    if (ps != MSRC_OK) return ps;
+    room->arr_moving = true;
+    room->arr = *traj;
+  }
+  room->validated_until = -1.0;
+  room->max_speed = 0.0;
+  if (room->has_traj) {
+    msrc_status s = validate_traj_range(*room, room->traj.duration_s);
+    if (s != MSRC_OK) {
+      *room = saved;
+      return s;
+    }
   }
   return MSRC_OK;
 }

@@ -59,7 +59,7 @@ static_assert((kDxSlots * sizeof(float)) % 16 == 0 && (kBwRecCap * sizeof(float2
 static_assert((kFarrowSegs * kGradWcap * sizeof(float2)) % 16 == 0, "gradient window alignment");
 constexpr size_t kDxSmem = size_t(kDxSlots) * (sizeof(float4) + sizeof(float)) +
                            size_t(kBwRecCap) * sizeof(float2) + size_t(kBwBlock) * sizeof(int4) +
-                           size_t(kBwTile + 4 + 2 * kBwBlock) * sizeof(float4);
+                           size_t(2 * (kBwTile + 4) + 3 * kBwBlock) * sizeof(float4);
 static_assert(kBwRecCap % 2 == 0, "16-byte alignment of the image records");
 static_assert(kGradSmem <= 232448 && kDxSmem <= 232448, "shared memory per CTA");
 
@@ -219,9 +219,10 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
   float4* unit_s = reinterpret_cast<float4*>(img_s + kBwBlock);        // [image][knot]
   float4* bw_s = unit_s + kBwUnitCap;                                   // 2 per image
   float4* u_s = sm;                                                     // prologue scratch
-  float4* anc_s = sm + kBwTile + 4;
+  float4* um_s = sm + kBwTile + 4;
+  float4* anc_s = um_s + kBwTile + 4;
   float* seg_s = reinterpret_cast<float*>(sm);                          // knot scan scratch (after the loop)
-  static_assert(kBwTile + 4 + 2 * kBwBlock <= kFarrowSegs * kGradWcap, "prologue scratch");
+  static_assert(2 * (kBwTile + 4) + 3 * kBwBlock <= kFarrowSegs * kGradWcap, "prologue scratch");
   static_assert(6 * kSegCap * (kBwTile / 32) <= 4 * kFarrowSegs * kGradWcap, "scan scratch");
   __shared__ int s_item;
   __shared__ float s_red[2][kBwThreads / 32];
@@ -242,16 +243,26 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     const float fsc = S.fsc;
 
     float tmin, tmax;
-    item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, anc_s, &tmin, &tmax);
+    item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, &tmin, &tmax);
     // unit vectors (sigma o Delta) / d of every image at every knot of the tile
+    // (sigma o Delta_j = w + u - sigma o u_m with a moving array)
     for (int pidx = threadIdx.x; pidx < g.cnt * g.nk; pidx += kBwThreads) {
       const int ib = pidx / g.nk, jj = pidx - ib * g.nk;
       const float4 A = anc_s[2 * ib];
       const float4 U = u_s[jj];
-      float phi, d;
-      knot_increment(A, U, fsc, 0.0f, &phi, &d);
+      float phi, d, ex = 0.f, ey = 0.f, ez = 0.f;
+      if (S.arr_moving) {
+        const float4 sg = anc_s[2 * g.cnt + ib];
+        const float4 Um = um_s[jj];
+        knot_increment_moving(A, sg, U, Um, fsc, 0.0f, &phi, &d);
+        ex = sg.x * Um.x;
+        ey = sg.y * Um.y;
+        ez = sg.z * Um.z;
+      } else {
+        knot_increment(A, U, fsc, 0.0f, &phi, &d);
+      }
       const float inv = __fdividef(1.0f, d);
-      unit_s[pidx] = make_float4((A.x + U.x) * inv, (A.y + U.y) * inv, (A.z + U.z) * inv, 0.0f);
+      unit_s[pidx] = make_float4((A.x + U.x - ex) * inv, (A.y + U.y - ey) * inv, (A.z + U.z - ez) * inv, 0.0f);
     }
     // gains and dbeta_i/dbeta_w / (4 pi) of the block's images
     {
@@ -435,7 +446,8 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
   float2* rec_s = reinterpret_cast<float2*>(wp_s + kDxSlots);
   int4* img_s = reinterpret_cast<int4*>(rec_s + kBwRecCap);
   float4* u_s = reinterpret_cast<float4*>(img_s + kBwBlock);              // record scratch
-  float4* anc_s = u_s + kBwTile + 4;
+  float4* um_s = u_s + kBwTile + 4;
+  float4* anc_s = um_s + kBwTile + 4;                                      // 3 x kBwBlock
   __shared__ int s_item;
   __shared__ float s_red[2][kBwThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -470,7 +482,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
         __syncthreads();  // records of the previous block / tile are no longer read
         const ItemGeom g = item_geometry(S, (item0 + b) * S.n_tiles + tile, kBwTile);
         float lo, hi;
-        item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, anc_s, &lo, &hi);
+        item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, &lo, &hi);
         tmin = fminf(tmin, lo);
         tmax = fmaxf(tmax, hi);
       }
@@ -509,7 +521,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
           if (!reuse) {
             float lo, hi;
             __syncthreads();  // the previous block's records are no longer read
-            item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, anc_s, &lo, &hi);
+            item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, &lo, &hi);
           }
           __syncthreads();  // records and the zeroed window are complete
           if (width <= kDxWcap)

@@ -3,7 +3,8 @@
 //                  8 parities) with a sort key (scene, tier, distance)
 //   (radix sort)   images ordered by key
 //   k_image_table  packed image codes and gains beta_i / (4 pi) * fs / c
-//   k_traj_knots   source position s(t_j) at every knot of every tier, FP64
+//   k_traj_knots   source position s(t_j) (and the array displacement a(t_j) - a(0)
+//                  when the microphones move) at every knot of every tier, FP64
 //                  (Sec. II-C: trajectory sampled at the tier's spatial rate)
 #include <cub/device/device_radix_sort.cuh>
 
@@ -21,14 +22,16 @@ __device__ __forceinline__ int locate(const KernelArgs& a, const int64_t* prefix
   return s;
 }
 
-// Source position s(t) (FP64). Spline: clamped uniform cubic B-spline by de
-// Boor's algorithm on the knot vector {0,0,0,0, 1/m, ..., (m-1)/m, 1,1,1,1}.
-__device__ void source_position(const SceneDev& S, double t, double out[3]) {
-  const double* p = S.traj;
-  if (S.traj_kind == 0) {
+// Point of a trajectory (FP64): line p0 + v t dir/|dir|, circle
+// centre + R (cos, sin, 0)(theta0 + v t / R), or clamped uniform cubic B-spline
+// by de Boor's algorithm on the knot vector {0,0,0,0, 1/m, ..., (m-1)/m, 1,1,1,1}
+// with u = clamp(t / duration, 0, 1).
+__device__ void trajectory_point(int kind, const double* p, int n_ctrl, double duration, double t,
+                                 double out[3]) {
+  if (kind == 0) {
     const double inv = 1.0 / sqrt(p[3] * p[3] + p[4] * p[4] + p[5] * p[5]);
     for (int d = 0; d < 3; ++d) out[d] = p[d] + p[6] * t * p[3 + d] * inv;
-  } else if (S.traj_kind == 1) {
+  } else if (kind == 1) {
     const double ang = p[5] + p[4] * t / p[3];
     double sn, cs;
     sincos(ang, &sn, &cs);
@@ -36,8 +39,8 @@ __device__ void source_position(const SceneDev& S, double t, double out[3]) {
     out[1] = p[1] + p[3] * sn;
     out[2] = p[2];
   } else {
-    const int m = S.n_ctrl - 3;  // segments
-    double u = t / S.duration;
+    const int m = n_ctrl - 3;  // segments
+    double u = t / duration;
     u = fmin(1.0, fmax(0.0, u));
     int span = min(int(u * m), m - 1);  // segment index
     // knot i of the clamped vector: clamp((i - 3) / m, 0, 1)
@@ -55,6 +58,21 @@ __device__ void source_position(const SceneDev& S, double t, double out[3]) {
       }
     for (int c = 0; c < 3; ++c) out[c] = dd[3][c];
   }
+}
+
+// Source position s(t).
+__device__ void source_position(const SceneDev& S, double t, double out[3]) {
+  trajectory_point(S.traj_kind, S.traj, S.n_ctrl, S.duration, t, out);
+}
+
+// Displacement of the microphone array a(t) - a(0) (zero for a static array).
+__device__ void array_displacement(const SceneDev& S, double t, double out[3]) {
+  out[0] = out[1] = out[2] = 0.0;
+  if (!S.arr_moving) return;
+  double a0[3], at[3];
+  trajectory_point(S.arr_kind, S.arr_params, S.arr_n_ctrl, S.arr_duration, 0.0, a0);
+  trajectory_point(S.arr_kind, S.arr_params, S.arr_n_ctrl, S.arr_duration, t, at);
+  for (int d = 0; d < 3; ++d) out[d] = at[d] - a0[d];
 }
 
 __device__ __forceinline__ int tier_of(const SceneDev& S, int rho) {
@@ -94,11 +112,12 @@ __global__ void k_enumerate(const __grid_constant__ KernelArgs a) {
   for (int d = 0; d < 3; ++d) rho += abs(2 * n[d] - p[d]);
   const int tier = tier_of(S, rho);
   // distance to the first microphone at the middle of the trajectory
-  double sp[3];
+  double sp[3], ad[3];
   source_position(S, 0.5 * S.duration, sp);
+  array_displacement(S, 0.5 * S.duration, ad);
   double acc = 0.0;
   for (int d = 0; d < 3; ++d) {
-    const double v = (1.0 - 2.0 * p[d]) * sp[d] + 2.0 * n[d] * S.dims[d] - S.mics[0][d];
+    const double v = (1.0 - 2.0 * p[d]) * sp[d] + 2.0 * n[d] * S.dims[d] - (S.mics[0][d] + ad[d]);
     acc += v * v;
   }
   const double dist = fmin(sqrt(acc), 4095.0);
@@ -143,6 +162,14 @@ __global__ void k_traj_knots(const __grid_constant__ KernelArgs a) {
   out[0] = sp[0];
   out[1] = sp[1];
   out[2] = sp[2];
+  if (S.arr_moving) {
+    double ad[3];
+    array_displacement(S, time, ad);
+    double* o2 = a.p.arr_pos + 3 * (S.knot_base[t] + j);
+    o2[0] = ad[0];
+    o2[1] = ad[1];
+    o2[2] = ad[2];
+  }
 }
 
 }  // namespace

@@ -157,11 +157,12 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
                 "every shared array starts on a 16-byte boundary");
   // prologue scratch aliases the z window (used before the window is staged)
   float4* u_s = smem4;
-  float4* anc_s = u_s + kThreads * kChunks + 4;                          // 2 x kBlock
+  float4* um_s = u_s + kThreads * kChunks + 4;                           // moving array
+  float4* anc_s = um_s + kThreads * kChunks + 4;                         // 3 x kBlock
   __shared__ int s_item;
   __shared__ float s_red[2][kThreads / 32];
   constexpr int kTile = kThreads * kChunks;
-  static_assert(kTile + 4 + 2 * kBlock <= kFarrowSegs * kWcap, "prologue scratch");
+  static_assert(2 * (kTile + 4) + 3 * kBlock <= kFarrowSegs * kWcap, "prologue scratch");
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
 
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
 
     // --- delay knots of the block over the tile (records in shared memory)
     float tmin, tmax;
-    item_records<kThreads>(a, S, g, rec_s, img_s, u_s, anc_s, &tmin, &tmax);
+    item_records<kThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, &tmin, &tmax);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));

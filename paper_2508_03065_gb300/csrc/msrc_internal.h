@@ -46,6 +46,10 @@ struct SceneDev {
   double mics[MSRC_MAX_MICS][3];
   double traj[48];
   int32_t traj_kind, n_ctrl;
+  // microphone array motion: microphones at mics[m] + a(t) - a(0)
+  double arr_params[48];
+  double arr_duration;
+  int32_t arr_moving, arr_kind, arr_n_ctrl;
   int32_t K, n_mics, n_tiers, n_images;
   int32_t tier_max_rho[MSRC_MAX_TIERS];
   int32_t tier_step[MSRC_MAX_TIERS];       // knot spacing N_t (samples)
@@ -122,6 +126,7 @@ struct DevicePtrs {
   uint32_t* img_code;            // packed lattice triple and parity
   float* img_gain;               // beta_i / (4 pi)
   double* knot_pos;              // s(t_j), 3 doubles per knot
+  double* arr_pos;               // a(t_j) - a(0), 3 doubles per knot (scenes with a moving array)
   float4* zq;                    // prefiltered powers 0..3, [scene rows][segment][column]
   float* zp;                     // prefiltered power 4, same indexing
   float2* zg;                    // reverse mode: powers 4..5 of the degree-5 rows (zq holds 0..3)

@@ -75,6 +75,22 @@ __device__ __forceinline__ void knot_increment(const float4 A, const float4 U, f
   *d = A.w + dd;
 }
 
+// knot_increment with a moving array: the vector changes by v = sigma o u - u_m,
+// so q = |Delta_j|^2 - |Delta_a|^2 = 2 Delta_a.v + |v|^2
+//      = (2 w.u + |u|^2) - 2 sum_d sigma_d u_m,d (w_d + u_d) + |u_m|^2,
+// w = sigma o Delta_a (A.xyz), sigma in sg.xyz, u in U, u_m in Um.
+__device__ __forceinline__ void knot_increment_moving(const float4 A, const float4 sg, const float4 U,
+                                                      const float4 Um, float fsc, float fa, float* phi,
+                                                      float* d) {
+  float q = fmaf(2.0f, fmaf(A.x, U.x, fmaf(A.y, U.y, A.z * U.z)), U.w);
+  const float c = fmaf(sg.x * Um.x, A.x + U.x, fmaf(sg.y * Um.y, A.y + U.y, sg.z * Um.z * (A.z + U.z)));
+  q = fmaf(-2.0f, c, q) + Um.w;
+  const float den = A.w + sqrtf(fmaf(A.w, A.w, q));
+  const float dd = q / den;
+  *phi = fmaf(dd, fsc, fa);
+  *d = A.w + dd;
+}
+
 // Records of the item's images over its intervals, in shared memory.
 // With tau = d fs / c, D_a = floor(tau) at the anchor knot jf (FP64) and
 // phi_j = tau_j - D_a, the delay between knots j and j + 1 is
@@ -85,11 +101,15 @@ __device__ __forceinline__ void knot_increment(const float4 A, const float4 U, f
 //   img_s[ib]            = {I = n_jf - D_a, D_a - 1/(2S) (float), gain (float), 0}
 // so that Y(n) = Psi_j + sigma_j r = S (n - tau(n) - n_j + I + jj N_t) - 1/2 up to
 // the integer read position, and tau(n) = (D_a - 1/(2S)) - Y / S.
-// u_s (nk entries) and anc_s (2 * cnt entries) are scratch. Returns this
-// thread's min / max of tau over its knots (window bounds of the item).
+// u_s and um_s (nk entries each) and anc_s (3 * cnt entries) are scratch. With
+// a moving array the knots also carry the array displacement: per knot
+// u_m = a(t_j) - a(t_jf) and the image-to-microphone vector changes by
+// sigma o u - u_m. Returns this thread's min / max of tau over its knots
+// (window bounds of the item).
 template <int kThreads>
 __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
-                             int4* img_s, float4* u_s, float4* anc_s, float* tmin_out, float* tmax_out) {
+                             int4* img_s, float4* u_s, float4* um_s, float4* anc_s, float* tmin_out,
+                             float* tmax_out) {
   const double* kp = a.p.knot_pos + 3 * (S.knot_base[g.t] + g.jf);
   const double sa0 = kp[0], sa1 = kp[1], sa2 = kp[2];
   for (int jj = threadIdx.x; jj < g.nk; jj += kThreads) {
@@ -98,22 +118,34 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     const float uz = float(kp[3 * jj + 2] - sa2);
     u_s[jj] = make_float4(ux, uy, uz, fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
   }
+  const bool moving = S.arr_moving != 0;
+  double ma[3] = {S.mics[g.mic][0], S.mics[g.mic][1], S.mics[g.mic][2]};
+  if (moving) {
+    const double* ap = a.p.arr_pos + 3 * (S.knot_base[g.t] + g.jf);
+    for (int d = 0; d < 3; ++d) ma[d] += ap[d];
+    for (int jj = threadIdx.x; jj < g.nk; jj += kThreads) {
+      const float mx = float(ap[3 * jj] - ap[0]);
+      const float my = float(ap[3 * jj + 1] - ap[1]);
+      const float mz = float(ap[3 * jj + 2] - ap[2]);
+      um_s[jj] = make_float4(mx, my, mz, fmaf(mx, mx, fmaf(my, my, mz * mz)));
+    }
+  }
   const double fs_c = S.fs_over_c;
   const uint32_t* codes = a.p.img_code + S.img_base + S.tier_first[g.t] + g.img0;
   const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
-  const double* mic = S.mics[g.mic];
   for (int ib = threadIdx.x; ib < g.cnt; ib += kThreads) {
     int n[3], p[3];
     unpack_image(codes[ib], n, p);
     const double s0 = 1.0 - 2.0 * p[0], s1 = 1.0 - 2.0 * p[1], s2 = 1.0 - 2.0 * p[2];
-    const double D0 = s0 * sa0 + 2.0 * n[0] * S.dims[0] - mic[0];
-    const double D1 = s1 * sa1 + 2.0 * n[1] * S.dims[1] - mic[1];
-    const double D2 = s2 * sa2 + 2.0 * n[2] * S.dims[2] - mic[2];
+    const double D0 = s0 * sa0 + 2.0 * n[0] * S.dims[0] - ma[0];
+    const double D1 = s1 * sa1 + 2.0 * n[1] * S.dims[1] - ma[1];
+    const double D2 = s2 * sa2 + 2.0 * n[2] * S.dims[2] - ma[2];
     const double da = fast_sqrt(fma(D0, D0, fma(D1, D1, D2 * D2)));
     const double tau = da * fs_c;
     const double Dfl = floor(tau);
     anc_s[2 * ib] = make_float4(float(s0 * D0), float(s1 * D1), float(s2 * D2), float(da));
     anc_s[2 * ib + 1] = make_float4(float(tau - Dfl), float(Dfl), 0.0f, 0.0f);
+    anc_s[2 * g.cnt + ib] = make_float4(float(s0), float(s1), float(s2), 0.0f);
     img_s[ib] = make_int4(g.jf * g.N - int(Dfl), __float_as_int(float(Dfl) - 0.5f / kFarrowSegs),
                           __float_as_int(__ldg(gain + ib)), 0);
   }
@@ -129,8 +161,14 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     const float4 A = anc_s[2 * ib];
     const float4 A2 = anc_s[2 * ib + 1];
     float phi0, phi1, d0, d1;
-    knot_increment(A, u_s[jj], fsc, A2.x, &phi0, &d0);
-    knot_increment(A, u_s[jj + 1], fsc, A2.x, &phi1, &d1);
+    if (moving) {
+      const float4 sg = anc_s[2 * g.cnt + ib];
+      knot_increment_moving(A, sg, u_s[jj], um_s[jj], fsc, A2.x, &phi0, &d0);
+      knot_increment_moving(A, sg, u_s[jj + 1], um_s[jj + 1], fsc, A2.x, &phi1, &d1);
+    } else {
+      knot_increment(A, u_s[jj], fsc, A2.x, &phi0, &d0);
+      knot_increment(A, u_s[jj + 1], fsc, A2.x, &phi1, &d1);
+    }
     rec_s[jj * g.cnt + ib] = make_float2(fmaf(-float(kFarrowSegs), phi0, -0.5f), (phi0 - phi1) * sN);
     tmin = fminf(tmin, A2.y + fminf(phi0, phi1));
     tmax = fmaxf(tmax, A2.y + fmaxf(phi0, phi1));

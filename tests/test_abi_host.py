@@ -202,3 +202,18 @@ def test_knot_spacing_from_paper_rates():
         _lib.load().msrc_destroy_room(h)
     st, _ = _create(fs=16000.0, tiers=[(1, 16000.0), (2**31 - 1, 16000.0 / 3200.5)])
     assert st == _lib.ERR_INVALID_ARG
+
+
+def test_array_trajectory_validation():
+    # microphones carried out of the room, onto the source, or faster than
+    # sound are refused and leave the room unchanged; None makes it static
+    from paper_2508_03065_gb300 import api
+    spec = W.small_scene(seed=5, K=2, seconds=0.25)
+    room = api.Room.from_spec(spec)
+    with pytest.raises(RuntimeError):
+        room.set_array_trajectory(W.LINE, [0, 0, 0, 1.0, 0.0, 0.0, 40.0], spec.duration)
+    with pytest.raises(RuntimeError):
+        room.set_array_trajectory(W.LINE, [0, 0, 0, 1.0, 0.0, 0.0, 400.0], spec.duration)
+    room.set_array_trajectory(W.CIRCLE, [0, 0, 0, 0.1, 0.3, 0.0], spec.duration)
+    room.set_array_trajectory(None)
+
