@@ -62,9 +62,9 @@ def parse():
     ap.add_argument("--tile-config", type=int, default=None, help="synthesis tile configuration id")
     ap.add_argument("--batched-scenes", type=int, default=256,
                     help="scenes of the batched comparison (0 disables it)")
-    ap.add_argument("--sections", default="batched,backward,filters",
-                    help="extra measurements in the JSON line: batched, backward, array, filters")
-    ap.add_argument("--only", default=None, choices=["backward", "array", "batched", "filters"],
+    ap.add_argument("--sections", default="batched,backward,filters,moving_array",
+                    help="extra measurements in the JSON line: batched, backward, array, filters, moving_array")
+    ap.add_argument("--only", default=None, choices=["backward", "array", "batched", "filters", "moving_array"],
                     help="run one extra section alone (profiling captures) and print it")
     return ap.parse_args()
 
@@ -320,6 +320,8 @@ def run_gpu(args):
             line["array"] = run_array(args, torch, api, W)
         if "filters" in sections:
             line["filters"] = run_filters(args, torch, api, W)
+        if "moving_array" in sections:
+            line["moving_array"] = run_moving_array(args, torch, api, W)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, args.cpu_sample)
     if rank == 0:
@@ -466,6 +468,37 @@ def run_filters(args, torch, api, W):
     return out
 
 
+def run_moving_array(args, torch, api, W):
+    """The order-20 scene with the microphone rising at 0.3 m/s
+    (receiver motion on top of the circling source) vs the same scene with a
+    still microphone."""
+    from dataclasses import replace
+
+    base = W.config2()
+    x = torch.from_numpy(base.x).cuda()
+    ws = api.Workspace("cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, kw in (("still", {}), ("moving", dict(arr_kind=W.LINE, arr_traj=[0.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.3],
+                                                     arr_duration=base.duration))):
+        spec = replace(base, **kw)
+        room = api.Room.from_spec(spec)
+        work = room.image_count()[0] * spec.n_in * room.n_mics
+        y = api.synthesize([room], [x], workspace=ws)[0]
+        for _ in range(3):
+            api.synthesize([room], [x], out=[y], workspace=ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            api.synthesize([room], [x], out=[y], workspace=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        out[name] = {"ms": ms, "value": work / (ms * 1e-3), "unit": UNIT}
+    return out
+
+
 def launches_per_step():
     # enumerate, image table, trajectory knots, prefilter, synthesis, reduction
     # + the radix sort's kernels (histogram, exclusive sum, 5 onesweep passes
@@ -479,7 +512,8 @@ def run_only(args):
     from paper_2508_03065_gb300 import api
     from paper_2508_03065_gb300 import workloads as W
 
-    fn = {"backward": run_backward, "array": run_array, "batched": run_batched, "filters": run_filters}[args.only]
+    fn = {"backward": run_backward, "array": run_array, "batched": run_batched, "filters": run_filters,
+          "moving_array": run_moving_array}[args.only]
     print(json.dumps({args.only: fn(args, torch, api, W)}), flush=True)
     return 0
 
