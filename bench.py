@@ -62,9 +62,10 @@ def parse():
     ap.add_argument("--tile-config", type=int, default=None, help="synthesis tile configuration id")
     ap.add_argument("--batched-scenes", type=int, default=256,
                     help="scenes of the batched comparison (0 disables it)")
-    ap.add_argument("--sections", default="batched,backward,filters,moving_array",
-                    help="extra measurements in the JSON line: batched, backward, array, filters, moving_array")
-    ap.add_argument("--only", default=None, choices=["backward", "array", "batched", "filters", "moving_array"],
+    ap.add_argument("--sections", default="batched,backward,filters,moving_array,e1",
+                    help="extra measurements in the JSON line: batched, backward, array, filters, moving_array, e1")
+    ap.add_argument("--only", default=None,
+                    choices=["backward", "array", "batched", "filters", "moving_array", "e1"],
                     help="run one extra section alone (profiling captures) and print it")
     return ap.parse_args()
 
@@ -322,6 +323,8 @@ def run_gpu(args):
             line["filters"] = run_filters(args, torch, api, W)
         if "moving_array" in sections:
             line["moving_array"] = run_moving_array(args, torch, api, W)
+        if "e1" in sections:
+            line["e1"] = run_e1(args, torch, api, W)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(spec, args.cpu_sample)
     if rank == 0:
@@ -499,6 +502,36 @@ def run_moving_array(args, torch, api, W):
     return out
 
 
+def run_e1(args, torch, api, W):
+    """The paper's first experiment (Sec. III): a receding 1 kHz tone simulated
+    by the method (every image on 5 Hz knots) and by static-response splicing
+    at 25 Hz (hard switch and linear cross-fade); phase and gain steps at the
+    25 Hz frame boundaries, and the time of each."""
+    from paper_2508_03065_gb300 import motion_metrics, splicing
+
+    spec = W.receding_tone()
+    x = torch.from_numpy(spec.x).cuda()
+    room = api.Room.from_spec(spec)
+    frame = int(spec.fs / 25.0)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        y = fn()
+        torch.cuda.synchronize()
+        return y, (time.perf_counter() - t0) * 1e3
+
+    out = {"workload": spec.name}
+    for name, fn in (("method", lambda: api.synthesize([room], [x])[0]),
+                     ("splice_hard_25hz", lambda: splicing.static_splice(spec, x, 25.0, crossfade=False)),
+                     ("splice_crossfade_25hz", lambda: splicing.static_splice(spec, x, 25.0, crossfade=True))):
+        y, ms = timed(fn)
+        m = motion_metrics.continuity(y[0].cpu().numpy(), spec.fs, 1000.0, frame, skip=3000)
+        out[name] = {"ms": ms, **{k: round(v, 6) for k, v in m.items()}}
+    return out
+
+
 def launches_per_step():
     # enumerate, image table, trajectory knots, prefilter, synthesis, reduction
     # + the radix sort's kernels (histogram, exclusive sum, 5 onesweep passes
@@ -513,7 +546,7 @@ def run_only(args):
     from paper_2508_03065_gb300 import workloads as W
 
     fn = {"backward": run_backward, "array": run_array, "batched": run_batched, "filters": run_filters,
-          "moving_array": run_moving_array}[args.only]
+          "moving_array": run_moving_array, "e1": run_e1}[args.only]
     print(json.dumps({args.only: fn(args, torch, api, W)}), flush=True)
     return 0
 

@@ -122,6 +122,12 @@ msrc_status msrc_set_trajectory(msrc_room_t room, const msrc_traj_desc* traj,
  * Reverse mode differentiates with respect to the source trajectory only. */
 msrc_status msrc_set_array_trajectory(msrc_room_t room, const msrc_traj_desc* traj);
 
+/* Source positions s(t_k) of the room's trajectory at n_times times (seconds,
+ * host array) into out (n_times x 3 doubles, host), by the same formulas the
+ * knot kernel uses (Sec. II-C trajectory). Host only; used by tools that need
+ * positions along the path (e.g. static responses sampled along it). */
+msrc_status msrc_trajectory_positions(msrc_room_t room, const double* times, int64_t n_times, double* out);
+
 /* Replaces the six wall reflection coefficients of a room (beta: 6 doubles in
  * [0, 1], host memory); the Farrow fit and the trajectory are kept. Used by
  * optimisation loops that update the walls between forward calls. */

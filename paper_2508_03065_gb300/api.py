@@ -102,6 +102,15 @@ class Room:
         t.duration_s = float(duration)
         _lib.check(lib.msrc_set_array_trajectory(self._h, ctypes.byref(t)))
 
+    def positions(self, times) -> np.ndarray:
+        """Source positions (n x 3) of the trajectory at the given times (s)."""
+        lib = _lib.load()
+        t = np.ascontiguousarray(np.asarray(times, np.float64).reshape(-1))
+        out = np.zeros((t.size, 3), np.float64)
+        _lib.check(lib.msrc_trajectory_positions(self._h, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                 t.size, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
     def set_reflection(self, beta) -> None:
         lib = _lib.load()
         b = np.ascontiguousarray(np.asarray(beta, np.float64).reshape(6))

@@ -848,6 +848,13 @@ msrc_status msrc_set_trajectory(msrc_room_t room, const msrc_traj_desc* traj, co
   return MSRC_OK;
 }
 
+msrc_status msrc_trajectory_positions(msrc_room_t room, const double* times, int64_t n_times, double* out) {
+  if (!room || (n_times > 0 && (!times || !out)) || n_times < 0) return fail(MSRC_ERR_INVALID_ARG, "null argument");
+  if (!room->has_traj) return fail(MSRC_ERR_STATE, "room has no trajectory");
+  for (int64_t i = 0; i < n_times; ++i) host_source(room->traj, times[i], out + 3 * i);
+  return MSRC_OK;
+}
+
 msrc_status msrc_set_array_trajectory(msrc_room_t room, const msrc_traj_desc* traj) {
   if (!room) return fail(MSRC_ERR_INVALID_ARG, "null room");
   msrc_room saved = *room;
