@@ -342,6 +342,10 @@ def run_batched(args, torch, api, W):
     rooms = [api.Room.from_spec(sp) for sp in specs]
     xs = [torch.from_numpy(sp.x).cuda() for sp in specs]
     stream = torch.cuda.Stream()
+    # the tile shape for this scene mix (both arms use it), picked by the
+    # autotuner; the previous choice is restored afterwards
+    with tempfile.TemporaryDirectory() as tmp:
+        cfg = api.autotune(rooms, xs, reps=2, cache_path=os.path.join(tmp, "autotune.json"))
     batch = api.Batch(rooms, xs, stream=stream)
     work = batch.work()
     for _ in range(2):
@@ -370,7 +374,9 @@ def run_batched(args, torch, api, W):
         e1.record(stream)
         stream.synchronize()
     t_single = e0.elapsed_time(e1) / reps
-    return {"scenes": len(specs), "image_samples": work, "batched_ms": t_batched, "single_loop_ms": t_single,
+    api.set_tile_config(args.tile_config or 0)
+    return {"scenes": len(specs), "image_samples": work, "tile_config": cfg, "batched_ms": t_batched,
+            "single_loop_ms": t_single,
             "batched_value": work / (t_batched * 1e-3), "single_value": work / (t_single * 1e-3),
             "speedup": t_single / t_batched, "unit": UNIT,
             "how": "one persistent synthesis launch over all scenes, CUDA-graph replay, vs one msrc_synthesize "

@@ -46,7 +46,7 @@ constexpr int kBwRecCap = 3328;                 // records (image x interval)
 constexpr int kBwUnitCap = 3584;                // unit vectors (image x knot)
 constexpr int kBwBlock = 256;                   // images per block at most
 constexpr int kGradWcap = 1408;                 // shared z window of the gradient kernel
-constexpr int kDxWcap = 1792;                   // shared w window of the dx kernel
+constexpr int kDxWcap = 1760;                   // shared w window of the dx kernel
 constexpr int kSegCap = 33;                     // knot intervals touched by 32 consecutive samples
 
 constexpr size_t kGradSmem = size_t(kFarrowSegs) * kGradWcap * (sizeof(float4) + sizeof(float2)) +
@@ -59,7 +59,8 @@ static_assert((kDxSlots * sizeof(float)) % 16 == 0 && (kBwRecCap * sizeof(float2
 static_assert((kFarrowSegs * kGradWcap * sizeof(float2)) % 16 == 0, "gradient window alignment");
 constexpr size_t kDxSmem = size_t(kDxSlots) * (sizeof(float4) + sizeof(float)) +
                            size_t(kBwRecCap) * sizeof(float2) + size_t(kBwBlock) * sizeof(int4) +
-                           size_t(2 * (kBwTile + 4) + 3 * kBwBlock) * sizeof(float4);
+                           size_t(2 * (kBwTile + 4) + 3 * kBwBlock) * sizeof(float4) +
+                           size_t(kBwRecCap + kBwBlock) * sizeof(float);
 static_assert(kBwRecCap % 2 == 0, "16-byte alignment of the image records");
 static_assert(kGradSmem <= 232448 && kDxSmem <= 232448, "shared memory per CTA");
 
@@ -221,8 +222,10 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
   float4* u_s = sm;                                                     // prologue scratch
   float4* um_s = sm + kBwTile + 4;
   float4* anc_s = um_s + kBwTile + 4;
+  float* phi_s = reinterpret_cast<float*>(anc_s + 3 * kBwBlock);       // kBwRecCap + kBwBlock
   float* seg_s = reinterpret_cast<float*>(sm);                          // knot scan scratch (after the loop)
-  static_assert(2 * (kBwTile + 4) + 3 * kBwBlock <= kFarrowSegs * kGradWcap, "prologue scratch");
+  static_assert(4 * (2 * (kBwTile + 4) + 3 * kBwBlock) + kBwRecCap + kBwBlock <= 4 * kFarrowSegs * kGradWcap,
+                "prologue scratch");
   static_assert(6 * kSegCap * (kBwTile / 32) <= 4 * kFarrowSegs * kGradWcap, "scan scratch");
   __shared__ int s_item;
   __shared__ float s_red[2][kBwThreads / 32];
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     const float fsc = S.fsc;
 
     float tmin, tmax;
-    item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, &tmin, &tmax);
+    item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax);
     // unit vectors (sigma o Delta) / d of every image at every knot of the tile
     // (sigma o Delta_j = w + u - sigma o u_m with a moving array)
     for (int pidx = threadIdx.x; pidx < g.cnt * g.nk; pidx += kBwThreads) {
@@ -448,6 +451,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
   float4* u_s = reinterpret_cast<float4*>(img_s + kBwBlock);              // record scratch
   float4* um_s = u_s + kBwTile + 4;
   float4* anc_s = um_s + kBwTile + 4;                                      // 3 x kBwBlock
+  float* phi_s = reinterpret_cast<float*>(anc_s + 3 * kBwBlock);          // kBwRecCap + kBwBlock
   __shared__ int s_item;
   __shared__ float s_red[2][kBwThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -482,7 +486,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
         __syncthreads();  // records of the previous block / tile are no longer read
         const ItemGeom g = item_geometry(S, (item0 + b) * S.n_tiles + tile, kBwTile);
         float lo, hi;
-        item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, &lo, &hi);
+        item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &lo, &hi);
         tmin = fminf(tmin, lo);
         tmax = fmaxf(tmax, hi);
       }
@@ -521,7 +525,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
           if (!reuse) {
             float lo, hi;
             __syncthreads();  // the previous block's records are no longer read
-            item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, &lo, &hi);
+            item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &lo, &hi);
           }
           __syncthreads();  // records and the zeroed window are complete
           if (width <= kDxWcap)

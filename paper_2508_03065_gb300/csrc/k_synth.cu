@@ -159,10 +159,12 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
   float4* u_s = smem4;
   float4* um_s = u_s + kThreads * kChunks + 4;                           // moving array
   float4* anc_s = um_s + kThreads * kChunks + 4;                         // 3 x kBlock
+  float* phi_s = reinterpret_cast<float*>(anc_s + 3 * kBlock);           // kRecCap + kBlock
   __shared__ int s_item;
   __shared__ float s_red[2][kThreads / 32];
   constexpr int kTile = kThreads * kChunks;
-  static_assert(2 * (kTile + 4) + 3 * kBlock <= kFarrowSegs * kWcap, "prologue scratch");
+  static_assert(4 * (2 * (kTile + 4) + 3 * kBlock) + kRecCap + kBlock <= 4 * kFarrowSegs * kWcap,
+                "prologue scratch");
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
 
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
 
     // --- delay knots of the block over the tile (records in shared memory)
     float tmin, tmax;
-    item_records<kThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, &tmin, &tmax);
+    item_records<kThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
@@ -309,7 +311,9 @@ cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
   X(4, 512, 2, 2432, 4096, 256, 8)       \
   X(5, 512, 1, 2432, 4096, 256, 8)       \
   X(6, 512, 3, 2432, 4096, 256, 4)       \
-  X(7, 512, 2, 2432, 4096, 256, 16)
+  X(7, 512, 2, 2432, 4096, 256, 16)      \
+  X(8, 512, 3, 1792, 8192, 256, 8)       \
+  X(9, 512, 2, 1792, 8192, 256, 8)
 
 static const TileConfig kConfigs[] = {
 #define MSRC_ROW(id, th, ch, wc, rc, bl, un) {th, ch, wc, rc, bl},

@@ -101,15 +101,16 @@ __device__ __forceinline__ void knot_increment_moving(const float4 A, const floa
 //   img_s[ib]            = {I = n_jf - D_a, D_a - 1/(2S) (float), gain (float), 0}
 // so that Y(n) = Psi_j + sigma_j r = S (n - tau(n) - n_j + I + jj N_t) - 1/2 up to
 // the integer read position, and tau(n) = (D_a - 1/(2S)) - Y / S.
-// u_s and um_s (nk entries each) and anc_s (3 * cnt entries) are scratch. With
+// u_s and um_s (nk entries each), anc_s (3 * cnt entries) and phi_s (cnt * nk
+// floats, at most the record capacity plus the block size) are scratch. With
 // a moving array the knots also carry the array displacement: per knot
 // u_m = a(t_j) - a(t_jf) and the image-to-microphone vector changes by
 // sigma o u - u_m. Returns this thread's min / max of tau over its knots
 // (window bounds of the item).
 template <int kThreads>
 __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
-                             int4* img_s, float4* u_s, float4* um_s, float4* anc_s, float* tmin_out,
-                             float* tmax_out) {
+                             int4* img_s, float4* u_s, float4* um_s, float4* anc_s, float* phi_s,
+                             float* tmin_out, float* tmax_out) {
   const double* kp = a.p.knot_pos + 3 * (S.knot_base[g.t] + g.jf);
   const double sa0 = kp[0], sa1 = kp[1], sa2 = kp[2];
   for (int jj = threadIdx.x; jj < g.nk; jj += kThreads) {
@@ -150,28 +151,31 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
                           __float_as_int(__ldg(gain + ib)), 0);
   }
   __syncthreads();
+  // relative delay phi at every knot of every image (once per knot), then the
+  // records from consecutive knots
   const float fsc = S.fsc;
-  const float sN = float(kFarrowSegs) / float(g.N);
-  const int nrec = g.nk - 1;
-  const int total = g.cnt * nrec;
+  const int nk = g.nk;
   float tmin = 3.0e38f, tmax = -3.0e38f;
-  for (int pidx = threadIdx.x; pidx < total; pidx += kThreads) {
-    const int ib = pidx / nrec;
-    const int jj = pidx - ib * nrec;
+  for (int pidx = threadIdx.x; pidx < g.cnt * nk; pidx += kThreads) {
+    const int ib = pidx / nk;
+    const int jj = pidx - ib * nk;
     const float4 A = anc_s[2 * ib];
     const float4 A2 = anc_s[2 * ib + 1];
-    float phi0, phi1, d0, d1;
-    if (moving) {
-      const float4 sg = anc_s[2 * g.cnt + ib];
-      knot_increment_moving(A, sg, u_s[jj], um_s[jj], fsc, A2.x, &phi0, &d0);
-      knot_increment_moving(A, sg, u_s[jj + 1], um_s[jj + 1], fsc, A2.x, &phi1, &d1);
-    } else {
-      knot_increment(A, u_s[jj], fsc, A2.x, &phi0, &d0);
-      knot_increment(A, u_s[jj + 1], fsc, A2.x, &phi1, &d1);
-    }
+    float phi, d;
+    if (moving) knot_increment_moving(A, anc_s[2 * g.cnt + ib], u_s[jj], um_s[jj], fsc, A2.x, &phi, &d);
+    else knot_increment(A, u_s[jj], fsc, A2.x, &phi, &d);
+    phi_s[pidx] = phi;
+    tmin = fminf(tmin, A2.y + phi);
+    tmax = fmaxf(tmax, A2.y + phi);
+  }
+  __syncthreads();
+  const float sN = float(kFarrowSegs) / float(g.N);
+  const int nrec = nk - 1;
+  for (int pidx = threadIdx.x; pidx < g.cnt * nrec; pidx += kThreads) {
+    const int ib = pidx / nrec;
+    const int jj = pidx - ib * nrec;
+    const float phi0 = phi_s[ib * nk + jj], phi1 = phi_s[ib * nk + jj + 1];
     rec_s[jj * g.cnt + ib] = make_float2(fmaf(-float(kFarrowSegs), phi0, -0.5f), (phi0 - phi1) * sN);
-    tmin = fminf(tmin, A2.y + fminf(phi0, phi1));
-    tmax = fmaxf(tmax, A2.y + fmaxf(phi0, phi1));
   }
   *tmin_out = tmin;
   *tmax_out = tmax;
