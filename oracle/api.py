@@ -60,6 +60,8 @@ class _Scene(ctypes.Structure):
         ("arr_n_ctrl", ctypes.c_int32),
         ("arr_traj", ctypes.c_double * 48),
         ("arr_duration", ctypes.c_double),
+        ("tier_up", ctypes.c_int32 * 4),
+        ("up_halfwidth", ctypes.c_int32),
     ]
 
 
@@ -106,8 +108,11 @@ class Scene:
     arr_kind: -1 static microphone; else the microphone moves as
     mic + a(t) - a(0) with a(t) a trajectory of that kind (arr_traj,
     arr_n_ctrl, arr_duration as for the source).
-    tiers: list of (max_rho, knot_step_samples); an image goes to the first
-    tier whose max_rho >= its reflection count, else to the last tier.
+    tiers: list of (max_rho, knot_step_samples[, upsample]); an image goes to
+    the first tier whose max_rho >= its reflection count, else to the last
+    tier. upsample U > 1 (dividing the step) interpolates the knots' distances
+    band-limited to U virtual knots per interval (Kaiser(8)-windowed sinc over
+    2 up_halfwidth knots, normalised), then linearly.
     """
 
     dims: Sequence[float]
@@ -129,6 +134,7 @@ class Scene:
     arr_traj: Sequence[float] = field(default_factory=list)
     arr_n_ctrl: int = 0
     arr_duration: float = 1.0
+    up_halfwidth: int = 4
 
     def to_c(self) -> _Scene:
         s = _Scene()
@@ -146,11 +152,17 @@ class Scene:
         s.n_tiers = len(self.tiers)
         rho = [0] * 4
         step = [1] * 4
-        for t, (r, n) in enumerate(self.tiers):
-            rho[t] = int(min(r, 2**31 - 1))
-            step[t] = int(n)
+        up = [1] * 4
+        for t, tier in enumerate(self.tiers):
+            rho[t] = int(min(tier[0], 2**31 - 1))
+            step[t] = int(tier[1])
+            up[t] = int(tier[2]) if len(tier) > 2 else 1
+            if up[t] > 1 and step[t] % up[t]:
+                raise ValueError("upsampling factor must divide the knot step")
         s.tier_max_rho[:] = rho
         s.tier_step[:] = step
+        s.tier_up[:] = up
+        s.up_halfwidth = int(self.up_halfwidth)
         s.taps = int(self.taps)
         s.window = int(self.window)
         s.traj_kind = int(self.traj_kind)

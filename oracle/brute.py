@@ -123,7 +123,8 @@ def synthesize(scene, x, n_out, mic_index=0):
     `scene` is a workload scene description (tiers given as knot rates in Hz)."""
     dims = scene.dims
     mic = [float(v) for v in scene.mics[mic_index]]
-    tiers = [(r, int(round(scene.fs / rate))) for r, rate in scene.tiers]
+    tiers = [(t[0], int(round(scene.fs / t[1])), int(t[2]) if len(t) > 2 else 1) for t in scene.tiers]
+    Q = getattr(scene, "up_halfwidth", 4)
     imgs = []
     for sign, off, hits in mirror_images(dims, 2 * scene.K + 3):
         n, _ = lattice_of(sign, off, dims)
@@ -133,27 +134,46 @@ def synthesize(scene, x, n_out, mic_index=0):
         for w in range(6):
             beta *= scene.beta[w] ** hits[w]
         rho = sum(hits)
-        step = tiers[-1][1]
-        for max_rho, st in tiers:
+        step, up = tiers[-1][1], tiers[-1][2]
+        for max_rho, st, u in tiers:
             if rho <= max_rho:
-                step = st
+                step, up = st, u
                 break
-        imgs.append((sign, off, beta, step))
+        imgs.append((sign, off, beta, step, up))
 
     def dist(sign, off, t):
         q = source(scene, t)
         m = mic_at(scene, mic, t)
         return math.sqrt(sum((sign[d] * q[d] + off[d] - m[d]) ** 2 for d in range(3)))
 
+    def kaiser8(u):
+        z = max(0.0, 1.0 - (u / Q) ** 2)
+        return _bessel_i0(8.0 * math.sqrt(z)) / _bessel_i0(8.0)
+
+    def point(sign, off, step, up, k):
+        # distance at interpolation point k (sample k * step / up)
+        if up == 1:
+            return dist(sign, off, k * step / scene.fs)
+        j0 = math.floor(k / up)
+        x = k / up
+        ws, acc = 0.0, 0.0
+        for j in range(j0 - Q + 1, j0 + Q + 1):
+            u = x - j
+            h = (1.0 if u == 0 else math.sin(math.pi * u) / (math.pi * u)) * kaiser8(u)
+            ws += h
+            acc += h * dist(sign, off, j * step / scene.fs)
+        return acc / ws
+
     half = scene.taps // 2
     y = []
     for n in range(n_out):
         acc = 0.0
-        for sign, off, beta, step in imgs:
-            j0 = (n // step) * step
-            frac = (n - j0) / step
-            d0 = dist(sign, off, j0 / scene.fs)
-            d1 = dist(sign, off, (j0 + step) / scene.fs)
+        for sign, off, beta, step, up in imgs:
+            sp = step // up
+            k0 = n // sp
+            frac = (n - k0 * sp) / sp
+            d0 = point(sign, off, step, up, k0)
+            d1 = point(sign, off, step, up, k0 + 1)
             d = d0 + frac * (d1 - d0)
             t = n - d * scene.fs / scene.c
             m0 = math.floor(t)

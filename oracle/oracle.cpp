@@ -79,6 +79,10 @@ struct OracleScene {
   int32_t arr_n_ctrl;     //   source's) and the microphone sits at mic + a(t) - a(0)
   double arr_traj[48];
   double arr_duration;
+  int32_t tier_up[4];     // knot upsampling of tier t: <= 1 linear between knots; U > 1: the
+                          //   distance at U virtual knots per interval from a band-limited
+                          //   interpolation of the knots, then linear between virtual knots
+  int32_t up_halfwidth;   // half-width Q (knots) of that interpolation kernel
 };
 
 }  // extern "C"
@@ -294,17 +298,57 @@ inline double xval(const double* x, long Ns, long m) { return (m >= 0 && m < Ns)
 // Delay tau_i(n) (in samples), gain A_i(n) and distance d_i(n) at output sample
 // n: knots of image i's tier at n_j = j N_t, exact distances there, linear
 // interpolation of the distance in between (Sec. II-C, "Fast Architecture").
+//
+// Band-limited knot upsampling (tiers with U > 1, Sec. II-C: the distance is a
+// band-limited signal sampled at the knots, recovered by an upsampler): the
+// distance at virtual knot k (sample k N/U) is sum_j w_j d_j over the knots j
+// with |k/U - j| < Q, w_j = h(k/U - j) / sum_i h(k/U - i), h(u) = sinc(u) times
+// a Kaiser window over [-Q, Q] (shape 8, I0 by its power series); between
+// virtual knots it is linear. At a knot (k multiple of U) the weights reduce to
+// that knot alone.
+double bessel_i0_series(double x) {
+  double sum = 1.0, term = 1.0;
+  for (int j = 1; j < 80; ++j) {
+    term *= (x * x / 4.0) / (double(j) * double(j));
+    sum += term;
+  }
+  return sum;
+}
+
+template <class T>
+T upsampled_distance(const OracleScene& S, const Params<T>& P, const Image& im, long N, int U, long k) {
+  const int Q = S.up_halfwidth > 0 ? S.up_halfwidth : 4;
+  const double kBeta = 8.0;
+  const long j0 = (k >= 0) ? k / U : -((-k + U - 1) / U);  // floor(k / U)
+  const double x = double(k) / U;
+  double w[64];
+  double wsum = 0.0;
+  for (int i = 0; i < 2 * Q; ++i) {
+    const double u = x - double(j0 - Q + 1 + i);
+    const double sincv = (u == 0.0) ? 1.0 : std::sin(kPi * u) / (kPi * u);
+    const double z = std::max(0.0, 1.0 - (u / Q) * (u / Q));
+    w[i] = sincv * bessel_i0_series(kBeta * std::sqrt(z)) / bessel_i0_series(kBeta);
+    wsum += w[i];
+  }
+  T acc = T(0.0);
+  for (int i = 0; i < 2 * Q; ++i)
+    acc += (w[i] / wsum) * image_distance(S, P, im, double((j0 - Q + 1 + i) * N) / S.fs);
+  return acc;
+}
+
 template <class T>
 void delay_gain(const OracleScene& S, const Params<T>& P, const Image& im, long n,
                 T* tau, T* gain, T* dist) {
-  const long N = S.tier_step[im.tier];
+  const long Nc = S.tier_step[im.tier];
+  const int U = S.tier_up[im.tier] > 1 ? S.tier_up[im.tier] : 1;
+  const long N = Nc / U;  // spacing of the interpolated points
   const long j = n / N;
   const long nj = j * N;
   const double s = double(n - nj) / double(N);
-  T dj = image_distance(S, P, im, double(nj) / S.fs);
+  T dj = (U == 1) ? image_distance(S, P, im, double(nj) / S.fs) : upsampled_distance(S, P, im, Nc, U, j);
   T d = dj;
   if (s != 0.0) {
-    T dj1 = image_distance(S, P, im, double(nj + N) / S.fs);
+    T dj1 = (U == 1) ? image_distance(S, P, im, double(nj + N) / S.fs) : upsampled_distance(S, P, im, Nc, U, j + 1);
     d = dj + s * (dj1 - dj);
   }
   *dist = d;

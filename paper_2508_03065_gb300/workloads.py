@@ -28,7 +28,7 @@ class SceneSpec:
     mics: np.ndarray                        # (n_mics, 3)
     K: int                                  # image set |n|_1 <= K
     fs: float
-    tiers: Sequence[Tuple[int, float]]      # (max reflection count, knot rate in Hz)
+    tiers: Sequence[Tuple]                  # (max reflection count, knot rate in Hz[, upsampling U])
     taps: int = 32
     window: int = HANN
     kaiser_beta: float = 8.0
@@ -52,8 +52,12 @@ class SceneSpec:
         return int(self.x.size)
 
     def tier_steps(self):
-        """(max_rho, knot spacing in samples) per tier."""
-        return [(r, int(round(self.fs / rate))) for r, rate in self.tiers]
+        """(max_rho, knot spacing in samples[, upsampling factor]) per tier."""
+        out = []
+        for tier in self.tiers:
+            step = (tier[0], int(round(self.fs / tier[1])))
+            out.append(step + (int(tier[2]),) if len(tier) > 2 else step)
+        return out
 
 
 def image_count(K: int) -> int:
