@@ -79,6 +79,16 @@ typedef struct {
   double kaiser_beta;        /* Kaiser shape (used when window == 1), 0..20 */
   int32_t farrow_order;      /* window 2: polynomial order M, 1..4 */
   double passband;           /* window 2: passband edge as a fraction of pi, 0.05..0.98 */
+  int32_t tier_upsample[4];  /* knot upsampler of each tier (Sec. II-C "recovered using an
+                                upsampling algorithm"): 0 or 1 = linear interpolation of the
+                                distance between knots; U > 1 (dividing fs / rate, at most 512) =
+                                the distance at U virtual knots per interval from a band-limited
+                                interpolation of the knots (sinc times a Kaiser window of shape 8
+                                over 2 upsample_halfwidth knots, weights normalised to sum 1),
+                                then linear between virtual knots. Knots before t = 0 and after
+                                the end follow the trajectory's extension (line and circle
+                                continue, the spline clamps). Forward synthesis only. */
+  int32_t upsample_halfwidth;/* Q, half-width of that kernel in knots: 0 (= 4) or 1..8 */
 } msrc_room_desc;
 
 /* Source trajectory s(t) (Sec. II-C: a band-limited trajectory p(n)). */
@@ -223,7 +233,9 @@ msrc_status msrc_autotune(const msrc_room_t* rooms, int32_t n_rooms, const float
 
 /* Reads (and clears) the device-side error word of a workspace used by the
  * calls above; synchronises `stream`. *flags receives a bit set:
- * 1 = a bounded wait gave up, 2 = a shared-memory window had to be clamped. */
+ * 1 = a bounded wait gave up, 2 = a shared-memory window had to be clamped,
+ * 4 = a block's band-limited knot scratch did not fit (its records were
+ * skipped; the planner sizes blocks so that this does not happen). */
 msrc_status msrc_workspace_errors(void* workspace_dev, void* stream, uint32_t* flags);
 
 /* Number of images of a room and, per tier, how many fall in it (host only).

@@ -33,6 +33,8 @@ class RoomDesc(ctypes.Structure):
         ("kaiser_beta", ctypes.c_double),
         ("farrow_order", ctypes.c_int32),
         ("passband", ctypes.c_double),
+        ("tier_upsample", ctypes.c_int32 * 4),
+        ("upsample_halfwidth", ctypes.c_int32),
     ]
 
 

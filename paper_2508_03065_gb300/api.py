@@ -26,9 +26,12 @@ class Room:
     """A shoebox room with its image-source settings, trajectory and microphones."""
 
     def __init__(self, dims, beta, fs, max_order, tiers, taps=32, window=0, kaiser_beta=8.0,
-                 c=343.0, farrow_order=4, passband=0.9):
-        """window: 0 Hann- or 1 Kaiser-windowed sinc taps, 2 a least-squares
-        Farrow design of order `farrow_order` fitted up to `passband` * pi."""
+                 c=343.0, farrow_order=4, passband=0.9, upsample_halfwidth=4):
+        """tiers: (max reflection count, knot rate in Hz[, upsampling factor U]);
+        U > 1 recovers the distance between knots band-limited (see
+        msrc_room_desc.tier_upsample). window: 0 Hann- or 1 Kaiser-windowed sinc
+        taps, 2 a least-squares Farrow design of order `farrow_order` fitted up
+        to `passband` * pi."""
         lib = _lib.load()
         d = _lib.RoomDesc()
         d.dims[:] = [float(v) for v in dims]
@@ -39,11 +42,15 @@ class Room:
         d.n_tiers = len(tiers)
         rho = [0] * 4
         rate = [1.0] * 4
-        for t, (r, hz) in enumerate(tiers):
-            rho[t] = int(min(r, 2**31 - 1))
-            rate[t] = float(hz)
+        up = [1] * 4
+        for t, tier in enumerate(tiers):
+            rho[t] = int(min(tier[0], 2**31 - 1))
+            rate[t] = float(tier[1])
+            up[t] = int(tier[2]) if len(tier) > 2 else 1
         d.tier_max_rho[:] = rho
         d.tier_rate_hz[:] = rate
+        d.tier_upsample[:] = up
+        d.upsample_halfwidth = int(upsample_halfwidth)
         d.taps = int(taps)
         d.window = int(window)
         d.kaiser_beta = float(kaiser_beta)
@@ -59,7 +66,8 @@ class Room:
     @classmethod
     def from_spec(cls, spec) -> "Room":
         room = cls(spec.dims, spec.beta, spec.fs, spec.K, spec.tiers, spec.taps, spec.window,
-                   spec.kaiser_beta, spec.c, spec.farrow_order, spec.passband)
+                   spec.kaiser_beta, spec.c, spec.farrow_order, spec.passband,
+                   getattr(spec, "up_halfwidth", 4))
         room.set_trajectory(spec.traj_kind, spec.traj, spec.duration, spec.mics, spec.n_ctrl)
         if getattr(spec, "arr_kind", -1) >= 0:
             room.set_array_trajectory(spec.arr_kind, spec.arr_traj, spec.arr_duration, spec.arr_n_ctrl)
@@ -165,12 +173,13 @@ def _workspace(device) -> Workspace:
     return _default_ws[key]
 
 
-def workspace_size(rooms: Sequence[Room], n_in: Sequence[int], n_out: Sequence[int]):
+def workspace_size(rooms: Sequence[Room], n_in: Sequence[int], n_out: Sequence[int], backward: bool = False):
+    """(forward bytes, reverse-mode bytes or 0 unless `backward`)."""
     lib = _lib.load()
     hs = _lib.ptr_array([r.handle.value for r in rooms])
     fwd, bwd = ctypes.c_size_t(), ctypes.c_size_t()
     _lib.check(lib.msrc_workspace_size(hs, len(rooms), _lib.i64_array(n_in), _lib.i64_array(n_out),
-                                       ctypes.byref(fwd), ctypes.byref(bwd)))
+                                       ctypes.byref(fwd), ctypes.byref(bwd) if backward else None))
     return int(fwd.value), int(bwd.value)
 
 
@@ -271,7 +280,7 @@ def synthesize_backward(rooms: Sequence[Room], xs: Sequence[torch.Tensor], dys: 
     dx = [torch.empty(n, dtype=torch.float32, device=dev) for n in n_in] if want_dx else None
     dp = [torch.zeros(48, dtype=torch.float64, device=dev) for _ in rooms] if want_params else None
     db = [torch.zeros(6, dtype=torch.float64, device=dev) for _ in rooms] if want_beta else None
-    _, bwd = workspace_size(rooms, n_in, n_out)
+    _, bwd = workspace_size(rooms, n_in, n_out, backward=True)
     ws = workspace or _workspace(dev)
     buf = ws.get(bwd)
     hs = _lib.ptr_array([r.handle.value for r in rooms])

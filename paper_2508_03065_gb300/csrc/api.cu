@@ -46,8 +46,11 @@ struct msrc_room {
   int32_t n_mics;
   bool arr_moving;          // microphones carried by `arr`: m + a(t) - a(0)
   msrc_traj_desc arr;
-  double validated_until;  // trajectory checked on [0, validated_until]
+  double validated_from;   // trajectory checked on [validated_from, validated_until]
+  double validated_until;  // (empty while validated_until < validated_from)
   double max_speed;        // largest speed seen on that range (m/s, 1 ms steps)
+  int32_t tier_up[MSRC_MAX_TIERS];  // band-limited knot upsampling factor (1 = linear)
+  int32_t up_q;                     // its kernel half-width (knots)
 };
 
 namespace {
@@ -328,24 +331,27 @@ void host_source(const msrc_traj_desc& T, double t, double out[3]) {
   }
 }
 
-// Checks the source path and the microphones on a 1 ms grid up to t_end: the
-// source strictly inside the room, every microphone (carried by the array
-// motion when there is one) strictly inside and at least 0.1 m from the
-// source, and the source speed plus the array speed (a bound on the rate of
-// change of every image distance) below c. Records that largest rate.
-msrc_status validate_traj_range(msrc_room& R, double t_end) {
-  if (t_end <= R.validated_until) return MSRC_OK;
+// Checks the source path and the microphones on a 1 ms grid over
+// [t_begin, t_end] (t_begin <= 0 <= t_end; band-limited knot upsampling
+// evaluates the path's extension before 0 and past its end): the source
+// strictly inside the room, every microphone (carried by the array motion when
+// there is one) strictly inside and at least 0.1 m from the source, and the
+// source speed plus the array speed (a bound on the rate of change of every
+// image distance) below c. Records that largest rate.
+msrc_status validate_traj_range(msrc_room& R, double t_begin, double t_end) {
+  const bool have = R.validated_until >= R.validated_from;
+  if (have && t_begin >= R.validated_from && t_end <= R.validated_until) return MSRC_OK;
   const double dt = 1e-3;
-  const long steps = long(std::ceil(t_end / dt));
+  const long steps = long(std::ceil((t_end - t_begin) / dt));
   double prev[3], aprev[3] = {0.0, 0.0, 0.0}, a0[3] = {0.0, 0.0, 0.0};
   double vmax = 0.0;
-  host_source(R.traj, 0.0, prev);
+  host_source(R.traj, t_begin, prev);
   if (R.arr_moving) {
     host_source(R.arr, 0.0, a0);
-    std::memcpy(aprev, a0, sizeof(a0));
+    host_source(R.arr, t_begin, aprev);
   }
   for (long i = 0; i <= steps; ++i) {
-    const double t = std::min(i * dt, t_end);
+    const double t = std::min(t_begin + i * dt, t_end);
     double s[3], a[3] = {0.0, 0.0, 0.0};
     host_source(R.traj, t, s);
     if (R.arr_moving) host_source(R.arr, t, a);
@@ -377,9 +383,45 @@ msrc_status validate_traj_range(msrc_room& R, double t_end) {
     std::memcpy(prev, s, sizeof(prev));
     std::memcpy(aprev, a, sizeof(aprev));
   }
-  R.validated_until = t_end;
-  R.max_speed = vmax;
+  // both ranges contain [0, duration], so their union is an interval
+  R.validated_from = have ? std::min(R.validated_from, t_begin) : t_begin;
+  R.validated_until = have ? std::max(R.validated_until, t_end) : t_end;
+  R.max_speed = have ? std::max(R.max_speed, vmax) : vmax;
   return MSRC_OK;
+}
+
+// Band-limited knot upsampler (Sec. II-C): kernel h(u) = sinc(u) times a Kaiser
+// window of shape 8 over |u| < Q (bessel_i0 above). Row p of a factor-U
+// table holds the weights of knots j0 - Q + 1 .. j0 + Q at the point p / U past
+// knot j0, normalised to sum 1, then their first moment sum_i w_i (i - Q + 1).
+// Returns the largest sum_i |w_i| over the rows (the factor by which an
+// interpolated distance can exceed the largest knot distance).
+double upsampler_rows(int U, int Q, std::vector<float>& out) {
+  const double kShape = 8.0;
+  const double i0b = bessel_i0(kShape);
+  double l1max = 0.0;
+  std::vector<double> w(2 * Q);
+  for (int p = 0; p < U; ++p) {
+    const double x = double(p) / U;
+    double sum = 0.0;
+    for (int i = 0; i < 2 * Q; ++i) {
+      const double u = x - double(i - Q + 1);
+      const double sinc = (u == 0.0) ? 1.0 : std::sin(kPiD * u) / (kPiD * u);
+      const double r = u / Q;
+      w[i] = sinc * bessel_i0(kShape * std::sqrt(std::max(0.0, 1.0 - r * r))) / i0b;
+      sum += w[i];
+    }
+    double l1 = 0.0, moment = 0.0;
+    for (int i = 0; i < 2 * Q; ++i) {
+      w[i] /= sum;
+      l1 += std::fabs(w[i]);
+      moment += w[i] * double(i - Q + 1);
+      out.push_back(float(w[i]));
+    }
+    out.push_back(float(moment));
+    l1max = std::max(l1max, l1);
+  }
+  return l1max;
 }
 
 // ---------------------------------------------------------------- planning
@@ -400,6 +442,12 @@ struct Plan {
   size_t off_dxb = 0, off_kslot = 0, off_bpart = 0, off_gk = 0, off_ppart = 0, off_bwt = 0;
   int kL = 32;
   int taps = 32;
+  // band-limited knot upsampling: weight tables (uploaded to off_upw)
+  std::vector<float> upw;
+  std::vector<int> upw_key;       // U * 64 + Q of each table
+  std::vector<int> upw_at;        // its first float
+  std::vector<double> upw_l1;     // its largest absolute row sum
+  size_t off_upw = 0;
 };
 
 // Workspace layout and per-scene descriptors of one call. Forward mode uses
@@ -463,12 +511,24 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     S.fsc = float(S.fs_over_c);
     int first = 0, blk = 0;
     int64_t kfirst = 0;
-    int max_step = 1;
+    // trajectory range the knots reach, and the bound on an interpolated
+    // distance relative to the largest knot distance
+    double t_lo = 0.0, t_hi = R->traj.duration_s, l1 = 1.0;
+    const int Q = R->up_q;
+    S.up_q = Q;
     for (int t = 0; t < S.n_tiers; ++t) {
-      const int N = R->tier_step[t];
-      max_step = std::max(max_step, N);
+      const int Nc = R->tier_step[t];
+      const int U = R->tier_up[t];
+      const bool bl = U > 1;
+      const int N = Nc / U;  // record spacing: knots, or virtual knots when upsampled
+      if (bl && backward)
+        return fail(MSRC_ERR_UNSUPPORTED,
+                    "room %d: reverse mode does not support band-limited knot upsampling (tier %d)", s, t);
       S.tier_max_rho[t] = R->d.tier_max_rho[t];
       S.tier_step[t] = N;
+      S.tier_coarse[t] = Nc;
+      S.tier_up[t] = U;
+      S.knot_shift[t] = bl ? Q : 0;
       S.tier_count[t] = int32_t(R->tier_count[t]);
       S.tier_first[t] = first;
       first += S.tier_count[t];
@@ -481,13 +541,41 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
         return fail(MSRC_ERR_UNSUPPORTED, "tile configuration too small for knot spacing %d", N);
       int B = std::max(1, std::min(tc.block, tc.reccap / rec_per_image));
       if (backward) B = std::max(1, std::min(B, int(backward_unit_cap()) / (rec_per_image + 1)));
+      int64_t n_knots = J + 1;
+      if (bl) {
+        // the upsampler's scratch shares the shared z window (5 rows per segment)
+        const int nk = rec_per_image + 1;
+        const int nj = (nk - 1) / U + 2;
+        const int64_t per = bl_scratch_floats(1, nk, nj, Q);
+        const int64_t cap = int64_t(kFarrowSegs) * tc.wcap * 5;
+        if (per > cap)
+          return fail(MSRC_ERR_UNSUPPORTED, "tile configuration too small for the upsampling of tier %d", t);
+        B = std::min<int64_t>(B, cap / per);
+        const int key = U * 64 + Q;
+        size_t k = 0;
+        while (k < P.upw_key.size() && P.upw_key[k] != key) ++k;
+        if (k == P.upw_key.size()) {
+          P.upw_key.push_back(key);
+          P.upw_at.push_back(int(P.upw.size()));
+          P.upw_l1.push_back(upsampler_rows(U, Q, P.upw));
+        }
+        S.upw_base[t] = P.upw_at[k];
+        l1 = std::max(l1, P.upw_l1[k]);
+        // knots -Q .. J_c + Q, J_c the knot intervals covering the output
+        const int64_t Jc = (n_out[s] - 1) / Nc + 1;
+        n_knots = Jc + 1 + 2 * Q;
+        t_lo = std::min(t_lo, -double(Q) * Nc / R->d.fs);
+        t_hi = std::max(t_hi, double(Jc + Q) * Nc / R->d.fs);
+      } else {
+        t_hi = std::max(t_hi, double(J) * N / R->d.fs);
+      }
       S.tier_block_images[t] = B;
       S.tier_blocks[t] = (S.tier_count[t] + B - 1) / B;
       S.block_first[t] = blk;
       blk += S.tier_blocks[t];
       S.knot_base[t] = knot_acc + kfirst;
       S.knot_units_first[t] = kfirst;
-      kfirst += J + 1;
+      kfirst += n_knots;
     }
     S.n_blocks = blk;
     S.img_base = img_acc;
@@ -528,9 +616,10 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
       bpart_acc += int64_t(S.n_mics) * S.n_blocks * S.n_tiles * 8;
     }
     // z rows cover every read position: n - tau with tau in [0, tau_bound]
+    // (an upsampled distance is at most l1 times the largest knot distance)
     double maxL = 0, diag = 0;
     for (int d = 0; d < 3; ++d) { maxL = std::max(maxL, R->d.dims[d]); diag += R->d.dims[d] * R->d.dims[d]; }
-    const double dmax = 2.0 * S.K * maxL + 2.0 * std::sqrt(diag) + 1.0;
+    const double dmax = (2.0 * S.K * maxL + 2.0 * std::sqrt(diag) + 1.0) * l1;
     const int64_t tau_bound = int64_t(std::ceil(dmax * R->d.fs / R->d.c)) + 2;
     const int64_t zlo = -tau_bound - 16;
     const int64_t zhi = std::max(n_out[s], n_in[s] + R->d.taps) + 16;
@@ -538,9 +627,8 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     S.z_len = zhi - zlo;
     S.z_base = z_acc;
     S.part_base = part_acc;
-    // trajectory evaluated up to the last knot
-    const double t_last = double(((n_out[s] - 1) / max_step + 1) * max_step) / R->d.fs;
-    msrc_status vs = validate_traj_range(*R, std::max(t_last, R->traj.duration_s));
+    // trajectory evaluated at every knot
+    msrc_status vs = validate_traj_range(*R, t_lo, t_hi);
     if (vs != MSRC_OK) return vs;
     // reverse mode scatters one image's samples into shared (segment, column)
     // bins without atomics: below c/2 the read position advances by more than
@@ -587,6 +675,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.off_gain = off; off = align256(off + 4 * I);
   P.off_knots = off; off = align256(off + 24 * size_t(knot_acc));
   P.off_arr = off; off = align256(off + (any_moving ? 24 * size_t(knot_acc) : 0));
+  P.off_upw = off; off = align256(off + 4 * P.upw.size());
   P.off_z = off; off = align256(off + 16 * size_t(z_acc));
   // forward: power 4 of the degree-4 rows; reverse mode: powers 4..5 of the
   // degree-5 rows the gradient kernel reads (zq holds powers 0..3 either way)
@@ -624,6 +713,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.img_gain = reinterpret_cast<float*>(ws + P.off_gain);
   a.p.knot_pos = reinterpret_cast<double*>(ws + P.off_knots);
   a.p.arr_pos = reinterpret_cast<double*>(ws + P.off_arr);
+  a.p.upw = reinterpret_cast<const float*>(ws + P.off_upw);
   a.p.zq = reinterpret_cast<float4*>(ws + P.off_z);
   a.p.zp = P.backward ? nullptr : reinterpret_cast<float*>(ws + P.off_zp);
   a.p.zg = P.backward ? reinterpret_cast<float2*>(ws + P.off_zp) : nullptr;
@@ -668,8 +758,15 @@ msrc_status check_ws(const Plan& P, void* ws, size_t bytes) {
   return MSRC_OK;
 }
 
-// Uploads scene descriptors and prefix tables of a batched call.
+// Uploads the upsampler weight tables, and the scene descriptors and prefix
+// tables of a batched call (pageable sources: each copy returns once its data
+// is staged).
 msrc_status upload_tables(const Plan& P, char* ws, cudaStream_t st, std::vector<char>& blob) {
+  if (!P.upw.empty()) {
+    const cudaError_t e =
+        cudaMemcpyAsync(ws + P.off_upw, P.upw.data(), 4 * P.upw.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "upsampler table upload");
+  }
   if (P.scenes.size() <= 1) return MSRC_OK;
   blob.resize(P.desc_bytes);
   std::memcpy(blob.data(), P.scenes.data(), P.scenes.size() * sizeof(SceneDev));
@@ -753,10 +850,13 @@ msrc_status msrc_create_room(const msrc_room_desc* desc, msrc_room_t* out) {
     return fail(MSRC_ERR_INVALID_ARG, "farrow_order must be in [1, %d]", kFarrowDeg);
   if (d.window == 2 && !(d.passband >= 0.05 && d.passband <= 0.98))
     return fail(MSRC_ERR_INVALID_ARG, "passband must be in [0.05, 0.98]");
+  if (d.upsample_halfwidth < 0 || d.upsample_halfwidth > kMaxUpHalfwidth)
+    return fail(MSRC_ERR_INVALID_ARG, "upsample_halfwidth must be in [0, %d]", kMaxUpHalfwidth);
   msrc_room* R = new (std::nothrow) msrc_room;
   if (!R) return fail(MSRC_ERR_INVALID_ARG, "out of host memory");
   std::memset(R, 0, sizeof(*R));
   R->d = d;
+  R->up_q = d.upsample_halfwidth > 0 ? d.upsample_halfwidth : 4;
   for (int t = 0; t < d.n_tiers; ++t) {
     const double rate = d.tier_rate_hz[t];
     if (!(rate > 0.0) || rate > d.fs) { delete R; return fail(MSRC_ERR_INVALID_ARG, "tier %d rate must be in (0, fs]", t); }
@@ -767,6 +867,13 @@ msrc_status msrc_create_room(const msrc_room_desc* desc, msrc_room_t* out) {
       return fail(MSRC_ERR_INVALID_ARG, "tier %d: fs / rate must be an integer (got %.6f)", t, ratio);
     }
     R->tier_step[t] = int32_t(rr);
+    const int32_t U = d.tier_upsample[t];
+    if (U < 0 || U > kMaxUpsample || (U > 1 && R->tier_step[t] % U != 0)) {
+      delete R;
+      return fail(MSRC_ERR_INVALID_ARG, "tier %d: tier_upsample must be in [0, %d] and divide fs / rate",
+                  t, kMaxUpsample);
+    }
+    R->tier_up[t] = U > 1 ? U : 1;
     if (t > 0 && d.tier_max_rho[t] < d.tier_max_rho[t - 1] && t < d.n_tiers - 1) {
       delete R;
       return fail(MSRC_ERR_INVALID_ARG, "tier_max_rho must be non-decreasing");
@@ -837,10 +944,11 @@ msrc_status msrc_set_trajectory(msrc_room_t room, const msrc_traj_desc* traj, co
   room->n_mics = n_mics;
   for (int m = 0; m < n_mics; ++m)
     for (int d = 0; d < 3; ++d) room->mics[m][d] = mics[3 * m + d];
+  room->validated_from = 0.0;
   room->validated_until = -1.0;
   room->max_speed = 0.0;
   room->has_traj = true;
-  msrc_status s = validate_traj_range(*room, traj->duration_s);
+  msrc_status s = validate_traj_range(*room, 0.0, traj->duration_s);
   if (s != MSRC_OK) {
     *room = saved;
     return s;
@@ -866,10 +974,11 @@ msrc_status msrc_set_array_trajectory(msrc_room_t room, const msrc_traj_desc* tr
     room->arr_moving = true;
     room->arr = *traj;
   }
+  room->validated_from = 0.0;
   room->validated_until = -1.0;
   room->max_speed = 0.0;
   if (room->has_traj) {
-    msrc_status s = validate_traj_range(*room, room->traj.duration_s);
+    msrc_status s = validate_traj_range(*room, 0.0, room->traj.duration_s);
     if (s != MSRC_OK) {
       *room = saved;
       return s;

@@ -155,7 +155,9 @@ __global__ void k_traj_knots(const __grid_constant__ KernelArgs a) {
   int t = 0;
   while (t + 1 < S.n_tiers && local >= S.knot_units_first[t + 1]) ++t;
   const int64_t j = local - S.knot_units_first[t];
-  const double time = double(j * S.tier_step[t]) / S.fs;
+  // knot j of the table is knot j - knot_shift of the tier (band-limited tiers
+  // keep knot_shift knots before t = 0)
+  const double time = double((j - S.knot_shift[t]) * S.tier_coarse[t]) / S.fs;
   double sp[3];
   source_position(S, time, sp);
   double* out = a.p.knot_pos + 3 * (S.knot_base[t] + j);

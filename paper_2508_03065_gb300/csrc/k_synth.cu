@@ -184,7 +184,15 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
 
     // --- delay knots of the block over the tile (records in shared memory)
     float tmin, tmax;
-    item_records<kThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax);
+    int cnt = g.cnt;
+    if (S.tier_up[g.t] > 1) {
+      // band-limited knot upsampling: its scratch takes the z window and power rows
+      if (!item_records_bl<kThreads>(a, S, g, rec_s, img_s, reinterpret_cast<float*>(smem4),
+                                     int64_t(kFarrowSegs) * kWcap * 5, &tmin, &tmax))
+        cnt = 0;
+    } else {
+      item_records<kThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
@@ -243,9 +251,9 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       for (int c = 0; c < kChunks; ++c) rmj[c] = rr[c] - pass_lo + jc[c] * g.N;
       const unsigned wmax = unsigned(pw - 1);
       if (width <= kWcap)
-        gather_images<kWcap, kChunks, kUnroll, false>(zq_s, zp_s, rec_s, img_s, g.cnt, jc, rmj, rf, wmax, acc);
+        gather_images<kWcap, kChunks, kUnroll, false>(zq_s, zp_s, rec_s, img_s, cnt, jc, rmj, rf, wmax, acc);
       else
-        gather_images<kWcap, kChunks, kUnroll, true>(zq_s, zp_s, rec_s, img_s, g.cnt, jc, rmj, rf, wmax, acc);
+        gather_images<kWcap, kChunks, kUnroll, true>(zq_s, zp_s, rec_s, img_s, cnt, jc, rmj, rf, wmax, acc);
     }
     float* out = a.p.part + S.part_base + (int64_t(g.mic) * S.n_blocks + g.blk) * S.n_out;
 #pragma unroll

@@ -34,6 +34,10 @@ constexpr int kMaxScenesInline = 1;
 // Error bits of the device error word.
 constexpr uint32_t kErrTimeout = 1u;
 constexpr uint32_t kErrWindowClamp = 2u;
+constexpr uint32_t kErrUpsampleScratch = 4u;
+// Band-limited knot upsampling: largest upsampling factor and kernel half-width.
+constexpr int kMaxUpsample = 512;
+constexpr int kMaxUpHalfwidth = 8;
 
 // Per-scene description as the kernels see it. All offsets are in elements of
 // the array they index. Images are stored sorted by (tier, distance at the
@@ -62,6 +66,15 @@ struct SceneDev {
   int32_t n_tiles;                         // output tiles
   int32_t tile;                            // samples per tile
   int32_t tier_block_images[MSRC_MAX_TIERS];  // images per block of the tier
+  // band-limited knot upsampling (tier_up[t] > 1): records every
+  // tier_step = tier_coarse / tier_up samples at virtual knots interpolated
+  // from the knots (every tier_coarse samples) by a kernel of half-width
+  // up_q knots; the tier's knot table starts knot_shift knots before t = 0
+  int32_t tier_up[MSRC_MAX_TIERS];
+  int32_t tier_coarse[MSRC_MAX_TIERS];     // knot spacing (samples); tier_step when linear
+  int32_t knot_shift[MSRC_MAX_TIERS];      // up_q for band-limited tiers, else 0
+  int32_t up_q;
+  int32_t upw_base[MSRC_MAX_TIERS];        // first float of the tier's weight table in upw
   int64_t img_base;                        // first entry of this scene in the image table
   int64_t knot_base[MSRC_MAX_TIERS];       // first knot position (double3) per tier
   int64_t knot_units_first[MSRC_MAX_TIERS];// prefix over tiers of (J_t + 1)
@@ -139,6 +152,11 @@ struct DevicePtrs {
   double* gk;                    // dL/ds(t_j) per tier knot (3 doubles, indexed like knot_pos)
   double* ppart;                 // trajectory-parameter partials (48 doubles per (scene, knot chunk))
   float4* bwt;                   // per image: dbeta_i/dbeta_w / (4 pi) for walls 0..3 | walls 4..5, gain, 0
+  // band-limited knot upsampling: per (scene, tier) a table of tier_up rows
+  // of 2 up_q + 1 floats, row p = the normalised kernel weights of knots
+  // j0 - up_q + 1 .. j0 + up_q at the virtual knot p / tier_up past knot j0,
+  // then their first moment sum_i w_i (i - up_q + 1)
+  const float* upw;
 };
 constexpr int kParamPartialsPerScene = 32 * 48;
 
@@ -166,6 +184,14 @@ __host__ __device__ inline void unpack_image(uint32_t code, int n[3], int p[3]) 
   p[0] = int((code >> 21) & 1u);
   p[1] = int((code >> 22) & 1u);
   p[2] = int((code >> 23) & 1u);
+}
+
+// Shared-memory scratch (floats) of the band-limited record builder for `cnt`
+// images, nk virtual knots and nj knot intervals (nj - 1 + 2 Q knots): FP64
+// delays at the knots, the anchor, the chord rows and the relative delays.
+__host__ __device__ inline int64_t bl_scratch_floats(int cnt, int nk, int nj, int Q) {
+  const int nc = nj - 1 + 2 * Q;
+  return int64_t(cnt) * (2 * nc + 1 + nj * (2 * Q + 2) + nk);
 }
 
 // Launch entry points (defined in the .cu files).

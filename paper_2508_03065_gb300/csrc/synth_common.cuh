@@ -91,6 +91,21 @@ __device__ __forceinline__ void knot_increment_moving(const float4 A, const floa
   *d = A.w + dd;
 }
 
+// Interval records of an item from the relative delays phi at its knots
+// (phi_s[ib * nk + jj]); see item_records for the record layout.
+template <int kThreads>
+__device__ __forceinline__ void records_from_phi(const ItemGeom& g, const float* phi_s, float2* rec_s) {
+  const float sN = float(kFarrowSegs) / float(g.N);
+  const int nk = g.nk;
+  const int nrec = nk - 1;
+  for (int pidx = threadIdx.x; pidx < g.cnt * nrec; pidx += kThreads) {
+    const int ib = pidx / nrec;
+    const int jj = pidx - ib * nrec;
+    const float phi0 = phi_s[ib * nk + jj], phi1 = phi_s[ib * nk + jj + 1];
+    rec_s[jj * g.cnt + ib] = make_float2(fmaf(-float(kFarrowSegs), phi0, -0.5f), (phi0 - phi1) * sN);
+  }
+}
+
 // Records of the item's images over its intervals, in shared memory.
 // With tau = d fs / c, D_a = floor(tau) at the anchor knot jf (FP64) and
 // phi_j = tau_j - D_a, the delay between knots j and j + 1 is
@@ -169,16 +184,113 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     tmax = fmaxf(tmax, A2.y + phi);
   }
   __syncthreads();
-  const float sN = float(kFarrowSegs) / float(g.N);
-  const int nrec = nk - 1;
-  for (int pidx = threadIdx.x; pidx < g.cnt * nrec; pidx += kThreads) {
-    const int ib = pidx / nrec;
-    const int jj = pidx - ib * nrec;
-    const float phi0 = phi_s[ib * nk + jj], phi1 = phi_s[ib * nk + jj + 1];
-    rec_s[jj * g.cnt + ib] = make_float2(fmaf(-float(kFarrowSegs), phi0, -0.5f), (phi0 - phi1) * sN);
-  }
+  records_from_phi<kThreads>(g, phi_s, rec_s);
   *tmin_out = tmin;
   *tmax_out = tmax;
+}
+
+// item_records for a tier with band-limited knot upsampling (Sec. II-C: the
+// distance is a band-limited signal sampled at the knots and recovered by an
+// upsampler). The item's records sit at virtual knots k = jf .. jf + nk - 1
+// (every N = N_c / U samples, N_c the knot spacing); the distance there is
+// sum_i w_p[i] d(j0 - Q + 1 + i) with j0 = floor(k / U), p = k - j0 U and the
+// normalised weights w_p of the windowed-sinc kernel. With tau_j = d_j fs / c
+// at the knots (FP64), Delta = tau_{j0+1} - tau_j0 and the deviations from the
+// chord e_i = tau_{j0-Q+1+i} - tau_j0 - (i - Q + 1) Delta, and since the
+// weights sum to one,
+//   tau(k) = tau_j0 + Delta M_p + sum_i w_p[i] e_i,   M_p = sum_i w_p[i] (i - Q + 1),
+// so that the FP32 sum only carries the small chord deviations; tau_j0 - D
+// and Delta are formed in FP64 and rounded once. D = floor(tau) at knot
+// floor(jf / U) is the image's anchor. Scratch `scr` (16-byte aligned, `cap`
+// floats): tau_s (cnt x nc doubles), D (cnt), chord rows (cnt x nj x (2Q + 2)),
+// phi (cnt x nk). If the item does not fit, the error word gets
+// kErrUpsampleScratch, no record is written and the result is false (the
+// caller then treats the block as empty).
+template <int kThreads>
+__device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
+                                int4* img_s, float* scr, int64_t cap, float* tmin_out, float* tmax_out) {
+  const int U = S.tier_up[g.t];
+  const int Q = S.up_q;
+  const int nk = g.nk;
+  const int j0_first = g.jf / U;
+  const int nj = (g.jf + nk - 1) / U - j0_first + 1;
+  const int nc = nj - 1 + 2 * Q;
+  float tmin = 3.0e38f, tmax = -3.0e38f;
+  if (bl_scratch_floats(g.cnt, nk, nj, Q) > cap) {
+    if (threadIdx.x == 0) atomicOr(a.p.err, kErrUpsampleScratch);
+    *tmin_out = 0.0f;
+    *tmax_out = 0.0f;
+    return false;
+  }
+  double* tau_s = reinterpret_cast<double*>(scr);
+  float* dfl_s = scr + 2 * g.cnt * nc;
+  float* e_s = dfl_s + g.cnt;
+  const int er = 2 * Q + 2;
+  float* phi_s = e_s + g.cnt * nj * er;
+  // table index of the first coarse knot j0_first - Q + 1 (the table starts at knot -Q)
+  const int64_t kc0 = S.knot_base[g.t] + (j0_first - Q + 1) + S.knot_shift[g.t];
+  const double* kp = a.p.knot_pos + 3 * kc0;
+  const double* ap = a.p.arr_pos + 3 * kc0;
+  const bool moving = S.arr_moving != 0;
+  const double fs_c = S.fs_over_c;
+  const uint32_t* codes = a.p.img_code + S.img_base + S.tier_first[g.t] + g.img0;
+  const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
+  const double* mic = S.mics[g.mic];
+  for (int pidx = threadIdx.x; pidx < g.cnt * nc; pidx += kThreads) {
+    const int ib = pidx / nc;
+    const int c = pidx - ib * nc;
+    int n[3], p[3];
+    unpack_image(codes[ib], n, p);
+    double acc = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double m = mic[d] + (moving ? ap[3 * c + d] : 0.0);
+      const double v = (1.0 - 2.0 * p[d]) * kp[3 * c + d] + 2.0 * n[d] * S.dims[d] - m;
+      acc = fma(v, v, acc);
+    }
+    const double tau = fast_sqrt(acc) * fs_c;
+    tau_s[pidx] = tau;
+    if (c == Q - 1) {  // knot floor(jf / U): the anchor
+      const double Dfl = floor(tau);
+      dfl_s[ib] = float(Dfl);
+      img_s[ib] = make_int4(g.jf * g.N - int(Dfl), __float_as_int(float(Dfl) - 0.5f / kFarrowSegs),
+                            __float_as_int(__ldg(gain + ib)), 0);
+    }
+  }
+  __syncthreads();
+  for (int pidx = threadIdx.x; pidx < g.cnt * nj; pidx += kThreads) {
+    const int ib = pidx / nj;
+    const int jr = pidx - ib * nj;
+    const double* tv = tau_s + ib * nc + jr;  // knots j0 - Q + 1 .. j0 + Q
+    const double t0 = tv[Q - 1];
+    const double dl = tv[Q] - t0;
+    float* E = e_s + pidx * er;
+    for (int i = 0; i < 2 * Q; ++i) E[i] = float(tv[i] - t0 - double(i - Q + 1) * dl);
+    E[2 * Q] = float(t0 - double(dfl_s[ib]));
+    E[2 * Q + 1] = float(dl);
+  }
+  __syncthreads();
+  const float* W0 = a.p.upw + S.upw_base[g.t];
+  for (int pidx = threadIdx.x; pidx < g.cnt * nk; pidx += kThreads) {
+    const int ib = pidx / nk;
+    const int jj = pidx - ib * nk;
+    const int k = g.jf + jj;
+    const int j0 = k / U;
+    const int pp = k - j0 * U;
+    const float* E = e_s + (ib * nj + (j0 - j0_first)) * er;
+    const float* W = W0 + pp * (2 * Q + 1);
+    float phi = fmaf(E[2 * Q + 1], __ldg(W + 2 * Q), E[2 * Q]);
+    for (int i = 0; i < 2 * Q; ++i) phi = fmaf(__ldg(W + i), E[i], phi);
+    phi_s[pidx] = phi;
+    const float D = dfl_s[ib];
+    tmin = fminf(tmin, D + phi);
+    tmax = fmaxf(tmax, D + phi);
+  }
+  __syncthreads();
+  records_from_phi<kThreads>(g, phi_s, rec_s);
+  *tmin_out = tmin;
+  *tmax_out = tmax;
+  return true;
 }
 
 // Interpolated delay of one image-sample split into the read position m0

@@ -34,6 +34,7 @@ class SceneSpec:
     kaiser_beta: float = 8.0
     farrow_order: int = 4                   # window FARROW_LS: polynomial order
     passband: float = 0.9                   # window FARROW_LS: passband edge / pi
+    up_halfwidth: int = 4                   # knot upsampler: kernel half-width (knots)
     arr_kind: int = -1                      # microphone array motion: -1 static, else a
     arr_traj: List[float] = field(default_factory=list)   # trajectory a(t) of the source's kinds;
     arr_n_ctrl: int = 0                     # microphones sit at mics + a(t) - a(0)

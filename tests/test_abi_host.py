@@ -44,10 +44,14 @@ def _desc(**kw):
     d.n_tiers = len(tiers)
     rho = [0] * 4
     rate = [1.0] * 4
-    for t, (r, hz) in enumerate(tiers):
-        rho[t], rate[t] = r, hz
+    up = [0] * 4
+    for t, tier in enumerate(tiers):
+        rho[t], rate[t] = tier[0], tier[1]
+        up[t] = tier[2] if len(tier) > 2 else 0
     d.tier_max_rho[:] = rho
     d.tier_rate_hz[:] = rate
+    d.tier_upsample[:] = up
+    d.upsample_halfwidth = kw.get("upsample_halfwidth", 0)
     d.taps = kw.get("taps", 32)
     d.window = kw.get("window", 0)
     d.kaiser_beta = kw.get("kaiser_beta", 8.0)
@@ -68,7 +72,9 @@ def _create(**kw):
     dict(K=61), dict(K=-1), dict(taps=31), dict(taps=4), dict(taps=66), dict(window=3),
     dict(tiers=[(1, 16000.0), (2**31 - 1, 700.0)]), dict(tiers=[]),
     dict(window=1, kaiser_beta=-1.0), dict(window=2, farrow_order=0), dict(window=2, farrow_order=5),
-    dict(window=2, passband=0.01), dict(window=2, passband=0.99)])
+    dict(window=2, passband=0.01), dict(window=2, passband=0.99),
+    dict(tiers=[(1, 16000.0), (2**31 - 1, 1000.0, 7)]), dict(tiers=[(2**31 - 1, 25.0, 1280)]),
+    dict(tiers=[(2**31 - 1, 1000.0, -1)]), dict(upsample_halfwidth=9), dict(upsample_halfwidth=-1)])
 def test_create_room_rejects_bad_descriptions(bad):
     st, h = _create(**bad)
     assert st == _lib.ERR_INVALID_ARG
@@ -217,3 +223,33 @@ def test_array_trajectory_validation():
     room.set_array_trajectory(W.CIRCLE, [0, 0, 0, 0.1, 0.3, 0.0], spec.duration)
     room.set_array_trajectory(None)
 
+
+
+def test_band_limited_upsampling_planning():
+    """Band-limited tiers plan a forward call, refuse reverse mode, and check
+    the path's extension before t = 0 that their knots reach."""
+    lib = _lib.load()
+    n = _lib.i64_array([16000])
+    arr, p = _mics((2.5, 2.0, 1.2))
+    sizes = []
+    for tiers in ([(1, 16000.0), (2**31 - 1, 5.0)], [(1, 16000.0), (2**31 - 1, 5.0, 100)]):
+        st, h = _create(tiers=tiers)
+        assert st == _lib.OK
+        assert lib.msrc_set_trajectory(h, ctypes.byref(_traj()), p, 1) == _lib.OK
+        hs = _lib.ptr_array([h.value])
+        fwd, bwd = ctypes.c_size_t(), ctypes.c_size_t()
+        assert lib.msrc_workspace_size(hs, 1, n, n, ctypes.byref(fwd), None) == _lib.OK
+        sizes.append(fwd.value)
+        st = lib.msrc_workspace_size(hs, 1, n, n, None, ctypes.byref(bwd))
+        assert st == (_lib.OK if len(tiers[1]) == 2 else _lib.ERR_UNSUPPORTED)
+        lib.msrc_destroy_room(h)
+    assert sizes[1] > sizes[0]
+    # 2 m/s along (3, 2, 0) from x = 1 m: inside the room on [0, 1] s, but the
+    # 5 Hz tier's kernel reaches 4 knots (0.8 s) before t = 0, where x < 0
+    fast = _traj(params=(1.0, 1.0, 1.5, 3.0, 2.0, 0.0, 2.0))
+    for U, want in ((0, _lib.OK), (100, _lib.ERR_INVALID_ARG)):
+        st, h = _create(tiers=[(1, 16000.0), (2**31 - 1, 5.0, U)])
+        assert lib.msrc_set_trajectory(h, ctypes.byref(fast), p, 1) == _lib.OK
+        fwd = ctypes.c_size_t()
+        assert lib.msrc_workspace_size(_lib.ptr_array([h.value]), 1, n, n, ctypes.byref(fwd), None) == want
+        lib.msrc_destroy_room(h)
