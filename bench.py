@@ -62,10 +62,11 @@ def parse():
     ap.add_argument("--tile-config", type=int, default=None, help="synthesis tile configuration id")
     ap.add_argument("--batched-scenes", type=int, default=256,
                     help="scenes of the batched comparison (0 disables it)")
-    ap.add_argument("--sections", default="batched,backward,filters,moving_array,e1",
-                    help="extra measurements in the JSON line: batched, backward, array, filters, moving_array, e1")
+    ap.add_argument("--sections", default="batched,backward,filters,moving_array,upsampled,e1",
+                    help="extra measurements in the JSON line: batched, backward, array, filters, moving_array, "
+                         "upsampled, e1")
     ap.add_argument("--only", default=None,
-                    choices=["backward", "array", "batched", "filters", "moving_array", "e1"],
+                    choices=["backward", "array", "batched", "filters", "moving_array", "upsampled", "e1"],
                     help="run one extra section alone (profiling captures) and print it")
     return ap.parse_args()
 
@@ -323,6 +324,8 @@ def run_gpu(args):
             line["filters"] = run_filters(args, torch, api, W)
         if "moving_array" in sections:
             line["moving_array"] = run_moving_array(args, torch, api, W)
+        if "upsampled" in sections:
+            line["upsampled"] = run_upsampled(args, torch, api, W)
         if "e1" in sections:
             line["e1"] = run_e1(args, torch, api, W)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -446,20 +449,14 @@ def run_array(args, torch, api, W):
             "forward_value": work / (t_f * 1e-3), "backward_value": work / (t_b * 1e-3), "unit": UNIT}
 
 
-def run_filters(args, torch, api, W):
-    """The order-20 scene with each tap-weight design: Kaiser-windowed sinc (the
-    main line) and the least-squares Farrow designs of order 2 and 4. The
-    kernels are the same; only the segment tables differ."""
-    from dataclasses import replace
-
+def _time_variants(torch, api, variants):
+    """Mean device time of 5 calls (after 3 warm-up calls) of each named scene
+    on the order-20 signal, with the throughput in image-samples/s."""
     out = {}
-    base = W.config2()
-    x = torch.from_numpy(base.x).cuda()
     ws = api.Workspace("cuda")
     stream = torch.cuda.current_stream()
-    for name, kw in (("kaiser", {}), ("least_squares_order2", dict(window=W.FARROW_LS, farrow_order=2, passband=0.9)),
-                     ("least_squares_order4", dict(window=W.FARROW_LS, farrow_order=4, passband=0.9))):
-        spec = replace(base, **kw)
+    for name, spec in variants:
+        x = torch.from_numpy(spec.x).cuda()
         room = api.Room.from_spec(spec)
         work = room.image_count()[0] * spec.n_in * room.n_mics
         y = api.synthesize([room], [x], workspace=ws)[0]
@@ -475,6 +472,19 @@ def run_filters(args, torch, api, W):
         ms = e0.elapsed_time(e1) / 5
         out[name] = {"ms": ms, "value": work / (ms * 1e-3), "unit": UNIT}
     return out
+
+
+def run_filters(args, torch, api, W):
+    """The order-20 scene with each tap-weight design: Kaiser-windowed sinc (the
+    main line) and the least-squares Farrow designs of order 2 and 4. The
+    kernels are the same; only the segment tables differ."""
+    from dataclasses import replace
+
+    base = W.config2()
+    return _time_variants(torch, api, [
+        ("kaiser", base),
+        ("least_squares_order2", replace(base, window=W.FARROW_LS, farrow_order=2, passband=0.9)),
+        ("least_squares_order4", replace(base, window=W.FARROW_LS, farrow_order=4, passband=0.9))])
 
 
 def run_moving_array(args, torch, api, W):
@@ -484,28 +494,21 @@ def run_moving_array(args, torch, api, W):
     from dataclasses import replace
 
     base = W.config2()
-    x = torch.from_numpy(base.x).cuda()
-    ws = api.Workspace("cuda")
-    stream = torch.cuda.current_stream()
-    out = {}
-    for name, kw in (("still", {}), ("moving", dict(arr_kind=W.LINE, arr_traj=[0.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.3],
-                                                     arr_duration=base.duration))):
-        spec = replace(base, **kw)
-        room = api.Room.from_spec(spec)
-        work = room.image_count()[0] * spec.n_in * room.n_mics
-        y = api.synthesize([room], [x], workspace=ws)[0]
-        for _ in range(3):
-            api.synthesize([room], [x], out=[y], workspace=ws)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(5):
-            api.synthesize([room], [x], out=[y], workspace=ws)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / 5
-        out[name] = {"ms": ms, "value": work / (ms * 1e-3), "unit": UNIT}
-    return out
+    return _time_variants(torch, api, [
+        ("still", base),
+        ("moving", replace(base, arr_kind=W.LINE, arr_traj=[0.0, 0.0, 0.0, 0.0, 0.0, 1.0, 0.3],
+                           arr_duration=base.duration))])
+
+
+def run_upsampled(args, torch, api, W):
+    """The order-20 scene with its last tier on linear 500 Hz knots (the main
+    line) vs band-limited knots at 50 Hz x 10 and 5 Hz x 100 (records at the
+    same 96-sample spacing; the difference is the upsampler's share of the
+    record prologue)."""
+    return _time_variants(torch, api, [
+        ("linear_500hz", W.config2()),
+        ("band_limited_50hz_x10", W.config2_upsampled(50.0, 10)),
+        ("band_limited_5hz_x100", W.config2_upsampled(5.0, 100))])
 
 
 def run_e1(args, torch, api, W):
@@ -552,7 +555,7 @@ def run_only(args):
     from paper_2508_03065_gb300 import workloads as W
 
     fn = {"backward": run_backward, "array": run_array, "batched": run_batched, "filters": run_filters,
-          "moving_array": run_moving_array, "e1": run_e1}[args.only]
+          "moving_array": run_moving_array, "upsampled": run_upsampled, "e1": run_e1}[args.only]
     print(json.dumps({args.only: fn(args, torch, api, W)}), flush=True)
     return 0
 

@@ -429,8 +429,8 @@ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Plan {
   std::vector<SceneDev> scenes;
-  std::vector<int64_t> prefix[6];
-  int64_t totals[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<int64_t> prefix[kUnitKinds];
+  int64_t totals[kUnitKinds] = {0, 0, 0, 0, 0, 0, 0};
   int end_bit = 40;
   // byte offsets in the workspace
   size_t off_desc = 0, off_keys_in = 0, off_keys_out = 0, off_vals_in = 0, off_vals_out = 0;
@@ -447,7 +447,7 @@ struct Plan {
   std::vector<int> upw_key;       // U * 64 + Q of each table
   std::vector<int> upw_at;        // its first float
   std::vector<double> upw_l1;     // its largest absolute row sum
-  size_t off_upw = 0;
+  size_t off_upw = 0, off_bl_tau = 0;
 };
 
 // Workspace layout and per-scene descriptors of one call. Forward mode uses
@@ -463,7 +463,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.scenes.resize(n);
   for (auto& v : P.prefix) v.assign(n + 1, 0);
   int64_t img_acc = 0, knot_acc = 0, z_acc = 0, part_acc = 0;
-  int64_t dxb_acc = 0, kslot_acc = 0, bpart_acc = 0;
+  int64_t dxb_acc = 0, kslot_acc = 0, bpart_acc = 0, bl_acc = 0;
   bool any_moving = false;
   for (int s = 0; s < n; ++s) {
     msrc_room* R = rooms[s];
@@ -510,7 +510,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     S.fs_over_c = R->d.fs / R->d.c;
     S.fsc = float(S.fs_over_c);
     int first = 0, blk = 0;
-    int64_t kfirst = 0;
+    int64_t kfirst = 0, bl_units = 0;
     // trajectory range the knots reach, and the bound on an interpolated
     // distance relative to the largest knot distance
     double t_lo = 0.0, t_hi = R->traj.duration_s, l1 = 1.0;
@@ -564,6 +564,12 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
         // knots -Q .. J_c + Q, J_c the knot intervals covering the output
         const int64_t Jc = (n_out[s] - 1) / Nc + 1;
         n_knots = Jc + 1 + 2 * Q;
+        // k_bl_tau units: (microphone, image) rows of n_knots delays
+        S.bl_knots[t] = int32_t(n_knots);
+        S.bl_units_first[t] = bl_units;
+        S.bl_tau_base[t] = bl_acc;
+        bl_units += int64_t(R->n_mics) * R->tier_count[t];
+        bl_acc += int64_t(R->n_mics) * R->tier_count[t] * n_knots;
         t_lo = std::min(t_lo, -double(Q) * Nc / R->d.fs);
         t_hi = std::max(t_hi, double(Jc + Q) * Nc / R->d.fs);
       } else {
@@ -644,10 +650,11 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     // items (microphone, image block) in the reduction slot
     const int64_t u_item = int64_t(S.n_mics) * S.n_blocks * S.n_tiles;
     const int64_t u_red = backward ? int64_t(S.n_mics) * S.n_groups * S.n_ranges : int64_t(S.n_mics) * S.n_out;
+    const int64_t u_bl = bl_units;  // (mic, image) rows of FP64 knot delays of upsampled tiers
     if (int64_t(S.n_mics) * S.n_blocks * S.n_tiles >= (int64_t(1) << 31))
       return fail(MSRC_ERR_UNSUPPORTED, "room %d: more than 2^31 work items", s);
-    const int64_t u[6] = {u_enum, u_knots, u_rec, u_z, u_item, u_red};
-    for (int k = 0; k < 6; ++k) {
+    const int64_t u[kUnitKinds] = {u_enum, u_knots, u_rec, u_z, u_item, u_red, u_bl};
+    for (int k = 0; k < kUnitKinds; ++k) {
       P.prefix[k][s + 1] = P.prefix[k][s] + u[k];
       P.totals[k] += u[k];
     }
@@ -662,7 +669,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   while ((int64_t(1) << (P.end_bit - 40)) < n) ++P.end_bit;
   // workspace layout
   size_t off = 256;  // error word + work counter
-  P.desc_bytes = (n > 1) ? n * sizeof(SceneDev) + 6 * (n + 1) * sizeof(int64_t) : 0;
+  P.desc_bytes = (n > 1) ? n * sizeof(SceneDev) + kUnitKinds * (n + 1) * sizeof(int64_t) : 0;
   P.off_desc = off; off = align256(off + P.desc_bytes);
   const size_t I = size_t(img_acc);
   P.off_keys_in = off; off = align256(off + 8 * I);
@@ -676,6 +683,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.off_knots = off; off = align256(off + 24 * size_t(knot_acc));
   P.off_arr = off; off = align256(off + (any_moving ? 24 * size_t(knot_acc) : 0));
   P.off_upw = off; off = align256(off + 4 * P.upw.size());
+  P.off_bl_tau = off; off = align256(off + 8 * size_t(bl_acc));
   P.off_z = off; off = align256(off + 16 * size_t(z_acc));
   // forward: power 4 of the degree-4 rows; reverse mode: powers 4..5 of the
   // degree-5 rows the gradient kernel reads (zq holds powers 0..3 either way)
@@ -700,7 +708,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   std::memset(&a, 0, sizeof(a));
   a.n_scenes = int32_t(P.scenes.size());
   if (a.n_scenes == 1) a.scene0 = P.scenes[0];
-  for (int k = 0; k < 6; ++k) a.totals[k] = P.totals[k];
+  for (int k = 0; k < kUnitKinds; ++k) a.totals[k] = P.totals[k];
   a.p.err = reinterpret_cast<uint32_t*>(ws);
   a.p.counter = reinterpret_cast<uint32_t*>(ws + 4);
   a.p.keys_in = reinterpret_cast<uint64_t*>(ws + P.off_keys_in);
@@ -714,6 +722,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.knot_pos = reinterpret_cast<double*>(ws + P.off_knots);
   a.p.arr_pos = reinterpret_cast<double*>(ws + P.off_arr);
   a.p.upw = reinterpret_cast<const float*>(ws + P.off_upw);
+  a.p.bl_tau = reinterpret_cast<double*>(ws + P.off_bl_tau);
   a.p.zq = reinterpret_cast<float4*>(ws + P.off_z);
   a.p.zp = P.backward ? nullptr : reinterpret_cast<float*>(ws + P.off_zp);
   a.p.zg = P.backward ? reinterpret_cast<float2*>(ws + P.off_zp) : nullptr;
@@ -746,6 +755,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
     a.tab.z_prefix = pre + 3 * n1;
     a.tab.item_prefix = pre + 4 * n1;
     a.tab.red_prefix = pre + 5 * n1;
+    a.tab.bl_prefix = pre + 6 * n1;
   }
 }
 
@@ -772,8 +782,7 @@ msrc_status upload_tables(const Plan& P, char* ws, cudaStream_t st, std::vector<
   std::memcpy(blob.data(), P.scenes.data(), P.scenes.size() * sizeof(SceneDev));
   int64_t* pre = reinterpret_cast<int64_t*>(blob.data() + P.scenes.size() * sizeof(SceneDev));
   const size_t n1 = P.scenes.size() + 1;
-  const int order[6] = {0, 1, 2, 3, 4, 5};
-  for (int k = 0; k < 6; ++k) std::memcpy(pre + k * n1, P.prefix[order[k]].data(), n1 * sizeof(int64_t));
+  for (int k = 0; k < kUnitKinds; ++k) std::memcpy(pre + k * n1, P.prefix[k].data(), n1 * sizeof(int64_t));
   cudaError_t e = cudaMemcpyAsync(ws + P.off_desc, blob.data(), P.desc_bytes, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "descriptor upload");
   return MSRC_OK;

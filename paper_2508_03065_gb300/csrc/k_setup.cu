@@ -174,6 +174,47 @@ __global__ void k_traj_knots(const __grid_constant__ KernelArgs a) {
   }
 }
 
+// FP64 delay tau = d fs / c of every (microphone, image, knot) of a tier with
+// band-limited knot upsampling (the upsampler's input, Sec. II-C), once per
+// knot: every synthesis item whose virtual knots reach a knot reads it. One
+// warp per (microphone, image) row, lanes over its knots (coalesced stores);
+// the image's constant part 2 n L - m is formed once per lane.
+constexpr int kBlTauThreads = 256;
+__global__ void k_bl_tau(const __grid_constant__ KernelArgs a) {
+  const int64_t wid = (int64_t(blockIdx.x) * kBlTauThreads + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= a.totals[6]) return;
+  int64_t local;
+  const int s = locate(a, a.tab.bl_prefix, wid, &local);
+  const SceneDev& S = scene_of(a, s);
+  int t = -1;
+  for (int k = 0; k < S.n_tiers; ++k)
+    if (S.tier_up[k] > 1 && S.bl_units_first[k] <= local) t = k;
+  if (t < 0) return;
+  const int64_t row = local - S.bl_units_first[t];
+  const int nkt = S.bl_knots[t];
+  const int mic = int(row / S.tier_count[t]);
+  const int img = int(row - int64_t(mic) * S.tier_count[t]);
+  int n[3], p[3];
+  unpack_image(a.p.img_code[S.img_base + S.tier_first[t] + img], n, p);
+  double o[3];
+  for (int d = 0; d < 3; ++d) o[d] = fma(2.0 * n[d], S.dims[d], -S.mics[mic][d]);
+  const bool moving = S.arr_moving != 0;
+  double* out = a.p.bl_tau + S.bl_tau_base[t] + row * nkt;
+  for (int j = lane; j < nkt; j += 32) {
+    const double* kp = a.p.knot_pos + 3 * (S.knot_base[t] + j);
+    const double* ap = a.p.arr_pos + 3 * (S.knot_base[t] + j);
+    double acc = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double v = (p[d] ? o[d] - kp[d] : o[d] + kp[d]);
+      if (moving) v -= ap[d];
+      acc = fma(v, v, acc);
+    }
+    out[j] = fast_sqrt(acc) * S.fs_over_c;
+  }
+}
+
 }  // namespace
 
 size_t sort_temp_bytes(int64_t n_items, int end_bit) {
@@ -210,6 +251,8 @@ cudaError_t launch_setup(const KernelArgs& a, cudaStream_t st) {
     k_image_table<<<blocks_for(a.totals[0], T), T, 0, st>>>(a);
   }
   if (a.totals[1] > 0) k_traj_knots<<<blocks_for(a.totals[1], T), T, 0, st>>>(a);
+  // k_bl_tau: one warp per unit (a (microphone, image) row of knots)
+  if (a.totals[6] > 0) k_bl_tau<<<blocks_for(a.totals[6] * 32, kBlTauThreads), kBlTauThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

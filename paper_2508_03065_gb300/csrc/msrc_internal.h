@@ -75,6 +75,9 @@ struct SceneDev {
   int32_t knot_shift[MSRC_MAX_TIERS];      // up_q for band-limited tiers, else 0
   int32_t up_q;
   int32_t upw_base[MSRC_MAX_TIERS];        // first float of the tier's weight table in upw
+  int64_t bl_tau_base[MSRC_MAX_TIERS];     // first double of the tier's knot delays in bl_tau
+  int64_t bl_units_first[MSRC_MAX_TIERS];  // prefix over upsampled tiers of mics x images x knots
+  int32_t bl_knots[MSRC_MAX_TIERS];        // knots per image in the tier's table (J_c + 1 + 2 up_q)
   int64_t img_base;                        // first entry of this scene in the image table
   int64_t knot_base[MSRC_MAX_TIERS];       // first knot position (double3) per tier
   int64_t knot_units_first[MSRC_MAX_TIERS];// prefix over tiers of (J_t + 1)
@@ -125,6 +128,7 @@ struct LaunchTables {
   const int64_t* z_prefix;       // prefilter units
   const int64_t* item_prefix;    // synthesis items
   const int64_t* red_prefix;     // reduction units
+  const int64_t* bl_prefix;      // knot delays of upsampled tiers
 };
 
 struct DevicePtrs {
@@ -157,14 +161,19 @@ struct DevicePtrs {
   // j0 - up_q + 1 .. j0 + up_q at the virtual knot p / tier_up past knot j0,
   // then their first moment sum_i w_i (i - up_q + 1)
   const float* upw;
+  // and the FP64 delay tau = d fs / c of every (microphone, image, knot) of an
+  // upsampled tier, [mic][image][knot] from bl_tau_base[t]
+  double* bl_tau;
 };
 constexpr int kParamPartialsPerScene = 32 * 48;
+
+constexpr int kUnitKinds = 7;
 
 struct KernelArgs {
   SceneDev scene0;               // used when n_scenes == 1
   const SceneDev* scenes;        // used when n_scenes > 1
   int32_t n_scenes;
-  int64_t totals[6];             // total units per kernel kind (enum, knots, rec, z, item, red)
+  int64_t totals[kUnitKinds];    // total units per kernel kind (enum, knots, rec, z, item, red, bl)
   LaunchTables tab;
   DevicePtrs p;
   float farrow[kFarrowSegs][kFarrowCoef][kMaxTaps];  // coefficients c[s][q][k + L/2] of the powers of w
@@ -187,11 +196,10 @@ __host__ __device__ inline void unpack_image(uint32_t code, int n[3], int p[3]) 
 }
 
 // Shared-memory scratch (floats) of the band-limited record builder for `cnt`
-// images, nk virtual knots and nj knot intervals (nj - 1 + 2 Q knots): FP64
-// delays at the knots, the anchor, the chord rows and the relative delays.
+// images, nk virtual knots and nj knot intervals: the anchor, the chord rows
+// and the relative delays.
 __host__ __device__ inline int64_t bl_scratch_floats(int cnt, int nk, int nj, int Q) {
-  const int nc = nj - 1 + 2 * Q;
-  return int64_t(cnt) * (2 * nc + 1 + nj * (2 * Q + 2) + nk);
+  return int64_t(cnt) * (1 + nj * (2 * Q + 2) + nk);
 }
 
 // Launch entry points (defined in the .cu files).

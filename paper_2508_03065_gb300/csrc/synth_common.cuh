@@ -195,17 +195,17 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
 // (every N = N_c / U samples, N_c the knot spacing); the distance there is
 // sum_i w_p[i] d(j0 - Q + 1 + i) with j0 = floor(k / U), p = k - j0 U and the
 // normalised weights w_p of the windowed-sinc kernel. With tau_j = d_j fs / c
-// at the knots (FP64), Delta = tau_{j0+1} - tau_j0 and the deviations from the
-// chord e_i = tau_{j0-Q+1+i} - tau_j0 - (i - Q + 1) Delta, and since the
-// weights sum to one,
+// at the knots (FP64, computed once per knot by k_bl_tau), Delta =
+// tau_{j0+1} - tau_j0 and the deviations from the chord
+// e_i = tau_{j0-Q+1+i} - tau_j0 - (i - Q + 1) Delta, and since the weights sum
+// to one,
 //   tau(k) = tau_j0 + Delta M_p + sum_i w_p[i] e_i,   M_p = sum_i w_p[i] (i - Q + 1),
 // so that the FP32 sum only carries the small chord deviations; tau_j0 - D
 // and Delta are formed in FP64 and rounded once. D = floor(tau) at knot
-// floor(jf / U) is the image's anchor. Scratch `scr` (16-byte aligned, `cap`
-// floats): tau_s (cnt x nc doubles), D (cnt), chord rows (cnt x nj x (2Q + 2)),
-// phi (cnt x nk). If the item does not fit, the error word gets
-// kErrUpsampleScratch, no record is written and the result is false (the
-// caller then treats the block as empty).
+// floor(jf / U) is the image's anchor. Scratch `scr` (`cap` floats): D (cnt),
+// chord rows (cnt x nj x (2Q + 2)), phi (cnt x nk). If the item does not fit,
+// the error word gets kErrUpsampleScratch, no record is written and the result
+// is false (the caller then treats the block as empty).
 template <int kThreads>
 __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                                 int4* img_s, float* scr, int64_t cap, float* tmin_out, float* tmax_out) {
@@ -214,7 +214,6 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
   const int nk = g.nk;
   const int j0_first = g.jf / U;
   const int nj = (g.jf + nk - 1) / U - j0_first + 1;
-  const int nc = nj - 1 + 2 * Q;
   float tmin = 3.0e38f, tmax = -3.0e38f;
   if (bl_scratch_floats(g.cnt, nk, nj, Q) > cap) {
     if (threadIdx.x == 0) atomicOr(a.p.err, kErrUpsampleScratch);
@@ -222,51 +221,36 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
     *tmax_out = 0.0f;
     return false;
   }
-  double* tau_s = reinterpret_cast<double*>(scr);
-  float* dfl_s = scr + 2 * g.cnt * nc;
+  float* dfl_s = scr;
   float* e_s = dfl_s + g.cnt;
   const int er = 2 * Q + 2;
   float* phi_s = e_s + g.cnt * nj * er;
-  // table index of the first coarse knot j0_first - Q + 1 (the table starts at knot -Q)
-  const int64_t kc0 = S.knot_base[g.t] + (j0_first - Q + 1) + S.knot_shift[g.t];
-  const double* kp = a.p.knot_pos + 3 * kc0;
-  const double* ap = a.p.arr_pos + 3 * kc0;
-  const bool moving = S.arr_moving != 0;
-  const double fs_c = S.fs_over_c;
-  const uint32_t* codes = a.p.img_code + S.img_base + S.tier_first[g.t] + g.img0;
+  const int nkt = S.bl_knots[g.t];
+  // delays of image ib: rows[ib * nkt + j + Q] is knot j (the table starts at knot -Q)
+  const double* rows = a.p.bl_tau + S.bl_tau_base[g.t] +
+                       (int64_t(g.mic) * S.tier_count[g.t] + g.img0) * nkt + Q;
   const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
-  const double* mic = S.mics[g.mic];
-  for (int pidx = threadIdx.x; pidx < g.cnt * nc; pidx += kThreads) {
-    const int ib = pidx / nc;
-    const int c = pidx - ib * nc;
-    int n[3], p[3];
-    unpack_image(codes[ib], n, p);
-    double acc = 0.0;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const double m = mic[d] + (moving ? ap[3 * c + d] : 0.0);
-      const double v = (1.0 - 2.0 * p[d]) * kp[3 * c + d] + 2.0 * n[d] * S.dims[d] - m;
-      acc = fma(v, v, acc);
-    }
-    const double tau = fast_sqrt(acc) * fs_c;
-    tau_s[pidx] = tau;
-    if (c == Q - 1) {  // knot floor(jf / U): the anchor
-      const double Dfl = floor(tau);
+  for (int pidx = threadIdx.x; pidx < g.cnt * nj; pidx += kThreads) {
+    const int ib = pidx / nj;
+    const int jr = pidx - ib * nj;
+    const double* row = rows + int64_t(ib) * nkt;
+    const double Dfl = floor(row[j0_first]);  // the anchor, knot floor(jf / U)
+    if (jr == 0) {
       dfl_s[ib] = float(Dfl);
       img_s[ib] = make_int4(g.jf * g.N - int(Dfl), __float_as_int(float(Dfl) - 0.5f / kFarrowSegs),
                             __float_as_int(__ldg(gain + ib)), 0);
     }
-  }
-  __syncthreads();
-  for (int pidx = threadIdx.x; pidx < g.cnt * nj; pidx += kThreads) {
-    const int ib = pidx / nj;
-    const int jr = pidx - ib * nj;
-    const double* tv = tau_s + ib * nc + jr;  // knots j0 - Q + 1 .. j0 + Q
+    const double* tv = row + (j0_first + jr - Q + 1);  // knots j0 - Q + 1 .. j0 + Q
     const double t0 = tv[Q - 1];
     const double dl = tv[Q] - t0;
+    // chord value at knot i: t0 + (i - Q + 1) dl = base + i dl (i a constant
+    // after unrolling); knots j0 and j0 + 1 lie on the chord (e = 0)
+    const double base = fma(-double(Q - 1), dl, t0);
     float* E = e_s + pidx * er;
-    for (int i = 0; i < 2 * Q; ++i) E[i] = float(tv[i] - t0 - double(i - Q + 1) * dl);
-    E[2 * Q] = float(t0 - double(dfl_s[ib]));
+#pragma unroll
+    for (int i = 0; i < 2 * kMaxUpHalfwidth; ++i)
+      if (i < 2 * Q) E[i] = (i == Q - 1 || i == Q) ? 0.0f : float(tv[i] - fma(double(i), dl, base));
+    E[2 * Q] = float(t0 - Dfl);
     E[2 * Q + 1] = float(dl);
   }
   __syncthreads();

@@ -165,6 +165,16 @@ def config2() -> SceneSpec:
         name="room 10x8x4 m, order 20 (92168 images), 48 kHz, 4 s pink noise, circle 1.5 m/s")
 
 
+def config2_upsampled(rate_hz: float = 50.0, U: int = 10) -> SceneSpec:
+    """The order-20 scene with its last tier (reflection counts above 8, most
+    of the images) on band-limited knots: knots at rate_hz, U virtual knots per
+    interval (records every fs / (rate_hz U) samples; 50 Hz x 10 keeps the
+    500 Hz record spacing of config2)."""
+    base = config2()
+    return replace(base, tiers=[(2, 48000.0), (8, 4000.0), (RHO_INF, rate_hz, U)],
+                   name=base.name + f", last tier on {rate_hz:g} Hz knots upsampled x{U}")
+
+
 def config3_scene(s: int) -> SceneSpec:
     """One of the 256 batched scenes (seed 1000+s)."""
     rng = np.random.default_rng(1000 + s)

@@ -90,3 +90,15 @@ def test_batch_mixing_linear_and_upsampled_tiers():
     for s, y, y1 in zip(specs, ys, single):
         assert np.array_equal(y, y1)
         assert rel_l2(y[0], oracle_full(s)) < TOL
+
+
+@pytest.mark.parametrize("rate,U", [(50.0, 10), (5.0, 100)])
+def test_order20_upsampled_full_size_sampled(rate, U):
+    """The order-20, 48 kHz, 4 s scene (92 168 images) with its last tier on
+    band-limited knots, in the bench's launch configuration, on sampled outputs
+    the oracle evaluates one by one."""
+    spec = W.config2_upsampled(rate, U)
+    y = gpu_run([spec])[0][0]
+    idx = np.concatenate([np.arange(0, 192000, 192000 // 24), [191999, 100, 101, 57000, 57001]])
+    ref = oracle.y_at(oracle_scene(spec), spec.x.astype(np.float64), idx)
+    assert rel_l2(y[idx], ref) < TOL
