@@ -62,6 +62,7 @@ class _Scene(ctypes.Structure):
         ("arr_duration", ctypes.c_double),
         ("tier_up", ctypes.c_int32 * 4),
         ("up_halfwidth", ctypes.c_int32),
+        ("delay_model", ctypes.c_int32),
     ]
 
 
@@ -82,6 +83,7 @@ def _load():
             lib.oracle_enumerate.argtypes = [_S, _I32, _I32, _I32, _I32, _I32, _D]
             lib.oracle_source_position.argtypes = [_S, _D, L, _D]
             lib.oracle_image_distance.argtypes = [_S, L, _D, L, _D]
+            lib.oracle_knot_delay.argtypes = [_S, L, _D, L, _D]
             lib.oracle_delay_gain.argtypes = [_S, L, _I64, L, _D, _D, _D]
             lib.oracle_tap_weights.argtypes = [_S, _D, L, _D]
             lib.oracle_window.argtypes = [_S, _D, L, _D]
@@ -113,6 +115,8 @@ class Scene:
     tier. upsample U > 1 (dividing the step) interpolates the knots' distances
     band-limited to U virtual knots per interval (Kaiser(8)-windowed sinc over
     2 up_halfwidth knots, normalised), then linearly.
+    delay_model: 0 the knot distance is taken at the reception time; 1 it is
+    the emission-time (retarded) path length c tau, c tau = |r_i(t - tau) - m(t)|.
     """
 
     dims: Sequence[float]
@@ -135,6 +139,7 @@ class Scene:
     arr_n_ctrl: int = 0
     arr_duration: float = 1.0
     up_halfwidth: int = 4
+    delay_model: int = 0
 
     def to_c(self) -> _Scene:
         s = _Scene()
@@ -163,6 +168,7 @@ class Scene:
         s.tier_step[:] = step
         s.tier_up[:] = up
         s.up_halfwidth = int(self.up_halfwidth)
+        s.delay_model = int(self.delay_model)
         s.taps = int(self.taps)
         s.window = int(self.window)
         s.traj_kind = int(self.traj_kind)
@@ -220,6 +226,15 @@ def image_distance(scene: Scene, idx: int, t) -> np.ndarray:
     out = np.zeros(t.size)
     sc = scene.to_c()
     _load().oracle_image_distance(ctypes.byref(sc), int(idx), _dp(t), t.size, _dp(out))
+    return out
+
+
+def knot_delay(scene: Scene, idx: int, t) -> np.ndarray:
+    """Delay (s) of image idx at times t under the scene's delay model."""
+    t = np.ascontiguousarray(np.atleast_1d(t), np.float64)
+    out = np.zeros(t.size)
+    sc = scene.to_c()
+    _load().oracle_knot_delay(ctypes.byref(sc), int(idx), _dp(t), t.size, _dp(out))
     return out
 
 

@@ -141,17 +141,43 @@ def synthesize(scene, x, n_out, mic_index=0):
                 break
         imgs.append((sign, off, beta, step, up))
 
-    def dist(sign, off, t):
-        q = source(scene, t)
-        m = mic_at(scene, mic, t)
+    def dist_at(sign, off, te, m):
+        q = source(scene, te)
         return math.sqrt(sum((sign[d] * q[d] + off[d] - m[d]) ** 2 for d in range(3)))
+
+    def dist(sign, off, t):
+        m = mic_at(scene, mic, t)
+        if getattr(scene, "delay_model", 0) != 1:
+            return dist_at(sign, off, t, m)
+        # emission-time path length: c tau = |r(t - tau) - m(t)|, by bisection
+        # (c tau - |r(t - tau) - m| increases with tau below the speed of sound)
+        lo, hi = 0.0, 1.0
+        while scene.c * hi - dist_at(sign, off, t - hi, m) < 0.0:
+            hi *= 2.0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if scene.c * mid - dist_at(sign, off, t - mid, m) < 0.0:
+                lo = mid
+            else:
+                hi = mid
+            if hi - lo <= 1e-17:
+                break
+        return scene.c * 0.5 * (lo + hi)
 
     def kaiser8(u):
         z = max(0.0, 1.0 - (u / Q) ** 2)
         return _bessel_i0(8.0 * math.sqrt(z)) / _bessel_i0(8.0)
 
+    memo = {}
+
     def point(sign, off, step, up, k):
-        # distance at interpolation point k (sample k * step / up)
+        # distance at interpolation point k (sample k * step / up), memoised
+        key = (sign, off, step, up, k)
+        if key not in memo:
+            memo[key] = point_eval(sign, off, step, up, k)
+        return memo[key]
+
+    def point_eval(sign, off, step, up, k):
         if up == 1:
             return dist(sign, off, k * step / scene.fs)
         j0 = math.floor(k / up)

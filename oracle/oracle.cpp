@@ -14,7 +14,9 @@
 //     image i is in tier t (by rho_i); its distance d_i is evaluated exactly at
 //     knots n_j = j*N_t and linearly interpolated to every audio sample;
 //   * delay tau_i(n) = d_i(n) fs / c and gain A_i(n) = beta_i / (4 pi d_i(n))
-//     (Sec. II-A, text after Eq. 2; Sec. II-C, text before Eq. 8);
+//     (Sec. II-A, text after Eq. 2; Sec. II-C, text before Eq. 8); d_i at a
+//     knot is the distance at the reception time, or (delay model 1) the
+//     emission-time path length c tau with c tau = |r_i(t - tau) - m(t)|;
 //   * discrete time-varying fractional delay (Sec. II-B): the ideal delay kernel
 //     sin(pi u)/(pi u), truncated to L taps k = -L/2 .. L/2-1 and windowed
 //     (Hann or Kaiser) -- or a Farrow polynomial per tap (Eq. 3) whose
@@ -38,6 +40,8 @@
 #include <complex>
 #include <cstdint>
 #include <cstring>
+#include <limits>
+#include <type_traits>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
@@ -83,6 +87,9 @@ struct OracleScene {
                           //   distance at U virtual knots per interval from a band-limited
                           //   interpolation of the knots, then linear between virtual knots
   int32_t up_halfwidth;   // half-width Q (knots) of that interpolation kernel
+  int32_t delay_model;    // 0: the knot distance is |r_i(t) - m(t)| at the reception time t;
+                          // 1: it is the emission-time (retarded) path length c tau with
+                          //    c tau = |r_i(t - tau) - m(t)|
 };
 
 }  // extern "C"
@@ -242,6 +249,54 @@ T image_distance(const OracleScene& S, const Params<T>& P, const Image& im, doub
   return std::sqrt(acc);
 }
 
+// Emission-time (retarded) delay at reception time t (s): the tau > 0 with
+// c tau = |r_i(t - tau) - m(t)|, i.e. the sound that reaches the microphone at
+// t left the moving image at t - tau (the Green's function of Sec. II-A
+// integrated along the image's path; Sec. II-A's delta(t - t' - R/c) read with
+// R measured from the emission point). Newton's method from the reception-time
+// distance, with the path's rate of change by a central difference (which only
+// sets the rate of convergence), until the step is below 1e-15 s. The
+// function t_e -> t_e + |r_i(t_e) - m| / c is increasing below the speed of
+// sound, so the root is unique.
+double retarded_delay(const OracleScene& S, const Params<double>& P, const Image& im, double t) {
+  double m[3];
+  mic_position(S, t, m);
+  auto dist = [&](double te) {
+    double s[3];
+    source_position(S, P, te, s);
+    double acc = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double r = (1.0 - 2.0 * im.p[d]) * s[d] + 2.0 * im.n[d] * S.dims[d] - m[d];
+      acc += r * r;
+    }
+    return std::sqrt(acc);
+  };
+  double tau = dist(t) / S.c;
+  const double h = 1e-6;
+  for (int it = 0; it < 100; ++it) {
+    const double te = t - tau;
+    const double F = S.c * tau - dist(te);
+    const double dF = S.c + (dist(te + h) - dist(te - h)) / (2.0 * h);
+    const double step = F / dF;
+    tau -= step;
+    if (std::fabs(step) < 1e-15) break;
+  }
+  return tau;
+}
+
+// Distance that sets an image's delay and gain at knot time t: the distance at
+// the reception time, or the emission-time path length (delay_model 1; real
+// arithmetic only: the complex-step gradients cover the reception-time model).
+template <class T>
+T knot_distance(const OracleScene& S, const Params<T>& P, const Image& im, double t) {
+  if (S.delay_model != 1) return image_distance(S, P, im, t);
+  if constexpr (std::is_same<T, double>::value) {
+    return S.c * retarded_delay(S, P, im, t);
+  } else {
+    return T(std::numeric_limits<double>::quiet_NaN());
+  }
+}
+
 template <class T>
 T image_beta(const Params<T>& P, const Image& im) {
   T b = T(1.0);
@@ -332,7 +387,7 @@ T upsampled_distance(const OracleScene& S, const Params<T>& P, const Image& im, 
   }
   T acc = T(0.0);
   for (int i = 0; i < 2 * Q; ++i)
-    acc += (w[i] / wsum) * image_distance(S, P, im, double((j0 - Q + 1 + i) * N) / S.fs);
+    acc += (w[i] / wsum) * knot_distance(S, P, im, double((j0 - Q + 1 + i) * N) / S.fs);
   return acc;
 }
 
@@ -345,10 +400,10 @@ void delay_gain(const OracleScene& S, const Params<T>& P, const Image& im, long 
   const long j = n / N;
   const long nj = j * N;
   const double s = double(n - nj) / double(N);
-  T dj = (U == 1) ? image_distance(S, P, im, double(nj) / S.fs) : upsampled_distance(S, P, im, Nc, U, j);
+  T dj = (U == 1) ? knot_distance(S, P, im, double(nj) / S.fs) : upsampled_distance(S, P, im, Nc, U, j);
   T d = dj;
   if (s != 0.0) {
-    T dj1 = (U == 1) ? image_distance(S, P, im, double(nj + N) / S.fs) : upsampled_distance(S, P, im, Nc, U, j + 1);
+    T dj1 = (U == 1) ? knot_distance(S, P, im, double(nj + N) / S.fs) : upsampled_distance(S, P, im, Nc, U, j + 1);
     d = dj + s * (dj1 - dj);
   }
   *dist = d;
@@ -422,6 +477,13 @@ void oracle_source_position(const OracleScene* S, const double* t, long n_t, dou
 }
 
 // Exact distance of image `idx` (enumeration order) at times t[].
+// Delay (s) of image idx at knot times t under the scene's delay model.
+void oracle_knot_delay(const OracleScene* S, long idx, const double* t, long n_t, double* out) {
+  const std::vector<Image> imgs = enumerate_images(*S);
+  Params<double> P = params_from<double>(*S);
+  for (long i = 0; i < n_t; ++i) out[i] = knot_distance(*S, P, imgs[idx], t[i]) / S->c;
+}
+
 void oracle_image_distance(const OracleScene* S, long idx, const double* t, long n_t, double* out) {
   std::vector<Image> imgs = enumerate_images(*S);
   Params<double> P = params_from<double>(*S);

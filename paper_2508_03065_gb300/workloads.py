@@ -35,6 +35,7 @@ class SceneSpec:
     farrow_order: int = 4                   # window FARROW_LS: polynomial order
     passband: float = 0.9                   # window FARROW_LS: passband edge / pi
     up_halfwidth: int = 4                   # knot upsampler: kernel half-width (knots)
+    delay_model: int = 0                    # 0 distance at reception time, 1 emission-time path length
     arr_kind: int = -1                      # microphone array motion: -1 static, else a
     arr_traj: List[float] = field(default_factory=list)   # trajectory a(t) of the source's kinds;
     arr_n_ctrl: int = 0                     # microphones sit at mics + a(t) - a(0)

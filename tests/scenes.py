@@ -11,7 +11,8 @@ def oracle_scene(spec: W.SceneSpec, mic: int = 0, **override) -> oracle.Scene:
         fs=spec.fs, c=spec.c, tiers=spec.tier_steps(), taps=spec.taps, window=spec.window,
         kaiser_beta=spec.kaiser_beta, traj_kind=spec.traj_kind, traj=list(spec.traj),
         n_ctrl=spec.n_ctrl, duration=spec.duration, arr_kind=spec.arr_kind, arr_traj=list(spec.arr_traj),
-        arr_n_ctrl=spec.arr_n_ctrl, arr_duration=spec.arr_duration, up_halfwidth=spec.up_halfwidth)
+        arr_n_ctrl=spec.arr_n_ctrl, arr_duration=spec.arr_duration, up_halfwidth=spec.up_halfwidth,
+        delay_model=spec.delay_model)
     if spec.window == 2:  # least-squares Farrow design: the oracle's own
         from oracle import gls
         kw["farrow"] = gls.design(spec.taps, spec.farrow_order, spec.passband)
