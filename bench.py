@@ -59,14 +59,17 @@ def parse():
     ap.add_argument("--seconds", type=float, default=None,
                     help="shorten the scene (profiling captures); the benchmark default is 4 s")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--delay-model", type=int, default=0, choices=[0, 1],
+                    help="knot distances at the reception time (0, the benchmark) or emission-time path lengths (1)")
     ap.add_argument("--tile-config", type=int, default=None, help="synthesis tile configuration id")
     ap.add_argument("--batched-scenes", type=int, default=256,
                     help="scenes of the batched comparison (0 disables it)")
-    ap.add_argument("--sections", default="batched,backward,filters,moving_array,upsampled,e1",
+    ap.add_argument("--sections", default="batched,backward,filters,moving_array,upsampled,emission_time,e1",
                     help="extra measurements in the JSON line: batched, backward, array, filters, moving_array, "
-                         "upsampled, e1")
+                         "upsampled, emission_time, e1")
     ap.add_argument("--only", default=None,
-                    choices=["backward", "array", "batched", "filters", "moving_array", "upsampled", "e1"],
+                    choices=["backward", "array", "batched", "filters", "moving_array", "upsampled", "emission_time",
+                             "e1"],
                     help="run one extra section alone (profiling captures) and print it")
     return ap.parse_args()
 
@@ -186,7 +189,8 @@ def workload_config(spec, tier_counts=None):
 
     return {"workload": spec.name, "images": W.image_count(spec.K), "n_out": spec.n_in, "fs": spec.fs,
             "taps": spec.taps, "window": "kaiser(8)" if spec.window == 1 else "hann",
-            "tiers": [[r if r < W.RHO_INF else "rest", hz] for r, hz in spec.tiers],
+            "tiers": [[t[0] if t[0] < W.RHO_INF else "rest"] + list(t[1:]) for t in spec.tiers],
+            "delay": "emission time" if getattr(spec, "delay_model", 0) == 1 else "reception time",
             "l2": "every step writes and reads the per-(block, tile) partial sums "
                   + (f"({partial_bytes(spec, tier_counts) / 1e6:.0f} MB, " if tier_counts else "(")
                   + "larger than the 129 MB L2)"}
@@ -223,6 +227,8 @@ def run_gpu(args):
         n = int(args.seconds * spec.fs)
         spec = W.with_signal(spec, spec.x[:n])
         spec.duration = n / spec.fs
+    if args.delay_model:
+        spec.delay_model = args.delay_model
     if world > 1 and rank > 0:  # an independent scene per rank (own source signal)
         spec = W.with_signal(spec, W.pink(2 + 1000 * rank, spec.n_in))
     if args.tile_config is not None:
@@ -326,6 +332,8 @@ def run_gpu(args):
             line["moving_array"] = run_moving_array(args, torch, api, W)
         if "upsampled" in sections:
             line["upsampled"] = run_upsampled(args, torch, api, W)
+        if "emission_time" in sections:
+            line["emission_time"] = run_emission_time(args, torch, api, W)
         if "e1" in sections:
             line["e1"] = run_e1(args, torch, api, W)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -500,6 +508,17 @@ def run_moving_array(args, torch, api, W):
                            arr_duration=base.duration))])
 
 
+def run_emission_time(args, torch, api, W):
+    """The order-20 scene with knot distances at the reception time (the main
+    line) vs emission-time (retarded) path lengths: an FP64 Newton solve per
+    image and item at the anchor knot, FP32 Newton increments at the others."""
+    from dataclasses import replace
+
+    base = W.config2()
+    return _time_variants(torch, api, [("reception_time", base),
+                                       ("emission_time", replace(base, delay_model=1))])
+
+
 def run_upsampled(args, torch, api, W):
     """The order-20 scene with its last tier on linear 500 Hz knots (the main
     line) vs band-limited knots at 50 Hz x 10 and 5 Hz x 100 (records at the
@@ -555,7 +574,8 @@ def run_only(args):
     from paper_2508_03065_gb300 import workloads as W
 
     fn = {"backward": run_backward, "array": run_array, "batched": run_batched, "filters": run_filters,
-          "moving_array": run_moving_array, "upsampled": run_upsampled, "e1": run_e1}[args.only]
+          "moving_array": run_moving_array, "upsampled": run_upsampled,
+          "emission_time": run_emission_time, "e1": run_e1}[args.only]
     print(json.dumps({args.only: fn(args, torch, api, W)}), flush=True)
     return 0
 

@@ -89,6 +89,15 @@ typedef struct {
                                 the end follow the trajectory's extension (line and circle
                                 continue, the spline clamps). Forward synthesis only. */
   int32_t upsample_halfwidth;/* Q, half-width of that kernel in knots: 0 (= 4) or 1..8 */
+  int32_t delay_model;       /* 0: an image's distance at a knot is taken at the reception time,
+                                d = |r_i(t) - m(t)| (Sec. II-A, Eq. 2 evaluated at the output time);
+                                1: emission-time (retarded) path length d = c tau with
+                                c tau = |r_i(t - tau) - m(t)|, the sound reaching the microphone
+                                at t having left the moving image at t - tau. Delay and gain
+                                follow from d in both models. Model 1 is forward only, needs
+                                linear knot interpolation (tier_upsample <= 1) and the path valid
+                                over [-(largest delay), end] (line and circle continue before
+                                t = 0, the spline clamps). */
 } msrc_room_desc;
 
 /* Source trajectory s(t) (Sec. II-C: a band-limited trajectory p(n)). */

@@ -35,6 +35,7 @@ class RoomDesc(ctypes.Structure):
         ("passband", ctypes.c_double),
         ("tier_upsample", ctypes.c_int32 * 4),
         ("upsample_halfwidth", ctypes.c_int32),
+        ("delay_model", ctypes.c_int32),
     ]
 
 

@@ -26,12 +26,13 @@ class Room:
     """A shoebox room with its image-source settings, trajectory and microphones."""
 
     def __init__(self, dims, beta, fs, max_order, tiers, taps=32, window=0, kaiser_beta=8.0,
-                 c=343.0, farrow_order=4, passband=0.9, upsample_halfwidth=4):
+                 c=343.0, farrow_order=4, passband=0.9, upsample_halfwidth=4, delay_model=0):
         """tiers: (max reflection count, knot rate in Hz[, upsampling factor U]);
         U > 1 recovers the distance between knots band-limited (see
         msrc_room_desc.tier_upsample). window: 0 Hann- or 1 Kaiser-windowed sinc
         taps, 2 a least-squares Farrow design of order `farrow_order` fitted up
-        to `passband` * pi."""
+        to `passband` * pi. delay_model: 0 distance at the reception time, 1
+        emission-time (retarded) path length (see msrc_room_desc.delay_model)."""
         lib = _lib.load()
         d = _lib.RoomDesc()
         d.dims[:] = [float(v) for v in dims]
@@ -51,6 +52,7 @@ class Room:
         d.tier_rate_hz[:] = rate
         d.tier_upsample[:] = up
         d.upsample_halfwidth = int(upsample_halfwidth)
+        d.delay_model = int(delay_model)
         d.taps = int(taps)
         d.window = int(window)
         d.kaiser_beta = float(kaiser_beta)
@@ -67,7 +69,7 @@ class Room:
     def from_spec(cls, spec) -> "Room":
         room = cls(spec.dims, spec.beta, spec.fs, spec.K, spec.tiers, spec.taps, spec.window,
                    spec.kaiser_beta, spec.c, spec.farrow_order, spec.passband,
-                   getattr(spec, "up_halfwidth", 4))
+                   getattr(spec, "up_halfwidth", 4), getattr(spec, "delay_model", 0))
         room.set_trajectory(spec.traj_kind, spec.traj, spec.duration, spec.mics, spec.n_ctrl)
         if getattr(spec, "arr_kind", -1) >= 0:
             room.set_array_trajectory(spec.arr_kind, spec.arr_traj, spec.arr_duration, spec.arr_n_ctrl)

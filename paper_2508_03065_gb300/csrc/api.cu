@@ -430,7 +430,7 @@ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 struct Plan {
   std::vector<SceneDev> scenes;
   std::vector<int64_t> prefix[kUnitKinds];
-  int64_t totals[kUnitKinds] = {0, 0, 0, 0, 0, 0, 0};
+  int64_t totals[kUnitKinds] = {0, 0, 0, 0, 0, 0, 0, 0};
   int end_bit = 40;
   // byte offsets in the workspace
   size_t off_desc = 0, off_keys_in = 0, off_keys_out = 0, off_vals_in = 0, off_vals_out = 0;
@@ -447,7 +447,7 @@ struct Plan {
   std::vector<int> upw_key;       // U * 64 + Q of each table
   std::vector<int> upw_at;        // its first float
   std::vector<double> upw_l1;     // its largest absolute row sum
-  size_t off_upw = 0, off_bl_tau = 0;
+  size_t off_upw = 0, off_bl_tau = 0, off_dense64 = 0, off_dense_hi = 0, off_dense_lo = 0;
 };
 
 // Workspace layout and per-scene descriptors of one call. Forward mode uses
@@ -463,7 +463,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.scenes.resize(n);
   for (auto& v : P.prefix) v.assign(n + 1, 0);
   int64_t img_acc = 0, knot_acc = 0, z_acc = 0, part_acc = 0;
-  int64_t dxb_acc = 0, kslot_acc = 0, bpart_acc = 0, bl_acc = 0;
+  int64_t dxb_acc = 0, kslot_acc = 0, bpart_acc = 0, bl_acc = 0, dense_acc = 0;
   bool any_moving = false;
   for (int s = 0; s < n; ++s) {
     msrc_room* R = rooms[s];
@@ -633,7 +633,28 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     S.z_len = zhi - zlo;
     S.z_base = z_acc;
     S.part_base = part_acc;
-    // trajectory evaluated at every knot
+    // emission-time delays: the source path table spans the emission times of
+    // every knot, [first knot - tau_bound, last knot] with a margin, in steps
+    // of 1 / (kDenseOver fs)
+    S.delay_model = R->d.delay_model;
+    int64_t u_dense = 0;
+    if (S.delay_model == 1) {
+      if (backward)
+        return fail(MSRC_ERR_UNSUPPORTED, "room %d: reverse mode does not support emission-time delays", s);
+      for (int t = 0; t < S.n_tiers; ++t)
+        if (S.tier_up[t] > 1)
+          return fail(MSRC_ERR_UNSUPPORTED,
+                      "room %d: emission-time delays need linear knot interpolation (tier %d is upsampled)", s, t);
+      const int64_t last = int64_t(std::ceil(t_hi * R->d.fs)) + 4;
+      S.dense_k0 = int64_t(kDenseOver) * (-tau_bound - 4);
+      S.n_dense = int64_t(kDenseOver) * last - S.dense_k0 + 1;
+      S.dense_base = dense_acc;
+      dense_acc += S.n_dense;
+      u_dense = S.n_dense;
+      t_lo = std::min(t_lo, double(S.dense_k0) / (kDenseOver * R->d.fs));
+      t_hi = std::max(t_hi, double(last) / R->d.fs);
+    }
+    // trajectory evaluated at every knot (and every emission time)
     msrc_status vs = validate_traj_range(*R, t_lo, t_hi);
     if (vs != MSRC_OK) return vs;
     // reverse mode scatters one image's samples into shared (segment, column)
@@ -653,7 +674,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     const int64_t u_bl = bl_units;  // (mic, image) rows of FP64 knot delays of upsampled tiers
     if (int64_t(S.n_mics) * S.n_blocks * S.n_tiles >= (int64_t(1) << 31))
       return fail(MSRC_ERR_UNSUPPORTED, "room %d: more than 2^31 work items", s);
-    const int64_t u[kUnitKinds] = {u_enum, u_knots, u_rec, u_z, u_item, u_red, u_bl};
+    const int64_t u[kUnitKinds] = {u_enum, u_knots, u_rec, u_z, u_item, u_red, u_bl, u_dense};
     for (int k = 0; k < kUnitKinds; ++k) {
       P.prefix[k][s + 1] = P.prefix[k][s] + u[k];
       P.totals[k] += u[k];
@@ -684,6 +705,9 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.off_arr = off; off = align256(off + (any_moving ? 24 * size_t(knot_acc) : 0));
   P.off_upw = off; off = align256(off + 4 * P.upw.size());
   P.off_bl_tau = off; off = align256(off + 8 * size_t(bl_acc));
+  P.off_dense64 = off; off = align256(off + 32 * size_t(dense_acc));
+  P.off_dense_hi = off; off = align256(off + 16 * size_t(dense_acc));
+  P.off_dense_lo = off; off = align256(off + 16 * size_t(dense_acc));
   P.off_z = off; off = align256(off + 16 * size_t(z_acc));
   // forward: power 4 of the degree-4 rows; reverse mode: powers 4..5 of the
   // degree-5 rows the gradient kernel reads (zq holds powers 0..3 either way)
@@ -723,6 +747,9 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.arr_pos = reinterpret_cast<double*>(ws + P.off_arr);
   a.p.upw = reinterpret_cast<const float*>(ws + P.off_upw);
   a.p.bl_tau = reinterpret_cast<double*>(ws + P.off_bl_tau);
+  a.p.dense64 = reinterpret_cast<double*>(ws + P.off_dense64);
+  a.p.dense_hi = reinterpret_cast<float4*>(ws + P.off_dense_hi);
+  a.p.dense_lo = reinterpret_cast<float4*>(ws + P.off_dense_lo);
   a.p.zq = reinterpret_cast<float4*>(ws + P.off_z);
   a.p.zp = P.backward ? nullptr : reinterpret_cast<float*>(ws + P.off_zp);
   a.p.zg = P.backward ? reinterpret_cast<float2*>(ws + P.off_zp) : nullptr;
@@ -756,6 +783,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
     a.tab.item_prefix = pre + 4 * n1;
     a.tab.red_prefix = pre + 5 * n1;
     a.tab.bl_prefix = pre + 6 * n1;
+    a.tab.dense_prefix = pre + 7 * n1;
   }
 }
 
@@ -859,6 +887,7 @@ msrc_status msrc_create_room(const msrc_room_desc* desc, msrc_room_t* out) {
     return fail(MSRC_ERR_INVALID_ARG, "farrow_order must be in [1, %d]", kFarrowDeg);
   if (d.window == 2 && !(d.passband >= 0.05 && d.passband <= 0.98))
     return fail(MSRC_ERR_INVALID_ARG, "passband must be in [0.05, 0.98]");
+  if (d.delay_model < 0 || d.delay_model > 1) return fail(MSRC_ERR_INVALID_ARG, "delay_model must be 0 or 1");
   if (d.upsample_halfwidth < 0 || d.upsample_halfwidth > kMaxUpHalfwidth)
     return fail(MSRC_ERR_INVALID_ARG, "upsample_halfwidth must be in [0, %d]", kMaxUpHalfwidth);
   msrc_room* R = new (std::nothrow) msrc_room;

@@ -215,6 +215,28 @@ __global__ void k_bl_tau(const __grid_constant__ KernelArgs a) {
   }
 }
 
+// Source path table of a scene with emission-time delays: s(t) at
+// t = (dense_k0 + k) / (kDenseOver fs), FP64 and as FP32 pairs hi + lo.
+__global__ void k_dense_traj(const __grid_constant__ KernelArgs a) {
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= a.totals[7]) return;
+  int64_t local;
+  const int s = locate(a, a.tab.dense_prefix, gid, &local);
+  const SceneDev& S = scene_of(a, s);
+  const double t = double(S.dense_k0 + local) / (double(kDenseOver) * S.fs);
+  double sp[3];
+  source_position(S, t, sp);
+  const int64_t e = S.dense_base + local;
+  double* o = a.p.dense64 + 4 * e;
+  o[0] = sp[0];
+  o[1] = sp[1];
+  o[2] = sp[2];
+  o[3] = 0.0;
+  const float hx = float(sp[0]), hy = float(sp[1]), hz = float(sp[2]);
+  a.p.dense_hi[e] = make_float4(hx, hy, hz, 0.0f);
+  a.p.dense_lo[e] = make_float4(float(sp[0] - hx), float(sp[1] - hy), float(sp[2] - hz), 0.0f);
+}
+
 }  // namespace
 
 size_t sort_temp_bytes(int64_t n_items, int end_bit) {
@@ -253,6 +275,7 @@ cudaError_t launch_setup(const KernelArgs& a, cudaStream_t st) {
   if (a.totals[1] > 0) k_traj_knots<<<blocks_for(a.totals[1], T), T, 0, st>>>(a);
   // k_bl_tau: one warp per unit (a (microphone, image) row of knots)
   if (a.totals[6] > 0) k_bl_tau<<<blocks_for(a.totals[6] * 32, kBlTauThreads), kBlTauThreads, 0, st>>>(a);
+  if (a.totals[7] > 0) k_dense_traj<<<blocks_for(a.totals[7], T), T, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -160,11 +160,16 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
   float4* um_s = u_s + kThreads * kChunks + 4;                           // moving array
   float4* anc_s = um_s + kThreads * kChunks + 4;                         // 3 x kBlock
   float* phi_s = reinterpret_cast<float*>(anc_s + 3 * kBlock);           // kRecCap + kBlock
+  // emission-time delays: u_s holds the array increments, then 6 x kBlock anchors, then phi
+  float4* an6_s = um_s;
+  float* phi_r = reinterpret_cast<float*>(an6_s + 6 * kBlock);
   __shared__ int s_item;
   __shared__ float s_red[2][kThreads / 32];
   constexpr int kTile = kThreads * kChunks;
   static_assert(4 * (2 * (kTile + 4) + 3 * kBlock) + kRecCap + kBlock <= 4 * kFarrowSegs * kWcap,
                 "prologue scratch");
+  static_assert(4 * ((kTile + 4) + 6 * kBlock) + kRecCap + kBlock <= 4 * kFarrowSegs * kWcap,
+                "prologue scratch (emission-time delays)");
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
 
@@ -185,7 +190,9 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
     // --- delay knots of the block over the tile (records in shared memory)
     float tmin, tmax;
     int cnt = g.cnt;
-    if (S.tier_up[g.t] > 1) {
+    if (S.delay_model == 1) {
+      item_records_ret<kThreads>(a, S, g, rec_s, img_s, u_s, an6_s, phi_r, &tmin, &tmax);
+    } else if (S.tier_up[g.t] > 1) {
       // band-limited knot upsampling: its scratch takes the z window and power rows
       if (!item_records_bl<kThreads>(a, S, g, rec_s, img_s, reinterpret_cast<float*>(smem4),
                                      int64_t(kFarrowSegs) * kWcap * 5, &tmin, &tmax))

@@ -38,6 +38,9 @@ constexpr uint32_t kErrUpsampleScratch = 4u;
 // Band-limited knot upsampling: largest upsampling factor and kernel half-width.
 constexpr int kMaxUpsample = 512;
 constexpr int kMaxUpHalfwidth = 8;
+// Emission-time delays: the source path table holds kDenseOver points per
+// sample (linear interpolation between them is exact to h^2 |s''| / 8).
+constexpr int kDenseOver = 4;
 
 // Per-scene description as the kernels see it. All offsets are in elements of
 // the array they index. Images are stored sorted by (tier, distance at the
@@ -78,6 +81,11 @@ struct SceneDev {
   int64_t bl_tau_base[MSRC_MAX_TIERS];     // first double of the tier's knot delays in bl_tau
   int64_t bl_units_first[MSRC_MAX_TIERS];  // prefix over upsampled tiers of mics x images x knots
   int32_t bl_knots[MSRC_MAX_TIERS];        // knots per image in the tier's table (J_c + 1 + 2 up_q)
+  // emission-time delays (delay_model 1): the source path sampled every
+  // 1 / (kDenseOver fs) s from entry dense_k0 (in those units) on, n_dense
+  // entries from dense_base in the dense tables
+  int32_t delay_model;
+  int64_t dense_base, dense_k0, n_dense;
   int64_t img_base;                        // first entry of this scene in the image table
   int64_t knot_base[MSRC_MAX_TIERS];       // first knot position (double3) per tier
   int64_t knot_units_first[MSRC_MAX_TIERS];// prefix over tiers of (J_t + 1)
@@ -129,6 +137,7 @@ struct LaunchTables {
   const int64_t* item_prefix;    // synthesis items
   const int64_t* red_prefix;     // reduction units
   const int64_t* bl_prefix;      // knot delays of upsampled tiers
+  const int64_t* dense_prefix;   // source path table entries (emission-time delays)
 };
 
 struct DevicePtrs {
@@ -164,16 +173,21 @@ struct DevicePtrs {
   // and the FP64 delay tau = d fs / c of every (microphone, image, knot) of an
   // upsampled tier, [mic][image][knot] from bl_tau_base[t]
   double* bl_tau;
+  // emission-time delays: the source path every 1 / (kDenseOver fs) s as FP64
+  // (x, y, z, 0) and as the FP32 pair hi + lo of each coordinate
+  double* dense64;
+  float4* dense_hi;
+  float4* dense_lo;
 };
 constexpr int kParamPartialsPerScene = 32 * 48;
 
-constexpr int kUnitKinds = 7;
+constexpr int kUnitKinds = 8;
 
 struct KernelArgs {
   SceneDev scene0;               // used when n_scenes == 1
   const SceneDev* scenes;        // used when n_scenes > 1
   int32_t n_scenes;
-  int64_t totals[kUnitKinds];    // total units per kernel kind (enum, knots, rec, z, item, red, bl)
+  int64_t totals[kUnitKinds];    // total units per kernel kind (enum, knots, rec, z, item, red, bl, dense)
   LaunchTables tab;
   DevicePtrs p;
   float farrow[kFarrowSegs][kFarrowCoef][kMaxTaps];  // coefficients c[s][q][k + L/2] of the powers of w

@@ -277,6 +277,196 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
   return true;
 }
 
+// item_records for emission-time (retarded) delays (delay_model 1): the
+// distance at reception knot j is the path length d_j = c tau_j with
+// c tau_j = |r_i(t_j - tau_j) - m(t_j)|; records, delay and gain follow from
+// d_j exactly as for reception-time distances.
+//   Anchor (knot jf, FP64, per image): the first-order guess
+//   tau_0 = d(t) / (c + u . sigma o s'(t)) (reception-time distance, unit
+//   vector and source velocity), one Newton step on F(tau) = tau - |Delta(tau)| fs / c
+//   (source at the emission time read from the path table, linear between its
+//   points, kDenseOver per sample; slope in FP32) to tau_a, and the residual
+//   eps = |Delta(tau_a)| fs / c - tau_a, which the FP32 stage absorbs.
+//   Other knots (FP32, per image and knot): delta_j = tau_j - tau_a solves
+//   delta = (d_j - d_a) fs / c + eps, d_a = |Delta(tau_a)|; two Newton steps
+//   from delta = eps + r jj N (r the anchor's rate of change of the delay).
+//   d_j - d_a uses the exact identity of knot_increment with the vector change
+//   v = sigma o (s(e_j) - s(e_a)) - (m_j - m_a). The source displacement
+//   between the two emission points comes from the FP32 pair tables (hi
+//   differences of nearby positions are exact); the second step reads the
+//   table again only when its emission point lies in another segment.
+// Scratch: um_s (nk, moving array), an6 (6 x cnt float4), phi_s (cnt x nk).
+struct RetAnchor {
+  float4 A, H, Lw, dA, Sg, E;
+};
+
+__device__ __forceinline__ float ret_increment(const RetAnchor& r, const float4 um, const float4* HI,
+                                               const float4* LO, int64_t base_idx, int64_t kmax, float fsc,
+                                               float c4, float delta) {
+  const int64_t Ka = int64_t(__float_as_int(r.Sg.w)) + base_idx;
+  int64_t I = -1;
+  float dx = 0.0f, dy = 0.0f, dz = 0.0f, bx = 0.0f, by = 0.0f, bz = 0.0f;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const float gq = fmaf(-float(kDenseOver), delta, r.H.w);
+    const float gi = floorf(gq);
+    const float fr = gq - gi;
+    const int64_t In = min(max(Ka + int64_t(gi), int64_t(0)), kmax);
+    if (In != I) {  // the emission point left the table segment read last: read its own
+      I = In;
+      const float4 h0 = HI[I], h1 = HI[I + 1], l0 = LO[I], l1 = LO[I + 1];
+      dx = (h1.x - h0.x) + (l1.x - l0.x);
+      dy = (h1.y - h0.y) + (l1.y - l0.y);
+      dz = (h1.z - h0.z) + (l1.z - l0.z);
+      // displacement of the segment start from the anchor's emission point
+      bx = fmaf(-r.H.w, r.dA.x, (h0.x - r.H.x) + (l0.x - r.Lw.x));
+      by = fmaf(-r.H.w, r.dA.y, (h0.y - r.H.y) + (l0.y - r.Lw.y));
+      bz = fmaf(-r.H.w, r.dA.z, (h0.z - r.H.z) + (l0.z - r.Lw.z));
+    }
+    const float frc = (In == Ka + int64_t(gi)) ? fr : gq - float(I - Ka);  // clamped: extrapolate
+    const float vx = fmaf(r.Sg.x, fmaf(frc, dx, bx), -um.x);
+    const float vy = fmaf(r.Sg.y, fmaf(frc, dy, by), -um.y);
+    const float vz = fmaf(r.Sg.z, fmaf(frc, dz, bz), -um.z);
+    const float q = fmaf(2.0f, fmaf(r.A.x, vx, fmaf(r.A.y, vy, r.A.z * vz)), fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
+    const float dd = __fdividef(q, r.A.w + sqrtf(fmaf(r.A.w, r.A.w, q)));
+    const float gs = __fdividef((r.A.x + vx) * r.Sg.x * dx + (r.A.y + vy) * r.Sg.y * dy + (r.A.z + vz) * r.Sg.z * dz,
+                                r.A.w + dd);
+    delta -= __fdividef(delta - fmaf(dd, fsc, r.E.x), fmaf(gs, c4, 1.0f));
+  }
+  return delta;
+}
+
+template <int kThreads>
+__device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
+                                 int4* img_s, float4* um_s, float4* an6, float* phi_s, float* tmin_out,
+                                 float* tmax_out) {
+  const bool moving = S.arr_moving != 0;
+  const double* ap = a.p.arr_pos + 3 * (S.knot_base[g.t] + g.jf);
+  if (moving) {
+    for (int jj = threadIdx.x; jj < g.nk; jj += kThreads) {
+      const float mx = float(ap[3 * jj] - ap[0]);
+      const float my = float(ap[3 * jj + 1] - ap[1]);
+      const float mz = float(ap[3 * jj + 2] - ap[2]);
+      um_s[jj] = make_float4(mx, my, mz, 0.0f);
+    }
+  }
+  const double fs_c = S.fs_over_c;
+  const double* kp = a.p.knot_pos + 3 * (S.knot_base[g.t] + g.jf);
+  double ma[3] = {S.mics[g.mic][0], S.mics[g.mic][1], S.mics[g.mic][2]};
+  if (moving)
+    for (int d = 0; d < 3; ++d) ma[d] += ap[d];
+  const uint32_t* codes = a.p.img_code + S.img_base + S.tier_first[g.t] + g.img0;
+  const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
+  const double* P64 = a.p.dense64 + 4 * S.dense_base;
+  const float4* HI = a.p.dense_hi + S.dense_base;
+  const float4* LO = a.p.dense_lo + S.dense_base;
+  const int64_t kmax = S.n_dense - 2;  // last table index whose successor exists
+  const double n_a = double(g.jf) * g.N;
+  const float c4 = float(kDenseOver) * S.fsc;  // delay change (samples) per metre and table step
+  // table index of the reception time itself (the velocity there seeds the anchor)
+  const int64_t k_rec = min(max(int64_t(kDenseOver) * (int64_t(g.jf) * g.N) - S.dense_k0, int64_t(0)), kmax);
+  const float4 vr0 = HI[k_rec], vr1 = HI[k_rec + 1];
+  for (int ib = threadIdx.x; ib < g.cnt; ib += kThreads) {
+    int n[3], p[3];
+    unpack_image(codes[ib], n, p);
+    double o[3], sg[3];
+    for (int d = 0; d < 3; ++d) {
+      sg[d] = 1.0 - 2.0 * p[d];
+      o[d] = fma(2.0 * n[d], S.dims[d], -ma[d]);
+    }
+    double tau;
+    {
+      const double D0 = fma(sg[0], kp[0], o[0]), D1 = fma(sg[1], kp[1], o[1]), D2 = fma(sg[2], kp[2], o[2]);
+      const double d0 = fast_sqrt(fma(D0, D0, fma(D1, D1, D2 * D2)));
+      const float gsl = (float(D0) * float(sg[0]) * (vr1.x - vr0.x) + float(D1) * float(sg[1]) * (vr1.y - vr0.y) +
+                         float(D2) * float(sg[2]) * (vr1.z - vr0.z)) / float(d0) * c4;
+      tau = d0 * fs_c * double(1.0f / (1.0f + gsl));
+    }
+    double Dv[3];
+    double dist = 0.0;
+    int64_t k = 0;
+    double f = 0.0;
+    float4 h0, h1;
+    auto eval = [&](double tv) {
+      const double x = double(kDenseOver) * (n_a - tv) - double(S.dense_k0);
+      k = min(max(int64_t(floor(x)), int64_t(0)), kmax);
+      f = x - double(k);
+      const double* q0 = P64 + 4 * k;
+      h0 = HI[k];
+      h1 = HI[k + 1];
+      double acc = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        const double sd = fma(f, q0[4 + d] - q0[d], q0[d]);
+        Dv[d] = fma(sg[d], sd, o[d]);
+        acc = fma(Dv[d], Dv[d], acc);
+      }
+      dist = fast_sqrt(acc);
+    };
+    eval(tau);
+    {
+      const float gsl = (float(Dv[0]) * float(sg[0]) * (h1.x - h0.x) + float(Dv[1]) * float(sg[1]) * (h1.y - h0.y) +
+                         float(Dv[2]) * float(sg[2]) * (h1.z - h0.z)) / float(dist) * c4;
+      tau -= (tau - dist * fs_c) * double(1.0f / (1.0f + gsl));
+    }
+    eval(tau);
+    const float eps = float(fma(dist, fs_c, -tau));
+    const double Dfl = floor(tau);
+    // the anchor's emission point: table index k, fraction f, its FP32 pair
+    const float4 l0 = LO[k], l1 = LO[k + 1];
+    const float dsx = (h1.x - h0.x) + (l1.x - l0.x);
+    const float dsy = (h1.y - h0.y) + (l1.y - l0.y);
+    const float dsz = (h1.z - h0.z) + (l1.z - l0.z);
+    const float Ax = float(Dv[0]), Ay = float(Dv[1]), Az = float(Dv[2]), da = float(dist);
+    const float gsl = (Ax * float(sg[0]) * dsx + Ay * float(sg[1]) * dsy + Az * float(sg[2]) * dsz) / da * c4;
+    an6[6 * ib + 0] = make_float4(Ax, Ay, Az, da);
+    an6[6 * ib + 1] = make_float4(h0.x, h0.y, h0.z, float(f));
+    an6[6 * ib + 2] = make_float4(l0.x, l0.y, l0.z, float(tau - Dfl));
+    // table step of the path there; rate of change of the delay per output sample (still microphone)
+    an6[6 * ib + 3] = make_float4(dsx, dsy, dsz, gsl / (1.0f + gsl));
+    an6[6 * ib + 4] = make_float4(float(sg[0]), float(sg[1]), float(sg[2]), __int_as_float(int(k)));
+    an6[6 * ib + 5] = make_float4(eps, float(Dfl), 0.0f, 0.0f);
+    img_s[ib] = make_int4(g.jf * g.N - int(Dfl), __float_as_int(float(Dfl) - 0.5f / kFarrowSegs),
+                          __float_as_int(__ldg(gain + ib)), 0);
+  }
+  __syncthreads();
+  const int nk = g.nk;
+  const float fsc = S.fsc;
+  float tmin = 3.0e38f, tmax = -3.0e38f;
+  const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  // two (image, knot) units per pass: their table reads overlap
+  const int units = g.cnt * nk;
+  for (int p0 = threadIdx.x; p0 < units; p0 += 2 * kThreads) {
+    const int p1 = p0 + kThreads;
+    const int q1 = p1 < units ? p1 : p0;
+    const int ib0 = p0 / nk, jj0 = p0 - ib0 * nk;
+    const int ib1 = q1 / nk, jj1 = q1 - ib1 * nk;
+    const RetAnchor r0{an6[6 * ib0], an6[6 * ib0 + 1], an6[6 * ib0 + 2], an6[6 * ib0 + 3], an6[6 * ib0 + 4],
+                       an6[6 * ib0 + 5]};
+    const RetAnchor r1{an6[6 * ib1], an6[6 * ib1 + 1], an6[6 * ib1 + 2], an6[6 * ib1 + 3], an6[6 * ib1 + 4],
+                       an6[6 * ib1 + 5]};
+    const float4 um0 = moving ? um_s[jj0] : zero4;
+    const float4 um1 = moving ? um_s[jj1] : zero4;
+    const float de0 = ret_increment(r0, um0, HI, LO, int64_t(kDenseOver) * jj0 * g.N, kmax, fsc, c4,
+                                    fmaf(r0.dA.w, float(jj0 * g.N), r0.E.x));
+    const float de1 = ret_increment(r1, um1, HI, LO, int64_t(kDenseOver) * jj1 * g.N, kmax, fsc, c4,
+                                    fmaf(r1.dA.w, float(jj1 * g.N), r1.E.x));
+    const float phi0 = r0.Lw.w + de0;
+    phi_s[p0] = phi0;
+    tmin = fminf(tmin, r0.E.y + phi0);
+    tmax = fmaxf(tmax, r0.E.y + phi0);
+    if (p1 < units) {
+      const float phi1 = r1.Lw.w + de1;
+      phi_s[p1] = phi1;
+      tmin = fminf(tmin, r1.E.y + phi1);
+      tmax = fmaxf(tmax, r1.E.y + phi1);
+    }
+  }
+  __syncthreads();
+  records_from_phi<kThreads>(g, phi_s, rec_s);
+  *tmin_out = tmin;
+  *tmax_out = tmax;
+}
+
 // Interpolated delay of one image-sample split into the read position m0
 // (window column `col`, not clamped), the Farrow segment `seg` of the fraction
 // alpha, its local variable w and the delay tau in samples.

@@ -52,6 +52,7 @@ def _desc(**kw):
     d.tier_rate_hz[:] = rate
     d.tier_upsample[:] = up
     d.upsample_halfwidth = kw.get("upsample_halfwidth", 0)
+    d.delay_model = kw.get("delay_model", 0)
     d.taps = kw.get("taps", 32)
     d.window = kw.get("window", 0)
     d.kaiser_beta = kw.get("kaiser_beta", 8.0)
@@ -74,7 +75,8 @@ def _create(**kw):
     dict(window=1, kaiser_beta=-1.0), dict(window=2, farrow_order=0), dict(window=2, farrow_order=5),
     dict(window=2, passband=0.01), dict(window=2, passband=0.99),
     dict(tiers=[(1, 16000.0), (2**31 - 1, 1000.0, 7)]), dict(tiers=[(2**31 - 1, 25.0, 1280)]),
-    dict(tiers=[(2**31 - 1, 1000.0, -1)]), dict(upsample_halfwidth=9), dict(upsample_halfwidth=-1)])
+    dict(tiers=[(2**31 - 1, 1000.0, -1)]), dict(upsample_halfwidth=9), dict(upsample_halfwidth=-1),
+    dict(delay_model=2), dict(delay_model=-1)])
 def test_create_room_rejects_bad_descriptions(bad):
     st, h = _create(**bad)
     assert st == _lib.ERR_INVALID_ARG
