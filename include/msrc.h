@@ -147,6 +147,24 @@ msrc_status msrc_set_array_trajectory(msrc_room_t room, const msrc_traj_desc* tr
  * positions along the path (e.g. static responses sampled along it). */
 msrc_status msrc_trajectory_positions(msrc_room_t room, const double* times, int64_t n_times, double* out);
 
+/* Knot rates from the motion (Sec. II-C, "Bandwidth Analysis of d_i(t)": the
+ * distance of an image changes as smoothly as the motion allows, and the
+ * farther the image, the more slowly; dense knots for the direct sound and
+ * low orders, sparse knots for high orders). For every tier of the room,
+ * writes to rates_hz[t] (host array of n_tiers doubles) the lowest rate fs / N
+ * (N an integer in [1, max_step]) at which linear interpolation between knots
+ * keeps the delay of every image of the tier within tol_samples of its exact
+ * value over [0, duration]. It uses the chord bound (N / fs)^2 / 8 * max |d''|
+ * * fs / c with |d''| <= (|s'| + |m'|)^2 / d_min + |s''| + |m''|: speeds and
+ * accelerations of the source (and array) from second differences on a 1 ms
+ * grid, d_min the tier's smallest image distance on a 256-point grid, lowered
+ * by the largest motion between grid points, and a safety factor of 1.25. For
+ * a spline path (source or array) N also divides the path's length in samples,
+ * so that its clamped end, where the velocity jumps, is a knot.
+ * tol_samples > 0, max_step >= 1; needs a trajectory (MSRC_ERR_STATE). The
+ * room's own tier rates are not changed: create a room with these rates. */
+msrc_status msrc_suggest_knot_rates(msrc_room_t room, double tol_samples, int32_t max_step, double* rates_hz);
+
 /* Replaces the six wall reflection coefficients of a room (beta: 6 doubles in
  * [0, 1], host memory); the Farrow fit and the trajectory are kept. Used by
  * optimisation loops that update the walls between forward calls. */

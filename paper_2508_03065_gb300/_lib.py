@@ -69,6 +69,7 @@ SIGNATURES = [
     ("msrc_set_array_trajectory", _I32, [_P, ctypes.POINTER(TrajDesc)]),
     ("msrc_trajectory_positions", _I32, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_double)]),
+    ("msrc_suggest_knot_rates", _I32, [_P, ctypes.c_double, _I32, ctypes.POINTER(ctypes.c_double)]),
     ("msrc_set_reflection", _I32, [_P, ctypes.POINTER(ctypes.c_double)]),
     ("msrc_workspace_size", _I32, [ctypes.POINTER(_P), _I32, _I64P, _I64P, _SZP, _SZP]),
     ("msrc_synthesize", _I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P), _I64P, ctypes.POINTER(_P),

@@ -121,6 +121,15 @@ class Room:
                                                  t.size, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
 
+    def suggest_knot_rates(self, tol_samples: float, max_step: int = 4096) -> list:
+        """Per tier, the lowest knot rate (Hz, fs / integer) whose linear
+        interpolation keeps every image delay within tol_samples (see
+        msrc_suggest_knot_rates)."""
+        lib = _lib.load()
+        out = (ctypes.c_double * 4)()
+        _lib.check(lib.msrc_suggest_knot_rates(self._h, float(tol_samples), int(max_step), out))
+        return [float(out[t]) for t in range(self._desc.n_tiers)]
+
     def set_reflection(self, beta) -> None:
         lib = _lib.load()
         b = np.ascontiguousarray(np.asarray(beta, np.float64).reshape(6))

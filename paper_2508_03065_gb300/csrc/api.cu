@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -998,6 +999,113 @@ msrc_status msrc_trajectory_positions(msrc_room_t room, const double* times, int
   if (!room || (n_times > 0 && (!times || !out)) || n_times < 0) return fail(MSRC_ERR_INVALID_ARG, "null argument");
   if (!room->has_traj) return fail(MSRC_ERR_STATE, "room has no trajectory");
   for (int64_t i = 0; i < n_times; ++i) host_source(room->traj, times[i], out + 3 * i);
+  return MSRC_OK;
+}
+
+msrc_status msrc_suggest_knot_rates(msrc_room_t room, double tol_samples, int32_t max_step, double* rates_hz) {
+  if (!room || !rates_hz) return fail(MSRC_ERR_INVALID_ARG, "null argument");
+  if (!(tol_samples > 0.0) || max_step < 1) return fail(MSRC_ERR_INVALID_ARG, "need tol_samples > 0 and max_step >= 1");
+  if (!room->has_traj) return fail(MSRC_ERR_STATE, "room has no trajectory");
+  const msrc_room& R = *room;
+  const double T = R.traj.duration_s, fs = R.d.fs, c = R.d.c;
+  // motion bounds between coarse grid points from second differences on a 1 ms grid
+  constexpr int kGrid = 256;
+  const double hs = 1e-3;
+  const long fine = std::max(2L, long(std::ceil(T / hs)));
+  std::vector<double> vmax(kGrid, 0.0), amax(kGrid, 0.0);
+  auto pos = [&](double t, double out[3]) {
+    host_source(R.traj, t, out);
+    if (R.arr_moving) {
+      double a0[3], at[3];
+      host_source(R.arr, 0.0, a0);
+      host_source(R.arr, t, at);
+      for (int d = 0; d < 3; ++d) out[d + 3] = at[d] - a0[d];
+    } else {
+      out[3] = out[4] = out[5] = 0.0;
+    }
+  };
+  double vall = 0.0;
+  for (long i = 0; i <= fine; ++i) {
+    // interior points only: the clamped spline's end kinks are knots (t = 0) or past the bound
+    const double t = std::min(std::max(i * T / fine, 0.5 * hs), T - 0.5 * hs);
+    const double e = std::min(0.25 * hs, 0.5 * std::min(t, T - t));
+    double p0[6], pm[6], pp[6];
+    pos(t, p0);
+    pos(t - e, pm);
+    pos(t + e, pp);
+    double vs = 0, vm = 0, as = 0, am = 0;
+    for (int d = 0; d < 3; ++d) {
+      vs += std::pow((pp[d] - pm[d]) / (2 * e), 2);
+      vm += std::pow((pp[d + 3] - pm[d + 3]) / (2 * e), 2);
+      as += std::pow((pp[d] - 2 * p0[d] + pm[d]) / (e * e), 2);
+      am += std::pow((pp[d + 3] - 2 * p0[d + 3] + pm[d + 3]) / (e * e), 2);
+    }
+    const double v = std::sqrt(vs) + std::sqrt(vm), a = std::sqrt(as) + std::sqrt(am);
+    const int g = std::min(kGrid - 1, int(double(i) / fine * kGrid));
+    vmax[g] = std::max(vmax[g], v);
+    amax[g] = std::max(amax[g], a);
+    vall = std::max(vall, v);
+  }
+  // smallest image distance of each tier at the coarse grid points
+  std::vector<double> dmin(size_t(R.d.n_tiers) * (kGrid + 1), 1e300);
+  std::vector<double> src(3 * (kGrid + 1)), mic(3 * (kGrid + 1));
+  for (int gi = 0; gi <= kGrid; ++gi) {
+    double q[6];
+    pos(T * gi / kGrid, q);
+    for (int d = 0; d < 3; ++d) src[3 * gi + d] = q[d];
+    for (int d = 0; d < 3; ++d) mic[3 * gi + d] = q[d + 3];
+  }
+  const int K = R.d.max_order;
+  for (int nx = -K; nx <= K; ++nx)
+    for (int ny = -K; ny <= K; ++ny)
+      for (int nz = -K; nz <= K; ++nz) {
+        if (std::abs(nx) + std::abs(ny) + std::abs(nz) > K) continue;
+        const int n[3] = {nx, ny, nz};
+        for (int pb = 0; pb < 8; ++pb) {
+          int rho = 0;
+          double sg[3], off[3];
+          for (int d = 0; d < 3; ++d) {
+            const int p = (pb >> d) & 1;
+            rho += std::abs(2 * n[d] - p);
+            sg[d] = 1.0 - 2.0 * p;
+            off[d] = 2.0 * n[d] * R.d.dims[d];
+          }
+          double* dm = dmin.data() + size_t(tier_of(R.d, rho)) * (kGrid + 1);
+          for (int m = 0; m < R.n_mics; ++m)
+            for (int gi = 0; gi <= kGrid; ++gi) {
+              double acc = 0.0;
+              for (int d = 0; d < 3; ++d) {
+                const double v = sg[d] * src[3 * gi + d] + off[d] - (R.mics[m][d] + mic[3 * gi + d]);
+                acc += v * v;
+              }
+              dm[gi] = std::min(dm[gi], std::sqrt(acc));
+            }
+        }
+      }
+  for (int t = 0; t < R.d.n_tiers; ++t) {
+    const double* dm = dmin.data() + size_t(t) * (kGrid + 1);
+    double D2 = 0.0;
+    for (int g = 0; g < kGrid; ++g) {
+      if (dm[g] > 1e299) continue;  // empty tier
+      const double dlo = std::max(0.05, std::min(dm[g], dm[g + 1]) - 0.5 * vall * T / kGrid);
+      D2 = std::max(D2, vmax[g] * vmax[g] / dlo + amax[g]);
+    }
+    D2 *= 1.25;
+    double Nb = double(max_step);
+    if (D2 > 0.0) Nb = std::min(Nb, std::floor(std::sqrt(8.0 * tol_samples * c * fs / D2)));
+    long N = std::max(1L, long(Nb));
+    // a clamped spline stops at its end: with N dividing the path's length in
+    // samples that end is a knot, so no interval straddles its kink
+    long len = 0;
+    if (R.traj.kind == 2) len = std::llround(T * fs);
+    if (R.arr_moving && R.arr.kind == 2) {
+      const long la = std::llround(R.arr.duration_s * fs);
+      len = len ? std::gcd(len, la) : la;
+    }
+    if (len > 0)
+      while (N > 1 && len % N != 0) --N;
+    rates_hz[t] = fs / double(N);
+  }
   return MSRC_OK;
 }
 
