@@ -392,9 +392,13 @@ def autotune(rooms: Sequence[Room], xs: Sequence[torch.Tensor], n_out: Optional[
     n_in = [int(x.numel()) for x in xs]
     n_out = list(n_in) if n_out is None else [int(v) for v in n_out]
     dev = xs[0].device
+    # the work's shape: images, lengths, taps and the per-tier knot layout and
+    # delay model that decide the record prologue
     key = json.dumps([torch.cuda.get_device_name(dev), len(rooms),
                       sum(r.image_count()[0] for r in rooms), sum(n_out), sum(n_in),
-                      sorted({int(r._desc.taps) for r in rooms})])
+                      sorted({int(r._desc.taps) for r in rooms}),
+                      sorted({(int(r._desc.delay_model), tuple(float(v) for v in r._desc.tier_rate_hz),
+                               tuple(int(v) for v in r._desc.tier_upsample)) for r in rooms})])
     path = cache_path or os.environ.get("MSRC_AUTOTUNE_CACHE") or os.path.expanduser("~/.cache/msrc_autotune.json")
     cache = {}
     if os.path.exists(path):
