@@ -100,3 +100,23 @@ def test_emission_time_refuses_reverse_mode_and_upsampled_tiers():
     ups = replace(spec, tiers=[(1, 16000.0), (W.RHO_INF, 500.0, 8)])
     with pytest.raises(_lib.MsrcError):
         api.synthesize([api.Room.from_spec(ups)], [x])
+
+
+@pytest.mark.parametrize("n_out", [1, 7, 1000, 6000])
+def test_emission_time_output_lengths(n_out):
+    """Outputs shorter and longer than the input, down to one sample."""
+    spec = replace(W.small_scene(seed=62, K=3, traj_kind=W.CIRCLE, seconds=0.25), delay_model=1)
+    y = gpu_run([spec], n_out=[n_out])[0]
+    ref = oracle.synthesize(oracle_scene(spec), spec.x.astype(np.float64), n_out)
+    assert y.shape == (1, n_out)
+    assert rel_l2(y[0], ref) < TOL or np.max(np.abs(y[0] - ref)) < 1e-9
+
+
+def test_emission_time_free_field_receding_source():
+    """Free field (walls absorbing), a source receding from the microphone: the
+    GPU's emission-time output equals the oracle's, whose closed form the pins
+    check."""
+    spec = W.small_scene(seed=63, K=0, traj_kind=W.LINE, seconds=0.5)
+    spec = replace(spec, beta=(0.0,) * 6, delay_model=1)
+    y = gpu_run([spec])[0]
+    assert rel_l2(y[0], oracle_full(spec)) < TOL

@@ -102,3 +102,15 @@ def test_order20_upsampled_full_size_sampled(rate, U):
     idx = np.concatenate([np.arange(0, 192000, 192000 // 24), [191999, 100, 101, 57000, 57001]])
     ref = oracle.y_at(oracle_scene(spec), spec.x.astype(np.float64), idx)
     assert rel_l2(y[idx], ref) < TOL
+
+
+@pytest.mark.parametrize("n_out", [1, 7, 1000, 6000])
+def test_upsampled_output_lengths(n_out):
+    """Outputs shorter and longer than the input (the knot table then reaches
+    past the path's end), down to one sample."""
+    spec = replace(W.small_scene(seed=20, K=2, traj_kind=W.CIRCLE, seconds=0.25,
+                                 tiers=[(0, 16000.0), (W.RHO_INF, 250.0, 16)]), up_halfwidth=3)
+    y = gpu_run([spec], n_out=[n_out])[0]
+    ref = oracle.synthesize(oracle_scene(spec), spec.x.astype(np.float64), n_out)
+    assert y.shape == (1, n_out)
+    assert rel_l2(y[0], ref) < TOL or np.max(np.abs(y[0] - ref)) < 1e-9
