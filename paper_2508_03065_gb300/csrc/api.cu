@@ -440,7 +440,7 @@ struct Plan {
   // reverse mode
   bool backward = false;
   int64_t dxb_floats = 0;
-  size_t off_dxb = 0, off_kslot = 0, off_bpart = 0, off_gk = 0, off_ppart = 0, off_bwt = 0;
+  size_t off_dxb = 0, off_kslot = 0, off_bpart = 0, off_gk = 0, off_ppart = 0, off_bwt = 0, off_trange = 0;
   int kL = 32;
   int taps = 32;
   // band-limited knot upsampling: weight tables (uploaded to off_upw)
@@ -723,6 +723,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     P.off_gk = off; off = align256(off + 24 * size_t(knot_acc));
     P.off_ppart = off; off = align256(off + 8 * size_t(n) * kParamPartialsPerScene);
     P.off_bwt = off; off = align256(off + 32 * I);
+    P.off_trange = off; off = align256(off + 8 * size_t(P.totals[4]));
   }
   P.fwd_bytes = off;
   if (I > (size_t(1) << 31)) return fail(MSRC_ERR_UNSUPPORTED, "more than 2^31 images in one call");
@@ -763,6 +764,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
     a.p.gk = reinterpret_cast<double*>(ws + P.off_gk);
     a.p.ppart = reinterpret_cast<double*>(ws + P.off_ppart);
     a.p.bwt = reinterpret_cast<float4*>(ws + P.off_bwt);
+    a.p.trange = reinterpret_cast<float2*>(ws + P.off_trange);
   }
   // device tables: coefficients of the powers of w = v / 2 (c_q 2^q, exact)
   for (int sg = 0; sg < kFarrowSegs; ++sg)

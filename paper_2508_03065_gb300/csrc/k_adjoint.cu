@@ -27,8 +27,8 @@
 //   atomics are used. Each tile's window is correlated once with the Farrow
 //   coefficients and added, in tile order, to the dx row of the range's parity
 //   (ranges two apart write disjoint columns). The window
-//   is the union of the blocks' delay ranges (a first sweep over the blocks'
-//   records); wide windows run in several column passes.
+//   is the union of the blocks' delay ranges, which the gradient kernel stores
+//   per (mic, block, tile) item; wide windows run in several column passes.
 // k_dx_final / k_knot_final / k_param_partial + k_param_final / k_beta_final:
 // fixed-order sums.
 #include <cstdint>
@@ -121,10 +121,12 @@ __device__ __forceinline__ int next_item(const KernelArgs& a, int* s_item) {
   return *s_item;
 }
 
-// Item delay range -> window [m_lo, m_lo + width).
+// Item delay range -> window [m_lo, m_lo + width); the block-wide range is
+// returned in *tmin_out / *tmax_out when they are not null.
 template <int kThreads>
 __device__ __forceinline__ void window_of(float tmin, float tmax, const ItemGeom& g, float (*s_red)[kThreads / 32],
-                                          int* m_lo, int* width) {
+                                          int* m_lo, int* width, float* tmin_out = nullptr,
+                                          float* tmax_out = nullptr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -141,6 +143,8 @@ __device__ __forceinline__ void window_of(float tmin, float tmax, const ItemGeom
   }
   *m_lo = g.n0 - int(ceilf(tmax)) - 2;
   *width = g.n_end - int(floorf(tmin)) + 2 - *m_lo + 1;
+  if (tmin_out) *tmin_out = tmin;
+  if (tmax_out) *tmax_out = tmax;
 }
 
 // The gradient kernel's image loop for this thread's chunks. Per image-sample:
@@ -273,7 +277,10 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
       for (int i = threadIdx.x; i < 2 * g.cnt; i += kBwThreads) bw_s[i] = bwt[i];
     }
     int m_lo, width;
-    window_of<kBwThreads>(tmin, tmax, g, s_red, &m_lo, &width);
+    float rmin, rmax;
+    window_of<kBwThreads>(tmin, tmax, g, s_red, &m_lo, &width, &rmin, &rmax);
+    // the item's delay range, for the dx kernel's window
+    if (threadIdx.x == 0) a.p.trange[item] = make_float2(rmin, rmax);
 
     int jc[kBwChunks], rr[kBwChunks];
     float rf[kBwChunks], sN[kBwChunks], dyf[kBwChunks];
@@ -479,16 +486,15 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
     float* dxrow = a.p.dxb + S.dxb_base + (mg * S.dx_rows + range % S.dx_rows) * S.n_in;
     const int tile_end = min(S.n_tiles, (range + 1) * S.range_tiles);
 
+    // the gradient kernel stored every (mic, block, tile) item's delay range
+    const float2* trange = a.p.trange + (a.n_scenes > 1 ? a.tab.item_prefix[s] : int64_t(0));
     for (int tile = range * S.range_tiles; tile < tile_end; ++tile) {
-      // the group's delay range over the tile: union of its blocks' records
+      // the group's delay range over the tile: union of its blocks' ranges
       float tmin = 3.0e38f, tmax = -3.0e38f;
       for (int b = b0; b < b1; ++b) {
-        __syncthreads();  // records of the previous block / tile are no longer read
-        const ItemGeom g = item_geometry(S, (item0 + b) * S.n_tiles + tile, kBwTile);
-        float lo, hi;
-        item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &lo, &hi);
-        tmin = fminf(tmin, lo);
-        tmax = fmaxf(tmax, hi);
+        const float2 r = trange[(item0 + b) * S.n_tiles + tile];
+        tmin = fminf(tmin, r.x);
+        tmax = fmaxf(tmax, r.y);
       }
       const ItemGeom g0 = item_geometry(S, (item0 + b0) * S.n_tiles + tile, kBwTile);
       int m_lo, width;
@@ -508,7 +514,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
         rf[c] = float(rr[c]);
         dyv[c] = valid[c] ? __ldg(S.dy + int64_t(mic) * S.n_out + n) : 0.0f;
       }
-      const bool reuse = (b1 - b0 == 1);  // a single block keeps its records
+      const bool single = (b1 - b0 == 1);  // a single block keeps its records over the passes
       for (int p0 = 0; p0 < width; p0 += kDxWcap) {
         const int pass_lo = m_lo + p0;
         const int pw = min(kDxWcap, width - p0);
@@ -522,7 +528,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
         for (int c = 0; c < kBwChunks; ++c) rmj[c] = rr[c] - pass_lo + jc[c] * g0.N;
         for (int b = b0; b < b1; ++b) {
           const ItemGeom g = item_geometry(S, (item0 + b) * S.n_tiles + tile, kBwTile);
-          if (!reuse) {
+          if (!single || p0 == 0) {
             float lo, hi;
             __syncthreads();  // the previous block's records are no longer read
             item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &lo, &hi);

@@ -165,6 +165,7 @@ struct DevicePtrs {
   double* gk;                    // dL/ds(t_j) per tier knot (3 doubles, indexed like knot_pos)
   double* ppart;                 // trajectory-parameter partials (48 doubles per (scene, knot chunk))
   float4* bwt;                   // per image: dbeta_i/dbeta_w / (4 pi) for walls 0..3 | walls 4..5, gain, 0
+  float2* trange;                // reverse mode: delay range (tmin, tmax) of every (mic, block, tile) item
   // band-limited knot upsampling: per (scene, tier) a table of tier_up rows
   // of 2 up_q + 1 floats, row p = the normalised kernel weights of knots
   // j0 - up_q + 1 .. j0 + up_q at the virtual knot p / tier_up past knot j0,
