@@ -117,7 +117,9 @@ __device__ __forceinline__ float image_sample(const float4* zq, const float* zp,
 
 // All images of the block for this thread's kChunks samples; rmj[c] =
 // r - m_lo + jj N_t of chunk c (its interval jj = jc[c]).
-template <int kStride, int kChunks, int kUnroll, bool kChecked>
+// kOne: every chunk of this lane lies in one knot interval (warp-uniform), so
+// one record load per image serves all chunks.
+template <int kStride, int kChunks, int kUnroll, bool kChecked, bool kOne>
 __device__ __forceinline__ void gather_images(const float4* zq, const float* zp, const float2* rec_s,
                                               const int4* img_s, int cnt, const int* jc, const int* rmj,
                                               const float* rf, unsigned wmax, float* acc) {
@@ -133,16 +135,20 @@ __device__ __forceinline__ void gather_images(const float4* zq, const float* zp,
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int4 im = img_s[ib + u];
+      const float2 r0 = row[0][ib + u];
 #pragma unroll
       for (int c = 0; c < kChunks; ++c)
-        acc[c] = image_sample<kStride, kChecked>(zq, zp, row[c][ib + u], im, rmj[c], rmc[c], rf[c], wmax, acc[c]);
+        acc[c] = image_sample<kStride, kChecked>(zq, zp, (kOne || c == 0) ? r0 : row[c][ib + u], im, rmj[c],
+                                                 rmc[c], rf[c], wmax, acc[c]);
     }
   }
   for (; ib < cnt; ++ib) {
     const int4 im = img_s[ib];
+    const float2 r0 = row[0][ib];
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)
-      acc[c] = image_sample<kStride, kChecked>(zq, zp, row[c][ib], im, rmj[c], rmc[c], rf[c], wmax, acc[c]);
+      acc[c] = image_sample<kStride, kChecked>(zq, zp, (kOne || c == 0) ? r0 : row[c][ib], im, rmj[c], rmc[c],
+                                               rf[c], wmax, acc[c]);
   }
 }
 
@@ -232,6 +238,12 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       rf[c] = float(rr[c]);
       acc[c] = 0.0f;
     }
+    // every chunk of every lane in one knot interval (e.g. 96-sample intervals
+    // aligned with this warp's 96 samples): one record load per image
+    bool one = true;
+#pragma unroll
+    for (int c = 1; c < kChunks; ++c) one = one && (jc[c] == jc[0]);
+    one = __all_sync(0xffffffffu, one);
     const float4* zqg = a.p.zq + S.z_base;
     const float* zpg = a.p.zp + S.z_base;
 
@@ -257,10 +269,14 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
 #pragma unroll
       for (int c = 0; c < kChunks; ++c) rmj[c] = rr[c] - pass_lo + jc[c] * g.N;
       const unsigned wmax = unsigned(pw - 1);
-      if (width <= kWcap)
-        gather_images<kWcap, kChunks, kUnroll, false>(zq_s, zp_s, rec_s, img_s, cnt, jc, rmj, rf, wmax, acc);
-      else
-        gather_images<kWcap, kChunks, kUnroll, true>(zq_s, zp_s, rec_s, img_s, cnt, jc, rmj, rf, wmax, acc);
+      if (width <= kWcap) {
+        if (one)
+          gather_images<kWcap, kChunks, kUnroll, false, true>(zq_s, zp_s, rec_s, img_s, cnt, jc, rmj, rf, wmax, acc);
+        else
+          gather_images<kWcap, kChunks, kUnroll, false, false>(zq_s, zp_s, rec_s, img_s, cnt, jc, rmj, rf, wmax, acc);
+      } else {
+        gather_images<kWcap, kChunks, kUnroll, true, false>(zq_s, zp_s, rec_s, img_s, cnt, jc, rmj, rf, wmax, acc);
+      }
     }
     float* out = a.p.part + S.part_base + (int64_t(g.mic) * S.n_blocks + g.blk) * S.n_out;
 #pragma unroll
