@@ -448,7 +448,8 @@ struct Plan {
   std::vector<int> upw_key;       // U * 64 + Q of each table
   std::vector<int> upw_at;        // its first float
   std::vector<double> upw_l1;     // its largest absolute row sum
-  size_t off_upw = 0, off_bl_tau = 0, off_dense64 = 0, off_dense_hi = 0, off_dense_lo = 0;
+  size_t off_upw = 0, off_bl_tau = 0, off_dense64 = 0, off_dense_hi = 0, off_dense_lo = 0, off_knot_hl = 0,
+         off_arr_hl = 0;
 };
 
 // Workspace layout and per-scene descriptors of one call. Forward mode uses
@@ -510,6 +511,15 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     S.c_over_fs = float(R->d.c / R->d.fs);
     S.fs_over_c = R->d.fs / R->d.c;
     S.fsc = float(S.fs_over_c);
+    // double-float pairs v = hi + lo (hi the nearest float, lo the rest)
+    auto split = [](double v, float* hl) {
+      hl[0] = float(v);
+      hl[1] = float(v - double(hl[0]));
+    };
+    for (int d = 0; d < 3; ++d) split(R->d.dims[d], S.dims_hl[d]);
+    for (int m = 0; m < R->n_mics; ++m)
+      for (int d = 0; d < 3; ++d) split(R->mics[m][d], S.mics_hl[m][d]);
+    split(S.fs_over_c, S.fsc_hl);
     int first = 0, blk = 0;
     int64_t kfirst = 0, bl_units = 0;
     // trajectory range the knots reach, and the bound on an interpolated
@@ -704,6 +714,8 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.off_gain = off; off = align256(off + 4 * I);
   P.off_knots = off; off = align256(off + 24 * size_t(knot_acc));
   P.off_arr = off; off = align256(off + (any_moving ? 24 * size_t(knot_acc) : 0));
+  P.off_knot_hl = off; off = align256(off + 32 * size_t(knot_acc));
+  P.off_arr_hl = off; off = align256(off + (any_moving ? 32 * size_t(knot_acc) : 0));
   P.off_upw = off; off = align256(off + 4 * P.upw.size());
   P.off_bl_tau = off; off = align256(off + 8 * size_t(bl_acc));
   P.off_dense64 = off; off = align256(off + 32 * size_t(dense_acc));
@@ -747,6 +759,8 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.img_gain = reinterpret_cast<float*>(ws + P.off_gain);
   a.p.knot_pos = reinterpret_cast<double*>(ws + P.off_knots);
   a.p.arr_pos = reinterpret_cast<double*>(ws + P.off_arr);
+  a.p.knot_hl = reinterpret_cast<float4*>(ws + P.off_knot_hl);
+  a.p.arr_hl = reinterpret_cast<float4*>(ws + P.off_arr_hl);
   a.p.upw = reinterpret_cast<const float*>(ws + P.off_upw);
   a.p.bl_tau = reinterpret_cast<double*>(ws + P.off_bl_tau);
   a.p.dense64 = reinterpret_cast<double*>(ws + P.off_dense64);

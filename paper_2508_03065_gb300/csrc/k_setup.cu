@@ -160,17 +160,26 @@ __global__ void k_traj_knots(const __grid_constant__ KernelArgs a) {
   const double time = double((j - S.knot_shift[t]) * S.tier_coarse[t]) / S.fs;
   double sp[3];
   source_position(S, time, sp);
-  double* out = a.p.knot_pos + 3 * (S.knot_base[t] + j);
+  const int64_t k = S.knot_base[t] + j;
+  double* out = a.p.knot_pos + 3 * k;
   out[0] = sp[0];
   out[1] = sp[1];
   out[2] = sp[2];
+  float4 hi = make_float4(float(sp[0]), float(sp[1]), float(sp[2]), 0.0f);
+  a.p.knot_hl[2 * k] = hi;
+  a.p.knot_hl[2 * k + 1] =
+      make_float4(float(sp[0] - double(hi.x)), float(sp[1] - double(hi.y)), float(sp[2] - double(hi.z)), 0.0f);
   if (S.arr_moving) {
     double ad[3];
     array_displacement(S, time, ad);
-    double* o2 = a.p.arr_pos + 3 * (S.knot_base[t] + j);
+    double* o2 = a.p.arr_pos + 3 * k;
     o2[0] = ad[0];
     o2[1] = ad[1];
     o2[2] = ad[2];
+    hi = make_float4(float(ad[0]), float(ad[1]), float(ad[2]), 0.0f);
+    a.p.arr_hl[2 * k] = hi;
+    a.p.arr_hl[2 * k + 1] =
+        make_float4(float(ad[0] - double(hi.x)), float(ad[1] - double(hi.y)), float(ad[2] - double(hi.z)), 0.0f);
   }
 }
 

@@ -86,6 +86,11 @@ struct SceneDev {
   // entries from dense_base in the dense tables
   int32_t delay_model;
   int64_t dense_base, dense_k0, n_dense;
+  // the anchors' double-float operands: hi + lo of L_d, of every microphone
+  // coordinate and of fs / c
+  float dims_hl[3][2];
+  float mics_hl[MSRC_MAX_MICS][3][2];
+  float fsc_hl[2];
   int64_t img_base;                        // first entry of this scene in the image table
   int64_t knot_base[MSRC_MAX_TIERS];       // first knot position (double3) per tier
   int64_t knot_units_first[MSRC_MAX_TIERS];// prefix over tiers of (J_t + 1)
@@ -153,6 +158,8 @@ struct DevicePtrs {
   float* img_gain;               // beta_i / (4 pi)
   double* knot_pos;              // s(t_j), 3 doubles per knot
   double* arr_pos;               // a(t_j) - a(0), 3 doubles per knot (scenes with a moving array)
+  float4* knot_hl;               // s(t_j) as double-float pairs: hi (x, y, z, 0) then lo, per knot
+  float4* arr_hl;                // a(t_j) - a(0) the same way (moving array)
   float4* zq;                    // prefiltered powers 0..3, [scene rows][segment][column]
   float* zp;                     // prefiltered power 4, same indexing
   float2* zg;                    // reverse mode: powers 4..5 of the degree-5 rows (zq holds 0..3)

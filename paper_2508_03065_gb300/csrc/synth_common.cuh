@@ -91,6 +91,71 @@ __device__ __forceinline__ void knot_increment_moving(const float4 A, const floa
   *d = A.w + dd;
 }
 
+// Double-float arithmetic (a value is hi + lo, |lo| <= ulp(hi) / 2): Knuth's
+// two-sum and the FMA two-product give the rounding error of a float sum or
+// product exactly, so sums and products of pairs keep about 44 bits. The
+// item anchors below use it in place of FP64, which runs at a small fraction
+// of the FP32 rate on this GPU.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  const DF s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  const float e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, fmaf(x.hi, y.hi, -p)));
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ DF df_sqrt(DF x) {  // x > 0
+  const float s = __fsqrt_rn(x.hi);
+  const float p = __fmul_rn(s, s);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), fmaf(s, s, -p)), x.lo);
+  return fast_two_sum(s, __fmul_rn(r, __fdiv_rn(0.5f, s)));
+}
+
+// Anchor of one image at a knot, in double-float: source at s (pairs sH + sL),
+// microphone at m (pairs mH + mL), Delta = sigma o s + 2 n o L - m,
+// d_a = |Delta|, tau = d_a fs / c, D_a = floor(tau):
+// A = {sigma o Delta, d_a}, B = {tau - D_a, D_a}, SG = {sigma, 0} (floats).
+// tau is good to about 1e-12 relative, far below the FP32 record terms.
+__device__ __forceinline__ void anchor_df(const SceneDev& S, uint32_t code, const float4 sH, const float4 sL,
+                                          const DF* m, float4* A, float2* B, float4* SG) {
+  int n[3], p[3];
+  unpack_image(code, n, p);
+  const float sh[3] = {sH.x, sH.y, sH.z}, sl[3] = {sL.x, sL.y, sL.z};
+  DF D[3];
+  DF q = {0.0f, 0.0f};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const DF sd = p[d] ? DF{-sh[d], -sl[d]} : DF{sh[d], sl[d]};
+    const float tn = float(2 * n[d]);  // exact
+    const float pr = __fmul_rn(tn, S.dims_hl[d][0]);
+    const DF off = fast_two_sum(pr, fmaf(tn, S.dims_hl[d][1], fmaf(tn, S.dims_hl[d][0], -pr)));
+    D[d] = df_add(df_add(sd, off), DF{-m[d].hi, -m[d].lo});
+    q = df_add(q, df_mul(D[d], D[d]));
+  }
+  const DF da = df_sqrt(q);
+  const DF tau = df_mul(da, DF{S.fsc_hl[0], S.fsc_hl[1]});
+  float Dfl = floorf(tau.hi);
+  if (tau.hi == Dfl && tau.lo < 0.0f) Dfl -= 1.0f;
+  const float fa = __fadd_rn(__fsub_rn(tau.hi, Dfl), tau.lo);
+  const float s0 = p[0] ? -1.0f : 1.0f, s1 = p[1] ? -1.0f : 1.0f, s2 = p[2] ? -1.0f : 1.0f;
+  *A = make_float4(s0 * D[0].hi, s1 * D[1].hi, s2 * D[2].hi, da.hi);
+  *B = make_float2(fa, Dfl);
+  *SG = make_float4(s0, s1, s2, 0.0f);
+}
+
 // Interval records of an item from the relative delays phi at its knots
 // (phi_s[ib * nk + jj]); see item_records for the record layout.
 template <int kThreads>
@@ -107,7 +172,7 @@ __device__ __forceinline__ void records_from_phi(const ItemGeom& g, const float*
 }
 
 // Records of the item's images over its intervals, in shared memory.
-// With tau = d fs / c, D_a = floor(tau) at the anchor knot jf (FP64) and
+// With tau = d fs / c, D_a = floor(tau) at the anchor knot jf (double-float) and
 // phi_j = tau_j - D_a, the delay between knots j and j + 1 is
 // tau(n) = D_a + phi_j + (phi_{j+1} - phi_j) r / N_t (r = n - n_j). Stored:
 //   rec_s[jj * cnt + ib] = {Psi_j = -S phi_j - 1/2, sigma_j = -S (phi_{j+1} - phi_j) / N_t}
@@ -126,43 +191,49 @@ template <int kThreads>
 __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                              int4* img_s, float4* u_s, float4* um_s, float4* anc_s, float* phi_s,
                              float* tmin_out, float* tmax_out) {
-  const double* kp = a.p.knot_pos + 3 * (S.knot_base[g.t] + g.jf);
-  const double sa0 = kp[0], sa1 = kp[1], sa2 = kp[2];
+  // knot positions and array displacements as double-float pairs; increments
+  // from the anchor knot jf: hi differences of nearby positions are exact
+  const int64_t kj = S.knot_base[g.t] + g.jf;
+  const float4* khl = a.p.knot_hl + 2 * kj;
+  const float4 sH = khl[0], sL = khl[1];
   for (int jj = threadIdx.x; jj < g.nk; jj += kThreads) {
-    const float ux = float(kp[3 * jj] - sa0);
-    const float uy = float(kp[3 * jj + 1] - sa1);
-    const float uz = float(kp[3 * jj + 2] - sa2);
+    const float4 h = khl[2 * jj], l = khl[2 * jj + 1];
+    const float ux = (h.x - sH.x) + (l.x - sL.x);
+    const float uy = (h.y - sH.y) + (l.y - sL.y);
+    const float uz = (h.z - sH.z) + (l.z - sL.z);
     u_s[jj] = make_float4(ux, uy, uz, fmaf(ux, ux, fmaf(uy, uy, uz * uz)));
   }
   const bool moving = S.arr_moving != 0;
-  double ma[3] = {S.mics[g.mic][0], S.mics[g.mic][1], S.mics[g.mic][2]};
+  const float4* ahl = a.p.arr_hl + 2 * kj;
+  const float4 aH = moving ? ahl[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 aL = moving ? ahl[1] : make_float4(0.f, 0.f, 0.f, 0.f);
   if (moving) {
-    const double* ap = a.p.arr_pos + 3 * (S.knot_base[g.t] + g.jf);
-    for (int d = 0; d < 3; ++d) ma[d] += ap[d];
     for (int jj = threadIdx.x; jj < g.nk; jj += kThreads) {
-      const float mx = float(ap[3 * jj] - ap[0]);
-      const float my = float(ap[3 * jj + 1] - ap[1]);
-      const float mz = float(ap[3 * jj + 2] - ap[2]);
+      const float4 h = ahl[2 * jj], l = ahl[2 * jj + 1];
+      const float mx = (h.x - aH.x) + (l.x - aL.x);
+      const float my = (h.y - aH.y) + (l.y - aL.y);
+      const float mz = (h.z - aH.z) + (l.z - aL.z);
       um_s[jj] = make_float4(mx, my, mz, fmaf(mx, mx, fmaf(my, my, mz * mz)));
     }
   }
-  const double fs_c = S.fs_over_c;
   const uint32_t* codes = a.p.img_code + S.img_base + S.tier_first[g.t] + g.img0;
   const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
+  // the microphone at the anchor knot (carried by the array), double-float
+  DF mdf[3];
+  {
+    const float ah[3] = {aH.x, aH.y, aH.z}, al[3] = {aL.x, aL.y, aL.z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      mdf[d] = df_add(DF{S.mics_hl[g.mic][d][0], S.mics_hl[g.mic][d][1]}, DF{ah[d], al[d]});
+  }
   for (int ib = threadIdx.x; ib < g.cnt; ib += kThreads) {
-    int n[3], p[3];
-    unpack_image(codes[ib], n, p);
-    const double s0 = 1.0 - 2.0 * p[0], s1 = 1.0 - 2.0 * p[1], s2 = 1.0 - 2.0 * p[2];
-    const double D0 = s0 * sa0 + 2.0 * n[0] * S.dims[0] - ma[0];
-    const double D1 = s1 * sa1 + 2.0 * n[1] * S.dims[1] - ma[1];
-    const double D2 = s2 * sa2 + 2.0 * n[2] * S.dims[2] - ma[2];
-    const double da = fast_sqrt(fma(D0, D0, fma(D1, D1, D2 * D2)));
-    const double tau = da * fs_c;
-    const double Dfl = floor(tau);
-    anc_s[2 * ib] = make_float4(float(s0 * D0), float(s1 * D1), float(s2 * D2), float(da));
-    anc_s[2 * ib + 1] = make_float4(float(tau - Dfl), float(Dfl), 0.0f, 0.0f);
-    anc_s[2 * g.cnt + ib] = make_float4(float(s0), float(s1), float(s2), 0.0f);
-    img_s[ib] = make_int4(g.jf * g.N - int(Dfl), __float_as_int(float(Dfl) - 0.5f / kFarrowSegs),
+    float4 A, SG;
+    float2 B;
+    anchor_df(S, codes[ib], sH, sL, mdf, &A, &B, &SG);
+    anc_s[2 * ib] = A;
+    anc_s[2 * ib + 1] = make_float4(B.x, B.y, 0.0f, 0.0f);
+    anc_s[2 * g.cnt + ib] = SG;
+    img_s[ib] = make_int4(g.jf * g.N - int(B.y), __float_as_int(B.y - 0.5f / kFarrowSegs),
                           __float_as_int(__ldg(gain + ib)), 0);
   }
   __syncthreads();
@@ -433,32 +504,35 @@ __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const I
   const float fsc = S.fsc;
   float tmin = 3.0e38f, tmax = -3.0e38f;
   const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  // two (image, knot) units per pass: their table reads overlap
+  // (image, knot) units knot-major, so that a warp's lanes take neighbouring
+  // images (nearby emission points, shared cache lines) at one knot; four
+  // units per pass so that their table reads are in flight together
+  constexpr int kRetUnits = 4;
   const int units = g.cnt * nk;
-  for (int p0 = threadIdx.x; p0 < units; p0 += 2 * kThreads) {
-    const int p1 = p0 + kThreads;
-    const int q1 = p1 < units ? p1 : p0;
-    const int ib0 = p0 / nk, jj0 = p0 - ib0 * nk;
-    const int ib1 = q1 / nk, jj1 = q1 - ib1 * nk;
-    const RetAnchor r0{an6[6 * ib0], an6[6 * ib0 + 1], an6[6 * ib0 + 2], an6[6 * ib0 + 3], an6[6 * ib0 + 4],
-                       an6[6 * ib0 + 5]};
-    const RetAnchor r1{an6[6 * ib1], an6[6 * ib1 + 1], an6[6 * ib1 + 2], an6[6 * ib1 + 3], an6[6 * ib1 + 4],
-                       an6[6 * ib1 + 5]};
-    const float4 um0 = moving ? um_s[jj0] : zero4;
-    const float4 um1 = moving ? um_s[jj1] : zero4;
-    const float de0 = ret_increment(r0, um0, HI, LO, int64_t(kDenseOver) * jj0 * g.N, kmax, fsc, c4,
-                                    fmaf(r0.dA.w, float(jj0 * g.N), r0.E.x));
-    const float de1 = ret_increment(r1, um1, HI, LO, int64_t(kDenseOver) * jj1 * g.N, kmax, fsc, c4,
-                                    fmaf(r1.dA.w, float(jj1 * g.N), r1.E.x));
-    const float phi0 = r0.Lw.w + de0;
-    phi_s[p0] = phi0;
-    tmin = fminf(tmin, r0.E.y + phi0);
-    tmax = fmaxf(tmax, r0.E.y + phi0);
-    if (p1 < units) {
-      const float phi1 = r1.Lw.w + de1;
-      phi_s[p1] = phi1;
-      tmin = fminf(tmin, r1.E.y + phi1);
-      tmax = fmaxf(tmax, r1.E.y + phi1);
+  for (int p0 = threadIdx.x; p0 < units; p0 += kRetUnits * kThreads) {
+    float de[kRetUnits], Eo[kRetUnits], Lo[kRetUnits];
+    int ib[kRetUnits], jj[kRetUnits];
+#pragma unroll
+    for (int k = 0; k < kRetUnits; ++k) {
+      const int u = min(p0 + k * kThreads, units - 1);
+      jj[k] = u / g.cnt;
+      ib[k] = u - jj[k] * g.cnt;
+      const RetAnchor r{an6[6 * ib[k]], an6[6 * ib[k] + 1], an6[6 * ib[k] + 2], an6[6 * ib[k] + 3],
+                        an6[6 * ib[k] + 4], an6[6 * ib[k] + 5]};
+      const float4 um = moving ? um_s[jj[k]] : zero4;
+      de[k] = ret_increment(r, um, HI, LO, int64_t(kDenseOver) * jj[k] * g.N, kmax, fsc, c4,
+                            fmaf(r.dA.w, float(jj[k] * g.N), r.E.x));
+      Eo[k] = r.E.y;
+      Lo[k] = r.Lw.w;
+    }
+#pragma unroll
+    for (int k = 0; k < kRetUnits; ++k) {
+      if (p0 + k * kThreads < units) {
+        const float phi = Lo[k] + de[k];
+        phi_s[ib[k] * nk + jj[k]] = phi;
+        tmin = fminf(tmin, Eo[k] + phi);
+        tmax = fmaxf(tmax, Eo[k] + phi);
+      }
     }
   }
   __syncthreads();
