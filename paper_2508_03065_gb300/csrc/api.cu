@@ -448,7 +448,7 @@ struct Plan {
   std::vector<int> upw_key;       // U * 64 + Q of each table
   std::vector<int> upw_at;        // its first float
   std::vector<double> upw_l1;     // its largest absolute row sum
-  size_t off_upw = 0, off_bl_tau = 0, off_dense64 = 0, off_dense_hi = 0, off_dense_lo = 0, off_knot_hl = 0,
+  size_t off_upw = 0, off_bl_tau = 0, off_dense_hi = 0, off_dense_lo = 0, off_knot_hl = 0,
          off_arr_hl = 0;
 };
 
@@ -718,7 +718,6 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.off_arr_hl = off; off = align256(off + (any_moving ? 32 * size_t(knot_acc) : 0));
   P.off_upw = off; off = align256(off + 4 * P.upw.size());
   P.off_bl_tau = off; off = align256(off + 8 * size_t(bl_acc));
-  P.off_dense64 = off; off = align256(off + 32 * size_t(dense_acc));
   P.off_dense_hi = off; off = align256(off + 16 * size_t(dense_acc));
   P.off_dense_lo = off; off = align256(off + 16 * size_t(dense_acc));
   P.off_z = off; off = align256(off + 16 * size_t(z_acc));
@@ -762,8 +761,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.knot_hl = reinterpret_cast<float4*>(ws + P.off_knot_hl);
   a.p.arr_hl = reinterpret_cast<float4*>(ws + P.off_arr_hl);
   a.p.upw = reinterpret_cast<const float*>(ws + P.off_upw);
-  a.p.bl_tau = reinterpret_cast<double*>(ws + P.off_bl_tau);
-  a.p.dense64 = reinterpret_cast<double*>(ws + P.off_dense64);
+  a.p.bl_tau = reinterpret_cast<float2*>(ws + P.off_bl_tau);
   a.p.dense_hi = reinterpret_cast<float4*>(ws + P.off_dense_hi);
   a.p.dense_lo = reinterpret_cast<float4*>(ws + P.off_dense_lo);
   a.p.zq = reinterpret_cast<float4*>(ws + P.off_z);

@@ -183,11 +183,11 @@ __global__ void k_traj_knots(const __grid_constant__ KernelArgs a) {
   }
 }
 
-// FP64 delay tau = d fs / c of every (microphone, image, knot) of a tier with
-// band-limited knot upsampling (the upsampler's input, Sec. II-C), once per
-// knot: every synthesis item whose virtual knots reach a knot reads it. One
-// warp per (microphone, image) row, lanes over its knots (coalesced stores);
-// the image's constant part 2 n L - m is formed once per lane.
+// Delay tau = d fs / c (double-float) of every (microphone, image, knot) of a
+// tier with band-limited knot upsampling (the upsampler's input, Sec. II-C),
+// once per knot: every synthesis item whose virtual knots reach a knot reads
+// it. One warp per (microphone, image) row, lanes over its knots (coalesced
+// stores); the image's constant part 2 n L - m is formed once per lane.
 constexpr int kBlTauThreads = 256;
 __global__ void k_bl_tau(const __grid_constant__ KernelArgs a) {
   const int64_t wid = (int64_t(blockIdx.x) * kBlTauThreads + threadIdx.x) >> 5;
@@ -206,26 +206,40 @@ __global__ void k_bl_tau(const __grid_constant__ KernelArgs a) {
   const int img = int(row - int64_t(mic) * S.tier_count[t]);
   int n[3], p[3];
   unpack_image(a.p.img_code[S.img_base + S.tier_first[t] + img], n, p);
-  double o[3];
-  for (int d = 0; d < 3; ++d) o[d] = fma(2.0 * n[d], S.dims[d], -S.mics[mic][d]);
+  DF o[3];  // 2 n L - m, double-float
+  for (int d = 0; d < 3; ++d) {
+    const float tn = float(2 * n[d]);  // exact
+    const float pr = __fmul_rn(tn, S.dims_hl[d][0]);
+    const DF off = fast_two_sum(pr, fmaf(tn, S.dims_hl[d][1], fmaf(tn, S.dims_hl[d][0], -pr)));
+    o[d] = df_add(off, DF{-S.mics_hl[mic][d][0], -S.mics_hl[mic][d][1]});
+  }
   const bool moving = S.arr_moving != 0;
-  double* out = a.p.bl_tau + S.bl_tau_base[t] + row * nkt;
+  const DF fscd{S.fsc_hl[0], S.fsc_hl[1]};
+  float2* out = a.p.bl_tau + S.bl_tau_base[t] + row * nkt;
   for (int j = lane; j < nkt; j += 32) {
-    const double* kp = a.p.knot_pos + 3 * (S.knot_base[t] + j);
-    const double* ap = a.p.arr_pos + 3 * (S.knot_base[t] + j);
-    double acc = 0.0;
+    const int64_t k = S.knot_base[t] + j;
+    const float4 h = a.p.knot_hl[2 * k], l = a.p.knot_hl[2 * k + 1];
+    const float sh[3] = {h.x, h.y, h.z}, sl[3] = {l.x, l.y, l.z};
+    float ah[3] = {0.f, 0.f, 0.f}, al[3] = {0.f, 0.f, 0.f};
+    if (moving) {
+      const float4 ha = a.p.arr_hl[2 * k], la = a.p.arr_hl[2 * k + 1];
+      ah[0] = ha.x; ah[1] = ha.y; ah[2] = ha.z;
+      al[0] = la.x; al[1] = la.y; al[2] = la.z;
+    }
+    DF q = {0.0f, 0.0f};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      double v = (p[d] ? o[d] - kp[d] : o[d] + kp[d]);
-      if (moving) v -= ap[d];
-      acc = fma(v, v, acc);
+      const DF sd = p[d] ? DF{-sh[d], -sl[d]} : DF{sh[d], sl[d]};
+      const DF v = df_add(df_add(sd, o[d]), DF{-ah[d], -al[d]});
+      q = df_add(q, df_mul(v, v));
     }
-    out[j] = fast_sqrt(acc) * S.fs_over_c;
+    const DF tau = df_mul(df_sqrt(q), fscd);
+    out[j] = make_float2(tau.hi, tau.lo);
   }
 }
 
 // Source path table of a scene with emission-time delays: s(t) at
-// t = (dense_k0 + k) / (kDenseOver fs), FP64 and as FP32 pairs hi + lo.
+// t = (dense_k0 + k) / (kDenseOver fs) as FP32 pairs hi + lo.
 __global__ void k_dense_traj(const __grid_constant__ KernelArgs a) {
   const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (gid >= a.totals[7]) return;
@@ -236,11 +250,6 @@ __global__ void k_dense_traj(const __grid_constant__ KernelArgs a) {
   double sp[3];
   source_position(S, t, sp);
   const int64_t e = S.dense_base + local;
-  double* o = a.p.dense64 + 4 * e;
-  o[0] = sp[0];
-  o[1] = sp[1];
-  o[2] = sp[2];
-  o[3] = 0.0;
   const float hx = float(sp[0]), hy = float(sp[1]), hz = float(sp[2]);
   a.p.dense_hi[e] = make_float4(hx, hy, hz, 0.0f);
   a.p.dense_lo[e] = make_float4(float(sp[0] - hx), float(sp[1] - hy), float(sp[2] - hz), 0.0f);

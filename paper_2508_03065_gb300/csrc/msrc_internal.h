@@ -178,12 +178,11 @@ struct DevicePtrs {
   // j0 - up_q + 1 .. j0 + up_q at the virtual knot p / tier_up past knot j0,
   // then their first moment sum_i w_i (i - up_q + 1)
   const float* upw;
-  // and the FP64 delay tau = d fs / c of every (microphone, image, knot) of an
-  // upsampled tier, [mic][image][knot] from bl_tau_base[t]
-  double* bl_tau;
-  // emission-time delays: the source path every 1 / (kDenseOver fs) s as FP64
-  // (x, y, z, 0) and as the FP32 pair hi + lo of each coordinate
-  double* dense64;
+  // and the delay tau = d fs / c of every (microphone, image, knot) of an
+  // upsampled tier as a double-float pair, [mic][image][knot] from bl_tau_base[t]
+  float2* bl_tau;
+  // emission-time delays: the source path every 1 / (kDenseOver fs) s as the
+  // FP32 pair hi + lo of each coordinate
   float4* dense_hi;
   float4* dense_lo;
 };

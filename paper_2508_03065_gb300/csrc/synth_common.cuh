@@ -53,15 +53,7 @@ __device__ __forceinline__ ItemGeom item_geometry(const SceneDev& S, int64_t li,
   return g;
 }
 
-// sqrt(q) for q > 0 in FP64 from an FP32 reciprocal-square-root seed and one
-// Newton step: the seed has relative error ~1e-7, the step squares it (~1e-14).
-__device__ __forceinline__ double fast_sqrt(double q) {
-  const float r = rsqrtf(float(q));
-  const double d0 = double(float(q) * r);
-  return fma(fma(-d0, d0, q), 0.5 * double(r), d0);
-}
-
-// Knot j of an image relative to its anchor knot a: with Delta the FP64
+// Knot j of an image relative to its anchor knot a: with Delta the
 // image-to-microphone vector at the anchor, w = sigma o Delta_a (FP32),
 // u = s(t_j) - s(t_a) and q = |Delta_j|^2 - |Delta_a|^2 = 2 w.u + |u|^2 exactly,
 // the distance increment is d_j - d_a = q / (d_a + sqrt(d_a^2 + q)); every
@@ -122,6 +114,12 @@ __device__ __forceinline__ DF df_sqrt(DF x) {  // x > 0
   const float p = __fmul_rn(s, s);
   const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p), fmaf(s, s, -p)), x.lo);
   return fast_two_sum(s, __fmul_rn(r, __fdiv_rn(0.5f, s)));
+}
+
+__device__ __forceinline__ float df_floor(DF x) {  // floor of hi + lo (|hi| < 2^24)
+  float f = floorf(x.hi);
+  if (x.hi == f && x.lo < 0.0f) f -= 1.0f;
+  return f;
 }
 
 // Anchor of one image at a knot, in double-float: source at s (pairs sH + sL),
@@ -266,13 +264,13 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
 // (every N = N_c / U samples, N_c the knot spacing); the distance there is
 // sum_i w_p[i] d(j0 - Q + 1 + i) with j0 = floor(k / U), p = k - j0 U and the
 // normalised weights w_p of the windowed-sinc kernel. With tau_j = d_j fs / c
-// at the knots (FP64, computed once per knot by k_bl_tau), Delta =
+// at the knots (double-float, computed once per knot by k_bl_tau), Delta =
 // tau_{j0+1} - tau_j0 and the deviations from the chord
 // e_i = tau_{j0-Q+1+i} - tau_j0 - (i - Q + 1) Delta, and since the weights sum
 // to one,
 //   tau(k) = tau_j0 + Delta M_p + sum_i w_p[i] e_i,   M_p = sum_i w_p[i] (i - Q + 1),
 // so that the FP32 sum only carries the small chord deviations; tau_j0 - D
-// and Delta are formed in FP64 and rounded once. D = floor(tau) at knot
+// and Delta are formed in double-float and rounded once. D = floor(tau) at knot
 // floor(jf / U) is the image's anchor. Scratch `scr` (`cap` floats): D (cnt),
 // chord rows (cnt x nj x (2Q + 2)), phi (cnt x nk). If the item does not fit,
 // the error word gets kErrUpsampleScratch, no record is written and the result
@@ -298,31 +296,41 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
   float* phi_s = e_s + g.cnt * nj * er;
   const int nkt = S.bl_knots[g.t];
   // delays of image ib: rows[ib * nkt + j + Q] is knot j (the table starts at knot -Q)
-  const double* rows = a.p.bl_tau + S.bl_tau_base[g.t] +
+  const float2* rows = a.p.bl_tau + S.bl_tau_base[g.t] +
                        (int64_t(g.mic) * S.tier_count[g.t] + g.img0) * nkt + Q;
   const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
   for (int pidx = threadIdx.x; pidx < g.cnt * nj; pidx += kThreads) {
     const int ib = pidx / nj;
     const int jr = pidx - ib * nj;
-    const double* row = rows + int64_t(ib) * nkt;
-    const double Dfl = floor(row[j0_first]);  // the anchor, knot floor(jf / U)
+    const float2* row = rows + int64_t(ib) * nkt;
+    const float2 an = row[j0_first];
+    const float Dfl = df_floor(DF{an.x, an.y});  // the anchor, knot floor(jf / U)
     if (jr == 0) {
-      dfl_s[ib] = float(Dfl);
-      img_s[ib] = make_int4(g.jf * g.N - int(Dfl), __float_as_int(float(Dfl) - 0.5f / kFarrowSegs),
+      dfl_s[ib] = Dfl;
+      img_s[ib] = make_int4(g.jf * g.N - int(Dfl), __float_as_int(Dfl - 0.5f / kFarrowSegs),
                             __float_as_int(__ldg(gain + ib)), 0);
     }
-    const double* tv = row + (j0_first + jr - Q + 1);  // knots j0 - Q + 1 .. j0 + Q
-    const double t0 = tv[Q - 1];
-    const double dl = tv[Q] - t0;
-    // chord value at knot i: t0 + (i - Q + 1) dl = base + i dl (i a constant
-    // after unrolling); knots j0 and j0 + 1 lie on the chord (e = 0)
-    const double base = fma(-double(Q - 1), dl, t0);
+    const float2* tv = row + (j0_first + jr - Q + 1);  // knots j0 - Q + 1 .. j0 + Q
+    const DF t0{tv[Q - 1].x, tv[Q - 1].y};
+    const DF dl = df_add(DF{tv[Q].x, tv[Q].y}, DF{-t0.hi, -t0.lo});
+    // chord value at knot i: t0 + (i - Q + 1) dl; knots j0 and j0 + 1 lie on
+    // the chord (e = 0)
     float* E = e_s + pidx * er;
 #pragma unroll
-    for (int i = 0; i < 2 * kMaxUpHalfwidth; ++i)
-      if (i < 2 * Q) E[i] = (i == Q - 1 || i == Q) ? 0.0f : float(tv[i] - fma(double(i), dl, base));
-    E[2 * Q] = float(t0 - Dfl);
-    E[2 * Q + 1] = float(dl);
+    for (int i = 0; i < 2 * kMaxUpHalfwidth; ++i) {
+      if (i < 2 * Q) {
+        if (i == Q - 1 || i == Q) {
+          E[i] = 0.0f;
+        } else {
+          const DF ch = df_add(t0, df_mul(dl, DF{float(i - Q + 1), 0.0f}));
+          const DF e = df_add(DF{tv[i].x, tv[i].y}, DF{-ch.hi, -ch.lo});
+          E[i] = e.hi + e.lo;
+        }
+      }
+    }
+    const DF r0 = df_add(t0, DF{-Dfl, 0.0f});
+    E[2 * Q] = r0.hi + r0.lo;
+    E[2 * Q + 1] = dl.hi + dl.lo;
   }
   __syncthreads();
   const float* W0 = a.p.upw + S.upw_base[g.t];
@@ -352,12 +360,12 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
 // distance at reception knot j is the path length d_j = c tau_j with
 // c tau_j = |r_i(t_j - tau_j) - m(t_j)|; records, delay and gain follow from
 // d_j exactly as for reception-time distances.
-//   Anchor (knot jf, FP64, per image): the first-order guess
+//   Anchor (knot jf, double-float, per image): the first-order guess
 //   tau_0 = d(t) / (c + u . sigma o s'(t)) (reception-time distance, unit
 //   vector and source velocity), one Newton step on F(tau) = tau - |Delta(tau)| fs / c
-//   (source at the emission time read from the path table, linear between its
-//   points, kDenseOver per sample; slope in FP32) to tau_a, and the residual
-//   eps = |Delta(tau_a)| fs / c - tau_a, which the FP32 stage absorbs.
+//   (source at the emission time read from the path table's pairs, linear
+//   between its points, kDenseOver per sample; slope in FP32) to tau_a, and the
+//   residual eps = |Delta(tau_a)| fs / c - tau_a, which the FP32 stage absorbs.
 //   Other knots (FP32, per image and knot): delta_j = tau_j - tau_a solves
 //   delta = (d_j - d_a) fs / c + eps, d_a = |Delta(tau_a)|; two Newton steps
 //   from delta = eps + r jj N (r the anchor's rate of change of the delay).
@@ -412,91 +420,124 @@ __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const I
                                  int4* img_s, float4* um_s, float4* an6, float* phi_s, float* tmin_out,
                                  float* tmax_out) {
   const bool moving = S.arr_moving != 0;
-  const double* ap = a.p.arr_pos + 3 * (S.knot_base[g.t] + g.jf);
+  const int64_t kj = S.knot_base[g.t] + g.jf;
+  const float4* ahl = a.p.arr_hl + 2 * kj;
+  const float4 aH = moving ? ahl[0] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 aL = moving ? ahl[1] : make_float4(0.f, 0.f, 0.f, 0.f);
   if (moving) {
     for (int jj = threadIdx.x; jj < g.nk; jj += kThreads) {
-      const float mx = float(ap[3 * jj] - ap[0]);
-      const float my = float(ap[3 * jj + 1] - ap[1]);
-      const float mz = float(ap[3 * jj + 2] - ap[2]);
-      um_s[jj] = make_float4(mx, my, mz, 0.0f);
+      const float4 h = ahl[2 * jj], l = ahl[2 * jj + 1];
+      um_s[jj] = make_float4((h.x - aH.x) + (l.x - aL.x), (h.y - aH.y) + (l.y - aL.y), (h.z - aH.z) + (l.z - aL.z),
+                             0.0f);
     }
   }
-  const double fs_c = S.fs_over_c;
-  const double* kp = a.p.knot_pos + 3 * (S.knot_base[g.t] + g.jf);
-  double ma[3] = {S.mics[g.mic][0], S.mics[g.mic][1], S.mics[g.mic][2]};
-  if (moving)
-    for (int d = 0; d < 3; ++d) ma[d] += ap[d];
+  // double-float operands: the source at the anchor's reception time and the
+  // microphone there (carried by the array)
+  const float4 sH = a.p.knot_hl[2 * kj], sL = a.p.knot_hl[2 * kj + 1];
+  DF mdf[3];
+  {
+    const float ah[3] = {aH.x, aH.y, aH.z}, al[3] = {aL.x, aL.y, aL.z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      mdf[d] = df_add(DF{S.mics_hl[g.mic][d][0], S.mics_hl[g.mic][d][1]}, DF{ah[d], al[d]});
+  }
+  const DF fscd{S.fsc_hl[0], S.fsc_hl[1]};
   const uint32_t* codes = a.p.img_code + S.img_base + S.tier_first[g.t] + g.img0;
   const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
-  const double* P64 = a.p.dense64 + 4 * S.dense_base;
   const float4* HI = a.p.dense_hi + S.dense_base;
   const float4* LO = a.p.dense_lo + S.dense_base;
   const int64_t kmax = S.n_dense - 2;  // last table index whose successor exists
-  const double n_a = double(g.jf) * g.N;
+  // table coordinate of emission sample n_a - tau is x0 - kDenseOver tau
+  const int64_t x0 = int64_t(kDenseOver) * (int64_t(g.jf) * g.N) - S.dense_k0;
   const float c4 = float(kDenseOver) * S.fsc;  // delay change (samples) per metre and table step
   // table index of the reception time itself (the velocity there seeds the anchor)
-  const int64_t k_rec = min(max(int64_t(kDenseOver) * (int64_t(g.jf) * g.N) - S.dense_k0, int64_t(0)), kmax);
+  const int64_t k_rec = min(max(x0, int64_t(0)), kmax);
   const float4 vr0 = HI[k_rec], vr1 = HI[k_rec + 1];
   for (int ib = threadIdx.x; ib < g.cnt; ib += kThreads) {
     int n[3], p[3];
     unpack_image(codes[ib], n, p);
-    double o[3], sg[3];
+    float sg[3];
+    DF o[3];
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
-      sg[d] = 1.0 - 2.0 * p[d];
-      o[d] = fma(2.0 * n[d], S.dims[d], -ma[d]);
+      sg[d] = p[d] ? -1.0f : 1.0f;
+      const float tn = float(2 * n[d]);  // exact
+      const float pr = __fmul_rn(tn, S.dims_hl[d][0]);
+      const DF off = fast_two_sum(pr, fmaf(tn, S.dims_hl[d][1], fmaf(tn, S.dims_hl[d][0], -pr)));
+      o[d] = df_add(off, DF{-mdf[d].hi, -mdf[d].lo});  // 2 n L - m
     }
-    double tau;
+    // first-order guess from the reception-time distance and the source velocity
+    DF tau;
     {
-      const double D0 = fma(sg[0], kp[0], o[0]), D1 = fma(sg[1], kp[1], o[1]), D2 = fma(sg[2], kp[2], o[2]);
-      const double d0 = fast_sqrt(fma(D0, D0, fma(D1, D1, D2 * D2)));
-      const float gsl = (float(D0) * float(sg[0]) * (vr1.x - vr0.x) + float(D1) * float(sg[1]) * (vr1.y - vr0.y) +
-                         float(D2) * float(sg[2]) * (vr1.z - vr0.z)) / float(d0) * c4;
-      tau = d0 * fs_c * double(1.0f / (1.0f + gsl));
+      const float shh[3] = {sH.x, sH.y, sH.z}, sll[3] = {sL.x, sL.y, sL.z};
+      DF q = {0.0f, 0.0f};
+      float dot = 0.0f;
+      const float vd[3] = {vr1.x - vr0.x, vr1.y - vr0.y, vr1.z - vr0.z};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const DF D = df_add(DF{sg[d] * shh[d], sg[d] * sll[d]}, o[d]);
+        q = df_add(q, df_mul(D, D));
+        dot = fmaf(D.hi * sg[d], vd[d], dot);
+      }
+      const DF d0 = df_sqrt(q);
+      const float gsl = dot / d0.hi * c4;
+      tau = df_mul(df_mul(d0, fscd), DF{1.0f / (1.0f + gsl), 0.0f});
     }
-    double Dv[3];
-    double dist = 0.0;
+    // source at the emission time n_a - tau from the path table (linear between
+    // its points), and the image-to-microphone vector and distance there
+    DF Dv[3], dist;
     int64_t k = 0;
-    double f = 0.0;
-    float4 h0, h1;
-    auto eval = [&](double tv) {
-      const double x = double(kDenseOver) * (n_a - tv) - double(S.dense_k0);
-      k = min(max(int64_t(floor(x)), int64_t(0)), kmax);
-      f = x - double(k);
-      const double* q0 = P64 + 4 * k;
+    float f = 0.0f;
+    float4 h0, h1, l0, l1;
+    auto eval = [&](DF tv) {
+      const float ti = df_floor(tv);
+      const float tr = __fadd_rn(__fsub_rn(tv.hi, ti), tv.lo);  // tau - ti, in [0, 1) up to rounding
+      const float xr = -float(kDenseOver) * tr;
+      const float xi = floorf(xr);
+      const int64_t kk = x0 - int64_t(kDenseOver) * int64_t(ti) + int64_t(xi);
+      k = min(max(kk, int64_t(0)), kmax);
+      f = (xr - xi) + float(kk - k);  // the fraction (extrapolated when clamped)
       h0 = HI[k];
       h1 = HI[k + 1];
-      double acc = 0.0;
+      l0 = LO[k];
+      l1 = LO[k + 1];
+      const float h0v[3] = {h0.x, h0.y, h0.z}, l0v[3] = {l0.x, l0.y, l0.z};
+      const float dsv[3] = {(h1.x - h0.x) + (l1.x - l0.x), (h1.y - h0.y) + (l1.y - l0.y),
+                            (h1.z - h0.z) + (l1.z - l0.z)};
+      DF q = {0.0f, 0.0f};
+#pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const double sd = fma(f, q0[4 + d] - q0[d], q0[d]);
-        Dv[d] = fma(sg[d], sd, o[d]);
-        acc = fma(Dv[d], Dv[d], acc);
+        const DF sd = df_add(DF{h0v[d], l0v[d]}, DF{__fmul_rn(f, dsv[d]), 0.0f});
+        Dv[d] = df_add(DF{sg[d] * sd.hi, sg[d] * sd.lo}, o[d]);
+        q = df_add(q, df_mul(Dv[d], Dv[d]));
       }
-      dist = fast_sqrt(acc);
+      dist = df_sqrt(q);
     };
     eval(tau);
     {
-      const float gsl = (float(Dv[0]) * float(sg[0]) * (h1.x - h0.x) + float(Dv[1]) * float(sg[1]) * (h1.y - h0.y) +
-                         float(Dv[2]) * float(sg[2]) * (h1.z - h0.z)) / float(dist) * c4;
-      tau -= (tau - dist * fs_c) * double(1.0f / (1.0f + gsl));
+      const float gsl = ((Dv[0].hi * sg[0]) * (h1.x - h0.x) + (Dv[1].hi * sg[1]) * (h1.y - h0.y) +
+                         (Dv[2].hi * sg[2]) * (h1.z - h0.z)) / dist.hi * c4;
+      const DF res = df_add(tau, df_mul(dist, DF{-fscd.hi, -fscd.lo}));  // tau - d fs / c
+      tau = df_add(tau, DF{-res.hi / (1.0f + gsl), 0.0f});
     }
     eval(tau);
-    const float eps = float(fma(dist, fs_c, -tau));
-    const double Dfl = floor(tau);
-    // the anchor's emission point: table index k, fraction f, its FP32 pair
-    const float4 l0 = LO[k], l1 = LO[k + 1];
+    const DF resid = df_add(df_mul(dist, fscd), DF{-tau.hi, -tau.lo});
+    const float eps = resid.hi + resid.lo;
+    const float Dfl = df_floor(tau);
+    const float fa = __fadd_rn(__fsub_rn(tau.hi, Dfl), tau.lo);
     const float dsx = (h1.x - h0.x) + (l1.x - l0.x);
     const float dsy = (h1.y - h0.y) + (l1.y - l0.y);
     const float dsz = (h1.z - h0.z) + (l1.z - l0.z);
-    const float Ax = float(Dv[0]), Ay = float(Dv[1]), Az = float(Dv[2]), da = float(dist);
-    const float gsl = (Ax * float(sg[0]) * dsx + Ay * float(sg[1]) * dsy + Az * float(sg[2]) * dsz) / da * c4;
+    const float Ax = Dv[0].hi, Ay = Dv[1].hi, Az = Dv[2].hi, da = dist.hi;
+    const float gsl = (Ax * sg[0] * dsx + Ay * sg[1] * dsy + Az * sg[2] * dsz) / da * c4;
     an6[6 * ib + 0] = make_float4(Ax, Ay, Az, da);
-    an6[6 * ib + 1] = make_float4(h0.x, h0.y, h0.z, float(f));
-    an6[6 * ib + 2] = make_float4(l0.x, l0.y, l0.z, float(tau - Dfl));
+    an6[6 * ib + 1] = make_float4(h0.x, h0.y, h0.z, f);
+    an6[6 * ib + 2] = make_float4(l0.x, l0.y, l0.z, fa);
     // table step of the path there; rate of change of the delay per output sample (still microphone)
     an6[6 * ib + 3] = make_float4(dsx, dsy, dsz, gsl / (1.0f + gsl));
-    an6[6 * ib + 4] = make_float4(float(sg[0]), float(sg[1]), float(sg[2]), __int_as_float(int(k)));
-    an6[6 * ib + 5] = make_float4(eps, float(Dfl), 0.0f, 0.0f);
-    img_s[ib] = make_int4(g.jf * g.N - int(Dfl), __float_as_int(float(Dfl) - 0.5f / kFarrowSegs),
+    an6[6 * ib + 4] = make_float4(sg[0], sg[1], sg[2], __int_as_float(int(k)));
+    an6[6 * ib + 5] = make_float4(eps, Dfl, 0.0f, 0.0f);
+    img_s[ib] = make_int4(g.jf * g.N - int(Dfl), __float_as_int(Dfl - 0.5f / kFarrowSegs),
                           __float_as_int(__ldg(gain + ib)), 0);
   }
   __syncthreads();
