@@ -641,7 +641,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     const int64_t zlo = -tau_bound - 16;
     const int64_t zhi = std::max(n_out[s], n_in[s] + R->d.taps) + 16;
     S.z_m0 = zlo;
-    S.z_len = zhi - zlo;
+    S.z_len = (zhi - zlo + 3) & ~int64_t(3);  // rows start on 16-byte boundaries (bulk copies)
     S.z_base = z_acc;
     S.part_base = part_acc;
     // emission-time delays: the source path table spans the emission times of
@@ -723,7 +723,8 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.off_z = off; off = align256(off + 16 * size_t(z_acc));
   // forward: power 4 of the degree-4 rows; reverse mode: powers 4..5 of the
   // degree-5 rows the gradient kernel reads (zq holds powers 0..3 either way)
-  P.off_zp = off; off = align256(off + (backward ? 8 : 4) * size_t(z_acc));
+  // (+64 B: a bulk copy of a row's last columns may read up to 12 B past it)
+  P.off_zp = off; off = align256(off + (backward ? 8 : 4) * size_t(z_acc) + 64);
   if (!backward) {
     P.off_part = off; off = align256(off + 4 * size_t(part_acc));
   } else {

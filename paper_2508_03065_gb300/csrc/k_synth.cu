@@ -78,16 +78,41 @@ __global__ void __launch_bounds__(kPreThreads) k_prefilter(const __grid_constant
 }
 
 // ------------------------------------------------------------------ synthesis
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+// Bulk copies through the tensor memory accelerator (cp.async.bulk, untiled):
+// one thread issues a whole z row segment into shared memory and the copies
+// complete on an mbarrier that every thread then waits on (a bounded wait).
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+__device__ __forceinline__ void mbar_init(uint64_t* mb, unsigned count) {
+  asm volatile("mbarrier.init.shared.b64 [%0], %1;\n" ::"r"(smem_u32(mb)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mb, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;\n" ::"r"(smem_u32(mb)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* mb) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mb))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mb, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(mb)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// Waits for the phase `parity` of the mbarrier, giving up after kSpinLimit
+// polls (each poll may suspend the thread for a while); true on completion.
+constexpr int kSpinLimit = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(uint64_t* mb, unsigned parity) {
+  for (int it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(mb, parity)) return true;
+  return false;
 }
 
 // acc + (beta_i / (4 pi d_i(n))) e_i(n) for one image-sample read from the
@@ -171,6 +196,8 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
   float* phi_r = reinterpret_cast<float*>(an6_s + 6 * kBlock);
   __shared__ int s_item;
   __shared__ float s_red[2][kThreads / 32];
+  __shared__ __align__(8) uint64_t s_mbar;  // completion of the window's bulk copies
+  static_assert(kWcap % 4 == 0, "16-byte aligned power-4 row segments");
   constexpr int kTile = kThreads * kChunks;
   static_assert(4 * (2 * (kTile + 4) + 3 * kBlock) + kRecCap + kBlock <= 4 * kFarrowSegs * kWcap,
                 "prologue scratch");
@@ -178,6 +205,8 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
                 "prologue scratch (emission-time delays)");
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) mbar_init(&s_mbar, 1);
+  unsigned phase = 0;  // of s_mbar, the same in every thread
 
   for (;;) {
     if (threadIdx.x == 0) s_item = int(atomicAdd(a.p.counter, 1u));
@@ -220,7 +249,10 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       tmin = fminf(tmin, s_red[0][w]);
       tmax = fmaxf(tmax, s_red[1][w]);
     }
-    const int m_lo = g.n0 - int(ceilf(tmax)) - 2;
+    // window start congruent to the z rows' origin mod 4: power-4 row segments
+    // then start on 16-byte boundaries on both sides of the bulk copy
+    int m_lo = g.n0 - int(ceilf(tmax)) - 2;
+    m_lo -= int(((int64_t(m_lo) - S.z_m0) % 4 + 4) % 4);
     const int width = g.n_end - int(floorf(tmin)) + 2 - m_lo + 1;
 
     // this thread's samples: warp w owns n0 + 32 (w kChunks + c) + lane
@@ -251,21 +283,37 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
     for (int p0 = 0; p0 < width; p0 += kWcap) {
       const int pass_lo = m_lo + p0;
       const int pw = min(kWcap, width - p0);
-      if (p0 > 0) __syncthreads();  // the previous pass is done with the window
+      // generic-proxy reads and writes of this shared memory (the prologue
+      // scratch, or the previous pass) are done before the async copies land
+      fence_proxy_async();
+      __syncthreads();
       const int64_t lo_c = max(int64_t(pass_lo), S.z_m0);
       const int64_t hi_c = min(int64_t(pass_lo) + pw, S.z_m0 + S.z_len);
       if ((lo_c != pass_lo || hi_c != int64_t(pass_lo) + pw) && threadIdx.x == 0)
         atomicOr(a.p.err, kErrWindowClamp);
       const int cnt_c = int(hi_c > lo_c ? hi_c - lo_c : int64_t(0));
-      const int dst0 = int(lo_c - pass_lo);
-      const int64_t src0 = lo_c - S.z_m0;
-      for (int i = threadIdx.x; i < kFarrowSegs * cnt_c; i += kThreads) {
-        const int sg = i / cnt_c, c = i - sg * cnt_c;
-        cp_async16(zq_s + sg * kWcap + dst0 + c, zqg + int64_t(sg) * S.z_len + src0 + c);
-        cp_async4(zp_s + sg * kWcap + dst0 + c, zpg + int64_t(sg) * S.z_len + src0 + c);
+      const int dst0 = int(lo_c - pass_lo);    // a multiple of 4 (see m_lo)
+      const int64_t src0 = lo_c - S.z_m0;      // a multiple of 4
+      if (cnt_c > 0) {
+        if (threadIdx.x == 0) {
+          const unsigned bq = unsigned(cnt_c) * 16u;
+          const unsigned bp = unsigned((cnt_c + 3) & ~3) * 4u;  // within the padded rows
+          mbar_expect_tx(&s_mbar, unsigned(kFarrowSegs) * (bq + bp));
+          for (int sg = 0; sg < kFarrowSegs; ++sg) {
+            bulk_g2s(zq_s + sg * kWcap + dst0, zqg + int64_t(sg) * S.z_len + src0, bq, &s_mbar);
+            bulk_g2s(zp_s + sg * kWcap + dst0, zpg + int64_t(sg) * S.z_len + src0, bp, &s_mbar);
+          }
+        }
+        const bool ok = mbar_wait(&s_mbar, phase);
+        if (__syncthreads_or(!ok)) {
+          // the copies did not complete in time: flag it, give them one more
+          // bounded wait, and stop this CTA
+          if (threadIdx.x == 0) atomicOr(a.p.err, kErrTimeout);
+          mbar_wait(&s_mbar, phase);
+          return;
+        }
+        phase ^= 1u;
       }
-      cp_async_wait_all();
-      __syncthreads();
 #pragma unroll
       for (int c = 0; c < kChunks; ++c) rmj[c] = rr[c] - pass_lo + jc[c] * g.N;
       const unsigned wmax = unsigned(pw - 1);
