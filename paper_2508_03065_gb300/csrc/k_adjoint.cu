@@ -64,18 +64,6 @@ constexpr size_t kDxSmem = size_t(kDxSlots) * (sizeof(float4) + sizeof(float)) +
 static_assert(kBwRecCap % 2 == 0, "16-byte alignment of the image records");
 static_assert(kGradSmem <= 232448 && kDxSmem <= 232448, "shared memory per CTA");
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-}
-
 // dbeta_i / dbeta_w of beta_i = prod_w beta_w^{e_w} (FP64; handles beta_w = 0).
 __device__ void beta_weights(const SceneDev& S, uint32_t code, double out[6]) {
   int n[3], p[3];
@@ -231,6 +219,10 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
   static_assert(4 * (2 * (kBwTile + 4) + 3 * kBwBlock) + kBwRecCap + kBwBlock <= 4 * kFarrowSegs * kGradWcap,
                 "prologue scratch");
   static_assert(6 * kSegCap * (kBwTile / 32) <= 4 * kFarrowSegs * kGradWcap, "scan scratch");
+  static_assert(kGradWcap % 4 == 0, "16-byte aligned row segments");
+  __shared__ __align__(8) uint64_t s_mbar;  // completion of the window's bulk copies
+  if (threadIdx.x == 0) mbar_init(&s_mbar, 1);
+  unsigned phase = 0;
   __shared__ int s_item;
   __shared__ float s_red[2][kBwThreads / 32];
   __shared__ float s_beta[kBwThreads / 32][6];
@@ -279,6 +271,11 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     int m_lo, width;
     float rmin, rmax;
     window_of<kBwThreads>(tmin, tmax, g, s_red, &m_lo, &width, &rmin, &rmax);
+    {  // window start congruent to the z rows' origin mod 4 (16-byte row segments)
+      const int sh = int(((int64_t(m_lo) - S.z_m0) % 4 + 4) % 4);
+      m_lo -= sh;
+      width += sh;
+    }
     // the item's delay range, for the dx kernel's window
     if (threadIdx.x == 0) a.p.trange[item] = make_float2(rmin, rmax);
 
@@ -306,19 +303,33 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     for (int p0 = 0; p0 < width; p0 += kGradWcap) {
       const int pass_lo = m_lo + p0;
       const int pw = min(kGradWcap, width - p0);
-      __syncthreads();  // prologue scratch / previous pass done
+      // prologue scratch / previous pass done (generic proxy) before the async copies
+      fence_proxy_async();
+      __syncthreads();
       const int64_t lo_c = max(int64_t(pass_lo), S.z_m0);
       const int64_t hi_c = min(int64_t(pass_lo) + pw, S.z_m0 + S.z_len);
       const int cnt_c = int(hi_c > lo_c ? hi_c - lo_c : int64_t(0));
       if (cnt_c != pw && threadIdx.x == 0) atomicOr(a.p.err, kErrWindowClamp);
-      const int dst0 = int(lo_c - pass_lo);
-      for (int i = threadIdx.x; i < kFarrowSegs * cnt_c; i += kBwThreads) {
-        const int sg = i / cnt_c, c = i - sg * cnt_c;
-        cp_async16(zq_s + sg * kGradWcap + dst0 + c, zqg + int64_t(sg) * S.z_len + (lo_c - S.z_m0) + c);
-        cp_async8(zp_s + sg * kGradWcap + dst0 + c, zpg + int64_t(sg) * S.z_len + (lo_c - S.z_m0) + c);
+      const int dst0 = int(lo_c - pass_lo);  // multiples of 4 (see m_lo)
+      const int64_t src0 = lo_c - S.z_m0;
+      if (cnt_c > 0) {
+        if (threadIdx.x == 0) {
+          const unsigned bq = unsigned(cnt_c) * 16u;
+          const unsigned bp = unsigned((cnt_c + 3) & ~3) * 8u;  // within the padded rows
+          mbar_expect_tx(&s_mbar, unsigned(kFarrowSegs) * (bq + bp));
+          for (int sg = 0; sg < kFarrowSegs; ++sg) {
+            bulk_g2s(zq_s + sg * kGradWcap + dst0, zqg + int64_t(sg) * S.z_len + src0, bq, &s_mbar);
+            bulk_g2s(zp_s + sg * kGradWcap + dst0, zpg + int64_t(sg) * S.z_len + src0, bp, &s_mbar);
+          }
+        }
+        const bool ok = mbar_wait(&s_mbar, phase);
+        if (__syncthreads_or(!ok)) {
+          if (threadIdx.x == 0) atomicOr(a.p.err, kErrTimeout);
+          mbar_wait(&s_mbar, phase);
+          return;
+        }
+        phase ^= 1u;
       }
-      cp_async_wait_all();
-      __syncthreads();
       int rmj[kBwChunks];
 #pragma unroll
       for (int c = 0; c < kBwChunks; ++c) rmj[c] = rr[c] - pass_lo + jc[c] * g.N;

@@ -83,6 +83,43 @@ __device__ __forceinline__ void knot_increment_moving(const float4 A, const floa
   *d = A.w + dd;
 }
 
+// Bulk copies through the tensor memory accelerator (cp.async.bulk, untiled):
+// one thread issues a whole z row segment into shared memory and the copies
+// complete on an mbarrier that every thread then waits on (a bounded wait).
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* mb, unsigned count) {
+  asm volatile("mbarrier.init.shared.b64 [%0], %1;\n" ::"r"(smem_u32(mb)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mb, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;\n" ::"r"(smem_u32(mb)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* mb) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mb))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mb, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(mb)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// Waits for the phase `parity` of the mbarrier, giving up after kSpinLimit
+// polls (each poll may suspend the thread for a while); true on completion.
+constexpr int kSpinLimit = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(uint64_t* mb, unsigned parity) {
+  for (int it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(mb, parity)) return true;
+  return false;
+}
+
 // Double-float arithmetic (a value is hi + lo, |lo| <= ulp(hi) / 2): Knuth's
 // two-sum and the FMA two-product give the rounding error of a float sum or
 // product exactly, so sums and products of pairs keep about 44 bits. The
