@@ -62,6 +62,7 @@ constexpr size_t kDxSmem = size_t(kDxSlots) * (sizeof(float4) + sizeof(float)) +
                            size_t(2 * (kBwTile + 4) + 3 * kBwBlock) * sizeof(float4) +
                            size_t(kBwRecCap + kBwBlock) * sizeof(float);
 static_assert(kBwRecCap % 2 == 0, "16-byte alignment of the image records");
+static_assert(kBwBlock <= kBwThreads, "the record builders give every image at least one thread");
 static_assert(kGradSmem <= 232448 && kDxSmem <= 232448, "shared memory per CTA");
 
 // dbeta_i / dbeta_w of beta_i = prod_w beta_w^{e_w} (FP64; handles beta_w = 0).

@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
   __shared__ float s_red[2][kThreads / 32];
   __shared__ __align__(8) uint64_t s_mbar;  // completion of the window's bulk copies
   static_assert(kWcap % 4 == 0, "16-byte aligned power-4 row segments");
+  static_assert(kBlock <= kThreads, "the record builders give every image at least one thread");
   constexpr int kTile = kThreads * kChunks;
   static_assert(4 * (2 * (kTile + 4) + 3 * kBlock) + kRecCap + kBlock <= 4 * kFarrowSegs * kWcap,
                 "prologue scratch");

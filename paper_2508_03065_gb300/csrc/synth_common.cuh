@@ -198,11 +198,15 @@ __device__ __forceinline__ void records_from_phi(const ItemGeom& g, const float*
   const float sN = float(kFarrowSegs) / float(g.N);
   const int nk = g.nk;
   const int nrec = nk - 1;
-  for (int pidx = threadIdx.x; pidx < g.cnt * nrec; pidx += kThreads) {
-    const int ib = pidx / nrec;
-    const int jj = pidx - ib * nrec;
-    const float phi0 = phi_s[ib * nk + jj], phi1 = phi_s[ib * nk + jj + 1];
-    rec_s[jj * g.cnt + ib] = make_float2(fmaf(-float(kFarrowSegs), phi0, -0.5f), (phi0 - phi1) * sN);
+  // image-fastest as in item_records: consecutive threads, consecutive records
+  const int tpi = kThreads / g.cnt;
+  if (threadIdx.x < tpi * g.cnt) {
+    const int j0 = threadIdx.x / g.cnt;
+    const int ib = threadIdx.x - j0 * g.cnt;
+    for (int jj = j0; jj < nrec; jj += tpi) {
+      const float phi0 = phi_s[ib * nk + jj], phi1 = phi_s[ib * nk + jj + 1];
+      rec_s[jj * g.cnt + ib] = make_float2(fmaf(-float(kFarrowSegs), phi0, -0.5f), (phi0 - phi1) * sN);
+    }
   }
 }
 
@@ -277,17 +281,23 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
   const float fsc = S.fsc;
   const int nk = g.nk;
   float tmin = 3.0e38f, tmax = -3.0e38f;
-  for (int pidx = threadIdx.x; pidx < g.cnt * nk; pidx += kThreads) {
-    const int ib = pidx / nk;
-    const int jj = pidx - ib * nk;
+  // thread t takes image t mod cnt and every (kThreads / cnt)-th knot from
+  // t / cnt: no division per unit, one anchor load per thread
+  const int tpi = kThreads / g.cnt;  // >= 1: a block holds at most kThreads images
+  if (threadIdx.x < tpi * g.cnt) {
+    const int j0 = threadIdx.x / g.cnt;
+    const int ib = threadIdx.x - j0 * g.cnt;
     const float4 A = anc_s[2 * ib];
     const float4 A2 = anc_s[2 * ib + 1];
-    float phi, d;
-    if (moving) knot_increment_moving(A, anc_s[2 * g.cnt + ib], u_s[jj], um_s[jj], fsc, A2.x, &phi, &d);
-    else knot_increment(A, u_s[jj], fsc, A2.x, &phi, &d);
-    phi_s[pidx] = phi;
-    tmin = fminf(tmin, A2.y + phi);
-    tmax = fmaxf(tmax, A2.y + phi);
+    const float4 SG = anc_s[2 * g.cnt + ib];
+    for (int jj = j0; jj < nk; jj += tpi) {
+      float phi, d;
+      if (moving) knot_increment_moving(A, SG, u_s[jj], um_s[jj], fsc, A2.x, &phi, &d);
+      else knot_increment(A, u_s[jj], fsc, A2.x, &phi, &d);
+      phi_s[ib * nk + jj] = phi;
+      tmin = fminf(tmin, A2.y + phi);
+      tmax = fmaxf(tmax, A2.y + phi);
+    }
   }
   __syncthreads();
   records_from_phi<kThreads>(g, phi_s, rec_s);
