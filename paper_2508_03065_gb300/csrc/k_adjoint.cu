@@ -246,23 +246,28 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax);
     // unit vectors (sigma o Delta) / d of every image at every knot of the tile
     // (sigma o Delta_j = w + u - sigma o u_m with a moving array)
-    for (int pidx = threadIdx.x; pidx < g.cnt * g.nk; pidx += kBwThreads) {
-      const int ib = pidx / g.nk, jj = pidx - ib * g.nk;
+    // (image-fastest thread mapping: one division per thread)
+    if (const int tpi = kBwThreads / g.cnt; threadIdx.x < tpi * g.cnt) {
+      const int j0 = threadIdx.x / g.cnt;
+      const int ib = threadIdx.x - j0 * g.cnt;
       const float4 A = anc_s[2 * ib];
-      const float4 U = u_s[jj];
-      float phi, d, ex = 0.f, ey = 0.f, ez = 0.f;
-      if (S.arr_moving) {
-        const float4 sg = anc_s[2 * g.cnt + ib];
-        const float4 Um = um_s[jj];
-        knot_increment_moving(A, sg, U, Um, fsc, 0.0f, &phi, &d);
-        ex = sg.x * Um.x;
-        ey = sg.y * Um.y;
-        ez = sg.z * Um.z;
-      } else {
-        knot_increment(A, U, fsc, 0.0f, &phi, &d);
+      const float4 sg = anc_s[2 * g.cnt + ib];
+      for (int jj = j0; jj < g.nk; jj += tpi) {
+        const float4 U = u_s[jj];
+        float phi, d, ex = 0.f, ey = 0.f, ez = 0.f;
+        if (S.arr_moving) {
+          const float4 Um = um_s[jj];
+          knot_increment_moving(A, sg, U, Um, fsc, 0.0f, &phi, &d);
+          ex = sg.x * Um.x;
+          ey = sg.y * Um.y;
+          ez = sg.z * Um.z;
+        } else {
+          knot_increment(A, U, fsc, 0.0f, &phi, &d);
+        }
+        const float inv = __fdividef(1.0f, d);
+        unit_s[ib * g.nk + jj] =
+            make_float4((A.x + U.x - ex) * inv, (A.y + U.y - ey) * inv, (A.z + U.z - ez) * inv, 0.0f);
       }
-      const float inv = __fdividef(1.0f, d);
-      unit_s[pidx] = make_float4((A.x + U.x - ex) * inv, (A.y + U.y - ey) * inv, (A.z + U.z - ez) * inv, 0.0f);
     }
     // gains and dbeta_i/dbeta_w / (4 pi) of the block's images
     {

@@ -346,9 +346,15 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
   const float2* rows = a.p.bl_tau + S.bl_tau_base[g.t] +
                        (int64_t(g.mic) * S.tier_count[g.t] + g.img0) * nkt + Q;
   const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
-  for (int pidx = threadIdx.x; pidx < g.cnt * nj; pidx += kThreads) {
-    const int ib = pidx / nj;
-    const int jr = pidx - ib * nj;
+  // image-fastest thread mapping (one division per thread): image t mod cnt,
+  // intervals / knots from t / cnt in steps of kThreads / cnt
+  const int tpi = kThreads / g.cnt;
+  const bool act = threadIdx.x < tpi * g.cnt;
+  const int t0i = threadIdx.x / g.cnt;
+  const int tib = threadIdx.x - t0i * g.cnt;
+  for (int jr = act ? t0i : nj; jr < nj; jr += tpi) {
+    const int ib = tib;
+    const int pidx = ib * nj + jr;
     const float2* row = rows + int64_t(ib) * nkt;
     const float2 an = row[j0_first];
     const float Dfl = df_floor(DF{an.x, an.y});  // the anchor, knot floor(jf / U)
@@ -381,20 +387,26 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
   }
   __syncthreads();
   const float* W0 = a.p.upw + S.upw_base[g.t];
-  for (int pidx = threadIdx.x; pidx < g.cnt * nk; pidx += kThreads) {
-    const int ib = pidx / nk;
-    const int jj = pidx - ib * nk;
-    const int k = g.jf + jj;
-    const int j0 = k / U;
-    const int pp = k - j0 * U;
-    const float* E = e_s + (ib * nj + (j0 - j0_first)) * er;
-    const float* W = W0 + pp * (2 * Q + 1);
-    float phi = fmaf(E[2 * Q + 1], __ldg(W + 2 * Q), E[2 * Q]);
-    for (int i = 0; i < 2 * Q; ++i) phi = fmaf(__ldg(W + i), E[i], phi);
-    phi_s[pidx] = phi;
+  if (act) {
+    const int ib = tib;
     const float D = dfl_s[ib];
-    tmin = fminf(tmin, D + phi);
-    tmax = fmaxf(tmax, D + phi);
+    // virtual knot k = jf + jj = j0 U + pp, advanced by tpi without dividing
+    int j0 = (g.jf + t0i) / U;
+    int pp = g.jf + t0i - j0 * U;
+    for (int jj = t0i; jj < nk; jj += tpi) {
+      const float* E = e_s + (ib * nj + (j0 - j0_first)) * er;
+      const float* W = W0 + pp * (2 * Q + 1);
+      float phi = fmaf(E[2 * Q + 1], __ldg(W + 2 * Q), E[2 * Q]);
+      for (int i = 0; i < 2 * Q; ++i) phi = fmaf(__ldg(W + i), E[i], phi);
+      phi_s[ib * nk + jj] = phi;
+      tmin = fminf(tmin, D + phi);
+      tmax = fmaxf(tmax, D + phi);
+      pp += tpi;
+      while (pp >= U) {
+        pp -= U;
+        ++j0;
+      }
+    }
   }
   __syncthreads();
   records_from_phi<kThreads>(g, phi_s, rec_s);
@@ -592,34 +604,34 @@ __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const I
   const float fsc = S.fsc;
   float tmin = 3.0e38f, tmax = -3.0e38f;
   const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  // (image, knot) units knot-major, so that a warp's lanes take neighbouring
+  // (image, knot) units image-fastest, so that a warp's lanes take neighbouring
   // images (nearby emission points, shared cache lines) at one knot; four
-  // units per pass so that their table reads are in flight together
+  // knots per pass so that their table reads are in flight together
   constexpr int kRetUnits = 4;
-  const int units = g.cnt * nk;
-  for (int p0 = threadIdx.x; p0 < units; p0 += kRetUnits * kThreads) {
-    float de[kRetUnits], Eo[kRetUnits], Lo[kRetUnits];
-    int ib[kRetUnits], jj[kRetUnits];
+  const int tpi = kThreads / g.cnt;  // image-fastest mapping: one division per thread
+  if (threadIdx.x < tpi * g.cnt) {
+    const int j0 = threadIdx.x / g.cnt;
+    const int ib = threadIdx.x - j0 * g.cnt;
+    const RetAnchor r{an6[6 * ib], an6[6 * ib + 1], an6[6 * ib + 2], an6[6 * ib + 3], an6[6 * ib + 4],
+                      an6[6 * ib + 5]};
+    for (int jb = j0; jb < nk; jb += kRetUnits * tpi) {
+      float de[kRetUnits];
 #pragma unroll
-    for (int k = 0; k < kRetUnits; ++k) {
-      const int u = min(p0 + k * kThreads, units - 1);
-      jj[k] = u / g.cnt;
-      ib[k] = u - jj[k] * g.cnt;
-      const RetAnchor r{an6[6 * ib[k]], an6[6 * ib[k] + 1], an6[6 * ib[k] + 2], an6[6 * ib[k] + 3],
-                        an6[6 * ib[k] + 4], an6[6 * ib[k] + 5]};
-      const float4 um = moving ? um_s[jj[k]] : zero4;
-      de[k] = ret_increment(r, um, HI, LO, int64_t(kDenseOver) * jj[k] * g.N, kmax, fsc, c4,
-                            fmaf(r.dA.w, float(jj[k] * g.N), r.E.x));
-      Eo[k] = r.E.y;
-      Lo[k] = r.Lw.w;
-    }
+      for (int k = 0; k < kRetUnits; ++k) {
+        const int jj = min(jb + k * tpi, nk - 1);
+        const float4 um = moving ? um_s[jj] : zero4;
+        de[k] = ret_increment(r, um, HI, LO, int64_t(kDenseOver) * jj * g.N, kmax, fsc, c4,
+                              fmaf(r.dA.w, float(jj * g.N), r.E.x));
+      }
 #pragma unroll
-    for (int k = 0; k < kRetUnits; ++k) {
-      if (p0 + k * kThreads < units) {
-        const float phi = Lo[k] + de[k];
-        phi_s[ib[k] * nk + jj[k]] = phi;
-        tmin = fminf(tmin, Eo[k] + phi);
-        tmax = fmaxf(tmax, Eo[k] + phi);
+      for (int k = 0; k < kRetUnits; ++k) {
+        const int jj = jb + k * tpi;
+        if (jj < nk) {
+          const float phi = r.Lw.w + de[k];
+          phi_s[ib * nk + jj] = phi;
+          tmin = fminf(tmin, r.E.y + phi);
+          tmax = fmaxf(tmax, r.E.y + phi);
+        }
       }
     }
   }
