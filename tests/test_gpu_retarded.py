@@ -120,3 +120,16 @@ def test_emission_time_free_field_receding_source():
     spec = replace(spec, beta=(0.0,) * 6, delay_model=1)
     y = gpu_run([spec])[0]
     assert rel_l2(y[0], oracle_full(spec)) < TOL
+
+
+def test_emission_time_every_tile_config():
+    """Every synthesis tile configuration gives the same emission-time result."""
+    spec = replace(W.small_scene(seed=64, K=3, traj_kind=W.SPLINE, seconds=0.3), delay_model=1)
+    ref = oracle_full(spec)
+    try:
+        for cfg in range(api.tile_configs()):
+            api.set_tile_config(cfg)
+            y = gpu_run([spec])[0]
+            assert rel_l2(y[0], ref) < TOL, cfg
+    finally:
+        api.set_tile_config(0)

@@ -114,3 +114,18 @@ def test_upsampled_output_lengths(n_out):
     ref = oracle.synthesize(oracle_scene(spec), spec.x.astype(np.float64), n_out)
     assert y.shape == (1, n_out)
     assert rel_l2(y[0], ref) < TOL or np.max(np.abs(y[0] - ref)) < 1e-9
+
+
+def test_upsampled_every_tile_config():
+    """Every synthesis tile configuration gives the same band-limited result
+    (the record scratch and block sizes depend on the configuration)."""
+    spec = W.small_scene(seed=21, K=3, traj_kind=W.CIRCLE, seconds=0.3,
+                         tiers=[(1, 16000.0), (W.RHO_INF, 200.0, 10)])
+    ref = oracle_full(spec)
+    try:
+        for cfg in range(api.tile_configs()):
+            api.set_tile_config(cfg)
+            y = gpu_run([spec])[0]
+            assert rel_l2(y[0], ref) < TOL, cfg
+    finally:
+        api.set_tile_config(0)
