@@ -164,6 +164,7 @@ __device__ __forceinline__ void grad_images(const float4* zq_s, const float2* zp
     const int4 im = img_s[ib];
     const float Dp = __int_as_float(im.y);
     const int ub = ib * nk;
+    float hsum = 0.0f;  // this thread's dy e (fs/c) / tau of the image, over its chunks
 #pragma unroll
     for (int c = 0; c < kBwChunks; ++c) {
       float w, tau, dy = dyf[c];
@@ -190,16 +191,17 @@ __device__ __forceinline__ void grad_images(const float4* zq_s, const float2* zp
       const float rt = __fdividef(1.0f, tau);
       const float et = pe * rt;                                          // e / tau
       const float ad = -(dy * B1.z * rt) * fmaf(float(kFarrowSegs), pd, et);  // dL/dd_i(n)
-      const float hbv = dy * et;                                         // dy e (fs/c) / tau
+      hsum = fmaf(dy, et, hsum);                                         // dy e (fs/c) / tau
       const float4 U0 = urow[c][ub];
       const float4 U1 = urow[c][ub + 1];
       const float w1 = ad * sN[c], w0 = ad - w1;
       V[c][0] = fmaf(w0, U0.x, V[c][0]); V[c][1] = fmaf(w0, U0.y, V[c][1]); V[c][2] = fmaf(w0, U0.z, V[c][2]);
       V[c][3] = fmaf(w1, U1.x, V[c][3]); V[c][4] = fmaf(w1, U1.y, V[c][4]); V[c][5] = fmaf(w1, U1.z, V[c][5]);
-      bacc[0] = fmaf(hbv, B0.x, bacc[0]); bacc[1] = fmaf(hbv, B0.y, bacc[1]);
-      bacc[2] = fmaf(hbv, B0.z, bacc[2]); bacc[3] = fmaf(hbv, B0.w, bacc[3]);
-      bacc[4] = fmaf(hbv, B1.x, bacc[4]); bacc[5] = fmaf(hbv, B1.y, bacc[5]);
     }
+    // the wall weights depend on the image only: once per image
+    bacc[0] = fmaf(hsum, B0.x, bacc[0]); bacc[1] = fmaf(hsum, B0.y, bacc[1]);
+    bacc[2] = fmaf(hsum, B0.z, bacc[2]); bacc[3] = fmaf(hsum, B0.w, bacc[3]);
+    bacc[4] = fmaf(hsum, B1.x, bacc[4]); bacc[5] = fmaf(hsum, B1.y, bacc[5]);
   }
 }
 
