@@ -9,10 +9,17 @@
  *     the gain A_i = beta_i / (4 pi d_i) (Sec. II-A, text after Eq. 2).
  *   - d_i is evaluated exactly at knots whose spacing depends on the image's
  *     reflection count (dense for low orders, sparse for high orders) and is
- *     linearly interpolated to audio rate (Sec. II-C, "Fast Architecture").
+ *     linearly interpolated to audio rate (Sec. II-C, "Fast Architecture"),
+ *     or first upsampled band-limited (tier_upsample).
  *   - Each image is a discrete time-varying fractional delay realised with a
  *     Farrow structure (Sec. II-B, Eq. 3-5) approximating an L-tap windowed
- *     sinc (Hann or Kaiser); the outputs of all images are summed (Eq. 8).
+ *     sinc (Hann or Kaiser) or following a least-squares design; the outputs
+ *     of all images are summed (Eq. 8).
+ *   - Options: microphones on a moving array (msrc_set_array_trajectory),
+ *     emission-time (retarded) distances (delay_model), knot rates chosen
+ *     from the motion (msrc_suggest_knot_rates). Reverse mode
+ *     (msrc_synthesize_backward) gives gradients for the signal, trajectory
+ *     parameters and wall coefficients.
  *
  * Conventions for every entry point:
  *   - Every call returns an msrc_status; nothing aborts and no C++ exception
@@ -20,8 +27,8 @@
  *     describing the last failure of the calling thread.
  *   - Device work is asynchronous on the given stream (a cudaStream_t passed
  *     as void*, NULL = legacy default stream). Device-side errors (a bounded
- *     wait that timed out, a window clamp) are recorded in the workspace and
- *     reported by msrc_workspace_errors().
+ *     wait that timed out, a window clamp, a scratch overflow) are recorded in
+ *     the workspace and reported by msrc_workspace_errors().
  *   - Device buffers (signals, outputs, workspace) are owned by the caller; the
  *     library never allocates device memory and never frees caller memory.
  *     Rooms are host objects owned by the library between create and destroy.
