@@ -426,8 +426,10 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
 //   between its points, kDenseOver per sample; slope in FP32) to tau_a, and the
 //   residual eps = |Delta(tau_a)| fs / c - tau_a, which the FP32 stage absorbs.
 //   Other knots (FP32, per image and knot): delta_j = tau_j - tau_a solves
-//   delta = (d_j - d_a) fs / c + eps, d_a = |Delta(tau_a)|; two Newton steps
-//   from delta = eps + r jj N (r the anchor's rate of change of the delay).
+//   delta = (d_j - d_a) fs / c + eps, d_a = |Delta(tau_a)|; Newton steps from
+//   delta = eps + r h + r2 h^2 / 2 (h = jj N; r, r2 the anchor's first and
+//   second derivatives of the delay), a second step only when the first moved
+//   delta by 1e-2 samples or more.
 //   d_j - d_a uses the exact identity of knot_increment with the vector change
 //   v = sigma o (s(e_j) - s(e_a)) - (m_j - m_a). The source displacement
 //   between the two emission points comes from the FP32 pair tables (hi
@@ -444,8 +446,12 @@ __device__ __forceinline__ float ret_increment(const RetAnchor& r, const float4 
   const int64_t Ka = int64_t(__float_as_int(r.Sg.w)) + base_idx;
   int64_t I = -1;
   float dx = 0.0f, dy = 0.0f, dz = 0.0f, bx = 0.0f, by = 0.0f, bz = 0.0f;
+  float step = 1.0f;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
+    // from the quadratic guess one step is usually enough: a step below 1e-2
+    // samples leaves an error of order tau'' (1e-2)^2, far below FP32 rounding
+    if (it == 1 && fabsf(step) < 1e-2f) break;
     const float gq = fmaf(-float(kDenseOver), delta, r.H.w);
     const float gi = floorf(gq);
     const float fr = gq - gi;
@@ -469,7 +475,8 @@ __device__ __forceinline__ float ret_increment(const RetAnchor& r, const float4 
     const float dd = __fdividef(q, r.A.w + sqrtf(fmaf(r.A.w, r.A.w, q)));
     const float gs = __fdividef((r.A.x + vx) * r.Sg.x * dx + (r.A.y + vy) * r.Sg.y * dy + (r.A.z + vz) * r.Sg.z * dz,
                                 r.A.w + dd);
-    delta -= __fdividef(delta - fmaf(dd, fsc, r.E.x), fmaf(gs, c4, 1.0f));
+    step = __fdividef(delta - fmaf(dd, fsc, r.E.x), fmaf(gs, c4, 1.0f));
+    delta -= step;
   }
   return delta;
 }
@@ -589,13 +596,31 @@ __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const I
     const float dsz = (h1.z - h0.z) + (l1.z - l0.z);
     const float Ax = Dv[0].hi, Ay = Dv[1].hi, Az = Dv[2].hi, da = dist.hi;
     const float gsl = (Ax * sg[0] * dsx + Ay * sg[1] * dsy + Az * sg[2] * dsz) / da * c4;
+    // curvature of the delay for the guess of the other knots (still microphone):
+    // with D(e) = d(e) fs / c, tau'' = D'' / (1 + D')^3, D'' = fs/c ((|v|^2 - (u.v)^2) / d + u.a),
+    // v and a the per-sample velocity and acceleration of sigma o s from table differences
+    float r2;
+    {
+      const int64_t k2 = min(k + 2, kmax + 1);
+      const float4 h2 = HI[k2], l2 = LO[k2];
+      const float ax = ((h2.x - h1.x) + (l2.x - l1.x)) - dsx;
+      const float ay = ((h2.y - h1.y) + (l2.y - l1.y)) - dsy;
+      const float az = ((h2.z - h1.z) + (l2.z - l1.z)) - dsz;
+      const float kd = float(kDenseOver), kd2 = kd * kd;
+      const float uv = (Ax * sg[0] * dsx + Ay * sg[1] * dsy + Az * sg[2] * dsz) / da * kd;
+      const float ua = (Ax * sg[0] * ax + Ay * sg[1] * ay + Az * sg[2] * az) / da * kd2;
+      const float vv = (dsx * dsx + dsy * dsy + dsz * dsz) * kd2;
+      const float D2 = S.fsc * ((vv - uv * uv) / da + ua);
+      const float o1 = 1.0f + gsl;
+      r2 = D2 / (o1 * o1 * o1);
+    }
     an6[6 * ib + 0] = make_float4(Ax, Ay, Az, da);
     an6[6 * ib + 1] = make_float4(h0.x, h0.y, h0.z, f);
     an6[6 * ib + 2] = make_float4(l0.x, l0.y, l0.z, fa);
     // table step of the path there; rate of change of the delay per output sample (still microphone)
     an6[6 * ib + 3] = make_float4(dsx, dsy, dsz, gsl / (1.0f + gsl));
     an6[6 * ib + 4] = make_float4(sg[0], sg[1], sg[2], __int_as_float(int(k)));
-    an6[6 * ib + 5] = make_float4(eps, Dfl, 0.0f, 0.0f);
+    an6[6 * ib + 5] = make_float4(eps, Dfl, r2, 0.0f);
     img_s[ib] = make_int4(g.jf * g.N - int(Dfl), __float_as_int(Dfl - 0.5f / kFarrowSegs),
                           __float_as_int(__ldg(gain + ib)), 0);
   }
@@ -620,8 +645,9 @@ __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const I
       for (int k = 0; k < kRetUnits; ++k) {
         const int jj = min(jb + k * tpi, nk - 1);
         const float4 um = moving ? um_s[jj] : zero4;
+        const float h = float(jj * g.N);
         de[k] = ret_increment(r, um, HI, LO, int64_t(kDenseOver) * jj * g.N, kmax, fsc, c4,
-                              fmaf(r.dA.w, float(jj * g.N), r.E.x));
+                              fmaf(0.5f * r.E.z * h, h, fmaf(r.dA.w, h, r.E.x)));
       }
 #pragma unroll
       for (int k = 0; k < kRetUnits; ++k) {
