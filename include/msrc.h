@@ -17,7 +17,8 @@
  *     of all images are summed (Eq. 8).
  *   - Options: microphones on a moving array (msrc_set_array_trajectory),
  *     emission-time (retarded) distances (delay_model), knot rates chosen
- *     from the motion (msrc_suggest_knot_rates). Reverse mode
+ *     from the motion (msrc_suggest_knot_rates, msrc_suggest_bandlimited_rates).
+ *     Reverse mode
  *     (msrc_synthesize_backward) gives gradients for the signal, trajectory
  *     parameters and wall coefficients.
  *
@@ -171,6 +172,19 @@ msrc_status msrc_trajectory_positions(msrc_room_t room, const double* times, int
  * tol_samples > 0, max_step >= 1; needs a trajectory (MSRC_ERR_STATE). The
  * room's own tier rates are not changed: create a room with these rates. */
 msrc_status msrc_suggest_knot_rates(msrc_room_t room, double tol_samples, int32_t max_step, double* rates_hz);
+
+/* Knot rates for band-limited upsampling (Sec. II-C: the image distance is
+ * band-limited by the motion, so knots at a rate above twice its bandwidth
+ * recover it; the nearer the image, the wider the band). For every tier,
+ * writes to rates_hz[t] the lowest rate fs / N (N an integer, rates tried
+ * from 1 / duration up in steps of 1.25x) at which the room's band-limited
+ * kernel (upsample_halfwidth) reproduces the distances of the tier's four
+ * nearest images within tol_samples of delay. The error is checked at 16
+ * points per knot interval over [0, duration], for microphone 0 carried by
+ * the array, with the knots beyond the ends on the path's extension. Use the
+ * rates with tier_upsample; linear interpolation between the virtual knots
+ * adds its own chord error. tol_samples > 0; needs a trajectory (MSRC_ERR_STATE). */
+msrc_status msrc_suggest_bandlimited_rates(msrc_room_t room, double tol_samples, double* rates_hz);
 
 /* Replaces the six wall reflection coefficients of a room (beta: 6 doubles in
  * [0, 1], host memory); the Farrow fit and the trajectory are kept. Used by

@@ -70,6 +70,7 @@ SIGNATURES = [
     ("msrc_trajectory_positions", _I32, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_double)]),
     ("msrc_suggest_knot_rates", _I32, [_P, ctypes.c_double, _I32, ctypes.POINTER(ctypes.c_double)]),
+    ("msrc_suggest_bandlimited_rates", _I32, [_P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
     ("msrc_set_reflection", _I32, [_P, ctypes.POINTER(ctypes.c_double)]),
     ("msrc_workspace_size", _I32, [ctypes.POINTER(_P), _I32, _I64P, _I64P, _SZP, _SZP]),
     ("msrc_synthesize", _I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P), _I64P, ctypes.POINTER(_P),

@@ -130,6 +130,15 @@ class Room:
         _lib.check(lib.msrc_suggest_knot_rates(self._h, float(tol_samples), int(max_step), out))
         return [float(out[t]) for t in range(self._desc.n_tiers)]
 
+    def suggest_bandlimited_rates(self, tol_samples: float) -> list:
+        """Per tier, the lowest knot rate (Hz, fs / integer) at which the
+        band-limited upsampler reproduces the delays of the tier's nearest
+        images within tol_samples (see msrc_suggest_bandlimited_rates)."""
+        lib = _lib.load()
+        out = (ctypes.c_double * 4)()
+        _lib.check(lib.msrc_suggest_bandlimited_rates(self._h, float(tol_samples), out))
+        return [float(out[t]) for t in range(self._desc.n_tiers)]
+
     def set_reflection(self, beta) -> None:
         lib = _lib.load()
         b = np.ascontiguousarray(np.asarray(beta, np.float64).reshape(6))

@@ -1124,6 +1124,87 @@ msrc_status msrc_suggest_knot_rates(msrc_room_t room, double tol_samples, int32_
   return MSRC_OK;
 }
 
+msrc_status msrc_suggest_bandlimited_rates(msrc_room_t room, double tol_samples, double* rates_hz) {
+  if (!room || !rates_hz) return fail(MSRC_ERR_INVALID_ARG, "null argument");
+  if (!(tol_samples > 0.0)) return fail(MSRC_ERR_INVALID_ARG, "need tol_samples > 0");
+  if (!room->has_traj) return fail(MSRC_ERR_STATE, "room has no trajectory");
+  const msrc_room& R = *room;
+  const double T = R.traj.duration_s, fs = R.d.fs, fs_c = R.d.fs / R.d.c;
+  const int Q = R.up_q;
+  // microphone 0 (carried by the array) and the source at time t
+  auto geometry = [&](double t, double s[3], double m[3]) {
+    host_source(R.traj, t, s);
+    double a0[3] = {0, 0, 0}, at[3] = {0, 0, 0};
+    if (R.arr_moving) {
+      host_source(R.arr, 0.0, a0);
+      host_source(R.arr, t, at);
+    }
+    for (int d = 0; d < 3; ++d) m[d] = R.mics[0][d] + at[d] - a0[d];
+  };
+  struct Img { double dist; int n[3], p[3]; };
+  auto distance = [&](const Img& c, double t) {
+    double s[3], m[3];
+    geometry(t, s, m);
+    double acc = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double v = (1.0 - 2.0 * c.p[d]) * s[d] + 2.0 * c.n[d] * R.d.dims[d] - m[d];
+      acc += v * v;
+    }
+    return std::sqrt(acc);
+  };
+  // the tier's four nearest images at mid-duration
+  std::vector<std::vector<Img>> near(R.d.n_tiers);
+  const int K = R.d.max_order;
+  for (int nx = -K; nx <= K; ++nx)
+    for (int ny = -K; ny <= K; ++ny)
+      for (int nz = -K; nz <= K; ++nz) {
+        if (std::abs(nx) + std::abs(ny) + std::abs(nz) > K) continue;
+        for (int pb = 0; pb < 8; ++pb) {
+          Img c{0.0, {nx, ny, nz}, {pb & 1, (pb >> 1) & 1, (pb >> 2) & 1}};
+          int rho = 0;
+          for (int d = 0; d < 3; ++d) rho += std::abs(2 * c.n[d] - c.p[d]);
+          c.dist = distance(c, 0.5 * T);
+          auto& v = near[tier_of(R.d, rho)];
+          v.push_back(c);
+          std::sort(v.begin(), v.end(), [](const Img& x, const Img& y) { return x.dist < y.dist; });
+          if (v.size() > 4) v.pop_back();
+        }
+      }
+  // the kernel's weights at 16 points per knot interval
+  constexpr int kPts = 16;
+  std::vector<float> wt;
+  upsampler_rows(kPts, Q, wt);
+  for (int t = 0; t < R.d.n_tiers; ++t) {
+    double chosen = fs;
+    std::vector<double> dk;
+    for (double rate = std::max(0.5, 1.0 / T);; rate *= 1.25) {
+      const double Nc = std::max(1.0, std::floor(fs / rate));
+      const double h = Nc / fs;  // knot spacing (s)
+      const int J = int(std::ceil(T / h));
+      double worst = 0.0;
+      for (const Img& c : near[t]) {
+        dk.resize(J + 1 + 2 * Q);
+        for (int j = -Q; j <= J + Q; ++j) dk[j + Q] = distance(c, j * h);
+        for (int j = 0; j < J; ++j)
+          for (int p = 0; p < kPts; ++p) {
+            const float* w = &wt[p * (2 * Q + 1)];
+            double acc = 0.0;
+            for (int i = 0; i < 2 * Q; ++i) acc += double(w[i]) * dk[j - Q + 1 + i + Q];
+            const double tt = (j + double(p) / kPts) * h;
+            if (tt > T) break;
+            worst = std::max(worst, std::fabs(acc - distance(c, tt)));
+          }
+      }
+      if (worst * fs_c <= tol_samples || Nc <= 1.0) {
+        chosen = fs / Nc;
+        break;
+      }
+    }
+    rates_hz[t] = chosen;
+  }
+  return MSRC_OK;
+}
+
 msrc_status msrc_set_array_trajectory(msrc_room_t room, const msrc_traj_desc* traj) {
   if (!room) return fail(MSRC_ERR_INVALID_ARG, "null room");
   msrc_room saved = *room;

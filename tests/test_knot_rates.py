@@ -52,3 +52,37 @@ def test_suggested_rates_meet_the_delay_tolerance(kw, arr, tol):
     assert np.all(worst <= tol)
     # and not wastefully dense: the sparsest-knot tier uses a good part of its budget
     assert worst[-1] >= tol / 40 or rates[-1] == spec.fs / 2000
+
+
+def _max_bl_delay_error(spec, rates, Q):
+    """Largest |tau| difference between band-limited knots at `rates` (a
+    virtual knot at every sample, so only the upsampler's error remains) and
+    the dense delays, over every image and sample (oracle)."""
+    steps = [int(round(spec.fs / r)) for r in rates]
+    tiered = oracle_scene(replace(spec, up_halfwidth=Q,
+                                  tiers=[(t[0], spec.fs / s, s) for t, s in zip(spec.tiers, steps)]))
+    dense = oracle_scene(replace(spec, tiers=[(t[0], spec.fs) for t in spec.tiers]))
+    n = np.arange(spec.n_in)
+    worst = np.zeros(len(spec.tiers))
+    tab = oracle.enumerate_images(dense)
+    for i in range(tab["tier"].size):
+        t0, _, _ = oracle.delay_gain(dense, i, n)
+        t1, _, _ = oracle.delay_gain(tiered, i, n)
+        worst[tab["tier"][i]] = max(worst[tab["tier"][i]], np.max(np.abs(t1 - t0)))
+    return worst
+
+
+@pytest.mark.parametrize("tol", [1e-2, 1e-3])
+def test_bandlimited_rates_meet_the_delay_tolerance(tol):
+    """Sec. II-C: knots at a rate chosen from the motion recover the distance
+    band-limited. On a 1 s circle the suggested rates are a few Hz to tens of
+    Hz, and the upsampled delays of every image stay within the tolerance."""
+    spec = W.small_scene(seed=12, K=1, traj_kind=W.CIRCLE, seconds=1.0,
+                         tiers=[(0, 16000.0), (W.RHO_INF, 1000.0)])
+    room = api.Room.from_spec(spec)
+    rates = room.suggest_bandlimited_rates(tol)
+    assert all(r < 100.0 for r in rates)
+    worst = _max_bl_delay_error(spec, rates, Q=4)
+    assert np.all(worst <= 1.5 * tol)
+    # a quarter of the rate is not enough
+    assert np.any(_max_bl_delay_error(spec, [r / 4 for r in rates], Q=4) > tol)
