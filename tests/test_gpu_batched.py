@@ -68,3 +68,25 @@ def test_autotuner_picks_and_caches(tmp_path):
         assert rel_l2(y[0].double().cpu().numpy(), ref) < 1e-5
     finally:
         api.set_tile_config(0)
+
+
+def test_batched_config3_full_size_sampled():
+    """All 256 batched scenes in one graph-replayed persistent launch, in the
+    tile configuration the benchmark's autotuner picks for them (9), checked on
+    sampled outputs of every 8th scene that the oracle evaluates one by one."""
+    specs = [W.config3_scene(s) for s in range(256)]
+    rooms = [api.Room.from_spec(s) for s in specs]
+    xs = [torch.from_numpy(s.x).cuda() for s in specs]
+    try:
+        api.set_tile_config(9)
+        b = api.Batch(rooms, xs)
+        ys = [y.clone() for y in b.run(True)]
+        b.stream.synchronize()
+    finally:
+        api.set_tile_config(0)
+    for i in range(0, 256, 8):
+        spec = specs[i]
+        idx = np.array([0, spec.n_in // 3, spec.n_in // 2, spec.n_in - 1], np.int64)
+        ref = oracle.y_at(oracle_scene(spec), spec.x.astype(np.float64), idx)
+        got = ys[i][0].double().cpu().numpy()[idx]
+        assert rel_l2(got, ref) < 1e-5 or np.max(np.abs(got - ref)) < 1e-9, i
