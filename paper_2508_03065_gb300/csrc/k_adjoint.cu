@@ -427,10 +427,40 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
 // slower than c/2), so images are separated by a barrier and no atomics are
 // needed.
 template <bool kChecked>
+__device__ __forceinline__ void dx_bins(const float2* const* row, const int4 im, const unsigned* rmc, const int* rmj,
+                                        const float* rf, const float* dyv, const bool* valid, unsigned pw,
+                                        unsigned* idx, float* val, float* w) {
+  constexpr unsigned kDiscard = unsigned(kFarrowSegs * kDxWcap);
+  const float gi = __int_as_float(im.z);
+  const float Dp = __int_as_float(im.y);
+#pragma unroll
+  for (int c = 0; c < kBwChunks; ++c) {
+    float tau;
+    if (kChecked) {
+      const DelaySplit ds = split_delay(row[c][0], rmj[c] + im.x, rf[c], Dp);
+      idx[c] = (valid[c] && unsigned(ds.col) < pw) ? unsigned(ds.seg * kDxWcap + ds.col) : kDiscard;
+      w[c] = ds.w;
+      tau = ds.tau;
+    } else {
+      const unsigned i = split_index<kDxWcap>(row[c][0], im.x, rmc[c], rf[c], Dp, &w[c], &tau);
+      idx[c] = valid[c] ? min(i, kDiscard - 1) : kDiscard;
+    }
+    val[c] = dyv[c] * __fdividef(gi, tau);  // dy g
+  }
+}
+
+// The dx kernel's scatter of one block's images into the w window: per
+// image-sample, dy g w^q goes to bin (segment, column); samples past the output
+// (and, with kChecked, read positions outside this pass) go to a discard slot
+// past the window. Within one image no two samples share a bin (the source is
+// slower than c/2), so images are separated by a barrier and no atomics are
+// needed. The bins and values of the next image are computed while this
+// image's window reads are in flight (the records are read-only here).
+template <bool kChecked>
 __device__ __forceinline__ void dx_images(float4* wq_s, float* wp_s, const float2* rec_s, const int4* img_s, int cnt,
                                           const int* jc, const int* rmj, const float* rf, const float* dyv,
                                           const bool* valid, unsigned pw) {
-  constexpr unsigned kDiscard = unsigned(kFarrowSegs * kDxWcap);
+  if (cnt <= 0) return;
   const float2* row[kBwChunks];
   unsigned rmc[kBwChunks];
 #pragma unroll
@@ -438,31 +468,44 @@ __device__ __forceinline__ void dx_images(float4* wq_s, float* wp_s, const float
     row[c] = rec_s + jc[c] * cnt;
     rmc[c] = fold_rounding(rmj[c]);
   }
+  unsigned idx[kBwChunks];
+  float val[kBwChunks], w[kBwChunks];
+  dx_bins<kChecked>(row, img_s[0], rmc, rmj, rf, dyv, valid, pw, idx, val, w);
   for (int ib = 0; ib < cnt; ++ib) {
-    const int4 im = img_s[ib];
-    const float gi = __int_as_float(im.z);
-    const float Dp = __int_as_float(im.y);
+    float4 wa[kBwChunks];
+    float wb[kBwChunks];
 #pragma unroll
     for (int c = 0; c < kBwChunks; ++c) {
-      float w, tau;
-      unsigned idx;
-      if (kChecked) {
-        const DelaySplit ds = split_delay(row[c][ib], rmj[c] + im.x, rf[c], Dp);
-        idx = (valid[c] && unsigned(ds.col) < pw) ? unsigned(ds.seg * kDxWcap + ds.col) : kDiscard;
-        w = ds.w;
-        tau = ds.tau;
-      } else {
-        idx = split_index<kDxWcap>(row[c][ib], im.x, rmc[c], rf[c], Dp, &w, &tau);
-        idx = valid[c] ? min(idx, kDiscard - 1) : kDiscard;
-      }
-      const float val = dyv[c] * __fdividef(gi, tau);  // dy g
-      const float p1 = val * w, p2 = p1 * w, p3 = p2 * w, p4 = p3 * w;
-      float4 wa = wq_s[idx];
-      wa.x += val; wa.y += p1; wa.z += p2; wa.w += p3;
-      wq_s[idx] = wa;
-      wp_s[idx] += p4;
+      wa[c] = wq_s[idx[c]];
+      wb[c] = wp_s[idx[c]];
+    }
+    // the last image recomputes its own bins (unused)
+    const int nb = min(ib + 1, cnt - 1);
+    unsigned nidx[kBwChunks];
+    float nval[kBwChunks], nw[kBwChunks];
+    const float2* nrow[kBwChunks];
+#pragma unroll
+    for (int c = 0; c < kBwChunks; ++c) nrow[c] = row[c] + nb;
+    dx_bins<kChecked>(nrow, img_s[nb], rmc, rmj, rf, dyv, valid, pw, nidx, nval, nw);
+#pragma unroll
+    for (int c = 0; c < kBwChunks; ++c) {
+      const float p1 = val[c] * w[c], p2 = p1 * w[c], p3 = p2 * w[c], p4 = p3 * w[c];
+      wa[c].x += val[c]; wa[c].y += p1; wa[c].z += p2; wa[c].w += p3;
+      wb[c] += p4;
+    }
+    // both chunks of a thread lie in different bins, or both in the discard slot
+#pragma unroll
+    for (int c = 0; c < kBwChunks; ++c) {
+      wq_s[idx[c]] = wa[c];
+      wp_s[idx[c]] = wb[c];
     }
     __syncthreads();  // the next image may write the same bins
+#pragma unroll
+    for (int c = 0; c < kBwChunks; ++c) {
+      idx[c] = nidx[c];
+      val[c] = nval[c];
+      w[c] = nw[c];
+    }
   }
 }
 
@@ -558,16 +601,20 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
           else
             dx_images<true>(wq_s, wp_s, rec_s, img_s, g.cnt, jc, rmj, rf, dyv, valid, unsigned(pw));
         }
-        // dx[m'] += sum_{row, k} c[row][k] w[row][m' + k], 4 consecutive m' per thread
+        // dx[m'] += sum_{row, k} c[row][k] w[row][m' + k] for the outputs m' =
+        // pass_lo - kL/2 + 1 + q, q in [0, pw + kL - 1); output q reads window
+        // columns q + 1 - kL + k. A thread takes the 4 outputs q = 32 g + l + 8 o
+        // (g = i / 8, l = i % 8, o = 0..3), so the 8 lanes of a quarter warp read
+        // 8 consecutive columns (no bank conflicts) and every column a thread
+        // reads serves up to 4 of its outputs.
         const int n_outv = pw + kL - 1;
-        for (int o4 = threadIdx.x; 4 * o4 < n_outv; o4 += kBwThreads) {
-          const int mp0 = pass_lo - kL / 2 + 1 + 4 * o4;
+        for (int i = threadIdx.x; 32 * (i >> 3) + (i & 7) < n_outv; i += kBwThreads) {
+          const int q0 = 32 * (i >> 3) + (i & 7);
           float acc4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-          for (int tt = 0; tt < kL + 3; ++tt) {
-            // window column of m = mp0 - kL/2 + tt feeds output mp0 + o through
-            // tap index kk = k + kL/2 = tt - o
-            const int cc = mp0 - pass_lo - kL / 2 + tt;
+          for (int tt = 0; tt < kL + 24; ++tt) {
+            // column q0 + 1 - kL + tt feeds output q0 + 8 o through tap kk = tt - 8 o
+            const int cc = q0 + 1 - kL + tt;
             if (cc < 0 || cc >= pw) continue;
             float wv[kZRows];
 #pragma unroll
@@ -578,7 +625,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
             }
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
-              const int kk = tt - o;
+              const int kk = tt - 8 * o;
               if (kk < 0 || kk >= kL) continue;
 #pragma unroll
               for (int row = 0; row < kZRows; ++row)
@@ -587,8 +634,9 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
           }
 #pragma unroll
           for (int o = 0; o < 4; ++o) {
-            const int mp = mp0 + o;
-            if (4 * o4 + o < n_outv && mp >= 0 && mp < S.n_in) dxrow[mp] += acc4[o];
+            const int q = q0 + 8 * o;
+            const int mp = pass_lo - kL / 2 + 1 + q;
+            if (q < n_outv && mp >= 0 && mp < S.n_in) dxrow[mp] += acc4[o];
           }
         }
       }
