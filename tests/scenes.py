@@ -24,3 +24,13 @@ def rel_l2(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def max_length_scene() -> W.SceneSpec:
+    """The longest signal the library takes: 2^24 samples (17.5 min at 16 kHz),
+    a circle so that the source stays in the room, order 2, one 500 Hz tier."""
+    from dataclasses import replace
+    n = 1 << 24
+    spec = W.small_scene(seed=50, K=2, traj_kind=W.CIRCLE, seconds=1.0, tiers=[(W.RHO_INF, 500.0)])
+    rng = np.random.default_rng(50)
+    return replace(spec, x=(rng.standard_normal(n) * 0.1).astype(np.float32), duration=n / spec.fs)

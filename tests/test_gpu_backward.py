@@ -17,7 +17,7 @@ import torch
 from oracle import api as oracle
 from paper_2508_03065_gb300 import api
 from paper_2508_03065_gb300 import workloads as W
-from tests.scenes import oracle_scene, rel_l2
+from tests.scenes import max_length_scene, oracle_scene, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -63,6 +63,23 @@ def test_dot_product_identity_on_gpu():
     v = torch.from_numpy(rng.standard_normal(spec.n_in).astype(np.float32)).cuda()
     y = api.synthesize([room], [x])[0][0]
     dx = api.synthesize_backward([room], [x], [v[None]], want_params=False, want_beta=False)[0][0]
+    lhs = float(torch.dot(y.double(), v.double()))
+    rhs = float(torch.dot(x.double(), dx.double()))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_dot_product_identity_at_maximum_length():
+    # reverse mode over the longest signal the library takes (2^24 samples):
+    # <A x, v> = <x, A^T v> with v leaning on A x so that neither side is small
+    spec = max_length_scene()
+    room = api.Room.from_spec(spec)
+    x = torch.from_numpy(spec.x).cuda()
+    y = api.synthesize([room], [x])[0][0]
+    rng = np.random.default_rng(3)
+    v = y / y.norm() * float(np.sqrt(spec.n_in)) + torch.from_numpy(
+        rng.standard_normal(spec.n_in).astype(np.float32)).cuda()
+    dx = api.synthesize_backward([room], [x], [v[None]], want_params=False, want_beta=False)[0][0]
+    assert dx.shape == (spec.n_in,) and bool(torch.isfinite(dx).all())
     lhs = float(torch.dot(y.double(), v.double()))
     rhs = float(torch.dot(x.double(), dx.double()))
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)

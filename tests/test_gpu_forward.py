@@ -4,8 +4,9 @@ Tolerance: relative L2 <= 1e-5 per scene and microphone (FP32 path vs FP64
 oracle), the bar the method is held to. Cases span several output tiles with a
 ragged tail, several image blocks with a ragged last block, every tier layout,
 both windows, 8/32/64 taps, every trajectory kind, multiple microphones,
-batched scenes and the degenerate cases (free field, one sample, outputs longer
-or shorter than the input).
+batched scenes, the longest signal the library takes (2^24 samples) and the
+degenerate cases (free field, one sample, outputs longer or shorter than the
+input).
 """
 import numpy as np
 import pytest
@@ -14,7 +15,7 @@ import torch
 from oracle import api as oracle
 from paper_2508_03065_gb300 import api
 from paper_2508_03065_gb300 import workloads as W
-from tests.scenes import oracle_scene, rel_l2
+from tests.scenes import max_length_scene, oracle_scene, rel_l2
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -117,6 +118,17 @@ def test_config2_full_size_sampled():
     spec = W.config2()
     y = gpu_run([spec])[0][0]
     idx = np.concatenate([np.arange(0, 192000, 192000 // 24), [191999, 100, 101, 57000, 57001]])
+    ref = oracle.y_at(oracle_scene(spec), spec.x.astype(np.float64), idx)
+    assert rel_l2(y[idx], ref) < TOL
+
+
+def test_maximum_signal_length_sampled():
+    # sample and column indices at their largest, checked on sampled outputs
+    spec = max_length_scene()
+    n = spec.n_in
+    y = gpu_run([spec])[0][0]
+    assert y.shape == (n,)
+    idx = np.concatenate([np.arange(0, n, n // 24), [n - 1, n - 2, n - 33, 1 << 23, (1 << 23) - 1]])
     ref = oracle.y_at(oracle_scene(spec), spec.x.astype(np.float64), idx)
     assert rel_l2(y[idx], ref) < TOL
 
