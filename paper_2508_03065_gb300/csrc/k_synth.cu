@@ -86,22 +86,31 @@ __global__ void __launch_bounds__(kPreThreads) k_prefilter(const __grid_constant
 // kChecked: the window is processed in several column passes and only columns
 // inside this pass count; otherwise every read position lies inside the window
 // by construction and the index is only clamped to the window arrays.
+// Unchecked reads index the window by byte offset (split_offset): the offset
+// of the power-4 value, 4 times it for the powers 0..3.
 template <int kStride, bool kChecked>
 __device__ __forceinline__ float image_sample(const float4* zq, const float* zp, const float2 rec, const int4 im,
-                                              int rmj, unsigned rmc, float rf, unsigned wmax, float acc) {
+                                              unsigned I4, int rmj, unsigned rmc4, float rf, unsigned wmax,
+                                              float acc) {
   const float Dp = __int_as_float(im.y);
   float w, tau;
-  unsigned idx;
+  float4 A;
+  float B;
   if (kChecked) {
     const DelaySplit ds = split_delay(rec, rmj + im.x, rf, Dp);
     if (unsigned(ds.col) > wmax) return acc;
-    idx = unsigned(ds.seg * kStride + ds.col);
+    const unsigned idx = unsigned(ds.seg * kStride + ds.col);
+    A = zq[idx];
+    B = zp[idx];
     w = ds.w;
     tau = ds.tau;
   } else {
-    idx = min(split_index<kStride>(rec, im.x, rmc, rf, Dp, &w, &tau), unsigned(kFarrowSegs * kStride - 1));
+    const unsigned off = min(split_offset<kStride>(rec, I4, rmc4, rf, Dp, &w, &tau),
+                             unsigned(4 * (kFarrowSegs * kStride - 1)));
+    A = *reinterpret_cast<const float4*>(reinterpret_cast<const unsigned char*>(zq) + 4u * off);
+    B = *reinterpret_cast<const float*>(reinterpret_cast<const unsigned char*>(zp) + off);
   }
-  const float e = horner5(zq[idx], zp[idx], w);
+  const float e = horner5(A, B, w);
   return fmaf(__fdividef(__int_as_float(im.z), tau), e, acc);
 }
 
@@ -113,11 +122,11 @@ template <int kStride, int kChunks, int kUnroll, bool kChecked, bool kOne>
 __device__ __forceinline__ void gather_images(const float4* zq, const float* zp, const float2* rec_s,
                                               const int4* img_s, int cnt, const int* jc, const int* rmj,
                                               const float* rf, unsigned wmax, float* acc) {
-  unsigned rmc[kChunks];
+  unsigned rmc4[kChunks];
   const float2* row[kChunks];  // records of chunk c: row jc[c] of the interval-major table
 #pragma unroll
   for (int c = 0; c < kChunks; ++c) {
-    rmc[c] = fold_rounding(rmj[c]);
+    rmc4[c] = fold_rounding(rmj[c]) << 2;
     row[c] = rec_s + jc[c] * cnt;
   }
   int ib = 0;
@@ -125,20 +134,22 @@ __device__ __forceinline__ void gather_images(const float4* zq, const float* zp,
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int4 im = img_s[ib + u];
+      const unsigned I4 = unsigned(im.x) << 2;
       const float2 r0 = row[0][ib + u];
 #pragma unroll
       for (int c = 0; c < kChunks; ++c)
-        acc[c] = image_sample<kStride, kChecked>(zq, zp, (kOne || c == 0) ? r0 : row[c][ib + u], im, rmj[c],
-                                                 rmc[c], rf[c], wmax, acc[c]);
+        acc[c] = image_sample<kStride, kChecked>(zq, zp, (kOne || c == 0) ? r0 : row[c][ib + u], im, I4, rmj[c],
+                                                 rmc4[c], rf[c], wmax, acc[c]);
     }
   }
   for (; ib < cnt; ++ib) {
     const int4 im = img_s[ib];
+    const unsigned I4 = unsigned(im.x) << 2;
     const float2 r0 = row[0][ib];
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)
-      acc[c] = image_sample<kStride, kChecked>(zq, zp, (kOne || c == 0) ? r0 : row[c][ib], im, rmj[c], rmc[c],
-                                               rf[c], wmax, acc[c]);
+      acc[c] = image_sample<kStride, kChecked>(zq, zp, (kOne || c == 0) ? r0 : row[c][ib], im, I4, rmj[c],
+                                               rmc4[c], rf[c], wmax, acc[c]);
   }
 }
 

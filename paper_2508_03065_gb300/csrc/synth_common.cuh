@@ -720,6 +720,21 @@ __device__ __forceinline__ unsigned fold_rounding(int r_minus_mlo_plus_jjN) {
   return unsigned(r_minus_mlo_plus_jjN) - unsigned(kRoundBits >> 2);
 }
 
+// The same index times 4 (the byte offset of a 4-byte element), formed from
+// the rounded bits b without splitting them: with seg = b & 3,
+//   4 (seg kStride + col) = seg (4 kStride - 1) + b + 4 I + 4 rmc   (mod 2^32),
+// since b - seg = 4 (b >> 2). I4 = 4 img.x (once per image), rmc4 = 4 rmc.
+template <int kStride>
+__device__ __forceinline__ unsigned split_offset(const float2 rec, unsigned I4, unsigned rmc4, float rf, float Dp,
+                                                 float* w, float* tau) {
+  const float Y = fmaf(rf, rec.y, rec.x);
+  const float q = Y + kRound;
+  const unsigned b = unsigned(__float_as_int(q));
+  *w = Y - (q - kRound);
+  *tau = fmaf(Y, -1.0f / kFarrowSegs, Dp);
+  return (b & 3u) * unsigned(4 * kStride - 1) + b + (I4 + rmc4);
+}
+
 // Farrow polynomial (degree 4) from the powers 0..3 (A) and 4 (B), Horner in w.
 __device__ __forceinline__ float horner5(const float4 A, const float B, float w) {
   float e = fmaf(B, w, A.w);
