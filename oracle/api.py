@@ -90,6 +90,8 @@ def _load():
             lib.oracle_y_at.argtypes = [_S, _D, L, _I64, L, _I32, L, _D]
             lib.oracle_synthesize.argtypes = [_S, _D, L, L, _D]
             lib.oracle_adjoint_x.argtypes = [_S, _D, L, L, _D]
+            lib.oracle_synthesize_envelope.argtypes = [_S, _D, L, L, ctypes.c_double, _D, _D]
+            lib.oracle_adjoint_x_envelope.argtypes = [_S, _D, L, L, ctypes.c_double, _D, _D]
             lib.oracle_loss.argtypes = [_S, _D, L, L, _D]
             lib.oracle_loss.restype = ctypes.c_double
             lib.oracle_loss_grad_cs.argtypes = [_S, _D, L, L, _D, _I32, L, ctypes.c_double, _D]
@@ -285,6 +287,33 @@ def synthesize(scene: Scene, x: np.ndarray, n_out: Optional[int] = None) -> np.n
     sc = scene.to_c()
     _load().oracle_synthesize(ctypes.byref(sc), _dp(x), x.size, n_out, _dp(y))
     return y
+
+
+def synthesize_envelope(scene: Scene, x: np.ndarray, n_out: Optional[int] = None, delta: float = 1e-4):
+    """(y, env): y as synthesize(); env[n] sums, over the image-samples of
+    output n whose read position n - tau lies within `delta` samples of an
+    integer, |A_i(n)| times the difference between evaluating the taps on
+    either side of that integer ((m0, alpha) or (m0 -+ 1, alpha +- 1)). Where
+    the tap kernel jumps at the wrap (a low-order Farrow polynomial), the side
+    is decided by the precision of the delay, and any result within y +- env
+    is an evaluation of the method."""
+    x = np.ascontiguousarray(x, np.float64)
+    n_out = x.size if n_out is None else int(n_out)
+    y, env = np.zeros(n_out), np.zeros(n_out)
+    sc = scene.to_c()
+    _load().oracle_synthesize_envelope(ctypes.byref(sc), _dp(x), x.size, n_out, float(delta), _dp(y), _dp(env))
+    return y, env
+
+
+def adjoint_x_envelope(scene: Scene, dy: np.ndarray, n_in: int, delta: float = 1e-4):
+    """(dx, env): dx as adjoint_x(); env[m] bounds the change of dx[m] when the
+    image-samples near the wrap (as in synthesize_envelope) take the other side."""
+    dy = np.ascontiguousarray(dy, np.float64)
+    dx, env = np.zeros(int(n_in)), np.zeros(int(n_in))
+    sc = scene.to_c()
+    _load().oracle_adjoint_x_envelope(ctypes.byref(sc), _dp(dy), dy.size, int(n_in), float(delta), _dp(dx),
+                                      _dp(env))
+    return dx, env
 
 
 def adjoint_x(scene: Scene, dy: np.ndarray, n_in: int) -> np.ndarray:

@@ -25,6 +25,11 @@
 //     m0 = floor(t), alpha = t - m0, e_i(n) = sum_k w(alpha+k) sinc(alpha+k) x[m0-k];
 //   * superposition over images (Eq. 2 / Eq. 8): y[n] = sum_i A_i(n) e_i(n).
 // x[m] is zero outside [0, Ns).
+// Where the tap kernel jumps at the wrap alpha = 1 -> 0 (a low-order Farrow
+// polynomial), read positions within a small delta of an integer may take
+// either side in a lower precision; the *_envelope routines report the
+// difference between the two sides, for comparisons beyond it
+// (tests/test_oracle_envelope.py pins them).
 //
 // Every routine is templated on the scalar so that the same code, run in
 // std::complex<double>, gives complex-step derivatives of the loss with respect
@@ -54,6 +59,19 @@ constexpr double kPi = 3.14159265358979323846264338327950288;
 
 inline double re(double v) { return v; }
 inline double re(const cplx& v) { return v.real(); }
+
+// Read positions within `delta` samples of an integer: t = n - tau lies near
+// the wrap alpha = 0 <-> alpha = 1, where a precision other than FP64 may take
+// the other side, (m0 - 1, alpha + 1) or (m0 + 1, alpha - 1). Both sides are
+// evaluations of the method; they agree up to the tap kernel's jump at the
+// wrap (zero for the windowed sinc, not for a low-order Farrow polynomial).
+// Returns false away from the wrap, else true with the other side's m0 and
+// alpha in *m1, *a1.
+bool other_side(double alpha, long m0, double delta, long* m1, double* a1) {
+  if (alpha < delta) { *m1 = m0 - 1; *a1 = alpha + 1.0; return true; }
+  if (alpha > 1.0 - delta) { *m1 = m0 + 1; *a1 = alpha - 1.0; return true; }
+  return false;
+}
 
 }  // namespace
 
@@ -566,6 +584,77 @@ void oracle_adjoint_x(const OracleScene* S, const double* dy, long n_out, long N
     double s = 0.0;
     for (int t = 0; t < nthr; ++t) s += part[t][m];
     dx[m] = s;
+  }
+}
+
+// y as oracle_synthesize, and env[n] = sum over the image-samples of output n
+// whose read position lies within `delta` of an integer of |A_i(n)| times the
+// difference between the two sides' tap sums (see other_side): the spread of
+// valid results where the read position's side is a matter of precision.
+void oracle_synthesize_envelope(const OracleScene* S, const double* x, long Ns, long n_out, double delta,
+                                double* y, double* env) {
+  std::vector<Image> imgs = enumerate_images(*S);
+  Params<double> P = params_from<double>(*S);
+  const int half = S->taps / 2;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long n = 0; n < n_out; ++n) {
+    double acc = 0.0, spread = 0.0;
+    for (const Image& im : imgs) {
+      double tau, g, d;
+      delay_gain(*S, P, im, n, &tau, &g, &d);
+      const double t = double(n) - tau;
+      const long m0 = static_cast<long>(std::floor(t));
+      const double alpha = t - double(m0);
+      double e = 0.0;
+      for (int k = -half; k <= half - 1; ++k) e += tap_weight(*S, k, alpha) * xval(x, Ns, m0 - k);
+      acc += g * e;
+      long m1;
+      double a1;
+      if (other_side(alpha, m0, delta, &m1, &a1)) {
+        double e1 = 0.0;
+        for (int k = -half; k <= half - 1; ++k) e1 += tap_weight(*S, k, a1) * xval(x, Ns, m1 - k);
+        spread += std::fabs(g * (e1 - e));
+      }
+    }
+    y[n] = acc;
+    env[n] = spread;
+  }
+}
+
+// dx as oracle_adjoint_x, and env[m] = sum over the image-samples (n, i) near
+// the wrap (see other_side) of |dy[n] A_i(n)| times the difference between the
+// two sides' weights of x[m].
+void oracle_adjoint_x_envelope(const OracleScene* S, const double* dy, long n_out, long Ns, double delta,
+                               double* dx, double* env) {
+  std::vector<Image> imgs = enumerate_images(*S);
+  Params<double> P = params_from<double>(*S);
+  const int half = S->taps / 2;
+  for (long m = 0; m < Ns; ++m) { dx[m] = 0.0; env[m] = 0.0; }
+  std::vector<double> w0(S->taps + 1), w1(S->taps + 1);
+  for (long n = 0; n < n_out; ++n) {
+    if (dy[n] == 0.0) continue;
+    for (const Image& im : imgs) {
+      double tau, g, d;
+      delay_gain(*S, P, im, n, &tau, &g, &d);
+      const double t = double(n) - tau;
+      const long m0 = static_cast<long>(std::floor(t));
+      const double alpha = t - double(m0);
+      for (int k = -half; k <= half - 1; ++k) {
+        const long m = m0 - k;
+        if (m >= 0 && m < Ns) dx[m] += dy[n] * g * tap_weight(*S, k, alpha);
+      }
+      long m1;
+      double a1;
+      if (!other_side(alpha, m0, delta, &m1, &a1)) continue;
+      // weights of x[m] on either side, over the union of the two tap ranges
+      const long lo = std::min(m0, m1) - (half - 1), hi = std::max(m0, m1) + half;
+      for (long m = lo; m <= hi; ++m) {
+        const long k0 = m0 - m, k1 = m1 - m;
+        const double h0 = (k0 >= -half && k0 <= half - 1) ? tap_weight(*S, int(k0), alpha) : 0.0;
+        const double h1 = (k1 >= -half && k1 <= half - 1) ? tap_weight(*S, int(k1), a1) : 0.0;
+        if (m >= 0 && m < Ns) env[m] += std::fabs(dy[n] * g * (h1 - h0));
+      }
+    }
   }
 }
 

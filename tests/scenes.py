@@ -20,6 +20,21 @@ def oracle_scene(spec: W.SceneSpec, mic: int = 0, **override) -> oracle.Scene:
     return oracle.Scene(**kw)
 
 
+# Precision envelope of a parity comparison: read positions within this many
+# samples of an integer may fall on either side in FP32 (the device's delays
+# are good to about 1e-6 samples).
+WRAP_DELTA = 1e-4
+
+
+def beyond_envelope(a, ref, env):
+    """Relative L2 of the part of a - ref that the oracle's precision envelope
+    does not explain: max(|a - ref| - env, 0), over |ref|."""
+    a = np.asarray(a, np.float64)
+    ref = np.asarray(ref, np.float64)
+    r = np.maximum(np.abs(a - ref) - np.asarray(env, np.float64), 0.0)
+    return float(np.linalg.norm(r) / max(np.linalg.norm(ref), 1e-300))
+
+
 def rel_l2(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
