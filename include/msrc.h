@@ -51,7 +51,7 @@ extern "C" {
 typedef enum {
   MSRC_OK = 0,
   MSRC_ERR_INVALID_ARG = 1,  /* null pointer, out-of-range value, geometry not valid */
-  MSRC_ERR_UNSUPPORTED = 2,  /* valid request outside what this build handles */
+  MSRC_ERR_UNSUPPORTED = 2,  /* valid request outside what the library supports */
   MSRC_ERR_WORKSPACE = 3,    /* workspace too small or misaligned */
   MSRC_ERR_CUDA = 4,         /* a CUDA runtime call failed (message in msrc_last_error) */
   MSRC_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */

@@ -103,3 +103,27 @@ def test_random_scene_dx_parity(i):
         env += e
     err = beyond_envelope(dx, ref, env)
     assert err < TOL, (spec.name, err)
+
+
+def test_random_batch_equals_single_calls():
+    # one batched launch over 8 heterogeneous random scenes (taps and window
+    # shared, as a batch requires) equals the per-scene calls bitwise
+    specs = [replace(random_spec(i), taps=32, window=W.KAISER) for i in range(8)]
+    rooms = [api.Room.from_spec(s) for s in specs]
+    xs = [torch.from_numpy(s.x).cuda() for s in specs]
+    ys = api.synthesize(rooms, xs, n_out=[s.n_out for s in specs])
+    for r, s, x, yb in zip(rooms, specs, xs, ys):
+        assert torch.equal(yb, api.synthesize([r], [x], n_out=[s.n_out])[0]), s.name
+
+
+def test_random_backward_batch_equals_single_calls():
+    specs = [replace(random_spec(i, reverse=True), taps=32, window=W.HANN) for i in range(6)]
+    rooms = [api.Room.from_spec(s) for s in specs]
+    xs = [torch.from_numpy(s.x).cuda() for s in specs]
+    dys = [torch.from_numpy(np.random.default_rng(9100 + i).standard_normal((len(s.mics), s.n_out))
+                            .astype(np.float32)).cuda() for i, s in enumerate(specs)]
+    batched = api.synthesize_backward(rooms, xs, dys)
+    for r, s, x, dy, got in zip(rooms, specs, xs, dys, batched):
+        one = api.synthesize_backward([r], [x], [dy])[0]
+        for a, b in zip(got, one):
+            assert torch.equal(a, b), s.name
