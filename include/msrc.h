@@ -286,6 +286,14 @@ msrc_status msrc_autotune(const msrc_room_t* rooms, int32_t n_rooms, const float
  * skipped; the planner sizes blocks so that this does not happen). */
 msrc_status msrc_workspace_errors(void* workspace_dev, void* stream, uint32_t* flags);
 
+/* Test hook for the bounded waits. With bytes > 0 (a multiple of 16), every
+ * shared-window staging of later synthesis and reverse-mode launches in this
+ * process waits for `bytes` more than its copies deliver: the wait gives up
+ * after about one second, the block records bit 1 in the error word and stops,
+ * and the context stays usable (outputs of that launch are undefined).
+ * 0 (the default) turns it off. Host only; INVALID_ARG for other sizes. */
+msrc_status msrc_test_stall_window_copies(uint32_t bytes);
+
 /* Number of images of a room and, per tier, how many fall in it (host only).
  * per_tier: MSRC_MAX_TIERS entries, nullable. */
 msrc_status msrc_room_image_count(msrc_room_t room, int64_t* count, int64_t* per_tier);

@@ -57,6 +57,7 @@ struct msrc_room {
 namespace {
 
 int g_tile_config = 0;
+uint32_t g_test_extra_tx = 0;  // msrc_test_stall_window_copies
 
 // Optional per-phase timing with CUDA events recorded on the launching stream.
 // Phases: 0 setup (images, sort, knots, records), 1 prefilter, 2 synthesis, 3 reduction.
@@ -747,6 +748,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.n_scenes = int32_t(P.scenes.size());
   if (a.n_scenes == 1) a.scene0 = P.scenes[0];
   for (int k = 0; k < kUnitKinds; ++k) a.totals[k] = P.totals[k];
+  a.test_extra_tx = g_test_extra_tx;
   a.p.err = reinterpret_cast<uint32_t*>(ws);
   a.p.counter = reinterpret_cast<uint32_t*>(ws + 4);
   a.p.keys_in = reinterpret_cast<uint64_t*>(ws + P.off_keys_in);
@@ -1538,6 +1540,12 @@ msrc_status msrc_profile_read(double* ms, int32_t* n_calls) {
   }
   *n_calls = n;
   g_prof.pending = 0;
+  return MSRC_OK;
+}
+
+msrc_status msrc_test_stall_window_copies(uint32_t bytes) {
+  if (bytes % 16) return fail(MSRC_ERR_INVALID_ARG, "bytes must be a multiple of 16");
+  g_test_extra_tx = bytes;
   return MSRC_OK;
 }
 

@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
         if (threadIdx.x == 0) {
           const unsigned bq = unsigned(cnt_c) * 16u;
           const unsigned bp = unsigned((cnt_c + 3) & ~3) * 4u;  // within the padded rows
-          mbar_expect_tx(&s_mbar, unsigned(kFarrowSegs) * (bq + bp));
+          mbar_expect_tx(&s_mbar, unsigned(kFarrowSegs) * (bq + bp) + a.test_extra_tx);
           for (int sg = 0; sg < kFarrowSegs; ++sg) {
             bulk_g2s(zq_s + sg * kWcap + dst0, zqg + int64_t(sg) * S.z_len + src0, bq, &s_mbar);
             bulk_g2s(zp_s + sg * kWcap + dst0, zpg + int64_t(sg) * S.z_len + src0, bp, &s_mbar);

@@ -200,6 +200,7 @@ struct KernelArgs {
   float farrow[kFarrowSegs][kFarrowCoef][kMaxTaps];  // coefficients c[s][q][k + L/2] of the powers of w
   float farrow_g[kFarrowSegs][kGradCoef][kMaxTaps];  // degree-5 coefficients (gradient kernel)
   int32_t taps;
+  uint32_t test_extra_tx;        // test hook: bytes a window staging expects beyond its copies (0)
 };
 
 // Image code: n_d + 64 in 7 bits each, parity bits above.

@@ -101,22 +101,35 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                "l"(src), "r"(bytes), "r"(smem_u32(mb))
                : "memory");
 }
+// One poll of the mbarrier phase; the thread may be suspended for at most
+// about kSuspendHintNs while the phase is incomplete.
+constexpr unsigned kSuspendHintNs = 8192;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* mb, unsigned parity) {
   unsigned ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_u32(mb)), "r"(parity)
+      : "r"(smem_u32(mb)), "r"(parity), "r"(kSuspendHintNs)
       : "memory");
   return ok != 0;
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-// Waits for the phase `parity` of the mbarrier, giving up after kSpinLimit
-// polls (each poll may suspend the thread for a while); true on completion.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for the phase `parity` of the mbarrier; gives up (false) after about
+// kWaitLimitNs of wall time, or after kSpinLimit polls, whichever comes first.
 constexpr int kSpinLimit = 1 << 20;
+constexpr uint64_t kWaitLimitNs = uint64_t(1) << 30;  // about 1.07 s
 __device__ __forceinline__ bool mbar_wait(uint64_t* mb, unsigned parity) {
-  for (int it = 0; it < kSpinLimit; ++it)
+  if (mbar_try_wait(mb, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (int it = 1; it < kSpinLimit; ++it) {
     if (mbar_try_wait(mb, parity)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
   return false;
 }
 
