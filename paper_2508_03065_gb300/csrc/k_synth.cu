@@ -369,7 +369,8 @@ cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
   X(6, 512, 3, 2432, 4096, 256, 4)       \
   X(7, 512, 2, 2432, 4096, 256, 16)      \
   X(8, 512, 3, 1792, 8192, 256, 8)       \
-  X(9, 512, 2, 1792, 8192, 256, 8)
+  X(9, 512, 2, 1792, 8192, 256, 8)       \
+  X(10, 512, 2, 1536, 10240, 256, 8)
 
 static const TileConfig kConfigs[] = {
 #define MSRC_ROW(id, th, ch, wc, rc, bl, un) {th, ch, wc, rc, bl},
