@@ -289,6 +289,9 @@ def run_gpu(args):
         e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
 
     synth_ms = phase_ms[2] / max(n_calls, 1)
+    # measured FMA peaks of this GPU, after the timed regions (context for the
+    # derived unit-count peak below)
+    peak32, peak64 = api.measure_alu_peaks()
     sm_mhz = clk.get("sm_mhz") or 2070.0
     clk_hz = sm_mhz * 1e6
     smem_peak = SM_COUNT * SMEM_BYTES_PER_CLK_PER_SM * clk_hz / 1e9  # GB/s
@@ -309,6 +312,10 @@ def run_gpu(args):
                      "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x median SM "
                                     f"clock {sm_mhz:.0f} MHz under load (derived, not measured)",
                      "flops_per_image_sample": FLOPS_PER_IMAGE_SAMPLE,
+                     "measured_peaks": {"fp32_tflops": peak32, "fp64_tflops": peak64,
+                                        "frac_of_measured_fp32": fp32 / peak32,
+                                        "how": "independent FMA chains in every thread of a full grid, best of "
+                                               "5 launches (msrc_measure_alu_peaks)"},
                      "smem": {"achieved_gbs": achieved, "peak_gbs": smem_peak, "frac": achieved / smem_peak,
                               "bytes_per_image_sample": Z_BYTES_PER_IMAGE_SAMPLE,
                               "peak_source": f"{SM_COUNT} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x "

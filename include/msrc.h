@@ -294,6 +294,15 @@ msrc_status msrc_workspace_errors(void* workspace_dev, void* stream, uint32_t* f
  * 0 (the default) turns it off. Host only; INVALID_ARG for other sizes. */
 msrc_status msrc_test_stall_window_copies(uint32_t bytes);
 
+/* Measured ALU peaks of the current GPU: every thread of a full grid runs 16
+ * independent fused multiply-add chains, FP32 and then FP64; best of 5 timed
+ * launches after a warm-up, in TFLOP/s at 2 flops per FMA. These are the
+ * measured counterparts of the unit-count peak (SMs x lanes x 2 x clock) that
+ * the synthesis roofline is quoted against. scratch_dev: at least 16 bytes of
+ * caller-owned device memory (never written in practice). Synchronises
+ * `stream`; takes a few tens of milliseconds. */
+msrc_status msrc_measure_alu_peaks(void* scratch_dev, void* stream, double* fp32_tflops, double* fp64_tflops);
+
 /* Number of images of a room and, per tier, how many fall in it (host only).
  * per_tier: MSRC_MAX_TIERS entries, nullable. */
 msrc_status msrc_room_image_count(msrc_room_t room, int64_t* count, int64_t* per_tier);

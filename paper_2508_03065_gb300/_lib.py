@@ -83,6 +83,7 @@ SIGNATURES = [
                                         ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.c_size_t, _P]),
     ("msrc_workspace_errors", _I32, [_P, _P, ctypes.POINTER(ctypes.c_uint32)]),
     ("msrc_test_stall_window_copies", _I32, [ctypes.c_uint32]),
+    ("msrc_measure_alu_peaks", _I32, [_P, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("msrc_room_image_count", _I32, [_P, _I64P, _I64P]),
     ("msrc_room_fit_error", _I32, [_P, ctypes.POINTER(ctypes.c_double)]),
     ("msrc_set_tile_config", _I32, [_I32]),

@@ -262,6 +262,16 @@ def workspace_errors(workspace: Workspace, stream: Optional[torch.cuda.Stream] =
     return int(flags.value)
 
 
+def measure_alu_peaks(stream: Optional[torch.cuda.Stream] = None):
+    """(FP32, FP64) fused multiply-add peaks of the current GPU in TFLOP/s,
+    measured (see msrc_measure_alu_peaks)."""
+    scratch = torch.empty(16, dtype=torch.uint8, device="cuda")
+    f32, f64 = ctypes.c_double(), ctypes.c_double()
+    _lib.check(_lib.load().msrc_measure_alu_peaks(ctypes.c_void_p(scratch.data_ptr()), _stream_handle(stream),
+                                                   ctypes.byref(f32), ctypes.byref(f64)))
+    return float(f32.value), float(f64.value)
+
+
 def set_tile_config(cfg: int) -> None:
     _lib.check(_lib.load().msrc_set_tile_config(int(cfg)))
 

@@ -11,6 +11,9 @@
 
 namespace msrc {
 
+// Thread-local message returned by msrc_last_error (defined with the C ABI).
+void set_last_error(const char* msg);
+
 // Signal-side Farrow structure (Sec. II-B, Eq. 5): the tap weight of tap k is a
 // degree-kFarrowDeg polynomial in a local variable of the fractional delay,
 // piecewise over kFarrowSegs segments of [0, 1). The prefilter produces one
