@@ -11,7 +11,7 @@ gather-accumulate and reduction. Metric: image-samples per second
 synthesises its own scene (scene sharding, no collective on the data path);
 `value` is the total over ranks divided by the slowest rank's time.
 
-`--impl reference` times the FP64 CPU oracle (the checker of the GPU path) on
+`--impl reference` times the FP64 CPU oracle (the reference the GPU path is tested against) on
 the host cores, on a bounded sample of output samples of the same scene.
 Prints one JSON line (rank 0).
 """
