@@ -255,3 +255,13 @@ def test_band_limited_upsampling_planning():
         fwd = ctypes.c_size_t()
         assert lib.msrc_workspace_size(_lib.ptr_array([h.value]), 1, n, n, ctypes.byref(fwd), None) == want
         lib.msrc_destroy_room(h)
+
+
+def test_host_only_hooks_validate_arguments():
+    # the bounded-wait test hook takes multiples of 16 bytes and 0 (off); the
+    # peak measurement refuses null pointers before touching a device
+    lib = _lib.load()
+    assert lib.msrc_test_stall_window_copies(3) == _lib.ERR_INVALID_ARG
+    assert lib.msrc_test_stall_window_copies(0) == _lib.OK
+    f32, f64 = ctypes.c_double(), ctypes.c_double()
+    assert lib.msrc_measure_alu_peaks(None, None, ctypes.byref(f32), ctypes.byref(f64)) == _lib.ERR_INVALID_ARG

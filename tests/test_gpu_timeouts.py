@@ -32,10 +32,6 @@ def _stalled(fn):
         assert lib.msrc_test_stall_window_copies(0) == _lib.OK
 
 
-def test_hook_rejects_unaligned_sizes():
-    assert _lib.load().msrc_test_stall_window_copies(3) == _lib.ERR_INVALID_ARG
-
-
 def test_synthesis_wait_times_out_and_context_survives():
     spec = W.small_scene(seed=3, K=3)
     room = api.Room.from_spec(spec)
