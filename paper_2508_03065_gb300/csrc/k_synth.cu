@@ -134,7 +134,7 @@ __device__ __forceinline__ void gather_images(const float4* zq, const float* zp,
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int4 im = img_s[ib + u];
-      const unsigned I4 = unsigned(im.x) << 2;
+      const unsigned I4 = unsigned(im.w);  // 4 im.x
       const float2 r0 = row[0][ib + u];
 #pragma unroll
       for (int c = 0; c < kChunks; ++c)
@@ -144,7 +144,7 @@ __device__ __forceinline__ void gather_images(const float4* zq, const float* zp,
   }
   for (; ib < cnt; ++ib) {
     const int4 im = img_s[ib];
-    const unsigned I4 = unsigned(im.x) << 2;
+    const unsigned I4 = unsigned(im.w);  // 4 im.x
     const float2 r0 = row[0][ib];
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)

@@ -230,7 +230,7 @@ __device__ __forceinline__ void records_from_phi(const ItemGeom& g, const float*
 //   rec_s[jj * cnt + ib] = {Psi_j = -S phi_j - 1/2, sigma_j = -S (phi_{j+1} - phi_j) / N_t}
 //                          (float2, interval-major so that consecutive images of one
 //                          interval are adjacent; j = jf + jj; S = kFarrowSegs),
-//   img_s[ib]            = {I = n_jf - D_a, D_a - 1/(2S) (float), gain (float), 0}
+//   img_s[ib]            = {I = n_jf - D_a, D_a - 1/(2S) (float), gain (float), 4 I}
 // so that Y(n) = Psi_j + sigma_j r = S (n - tau(n) - n_j + I + jj N_t) - 1/2 up to
 // the integer read position, and tau(n) = (D_a - 1/(2S)) - Y / S.
 // u_s and um_s (nk entries each), anc_s (3 * cnt entries) and phi_s (cnt * nk
@@ -239,6 +239,12 @@ __device__ __forceinline__ void records_from_phi(const ItemGeom& g, const float*
 // u_m = a(t_j) - a(t_jf) and the image-to-microphone vector changes by
 // sigma o u - u_m. Returns this thread's min / max of tau over its knots
 // (window bounds of the item).
+// Image record of a work item: {I = n_jf - D_a (column offset), D_a - 1/8
+// (bits), gain (bits), 4 I (the synthesis gather's byte offset of the column)}.
+__device__ __forceinline__ int4 image_record(int I, float Dfl, float gain) {
+  return make_int4(I, __float_as_int(Dfl - 0.5f / kFarrowSegs), __float_as_int(gain), int(unsigned(I) << 2));
+}
+
 template <int kThreads>
 __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                              int4* img_s, float4* u_s, float4* um_s, float4* anc_s, float* phi_s,
@@ -285,8 +291,7 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     anc_s[2 * ib] = A;
     anc_s[2 * ib + 1] = make_float4(B.x, B.y, 0.0f, 0.0f);
     anc_s[2 * g.cnt + ib] = SG;
-    img_s[ib] = make_int4(g.jf * g.N - int(B.y), __float_as_int(B.y - 0.5f / kFarrowSegs),
-                          __float_as_int(__ldg(gain + ib)), 0);
+    img_s[ib] = image_record(g.jf * g.N - int(B.y), B.y, __ldg(gain + ib));
   }
   __syncthreads();
   // relative delay phi at every knot of every image (once per knot), then the
@@ -373,8 +378,7 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
     const float Dfl = df_floor(DF{an.x, an.y});  // the anchor, knot floor(jf / U)
     if (jr == 0) {
       dfl_s[ib] = Dfl;
-      img_s[ib] = make_int4(g.jf * g.N - int(Dfl), __float_as_int(Dfl - 0.5f / kFarrowSegs),
-                            __float_as_int(__ldg(gain + ib)), 0);
+      img_s[ib] = image_record(g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib));
     }
     const float2* tv = row + (j0_first + jr - Q + 1);  // knots j0 - Q + 1 .. j0 + Q
     const DF t0{tv[Q - 1].x, tv[Q - 1].y};
@@ -634,8 +638,7 @@ __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const I
     an6[6 * ib + 3] = make_float4(dsx, dsy, dsz, gsl / (1.0f + gsl));
     an6[6 * ib + 4] = make_float4(sg[0], sg[1], sg[2], __int_as_float(int(k)));
     an6[6 * ib + 5] = make_float4(eps, Dfl, r2, 0.0f);
-    img_s[ib] = make_int4(g.jf * g.N - int(Dfl), __float_as_int(Dfl - 0.5f / kFarrowSegs),
-                          __float_as_int(__ldg(gain + ib)), 0);
+    img_s[ib] = image_record(g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib));
   }
   __syncthreads();
   const int nk = g.nk;
