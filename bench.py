@@ -80,11 +80,15 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed
+    region: started before the warm-up (so that its own start-up falls outside
+    the region), polled every 20 ms, and reduced to the samples whose
+    timestamps lie inside the region (all samples when none do)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -98,11 +102,42 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
-    def stop(self):
+    @classmethod
+    def summarise(cls, lines, t_on=None, t_off=None):
+        """Median SM clock, maximum clock and active throttle reasons of the
+        sample lines (timestamp first), restricted to [t_on, t_off] (epoch
+        seconds) when given and when any sample falls there."""
+        import datetime
+
+        rows = []
+        for line in lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                sm, smax = float(parts[2]), float(parts[3])
+            except ValueError:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            active = [name for name, v in zip(cls.REASONS, parts[6:10]) if v.lower().startswith("active")]
+            rows.append((ts, sm, smax, active))
+        if t_on is not None and t_off is not None:
+            inside = [r for r in rows if r[0] is not None and t_on <= r[0] <= t_off]
+            if inside:
+                rows = inside
+        sm = [r[1] for r in rows]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(r[2] for r in rows) if rows else None,
+                "reasons": sorted({a for r in rows for a in r[3]}), "samples": len(sm)}
+
+    def stop(self, t_on=None, t_off=None):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -111,24 +146,10 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for name, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(name)
+        with open(self.path) as f:
+            out = self.summarise(f.readlines(), t_on, t_off)
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return out
 
 
 def cpu_baseline(spec, n_sample: int):
@@ -252,20 +273,22 @@ def run_gpu(args):
             return v
         return multigpu.job_throughput(0.0, v)[1]
 
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(max(args.warmup, 3)):
         api.synthesize([room], [x], out=[y], workspace=ws)
     api.profile_enable(True)
     api.profile_read()
-    clocks = ClockSampler(local)
     barrier()
-    clocks.start()
+    t_on = time.time()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record(stream)
     for _ in range(args.steps):
         api.synthesize([room], [x], out=[y], workspace=ws)
     stop.record(stream)
     barrier()
-    clk = clocks.stop()
+    t_off = time.time()
+    clk = clocks.stop(t_on, t_off)
     phase_ms, n_calls = api.profile_read()
     api.profile_enable(False)
     ms = start.elapsed_time(stop) / args.steps
