@@ -213,6 +213,24 @@ msrc_status msrc_synthesize(const msrc_room_t* rooms, int32_t n_rooms,
                             float* const* y_dev, const int64_t* n_out,
                             void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* Tile configuration of a call (the synthesis launch's CTA shape, window and
+ * record capacity; msrc_tile_configs() lists how many exist):
+ * MSRC_TILE_DEFAULT = the process default (msrc_set_tile_config, initially 0),
+ * else 0 .. msrc_tile_configs() - 1. The _cfg entry points take it per call, so
+ * that workloads tuned differently (msrc_autotune) share a process without
+ * overwriting each other's choice. The workspace size depends on it: size the
+ * workspace with the configuration the call uses. An id out of range is
+ * MSRC_ERR_INVALID_ARG. Results of every configuration agree within FP32
+ * rounding; for a fixed configuration they are bitwise reproducible. */
+#define MSRC_TILE_DEFAULT (-1)
+msrc_status msrc_workspace_size_cfg(const msrc_room_t* rooms, int32_t n_rooms,
+                                    const int64_t* n_in, const int64_t* n_out, int32_t tile_config,
+                                    size_t* fwd_bytes, size_t* bwd_bytes);
+msrc_status msrc_synthesize_cfg(const msrc_room_t* rooms, int32_t n_rooms,
+                                const float* const* x_dev, const int64_t* n_in,
+                                float* const* y_dev, const int64_t* n_out, int32_t tile_config,
+                                void* workspace_dev, size_t workspace_bytes, void* stream);
+
 /* Same computation with HOST signal buffers: x_host[r] is copied to the
  * workspace, the scene is synthesised and y is copied back into y_host[r]
  * (n_mics x n_out[r] floats), all enqueued on `stream`. The caller synchronises
@@ -258,22 +276,30 @@ msrc_status msrc_synthesize_backward(const msrc_room_t* rooms, int32_t n_rooms,
  * first run captures them into a CUDA graph (the stream must not be the
  * legacy default stream) and later runs replay it. Arguments as for
  * msrc_synthesize; the workspace must stay allocated until the batch is
- * destroyed. The selected tile configuration is frozen at creation. */
+ * destroyed. msrc_batch_create runs in the process default tile configuration
+ * at creation, msrc_batch_create_cfg in the one it is given (see
+ * MSRC_TILE_DEFAULT); either is frozen for the life of the batch. */
 typedef struct msrc_batch* msrc_batch_t;
 msrc_status msrc_batch_create(const msrc_room_t* rooms, int32_t n_rooms,
                               const float* const* x_dev, const int64_t* n_in,
                               float* const* y_dev, const int64_t* n_out,
                               void* workspace_dev, size_t workspace_bytes, void* stream,
                               msrc_batch_t* out);
+msrc_status msrc_batch_create_cfg(const msrc_room_t* rooms, int32_t n_rooms,
+                                  const float* const* x_dev, const int64_t* n_in,
+                                  float* const* y_dev, const int64_t* n_out, int32_t tile_config,
+                                  void* workspace_dev, size_t workspace_bytes, void* stream,
+                                  msrc_batch_t* out);
 msrc_status msrc_batch_run(msrc_batch_t batch, int32_t use_graph, void* stream);
 msrc_status msrc_batch_destroy(msrc_batch_t batch);
 
 /* Autotuner of the synthesis launch: runs the given call (arguments as for
- * msrc_synthesize) once per tile configuration whose workspace fits, `reps`
+ * msrc_synthesize) in every tile configuration whose workspace fits, `reps`
  * times each after one warm-up, timed with CUDA events on `stream`; writes the
  * mean milliseconds per configuration into ms_per_config (msrc_tile_configs()
- * entries, -1 when skipped), selects the fastest for later calls and returns
- * its id in *best. Synchronises `stream`. */
+ * entries, -1 when skipped) and the fastest configuration's id into *best, for
+ * the caller to pass to the _cfg entry points. No process-wide state changes.
+ * Synchronises `stream`. */
 msrc_status msrc_autotune(const msrc_room_t* rooms, int32_t n_rooms, const float* const* x_dev,
                           const int64_t* n_in, float* const* y_dev, const int64_t* n_out,
                           void* workspace_dev, size_t workspace_bytes, void* stream, int32_t reps,
@@ -311,8 +337,20 @@ msrc_status msrc_room_image_count(msrc_room_t room, int64_t* count, int64_t* per
  * Farrow polynomials against the exact windowed sinc (host only). */
 msrc_status msrc_room_fit_error(msrc_room_t room, double* max_abs_error);
 
-/* Tuning of the synthesis launch: selects a tile configuration id (0 = default)
- * for subsequent calls in this process; msrc_tile_configs lists how many exist. */
+/* The Farrow table the kernels use for this room (Sec. II-B, Eq. 3-5), as the
+ * device receives it (host only). The fractional delay alpha in [0, 1) falls in
+ * segment s = floor(4 alpha) with local variable w = 4 alpha - s - 1/2 in
+ * [-1/2, 1/2), and tap k (k = -L/2 .. L/2 - 1, L = taps) weighs
+ *   h(k; alpha) = sum_{q < P} out[(s * P + q) * L + k + L/2] w^q.
+ * which = 0: the synthesis (and dx) table, P = 5; which = 1: the reverse-mode
+ * gradient kernel's table, P = 6. out: 4 * P * L floats (host, caller-owned);
+ * *n_powers receives P. */
+msrc_status msrc_room_farrow_table(msrc_room_t room, int32_t which, float* out, int32_t* n_powers);
+
+/* Process default tile configuration (0 initially): the configuration of every
+ * call that names none (msrc_synthesize, msrc_synthesize_host,
+ * msrc_workspace_size, msrc_batch_create, msrc_synthesize_noalloc, or
+ * MSRC_TILE_DEFAULT); msrc_tile_configs lists how many exist. Thread-safe. */
 msrc_status msrc_set_tile_config(int32_t config_id);
 int32_t msrc_tile_configs(void);
 
@@ -335,14 +373,24 @@ msrc_status msrc_profile_read(double* ms, int32_t* n_calls);
  * scratch array of MSRC_NOALLOC_SCRATCH_BYTES that the library reserves in
  * device memory on every GPU where it is loaded, for the life of the process.
  * Rooms whose workspace (msrc_workspace_size) exceeds that size are rejected
- * with MSRC_ERR_WORKSPACE. The first call on a device looks up the array's
- * device address with that device current; make that first call before any
- * stream capture. All calls share the one array and its contents persist
- * between calls: calls that may overlap on the GPU (other streams or threads)
- * race, so the caller serialises them. Nothing is allocated by this call. */
+ * with MSRC_ERR_WORKSPACE. The call makes no cudaMalloc or cudaFree. The array
+ * is committed when the library's device code is loaded on a GPU; under lazy
+ * module loading (the CUDA default) that is the first call on that device,
+ * which also looks up the array's device address with the device current: make
+ * that first call during set-up, before any stream capture. All calls share the
+ * one array and its contents persist between calls: calls that may overlap on
+ * the GPU (other streams or threads) race, so the caller serialises them.
+ * Device-side anomalies of these calls (the error bits of msrc_workspace_errors)
+ * are read with msrc_noalloc_errors. */
 #define MSRC_NOALLOC_SCRATCH_BYTES (32u << 20)
 msrc_status msrc_synthesize_noalloc(msrc_room_t room, const float* x_dev, int64_t n_in,
                                     float* y_dev, int64_t n_out, void* stream);
+
+/* Reads and clears the device error word of the allocation-free calls on the
+ * current device (the bit set of msrc_workspace_errors, for the scratch array
+ * of msrc_synthesize_noalloc); synchronises `stream`. Returns
+ * MSRC_ERR_TIMEOUT when bit 1 (a bounded wait gave up) is set. */
+msrc_status msrc_noalloc_errors(void* stream, uint32_t* flags);
 
 const char* msrc_status_string(msrc_status status);
 const char* msrc_last_error(void);

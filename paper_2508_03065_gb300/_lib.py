@@ -16,6 +16,7 @@ MAX_TIERS = 4
 MAX_MICS = 16
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = range(7)
+TILE_DEFAULT = -1  # MSRC_TILE_DEFAULT: the process default tile configuration
 
 
 class RoomDesc(ctypes.Structure):
@@ -75,6 +76,9 @@ SIGNATURES = [
     ("msrc_workspace_size", _I32, [ctypes.POINTER(_P), _I32, _I64P, _I64P, _SZP, _SZP]),
     ("msrc_synthesize", _I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P), _I64P, ctypes.POINTER(_P),
                                _I64P, _P, ctypes.c_size_t, _P]),
+    ("msrc_workspace_size_cfg", _I32, [ctypes.POINTER(_P), _I32, _I64P, _I64P, _I32, _SZP, _SZP]),
+    ("msrc_synthesize_cfg", _I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P), _I64P, ctypes.POINTER(_P),
+                                   _I64P, _I32, _P, ctypes.c_size_t, _P]),
     ("msrc_synthesize_host", _I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P), _I64P,
                                     ctypes.POINTER(_P), _I64P, _P, ctypes.c_size_t, _P]),
     ("msrc_host_io_bytes", _I32, [ctypes.POINTER(_P), _I32, _I64P, _I64P, _SZP]),
@@ -86,13 +90,17 @@ SIGNATURES = [
     ("msrc_measure_alu_peaks", _I32, [_P, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("msrc_room_image_count", _I32, [_P, _I64P, _I64P]),
     ("msrc_room_fit_error", _I32, [_P, ctypes.POINTER(ctypes.c_double)]),
+    ("msrc_room_farrow_table", _I32, [_P, _I32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_I32)]),
     ("msrc_set_tile_config", _I32, [_I32]),
     ("msrc_tile_configs", _I32, []),
     ("msrc_profile_enable", _I32, [_I32]),
     ("msrc_profile_read", _I32, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     ("msrc_synthesize_noalloc", _I32, [_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P]),
+    ("msrc_noalloc_errors", _I32, [_P, ctypes.POINTER(ctypes.c_uint32)]),
     ("msrc_batch_create", _I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P), _I64P, ctypes.POINTER(_P),
                                  _I64P, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    ("msrc_batch_create_cfg", _I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P), _I64P, ctypes.POINTER(_P),
+                                     _I64P, _I32, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
     ("msrc_batch_run", _I32, [_P, _I32, _P]),
     ("msrc_batch_destroy", _I32, [_P]),
     ("msrc_autotune", _I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P), _I64P, ctypes.POINTER(_P), _I64P,

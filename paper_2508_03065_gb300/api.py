@@ -162,6 +162,18 @@ class Room:
         _lib.check(lib.msrc_room_fit_error(self._h, ctypes.byref(e)))
         return float(e.value)
 
+    def farrow_table(self, which: int = 0) -> np.ndarray:
+        """The Farrow table the kernels use, shape (4 segments, P powers, taps):
+        h(k; alpha) = sum_q table[s, q, k + L/2] w^q with s = floor(4 alpha),
+        w = 4 alpha - s - 1/2 (which 0: synthesis, P = 5; 1: gradient, P = 6)."""
+        lib = _lib.load()
+        L = int(self._desc.taps)
+        out = np.zeros(4 * 6 * L, np.float32)
+        P = ctypes.c_int32()
+        _lib.check(lib.msrc_room_farrow_table(self._h, int(which), out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                              ctypes.byref(P)))
+        return out[:4 * P.value * L].reshape(4, P.value, L).copy()
+
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and _lib._lib is not None:
@@ -193,20 +205,29 @@ def _workspace(device) -> Workspace:
     return _default_ws[key]
 
 
-def workspace_size(rooms: Sequence[Room], n_in: Sequence[int], n_out: Sequence[int], backward: bool = False):
-    """(forward bytes, reverse-mode bytes or 0 unless `backward`)."""
+def _cfg(tile_config: Optional[int]) -> int:
+    return _lib.TILE_DEFAULT if tile_config is None else int(tile_config)
+
+
+def workspace_size(rooms: Sequence[Room], n_in: Sequence[int], n_out: Sequence[int], backward: bool = False,
+                   tile_config: Optional[int] = None):
+    """(forward bytes in the tile configuration `tile_config` (None = the
+    process default), reverse-mode bytes or 0 unless `backward`)."""
     lib = _lib.load()
     hs = _lib.ptr_array([r.handle.value for r in rooms])
     fwd, bwd = ctypes.c_size_t(), ctypes.c_size_t()
-    _lib.check(lib.msrc_workspace_size(hs, len(rooms), _lib.i64_array(n_in), _lib.i64_array(n_out),
-                                       ctypes.byref(fwd), ctypes.byref(bwd) if backward else None))
+    _lib.check(lib.msrc_workspace_size_cfg(hs, len(rooms), _lib.i64_array(n_in), _lib.i64_array(n_out),
+                                           _cfg(tile_config), ctypes.byref(fwd),
+                                           ctypes.byref(bwd) if backward else None))
     return int(fwd.value), int(bwd.value)
 
 
 def synthesize(rooms: Sequence[Room], xs: Sequence[torch.Tensor], n_out: Optional[Sequence[int]] = None,
                out: Optional[Sequence[torch.Tensor]] = None, workspace: Optional[Workspace] = None,
-               stream: Optional[torch.cuda.Stream] = None) -> List[torch.Tensor]:
-    """Forward synthesis (Eq. 8) of every room; returns (n_mics, n_out) float32 tensors."""
+               stream: Optional[torch.cuda.Stream] = None, tile_config: Optional[int] = None) -> List[torch.Tensor]:
+    """Forward synthesis (Eq. 8) of every room; returns (n_mics, n_out) float32
+    tensors. tile_config: a synthesis tile configuration for this call (e.g.
+    autotune's pick), None = the process default."""
     lib = _lib.load()
     if len(rooms) != len(xs) or len(rooms) == 0:
         raise ValueError("need one signal per room")
@@ -220,13 +241,13 @@ def synthesize(rooms: Sequence[Room], xs: Sequence[torch.Tensor], n_out: Optiona
     if out is None:
         out = [torch.empty((r.n_mics, no), dtype=torch.float32, device=dev) for r, no in zip(rooms, n_out)]
     ws = workspace or _workspace(dev)
-    fwd, _ = workspace_size(rooms, n_in, n_out)
+    fwd, _ = workspace_size(rooms, n_in, n_out, tile_config=tile_config)
     buf = ws.get(fwd)
     hs = _lib.ptr_array([r.handle.value for r in rooms])
-    _lib.check(lib.msrc_synthesize(hs, len(rooms), _lib.ptr_array([x.data_ptr() for x in xs]),
-                                   _lib.i64_array(n_in), _lib.ptr_array([y.data_ptr() for y in out]),
-                                   _lib.i64_array(n_out), ctypes.c_void_p(buf.data_ptr()),
-                                   buf.numel(), _stream_handle(stream)))
+    _lib.check(lib.msrc_synthesize_cfg(hs, len(rooms), _lib.ptr_array([x.data_ptr() for x in xs]),
+                                       _lib.i64_array(n_in), _lib.ptr_array([y.data_ptr() for y in out]),
+                                       _lib.i64_array(n_out), _cfg(tile_config), ctypes.c_void_p(buf.data_ptr()),
+                                       buf.numel(), _stream_handle(stream)))
     return list(out)
 
 
@@ -273,6 +294,7 @@ def measure_alu_peaks(stream: Optional[torch.cuda.Stream] = None):
 
 
 def set_tile_config(cfg: int) -> None:
+    """Sets the process default tile configuration (calls with tile_config=None)."""
     _lib.check(_lib.load().msrc_set_tile_config(int(cfg)))
 
 
@@ -359,10 +381,11 @@ def synthesize_ad(room: Room, x: torch.Tensor, params: torch.Tensor, beta: torch
 class Batch:
     """A planned batched synthesis (msrc_batch_*): descriptors uploaded once,
     kernels only per run, optionally replayed from a captured CUDA graph.
-    Signals and outputs are bound at creation."""
+    Signals and outputs are bound at creation; tile_config (None = the
+    process default) is frozen then too."""
 
     def __init__(self, rooms: Sequence[Room], xs: Sequence[torch.Tensor], n_out: Optional[Sequence[int]] = None,
-                 stream: Optional[torch.cuda.Stream] = None):
+                 stream: Optional[torch.cuda.Stream] = None, tile_config: Optional[int] = None):
         lib = _lib.load()
         self.rooms = list(rooms)
         self.xs = [x.contiguous() for x in xs]
@@ -371,16 +394,18 @@ class Batch:
         dev = self.xs[0].device
         self.ys = [torch.empty((r.n_mics, no), dtype=torch.float32, device=dev)
                    for r, no in zip(self.rooms, self.n_out)]
-        fwd, _ = workspace_size(self.rooms, self.n_in, self.n_out)
+        fwd, _ = workspace_size(self.rooms, self.n_in, self.n_out, tile_config=tile_config)
         self.ws = torch.empty(fwd, dtype=torch.uint8, device=dev)
         self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
         self.stream.wait_stream(torch.cuda.current_stream(dev))
         h = ctypes.c_void_p()
         hs = _lib.ptr_array([r.handle.value for r in self.rooms])
-        _lib.check(lib.msrc_batch_create(hs, len(self.rooms), _lib.ptr_array([x.data_ptr() for x in self.xs]),
-                                         _lib.i64_array(self.n_in), _lib.ptr_array([y.data_ptr() for y in self.ys]),
-                                         _lib.i64_array(self.n_out), ctypes.c_void_p(self.ws.data_ptr()),
-                                         self.ws.numel(), _stream_handle(self.stream), ctypes.byref(h)))
+        _lib.check(lib.msrc_batch_create_cfg(hs, len(self.rooms), _lib.ptr_array([x.data_ptr() for x in self.xs]),
+                                             _lib.i64_array(self.n_in),
+                                             _lib.ptr_array([y.data_ptr() for y in self.ys]),
+                                             _lib.i64_array(self.n_out), _cfg(tile_config),
+                                             ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                             _stream_handle(self.stream), ctypes.byref(h)))
         self._h = h
 
     def run(self, use_graph: bool = True) -> List[torch.Tensor]:
@@ -400,9 +425,10 @@ class Batch:
 
 def autotune(rooms: Sequence[Room], xs: Sequence[torch.Tensor], n_out: Optional[Sequence[int]] = None,
              reps: int = 3, cache_path: Optional[str] = None, stream: Optional[torch.cuda.Stream] = None) -> int:
-    """Selects the fastest synthesis tile configuration for this workload and
-    caches the choice in a JSON file (MSRC_AUTOTUNE_CACHE, else
-    ~/.cache/msrc_autotune.json) keyed by GPU and workload shape."""
+    """The fastest synthesis tile configuration for this workload (pass it as
+    tile_config to synthesize / Batch), cached in a JSON file
+    (MSRC_AUTOTUNE_CACHE, else ~/.cache/msrc_autotune.json) keyed by GPU and
+    workload shape. The process default is left as it is."""
     import json
     import os
 
@@ -427,14 +453,11 @@ def autotune(rooms: Sequence[Room], xs: Sequence[torch.Tensor], n_out: Optional[
         except (OSError, ValueError):
             cache = {}
     if key in cache:
-        set_tile_config(int(cache[key]["best"]))
         return int(cache[key]["best"])
     ys = [torch.empty((r.n_mics, no), dtype=torch.float32, device=dev) for r, no in zip(rooms, n_out)]
     need = 0
-    saved = None
     for c in range(tile_configs()):
-        set_tile_config(c)
-        need = max(need, workspace_size(rooms, n_in, n_out)[0])
+        need = max(need, workspace_size(rooms, n_in, n_out, tile_config=c)[0])
     ws = _workspace(dev).get(need)
     ms = (ctypes.c_double * tile_configs())()
     best = ctypes.c_int32()
@@ -450,5 +473,4 @@ def autotune(rooms: Sequence[Room], xs: Sequence[torch.Tensor], n_out: Optional[
             json.dump(cache, f, indent=1)
     except OSError:
         pass
-    del saved
     return int(best.value)

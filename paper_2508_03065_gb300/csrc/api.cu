@@ -1,6 +1,7 @@
 // Host side of the msrc C ABI: validation, Farrow coefficient fit, workspace
 // planning and launch sequencing. See include/msrc.h for the contract.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -56,8 +57,13 @@ struct msrc_room {
 
 namespace {
 
-int g_tile_config = 0;
+// Tile configuration of calls that name none (MSRC_TILE_DEFAULT): the process
+// default set by msrc_set_tile_config.
+std::atomic<int> g_tile_config{0};
 uint32_t g_test_extra_tx = 0;  // msrc_test_stall_window_copies
+
+// The configuration a call runs in: its own, or the process default.
+int call_config(int32_t tile_config) { return tile_config < 0 ? g_tile_config.load() : tile_config; }
 
 // Optional per-phase timing with CUDA events recorded on the launching stream.
 // Phases: 0 setup (images, sort, knots, records), 1 prefilter, 2 synthesis, 3 reduction.
@@ -433,13 +439,14 @@ struct Plan {
   std::vector<SceneDev> scenes;
   std::vector<int64_t> prefix[kUnitKinds];
   int64_t totals[kUnitKinds] = {0, 0, 0, 0, 0, 0, 0, 0};
-  int end_bit = 40;
+  int end_bit = kSortGroupShift;
   // byte offsets in the workspace
   size_t off_desc = 0, off_keys_in = 0, off_keys_out = 0, off_vals_in = 0, off_vals_out = 0;
   size_t off_sort = 0, sort_bytes = 0, off_code = 0, off_gain = 0, off_knots = 0;
-  size_t off_z = 0, off_zp = 0, off_part = 0, fwd_bytes = 0, desc_bytes = 0, off_arr = 0;
+  size_t off_z = 0, off_zp = 0, off_part = 0, fwd_bytes = 0, desc_bytes = 0, off_arr = 0, off_xmax = 0;
   // reverse mode
   bool backward = false;
+  int cfg = 0;                      // forward tile configuration
   int64_t dxb_floats = 0;
   size_t off_dxb = 0, off_kslot = 0, off_bpart = 0, off_gk = 0, off_ppart = 0, off_bwt = 0, off_trange = 0;
   int kL = 32;
@@ -451,21 +458,34 @@ struct Plan {
   std::vector<double> upw_l1;     // its largest absolute row sum
   size_t off_upw = 0, off_bl_tau = 0, off_dense_hi = 0, off_dense_lo = 0, off_knot_hl = 0,
          off_arr_hl = 0;
+  // time groups of the forward image order: source position and array
+  // displacement at every group's middle (6 doubles each, written by the setup
+  // kernels at off_gpos)
+  size_t off_gpos = 0;
+  int64_t n_sort_groups = 0;
+  int max_groups = 1;
 };
+
+// Output samples per time group of the forward image order (rounded to whole
+// tiles): short enough that a block's images stay close in delay over the
+// group, long enough that the extra copies of the image table stay cheap.
+constexpr int64_t kTimeGroupSamples = 12288;
 
 // Workspace layout and per-scene descriptors of one call. Forward mode uses
 // the selected synthesis tile configuration; reverse mode its own (one sample
 // per thread) and adds the gradient buffers.
 msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, const int64_t* n_out,
-                      Plan& P, bool backward = false) {
+                      Plan& P, bool backward = false, int cfg = 0) {
   if (!rooms || n <= 0 || !n_in || !n_out)
     return fail(MSRC_ERR_INVALID_ARG, "null rooms/lengths or n_rooms <= 0");
   P.backward = backward;
-  const TileConfig& tc = backward ? backward_tile_config() : tile_config(g_tile_config);
+  if (cfg < 0 || cfg >= tile_config_count()) return fail(MSRC_ERR_INVALID_ARG, "tile configuration %d out of range", cfg);
+  P.cfg = cfg;
+  const TileConfig& tc = backward ? backward_tile_config() : tile_config(cfg);
   const int T = tc.threads * tc.chunks;
   P.scenes.resize(n);
   for (auto& v : P.prefix) v.assign(n + 1, 0);
-  int64_t img_acc = 0, knot_acc = 0, z_acc = 0, part_acc = 0;
+  int64_t img_acc = 0, knot_acc = 0, z_acc = 0, part_acc = 0, group_acc = 0;
   int64_t dxb_acc = 0, kslot_acc = 0, bpart_acc = 0, bl_acc = 0, dense_acc = 0;
   bool any_moving = false;
   for (int s = 0; s < n; ++s) {
@@ -548,21 +568,24 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
       S.tier_intervals[t] = J;
       // images per block: the item's records (one per image and knot interval
       // touching the tile) must fit the shared record capacity
+      // (the forward synthesis stores them for image pairs: an even count)
       const int rec_per_image = (T - 1) / N + 2;
-      if (rec_per_image > tc.reccap)
+      if ((backward ? 1 : 2) * rec_per_image > tc.reccap)
         return fail(MSRC_ERR_UNSUPPORTED, "tile configuration too small for knot spacing %d", N);
       int B = std::max(1, std::min(tc.block, tc.reccap / rec_per_image));
       if (backward) B = std::max(1, std::min(B, int(backward_unit_cap()) / (rec_per_image + 1)));
+      else if (B > 1) B &= ~1;
       int64_t n_knots = J + 1;
       if (bl) {
-        // the upsampler's scratch shares the shared z window (5 rows per segment)
+        // the upsampler's scratch shares the shared z window (4 floats per column and segment)
         const int nk = rec_per_image + 1;
         const int nj = (nk - 1) / U + 2;
         const int64_t per = bl_scratch_floats(1, nk, nj, Q);
-        const int64_t cap = int64_t(kFarrowSegs) * tc.wcap * 5;
+        const int64_t cap = int64_t(kFarrowSegs) * tc.wcap * 4;
         if (per > cap)
           return fail(MSRC_ERR_UNSUPPORTED, "tile configuration too small for the upsampling of tier %d", t);
         B = std::min<int64_t>(B, cap / per);
+        if (B > 1) B &= ~1;
         const int key = U * 64 + Q;
         size_t k = 0;
         while (k < P.upw_key.size() && P.upw_key[k] != key) ++k;
@@ -597,6 +620,21 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     }
     S.n_blocks = blk;
     S.img_base = img_acc;
+    // time groups: one per kTimeGroupSamples of output in forward mode; one
+    // (ordered at the middle of the trajectory) in reverse mode and when a
+    // tier is upsampled (its knot-delay rows follow the first group's order)
+    {
+      bool any_bl = false;
+      for (int t = 0; t < S.n_tiers; ++t) any_bl = any_bl || S.tier_up[t] > 1;
+      const int tg = int(std::max<int64_t>(1, kTimeGroupSamples / T));
+      const bool grouped = !backward && !any_bl && S.n_tiles > tg;
+      S.tile_group = grouped ? tg : S.n_tiles;
+      S.n_time_groups = grouped ? (S.n_tiles + tg - 1) / tg : 1;
+      S.sort_group0 = group_acc;
+      S.gpos_base = group_acc;
+      group_acc += S.n_time_groups;
+      P.max_groups = std::max(P.max_groups, S.n_time_groups);
+    }
     if (backward) {
       int groups = 0;
       for (int t = 0; t < S.n_tiers; ++t) {
@@ -675,7 +713,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     if (backward && !(R->max_speed < 0.5 * R->d.c))
       return fail(MSRC_ERR_UNSUPPORTED, "room %d: reverse mode needs source speed below c/2", s);
 
-    const int64_t u_enum = S.n_images;
+    const int64_t u_enum = int64_t(S.n_time_groups) * S.n_images;
     const int64_t u_knots = kfirst;
     const int64_t u_rec = backward ? S.n_in : 0;  // reverse mode: dx samples
     const int64_t u_z = (S.z_len + 255) / 256;
@@ -691,15 +729,17 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
       P.prefix[k][s + 1] = P.prefix[k][s] + u[k];
       P.totals[k] += u[k];
     }
-    img_acc += S.n_images;
+    img_acc += u_enum;
     knot_acc += kfirst;
     z_acc += int64_t(kFarrowSegs) * S.z_len;
     part_acc += int64_t(S.n_mics) * S.n_blocks * S.n_out;
   }
   P.taps = rooms[0]->d.taps;
   P.kL = rooms[0]->kL;
-  P.end_bit = 40;
-  while ((int64_t(1) << (P.end_bit - 40)) < n) ++P.end_bit;
+  P.n_sort_groups = group_acc;
+  P.end_bit = kSortGroupShift;
+  while ((int64_t(1) << (P.end_bit - kSortGroupShift)) < group_acc) ++P.end_bit;
+  if (P.end_bit > 64) return fail(MSRC_ERR_UNSUPPORTED, "too many time groups in one call");
   // workspace layout
   size_t off = 256;  // error word + work counter
   P.desc_bytes = (n > 1) ? n * sizeof(SceneDev) + kUnitKinds * (n + 1) * sizeof(int64_t) : 0;
@@ -718,14 +758,16 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.off_knot_hl = off; off = align256(off + 32 * size_t(knot_acc));
   P.off_arr_hl = off; off = align256(off + (any_moving ? 32 * size_t(knot_acc) : 0));
   P.off_upw = off; off = align256(off + 4 * P.upw.size());
+  P.off_gpos = off; off = align256(off + 48 * size_t(group_acc));
   P.off_bl_tau = off; off = align256(off + 8 * size_t(bl_acc));
   P.off_dense_hi = off; off = align256(off + 16 * size_t(dense_acc));
   P.off_dense_lo = off; off = align256(off + 16 * size_t(dense_acc));
   P.off_z = off; off = align256(off + 16 * size_t(z_acc));
-  // forward: power 4 of the degree-4 rows; reverse mode: powers 4..5 of the
-  // degree-5 rows the gradient kernel reads (zq holds powers 0..3 either way)
+  // reverse mode: powers 4..5 of the degree-5 rows the gradient kernel reads
+  // (zq holds its powers 0..3; the forward rows are whole in zq)
   // (+64 B: a bulk copy of a row's last columns may read up to 12 B past it)
-  P.off_zp = off; off = align256(off + (backward ? 8 : 4) * size_t(z_acc) + 64);
+  P.off_zp = off; off = align256(off + (backward ? 8 * size_t(z_acc) + 64 : 0));
+  P.off_xmax = off; off = align256(off + 4 * size_t(n));
   if (!backward) {
     P.off_part = off; off = align256(off + 4 * size_t(part_acc));
   } else {
@@ -764,11 +806,14 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.knot_hl = reinterpret_cast<float4*>(ws + P.off_knot_hl);
   a.p.arr_hl = reinterpret_cast<float4*>(ws + P.off_arr_hl);
   a.p.upw = reinterpret_cast<const float*>(ws + P.off_upw);
+  a.p.gpos = reinterpret_cast<double*>(ws + P.off_gpos);
+  a.n_sort_groups = P.n_sort_groups;
+  a.max_time_groups = P.max_groups;
   a.p.bl_tau = reinterpret_cast<float2*>(ws + P.off_bl_tau);
   a.p.dense_hi = reinterpret_cast<float4*>(ws + P.off_dense_hi);
   a.p.dense_lo = reinterpret_cast<float4*>(ws + P.off_dense_lo);
   a.p.zq = reinterpret_cast<float4*>(ws + P.off_z);
-  a.p.zp = P.backward ? nullptr : reinterpret_cast<float*>(ws + P.off_zp);
+  a.p.xmax = reinterpret_cast<uint32_t*>(ws + P.off_xmax);
   a.p.zg = P.backward ? reinterpret_cast<float2*>(ws + P.off_zp) : nullptr;
   a.p.part = reinterpret_cast<float*>(ws + P.off_part);
   if (P.backward) {
@@ -788,6 +833,15 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   for (int sg = 0; sg < kFarrowSegs; ++sg)
     for (int q = 0; q < kGradCoef; ++q)
       for (int k = 0; k < kMaxTaps; ++k) a.farrow_g[sg][q][k] = std::ldexp(rooms[0]->farrow_g[sg][q][k], q);
+  // bound of |z_3|, |z_4| per unit max |x| (the half-precision scale)
+  double zg = 0.0;
+  for (int sg = 0; sg < kFarrowSegs; ++sg)
+    for (int q = 3; q <= 4; ++q) {
+      double l1 = 0.0;
+      for (int k = 0; k < kMaxTaps; ++k) l1 += std::fabs(double(a.farrow[sg][q][k]));
+      zg = std::max(zg, l1);
+    }
+  a.zh_gain = float(zg * (1.0 + 1e-6));
   a.taps = P.kL;
   if (a.n_scenes > 1) {
     char* d = ws + P.off_desc;
@@ -836,10 +890,10 @@ msrc_status upload_tables(const Plan& P, char* ws, cudaStream_t st, std::vector<
 
 msrc_status run_forward(const msrc_room_t* rooms, int32_t n, const float* const* x_dev,
                         const int64_t* n_in, float* const* y_dev, const int64_t* n_out,
-                        void* ws, size_t ws_bytes, cudaStream_t st) {
+                        void* ws, size_t ws_bytes, cudaStream_t st, int cfg) {
   if (!x_dev || !y_dev) return fail(MSRC_ERR_INVALID_ARG, "null signal pointer array");
   Plan P;
-  msrc_status s = make_plan(rooms, n, n_in, n_out, P);
+  msrc_status s = make_plan(rooms, n, n_in, n_out, P, false, cfg);
   if (s != MSRC_OK) return s;
   s = check_ws(P, ws, ws_bytes);
   if (s != MSRC_OK) return s;
@@ -868,7 +922,7 @@ msrc_status run_forward(const msrc_room_t* rooms, int32_t n, const float* const*
   }
   e = launch_setup(*a, st);
   if (ev) cudaEventRecord(ev[1], st);
-  if (e == cudaSuccess) e = launch_forward(*a, g_tile_config, st, ev ? ev + 2 : nullptr);
+  if (e == cudaSuccess) e = launch_forward(*a, P.cfg, st, ev ? ev + 2 : nullptr);
   if (ev) cudaEventRecord(ev[4], st);
   delete a;
   if (e != cudaSuccess) return cuda_fail(e, "synthesis launch");
@@ -1242,8 +1296,14 @@ msrc_status msrc_set_reflection(msrc_room_t room, const double* beta) {
 
 msrc_status msrc_workspace_size(const msrc_room_t* rooms, int32_t n_rooms, const int64_t* n_in,
                                 const int64_t* n_out, size_t* fwd_bytes, size_t* bwd_bytes) {
+  return msrc_workspace_size_cfg(rooms, n_rooms, n_in, n_out, MSRC_TILE_DEFAULT, fwd_bytes, bwd_bytes);
+}
+
+msrc_status msrc_workspace_size_cfg(const msrc_room_t* rooms, int32_t n_rooms, const int64_t* n_in,
+                                    const int64_t* n_out, int32_t tile_config, size_t* fwd_bytes,
+                                    size_t* bwd_bytes) {
   Plan P;
-  msrc_status s = make_plan(rooms, n_rooms, n_in, n_out, P);
+  msrc_status s = make_plan(rooms, n_rooms, n_in, n_out, P, false, call_config(tile_config));
   if (s != MSRC_OK) return s;
   if (fwd_bytes) *fwd_bytes = P.fwd_bytes;
   if (bwd_bytes) {
@@ -1259,7 +1319,14 @@ msrc_status msrc_synthesize(const msrc_room_t* rooms, int32_t n_rooms, const flo
                             const int64_t* n_in, float* const* y_dev, const int64_t* n_out,
                             void* ws, size_t ws_bytes, void* stream) {
   return run_forward(rooms, n_rooms, x_dev, n_in, y_dev, n_out, ws, ws_bytes,
-                     static_cast<cudaStream_t>(stream));
+                     static_cast<cudaStream_t>(stream), call_config(MSRC_TILE_DEFAULT));
+}
+
+msrc_status msrc_synthesize_cfg(const msrc_room_t* rooms, int32_t n_rooms, const float* const* x_dev,
+                                const int64_t* n_in, float* const* y_dev, const int64_t* n_out,
+                                int32_t tile_config, void* ws, size_t ws_bytes, void* stream) {
+  return run_forward(rooms, n_rooms, x_dev, n_in, y_dev, n_out, ws, ws_bytes,
+                     static_cast<cudaStream_t>(stream), call_config(tile_config));
 }
 
 msrc_status msrc_host_io_bytes(const msrc_room_t* rooms, int32_t n_rooms, const int64_t* n_in,
@@ -1278,8 +1345,9 @@ msrc_status msrc_synthesize_host(const msrc_room_t* rooms, int32_t n_rooms, cons
                                  const int64_t* n_in, float* const* y_host, const int64_t* n_out,
                                  void* ws, size_t ws_bytes, void* stream) {
   if (!x_host || !y_host) return fail(MSRC_ERR_INVALID_ARG, "null host signal array");
+  const int cfg = call_config(MSRC_TILE_DEFAULT);
   Plan P;
-  msrc_status s = make_plan(rooms, n_rooms, n_in, n_out, P);
+  msrc_status s = make_plan(rooms, n_rooms, n_in, n_out, P, false, cfg);
   if (s != MSRC_OK) return s;
   size_t io = 0;
   s = msrc_host_io_bytes(rooms, n_rooms, n_in, n_out, &io);
@@ -1302,7 +1370,7 @@ msrc_status msrc_synthesize_host(const msrc_room_t* rooms, int32_t n_rooms, cons
     xd[r] = xdev;
     yd[r] = ydev;
   }
-  s = run_forward(rooms, n_rooms, xd.data(), n_in, yd.data(), n_out, ws, P.fwd_bytes, st);
+  s = run_forward(rooms, n_rooms, xd.data(), n_in, yd.data(), n_out, ws, P.fwd_bytes, st, cfg);
   if (s != MSRC_OK) return s;
   for (int r = 0; r < n_rooms; ++r) {
     cudaError_t e = cudaMemcpyAsync(y_host[r], yd[r], 4 * size_t(n_out[r]) * size_t(rooms[r]->n_mics),
@@ -1372,11 +1440,18 @@ extern "C" {
 msrc_status msrc_batch_create(const msrc_room_t* rooms, int32_t n, const float* const* x_dev,
                               const int64_t* n_in, float* const* y_dev, const int64_t* n_out, void* ws,
                               size_t ws_bytes, void* stream, msrc_batch_t* out) {
+  return msrc_batch_create_cfg(rooms, n, x_dev, n_in, y_dev, n_out, MSRC_TILE_DEFAULT, ws, ws_bytes, stream, out);
+}
+
+msrc_status msrc_batch_create_cfg(const msrc_room_t* rooms, int32_t n, const float* const* x_dev,
+                                  const int64_t* n_in, float* const* y_dev, const int64_t* n_out,
+                                  int32_t tile_config, void* ws, size_t ws_bytes, void* stream,
+                                  msrc_batch_t* out) {
   if (!out || !x_dev || !y_dev) return fail(MSRC_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   msrc_batch* b = new (std::nothrow) msrc_batch;
   if (!b) return fail(MSRC_ERR_INVALID_ARG, "out of host memory");
-  msrc_status s = make_plan(rooms, n, n_in, n_out, b->P);
+  msrc_status s = make_plan(rooms, n, n_in, n_out, b->P, false, call_config(tile_config));
   if (s == MSRC_OK) s = check_ws(b->P, ws, ws_bytes);
   if (s != MSRC_OK) { delete b; return s; }
   for (int r = 0; r < n; ++r) {
@@ -1387,7 +1462,7 @@ msrc_status msrc_batch_create(const msrc_room_t* rooms, int32_t n, const float* 
   b->a = new (std::nothrow) KernelArgs;
   if (!b->a) { delete b; return fail(MSRC_ERR_INVALID_ARG, "out of host memory"); }
   b->ws = static_cast<char*>(ws);
-  b->cfg = g_tile_config;
+  b->cfg = b->P.cfg;
   fill_args(b->P, rooms, b->ws, *b->a);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   std::vector<char> blob;
@@ -1444,7 +1519,6 @@ msrc_status msrc_autotune(const msrc_room_t* rooms, int32_t n, const float* cons
                           int32_t reps, double* ms, int32_t* best) {
   if (!ms || !best || reps < 1) return fail(MSRC_ERR_INVALID_ARG, "null output or reps < 1");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int saved = g_tile_config;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(MSRC_ERR_CUDA, "event creation");
@@ -1453,14 +1527,13 @@ msrc_status msrc_autotune(const msrc_room_t* rooms, int32_t n, const float* cons
   msrc_status result = MSRC_OK;
   for (int c = 0; c < tile_config_count(); ++c) {
     ms[c] = -1.0;
-    g_tile_config = c;
     Plan P;
-    if (make_plan(rooms, n, n_in, n_out, P) != MSRC_OK || P.fwd_bytes > ws_bytes) continue;
-    msrc_status s = msrc_synthesize(rooms, n, x_dev, n_in, y_dev, n_out, ws, ws_bytes, stream);
+    if (make_plan(rooms, n, n_in, n_out, P, false, c) != MSRC_OK || P.fwd_bytes > ws_bytes) continue;
+    msrc_status s = msrc_synthesize_cfg(rooms, n, x_dev, n_in, y_dev, n_out, c, ws, ws_bytes, stream);
     if (s != MSRC_OK) { result = s; break; }
     cudaEventRecord(e0, st);
     for (int r = 0; r < reps && s == MSRC_OK; ++r)
-      s = msrc_synthesize(rooms, n, x_dev, n_in, y_dev, n_out, ws, ws_bytes, stream);
+      s = msrc_synthesize_cfg(rooms, n, x_dev, n_in, y_dev, n_out, c, ws, ws_bytes, stream);
     cudaEventRecord(e1, st);
     if (s != MSRC_OK) { result = s; break; }
     if (cudaEventSynchronize(e1) != cudaSuccess) { result = fail(MSRC_ERR_CUDA, "event synchronize"); break; }
@@ -1471,8 +1544,7 @@ msrc_status msrc_autotune(const msrc_room_t* rooms, int32_t n, const float* cons
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  g_tile_config = pick >= 0 ? pick : saved;
-  *best = g_tile_config;
+  *best = pick;
   if (result != MSRC_OK) return result;
   if (pick < 0) return fail(MSRC_ERR_WORKSPACE, "no tile configuration fits the workspace");
   return MSRC_OK;
@@ -1501,6 +1573,23 @@ msrc_status msrc_room_image_count(msrc_room_t room, int64_t* count, int64_t* per
 msrc_status msrc_room_fit_error(msrc_room_t room, double* err) {
   if (!room || !err) return fail(MSRC_ERR_INVALID_ARG, "null argument");
   *err = room->fit_error;
+  return MSRC_OK;
+}
+
+msrc_status msrc_room_farrow_table(msrc_room_t room, int32_t which, float* out, int32_t* n_powers) {
+  if (!room || !out || !n_powers) return fail(MSRC_ERR_INVALID_ARG, "null argument");
+  if (which != 0 && which != 1) return fail(MSRC_ERR_INVALID_ARG, "which must be 0 (synthesis) or 1 (gradient)");
+  const int P = which == 0 ? kFarrowCoef : kGradCoef;
+  const int L = room->d.taps, kL = room->kL;
+  // the values the kernels receive: coefficients of the powers of w = v / 2
+  // (c_q 2^q, an exact rescaling of the fit in v)
+  for (int sg = 0; sg < kFarrowSegs; ++sg)
+    for (int q = 0; q < P; ++q)
+      for (int k = -L / 2; k < L / 2; ++k) {
+        const float c = which == 0 ? room->farrow[sg][q][k + kL / 2] : room->farrow_g[sg][q][k + kL / 2];
+        out[(size_t(sg) * P + q) * L + (k + L / 2)] = std::ldexp(c, q);
+      }
+  *n_powers = P;
   return MSRC_OK;
 }
 
@@ -1551,7 +1640,7 @@ msrc_status msrc_test_stall_window_copies(uint32_t bytes) {
 
 msrc_status msrc_set_tile_config(int32_t id) {
   if (id < 0 || id >= tile_config_count()) return fail(MSRC_ERR_INVALID_ARG, "tile config %d out of range", id);
-  g_tile_config = id;
+  g_tile_config.store(id);
   return MSRC_OK;
 }
 

@@ -853,18 +853,11 @@ __global__ void __launch_bounds__(kBetaThreads) k_beta_final(const __grid_consta
 
 template <typename K>
 cudaError_t persistent_launch(K kern, size_t smem, int64_t items, const KernelArgs& a, cudaStream_t st,
-                              int* grid) {
-  if (*grid == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBwThreads, smem);
-    if (e != cudaSuccess) return e;
-    *grid = sms * (occ > 0 ? occ : 1);
-  }
-  const int g = int(items < *grid ? items : *grid);
+                              PerDevice* setup) {
+  int grid = 0;
+  cudaError_t pe = persistent_grid(*setup, kern, kBwThreads, smem, &grid);
+  if (pe != cudaSuccess) return pe;
+  const int g = int(items < grid ? items : grid);
   cudaError_t e = cudaMemsetAsync(a.p.counter, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   if (g > 0) kern<<<g, kBwThreads, smem, st>>>(a);
@@ -883,7 +876,8 @@ cudaError_t launch_prefilter(const KernelArgs& a, cudaStream_t st, bool gradient
 cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
   cudaError_t e = launch_prefilter(a, st, true);
   if (e != cudaSuccess) return e;
-  static int g_grad = 0, g_dx16 = 0, g_dx32 = 0, g_dx64 = 0;
+  // per device and kernel: shared-memory limit and persistent grid
+  static PerDevice g_grad, g_dx16, g_dx32, g_dx64;
   if (a.totals[0] > 0) k_beta_table<<<unsigned((a.totals[0] + 255) / 256), 256, 0, st>>>(a);
   e = persistent_launch(k_adj_grad, kGradSmem, a.totals[4], a, st, &g_grad);
   if (e != cudaSuccess) return e;
@@ -899,12 +893,20 @@ cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
     k_knot_final<<<unsigned((a.totals[1] + kKnotsPerCta - 1) / kKnotsPerCta), kKnotsPerCta * kKnotLanes, 0, st>>>(a);
   {
     constexpr size_t smem = 48 * kParamThreads * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-      e = cudaFuncSetAttribute(k_param_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    static PerDevice attr;  // the shared-memory limit, once per device
+    int dev = 0, done = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaError_t ae = cudaSuccess;
+    const int st_attr = attr.get(
+        dev,
+        [&](int* v) {
+          ae = cudaFuncSetAttribute(k_param_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+          *v = 1;
+          return ae == cudaSuccess ? 0 : 1;
+        },
+        &done);
+    if (st_attr != 0) return ae != cudaSuccess ? ae : cudaErrorInvalidDevice;
     k_param_partial<<<unsigned(a.n_scenes * kParamChunks), kParamThreads, smem, st>>>(a);
     k_param_final<<<unsigned(a.n_scenes), 64, 0, st>>>(a);
   }

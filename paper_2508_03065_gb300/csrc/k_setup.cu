@@ -1,6 +1,8 @@
 // Setup kernels of the synthesis path:
+//   k_group_pos    source position at the middle of every time group (sort keys)
 //   k_enumerate    image set of every scene (Sec. II-A, Eq. 1; lattice |n|_1 <= K,
-//                  8 parities) with a sort key (scene, tier, distance)
+//                  8 parities), one copy per time group of the scene, with a sort
+//                  key (scene and time group, tier, distance at the group's middle)
 //   (radix sort)   images ordered by key
 //   k_image_table  packed image codes and gains beta_i / (4 pi) * fs / c
 //   k_traj_knots   source position s(t_j) (and the array displacement a(t_j) - a(0)
@@ -81,14 +83,41 @@ __device__ __forceinline__ int tier_of(const SceneDev& S, int rho) {
   return S.n_tiers - 1;
 }
 
+// Source position and array displacement at the middle of every time group
+// (FP64), for the sort keys: thread x of block row y = group x of scene y.
+__global__ void k_group_pos(const __grid_constant__ KernelArgs a) {
+  const int s = blockIdx.y;
+  const int grp = blockIdx.x * blockDim.x + threadIdx.x;
+  const SceneDev& S = scene_of(a, s);
+  if (grp >= S.n_time_groups) return;
+  double tm = 0.5 * S.duration;  // one group: the middle of the trajectory
+  if (S.n_time_groups > 1) {
+    const int64_t a0 = int64_t(grp) * S.tile_group * S.tile;
+    const int64_t a1 = min(int64_t(grp + 1) * S.tile_group * S.tile, S.n_out);
+    tm = 0.5 * double(a0 + a1 - 1) / S.fs;
+  }
+  double sp[3], ad[3];
+  source_position(S, tm, sp);
+  array_displacement(S, tm, ad);
+  double* o = a.p.gpos + 6 * (S.gpos_base + grp);
+  for (int d = 0; d < 3; ++d) {
+    o[d] = sp[d];
+    o[3 + d] = ad[d];
+  }
+}
+
+// One unit per (scene, time group, image): the group's copy of the image set
+// with its sort key (group, tier, distance at the group's middle).
 __global__ void k_enumerate(const __grid_constant__ KernelArgs a) {
   const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (gid >= a.totals[0]) return;
   int64_t local;
   const int s = locate(a, a.tab.enum_prefix, gid, &local);
   const SceneDev& S = scene_of(a, s);
-  int li = int(local >> 3);
-  const int pb = int(local & 7);
+  const int64_t grp = local / S.n_images;
+  const int64_t unit = local - grp * S.n_images;  // the image within the group's copy
+  int li = int(unit >> 3);
+  const int pb = int(unit & 7);
   const int K = S.K;
   // lattice order: n_x ascending, then n_y, then n_z, over |n|_1 <= K
   int nx = -K;
@@ -111,18 +140,19 @@ __global__ void k_enumerate(const __grid_constant__ KernelArgs a) {
   int rho = 0;
   for (int d = 0; d < 3; ++d) rho += abs(2 * n[d] - p[d]);
   const int tier = tier_of(S, rho);
-  // distance to the first microphone at the middle of the trajectory
-  double sp[3], ad[3];
-  source_position(S, 0.5 * S.duration, sp);
-  array_displacement(S, 0.5 * S.duration, ad);
+  // distance to the first microphone at the middle of the time group (source
+  // position and array displacement there from the host-built table)
+  const double* gp = a.p.gpos + 6 * (S.gpos_base + grp);
   double acc = 0.0;
   for (int d = 0; d < 3; ++d) {
-    const double v = (1.0 - 2.0 * p[d]) * sp[d] + 2.0 * n[d] * S.dims[d] - (S.mics[0][d] + ad[d]);
+    const double v = (1.0 - 2.0 * p[d]) * gp[d] + 2.0 * n[d] * S.dims[d] - (S.mics[0][d] + gp[3 + d]);
     acc += v * v;
   }
-  const double dist = fmin(sqrt(acc), 4095.0);
-  const uint64_t dq = uint64_t(dist * 1048576.0);
-  a.p.keys_in[gid] = (uint64_t(s) << 40) | (uint64_t(tier) << 32) | dq;
+  // distance in 24 bits (units of 2^-12 m up to 4 km): the key only orders
+  // images, and fewer key bits are fewer radix passes
+  const double dist = fmin(sqrt(acc), 4095.99);
+  const uint64_t dq = uint64_t(dist * 4096.0);
+  a.p.keys_in[gid] = (uint64_t(S.sort_group0 + grp) << kSortGroupShift) | (uint64_t(tier) << 24) | dq;
   a.p.vals_in[gid] = pack_image(nx, ny, nz, pb);
 }
 
@@ -283,9 +313,10 @@ static inline unsigned blocks_for(int64_t n, int threads) {
 cudaError_t launch_setup(const KernelArgs& a, cudaStream_t st) {
   const int T = 256;
   if (a.totals[0] > 0) {
+    k_group_pos<<<dim3(unsigned((a.max_time_groups + 63) / 64), unsigned(a.n_scenes)), 64, 0, st>>>(a);
     k_enumerate<<<blocks_for(a.totals[0], T), T, 0, st>>>(a);
-    int end_bit = 40;
-    while ((int64_t(1) << (end_bit - 40)) < a.n_scenes) ++end_bit;
+    int end_bit = kSortGroupShift;
+    while ((int64_t(1) << (end_bit - kSortGroupShift)) < a.n_sort_groups) ++end_bit;
     cudaError_t e = launch_sort(a, a.totals[0], end_bit, st);
     if (e != cudaSuccess) return e;
     k_image_table<<<blocks_for(a.totals[0], T), T, 0, st>>>(a);

@@ -1,23 +1,31 @@
 // Forward synthesis kernels (Sec. II-B Eq. 3-5, Sec. II-C Eq. 8):
 //
+//   k_absmax     largest |x| of every scene (the scale of the half-precision
+//                powers of the prefiltered rows).
 //   k_prefilter  signal side of the Farrow structure (Eq. 5): for every
 //                segment s and power q of the tap polynomial,
-//                z[s][q][m] = sum_k c[s][q][k] x[m - k].
+//                z[s][q][m] = sum_k c[s][q][k] x[m - k], stored per column and
+//                segment as one float4 {z0, z1, z2, half2(s z3, s z4)}.
 //   k_synth      persistent gather-accumulate over a work queue of
 //                (scene, microphone, image block, output tile) items.
 //                Item prologue: the hierarchical delay knots of the block's
 //                images over the tile (Sec. II-C, "Fast Architecture") are
-//                evaluated into shared memory: one FP64 anchor distance per
-//                image, the other knots by an exact FP32 increment of the
-//                squared distance. Then the z window of the item is staged in
-//                shared memory with cp.async. Per image-sample: interpolate the
-//                delay linearly between knots, split it into read position m0
-//                and fraction alpha, evaluate e = sum_q w^q z[seg(alpha)][q][m0]
-//                by Horner and accumulate (beta_i / (4 pi d_i(n))) e. Each item
+//                evaluated into shared memory: a double-float anchor distance
+//                per image, the other knots by an exact FP32 increment of the
+//                squared distance, stored as interval records of image pairs.
+//                Then the z window of the item is staged in shared memory by
+//                bulk copies (cp.async.bulk) completing on an mbarrier. Per
+//                image-sample: interpolate the delay linearly between knots,
+//                split it into read position m0 and fraction alpha, evaluate
+//                e = sum_q w^q z[seg(alpha)][q][m0] by Horner and accumulate
+//                (beta_i / (4 pi d_i(n))) e; the delay arithmetic and the
+//                accumulation run on float2 pairs of images (FFMA2). Each item
 //                writes one partial row (no atomics).
 //   k_reduce     y[mic][n] = sum over image blocks of the partial rows, in a
 //                fixed order (bitwise reproducible).
 #include <cstdint>
+
+#include <cuda_fp16.h>
 
 #include "msrc_internal.h"
 #include "synth_common.cuh"
@@ -28,8 +36,34 @@ namespace {
 // ------------------------------------------------------------------ prefilter
 constexpr int kPreThreads = 256;
 
-// kCoef = kFarrowCoef: the synthesis rows (degree 4, zq + zp); kCoef =
-// kGradCoef: the gradient kernel's rows (degree 5, zq + zg).
+// Largest |x| of every scene (as float bits, atomicMax over the prefilter's
+// column tiles: order-independent, so reproducible); the synthesis rows' power
+// 3 and 4 values are scaled by it (zh_scale) before they are stored in half
+// precision.
+__global__ void __launch_bounds__(kPreThreads) k_absmax(const __grid_constant__ KernelArgs a) {
+  __shared__ unsigned red[kPreThreads / 32];
+  int s = 0;
+  int64_t blk = blockIdx.x;
+  if (a.n_scenes > 1) {
+    s = find_scene(a.tab.z_prefix, a.n_scenes, blk);
+    blk -= a.tab.z_prefix[s];
+  }
+  const SceneDev& S = scene_of(a, s);
+  const int64_t m = S.z_m0 + blk * kPreThreads + threadIdx.x;
+  unsigned v = (m >= 0 && m < S.n_in) ? __float_as_uint(fabsf(__ldg(S.x + m))) : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kPreThreads / 32; ++w) v = max(v, red[w]);
+    if (v) atomicMax(a.p.xmax + s, v);
+  }
+}
+
+// kCoef = kFarrowCoef: the synthesis rows (degree 4): per column and segment
+// one float4 {z0, z1, z2, (z3, z4) scaled in half precision} (zh_scale);
+// kCoef = kGradCoef: the gradient kernel's rows (degree 5, zq + zg, FP32).
 template <int kL, int kCoef>
 __global__ void __launch_bounds__(kPreThreads) k_prefilter(const __grid_constant__ KernelArgs a) {
   static_assert(kCoef == kFarrowCoef || kCoef == kGradCoef, "row sets");
@@ -68,88 +102,118 @@ __global__ void __launch_bounds__(kPreThreads) k_prefilter(const __grid_constant
     }
   }
   float4* zq = a.p.zq + S.z_base + col;
+  if constexpr (kCoef == kFarrowCoef) {
+    const float sc = zh_scale(a, s).x;
 #pragma unroll
-  for (int sg = 0; sg < kFarrowSegs; ++sg) {
-    const float* c = acc + sg * kCoef;
-    zq[int64_t(sg) * S.z_len] = make_float4(c[0], c[1], c[2], c[3]);
-    if constexpr (kCoef == kFarrowCoef) a.p.zp[S.z_base + col + int64_t(sg) * S.z_len] = c[4];
-    else a.p.zg[S.z_base + col + int64_t(sg) * S.z_len] = make_float2(c[4], c[kCoef - 1]);
+    for (int sg = 0; sg < kFarrowSegs; ++sg) {
+      const float* c = acc + sg * kCoef;
+      zq[int64_t(sg) * S.z_len] = make_float4(c[0], c[1], c[2], pack_half2(c[3] * sc, c[4] * sc));
+    }
+  } else {
+#pragma unroll
+    for (int sg = 0; sg < kFarrowSegs; ++sg) {
+      const float* c = acc + sg * kCoef;
+      zq[int64_t(sg) * S.z_len] = make_float4(c[0], c[1], c[2], c[3]);
+      a.p.zg[S.z_base + col + int64_t(sg) * S.z_len] = make_float2(c[4], c[kCoef - 1]);
+    }
   }
 }
 
 // ------------------------------------------------------------------ synthesis
 
 
-// acc + (beta_i / (4 pi d_i(n))) e_i(n) for one image-sample read from the
-// staged window (kStride columns per segment). The gain of the image record is
-// beta_i / (4 pi) * fs / c, so the gain at n is gain / tau with tau in samples.
+// Approximate reciprocal (one MUFU operation, relative error about 2^-23).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// acc + (beta_i / (4 pi d_i(n))) e_i(n) for one chunk sample of an image pair
+// (paired layout, see records_from_phi), read from the staged window (kStride
+// columns per segment). R = the pair's interval record, AB its gain terms, I4
+// its column byte offsets; rf2 = {r, r} with r the sample's offset in its knot
+// interval. The delay, its rounding, the local variable w, tau / G and the
+// accumulation run as float2 pairs (one instruction for both images); the
+// window offsets, the loads and the Farrow polynomial per image.
 // kChecked: the window is processed in several column passes and only columns
 // inside this pass count; otherwise every read position lies inside the window
 // by construction and the index is only clamped to the window arrays.
-// Unchecked reads index the window by byte offset (split_offset): the offset
-// of the power-4 value, 4 times it for the powers 0..3.
+// Unchecked reads index the window by byte offset (split_offset's form): the
+// offset of the power-4 value, 4 times it for the powers 0..3.
 template <int kStride, bool kChecked>
-__device__ __forceinline__ float image_sample(const float4* zq, const float* zp, const float2 rec, const int4 im,
-                                              unsigned I4, int rmj, unsigned rmc4, float rf, unsigned wmax,
-                                              float acc) {
-  const float Dp = __int_as_float(im.y);
-  float w, tau;
-  float4 A;
-  float B;
+__device__ __forceinline__ float2 pair_sample(const float4* zq, float2 inv2, const float4 R, const float4 AB,
+                                              const int2 I4, float2 rf2, unsigned rmc4, int rmj, unsigned wmax,
+                                              float2 acc) {
+  const float2 Y = __ffma2_rn(rf2, make_float2(R.z, R.w), make_float2(R.x, R.y));
+  const float2 q = __fadd2_rn(Y, make_float2(kRound, kRound));
+  const float2 t = __fadd2_rn(q, make_float2(-kRound, -kRound));
+  const float2 w = __ffma2_rn(t, make_float2(-1.0f, -1.0f), Y);       // Y - round(Y), exact
+  const float2 tg = __ffma2_rn(Y, make_float2(AB.x, AB.y), make_float2(AB.z, AB.w));  // tau / G
+  float g0 = rcp_approx(tg.x), g1 = rcp_approx(tg.y);
+  const unsigned b0 = __float_as_uint(q.x), b1 = __float_as_uint(q.y);
+  unsigned o0, o1;
   if (kChecked) {
-    const DelaySplit ds = split_delay(rec, rmj + im.x, rf, Dp);
-    if (unsigned(ds.col) > wmax) return acc;
-    const unsigned idx = unsigned(ds.seg * kStride + ds.col);
-    A = zq[idx];
-    B = zp[idx];
-    w = ds.w;
-    tau = ds.tau;
+    // column of the read position within this pass, then the byte offset of
+    // its power-4 value; columns outside the pass contribute nothing
+    int c0 = rmj + (I4.x >> 2) + (int(b0 >> 2) - (kRoundBits >> 2));
+    int c1 = rmj + (I4.y >> 2) + (int(b1 >> 2) - (kRoundBits >> 2));
+    if (unsigned(c0) > wmax) { g0 = 0.0f; c0 = 0; }
+    if (unsigned(c1) > wmax) { g1 = 0.0f; c1 = 0; }
+    o0 = 4u * ((b0 & 3u) * unsigned(kStride) + unsigned(c0));
+    o1 = 4u * ((b1 & 3u) * unsigned(kStride) + unsigned(c1));
   } else {
-    const unsigned off = min(split_offset<kStride>(rec, I4, rmc4, rf, Dp, &w, &tau),
-                             unsigned(4 * (kFarrowSegs * kStride - 1)));
-    A = *reinterpret_cast<const float4*>(reinterpret_cast<const unsigned char*>(zq) + 4u * off);
-    B = *reinterpret_cast<const float*>(reinterpret_cast<const unsigned char*>(zp) + off);
+    constexpr unsigned kCap = unsigned(4 * (kFarrowSegs * kStride - 1));
+    o0 = min((b0 & 3u) * unsigned(4 * kStride - 1) + b0 + (unsigned(I4.x) + rmc4), kCap);
+    o1 = min((b1 & 3u) * unsigned(4 * kStride - 1) + b1 + (unsigned(I4.y) + rmc4), kCap);
   }
-  const float e = horner5(A, B, w);
-  return fmaf(__fdividef(__int_as_float(im.z), tau), e, acc);
+  const unsigned char* zqb = reinterpret_cast<const unsigned char*>(zq);
+  const float4 A0 = *reinterpret_cast<const float4*>(zqb + 4u * o0);
+  const float4 A1 = *reinterpret_cast<const float4*>(zqb + 4u * o1);
+  const float2 ws = __fmul2_rn(w, inv2);  // w / zh_scale for the half-precision powers
+  const float e0 = horner_zh(A0, w.x, ws.x), e1 = horner_zh(A1, w.y, ws.y);
+  return __ffma2_rn(make_float2(g0, g1), make_float2(e0, e1), acc);
 }
 
-// All images of the block for this thread's kChunks samples; rmj[c] =
-// r - m_lo + jj N_t of chunk c (its interval jj = jc[c]).
+// All image pairs of the block for this thread's kChunks samples; rmj[c] =
+// r - m_lo + jj N_t of chunk c (its interval jj = jc[c]). acc[c] holds the
+// sums over the even and the odd images of the block.
 // kOne: every chunk of this lane lies in one knot interval (warp-uniform), so
-// one record load per image serves all chunks.
+// one record load per pair serves all chunks.
 template <int kStride, int kChunks, int kUnroll, bool kChecked, bool kOne>
-__device__ __forceinline__ void gather_images(const float4* zq, const float* zp, const float2* rec_s,
-                                              const int4* img_s, int cnt, const int* jc, const int* rmj,
-                                              const float* rf, unsigned wmax, float* acc) {
+__device__ __forceinline__ void gather_pairs(const float4* zq, float2 inv2, const float4* rec4,
+                                             const float4* ab_s, const int2* i4_s, int cntp, const int* jc,
+                                             const int* rmj, const float* rf, unsigned wmax, float2* acc) {
   unsigned rmc4[kChunks];
-  const float2* row[kChunks];  // records of chunk c: row jc[c] of the interval-major table
+  float2 rf2[kChunks];
+  const float4* row[kChunks];  // records of chunk c: row jc[c] of the interval-major table
 #pragma unroll
   for (int c = 0; c < kChunks; ++c) {
     rmc4[c] = fold_rounding(rmj[c]) << 2;
-    row[c] = rec_s + jc[c] * cnt;
+    rf2[c] = make_float2(rf[c], rf[c]);
+    row[c] = rec4 + jc[c] * cntp;
   }
-  int ib = 0;
-  for (; ib + kUnroll <= cnt; ib += kUnroll) {
+  int p = 0;
+  for (; p + kUnroll <= cntp; p += kUnroll) {
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      const int4 im = img_s[ib + u];
-      const unsigned I4 = unsigned(im.w);  // 4 im.x
-      const float2 r0 = row[0][ib + u];
+      const float4 AB = ab_s[p + u];
+      const int2 I4 = i4_s[p + u];
+      const float4 R0 = row[0][p + u];
 #pragma unroll
       for (int c = 0; c < kChunks; ++c)
-        acc[c] = image_sample<kStride, kChecked>(zq, zp, (kOne || c == 0) ? r0 : row[c][ib + u], im, I4, rmj[c],
-                                                 rmc4[c], rf[c], wmax, acc[c]);
+        acc[c] = pair_sample<kStride, kChecked>(zq, inv2, (kOne || c == 0) ? R0 : row[c][p + u], AB, I4, rf2[c],
+                                                rmc4[c], rmj[c], wmax, acc[c]);
     }
   }
-  for (; ib < cnt; ++ib) {
-    const int4 im = img_s[ib];
-    const unsigned I4 = unsigned(im.w);  // 4 im.x
-    const float2 r0 = row[0][ib];
+  for (; p < cntp; ++p) {
+    const float4 AB = ab_s[p];
+    const int2 I4 = i4_s[p];
+    const float4 R0 = row[0][p];
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)
-      acc[c] = image_sample<kStride, kChecked>(zq, zp, (kOne || c == 0) ? r0 : row[c][ib], im, I4, rmj[c],
-                                               rmc4[c], rf[c], wmax, acc[c]);
+      acc[c] = pair_sample<kStride, kChecked>(zq, inv2, (kOne || c == 0) ? R0 : row[c][p], AB, I4, rf2[c], rmc4[c],
+                                              rmj[c], wmax, acc[c]);
   }
 }
 
@@ -157,11 +221,9 @@ template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock, int kUn
 __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(const __grid_constant__ KernelArgs a) {
   extern __shared__ __align__(16) float4 smem4[];
   float4* zq_s = smem4;                                                  // kFarrowSegs x kWcap
-  float* zp_s = reinterpret_cast<float*>(smem4 + kFarrowSegs * kWcap);    // kFarrowSegs x kWcap
-  float2* rec_s = reinterpret_cast<float2*>(zp_s + kFarrowSegs * kWcap);  // kRecCap interval records
+  float2* rec_s = reinterpret_cast<float2*>(zq_s + kFarrowSegs * kWcap);  // kRecCap interval records
   int4* img_s = reinterpret_cast<int4*>(rec_s + kRecCap);                 // kBlock image records
-  static_assert((kRecCap * sizeof(float2)) % 16 == 0 && (kFarrowSegs * kWcap * sizeof(float)) % 16 == 0,
-                "every shared array starts on a 16-byte boundary");
+  static_assert((kRecCap * sizeof(float2)) % 16 == 0, "every shared array starts on a 16-byte boundary");
   // prologue scratch aliases the z window (used before the window is staged)
   float4* u_s = smem4;
   float4* um_s = u_s + kThreads * kChunks + 4;                           // moving array
@@ -173,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
   __shared__ int s_item;
   __shared__ float s_red[2][kThreads / 32];
   __shared__ __align__(8) uint64_t s_mbar;  // completion of the window's bulk copies
-  static_assert(kWcap % 4 == 0, "16-byte aligned power-4 row segments");
+  static_assert(kWcap % 4 == 0, "window columns in steps of 4 (the bulk copies' alignment of the rows)");
   static_assert(kBlock <= kThreads, "the record builders give every image at least one thread");
   constexpr int kTile = kThreads * kChunks;
   static_assert(4 * (2 * (kTile + 4) + 3 * kBlock) + kRecCap + kBlock <= 4 * kFarrowSegs * kWcap,
@@ -203,14 +265,14 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
     float tmin, tmax;
     int cnt = g.cnt;
     if (S.delay_model == 1) {
-      item_records_ret<kThreads>(a, S, g, rec_s, img_s, u_s, an6_s, phi_r, &tmin, &tmax);
+      item_records_ret<kThreads, true>(a, S, g, rec_s, img_s, u_s, an6_s, phi_r, &tmin, &tmax);
     } else if (S.tier_up[g.t] > 1) {
-      // band-limited knot upsampling: its scratch takes the z window and power rows
-      if (!item_records_bl<kThreads>(a, S, g, rec_s, img_s, reinterpret_cast<float*>(smem4),
-                                     int64_t(kFarrowSegs) * kWcap * 5, &tmin, &tmax))
+      // band-limited knot upsampling: its scratch takes the z window
+      if (!item_records_bl<kThreads, true>(a, S, g, rec_s, img_s, reinterpret_cast<float*>(smem4),
+                                           int64_t(kFarrowSegs) * kWcap * 4, &tmin, &tmax))
         cnt = 0;
     } else {
-      item_records<kThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax);
+      item_records<kThreads, true>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -226,15 +288,16 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       tmin = fminf(tmin, s_red[0][w]);
       tmax = fmaxf(tmax, s_red[1][w]);
     }
-    // window start congruent to the z rows' origin mod 4: power-4 row segments
-    // then start on 16-byte boundaries on both sides of the bulk copy
+    // window start congruent to the z rows' origin mod 4 (the rows are padded to
+    // a multiple of 4 columns; kept from the layout with a separate power-4 row)
     int m_lo = g.n0 - int(ceilf(tmax)) - 2;
     m_lo -= int(((int64_t(m_lo) - S.z_m0) % 4 + 4) % 4);
     const int width = g.n_end - int(floorf(tmin)) + 2 - m_lo + 1;
 
     // this thread's samples: warp w owns n0 + 32 (w kChunks + c) + lane
     int jc[kChunks], rr[kChunks], rmj[kChunks];
-    float rf[kChunks], acc[kChunks];
+    float rf[kChunks];
+    float2 acc[kChunks];
     bool valid[kChunks];
 #pragma unroll
     for (int c = 0; c < kChunks; ++c) {
@@ -245,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       rr[c] = nn - j * g.N;
       jc[c] = j - g.jf;
       rf[c] = float(rr[c]);
-      acc[c] = 0.0f;
+      acc[c] = make_float2(0.0f, 0.0f);
     }
     // every chunk of every lane in one knot interval (e.g. 96-sample intervals
     // aligned with this warp's 96 samples): one record load per image
@@ -253,8 +316,15 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
 #pragma unroll
     for (int c = 1; c < kChunks; ++c) one = one && (jc[c] == jc[0]);
     one = __all_sync(0xffffffffu, one);
+    // paired record layout (see records_from_phi)
+    const int cntp = pair_count(cnt);
+    const float4* rec4 = reinterpret_cast<const float4*>(rec_s);
+    const float4* ab_s = reinterpret_cast<const float4*>(img_s);
+    const int2* i4_s = reinterpret_cast<const int2*>(ab_s + cntp);
     const float4* zqg = a.p.zq + S.z_base;
-    const float* zpg = a.p.zp + S.z_base;
+    // scale of the half-precision powers 3 and 4 (see zh_scale), as a pair
+    const float inv_s = zh_scale(a, s).y;
+    const float2 inv2 = make_float2(inv_s, inv_s);
 
     // --- the window [m_lo, m_lo + width) in passes of at most kWcap columns
     for (int p0 = 0; p0 < width; p0 += kWcap) {
@@ -274,12 +344,9 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       if (cnt_c > 0) {
         if (threadIdx.x == 0) {
           const unsigned bq = unsigned(cnt_c) * 16u;
-          const unsigned bp = unsigned((cnt_c + 3) & ~3) * 4u;  // within the padded rows
-          mbar_expect_tx(&s_mbar, unsigned(kFarrowSegs) * (bq + bp) + a.test_extra_tx);
-          for (int sg = 0; sg < kFarrowSegs; ++sg) {
+          mbar_expect_tx(&s_mbar, unsigned(kFarrowSegs) * bq + a.test_extra_tx);
+          for (int sg = 0; sg < kFarrowSegs; ++sg)
             bulk_g2s(zq_s + sg * kWcap + dst0, zqg + int64_t(sg) * S.z_len + src0, bq, &s_mbar);
-            bulk_g2s(zp_s + sg * kWcap + dst0, zpg + int64_t(sg) * S.z_len + src0, bp, &s_mbar);
-          }
         }
         const bool ok = mbar_wait(&s_mbar, phase);
         if (__syncthreads_or(!ok)) {
@@ -294,20 +361,24 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
 #pragma unroll
       for (int c = 0; c < kChunks; ++c) rmj[c] = rr[c] - pass_lo + jc[c] * g.N;
       const unsigned wmax = unsigned(pw - 1);
+      constexpr int kPairUnroll = kUnroll >= 2 ? kUnroll / 2 : 1;
       if (width <= kWcap) {
         if (one)
-          gather_images<kWcap, kChunks, kUnroll, false, true>(zq_s, zp_s, rec_s, img_s, cnt, jc, rmj, rf, wmax, acc);
+          gather_pairs<kWcap, kChunks, kPairUnroll, false, true>(zq_s, inv2, rec4, ab_s, i4_s, cntp, jc, rmj, rf,
+                                                                 wmax, acc);
         else
-          gather_images<kWcap, kChunks, kUnroll, false, false>(zq_s, zp_s, rec_s, img_s, cnt, jc, rmj, rf, wmax, acc);
+          gather_pairs<kWcap, kChunks, kPairUnroll, false, false>(zq_s, inv2, rec4, ab_s, i4_s, cntp, jc, rmj, rf,
+                                                                  wmax, acc);
       } else {
-        gather_images<kWcap, kChunks, kUnroll, true, false>(zq_s, zp_s, rec_s, img_s, cnt, jc, rmj, rf, wmax, acc);
+        gather_pairs<kWcap, kChunks, kPairUnroll, true, false>(zq_s, inv2, rec4, ab_s, i4_s, cntp, jc, rmj, rf,
+                                                               wmax, acc);
       }
     }
     float* out = a.p.part + S.part_base + (int64_t(g.mic) * S.n_blocks + g.blk) * S.n_out;
 #pragma unroll
     for (int c = 0; c < kChunks; ++c) {
       const int n = g.n0 + 32 * (warp * kChunks + c) + lane;
-      if (valid[c]) out[n] = acc[c];
+      if (valid[c]) out[n] = acc[c].x + acc[c].y;
     }
     __syncthreads();  // shared memory and s_item are reused by the next item
   }
@@ -335,22 +406,15 @@ __global__ void k_reduce(const __grid_constant__ KernelArgs a) {
 template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock, int kUnroll>
 cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
   auto kern = k_synth<kThreads, kChunks, kWcap, kRecCap, kBlock, kUnroll>;
-  const size_t smem = size_t(kFarrowSegs) * kWcap * (sizeof(float4) + sizeof(float)) +
-                      size_t(kRecCap) * sizeof(float2) + size_t(kBlock) * sizeof(int4);
-  static int grid = 0;
-  if (grid == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    grid = sms * (occ > 0 ? occ : 1);
-  }
+  const size_t smem = size_t(kFarrowSegs) * kWcap * sizeof(float4) + size_t(kRecCap) * sizeof(float2) +
+                      size_t(kBlock) * sizeof(int4);
+  static PerDevice setup;  // per device: shared-memory limit set, grid computed
+  int grid = 0;
+  cudaError_t e = persistent_grid(setup, kern, kThreads, smem, &grid);
+  if (e != cudaSuccess) return e;
   const int64_t items = a.totals[4];
   const int g = int(items < grid ? items : grid);
-  cudaError_t e = cudaMemsetAsync(a.p.counter, 0, sizeof(uint32_t), st);
+  e = cudaMemsetAsync(a.p.counter, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   if (g > 0) kern<<<g, kThreads, smem, st>>>(a);
   return cudaGetLastError();
@@ -360,17 +424,18 @@ cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
 
 // Tile configurations of the synthesis launch (see TileConfig).
 #define MSRC_TILE_CONFIGS(X)             \
-  X(0, 512, 3, 2432, 4096, 256, 8)       \
-  X(1, 256, 2, 1152, 1664, 256, 4)       \
-  X(2, 384, 2, 2048, 3072, 256, 4)       \
-  X(3, 1024, 1, 2432, 4096, 256, 2)      \
-  X(4, 512, 2, 2432, 4096, 256, 8)       \
-  X(5, 512, 1, 2432, 4096, 256, 8)       \
-  X(6, 512, 3, 2432, 4096, 256, 4)       \
-  X(7, 512, 2, 2432, 4096, 256, 16)      \
-  X(8, 512, 3, 1792, 8192, 256, 8)       \
-  X(9, 512, 2, 1792, 8192, 256, 8)       \
-  X(10, 512, 2, 1536, 10240, 256, 8)
+  X(0, 512, 3, 3040, 4096, 256, 8)       \
+  X(1, 256, 2, 1440, 1664, 256, 4)       \
+  X(2, 384, 2, 2560, 3072, 256, 4)       \
+  X(3, 1024, 1, 3040, 4096, 256, 2)      \
+  X(4, 512, 2, 3040, 4096, 256, 8)       \
+  X(5, 512, 1, 3040, 4096, 256, 8)       \
+  X(6, 512, 3, 3040, 4096, 256, 4)       \
+  X(7, 512, 2, 3040, 4096, 256, 16)      \
+  X(8, 512, 3, 2240, 8192, 256, 8)       \
+  X(9, 512, 2, 2240, 8192, 256, 8)       \
+  X(10, 512, 2, 1920, 10240, 256, 8)     \
+  X(11, 256, 3, 1440, 2048, 256, 8)
 
 static const TileConfig kConfigs[] = {
 #define MSRC_ROW(id, th, ch, wc, rc, bl, un) {th, ch, wc, rc, bl},
@@ -384,6 +449,11 @@ const TileConfig& tile_config(int cfg) { return kConfigs[cfg]; }
 cudaError_t launch_prefilter(const KernelArgs& a, cudaStream_t st, bool gradient_rows) {
   if (a.totals[3] > 0) {
     const unsigned g = unsigned(a.totals[3]);
+    if (!gradient_rows) {  // the scale of the half-precision powers: max |x| per scene
+      const cudaError_t e = cudaMemsetAsync(a.p.xmax, 0, sizeof(uint32_t) * size_t(a.n_scenes), st);
+      if (e != cudaSuccess) return e;
+      k_absmax<<<g, kPreThreads, 0, st>>>(a);
+    }
     if (gradient_rows) {
       if (a.taps <= 16) k_prefilter<16, kGradCoef><<<g, kPreThreads, 0, st>>>(a);
       else if (a.taps <= 32) k_prefilter<32, kGradCoef><<<g, kPreThreads, 0, st>>>(a);

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 
+#include "device_cache.h"
 #include "msrc.h"
 
 namespace msrc {
@@ -18,9 +19,10 @@ void set_last_error(const char* msg);
 // degree-kFarrowDeg polynomial in a local variable of the fractional delay,
 // piecewise over kFarrowSegs segments of [0, 1). The prefilter produces one
 // signal row per (segment, power): z[s][q][m] = sum_k c[s][q][k] x[m - k],
-// stored per segment as a float4 row (powers 0..3) and a float row (power 4),
-// so that one image-sample gathers its 5 values with a 16-byte and a 4-byte
-// load (5 shared-memory wavefronts per warp).
+// stored per segment as one float4 per column, {z0, z1, z2, (z3, z4)} with the
+// two highest powers scaled by a power of two and rounded to half precision
+// (they carry under 1 % of the value), so that one image-sample gathers its 5
+// values with one 16-byte load (4 shared-memory wavefronts per warp).
 constexpr int kFarrowSegs = 4;
 constexpr int kFarrowDeg = 4;
 constexpr int kFarrowCoef = kFarrowDeg + 1;
@@ -95,6 +97,15 @@ struct SceneDev {
   float mics_hl[MSRC_MAX_MICS][3][2];
   float fsc_hl[2];
   int64_t img_base;                        // first entry of this scene in the image table
+  // time groups: the forward synthesis orders the images separately for every
+  // group of tile_group consecutive output tiles (by tier, then distance at the
+  // group's middle), so that the images of a block stay close in delay over the
+  // group's tiles; group g's table starts at img_base + g * n_images.
+  // Reverse mode and band-limited tiers use one group (tile_group >= n_tiles).
+  int32_t tile_group;                      // output tiles per time group
+  int32_t n_time_groups;                   // time groups of the scene
+  int64_t sort_group0;                     // the scene's first group in the sort key
+  int64_t gpos_base;                       // its first entry in the group position table
   int64_t knot_base[MSRC_MAX_TIERS];       // first knot position (double3) per tier
   int64_t knot_units_first[MSRC_MAX_TIERS];// prefix over tiers of (J_t + 1)
   int64_t part_base;                       // first partial-sum float
@@ -147,6 +158,9 @@ struct LaunchTables {
   const int64_t* bl_prefix;      // knot delays of upsampled tiers
   const int64_t* dense_prefix;   // source path table entries (emission-time delays)
 };
+// Image table units of the enumeration and sort: time groups x images. Sort
+// key: (scene's time group << kSortGroupShift) | (tier << 24) | distance (24 bits).
+constexpr int kSortGroupShift = 26;
 
 struct DevicePtrs {
   uint32_t* err;                 // device error word
@@ -158,13 +172,16 @@ struct DevicePtrs {
   void* sort_temp;
   size_t sort_temp_bytes;
   uint32_t* img_code;            // packed lattice triple and parity
+  double* gpos;                  // per (scene, time group): source position and array
+                                 // displacement at the group's middle (6 doubles), sort keys
   float* img_gain;               // beta_i / (4 pi)
   double* knot_pos;              // s(t_j), 3 doubles per knot
   double* arr_pos;               // a(t_j) - a(0), 3 doubles per knot (scenes with a moving array)
   float4* knot_hl;               // s(t_j) as double-float pairs: hi (x, y, z, 0) then lo, per knot
   float4* arr_hl;                // a(t_j) - a(0) the same way (moving array)
-  float4* zq;                    // prefiltered powers 0..3, [scene rows][segment][column]
-  float* zp;                     // prefiltered power 4, same indexing
+  float4* zq;                    // prefiltered rows, [scene rows][segment][column]: forward
+                                 // {z0, z1, z2, half2(s z3, s z4)}, reverse mode powers 0..3
+  uint32_t* xmax;                // per scene: max |x| (float bits), scale of the half-precision powers
   float2* zg;                    // reverse mode: powers 4..5 of the degree-5 rows (zq holds 0..3)
   float* part;                   // partial sums
   // reverse mode
@@ -203,6 +220,9 @@ struct KernelArgs {
   float farrow[kFarrowSegs][kFarrowCoef][kMaxTaps];  // coefficients c[s][q][k + L/2] of the powers of w
   float farrow_g[kFarrowSegs][kGradCoef][kMaxTaps];  // degree-5 coefficients (gradient kernel)
   int32_t taps;
+  float zh_gain;                 // max over segments of sum_k |c_q[k]| (q = 3, 4): z bound per unit |x|
+  int64_t n_sort_groups;         // time groups over all scenes (the sort key's leading field)
+  int32_t max_time_groups;       // largest time-group count of one scene
   uint32_t test_extra_tx;        // test hook: bytes a window staging expects beyond its copies (0)
 };
 
@@ -225,6 +245,35 @@ __host__ __device__ inline void unpack_image(uint32_t code, int n[3], int p[3]) 
 // and the relative delays.
 __host__ __device__ inline int64_t bl_scratch_floats(int cnt, int nk, int nj, int Q) {
   return int64_t(cnt) * (1 + nj * (2 * Q + 2) + nk);
+}
+
+// Grid of a persistent kernel on the current device (SMs x resident CTAs of
+// `threads` threads and `smem` bytes of dynamic shared memory), with the
+// kernel's dynamic shared-memory limit raised to `smem`: set up once per device
+// and kernel (one PerDevice per kernel instantiation), thread-safe.
+template <typename K>
+cudaError_t persistent_grid(PerDevice& cache, K kern, int threads, size_t smem, int* grid) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaError_t ie = cudaSuccess;
+  const int st = cache.get(
+      dev,
+      [&](int* v) {
+        ie = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (ie != cudaSuccess) return 1;
+        int sms = 0, occ = 0;
+        ie = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (ie != cudaSuccess) return 1;
+        ie = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+        if (ie != cudaSuccess) return 1;
+        *v = sms * (occ > 0 ? occ : 1);
+        return 0;
+      },
+      grid);
+  if (st == -1) return cudaErrorInvalidDevice;
+  if (st != 0) return ie != cudaSuccess ? ie : cudaErrorUnknown;
+  return cudaSuccess;
 }
 
 // Launch entry points (defined in the .cu files).

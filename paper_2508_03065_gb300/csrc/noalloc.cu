@@ -12,7 +12,11 @@
 // the output y.
 //
 // The array costs every GPU that loads the library kNoAllocScratchBytes of
-// device memory until the process exits.
+// device memory until the process exits. It is committed when the library's
+// device code is loaded on a GPU; with lazy module loading (the CUDA default)
+// that happens at the first allocation-free call there, which therefore
+// belongs in the caller's set-up phase. msrc_noalloc_errors reads the device
+// error word that the calls leave in the array.
 #include <cstdint>
 #include <cstdio>
 #include <mutex>
@@ -93,6 +97,19 @@ msrc_status msrc_synthesize_noalloc(msrc_room_t room, const float* x_dev, int64_
   // counter) on the stream before its kernels; every other scratch byte is
   // written before it is read within the call.
   return msrc_synthesize(&room, 1, &x_dev, &n_in, &y_dev, &n_out, scratch, kNoAllocScratchBytes, stream);
+}
+
+msrc_status msrc_noalloc_errors(void* stream, uint32_t* flags) {
+  if (!flags) {
+    msrc::set_last_error("null flags");
+    return MSRC_ERR_INVALID_ARG;
+  }
+  // the scratch's first word is the error word of the last allocation-free
+  // call on this device (the workspace header of msrc_synthesize)
+  void* scratch = nullptr;
+  msrc_status s = scratch_for_current_device(&scratch);
+  if (s != MSRC_OK) return s;
+  return msrc_workspace_errors(scratch, stream, flags);
 }
 
 }  // extern "C"

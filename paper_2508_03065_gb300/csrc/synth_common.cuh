@@ -6,6 +6,8 @@
 
 #include <cstdint>
 
+#include <cuda_fp16.h>
+
 #include "msrc_internal.h"
 
 namespace msrc {
@@ -29,6 +31,7 @@ __device__ __forceinline__ int find_scene(const int64_t* prefix, int n, int64_t 
 // jf .. jf+nk-1; the item's records cover intervals jf .. jf+nk-2.
 struct ItemGeom {
   int mic, blk, t, img0, cnt, N, n0, n_end, jf, nk;
+  int64_t img_off;  // the item's time group in the image table (group * n_images)
 };
 
 __device__ __forceinline__ ItemGeom item_geometry(const SceneDev& S, int64_t li, int tile) {
@@ -50,6 +53,7 @@ __device__ __forceinline__ ItemGeom item_geometry(const SceneDev& S, int64_t li,
   g.n_end = int(min(int64_t(g.n0 + tile), S.n_out)) - 1;
   g.jf = g.n0 / g.N;
   g.nk = g.n_end / g.N - g.jf + 2;
+  g.img_off = int64_t(tl / S.tile_group) * S.n_images;
   return g;
 }
 
@@ -204,13 +208,26 @@ __device__ __forceinline__ void anchor_df(const SceneDev& S, uint32_t code, cons
   *SG = make_float4(s0, s1, s2, 0.0f);
 }
 
+// Paired record layout of the forward synthesis (kPaired): images 2p and 2p + 1
+// of a block share one 16-byte interval record per interval jj,
+//   rec[jj * cntp + p] = {Psi_2p, Psi_2p+1, sigma_2p, sigma_2p+1}    (float4),
+// and their image records sit in two arrays at img_s,
+//   ab[p] = {a_2p, a_2p+1, b_2p, b_2p+1} (float4), i4[p] = {4 I_2p, 4 I_2p+1} (int2),
+// with a = -1 / (S G) and b = (D_a - 1/(2S)) / G (G the image's gain), so that
+// tau(n) / G = a Y(n) + b and the gain at n is its reciprocal. cntp = ceil(cnt / 2);
+// an odd block's last pair carries a copy of its last image with zero gain
+// (a = 0, b = +inf), which reads in-bounds columns and adds nothing. Every
+// operand of the pair arithmetic is then one aligned 8-byte register pair.
+__device__ __forceinline__ int pair_count(int cnt) { return (cnt + 1) >> 1; }
+
 // Interval records of an item from the relative delays phi at its knots
 // (phi_s[ib * nk + jj]); see item_records for the record layout.
-template <int kThreads>
+template <int kThreads, bool kPaired = false>
 __device__ __forceinline__ void records_from_phi(const ItemGeom& g, const float* phi_s, float2* rec_s) {
   const float sN = float(kFarrowSegs) / float(g.N);
   const int nk = g.nk;
   const int nrec = nk - 1;
+  const int cntp = pair_count(g.cnt);
   // image-fastest as in item_records: consecutive threads, consecutive records
   const int tpi = kThreads / g.cnt;
   if (threadIdx.x < tpi * g.cnt) {
@@ -218,7 +235,19 @@ __device__ __forceinline__ void records_from_phi(const ItemGeom& g, const float*
     const int ib = threadIdx.x - j0 * g.cnt;
     for (int jj = j0; jj < nrec; jj += tpi) {
       const float phi0 = phi_s[ib * nk + jj], phi1 = phi_s[ib * nk + jj + 1];
-      rec_s[jj * g.cnt + ib] = make_float2(fmaf(-float(kFarrowSegs), phi0, -0.5f), (phi0 - phi1) * sN);
+      const float psi = fmaf(-float(kFarrowSegs), phi0, -0.5f), sig = (phi0 - phi1) * sN;
+      if (kPaired) {
+        float* f = reinterpret_cast<float*>(reinterpret_cast<float4*>(rec_s) + jj * cntp + (ib >> 1));
+        const int h = ib & 1;
+        f[h] = psi;
+        f[2 + h] = sig;
+        if (h == 0 && ib == g.cnt - 1) {  // odd block: the zero-gain copy
+          f[1] = psi;
+          f[3] = sig;
+        }
+      } else {
+        rec_s[jj * g.cnt + ib] = make_float2(psi, sig);
+      }
     }
   }
 }
@@ -233,6 +262,7 @@ __device__ __forceinline__ void records_from_phi(const ItemGeom& g, const float*
 //   img_s[ib]            = {I = n_jf - D_a, D_a - 1/(2S) (float), gain (float), 4 I}
 // so that Y(n) = Psi_j + sigma_j r = S (n - tau(n) - n_j + I + jj N_t) - 1/2 up to
 // the integer read position, and tau(n) = (D_a - 1/(2S)) - Y / S.
+// (kPaired: the same values in the paired layout described above.)
 // u_s and um_s (nk entries each), anc_s (3 * cnt entries) and phi_s (cnt * nk
 // floats, at most the record capacity plus the block size) are scratch. With
 // a moving array the knots also carry the array displacement: per knot
@@ -245,7 +275,32 @@ __device__ __forceinline__ int4 image_record(int I, float Dfl, float gain) {
   return make_int4(I, __float_as_int(Dfl - 0.5f / kFarrowSegs), __float_as_int(gain), int(unsigned(I) << 2));
 }
 
-template <int kThreads>
+// Writes image ib's record (column offset I, anchor delay floor Dfl, gain) in
+// the layout of kPaired.
+template <bool kPaired>
+__device__ __forceinline__ void put_image_record(int4* img_s, int ib, int cnt, int I, float Dfl, float gain) {
+  if (!kPaired) {
+    img_s[ib] = image_record(I, Dfl, gain);
+    return;
+  }
+  float* ab = reinterpret_cast<float*>(reinterpret_cast<float4*>(img_s) + (ib >> 1));
+  int* i4 = reinterpret_cast<int*>(reinterpret_cast<int2*>(reinterpret_cast<float4*>(img_s) + pair_count(cnt)) +
+                                   (ib >> 1));
+  const int h = ib & 1;
+  const float inf = __int_as_float(0x7f800000);
+  const float Dp = Dfl - 0.5f / kFarrowSegs;
+  const bool live = gain > 0.0f;
+  ab[h] = live ? -(1.0f / kFarrowSegs) / gain : 0.0f;
+  ab[2 + h] = live ? Dp / gain : inf;
+  i4[h] = int(unsigned(I) << 2);
+  if (h == 0 && ib == cnt - 1) {  // odd block: the zero-gain copy
+    ab[1] = 0.0f;
+    ab[3] = inf;
+    i4[1] = i4[0];
+  }
+}
+
+template <int kThreads, bool kPaired = false>
 __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                              int4* img_s, float4* u_s, float4* um_s, float4* anc_s, float* phi_s,
                              float* tmin_out, float* tmax_out) {
@@ -274,8 +329,8 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
       um_s[jj] = make_float4(mx, my, mz, fmaf(mx, mx, fmaf(my, my, mz * mz)));
     }
   }
-  const uint32_t* codes = a.p.img_code + S.img_base + S.tier_first[g.t] + g.img0;
-  const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
+  const uint32_t* codes = a.p.img_code + S.img_base + g.img_off + S.tier_first[g.t] + g.img0;
+  const float* gain = a.p.img_gain + S.img_base + g.img_off + S.tier_first[g.t] + g.img0;
   // the microphone at the anchor knot (carried by the array), double-float
   DF mdf[3];
   {
@@ -291,7 +346,7 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     anc_s[2 * ib] = A;
     anc_s[2 * ib + 1] = make_float4(B.x, B.y, 0.0f, 0.0f);
     anc_s[2 * g.cnt + ib] = SG;
-    img_s[ib] = image_record(g.jf * g.N - int(B.y), B.y, __ldg(gain + ib));
+    put_image_record<kPaired>(img_s, ib, g.cnt, g.jf * g.N - int(B.y), B.y, __ldg(gain + ib));
   }
   __syncthreads();
   // relative delay phi at every knot of every image (once per knot), then the
@@ -318,7 +373,7 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     }
   }
   __syncthreads();
-  records_from_phi<kThreads>(g, phi_s, rec_s);
+  records_from_phi<kThreads, kPaired>(g, phi_s, rec_s);
   *tmin_out = tmin;
   *tmax_out = tmax;
 }
@@ -340,7 +395,7 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
 // chord rows (cnt x nj x (2Q + 2)), phi (cnt x nk). If the item does not fit,
 // the error word gets kErrUpsampleScratch, no record is written and the result
 // is false (the caller then treats the block as empty).
-template <int kThreads>
+template <int kThreads, bool kPaired = false>
 __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                                 int4* img_s, float* scr, int64_t cap, float* tmin_out, float* tmax_out) {
   const int U = S.tier_up[g.t];
@@ -363,7 +418,7 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
   // delays of image ib: rows[ib * nkt + j + Q] is knot j (the table starts at knot -Q)
   const float2* rows = a.p.bl_tau + S.bl_tau_base[g.t] +
                        (int64_t(g.mic) * S.tier_count[g.t] + g.img0) * nkt + Q;
-  const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
+  const float* gain = a.p.img_gain + S.img_base + g.img_off + S.tier_first[g.t] + g.img0;
   // image-fastest thread mapping (one division per thread): image t mod cnt,
   // intervals / knots from t / cnt in steps of kThreads / cnt
   const int tpi = kThreads / g.cnt;
@@ -378,7 +433,7 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
     const float Dfl = df_floor(DF{an.x, an.y});  // the anchor, knot floor(jf / U)
     if (jr == 0) {
       dfl_s[ib] = Dfl;
-      img_s[ib] = image_record(g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib));
+      put_image_record<kPaired>(img_s, ib, g.cnt, g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib));
     }
     const float2* tv = row + (j0_first + jr - Q + 1);  // knots j0 - Q + 1 .. j0 + Q
     const DF t0{tv[Q - 1].x, tv[Q - 1].y};
@@ -426,7 +481,7 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
     }
   }
   __syncthreads();
-  records_from_phi<kThreads>(g, phi_s, rec_s);
+  records_from_phi<kThreads, kPaired>(g, phi_s, rec_s);
   *tmin_out = tmin;
   *tmax_out = tmax;
   return true;
@@ -498,7 +553,7 @@ __device__ __forceinline__ float ret_increment(const RetAnchor& r, const float4 
   return delta;
 }
 
-template <int kThreads>
+template <int kThreads, bool kPaired = false>
 __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                                  int4* img_s, float4* um_s, float4* an6, float* phi_s, float* tmin_out,
                                  float* tmax_out) {
@@ -525,8 +580,8 @@ __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const I
       mdf[d] = df_add(DF{S.mics_hl[g.mic][d][0], S.mics_hl[g.mic][d][1]}, DF{ah[d], al[d]});
   }
   const DF fscd{S.fsc_hl[0], S.fsc_hl[1]};
-  const uint32_t* codes = a.p.img_code + S.img_base + S.tier_first[g.t] + g.img0;
-  const float* gain = a.p.img_gain + S.img_base + S.tier_first[g.t] + g.img0;
+  const uint32_t* codes = a.p.img_code + S.img_base + g.img_off + S.tier_first[g.t] + g.img0;
+  const float* gain = a.p.img_gain + S.img_base + g.img_off + S.tier_first[g.t] + g.img0;
   const float4* HI = a.p.dense_hi + S.dense_base;
   const float4* LO = a.p.dense_lo + S.dense_base;
   const int64_t kmax = S.n_dense - 2;  // last table index whose successor exists
@@ -638,7 +693,7 @@ __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const I
     an6[6 * ib + 3] = make_float4(dsx, dsy, dsz, gsl / (1.0f + gsl));
     an6[6 * ib + 4] = make_float4(sg[0], sg[1], sg[2], __int_as_float(int(k)));
     an6[6 * ib + 5] = make_float4(eps, Dfl, r2, 0.0f);
-    img_s[ib] = image_record(g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib));
+    put_image_record<kPaired>(img_s, ib, g.cnt, g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib));
   }
   __syncthreads();
   const int nk = g.nk;
@@ -678,7 +733,7 @@ __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const I
     }
   }
   __syncthreads();
-  records_from_phi<kThreads>(g, phi_s, rec_s);
+  records_from_phi<kThreads, kPaired>(g, phi_s, rec_s);
   *tmin_out = tmin;
   *tmax_out = tmax;
 }
@@ -749,6 +804,41 @@ __device__ __forceinline__ unsigned split_offset(const float2 rec, unsigned I4, 
   *w = Y - (q - kRound);
   *tau = fmaf(Y, -1.0f / kFarrowSegs, Dp);
   return (b & 3u) * unsigned(4 * kStride - 1) + b + (I4 + rmc4);
+}
+
+// Power-of-two scale of the half-precision powers 3 and 4 of the synthesis
+// rows. |z_q| <= (sum_k |c_q[k]|) max|x| for q = 3, 4 (zh_gain = the larger sum
+// over the segments), so s = 2^(14 - e) with C max|x| = m 2^e, m in [1/2, 1),
+// keeps every scaled value at or below 2^14 (half precision holds 65504) and
+// as high in its range as the bound allows (relative precision 2^-11 down to
+// 2^-14 of the bound). Exact powers of two: {s, 1/s}. A silent or non-finite
+// signal uses s = 1.
+__device__ __forceinline__ float2 zh_scale(const KernelArgs& a, int scene) {
+  const float mx = __uint_as_float(a.p.xmax[scene]) * a.zh_gain;
+  if (!(mx > 0.0f) || !(mx < 3.0e38f)) return make_float2(1.0f, 1.0f);
+  int e = 0;
+  const float m = frexpf(mx, &e);
+  int k = (m == 0.5f ? 15 : 14) - e;
+  k = max(-120, min(120, k));
+  return make_float2(ldexpf(1.0f, k), ldexpf(1.0f, -k));
+}
+
+// The bits of (lo, hi) rounded to half precision, as the 4th lane of a float4
+// row (moved, never used as a float).
+__device__ __forceinline__ float pack_half2(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return __uint_as_float(*reinterpret_cast<const unsigned*>(&h));
+}
+
+// Farrow polynomial (degree 4) from a synthesis row A = {z0, z1, z2, half2(s z3,
+// s z4)}: e = z0 + w (z1 + w (z2 + (w / s) (s z3 + w s z4))), ws = w / s.
+__device__ __forceinline__ float horner_zh(const float4 A, float w, float ws) {
+  const unsigned u = __float_as_uint(A.w);
+  const float2 h = __half22float2(*reinterpret_cast<const __half2*>(&u));
+  float e = fmaf(h.y, w, h.x);
+  e = fmaf(e, ws, A.z);
+  e = fmaf(e, w, A.y);
+  return fmaf(e, w, A.x);
 }
 
 // Farrow polynomial (degree 4) from the powers 0..3 (A) and 4 (B), Horner in w.

@@ -23,7 +23,7 @@ def oracle_scene(spec: W.SceneSpec, mic: int = 0, **override) -> oracle.Scene:
 # Precision envelope of a parity comparison: read positions within this many
 # samples of an integer may fall on either side in FP32 (the device's delays
 # are good to about 1e-6 samples).
-WRAP_DELTA = 1e-4
+WRAP_DELTA = 1e-5
 
 
 def beyond_envelope(a, ref, env):
@@ -33,6 +33,29 @@ def beyond_envelope(a, ref, env):
     ref = np.asarray(ref, np.float64)
     r = np.maximum(np.abs(a - ref) - np.asarray(env, np.float64), 0.0)
     return float(np.linalg.norm(r) / max(np.linalg.norm(ref), 1e-300))
+
+
+def tile_samples(n_out: int, tile: int, steps=(), mid: bool = True, edge_tiles: int = 8) -> np.ndarray:
+    """Output indices for a sampled full-size parity check: the first, middle
+    and last output of every output tile of `tile` samples (the synthesis work
+    item), and in `edge_tiles` tiles spread over the signal both edges of the
+    first two knot intervals (n mod N in {0, N - 1}) of every knot spacing N > 1
+    in `steps`."""
+    idx = []
+    for t0 in range(0, n_out, tile):
+        t1 = min(t0 + tile, n_out) - 1
+        idx += [t0, t1] + ([(t0 + t1) // 2] if mid else [])
+    n_tiles = (n_out + tile - 1) // tile
+    for k in np.linspace(0, n_tiles - 1, min(edge_tiles, n_tiles)).astype(int):
+        t0 = int(k) * tile
+        for N in steps:
+            if N <= 1:
+                continue
+            j = (t0 + N - 1) // N  # first knot at or after the tile start
+            for kn in (j, j + 1):
+                idx += [kn * N - 1, kn * N, kn * N + N - 1]
+    idx = np.unique(np.asarray(idx, np.int64))
+    return idx[(idx >= 0) & (idx < n_out)]
 
 
 def rel_l2(a, b):

@@ -148,6 +148,20 @@ def test_workspace_and_signal_checks_without_device():
     assert lib.msrc_synthesize(hs, 1, xs, n, ys, n, ctypes.c_void_p(257), fwd.value, None) == _lib.ERR_WORKSPACE
     zero = _lib.i64_array([0])
     assert lib.msrc_synthesize(hs, 1, xs, zero, ys, n, ctypes.c_void_p(256), fwd.value, None) == _lib.ERR_INVALID_ARG
+    # per-call tile configurations: the default's size, each configuration's
+    # own size, and ids out of range refused
+    fcfg = ctypes.c_size_t()
+    assert lib.msrc_workspace_size_cfg(hs, 1, n, n, _lib.TILE_DEFAULT, ctypes.byref(fcfg), None) == _lib.OK
+    assert fcfg.value == fwd.value
+    sizes = []
+    for c in range(lib.msrc_tile_configs()):
+        assert lib.msrc_workspace_size_cfg(hs, 1, n, n, c, ctypes.byref(fcfg), None) == _lib.OK
+        sizes.append(fcfg.value)
+    assert sizes[0] == fwd.value and len(set(sizes)) > 1
+    for bad in (lib.msrc_tile_configs(), 99):
+        assert lib.msrc_workspace_size_cfg(hs, 1, n, n, bad, ctypes.byref(fcfg), None) == _lib.ERR_INVALID_ARG
+        assert lib.msrc_synthesize_cfg(hs, 1, xs, n, ys, n, bad, ctypes.c_void_p(256), 1 << 30,
+                                       None) == _lib.ERR_INVALID_ARG
     lib.msrc_destroy_room(h)
 
 
@@ -265,3 +279,46 @@ def test_host_only_hooks_validate_arguments():
     assert lib.msrc_test_stall_window_copies(0) == _lib.OK
     f32, f64 = ctypes.c_double(), ctypes.c_double()
     assert lib.msrc_measure_alu_peaks(None, None, ctypes.byref(f32), ctypes.byref(f64)) == _lib.ERR_INVALID_ARG
+
+
+# Largest per-tap error of the device's Farrow table against the exact windowed
+# sinc (the oracle's tap weights) on a 1e5-point grid of fractional delays.
+# The synthesis table (4 segments x degree 4, Chebyshev nodes, float
+# coefficients) measures 0.80-0.91e-6 for L >= 16 and 1.1-1.4e-6 for L = 8;
+# the gradient kernel's degree-5 table 3e-8 to 7.4e-8. For one image and a
+# white signal the tap errors move the output by sqrt(sum_k dh_k^2) relative to
+# sqrt(sum_k h_k^2): at most 1.8e-6 (L >= 16) and 2.5e-6 (L = 8) at the worst
+# delay, and they oscillate in alpha and differ per tap, so summed over images
+# they stay near 3e-7 of the output: inside the 1e-5 parity bar.
+FARROW_PIN = {0: {8: 1.5e-6, "other": 1.0e-6}, 1: {8: 1e-7, "other": 1e-7}}
+
+
+@pytest.mark.parametrize("taps,window,beta", [(8, 0, 8.0), (16, 1, 8.0), (24, 1, 8.0), (32, 0, 8.0), (32, 1, 8.0),
+                                              (64, 1, 8.0), (32, 1, 4.0)])
+def test_device_farrow_table_against_oracle_taps(taps, window, beta):
+    lib = _lib.load()
+    st, h = _create(taps=taps, window=window, kaiser_beta=beta)
+    assert st == _lib.OK
+    alpha = (np.arange(100000) + 0.5) / 100000.0
+    sc = oracle.Scene(dims=(5.0, 4.0, 3.0), beta=(0.7,) * 6, mic=(2.5, 2.0, 1.2), K=0, fs=16000.0,
+                      tiers=[(2**31 - 1, 1)], taps=taps, window=window, kaiser_beta=beta)
+    exact = oracle.tap_weights(sc, alpha)  # (alpha, k + L/2)
+    seg = np.floor(4.0 * alpha).astype(int)
+    w = 4.0 * alpha - seg - 0.5
+    for which in (0, 1):
+        out = np.zeros(4 * 6 * taps, np.float32)
+        P = ctypes.c_int32()
+        assert lib.msrc_room_farrow_table(h, which, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                          ctypes.byref(P)) == _lib.OK
+        assert P.value == (5 if which == 0 else 6)
+        tab = out[:4 * P.value * taps].reshape(4, P.value, taps).astype(np.float64)
+        approx = np.zeros_like(exact)
+        for q in range(P.value - 1, -1, -1):  # Horner in w, per alpha's segment
+            approx = approx * w[:, None] + tab[seg, q, :]
+        err = float(np.max(np.abs(approx - exact)))
+        pin = FARROW_PIN[which][8 if taps == 8 else "other"]
+        assert err < pin, (which, err)
+        # the table is the fit of this room's kernel: a plausible mistake (a
+        # segment or a tap shifted by one) is far outside the pin
+        assert np.max(np.abs(approx[:, :-1] - exact[:, 1:])) > 100 * pin
+    lib.msrc_destroy_room(h)

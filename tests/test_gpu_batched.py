@@ -9,7 +9,7 @@ import torch
 from oracle import api as oracle
 from paper_2508_03065_gb300 import api
 from paper_2508_03065_gb300 import workloads as W
-from tests.scenes import oracle_scene, rel_l2
+from tests.scenes import oracle_scene, rel_l2, tile_samples
 
 pytestmark = pytest.mark.gpu
 
@@ -56,37 +56,35 @@ def test_autotuner_picks_and_caches(tmp_path):
     rooms = [api.Room.from_spec(s) for s in specs]
     xs = [torch.from_numpy(s.x).cuda() for s in specs]
     path = str(tmp_path / "tune.json")
-    try:
-        best = api.autotune(rooms, xs, reps=2, cache_path=path)
-        assert 0 <= best < api.tile_configs()
-        data = json.load(open(path))
-        (entry,) = data.values()
-        assert entry["best"] == best and min(v for v in entry["ms"] if v > 0) == entry["ms"][best]
-        assert api.autotune(rooms, xs, reps=2, cache_path=path) == best  # from the cache
-        y = api.synthesize(rooms, xs)[0]
-        ref = oracle.synthesize(oracle_scene(specs[0]), specs[0].x.astype(np.float64))
-        assert rel_l2(y[0].double().cpu().numpy(), ref) < 1e-5
-    finally:
-        api.set_tile_config(0)
+    before = api.synthesize(rooms, xs)[0].clone()
+    best = api.autotune(rooms, xs, reps=2, cache_path=path)
+    assert 0 <= best < api.tile_configs()
+    data = json.load(open(path))
+    (entry,) = data.values()
+    assert entry["best"] == best and min(v for v in entry["ms"] if v > 0) == entry["ms"][best]
+    assert api.autotune(rooms, xs, reps=2, cache_path=path) == best  # from the cache
+    y = api.synthesize(rooms, xs, tile_config=best)[0]
+    ref = oracle.synthesize(oracle_scene(specs[0]), specs[0].x.astype(np.float64))
+    assert rel_l2(y[0].double().cpu().numpy(), ref) < 1e-5
+    # the tuner returns its pick; calls without a configuration are unchanged
+    assert torch.equal(api.synthesize(rooms, xs)[0], before)
 
 
 def test_batched_config3_full_size_sampled():
     """All 256 batched scenes in one graph-replayed persistent launch, in the
     tile configuration the benchmark's autotuner picks for them (10), checked on
-    sampled outputs of every 8th scene that the oracle evaluates one by one."""
+    the first, middle and last output of every output tile and on knot-interval
+    edges of every 8th scene, which the oracle evaluates one by one."""
     specs = [W.config3_scene(s) for s in range(256)]
     rooms = [api.Room.from_spec(s) for s in specs]
     xs = [torch.from_numpy(s.x).cuda() for s in specs]
-    try:
-        api.set_tile_config(10)
-        b = api.Batch(rooms, xs)
-        ys = [y.clone() for y in b.run(True)]
-        b.stream.synchronize()
-    finally:
-        api.set_tile_config(0)
+    b = api.Batch(rooms, xs, tile_config=10)
+    ys = [y.clone() for y in b.run(True)]
+    b.stream.synchronize()
     for i in range(0, 256, 8):
         spec = specs[i]
-        idx = np.array([0, spec.n_in // 3, spec.n_in // 2, spec.n_in - 1], np.int64)
+        # every output tile of configuration 10 (1024 samples) and knot-interval edges
+        idx = tile_samples(spec.n_in, 1024, [N for _, N in spec.tier_steps()], edge_tiles=4)
         ref = oracle.y_at(oracle_scene(spec), spec.x.astype(np.float64), idx)
         got = ys[i][0].double().cpu().numpy()[idx]
         assert rel_l2(got, ref) < 1e-5 or np.max(np.abs(got - ref)) < 1e-9, i

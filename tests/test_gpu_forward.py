@@ -15,16 +15,17 @@ import torch
 from oracle import api as oracle
 from paper_2508_03065_gb300 import api
 from paper_2508_03065_gb300 import workloads as W
-from tests.scenes import WRAP_DELTA, beyond_envelope, max_length_scene, oracle_scene, rel_l2
+from tests.scenes import WRAP_DELTA, beyond_envelope, max_length_scene, oracle_scene, rel_l2, tile_samples
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
+TILE0 = 1536  # output samples of a work item in the default tile configuration (512 threads x 3 chunks)
 
 
-def gpu_run(specs, n_out=None):
+def gpu_run(specs, n_out=None, tile_config=None):
     rooms = [api.Room.from_spec(s) for s in specs]
     xs = [torch.from_numpy(s.x).cuda() for s in specs]
-    ys = api.synthesize(rooms, xs, n_out=n_out)
+    ys = api.synthesize(rooms, xs, n_out=n_out, tile_config=tile_config)
     torch.cuda.synchronize()
     return [y.cpu().numpy().astype(np.float64) for y in ys]
 
@@ -108,21 +109,33 @@ def test_bitwise_reproducible():
 def test_tile_configs_agree():
     spec = W.small_scene(seed=31, K=5, seconds=0.3)
     ref = oracle_full(spec)
-    try:
-        for cfg in range(api.tile_configs()):
-            api.set_tile_config(cfg)
-            y = gpu_run([spec])[0]
-            assert rel_l2(y[0], ref) < TOL, cfg
-    finally:
-        api.set_tile_config(0)
+    for cfg in range(api.tile_configs()):
+        y = gpu_run([spec], tile_config=cfg)[0]
+        assert rel_l2(y[0], ref) < TOL, cfg
+
+
+def test_per_call_tile_config_leaves_the_default():
+    # a call in its own configuration does not change what calls without one
+    # run in, and each configuration stays bitwise reproducible
+    spec = W.small_scene(seed=32, K=5, seconds=0.3)
+    d0 = gpu_run([spec])[0]
+    t0 = gpu_run([spec], tile_config=10)[0]
+    d1 = gpu_run([spec])[0]
+    t1 = gpu_run([spec], tile_config=10)[0]
+    assert np.array_equal(d0, d1) and np.array_equal(t0, t1)
+    assert np.array_equal(d0, gpu_run([spec], tile_config=0)[0])
+    with pytest.raises(api._lib.MsrcError):
+        gpu_run([spec], tile_config=api.tile_configs())
 
 
 def test_config2_full_size_sampled():
-    # order 20, 48 kHz, 4 s (92 168 images): checked on sampled outputs that
-    # the oracle evaluates one by one
+    # order 20, 48 kHz, 4 s (92 168 images): the first, middle and last output
+    # of every output tile and both edges of knot intervals of every tier, each
+    # evaluated by the oracle one by one
     spec = W.config2()
     y = gpu_run([spec])[0][0]
-    idx = np.concatenate([np.arange(0, 192000, 192000 // 24), [191999, 100, 101, 57000, 57001]])
+    idx = tile_samples(spec.n_in, TILE0, [N for _, N in spec.tier_steps()])
+    assert idx.size > 3 * (spec.n_in // TILE0)
     ref = oracle.y_at(oracle_scene(spec), spec.x.astype(np.float64), idx)
     assert rel_l2(y[idx], ref) < TOL
 
@@ -183,12 +196,16 @@ def test_moving_and_static_scenes_batched():
 
 def test_array_scene_full_size_sampled():
     """The 8-microphone array scene (order 25, 177 208 images, 10 s at 48 kHz,
-    Kaiser 64 taps) at full size, on sampled outputs of every microphone that
-    the oracle evaluates one by one."""
+    Kaiser 64 taps) at full size: the first and last output of every output
+    tile and both edges of knot intervals of every tier, on the microphone
+    that rotates with the tile index, each evaluated by the oracle one by
+    one."""
     spec = W.config5()
     y = gpu_run([spec])[0]
-    n = spec.n_in
-    idx = np.array([12345, 100000, 240001, 399999, n - 1])
-    for m in range(y.shape[0]):
-        ref = oracle.y_at(oracle_scene(spec, m), spec.x.astype(np.float64), idx)
-        assert rel_l2(y[m][idx], ref) < TOL, m
+    n_mics = y.shape[0]
+    idx = tile_samples(spec.n_in, TILE0, [N for _, N in spec.tier_steps()], mid=False)
+    mic_of = (idx // TILE0) % n_mics
+    for m in range(n_mics):
+        sel = idx[mic_of == m]
+        ref = oracle.y_at(oracle_scene(spec, m), spec.x.astype(np.float64), sel)
+        assert rel_l2(y[m][sel], ref) < TOL, m

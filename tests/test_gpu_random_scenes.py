@@ -7,7 +7,7 @@ rate, taps and tap-weight design (Hann, Kaiser, least-squares Farrow of order
 tiers (upsampling factor and kernel half-width), emission-time delays, a moving
 microphone array, one to three microphones and an output shorter or longer
 than the input. Parity bar: relative L2 <= 1e-5 per microphone beyond the
-oracle's precision envelope (read positions within 1e-4 samples of an integer
+oracle's precision envelope (read positions within 1e-5 samples of an integer
 may take either side; this only matters for the least-squares Farrow designs,
 whose taps jump there), and the device error word stays clear. The reverse-mode sweep draws from the same space
 without band-limited tiers and emission-time delays, and compares dL/dx for a

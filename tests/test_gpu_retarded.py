@@ -18,17 +18,17 @@ import torch
 from oracle import api as oracle
 from paper_2508_03065_gb300 import _lib, api
 from paper_2508_03065_gb300 import workloads as W
-from tests.scenes import oracle_scene, rel_l2
+from tests.scenes import oracle_scene, rel_l2, tile_samples
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
-def gpu_run(specs, n_out=None):
+def gpu_run(specs, n_out=None, tile_config=None):
     rooms = [api.Room.from_spec(s) for s in specs]
     xs = [torch.from_numpy(s.x).cuda() for s in specs]
     ws = api.Workspace()
-    ys = api.synthesize(rooms, xs, n_out=n_out, workspace=ws)
+    ys = api.synthesize(rooms, xs, n_out=n_out, workspace=ws, tile_config=tile_config)
     torch.cuda.synchronize()
     assert api.workspace_errors(ws) == 0
     return [y.cpu().numpy().astype(np.float64) for y in ys]
@@ -86,7 +86,7 @@ def test_batch_mixing_delay_models():
 def test_order20_emission_time_full_size_sampled():
     spec = replace(W.config2(), delay_model=1)
     y = gpu_run([spec])[0][0]
-    idx = np.concatenate([np.arange(0, 192000, 192000 // 24), [191999, 100, 101, 57000, 57001]])
+    idx = tile_samples(spec.n_in, 1536, [N for _, N, *_ in spec.tier_steps()])
     ref = oracle.y_at(oracle_scene(spec), spec.x.astype(np.float64), idx)
     assert rel_l2(y[idx], ref) < TOL
 
@@ -126,10 +126,6 @@ def test_emission_time_every_tile_config():
     """Every synthesis tile configuration gives the same emission-time result."""
     spec = replace(W.small_scene(seed=64, K=3, traj_kind=W.SPLINE, seconds=0.3), delay_model=1)
     ref = oracle_full(spec)
-    try:
-        for cfg in range(api.tile_configs()):
-            api.set_tile_config(cfg)
-            y = gpu_run([spec])[0]
-            assert rel_l2(y[0], ref) < TOL, cfg
-    finally:
-        api.set_tile_config(0)
+    for cfg in range(api.tile_configs()):
+        y = gpu_run([spec], tile_config=cfg)[0]
+        assert rel_l2(y[0], ref) < TOL, cfg

@@ -17,17 +17,17 @@ import torch
 from oracle import api as oracle
 from paper_2508_03065_gb300 import api
 from paper_2508_03065_gb300 import workloads as W
-from tests.scenes import oracle_scene, rel_l2
+from tests.scenes import oracle_scene, rel_l2, tile_samples
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
-def gpu_run(specs, n_out=None):
+def gpu_run(specs, n_out=None, tile_config=None):
     rooms = [api.Room.from_spec(s) for s in specs]
     xs = [torch.from_numpy(s.x).cuda() for s in specs]
     ws = api.Workspace()
-    ys = api.synthesize(rooms, xs, n_out=n_out, workspace=ws)
+    ys = api.synthesize(rooms, xs, n_out=n_out, workspace=ws, tile_config=tile_config)
     torch.cuda.synchronize()
     assert api.workspace_errors(ws) == 0
     return [y.cpu().numpy().astype(np.float64) for y in ys]
@@ -95,11 +95,14 @@ def test_batch_mixing_linear_and_upsampled_tiers():
 @pytest.mark.parametrize("rate,U", [(50.0, 10), (5.0, 100)])
 def test_order20_upsampled_full_size_sampled(rate, U):
     """The order-20, 48 kHz, 4 s scene (92 168 images) with its last tier on
-    band-limited knots, in the bench's launch configuration, on sampled outputs
-    the oracle evaluates one by one."""
+    band-limited knots, in the bench's launch configuration: the first, middle
+    and last output of every output tile and knot-interval edges, each evaluated
+    by the oracle one by one."""
     spec = W.config2_upsampled(rate, U)
     y = gpu_run([spec])[0][0]
-    idx = np.concatenate([np.arange(0, 192000, 192000 // 24), [191999, 100, 101, 57000, 57001]])
+    steps = spec.tier_steps()
+    # knot intervals and the virtual knots' intervals of the upsampled tier
+    idx = tile_samples(spec.n_in, 1536, [t[1] for t in steps] + [t[1] // t[2] for t in steps if len(t) > 2])
     ref = oracle.y_at(oracle_scene(spec), spec.x.astype(np.float64), idx)
     assert rel_l2(y[idx], ref) < TOL
 
@@ -122,10 +125,6 @@ def test_upsampled_every_tile_config():
     spec = W.small_scene(seed=21, K=3, traj_kind=W.CIRCLE, seconds=0.3,
                          tiers=[(1, 16000.0), (W.RHO_INF, 200.0, 10)])
     ref = oracle_full(spec)
-    try:
-        for cfg in range(api.tile_configs()):
-            api.set_tile_config(cfg)
-            y = gpu_run([spec])[0]
-            assert rel_l2(y[0], ref) < TOL, cfg
-    finally:
-        api.set_tile_config(0)
+    for cfg in range(api.tile_configs()):
+        y = gpu_run([spec], tile_config=cfg)[0]
+        assert rel_l2(y[0], ref) < TOL, cfg
