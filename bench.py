@@ -33,16 +33,16 @@ METRIC = "image-samples/s (forward, order-20 48 kHz)"
 UNIT = "image-samples/s"
 
 # Algorithmic work of the synthesis kernel per image-sample (signal-side Farrow,
-# 4 segments x degree 4): 5 prefiltered values gathered from shared memory.
-Z_BYTES_PER_IMAGE_SAMPLE = 5 * 4
+# 4 segments x degree 4): one 16-byte prefiltered row entry {z0, z1, z2, half2(z3, z4)}
+# gathered from shared memory.
+Z_BYTES_PER_IMAGE_SAMPLE = 16
 # FP32 operations per image-sample: delay interpolation 1 FMA (2), rounding and
-# local variable 3 adds (3), delay for the gain 1 FMA (2), gain 1 division (1),
+# local variable 3 adds (3), delay over gain 1 FMA (2), its reciprocal (1),
 # Farrow polynomial 4 FMA (8), accumulate 1 FMA (2) -> 18.
 FLOPS_PER_IMAGE_SAMPLE = 18
 # DRAM bytes (read + write) of one synthesis launch on this workload, from one
-# ncu capture of the full-size launch (28.87 MB read + 269.11 MB written, the
-# partial rows); None whenever the kernel changed since.
-K_SYNTH_TRAFFIC_BYTES = 28866816 + 269111040
+# ncu capture of the full-size launch; None whenever the kernel changed since.
+K_SYNTH_TRAFFIC_BYTES = None
 SM_COUNT = 152
 SMEM_BYTES_PER_CLK_PER_SM = 128
 FP32_LANES_PER_SM = 128

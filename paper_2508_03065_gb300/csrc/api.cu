@@ -438,11 +438,12 @@ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 struct Plan {
   std::vector<SceneDev> scenes;
   std::vector<int64_t> prefix[kUnitKinds];
-  int64_t totals[kUnitKinds] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t totals[kUnitKinds] = {};
   int end_bit = kSortGroupShift;
   // byte offsets in the workspace
   size_t off_desc = 0, off_keys_in = 0, off_keys_out = 0, off_vals_in = 0, off_vals_out = 0;
   size_t off_sort = 0, sort_bytes = 0, off_code = 0, off_gain = 0, off_knots = 0;
+  size_t off_mcode = 0, off_mgain = 0, off_moff = 0;
   size_t off_z = 0, off_zp = 0, off_part = 0, fwd_bytes = 0, desc_bytes = 0, off_arr = 0, off_xmax = 0;
   // reverse mode
   bool backward = false;
@@ -485,7 +486,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   const int T = tc.threads * tc.chunks;
   P.scenes.resize(n);
   for (auto& v : P.prefix) v.assign(n + 1, 0);
-  int64_t img_acc = 0, knot_acc = 0, z_acc = 0, part_acc = 0, group_acc = 0;
+  int64_t img_acc = 0, knot_acc = 0, z_acc = 0, part_acc = 0, group_acc = 0, master_acc = 0;
   int64_t dxb_acc = 0, kslot_acc = 0, bpart_acc = 0, bl_acc = 0, dense_acc = 0;
   bool any_moving = false;
   for (int s = 0; s < n; ++s) {
@@ -620,6 +621,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     }
     S.n_blocks = blk;
     S.img_base = img_acc;
+    S.master_base = master_acc;
     // time groups: one per kTimeGroupSamples of output in forward mode; one
     // (ordered at the middle of the trajectory) in reverse mode and when a
     // tier is upsampled (its knot-delay rows follow the first group's order)
@@ -724,12 +726,13 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     const int64_t u_bl = bl_units;  // (mic, image) rows of FP64 knot delays of upsampled tiers
     if (int64_t(S.n_mics) * S.n_blocks * S.n_tiles >= (int64_t(1) << 31))
       return fail(MSRC_ERR_UNSUPPORTED, "room %d: more than 2^31 work items", s);
-    const int64_t u[kUnitKinds] = {u_enum, u_knots, u_rec, u_z, u_item, u_red, u_bl, u_dense};
+    const int64_t u[kUnitKinds] = {u_enum, u_knots, u_rec, u_z, u_item, u_red, u_bl, u_dense, S.n_images};
     for (int k = 0; k < kUnitKinds; ++k) {
       P.prefix[k][s + 1] = P.prefix[k][s] + u[k];
       P.totals[k] += u[k];
     }
     img_acc += u_enum;
+    master_acc += S.n_images;
     knot_acc += kfirst;
     z_acc += int64_t(kFarrowSegs) * S.z_len;
     part_acc += int64_t(S.n_mics) * S.n_blocks * S.n_out;
@@ -752,6 +755,9 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.sort_bytes = sort_temp_bytes(int64_t(I), P.end_bit);
   P.off_sort = off; off = align256(off + P.sort_bytes);
   P.off_code = off; off = align256(off + 4 * I);
+  P.off_mcode = off; off = align256(off + 4 * size_t(master_acc));
+  P.off_mgain = off; off = align256(off + 4 * size_t(master_acc));
+  P.off_moff = off; off = align256(off + 16 * size_t(master_acc));
   P.off_gain = off; off = align256(off + 4 * I);
   P.off_knots = off; off = align256(off + 24 * size_t(knot_acc));
   P.off_arr = off; off = align256(off + (any_moving ? 24 * size_t(knot_acc) : 0));
@@ -801,6 +807,9 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.sort_temp_bytes = P.sort_bytes;
   a.p.img_code = reinterpret_cast<uint32_t*>(ws + P.off_code);
   a.p.img_gain = reinterpret_cast<float*>(ws + P.off_gain);
+  a.p.m_code = reinterpret_cast<uint32_t*>(ws + P.off_mcode);
+  a.p.m_gain = reinterpret_cast<float*>(ws + P.off_mgain);
+  a.p.m_off = reinterpret_cast<float4*>(ws + P.off_moff);
   a.p.knot_pos = reinterpret_cast<double*>(ws + P.off_knots);
   a.p.arr_pos = reinterpret_cast<double*>(ws + P.off_arr);
   a.p.knot_hl = reinterpret_cast<float4*>(ws + P.off_knot_hl);
@@ -856,6 +865,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
     a.tab.red_prefix = pre + 5 * n1;
     a.tab.bl_prefix = pre + 6 * n1;
     a.tab.dense_prefix = pre + 7 * n1;
+    a.tab.img_prefix = pre + 8 * n1;
   }
 }
 

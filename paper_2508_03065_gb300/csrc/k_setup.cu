@@ -1,10 +1,11 @@
 // Setup kernels of the synthesis path:
 //   k_group_pos    source position at the middle of every time group (sort keys)
+//   k_images       per image: code, gain and offset from the microphone
 //   k_enumerate    image set of every scene (Sec. II-A, Eq. 1; lattice |n|_1 <= K,
 //                  8 parities), one copy per time group of the scene, with a sort
 //                  key (scene and time group, tier, distance at the group's middle)
 //   (radix sort)   images ordered by key
-//   k_image_table  packed image codes and gains beta_i / (4 pi) * fs / c
+//   k_image_table  per time group: packed image codes and gains beta_i / (4 pi) * fs / c
 //   k_traj_knots   source position s(t_j) (and the array displacement a(t_j) - a(0)
 //                  when the microphones move) at every knot of every tier, FP64
 //                  (Sec. II-C: trajectory sampled at the tier's spatial rate)
@@ -106,16 +107,16 @@ __global__ void k_group_pos(const __grid_constant__ KernelArgs a) {
   }
 }
 
-// One unit per (scene, time group, image): the group's copy of the image set
-// with its sort key (group, tier, distance at the group's middle).
-__global__ void k_enumerate(const __grid_constant__ KernelArgs a) {
+// One unit per image of a scene (lattice order): its packed code, gain
+// beta_i / (4 pi) * fs / c (Allen-Berkley product, FP64) and, for the sort
+// keys of every time group, its offset 2 n o L - m from the first microphone
+// (FP32) with the parity bits and the tier.
+__global__ void k_images(const __grid_constant__ KernelArgs a) {
   const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (gid >= a.totals[0]) return;
-  int64_t local;
-  const int s = locate(a, a.tab.enum_prefix, gid, &local);
+  if (gid >= a.totals[8]) return;
+  int64_t unit;
+  const int s = locate(a, a.tab.img_prefix, gid, &unit);
   const SceneDev& S = scene_of(a, s);
-  const int64_t grp = local / S.n_images;
-  const int64_t unit = local - grp * S.n_images;  // the image within the group's copy
   int li = int(unit >> 3);
   const int pb = int(unit & 7);
   const int K = S.K;
@@ -140,40 +141,64 @@ __global__ void k_enumerate(const __grid_constant__ KernelArgs a) {
   int rho = 0;
   for (int d = 0; d < 3; ++d) rho += abs(2 * n[d] - p[d]);
   const int tier = tier_of(S, rho);
-  // distance to the first microphone at the middle of the time group (source
-  // position and array displacement there from the host-built table)
-  const double* gp = a.p.gpos + 6 * (S.gpos_base + grp);
-  double acc = 0.0;
+  // beta_i = prod_d beta_{d,0}^{|n_d - p_d|} beta_{d,1}^{|n_d|} (Allen-Berkley)
+  double b = 1.0;
   for (int d = 0; d < 3; ++d) {
-    const double v = (1.0 - 2.0 * p[d]) * gp[d] + 2.0 * n[d] * S.dims[d] - (S.mics[0][d] + gp[3 + d]);
-    acc += v * v;
+    const int e0 = abs(n[d] - p[d]), e1 = abs(n[d]);
+    for (int q = 0; q < e0; ++q) b *= S.beta[2 * d];
+    for (int q = 0; q < e1; ++q) b *= S.beta[2 * d + 1];
+  }
+  const int64_t m = S.master_base + unit;
+  a.p.m_code[m] = pack_image(nx, ny, nz, pb);
+  a.p.m_gain[m] = float(b / (4.0 * 3.14159265358979323846) * S.fs_over_c);
+  float o[3];
+  for (int d = 0; d < 3; ++d) o[d] = float(2.0 * n[d] * S.dims[d] - S.mics[0][d]);
+  a.p.m_off[m] = make_float4(o[0], o[1], o[2], __int_as_float(pb | (tier << 4)));
+}
+
+// One unit per (scene, time group, image): the sort key (time group, tier,
+// distance to the first microphone at the group's middle) and the image's
+// index in the scene's lattice order.
+__global__ void k_enumerate(const __grid_constant__ KernelArgs a) {
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= a.totals[0]) return;
+  int64_t local;
+  const int s = locate(a, a.tab.enum_prefix, gid, &local);
+  const SceneDev& S = scene_of(a, s);
+  const int64_t grp = local / S.n_images;
+  const int64_t unit = local - grp * S.n_images;  // the image within the group's copy
+  const float4 o = a.p.m_off[S.master_base + unit];
+  const int bits = __float_as_int(o.w);
+  const int tier = bits >> 4;
+  // source position and array displacement at the group's middle; FP32 is
+  // enough for an ordering key
+  const double* gp = a.p.gpos + 6 * (S.gpos_base + grp);
+  const float ov[3] = {o.x, o.y, o.z};
+  float acc = 0.0f;
+  for (int d = 0; d < 3; ++d) {
+    const float sd = float(gp[d]);
+    const float v = ((bits >> d) & 1 ? -sd : sd) + ov[d] - float(gp[3 + d]);
+    acc = fmaf(v, v, acc);
   }
   // distance in 24 bits (units of 2^-12 m up to 4 km): the key only orders
   // images, and fewer key bits are fewer radix passes
-  const double dist = fmin(sqrt(acc), 4095.99);
-  const uint64_t dq = uint64_t(dist * 4096.0);
+  const float dist = fminf(sqrtf(acc), 4095.99f);
+  const uint64_t dq = uint64_t(dist * 4096.0f);
   a.p.keys_in[gid] = (uint64_t(S.sort_group0 + grp) << kSortGroupShift) | (uint64_t(tier) << 24) | dq;
-  a.p.vals_in[gid] = pack_image(nx, ny, nz, pb);
+  a.p.vals_in[gid] = uint32_t(unit);
 }
 
+// The time groups' image tables in sorted order: code and gain gathered from
+// the per-image table.
 __global__ void k_image_table(const __grid_constant__ KernelArgs a) {
   const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (gid >= a.totals[0]) return;
   int64_t local;
   const int s = locate(a, a.tab.enum_prefix, gid, &local);
   const SceneDev& S = scene_of(a, s);
-  const uint32_t code = a.p.vals_out[gid];
-  int n[3], p[3];
-  unpack_image(code, n, p);
-  // beta_i = prod_d beta_{d,0}^{|n_d - p_d|} beta_{d,1}^{|n_d|} (Allen-Berkley)
-  double b = 1.0;
-  for (int d = 0; d < 3; ++d) {
-    const int e0 = abs(n[d] - p[d]), e1 = abs(n[d]);
-    for (int r = 0; r < e0; ++r) b *= S.beta[2 * d];
-    for (int r = 0; r < e1; ++r) b *= S.beta[2 * d + 1];
-  }
-  a.p.img_code[gid] = code;
-  a.p.img_gain[gid] = float(b / (4.0 * 3.14159265358979323846) * S.fs_over_c);
+  const int64_t m = S.master_base + a.p.vals_out[gid];
+  a.p.img_code[gid] = a.p.m_code[m];
+  a.p.img_gain[gid] = a.p.m_gain[m];
 }
 
 __global__ void k_traj_knots(const __grid_constant__ KernelArgs a) {
@@ -314,6 +339,7 @@ cudaError_t launch_setup(const KernelArgs& a, cudaStream_t st) {
   const int T = 256;
   if (a.totals[0] > 0) {
     k_group_pos<<<dim3(unsigned((a.max_time_groups + 63) / 64), unsigned(a.n_scenes)), 64, 0, st>>>(a);
+    k_images<<<blocks_for(a.totals[8], T), T, 0, st>>>(a);
     k_enumerate<<<blocks_for(a.totals[0], T), T, 0, st>>>(a);
     int end_bit = kSortGroupShift;
     while ((int64_t(1) << (end_bit - kSortGroupShift)) < a.n_sort_groups) ++end_bit;

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kPreThreads) k_prefilter(const __grid_constant
 #pragma unroll
     for (int sg = 0; sg < kFarrowSegs; ++sg) {
       const float* c = acc + sg * kCoef;
-      zq[int64_t(sg) * S.z_len] = make_float4(c[0], c[1], c[2], pack_half2(c[3] * sc, c[4] * sc));
+      zq[int64_t(sg) * S.z_len] = make_float4(c[0] * sc, c[1] * sc, c[2] * sc, pack_half2(c[3] * sc, c[4] * sc));
     }
   } else {
 #pragma unroll
@@ -142,7 +142,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // Unchecked reads index the window by byte offset (split_offset's form): the
 // offset of the power-4 value, 4 times it for the powers 0..3.
 template <int kStride, bool kChecked>
-__device__ __forceinline__ float2 pair_sample(const float4* zq, float2 inv2, const float4 R, const float4 AB,
+__device__ __forceinline__ float2 pair_sample(const float4* zq, const float4 R, const float4 AB,
                                               const int2 I4, float2 rf2, unsigned rmc4, int rmj, unsigned wmax,
                                               float2 acc) {
   const float2 Y = __ffma2_rn(rf2, make_float2(R.z, R.w), make_float2(R.x, R.y));
@@ -170,8 +170,7 @@ __device__ __forceinline__ float2 pair_sample(const float4* zq, float2 inv2, con
   const unsigned char* zqb = reinterpret_cast<const unsigned char*>(zq);
   const float4 A0 = *reinterpret_cast<const float4*>(zqb + 4u * o0);
   const float4 A1 = *reinterpret_cast<const float4*>(zqb + 4u * o1);
-  const float2 ws = __fmul2_rn(w, inv2);  // w / zh_scale for the half-precision powers
-  const float e0 = horner_zh(A0, w.x, ws.x), e1 = horner_zh(A1, w.y, ws.y);
+  const float e0 = horner_zh(A0, w.x), e1 = horner_zh(A1, w.y);  // s e (rows scaled by s, gains by 1/s)
   return __ffma2_rn(make_float2(g0, g1), make_float2(e0, e1), acc);
 }
 
@@ -181,7 +180,7 @@ __device__ __forceinline__ float2 pair_sample(const float4* zq, float2 inv2, con
 // kOne: every chunk of this lane lies in one knot interval (warp-uniform), so
 // one record load per pair serves all chunks.
 template <int kStride, int kChunks, int kUnroll, bool kChecked, bool kOne>
-__device__ __forceinline__ void gather_pairs(const float4* zq, float2 inv2, const float4* rec4,
+__device__ __forceinline__ void gather_pairs(const float4* zq, const float4* rec4,
                                              const float4* ab_s, const int2* i4_s, int cntp, const int* jc,
                                              const int* rmj, const float* rf, unsigned wmax, float2* acc) {
   unsigned rmc4[kChunks];
@@ -202,7 +201,7 @@ __device__ __forceinline__ void gather_pairs(const float4* zq, float2 inv2, cons
       const float4 R0 = row[0][p + u];
 #pragma unroll
       for (int c = 0; c < kChunks; ++c)
-        acc[c] = pair_sample<kStride, kChecked>(zq, inv2, (kOne || c == 0) ? R0 : row[c][p + u], AB, I4, rf2[c],
+        acc[c] = pair_sample<kStride, kChecked>(zq, (kOne || c == 0) ? R0 : row[c][p + u], AB, I4, rf2[c],
                                                 rmc4[c], rmj[c], wmax, acc[c]);
     }
   }
@@ -212,7 +211,7 @@ __device__ __forceinline__ void gather_pairs(const float4* zq, float2 inv2, cons
     const float4 R0 = row[0][p];
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)
-      acc[c] = pair_sample<kStride, kChecked>(zq, inv2, (kOne || c == 0) ? R0 : row[c][p], AB, I4, rf2[c], rmc4[c],
+      acc[c] = pair_sample<kStride, kChecked>(zq, (kOne || c == 0) ? R0 : row[c][p], AB, I4, rf2[c], rmc4[c],
                                               rmj[c], wmax, acc[c]);
   }
 }
@@ -262,17 +261,19 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
     const ItemGeom g = item_geometry(S, li, kTile);
 
     // --- delay knots of the block over the tile (records in shared memory)
+    // the rows are scaled by s (zh_scale), so the image gains are scaled by 1/s
+    const float gscale = zh_scale(a, s).y;
     float tmin, tmax;
     int cnt = g.cnt;
     if (S.delay_model == 1) {
-      item_records_ret<kThreads, true>(a, S, g, rec_s, img_s, u_s, an6_s, phi_r, &tmin, &tmax);
+      item_records_ret<kThreads, true>(a, S, g, rec_s, img_s, u_s, an6_s, phi_r, &tmin, &tmax, gscale);
     } else if (S.tier_up[g.t] > 1) {
       // band-limited knot upsampling: its scratch takes the z window
       if (!item_records_bl<kThreads, true>(a, S, g, rec_s, img_s, reinterpret_cast<float*>(smem4),
-                                           int64_t(kFarrowSegs) * kWcap * 4, &tmin, &tmax))
+                                           int64_t(kFarrowSegs) * kWcap * 4, &tmin, &tmax, gscale))
         cnt = 0;
     } else {
-      item_records<kThreads, true>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax);
+      item_records<kThreads, true>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax, gscale);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -322,9 +323,6 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
     const float4* ab_s = reinterpret_cast<const float4*>(img_s);
     const int2* i4_s = reinterpret_cast<const int2*>(ab_s + cntp);
     const float4* zqg = a.p.zq + S.z_base;
-    // scale of the half-precision powers 3 and 4 (see zh_scale), as a pair
-    const float inv_s = zh_scale(a, s).y;
-    const float2 inv2 = make_float2(inv_s, inv_s);
 
     // --- the window [m_lo, m_lo + width) in passes of at most kWcap columns
     for (int p0 = 0; p0 < width; p0 += kWcap) {
@@ -364,13 +362,13 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       constexpr int kPairUnroll = kUnroll >= 2 ? kUnroll / 2 : 1;
       if (width <= kWcap) {
         if (one)
-          gather_pairs<kWcap, kChunks, kPairUnroll, false, true>(zq_s, inv2, rec4, ab_s, i4_s, cntp, jc, rmj, rf,
+          gather_pairs<kWcap, kChunks, kPairUnroll, false, true>(zq_s, rec4, ab_s, i4_s, cntp, jc, rmj, rf,
                                                                  wmax, acc);
         else
-          gather_pairs<kWcap, kChunks, kPairUnroll, false, false>(zq_s, inv2, rec4, ab_s, i4_s, cntp, jc, rmj, rf,
+          gather_pairs<kWcap, kChunks, kPairUnroll, false, false>(zq_s, rec4, ab_s, i4_s, cntp, jc, rmj, rf,
                                                                   wmax, acc);
       } else {
-        gather_pairs<kWcap, kChunks, kPairUnroll, true, false>(zq_s, inv2, rec4, ab_s, i4_s, cntp, jc, rmj, rf,
+        gather_pairs<kWcap, kChunks, kPairUnroll, true, false>(zq_s, rec4, ab_s, i4_s, cntp, jc, rmj, rf,
                                                                wmax, acc);
       }
     }

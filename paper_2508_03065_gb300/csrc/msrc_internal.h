@@ -97,6 +97,7 @@ struct SceneDev {
   float mics_hl[MSRC_MAX_MICS][3][2];
   float fsc_hl[2];
   int64_t img_base;                        // first entry of this scene in the image table
+  int64_t master_base;                     // first entry in the per-image (lattice order) tables
   // time groups: the forward synthesis orders the images separately for every
   // group of tile_group consecutive output tiles (by tier, then distance at the
   // group's middle), so that the images of a block stay close in delay over the
@@ -157,6 +158,7 @@ struct LaunchTables {
   const int64_t* red_prefix;     // reduction units
   const int64_t* bl_prefix;      // knot delays of upsampled tiers
   const int64_t* dense_prefix;   // source path table entries (emission-time delays)
+  const int64_t* img_prefix;     // images (lattice order, once per scene)
 };
 // Image table units of the enumeration and sort: time groups x images. Sort
 // key: (scene's time group << kSortGroupShift) | (tier << 24) | distance (24 bits).
@@ -172,6 +174,9 @@ struct DevicePtrs {
   void* sort_temp;
   size_t sort_temp_bytes;
   uint32_t* img_code;            // packed lattice triple and parity
+  uint32_t* m_code;              // per image in lattice order: packed code,
+  float* m_gain;                 //   gain beta_i / (4 pi) * fs / c,
+  float4* m_off;                 //   2 n o L - m (FP32) and parity bits | tier << 4
   double* gpos;                  // per (scene, time group): source position and array
                                  // displacement at the group's middle (6 doubles), sort keys
   float* img_gain;               // beta_i / (4 pi)
@@ -208,13 +213,13 @@ struct DevicePtrs {
 };
 constexpr int kParamPartialsPerScene = 32 * 48;
 
-constexpr int kUnitKinds = 8;
+constexpr int kUnitKinds = 9;
 
 struct KernelArgs {
   SceneDev scene0;               // used when n_scenes == 1
   const SceneDev* scenes;        // used when n_scenes > 1
   int32_t n_scenes;
-  int64_t totals[kUnitKinds];    // total units per kernel kind (enum, knots, rec, z, item, red, bl, dense)
+  int64_t totals[kUnitKinds];    // total units per kernel kind (enum, knots, rec, z, item, red, bl, dense, img)
   LaunchTables tab;
   DevicePtrs p;
   float farrow[kFarrowSegs][kFarrowCoef][kMaxTaps];  // coefficients c[s][q][k + L/2] of the powers of w

@@ -303,7 +303,7 @@ __device__ __forceinline__ void put_image_record(int4* img_s, int ib, int cnt, i
 template <int kThreads, bool kPaired = false>
 __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                              int4* img_s, float4* u_s, float4* um_s, float4* anc_s, float* phi_s,
-                             float* tmin_out, float* tmax_out) {
+                             float* tmin_out, float* tmax_out, float gscale = 1.0f) {
   // knot positions and array displacements as double-float pairs; increments
   // from the anchor knot jf: hi differences of nearby positions are exact
   const int64_t kj = S.knot_base[g.t] + g.jf;
@@ -346,7 +346,7 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     anc_s[2 * ib] = A;
     anc_s[2 * ib + 1] = make_float4(B.x, B.y, 0.0f, 0.0f);
     anc_s[2 * g.cnt + ib] = SG;
-    put_image_record<kPaired>(img_s, ib, g.cnt, g.jf * g.N - int(B.y), B.y, __ldg(gain + ib));
+    put_image_record<kPaired>(img_s, ib, g.cnt, g.jf * g.N - int(B.y), B.y, __ldg(gain + ib) * gscale);
   }
   __syncthreads();
   // relative delay phi at every knot of every image (once per knot), then the
@@ -397,7 +397,8 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
 // is false (the caller then treats the block as empty).
 template <int kThreads, bool kPaired = false>
 __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
-                                int4* img_s, float* scr, int64_t cap, float* tmin_out, float* tmax_out) {
+                                int4* img_s, float* scr, int64_t cap, float* tmin_out, float* tmax_out,
+                                float gscale = 1.0f) {
   const int U = S.tier_up[g.t];
   const int Q = S.up_q;
   const int nk = g.nk;
@@ -433,7 +434,7 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
     const float Dfl = df_floor(DF{an.x, an.y});  // the anchor, knot floor(jf / U)
     if (jr == 0) {
       dfl_s[ib] = Dfl;
-      put_image_record<kPaired>(img_s, ib, g.cnt, g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib));
+      put_image_record<kPaired>(img_s, ib, g.cnt, g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib) * gscale);
     }
     const float2* tv = row + (j0_first + jr - Q + 1);  // knots j0 - Q + 1 .. j0 + Q
     const DF t0{tv[Q - 1].x, tv[Q - 1].y};
@@ -556,7 +557,7 @@ __device__ __forceinline__ float ret_increment(const RetAnchor& r, const float4 
 template <int kThreads, bool kPaired = false>
 __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                                  int4* img_s, float4* um_s, float4* an6, float* phi_s, float* tmin_out,
-                                 float* tmax_out) {
+                                 float* tmax_out, float gscale = 1.0f) {
   const bool moving = S.arr_moving != 0;
   const int64_t kj = S.knot_base[g.t] + g.jf;
   const float4* ahl = a.p.arr_hl + 2 * kj;
@@ -693,7 +694,7 @@ __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const I
     an6[6 * ib + 3] = make_float4(dsx, dsy, dsz, gsl / (1.0f + gsl));
     an6[6 * ib + 4] = make_float4(sg[0], sg[1], sg[2], __int_as_float(int(k)));
     an6[6 * ib + 5] = make_float4(eps, Dfl, r2, 0.0f);
-    put_image_record<kPaired>(img_s, ib, g.cnt, g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib));
+    put_image_record<kPaired>(img_s, ib, g.cnt, g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib) * gscale);
   }
   __syncthreads();
   const int nk = g.nk;
@@ -806,13 +807,14 @@ __device__ __forceinline__ unsigned split_offset(const float2 rec, unsigned I4, 
   return (b & 3u) * unsigned(4 * kStride - 1) + b + (I4 + rmc4);
 }
 
-// Power-of-two scale of the half-precision powers 3 and 4 of the synthesis
-// rows. |z_q| <= (sum_k |c_q[k]|) max|x| for q = 3, 4 (zh_gain = the larger sum
-// over the segments), so s = 2^(14 - e) with C max|x| = m 2^e, m in [1/2, 1),
-// keeps every scaled value at or below 2^14 (half precision holds 65504) and
-// as high in its range as the bound allows (relative precision 2^-11 down to
-// 2^-14 of the bound). Exact powers of two: {s, 1/s}. A silent or non-finite
-// signal uses s = 1.
+// Power-of-two scale of the synthesis rows, chosen for their half-precision
+// powers 3 and 4. |z_q| <= (sum_k |c_q[k]|) max|x| for q = 3, 4 (zh_gain = the
+// larger sum over the segments), so s = 2^(14 - e) with C max|x| = m 2^e,
+// m in [1/2, 1), keeps every scaled value at or below 2^14 (half precision
+// holds 65504) and as high in its range as the bound allows (relative
+// precision 2^-11 down to 2^-14 of the bound). All five powers are stored
+// times s and the image gains times 1/s (exact powers of two): {s, 1/s}. A
+// silent or non-finite signal uses s = 1.
 __device__ __forceinline__ float2 zh_scale(const KernelArgs& a, int scene) {
   const float mx = __uint_as_float(a.p.xmax[scene]) * a.zh_gain;
   if (!(mx > 0.0f) || !(mx < 3.0e38f)) return make_float2(1.0f, 1.0f);
@@ -830,13 +832,13 @@ __device__ __forceinline__ float pack_half2(float lo, float hi) {
   return __uint_as_float(*reinterpret_cast<const unsigned*>(&h));
 }
 
-// Farrow polynomial (degree 4) from a synthesis row A = {z0, z1, z2, half2(s z3,
-// s z4)}: e = z0 + w (z1 + w (z2 + (w / s) (s z3 + w s z4))), ws = w / s.
-__device__ __forceinline__ float horner_zh(const float4 A, float w, float ws) {
+// Farrow polynomial (degree 4) from a synthesis row A = {s z0, s z1, s z2,
+// half2(s z3, s z4)}, Horner in w: s e (the caller's gains carry the 1/s).
+__device__ __forceinline__ float horner_zh(const float4 A, float w) {
   const unsigned u = __float_as_uint(A.w);
   const float2 h = __half22float2(*reinterpret_cast<const __half2*>(&u));
   float e = fmaf(h.y, w, h.x);
-  e = fmaf(e, ws, A.z);
+  e = fmaf(e, w, A.z);
   e = fmaf(e, w, A.y);
   return fmaf(e, w, A.x);
 }
