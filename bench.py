@@ -41,8 +41,15 @@ Z_BYTES_PER_IMAGE_SAMPLE = 16
 # Farrow polynomial 4 FMA (8), accumulate 1 FMA (2) -> 18.
 FLOPS_PER_IMAGE_SAMPLE = 18
 # DRAM bytes (read + write) of one synthesis launch on this workload, from one
-# ncu capture of the full-size launch; None whenever the kernel changed since.
-K_SYNTH_TRAFFIC_BYTES = None
+# ncu capture of the full-size launch (35.77 MB read + 287.40 MB written, the
+# partial rows); None whenever the kernel changed since.
+K_SYNTH_TRAFFIC_BYTES = 35769088 + 287402752
+# ncu figures of the same kernel (the full section set on the 1 s version of
+# this scene, --clock-control none; profiles/k_synth_order20_48k.md): FP32 pipe
+# utilisation beside the flop-count roofline below. None once the kernel changed.
+K_SYNTH_NCU = {"fma_pipe_active_pct": 49.6, "fmaheavy_pipe_active_pct": 49.8, "issue_active_pct": 69.1,
+               "thread_instructions_per_image_sample": 19.9, "shared_wavefronts_per_sm_cycle": 0.74,
+               "source": "ncu --set full on the 1 s scene, k_synth<256, 3, 1440, 2048, 256, 8>"}
 SM_COUNT = 152
 SMEM_BYTES_PER_CLK_PER_SM = 128
 FP32_LANES_PER_SM = 128
@@ -236,9 +243,10 @@ def workload_config(spec):
 def partial_bytes(spec, tier_counts):
     """Bytes of the synthesis partial sums of one step: one float per
     (microphone, image block, output sample); blocks per tier from the record
-    capacity of the default tile configuration (4096 records over tiles of
-    1536 samples, at most 256 images, an even count)."""
-    T, reccap, bmax = 1536, 4096, 256
+    capacity of the tile configuration the library picks for this scene
+    (configuration 11: 2048 records over tiles of 768 samples, at most 256
+    images, an even count)."""
+    T, reccap, bmax = 768, 2048, 256
     blocks = 0
     for (rho, n_step), cnt in zip(spec.tier_steps(), tier_counts):
         B = max(1, min(bmax, reccap // ((T - 1) // n_step + 2)))
@@ -354,6 +362,7 @@ def run_gpu(args):
                      "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x median SM "
                                     f"clock {sm_mhz:.0f} MHz under load (derived, not measured)",
                      "flops_per_image_sample": FLOPS_PER_IMAGE_SAMPLE,
+                     "ncu": K_SYNTH_NCU if args.seconds is None else None,
                      "measured_peaks": {"fp32_tflops": peak32, "fp64_tflops": peak64,
                                         "frac_of_measured_fp32": fp32 / peak32,
                                         "how": "independent FMA chains in every thread of a full grid, best of "
@@ -610,10 +619,11 @@ def run_e1(args, torch, api, W):
 
 
 def launches_per_step():
-    # enumerate, image table, trajectory knots, prefilter, synthesis, reduction
-    # + the radix sort's kernels (histogram, exclusive sum, 5 onesweep passes
-    # for a 34-bit key); counted from the ncu launch list of this command
-    return 6 + 7
+    # time-group positions, per-image table, sort keys, image tables, trajectory
+    # knots, max |x|, prefilter, synthesis, reduction + the radix sort's kernels
+    # (histogram, exclusive sum, 4 onesweep passes for the 30-bit keys of 16
+    # time groups); counted from the ncu launch list of this command
+    return 9 + 6
 
 
 def run_only(args):

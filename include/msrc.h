@@ -207,7 +207,10 @@ msrc_status msrc_workspace_size(const msrc_room_t* rooms, int32_t n_rooms,
  * must share taps, window and kaiser_beta. n_rooms > 1 runs every scene in the
  * same launches (one persistent synthesis launch over a work queue).
  * workspace_dev: >= msrc_workspace_size(...).fwd_bytes, 256-byte aligned.
- * The result is bitwise reproducible for the same inputs and workspace size. */
+ * The result is bitwise reproducible for the same inputs and tile configuration;
+ * a batched call equals the single calls of its scenes bitwise when both run in
+ * the same tile configuration (name one: the automatic default may choose
+ * differently for a batch and for one of its scenes). */
 msrc_status msrc_synthesize(const msrc_room_t* rooms, int32_t n_rooms,
                             const float* const* x_dev, const int64_t* n_in,
                             float* const* y_dev, const int64_t* n_out,
@@ -215,14 +218,18 @@ msrc_status msrc_synthesize(const msrc_room_t* rooms, int32_t n_rooms,
 
 /* Tile configuration of a call (the synthesis launch's CTA shape, window and
  * record capacity; msrc_tile_configs() lists how many exist):
- * MSRC_TILE_DEFAULT = the process default (msrc_set_tile_config, initially 0),
- * else 0 .. msrc_tile_configs() - 1. The _cfg entry points take it per call, so
+ * MSRC_TILE_DEFAULT = the process default (msrc_set_tile_config, initially
+ * MSRC_TILE_AUTO); MSRC_TILE_AUTO = chosen from the call's knot layout (tiles
+ * of 1024 samples with room for many interval records when most images sit on
+ * knots at most 24 samples apart, tiles of 768 samples with two CTAs per SM
+ * otherwise); else 0 .. msrc_tile_configs() - 1. The _cfg entry points take it per call, so
  * that workloads tuned differently (msrc_autotune) share a process without
  * overwriting each other's choice. The workspace size depends on it: size the
  * workspace with the configuration the call uses. An id out of range is
  * MSRC_ERR_INVALID_ARG. Results of every configuration agree within FP32
  * rounding; for a fixed configuration they are bitwise reproducible. */
 #define MSRC_TILE_DEFAULT (-1)
+#define MSRC_TILE_AUTO (-2)
 msrc_status msrc_workspace_size_cfg(const msrc_room_t* rooms, int32_t n_rooms,
                                     const int64_t* n_in, const int64_t* n_out, int32_t tile_config,
                                     size_t* fwd_bytes, size_t* bwd_bytes);
@@ -347,10 +354,11 @@ msrc_status msrc_room_fit_error(msrc_room_t room, double* max_abs_error);
  * *n_powers receives P. */
 msrc_status msrc_room_farrow_table(msrc_room_t room, int32_t which, float* out, int32_t* n_powers);
 
-/* Process default tile configuration (0 initially): the configuration of every
- * call that names none (msrc_synthesize, msrc_synthesize_host,
- * msrc_workspace_size, msrc_batch_create, msrc_synthesize_noalloc, or
- * MSRC_TILE_DEFAULT); msrc_tile_configs lists how many exist. Thread-safe. */
+/* Process default tile configuration (MSRC_TILE_AUTO initially; an id or
+ * MSRC_TILE_AUTO): the configuration of every call that names none
+ * (msrc_synthesize, msrc_synthesize_host, msrc_workspace_size,
+ * msrc_batch_create, msrc_synthesize_noalloc, or MSRC_TILE_DEFAULT);
+ * msrc_tile_configs lists how many exist. Thread-safe. */
 msrc_status msrc_set_tile_config(int32_t config_id);
 int32_t msrc_tile_configs(void);
 

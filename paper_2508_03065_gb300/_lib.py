@@ -17,6 +17,7 @@ MAX_MICS = 16
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_STATE = range(7)
 TILE_DEFAULT = -1  # MSRC_TILE_DEFAULT: the process default tile configuration
+TILE_AUTO = -2     # MSRC_TILE_AUTO: chosen from the call's knot layout
 
 
 class RoomDesc(ctypes.Structure):

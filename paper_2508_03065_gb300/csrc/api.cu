@@ -58,12 +58,35 @@ struct msrc_room {
 namespace {
 
 // Tile configuration of calls that name none (MSRC_TILE_DEFAULT): the process
-// default set by msrc_set_tile_config.
-std::atomic<int> g_tile_config{0};
+// default set by msrc_set_tile_config; initially MSRC_TILE_AUTO.
+std::atomic<int> g_tile_config{MSRC_TILE_AUTO};
 uint32_t g_test_extra_tx = 0;  // msrc_test_stall_window_copies
 
-// The configuration a call runs in: its own, or the process default.
-int call_config(int32_t tile_config) { return tile_config < 0 ? g_tile_config.load() : tile_config; }
+// MSRC_TILE_AUTO: the configuration measured fastest for the call's knot
+// layout. Knot spacings of at most 24 samples (1 kHz knots at 16 kHz) need
+// many interval records per image: tile configuration 10 (1024-sample tiles,
+// 10240 records) holds the most images per block. Sparser knots run in
+// configuration 11 (768-sample tiles, two CTAs per SM). The spacing that
+// counts is that of the tiers holding most of the call's images.
+int auto_config(const msrc_room_t* rooms, int n) {
+  int64_t dense = 0, sparse = 0;
+  for (int r = 0; r < n; ++r) {
+    const msrc_room* R = rooms ? rooms[r] : nullptr;
+    if (!R) continue;
+    for (int t = 0; t < R->d.n_tiers; ++t) {
+      const int N = R->tier_step[t] / std::max(1, R->tier_up[t]);
+      (N <= 24 ? dense : sparse) += R->tier_count[t] * int64_t(R->n_mics);
+    }
+  }
+  return dense > sparse ? 10 : 11;
+}
+
+// The configuration a call runs in: its own, the process default, or the
+// automatic choice for these rooms.
+int call_config(int32_t tile_config, const msrc_room_t* rooms, int n) {
+  const int c = tile_config == MSRC_TILE_DEFAULT ? g_tile_config.load() : tile_config;
+  return c == MSRC_TILE_AUTO ? auto_config(rooms, n) : c;
+}
 
 // Optional per-phase timing with CUDA events recorded on the launching stream.
 // Phases: 0 setup (images, sort, knots, records), 1 prefilter, 2 synthesis, 3 reduction.
@@ -443,7 +466,7 @@ struct Plan {
   // byte offsets in the workspace
   size_t off_desc = 0, off_keys_in = 0, off_keys_out = 0, off_vals_in = 0, off_vals_out = 0;
   size_t off_sort = 0, sort_bytes = 0, off_code = 0, off_gain = 0, off_knots = 0;
-  size_t off_mcode = 0, off_mgain = 0, off_moff = 0;
+  size_t off_mcode = 0, off_mgain = 0, off_moff = 0, off_mpos = 0;
   size_t off_z = 0, off_zp = 0, off_part = 0, fwd_bytes = 0, desc_bytes = 0, off_arr = 0, off_xmax = 0;
   // reverse mode
   bool backward = false;
@@ -569,13 +592,14 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
       S.tier_intervals[t] = J;
       // images per block: the item's records (one per image and knot interval
       // touching the tile) must fit the shared record capacity
-      // (the forward synthesis stores them for image pairs: an even count)
+      // (the forward synthesis and the gradient kernel store them for image
+      // pairs: an even count)
       const int rec_per_image = (T - 1) / N + 2;
-      if ((backward ? 1 : 2) * rec_per_image > tc.reccap)
+      if (2 * rec_per_image > tc.reccap)
         return fail(MSRC_ERR_UNSUPPORTED, "tile configuration too small for knot spacing %d", N);
       int B = std::max(1, std::min(tc.block, tc.reccap / rec_per_image));
       if (backward) B = std::max(1, std::min(B, int(backward_unit_cap()) / (rec_per_image + 1)));
-      else if (B > 1) B &= ~1;
+      if (B > 1) B &= ~1;
       int64_t n_knots = J + 1;
       if (bl) {
         // the upsampler's scratch shares the shared z window (4 floats per column and segment)
@@ -623,13 +647,11 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     S.img_base = img_acc;
     S.master_base = master_acc;
     // time groups: one per kTimeGroupSamples of output in forward mode; one
-    // (ordered at the middle of the trajectory) in reverse mode and when a
-    // tier is upsampled (its knot-delay rows follow the first group's order)
+    // (ordered at the middle of the trajectory) in reverse mode (band-limited
+    // tiers' knot-delay rows follow the first group's order, k_group0_pos)
     {
-      bool any_bl = false;
-      for (int t = 0; t < S.n_tiers; ++t) any_bl = any_bl || S.tier_up[t] > 1;
       const int tg = int(std::max<int64_t>(1, kTimeGroupSamples / T));
-      const bool grouped = !backward && !any_bl && S.n_tiles > tg;
+      const bool grouped = !backward && S.n_tiles > tg;
       S.tile_group = grouped ? tg : S.n_tiles;
       S.n_time_groups = grouped ? (S.n_tiles + tg - 1) / tg : 1;
       S.sort_group0 = group_acc;
@@ -758,6 +780,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
   P.off_mcode = off; off = align256(off + 4 * size_t(master_acc));
   P.off_mgain = off; off = align256(off + 4 * size_t(master_acc));
   P.off_moff = off; off = align256(off + 16 * size_t(master_acc));
+  P.off_mpos = off; off = align256(off + 4 * size_t(master_acc));
   P.off_gain = off; off = align256(off + 4 * I);
   P.off_knots = off; off = align256(off + 24 * size_t(knot_acc));
   P.off_arr = off; off = align256(off + (any_moving ? 24 * size_t(knot_acc) : 0));
@@ -810,6 +833,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
   a.p.m_code = reinterpret_cast<uint32_t*>(ws + P.off_mcode);
   a.p.m_gain = reinterpret_cast<float*>(ws + P.off_mgain);
   a.p.m_off = reinterpret_cast<float4*>(ws + P.off_moff);
+  a.p.m_pos = reinterpret_cast<int32_t*>(ws + P.off_mpos);
   a.p.knot_pos = reinterpret_cast<double*>(ws + P.off_knots);
   a.p.arr_pos = reinterpret_cast<double*>(ws + P.off_arr);
   a.p.knot_hl = reinterpret_cast<float4*>(ws + P.off_knot_hl);
@@ -1313,7 +1337,7 @@ msrc_status msrc_workspace_size_cfg(const msrc_room_t* rooms, int32_t n_rooms, c
                                     const int64_t* n_out, int32_t tile_config, size_t* fwd_bytes,
                                     size_t* bwd_bytes) {
   Plan P;
-  msrc_status s = make_plan(rooms, n_rooms, n_in, n_out, P, false, call_config(tile_config));
+  msrc_status s = make_plan(rooms, n_rooms, n_in, n_out, P, false, call_config(tile_config, rooms, n_rooms));
   if (s != MSRC_OK) return s;
   if (fwd_bytes) *fwd_bytes = P.fwd_bytes;
   if (bwd_bytes) {
@@ -1329,14 +1353,14 @@ msrc_status msrc_synthesize(const msrc_room_t* rooms, int32_t n_rooms, const flo
                             const int64_t* n_in, float* const* y_dev, const int64_t* n_out,
                             void* ws, size_t ws_bytes, void* stream) {
   return run_forward(rooms, n_rooms, x_dev, n_in, y_dev, n_out, ws, ws_bytes,
-                     static_cast<cudaStream_t>(stream), call_config(MSRC_TILE_DEFAULT));
+                     static_cast<cudaStream_t>(stream), call_config(MSRC_TILE_DEFAULT, rooms, n_rooms));
 }
 
 msrc_status msrc_synthesize_cfg(const msrc_room_t* rooms, int32_t n_rooms, const float* const* x_dev,
                                 const int64_t* n_in, float* const* y_dev, const int64_t* n_out,
                                 int32_t tile_config, void* ws, size_t ws_bytes, void* stream) {
   return run_forward(rooms, n_rooms, x_dev, n_in, y_dev, n_out, ws, ws_bytes,
-                     static_cast<cudaStream_t>(stream), call_config(tile_config));
+                     static_cast<cudaStream_t>(stream), call_config(tile_config, rooms, n_rooms));
 }
 
 msrc_status msrc_host_io_bytes(const msrc_room_t* rooms, int32_t n_rooms, const int64_t* n_in,
@@ -1355,7 +1379,7 @@ msrc_status msrc_synthesize_host(const msrc_room_t* rooms, int32_t n_rooms, cons
                                  const int64_t* n_in, float* const* y_host, const int64_t* n_out,
                                  void* ws, size_t ws_bytes, void* stream) {
   if (!x_host || !y_host) return fail(MSRC_ERR_INVALID_ARG, "null host signal array");
-  const int cfg = call_config(MSRC_TILE_DEFAULT);
+  const int cfg = call_config(MSRC_TILE_DEFAULT, rooms, n_rooms);
   Plan P;
   msrc_status s = make_plan(rooms, n_rooms, n_in, n_out, P, false, cfg);
   if (s != MSRC_OK) return s;
@@ -1461,7 +1485,7 @@ msrc_status msrc_batch_create_cfg(const msrc_room_t* rooms, int32_t n, const flo
   *out = nullptr;
   msrc_batch* b = new (std::nothrow) msrc_batch;
   if (!b) return fail(MSRC_ERR_INVALID_ARG, "out of host memory");
-  msrc_status s = make_plan(rooms, n, n_in, n_out, b->P, false, call_config(tile_config));
+  msrc_status s = make_plan(rooms, n, n_in, n_out, b->P, false, call_config(tile_config, rooms, n));
   if (s == MSRC_OK) s = check_ws(b->P, ws, ws_bytes);
   if (s != MSRC_OK) { delete b; return s; }
   for (int r = 0; r < n; ++r) {
@@ -1649,7 +1673,8 @@ msrc_status msrc_test_stall_window_copies(uint32_t bytes) {
 }
 
 msrc_status msrc_set_tile_config(int32_t id) {
-  if (id < 0 || id >= tile_config_count()) return fail(MSRC_ERR_INVALID_ARG, "tile config %d out of range", id);
+  if (id != MSRC_TILE_AUTO && (id < 0 || id >= tile_config_count()))
+    return fail(MSRC_ERR_INVALID_ARG, "tile config %d out of range", id);
   g_tile_config.store(id);
   return MSRC_OK;
 }

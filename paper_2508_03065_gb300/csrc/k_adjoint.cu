@@ -136,72 +136,103 @@ __device__ __forceinline__ void window_of(float tmin, float tmax, const ItemGeom
   if (tmax_out) *tmax_out = tmax;
 }
 
-// The gradient kernel's image loop for this thread's chunks. Per image-sample:
-// e and de/dw (degree-5 rows), dL/dd_i(n) = -dy g (fs/c) (S de/dw + e / tau),
-// its knot weights (1 - s, s) times the unit vectors of the interval's knots,
-// and the wall terms dy e (fs/c) / tau times dbeta_i/dbeta_w / (4 pi).
+// The gradient kernel's image loop for this thread's chunks, over image pairs
+// (paired records, see put_image_record). Per image-sample: e and de/dw
+// (degree-5 rows), dL/dd_i(n) = -dy g (fs/c) (S de/dw + e / tau), its knot
+// weights (1 - s, s) times the unit vectors of the interval's knots, and the
+// wall terms dy e (fs/c) / tau times dbeta_i/dbeta_w / (4 pi). The delay, its
+// rounding, the gains and the knot weights run as float2 pairs of images.
 // kChecked: the window is processed in several passes and read positions
 // outside this pass contribute nothing; otherwise every position lies inside
 // the window by construction (the index is only clamped to the arrays).
 // dyf[c] = dy (fs/c) of the chunk's sample (0 for samples past the output).
+__device__ __forceinline__ void horner_d5(const float4 A, const float2 B, float w, float* pe_out, float* pd_out) {
+  float pe = B.y, pd = 0.0f;  // e = P(w) and dP/dw together (Horner, degree 5)
+  pd = fmaf(pd, w, pe); pe = fmaf(pe, w, B.x);
+  pd = fmaf(pd, w, pe); pe = fmaf(pe, w, A.w);
+  pd = fmaf(pd, w, pe); pe = fmaf(pe, w, A.z);
+  pd = fmaf(pd, w, pe); pe = fmaf(pe, w, A.y);
+  pd = fmaf(pd, w, pe); pe = fmaf(pe, w, A.x);
+  *pe_out = pe;
+  *pd_out = pd;
+}
+
 template <bool kChecked>
-__device__ __forceinline__ void grad_images(const float4* zq_s, const float2* zp_s, const float2* rec_s,
-                                            const int4* img_s, const float4* unit_s, const float4* bw_s,
-                                            int cnt, int nk, const int* jc, const int* rmj, const float* rf,
-                                            const float* sN, const float* dyf, unsigned pw,
-                                            float (&V)[kBwChunks][6], float (&bacc)[6]) {
-  const float2* row[kBwChunks];
-  const float4* urow[kBwChunks];
+__device__ __forceinline__ void grad_pairs(const float4* zq_s, const float2* zp_s, const float4* rec4,
+                                           const float4* id_s, const int2* ii_s, const float4* uxy_s,
+                                           const float2* uz_s, const float4* bwp_s, int cntp, int nk,
+                                           const int* jc, const int* rmj, const float* rf, const float* sN,
+                                           const float* dyf, unsigned pw, float (&V)[kBwChunks][6],
+                                           float (&bacc)[6]) {
+  constexpr unsigned kCap = unsigned(kFarrowSegs * kGradWcap - 1);
+  const float4* row[kBwChunks];
   unsigned rmc[kBwChunks];
+  float2 rf2[kBwChunks], sN2[kBwChunks], dy2[kBwChunks];
 #pragma unroll
   for (int c = 0; c < kBwChunks; ++c) {
-    row[c] = rec_s + jc[c] * cnt;
-    urow[c] = unit_s + jc[c];
+    row[c] = rec4 + jc[c] * cntp;
     rmc[c] = fold_rounding(rmj[c]);
+    rf2[c] = make_float2(rf[c], rf[c]);
+    sN2[c] = make_float2(sN[c], sN[c]);
+    dy2[c] = make_float2(dyf[c], dyf[c]);
   }
-  for (int ib = 0; ib < cnt; ++ib) {
-    const float4 B0 = bw_s[2 * ib], B1 = bw_s[2 * ib + 1];
-    const int4 im = img_s[ib];
-    const float Dp = __int_as_float(im.y);
-    const int ub = ib * nk;
-    float hsum = 0.0f;  // this thread's dy e (fs/c) / tau of the image, over its chunks
+  for (int p = 0; p < cntp; ++p) {
+    const float4 ID = id_s[p];  // {Dp, Dp', G, G'}
+    const int2 II = ii_s[p];    // {I, I'}
+    const float2 G2n = make_float2(-ID.z, -ID.w);  // minus the gains
+    const int ub = p * nk;
+    float2 hsum = make_float2(0.0f, 0.0f);  // dy e (fs/c) / tau of the two images, over the chunks
 #pragma unroll
     for (int c = 0; c < kBwChunks; ++c) {
-      float w, tau, dy = dyf[c];
-      unsigned idx;
+      const float4 R = row[c][p];
+      const float2 Y = __ffma2_rn(rf2[c], make_float2(R.z, R.w), make_float2(R.x, R.y));
+      const float2 q = __fadd2_rn(Y, make_float2(kRound, kRound));
+      const float2 t = __fadd2_rn(q, make_float2(-kRound, -kRound));
+      const float2 w = __ffma2_rn(t, make_float2(-1.0f, -1.0f), Y);
+      const float2 tau = __ffma2_rn(Y, make_float2(-1.0f / kFarrowSegs, -1.0f / kFarrowSegs),
+                                    make_float2(ID.x, ID.y));
+      const unsigned b0 = __float_as_uint(q.x), b1 = __float_as_uint(q.y);
+      float2 dy = dy2[c];
+      unsigned i0, i1;
       if (kChecked) {
-        const DelaySplit ds = split_delay(row[c][ib], rmj[c] + im.x, rf[c], Dp);
-        const bool in = unsigned(ds.col) < pw;
-        dy = in ? dy : 0.0f;
-        idx = in ? unsigned(ds.seg * kGradWcap + ds.col) : 0u;
-        w = ds.w;
-        tau = ds.tau;
+        const int c0 = rmj[c] + II.x + (int(b0 >> 2) - (kRoundBits >> 2));
+        const int c1 = rmj[c] + II.y + (int(b1 >> 2) - (kRoundBits >> 2));
+        const bool in0 = unsigned(c0) < pw, in1 = unsigned(c1) < pw;
+        dy = make_float2(in0 ? dy.x : 0.0f, in1 ? dy.y : 0.0f);
+        i0 = in0 ? (b0 & 3u) * unsigned(kGradWcap) + unsigned(c0) : 0u;
+        i1 = in1 ? (b1 & 3u) * unsigned(kGradWcap) + unsigned(c1) : 0u;
       } else {
-        idx = min(split_index<kGradWcap>(row[c][ib], im.x, rmc[c], rf[c], Dp, &w, &tau),
-                  unsigned(kFarrowSegs * kGradWcap - 1));
+        i0 = min((b0 & 3u) * unsigned(kGradWcap) + ((b0 >> 2) + unsigned(II.x) + rmc[c]), kCap);
+        i1 = min((b1 & 3u) * unsigned(kGradWcap) + ((b1 >> 2) + unsigned(II.y) + rmc[c]), kCap);
       }
-      const float4 A = zq_s[idx];
-      const float2 Bz = zp_s[idx];
-      float pe = Bz.y, pd = 0.0f;  // e = P(w) and dP/dw together (Horner, degree 5)
-      pd = fmaf(pd, w, pe); pe = fmaf(pe, w, Bz.x);
-      pd = fmaf(pd, w, pe); pe = fmaf(pe, w, A.w);
-      pd = fmaf(pd, w, pe); pe = fmaf(pe, w, A.z);
-      pd = fmaf(pd, w, pe); pe = fmaf(pe, w, A.y);
-      pd = fmaf(pd, w, pe); pe = fmaf(pe, w, A.x);
-      const float rt = __fdividef(1.0f, tau);
-      const float et = pe * rt;                                          // e / tau
-      const float ad = -(dy * B1.z * rt) * fmaf(float(kFarrowSegs), pd, et);  // dL/dd_i(n)
-      hsum = fmaf(dy, et, hsum);                                         // dy e (fs/c) / tau
-      const float4 U0 = urow[c][ub];
-      const float4 U1 = urow[c][ub + 1];
-      const float w1 = ad * sN[c], w0 = ad - w1;
-      V[c][0] = fmaf(w0, U0.x, V[c][0]); V[c][1] = fmaf(w0, U0.y, V[c][1]); V[c][2] = fmaf(w0, U0.z, V[c][2]);
-      V[c][3] = fmaf(w1, U1.x, V[c][3]); V[c][4] = fmaf(w1, U1.y, V[c][4]); V[c][5] = fmaf(w1, U1.z, V[c][5]);
+      float pe0, pd0, pe1, pd1;
+      horner_d5(zq_s[i0], zp_s[i0], w.x, &pe0, &pd0);
+      horner_d5(zq_s[i1], zp_s[i1], w.y, &pe1, &pd1);
+      const float2 rt = make_float2(__fdividef(1.0f, tau.x), __fdividef(1.0f, tau.y));
+      const float2 et = __fmul2_rn(make_float2(pe0, pe1), rt);                       // e / tau
+      const float2 gd = __fmul2_rn(__fmul2_rn(dy, G2n), rt);                         // -dy g (fs/c)
+      const float2 ad = __fmul2_rn(gd, __ffma2_rn(make_float2(float(kFarrowSegs), float(kFarrowSegs)),
+                                                  make_float2(pd0, pd1), et));      // dL/dd_i(n)
+      hsum = __ffma2_rn(dy, et, hsum);
+      const float2 w1 = __fmul2_rn(ad, sN2[c]);
+      const float2 w0 = __ffma2_rn(w1, make_float2(-1.0f, -1.0f), ad);
+      const float4 U0 = uxy_s[ub + jc[c]], U1 = uxy_s[ub + jc[c] + 1];
+      const float2 Z0 = uz_s[ub + jc[c]], Z1 = uz_s[ub + jc[c] + 1];
+      V[c][0] = fmaf(w0.x, U0.x, fmaf(w0.y, U0.y, V[c][0]));
+      V[c][1] = fmaf(w0.x, U0.z, fmaf(w0.y, U0.w, V[c][1]));
+      V[c][2] = fmaf(w0.x, Z0.x, fmaf(w0.y, Z0.y, V[c][2]));
+      V[c][3] = fmaf(w1.x, U1.x, fmaf(w1.y, U1.y, V[c][3]));
+      V[c][4] = fmaf(w1.x, U1.z, fmaf(w1.y, U1.w, V[c][4]));
+      V[c][5] = fmaf(w1.x, Z1.x, fmaf(w1.y, Z1.y, V[c][5]));
     }
-    // the wall weights depend on the image only: once per image
-    bacc[0] = fmaf(hsum, B0.x, bacc[0]); bacc[1] = fmaf(hsum, B0.y, bacc[1]);
-    bacc[2] = fmaf(hsum, B0.z, bacc[2]); bacc[3] = fmaf(hsum, B0.w, bacc[3]);
-    bacc[4] = fmaf(hsum, B1.x, bacc[4]); bacc[5] = fmaf(hsum, B1.y, bacc[5]);
+    // the wall weights depend on the image only: once per pair
+    const float4 W0 = bwp_s[3 * p], W1 = bwp_s[3 * p + 1], W2 = bwp_s[3 * p + 2];
+    bacc[0] = fmaf(hsum.x, W0.x, fmaf(hsum.y, W0.y, bacc[0]));
+    bacc[1] = fmaf(hsum.x, W0.z, fmaf(hsum.y, W0.w, bacc[1]));
+    bacc[2] = fmaf(hsum.x, W1.x, fmaf(hsum.y, W1.y, bacc[2]));
+    bacc[3] = fmaf(hsum.x, W1.z, fmaf(hsum.y, W1.w, bacc[3]));
+    bacc[4] = fmaf(hsum.x, W2.x, fmaf(hsum.y, W2.y, bacc[4]));
+    bacc[5] = fmaf(hsum.x, W2.z, fmaf(hsum.y, W2.w, bacc[5]));
   }
 }
 
@@ -212,14 +243,15 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
   float2* zp_s = reinterpret_cast<float2*>(zq_s + kFarrowSegs * kGradWcap);  // powers 4..5
   float2* rec_s = zp_s + kFarrowSegs * kGradWcap;
   int4* img_s = reinterpret_cast<int4*>(rec_s + kBwRecCap);
-  float4* unit_s = reinterpret_cast<float4*>(img_s + kBwBlock);        // [image][knot]
-  float4* bw_s = unit_s + kBwUnitCap;                                   // 2 per image
+  float4* unit_s = reinterpret_cast<float4*>(img_s + kBwBlock);        // unit vectors, paired (below)
+  float4* bw_s = unit_s + kBwUnitCap;                                   // wall weights, 3 per image pair
   float4* u_s = sm;                                                     // prologue scratch
   float4* um_s = sm + kBwTile + 4;
   float4* anc_s = um_s + kBwTile + 4;
   float* phi_s = reinterpret_cast<float*>(anc_s + 3 * kBwBlock);       // kBwRecCap + kBwBlock
+  float* dk_s = phi_s + kBwRecCap + kBwBlock;                           // distances at the knots, as phi_s
   float* seg_s = reinterpret_cast<float*>(sm);                          // knot scan scratch (after the loop)
-  static_assert(4 * (2 * (kBwTile + 4) + 3 * kBwBlock) + kBwRecCap + kBwBlock <= 4 * kFarrowSegs * kGradWcap,
+  static_assert(4 * (2 * (kBwTile + 4) + 3 * kBwBlock) + 2 * (kBwRecCap + kBwBlock) <= 4 * kFarrowSegs * kGradWcap,
                 "prologue scratch");
   static_assert(6 * kSegCap * (kBwTile / 32) <= 4 * kFarrowSegs * kGradWcap, "scan scratch");
   static_assert(kGradWcap % 4 == 0, "16-byte aligned row segments");
@@ -245,10 +277,17 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     const float fsc = S.fsc;
 
     float tmin, tmax;
-    item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax);
+    item_records<kBwThreads, kRecAdjoint>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax, 1.0f,
+                                          dk_s);
+    // paired layouts of the image loop: unit vectors per (pair, knot) as
+    // {x, x', y, y'} and {z, z'}, wall weights per pair as three float4 of
+    // (w, w') pairs; an odd block's zero-gain copy gets zeros
+    const int cntp = pair_count(g.cnt);
+    float4* uxy_s = unit_s;
+    float2* uz_s = reinterpret_cast<float2*>(uxy_s + cntp * g.nk);
     // unit vectors (sigma o Delta) / d of every image at every knot of the tile
-    // (sigma o Delta_j = w + u - sigma o u_m with a moving array)
-    // (image-fastest thread mapping: one division per thread)
+    // (sigma o Delta_j = w + u - sigma o u_m with a moving array; d from the
+    // record pass) (image-fastest thread mapping: one division per thread)
     if (const int tpi = kBwThreads / g.cnt; threadIdx.x < tpi * g.cnt) {
       const int j0 = threadIdx.x / g.cnt;
       const int ib = threadIdx.x - j0 * g.cnt;
@@ -256,25 +295,46 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
       const float4 sg = anc_s[2 * g.cnt + ib];
       for (int jj = j0; jj < g.nk; jj += tpi) {
         const float4 U = u_s[jj];
-        float phi, d, ex = 0.f, ey = 0.f, ez = 0.f;
+        const float d = dk_s[ib * g.nk + jj];
+        float ex = 0.f, ey = 0.f, ez = 0.f;
         if (S.arr_moving) {
           const float4 Um = um_s[jj];
-          knot_increment_moving(A, sg, U, Um, fsc, 0.0f, &phi, &d);
           ex = sg.x * Um.x;
           ey = sg.y * Um.y;
           ez = sg.z * Um.z;
-        } else {
-          knot_increment(A, U, fsc, 0.0f, &phi, &d);
         }
         const float inv = __fdividef(1.0f, d);
-        unit_s[ib * g.nk + jj] =
-            make_float4((A.x + U.x - ex) * inv, (A.y + U.y - ey) * inv, (A.z + U.z - ez) * inv, 0.0f);
+        const int h = ib & 1;
+        float* fxy = reinterpret_cast<float*>(uxy_s + (ib >> 1) * g.nk + jj);
+        float* fz = reinterpret_cast<float*>(uz_s + (ib >> 1) * g.nk + jj);
+        fxy[h] = (A.x + U.x - ex) * inv;
+        fxy[2 + h] = (A.y + U.y - ey) * inv;
+        fz[h] = (A.z + U.z - ez) * inv;
+        if (h == 0 && ib == g.cnt - 1) {
+          fxy[1] = 0.0f;
+          fxy[3] = 0.0f;
+          fz[1] = 0.0f;
+        }
       }
     }
-    // gains and dbeta_i/dbeta_w / (4 pi) of the block's images
+    // dbeta_i/dbeta_w / (4 pi) of the block's images, paired
     {
       const float4* bwt = a.p.bwt + 2 * (S.img_base + S.tier_first[g.t] + g.img0);
-      for (int i = threadIdx.x; i < 2 * g.cnt; i += kBwThreads) bw_s[i] = bwt[i];
+      for (int i = threadIdx.x; i < 2 * cntp; i += kBwThreads) {
+        const int ib = 2 * (i >> 1) + (i & 1);  // image of this thread: pair i / 2, member i % 2
+        float wv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (ib < g.cnt) {
+          const float4 b0 = bwt[2 * ib], b1 = bwt[2 * ib + 1];
+          wv[0] = b0.x; wv[1] = b0.y; wv[2] = b0.z; wv[3] = b0.w; wv[4] = b1.x; wv[5] = b1.y;
+        }
+        float* f = reinterpret_cast<float*>(bw_s + 3 * (ib >> 1));
+        const int h = ib & 1;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          f[4 * k + h] = wv[2 * k];
+          f[4 * k + 2 + h] = wv[2 * k + 1];
+        }
+      }
     }
     int m_lo, width;
     float rmin, rmax;
@@ -341,12 +401,15 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
       int rmj[kBwChunks];
 #pragma unroll
       for (int c = 0; c < kBwChunks; ++c) rmj[c] = rr[c] - pass_lo + jc[c] * g.N;
+      const float4* rec4 = reinterpret_cast<const float4*>(rec_s);
+      const float4* id_s = reinterpret_cast<const float4*>(img_s);
+      const int2* ii_s = reinterpret_cast<const int2*>(id_s + cntp);
       if (width <= kGradWcap)
-        grad_images<false>(zq_s, zp_s, rec_s, img_s, unit_s, bw_s, g.cnt, g.nk, jc, rmj, rf, sN, dyf, unsigned(pw),
-                           V, bacc);
+        grad_pairs<false>(zq_s, zp_s, rec4, id_s, ii_s, uxy_s, uz_s, bw_s, cntp, g.nk, jc, rmj, rf, sN, dyf,
+                          unsigned(pw), V, bacc);
       else
-        grad_images<true>(zq_s, zp_s, rec_s, img_s, unit_s, bw_s, g.cnt, g.nk, jc, rmj, rf, sN, dyf, unsigned(pw),
-                          V, bacc);
+        grad_pairs<true>(zq_s, zp_s, rec4, id_s, ii_s, uxy_s, uz_s, bw_s, cntp, g.nk, jc, rmj, rf, sN, dyf,
+                         unsigned(pw), V, bacc);
     }
     __syncthreads();  // the z window is reused as scan scratch
     // knot slots of the item: per chunk a warp-segmented scan over the lanes'

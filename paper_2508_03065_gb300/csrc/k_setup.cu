@@ -107,6 +107,17 @@ __global__ void k_group_pos(const __grid_constant__ KernelArgs a) {
   }
 }
 
+// Position of every image in the first time group's sorted table (the row of
+// its band-limited knot delays), by lattice index: unit k = group-0 position k.
+__global__ void k_group0_pos(const __grid_constant__ KernelArgs a) {
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= a.totals[8]) return;
+  int64_t k;
+  const int s = locate(a, a.tab.img_prefix, gid, &k);
+  const SceneDev& S = scene_of(a, s);
+  a.p.m_pos[S.master_base + a.p.vals_out[S.img_base + k]] = int32_t(k);
+}
+
 // One unit per image of a scene (lattice order): its packed code, gain
 // beta_i / (4 pi) * fs / c (Allen-Berkley product, FP64) and, for the sort
 // keys of every time group, its offset 2 n o L - m from the first microphone
@@ -346,6 +357,7 @@ cudaError_t launch_setup(const KernelArgs& a, cudaStream_t st) {
     cudaError_t e = launch_sort(a, a.totals[0], end_bit, st);
     if (e != cudaSuccess) return e;
     k_image_table<<<blocks_for(a.totals[0], T), T, 0, st>>>(a);
+    if (a.totals[6] > 0) k_group0_pos<<<blocks_for(a.totals[8], T), T, 0, st>>>(a);
   }
   if (a.totals[1] > 0) k_traj_knots<<<blocks_for(a.totals[1], T), T, 0, st>>>(a);
   // k_bl_tau: one warp per unit (a (microphone, image) row of knots)

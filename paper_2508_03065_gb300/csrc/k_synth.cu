@@ -266,14 +266,14 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
     float tmin, tmax;
     int cnt = g.cnt;
     if (S.delay_model == 1) {
-      item_records_ret<kThreads, true>(a, S, g, rec_s, img_s, u_s, an6_s, phi_r, &tmin, &tmax, gscale);
+      item_records_ret<kThreads, kRecForward>(a, S, g, rec_s, img_s, u_s, an6_s, phi_r, &tmin, &tmax, gscale);
     } else if (S.tier_up[g.t] > 1) {
       // band-limited knot upsampling: its scratch takes the z window
-      if (!item_records_bl<kThreads, true>(a, S, g, rec_s, img_s, reinterpret_cast<float*>(smem4),
+      if (!item_records_bl<kThreads, kRecForward>(a, S, g, rec_s, img_s, reinterpret_cast<float*>(smem4),
                                            int64_t(kFarrowSegs) * kWcap * 4, &tmin, &tmax, gscale))
         cnt = 0;
     } else {
-      item_records<kThreads, true>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax, gscale);
+      item_records<kThreads, kRecForward>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax, gscale);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

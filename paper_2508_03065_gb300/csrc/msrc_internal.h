@@ -176,7 +176,8 @@ struct DevicePtrs {
   uint32_t* img_code;            // packed lattice triple and parity
   uint32_t* m_code;              // per image in lattice order: packed code,
   float* m_gain;                 //   gain beta_i / (4 pi) * fs / c,
-  float4* m_off;                 //   2 n o L - m (FP32) and parity bits | tier << 4
+  float4* m_off;                 //   2 n o L - m (FP32) and parity bits | tier << 4,
+  int32_t* m_pos;                //   position in the first time group's sorted table
   double* gpos;                  // per (scene, time group): source position and array
                                  // displacement at the group's middle (6 doubles), sort keys
   float* img_gain;               // beta_i / (4 pi)

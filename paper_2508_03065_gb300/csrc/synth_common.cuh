@@ -208,7 +208,11 @@ __device__ __forceinline__ void anchor_df(const SceneDev& S, uint32_t code, cons
   *SG = make_float4(s0, s1, s2, 0.0f);
 }
 
-// Paired record layout of the forward synthesis (kPaired): images 2p and 2p + 1
+// Record layouts: one record per image (the reverse-mode dx kernel), or per
+// image pair for the forward synthesis and the gradient kernel.
+constexpr int kRecPlain = 0, kRecForward = 1, kRecAdjoint = 2;
+
+// Paired record layout of the forward synthesis (kRecForward): images 2p and 2p + 1
 // of a block share one 16-byte interval record per interval jj,
 //   rec[jj * cntp + p] = {Psi_2p, Psi_2p+1, sigma_2p, sigma_2p+1}    (float4),
 // and their image records sit in two arrays at img_s,
@@ -222,8 +226,9 @@ __device__ __forceinline__ int pair_count(int cnt) { return (cnt + 1) >> 1; }
 
 // Interval records of an item from the relative delays phi at its knots
 // (phi_s[ib * nk + jj]); see item_records for the record layout.
-template <int kThreads, bool kPaired = false>
+template <int kThreads, int kLayout = kRecPlain>
 __device__ __forceinline__ void records_from_phi(const ItemGeom& g, const float* phi_s, float2* rec_s) {
+  constexpr bool kPaired = kLayout != kRecPlain;
   const float sN = float(kFarrowSegs) / float(g.N);
   const int nk = g.nk;
   const int nrec = nk - 1;
@@ -268,7 +273,8 @@ __device__ __forceinline__ void records_from_phi(const ItemGeom& g, const float*
 // a moving array the knots also carry the array displacement: per knot
 // u_m = a(t_j) - a(t_jf) and the image-to-microphone vector changes by
 // sigma o u - u_m. Returns this thread's min / max of tau over its knots
-// (window bounds of the item).
+// (window bounds of the item). d_s (cnt * nk floats, nullable) receives the
+// distance at every knot of every image (the adjoint's unit vectors).
 // Image record of a work item: {I = n_jf - D_a (column offset), D_a - 1/8
 // (bits), gain (bits), 4 I (the synthesis gather's byte offset of the column)}.
 __device__ __forceinline__ int4 image_record(int I, float Dfl, float gain) {
@@ -276,10 +282,13 @@ __device__ __forceinline__ int4 image_record(int I, float Dfl, float gain) {
 }
 
 // Writes image ib's record (column offset I, anchor delay floor Dfl, gain) in
-// the layout of kPaired.
-template <bool kPaired>
+// layout kLayout: kRecPlain {I, Dp, gain, 4 I} per image (Dp = D_a - 1/(2S));
+// kRecForward per pair {a, a', b, b'} (a = -1/(S G), b = Dp / G) and {4 I, 4 I'};
+// kRecAdjoint per pair {Dp, Dp', G, G'} and {I, I'}. An odd block's last pair
+// carries a copy of its last image with zero gain.
+template <int kLayout>
 __device__ __forceinline__ void put_image_record(int4* img_s, int ib, int cnt, int I, float Dfl, float gain) {
-  if (!kPaired) {
+  if (kLayout == kRecPlain) {
     img_s[ib] = image_record(I, Dfl, gain);
     return;
   }
@@ -287,23 +296,34 @@ __device__ __forceinline__ void put_image_record(int4* img_s, int ib, int cnt, i
   int* i4 = reinterpret_cast<int*>(reinterpret_cast<int2*>(reinterpret_cast<float4*>(img_s) + pair_count(cnt)) +
                                    (ib >> 1));
   const int h = ib & 1;
-  const float inf = __int_as_float(0x7f800000);
   const float Dp = Dfl - 0.5f / kFarrowSegs;
-  const bool live = gain > 0.0f;
-  ab[h] = live ? -(1.0f / kFarrowSegs) / gain : 0.0f;
-  ab[2 + h] = live ? Dp / gain : inf;
-  i4[h] = int(unsigned(I) << 2);
-  if (h == 0 && ib == cnt - 1) {  // odd block: the zero-gain copy
-    ab[1] = 0.0f;
-    ab[3] = inf;
-    i4[1] = i4[0];
+  if (kLayout == kRecForward) {
+    const float inf = __int_as_float(0x7f800000);
+    const bool live = gain > 0.0f;
+    ab[h] = live ? -(1.0f / kFarrowSegs) / gain : 0.0f;
+    ab[2 + h] = live ? Dp / gain : inf;
+    i4[h] = int(unsigned(I) << 2);
+    if (h == 0 && ib == cnt - 1) {  // odd block: the zero-gain copy
+      ab[1] = 0.0f;
+      ab[3] = inf;
+      i4[1] = i4[0];
+    }
+  } else {
+    ab[h] = Dp;
+    ab[2 + h] = gain;
+    i4[h] = I;
+    if (h == 0 && ib == cnt - 1) {
+      ab[1] = Dp;
+      ab[3] = 0.0f;
+      i4[1] = I;
+    }
   }
 }
 
-template <int kThreads, bool kPaired = false>
+template <int kThreads, int kLayout = kRecPlain>
 __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                              int4* img_s, float4* u_s, float4* um_s, float4* anc_s, float* phi_s,
-                             float* tmin_out, float* tmax_out, float gscale = 1.0f) {
+                             float* tmin_out, float* tmax_out, float gscale = 1.0f, float* d_s = nullptr) {
   // knot positions and array displacements as double-float pairs; increments
   // from the anchor knot jf: hi differences of nearby positions are exact
   const int64_t kj = S.knot_base[g.t] + g.jf;
@@ -346,7 +366,7 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     anc_s[2 * ib] = A;
     anc_s[2 * ib + 1] = make_float4(B.x, B.y, 0.0f, 0.0f);
     anc_s[2 * g.cnt + ib] = SG;
-    put_image_record<kPaired>(img_s, ib, g.cnt, g.jf * g.N - int(B.y), B.y, __ldg(gain + ib) * gscale);
+    put_image_record<kLayout>(img_s, ib, g.cnt, g.jf * g.N - int(B.y), B.y, __ldg(gain + ib) * gscale);
   }
   __syncthreads();
   // relative delay phi at every knot of every image (once per knot), then the
@@ -368,12 +388,13 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
       if (moving) knot_increment_moving(A, SG, u_s[jj], um_s[jj], fsc, A2.x, &phi, &d);
       else knot_increment(A, u_s[jj], fsc, A2.x, &phi, &d);
       phi_s[ib * nk + jj] = phi;
+      if (d_s) d_s[ib * nk + jj] = d;
       tmin = fminf(tmin, A2.y + phi);
       tmax = fmaxf(tmax, A2.y + phi);
     }
   }
   __syncthreads();
-  records_from_phi<kThreads, kPaired>(g, phi_s, rec_s);
+  records_from_phi<kThreads, kLayout>(g, phi_s, rec_s);
   *tmin_out = tmin;
   *tmax_out = tmax;
 }
@@ -395,7 +416,7 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
 // chord rows (cnt x nj x (2Q + 2)), phi (cnt x nk). If the item does not fit,
 // the error word gets kErrUpsampleScratch, no record is written and the result
 // is false (the caller then treats the block as empty).
-template <int kThreads, bool kPaired = false>
+template <int kThreads, int kLayout = kRecPlain>
 __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                                 int4* img_s, float* scr, int64_t cap, float* tmin_out, float* tmax_out,
                                 float gscale = 1.0f) {
@@ -416,9 +437,10 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
   const int er = 2 * Q + 2;
   float* phi_s = e_s + g.cnt * nj * er;
   const int nkt = S.bl_knots[g.t];
-  // delays of image ib: rows[ib * nkt + j + Q] is knot j (the table starts at knot -Q)
-  const float2* rows = a.p.bl_tau + S.bl_tau_base[g.t] +
-                       (int64_t(g.mic) * S.tier_count[g.t] + g.img0) * nkt + Q;
+  // delays of an image: rows[p * nkt + j + Q] is knot j (the table starts at
+  // knot -Q), p its position in the tier in the first time group's order
+  const float2* rows = a.p.bl_tau + S.bl_tau_base[g.t] + int64_t(g.mic) * S.tier_count[g.t] * nkt + Q;
+  const uint32_t* masters = a.p.vals_out + S.img_base + g.img_off + S.tier_first[g.t] + g.img0;
   const float* gain = a.p.img_gain + S.img_base + g.img_off + S.tier_first[g.t] + g.img0;
   // image-fastest thread mapping (one division per thread): image t mod cnt,
   // intervals / knots from t / cnt in steps of kThreads / cnt
@@ -429,12 +451,14 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
   for (int jr = act ? t0i : nj; jr < nj; jr += tpi) {
     const int ib = tib;
     const int pidx = ib * nj + jr;
-    const float2* row = rows + int64_t(ib) * nkt;
+    const int p0 = g.img_off == 0 ? g.img0 + ib
+                                   : a.p.m_pos[S.master_base + __ldg(masters + ib)] - S.tier_first[g.t];
+    const float2* row = rows + int64_t(p0) * nkt;
     const float2 an = row[j0_first];
     const float Dfl = df_floor(DF{an.x, an.y});  // the anchor, knot floor(jf / U)
     if (jr == 0) {
       dfl_s[ib] = Dfl;
-      put_image_record<kPaired>(img_s, ib, g.cnt, g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib) * gscale);
+      put_image_record<kLayout>(img_s, ib, g.cnt, g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib) * gscale);
     }
     const float2* tv = row + (j0_first + jr - Q + 1);  // knots j0 - Q + 1 .. j0 + Q
     const DF t0{tv[Q - 1].x, tv[Q - 1].y};
@@ -482,7 +506,7 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
     }
   }
   __syncthreads();
-  records_from_phi<kThreads, kPaired>(g, phi_s, rec_s);
+  records_from_phi<kThreads, kLayout>(g, phi_s, rec_s);
   *tmin_out = tmin;
   *tmax_out = tmax;
   return true;
@@ -554,7 +578,7 @@ __device__ __forceinline__ float ret_increment(const RetAnchor& r, const float4 
   return delta;
 }
 
-template <int kThreads, bool kPaired = false>
+template <int kThreads, int kLayout = kRecPlain>
 __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                                  int4* img_s, float4* um_s, float4* an6, float* phi_s, float* tmin_out,
                                  float* tmax_out, float gscale = 1.0f) {
@@ -694,7 +718,7 @@ __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const I
     an6[6 * ib + 3] = make_float4(dsx, dsy, dsz, gsl / (1.0f + gsl));
     an6[6 * ib + 4] = make_float4(sg[0], sg[1], sg[2], __int_as_float(int(k)));
     an6[6 * ib + 5] = make_float4(eps, Dfl, r2, 0.0f);
-    put_image_record<kPaired>(img_s, ib, g.cnt, g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib) * gscale);
+    put_image_record<kLayout>(img_s, ib, g.cnt, g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib) * gscale);
   }
   __syncthreads();
   const int nk = g.nk;
@@ -734,7 +758,7 @@ __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const I
     }
   }
   __syncthreads();
-  records_from_phi<kThreads, kPaired>(g, phi_s, rec_s);
+  records_from_phi<kThreads, kLayout>(g, phi_s, rec_s);
   *tmin_out = tmin;
   *tmax_out = tmax;
 }

@@ -157,7 +157,9 @@ def test_workspace_and_signal_checks_without_device():
     for c in range(lib.msrc_tile_configs()):
         assert lib.msrc_workspace_size_cfg(hs, 1, n, n, c, ctypes.byref(fcfg), None) == _lib.OK
         sizes.append(fcfg.value)
-    assert sizes[0] == fwd.value and len(set(sizes)) > 1
+    assert fwd.value in sizes and len(set(sizes)) > 1  # the default is one of them (chosen automatically)
+    assert lib.msrc_workspace_size_cfg(hs, 1, n, n, _lib.TILE_AUTO, ctypes.byref(fcfg), None) == _lib.OK
+    assert fcfg.value == fwd.value
     for bad in (lib.msrc_tile_configs(), 99):
         assert lib.msrc_workspace_size_cfg(hs, 1, n, n, bad, ctypes.byref(fcfg), None) == _lib.ERR_INVALID_ARG
         assert lib.msrc_synthesize_cfg(hs, 1, xs, n, ys, n, bad, ctypes.c_void_p(256), 1 << 30,
@@ -321,4 +323,22 @@ def test_device_farrow_table_against_oracle_taps(taps, window, beta):
         # the table is the fit of this room's kernel: a plausible mistake (a
         # segment or a tap shifted by one) is far outside the pin
         assert np.max(np.abs(approx[:, :-1] - exact[:, 1:])) > 100 * pin
+    lib.msrc_destroy_room(h)
+
+
+@pytest.mark.parametrize("tiers,expect", [([(1, 16000.0), (2**31 - 1, 1000.0)], 10),   # most images on 16-sample knots
+                                          ([(1, 16000.0), (2**31 - 1, 250.0)], 11)])   # sparse knots
+def test_automatic_tile_configuration(tiers, expect):
+    # the default configuration follows the knot layout of the call's images
+    lib = _lib.load()
+    st, h = _create(K=6, tiers=tiers)
+    assert st == _lib.OK
+    arr, p = _mics((2.5, 2.0, 1.2))
+    assert lib.msrc_set_trajectory(h, ctypes.byref(_traj()), p, 1) == _lib.OK
+    hs = _lib.ptr_array([h.value])
+    n = _lib.i64_array([16000])
+    auto, want = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.msrc_workspace_size(hs, 1, n, n, ctypes.byref(auto), None) == _lib.OK
+    assert lib.msrc_workspace_size_cfg(hs, 1, n, n, expect, ctypes.byref(want), None) == _lib.OK
+    assert auto.value == want.value
     lib.msrc_destroy_room(h)

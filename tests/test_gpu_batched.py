@@ -40,11 +40,13 @@ def test_batched_config3_scenes_match_single_and_sampled_oracle():
     specs = _scenes(6)
     rooms = [api.Room.from_spec(s) for s in specs]
     xs = [torch.from_numpy(s.x).cuda() for s in specs]
-    b = api.Batch(rooms, xs)
+    # batched and single calls agree bitwise in one tile configuration (the
+    # automatic choice may differ between a batch and one of its scenes)
+    b = api.Batch(rooms, xs, tile_config=11)
     ys = [y.clone() for y in b.run(True)]
     b.stream.synchronize()
     for i, spec in enumerate(specs):
-        single = api.synthesize([rooms[i]], [xs[i]])[0]
+        single = api.synthesize([rooms[i]], [xs[i]], tile_config=11)[0]
         assert torch.equal(single, ys[i])
         idx = np.linspace(0, spec.n_in - 1, 12).astype(np.int64)
         ref = oracle.y_at(oracle_scene(spec), spec.x.astype(np.float64), idx)

@@ -92,9 +92,11 @@ def test_free_field_single_image():
 
 def test_batched_equals_single_and_oracle():
     specs = [W.small_scene(seed=20 + i, K=3 + i % 3, seconds=0.05 + 0.04 * i) for i in range(5)]
-    batched = gpu_run(specs)
+    # bitwise equal in one tile configuration (the automatic choice may differ
+    # between a batch and one of its scenes)
+    batched = gpu_run(specs, tile_config=11)
     for spec, yb in zip(specs, batched):
-        ys = gpu_run([spec])[0]
+        ys = gpu_run([spec], tile_config=11)[0]
         assert np.array_equal(yb, ys)
         assert rel_l2(yb[0], oracle_full(spec)) < TOL
 
@@ -123,7 +125,8 @@ def test_per_call_tile_config_leaves_the_default():
     d1 = gpu_run([spec])[0]
     t1 = gpu_run([spec], tile_config=10)[0]
     assert np.array_equal(d0, d1) and np.array_equal(t0, t1)
-    assert np.array_equal(d0, gpu_run([spec], tile_config=0)[0])
+    # the process default is the automatic choice from the knot layout
+    assert np.array_equal(d0, gpu_run([spec], tile_config=api._lib.TILE_AUTO)[0])
     with pytest.raises(api._lib.MsrcError):
         gpu_run([spec], tile_config=api.tile_configs())
 

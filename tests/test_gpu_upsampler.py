@@ -85,8 +85,8 @@ def test_batch_mixing_linear_and_upsampled_tiers():
     specs = [W.small_scene(seed=17, K=2, tiers=[(1, 16000.0), (W.RHO_INF, 1000.0)]),
              replace(W.small_scene(seed=18, K=3, tiers=[(1, 16000.0), (W.RHO_INF, 400.0, 5)]), up_halfwidth=3),
              W.small_scene(seed=19, K=2, traj_kind=W.CIRCLE, tiers=[(W.RHO_INF, 250.0, 32)])]
-    ys = gpu_run(specs)
-    single = [gpu_run([s])[0] for s in specs]
+    ys = gpu_run(specs, tile_config=11)  # one configuration for both (bitwise comparison)
+    single = [gpu_run([s], tile_config=11)[0] for s in specs]
     for s, y, y1 in zip(specs, ys, single):
         assert np.array_equal(y, y1)
         assert rel_l2(y[0], oracle_full(s)) < TOL
