@@ -84,6 +84,7 @@ def _load():
             lib.oracle_source_position.argtypes = [_S, _D, L, _D]
             lib.oracle_image_distance.argtypes = [_S, L, _D, L, _D]
             lib.oracle_knot_delay.argtypes = [_S, L, _D, L, _D]
+            lib.oracle_knot_delay_cs.argtypes = [_S, L, _D, L, ctypes.c_int32, ctypes.c_double, _D]
             lib.oracle_delay_gain.argtypes = [_S, L, _I64, L, _D, _D, _D]
             lib.oracle_tap_weights.argtypes = [_S, _D, L, _D]
             lib.oracle_window.argtypes = [_S, _D, L, _D]
@@ -237,6 +238,16 @@ def knot_delay(scene: Scene, idx: int, t) -> np.ndarray:
     out = np.zeros(t.size)
     sc = scene.to_c()
     _load().oracle_knot_delay(ctypes.byref(sc), int(idx), _dp(t), t.size, _dp(out))
+    return out
+
+
+def knot_delay_cs(scene: Scene, idx: int, t, param_id: int, h: float = 1e-20) -> np.ndarray:
+    """Complex-step derivative of knot_delay (s) with respect to one parameter
+    (ids < 48 index traj[], 48..53 the wall reflection coefficients)."""
+    t = np.ascontiguousarray(np.atleast_1d(t), np.float64)
+    out = np.zeros(t.size)
+    sc = scene.to_c()
+    _load().oracle_knot_delay_cs(ctypes.byref(sc), int(idx), _dp(t), t.size, int(param_id), float(h), _dp(out))
     return out
 
 

@@ -33,8 +33,10 @@
 //
 // Every routine is templated on the scalar so that the same code, run in
 // std::complex<double>, gives complex-step derivatives of the loss with respect
-// to trajectory parameters and wall reflection coefficients. Integer decisions
-// (floor, tier, knot index) always use the real part.
+// to trajectory parameters and wall reflection coefficients, under either delay
+// model (the emission-time delay's Newton iteration runs in the same scalar).
+// Integer decisions (floor, tier, knot index, spline span) always use the real
+// part.
 //
 // Parity pins: tests/test_oracle_pins.py (closed forms, library special
 // cases, brute force, invariants). Readings of the paper where it is silent or
@@ -164,15 +166,19 @@ Params<T> params_from(const OracleScene& S) {
 }
 
 // Cox-de Boor recursion for the clamped uniform cubic B-spline basis.
-// Knot vector: four zeros, interior knots k/(n_ctrl-3), four ones.
-double bspline_basis(int i, int deg, double u, const std::vector<double>& kv) {
+// Knot vector: four zeros, interior knots k/(n_ctrl-3), four ones. The
+// parameter u may be complex (a complex-step emission time): the knot span is
+// chosen by its real part and the basis is the span's polynomial in u.
+template <class U>
+U bspline_basis(int i, int deg, U u, const std::vector<double>& kv) {
+  const double ur = re(u);
   if (deg == 0) {
     const int last = static_cast<int>(kv.size()) - 1;
     // the closing interval includes u = 1
-    if (u == kv[last]) return (kv[i] < u && kv[i + 1] == u) ? 1.0 : 0.0;
-    return (kv[i] <= u && u < kv[i + 1]) ? 1.0 : 0.0;
+    if (ur == kv[last]) return U((kv[i] < ur && kv[i + 1] == ur) ? 1.0 : 0.0);
+    return U((kv[i] <= ur && ur < kv[i + 1]) ? 1.0 : 0.0);
   }
-  double a = 0.0, b = 0.0;
+  U a = U(0.0), b = U(0.0);
   const double d1 = kv[i + deg] - kv[i];
   const double d2 = kv[i + deg + 1] - kv[i + 1];
   if (d1 > 0) a = (u - kv[i]) / d1 * bspline_basis(i, deg - 1, u, kv);
@@ -194,8 +200,9 @@ std::vector<double> clamped_knots(int n_ctrl) {
 //   line:   p0[3], direction[3] (normalised here), speed v      -> p0 + v t dir
 //   circle: centre[3], radius R, speed v, start angle theta0    -> centre + R(cos, sin, 0)(theta0 + v t / R)
 //   spline: control points P_0..P_{n_ctrl-1} (3 each); u = clamp(t / T, 0, 1)
-template <class T>
-void source_position(const OracleScene& S, const Params<T>& P, double t, T out[3]) {
+template <class T, class TT>
+void source_position(const OracleScene& S, const Params<T>& P, TT t, T out[3]) {
+  // the time t is real, or complex (the emission time of a complex-step delay)
   if (S.traj_kind == 0) {
     T nrm = std::sqrt(P.traj[3] * P.traj[3] + P.traj[4] * P.traj[4] + P.traj[5] * P.traj[5]);
     for (int d = 0; d < 3; ++d) out[d] = P.traj[d] + P.traj[6] * t * P.traj[3 + d] / nrm;
@@ -206,12 +213,14 @@ void source_position(const OracleScene& S, const Params<T>& P, double t, T out[3
     out[1] = P.traj[1] + R * std::sin(ang);
     out[2] = P.traj[2];
   } else {
-    double u = t / S.duration;
-    u = std::min(1.0, std::max(0.0, u));
+    // u = clamp(t / T, 0, 1), by the real part (a clamped u is constant)
+    TT u = t / S.duration;
+    if (re(u) < 0.0) u = TT(0.0);
+    if (re(u) > 1.0) u = TT(1.0);
     const std::vector<double> kv = clamped_knots(S.n_ctrl);
     for (int d = 0; d < 3; ++d) out[d] = T(0.0);
     for (int c = 0; c < S.n_ctrl; ++c) {
-      const double B = bspline_basis(c, 3, u, kv);
+      const TT B = bspline_basis(c, 3, u, kv);
       for (int d = 0; d < 3; ++d) out[d] += B * P.traj[3 * c + d];
     }
   }
@@ -273,46 +282,47 @@ T image_distance(const OracleScene& S, const Params<T>& P, const Image& im, doub
 // integrated along the image's path; Sec. II-A's delta(t - t' - R/c) read with
 // R measured from the emission point). Newton's method from the reception-time
 // distance, with the path's rate of change by a central difference (which only
-// sets the rate of convergence), until the step is below 1e-15 s. The
-// function t_e -> t_e + |r_i(t_e) - m| / c is increasing below the speed of
-// sound, so the root is unique.
-double retarded_delay(const OracleScene& S, const Params<double>& P, const Image& im, double t) {
+// sets the rate of convergence), until the step's real part is below 1e-15 s,
+// then three more steps. The function t_e -> t_e + |r_i(t_e) - m| / c is
+// increasing below the speed of sound, so the root is unique. In complex
+// arithmetic (a complex-step parameter) the iteration converges to the complex
+// root, whose imaginary part is h times the implicit derivative of tau; the
+// extra steps let that part settle (each step multiplies its error by about
+// the difference between the slope and its central-difference estimate).
+template <class T>
+T retarded_delay(const OracleScene& S, const Params<T>& P, const Image& im, double t) {
   double m[3];
   mic_position(S, t, m);
-  auto dist = [&](double te) {
-    double s[3];
+  auto dist = [&](T te) {
+    T s[3];
     source_position(S, P, te, s);
-    double acc = 0.0;
+    T acc = T(0.0);
     for (int d = 0; d < 3; ++d) {
-      const double r = (1.0 - 2.0 * im.p[d]) * s[d] + 2.0 * im.n[d] * S.dims[d] - m[d];
+      const T r = (1.0 - 2.0 * im.p[d]) * s[d] + 2.0 * im.n[d] * S.dims[d] - m[d];
       acc += r * r;
     }
     return std::sqrt(acc);
   };
-  double tau = dist(t) / S.c;
+  T tau = dist(T(t)) / S.c;
   const double h = 1e-6;
-  for (int it = 0; it < 100; ++it) {
-    const double te = t - tau;
-    const double F = S.c * tau - dist(te);
-    const double dF = S.c + (dist(te + h) - dist(te - h)) / (2.0 * h);
-    const double step = F / dF;
+  int settled = 0;
+  for (int it = 0; it < 100 && settled < 4; ++it) {
+    const T te = t - tau;
+    const T F = S.c * tau - dist(te);
+    const T dF = S.c + (dist(te + h) - dist(te - h)) / (2.0 * h);
+    const T step = F / dF;
     tau -= step;
-    if (std::fabs(step) < 1e-15) break;
+    if (std::fabs(re(step)) < 1e-15) ++settled;
   }
   return tau;
 }
 
 // Distance that sets an image's delay and gain at knot time t: the distance at
-// the reception time, or the emission-time path length (delay_model 1; real
-// arithmetic only: the complex-step gradients cover the reception-time model).
+// the reception time, or the emission-time path length (delay_model 1).
 template <class T>
 T knot_distance(const OracleScene& S, const Params<T>& P, const Image& im, double t) {
   if (S.delay_model != 1) return image_distance(S, P, im, t);
-  if constexpr (std::is_same<T, double>::value) {
-    return S.c * retarded_delay(S, P, im, t);
-  } else {
-    return T(std::numeric_limits<double>::quiet_NaN());
-  }
+  return S.c * retarded_delay(S, P, im, t);
 }
 
 template <class T>
@@ -500,6 +510,18 @@ void oracle_knot_delay(const OracleScene* S, long idx, const double* t, long n_t
   const std::vector<Image> imgs = enumerate_images(*S);
   Params<double> P = params_from<double>(*S);
   for (long i = 0; i < n_t; ++i) out[i] = knot_distance(*S, P, imgs[idx], t[i]) / S->c;
+}
+
+// Complex-step derivative of the knot delay (s) of image idx at times t[]
+// with respect to one parameter (ids as in oracle_loss_grad_cs):
+// out[i] = Im(delay(theta + i h e_q)) / h.
+void oracle_knot_delay_cs(const OracleScene* S, long idx, const double* t, long n_t, int32_t param_id, double h,
+                          double* out) {
+  const std::vector<Image> imgs = enumerate_images(*S);
+  Params<cplx> P = params_from<cplx>(*S);
+  if (param_id < 48) P.traj[param_id] += cplx(0.0, h);
+  else P.beta[param_id - 48] += cplx(0.0, h);
+  for (long i = 0; i < n_t; ++i) out[i] = (knot_distance(*S, P, imgs[idx], t[i]) / S->c).imag() / h;
 }
 
 void oracle_image_distance(const OracleScene* S, long idx, const double* t, long n_t, double* out) {

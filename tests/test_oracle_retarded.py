@@ -12,7 +12,11 @@ function of Sec. II-A integrated along the image's path). Pinned by:
   the root of a quadratic;
 - the defining equation at knots, checked with the brute force's own path and
   mirroring (spline source, circling array);
-- the pure-Python brute force (bisection) on a tiny room.
+- the pure-Python brute force (bisection) on a tiny room;
+- derivatives: the complex-step derivative of the delay against the
+  derivative of the closed-form root for uniform linear motion, and the
+  complex-step loss gradient against Richardson-extrapolated central
+  differences of the real-valued loss.
 """
 import math
 from dataclasses import replace
@@ -118,3 +122,72 @@ def test_brute_force_tiny_room_retarded(traj_kind, arr):
     assert rel_l2(y, yb) < 1e-12
     y0 = oracle.synthesize(oracle_scene(replace(spec, delay_model=0)), x)
     assert rel_l2(y, y0) > 1e-6   # the models differ on a moving source
+
+
+def _closed_form_delay(p0, vel, m, c, t):
+    # uniform motion r(t) = p0 + vel t, still microphone m: c tau = |A - vel tau|
+    # with A = r(t) - m, the positive root of a quadratic (complex-safe)
+    A = [p0[d] + vel[d] * t - m[d] for d in range(3)]
+    vv = sum(v * v for v in vel)
+    av = sum(a * v for a, v in zip(A, vel))
+    aa = sum(a * a for a in A)
+    a2 = c * c - vv
+    return (-av + np.sqrt(av * av + a2 * aa)) / a2
+
+
+@pytest.mark.parametrize("param", [0, 2, 3, 4, 6])
+def test_delay_derivative_matches_closed_form_uniform_motion(param):
+    """Complex-step derivative of the emission-time delay against the
+    derivative of the closed-form root for uniform linear motion, for the
+    direct path and mirrored images (each image moves uniformly too)."""
+    c, h = 343.0, 1e-20
+    base = [1.7, 2.2, 1.3, 0.6, -0.7, 0.2, 9.0]
+    m = (4.1, 3.3, 1.6)
+    dims = (6.0, 5.0, 3.0)
+    sc = oracle.Scene(dims=dims, beta=(0.8,) * 6, mic=m, K=1, fs=16000.0, c=c,
+                      traj_kind=0, traj=list(base), delay_model=1)
+    tab = oracle.enumerate_images(sc)
+    t = np.array([0.0, 0.011, 0.37])
+    for i in range(0, tab["tier"].size, 5):
+        got = oracle.knot_delay_cs(sc, i, t, param)
+        sg = [1 - 2 * int(p) for p in tab["p"][i]]
+        off = [2.0 * int(n) * L for n, L in zip(tab["n"][i], dims)]
+        q = [complex(v) for v in base]
+        q[param] += 1j * h
+        nrm = np.sqrt(q[3] ** 2 + q[4] ** 2 + q[5] ** 2)
+        p0 = [sg[d] * q[d] + off[d] for d in range(3)]
+        vel = [sg[d] * q[6] * q[3 + d] / nrm for d in range(3)]
+        want = np.array([_closed_form_delay(p0, vel, m, c, tk).imag / h for tk in t])
+        assert np.max(np.abs(got - want)) <= 1e-10 * np.max(np.abs(want)), (i, got, want)
+
+
+@pytest.mark.parametrize("traj_kind,ids", [(W.SPLINE, [0, 4, 8, 10]), (W.CIRCLE, [0, 1, 3, 4, 5])])
+def test_loss_gradient_emission_time_matches_richardson(traj_kind, ids):
+    """Complex-step loss gradient under emission-time delays against central
+    differences of the real-valued loss with Richardson extrapolation."""
+    spec = W.small_scene(seed=44, K=1, seconds=0.02, window=W.HANN, taps=16, traj_kind=traj_kind,
+                         tiers=[(0, 16000.0), (W.RHO_INF, 2000.0)])
+    spec = replace(spec, delay_model=1)
+    sc = oracle_scene(spec)
+    x = spec.x.astype(np.float64)
+    target = np.random.default_rng(5).standard_normal(spec.n_in) * 0.01
+    g_cs = oracle.loss_grad_cs(sc, x, target, ids + [48, 51])
+
+    def loss_at(pid, dv):
+        if pid < 48:
+            tr = list(sc.traj)
+            tr[pid] += dv
+            return oracle.loss(replace(sc, traj=tr), x, target)
+        be = list(sc.beta)
+        be[pid - 48] += dv
+        return oracle.loss(replace(sc, beta=tuple(be)), x, target)
+
+    for q, pid in enumerate(ids + [48, 51]):
+        hh = 1e-4
+        d1 = (loss_at(pid, hh) - loss_at(pid, -hh)) / (2 * hh)
+        d2 = (loss_at(pid, hh / 2) - loss_at(pid, -hh / 2)) / hh
+        fd = (4 * d2 - d1) / 3
+        assert abs(fd - g_cs[q]) <= 1e-6 * np.max(np.abs(g_cs)) + 1e-6 * abs(g_cs[q]), (pid, fd, g_cs[q])
+    # the emission-time gradient is not the reception-time one
+    g0 = oracle.loss_grad_cs(oracle_scene(replace(spec, delay_model=0)), x, target, ids)
+    assert np.linalg.norm(g0 - g_cs[:len(ids)]) > 1e-4 * np.linalg.norm(g_cs[:len(ids)])
