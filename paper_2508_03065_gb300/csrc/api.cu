@@ -473,6 +473,7 @@ struct Plan {
   int cfg = 0;                      // forward tile configuration
   int64_t dxb_floats = 0;
   size_t off_dxb = 0, off_kslot = 0, off_bpart = 0, off_gk = 0, off_ppart = 0, off_bwt = 0, off_trange = 0;
+  size_t off_otau = 0, off_ograd = 0;
   int kL = 32;
   int taps = 32;
   // band-limited knot upsampling: weight tables (uploaded to off_upw)
@@ -577,9 +578,6 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
       const int U = R->tier_up[t];
       const bool bl = U > 1;
       const int N = Nc / U;  // record spacing: knots, or virtual knots when upsampled
-      if (bl && backward)
-        return fail(MSRC_ERR_UNSUPPORTED,
-                    "room %d: reverse mode does not support band-limited knot upsampling (tier %d)", s, t);
       S.tier_max_rho[t] = R->d.tier_max_rho[t];
       S.tier_step[t] = N;
       S.tier_coarse[t] = Nc;
@@ -606,7 +604,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
         const int nk = rec_per_image + 1;
         const int nj = (nk - 1) / U + 2;
         const int64_t per = bl_scratch_floats(1, nk, nj, Q);
-        const int64_t cap = int64_t(kFarrowSegs) * tc.wcap * 4;
+        const int64_t cap = backward ? backward_bl_scratch_floats() : int64_t(kFarrowSegs) * tc.wcap * 4;
         if (per > cap)
           return fail(MSRC_ERR_UNSUPPORTED, "tile configuration too small for the upsampling of tier %d", t);
         B = std::min<int64_t>(B, cap / per);
@@ -713,8 +711,6 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     S.delay_model = R->d.delay_model;
     int64_t u_dense = 0;
     if (S.delay_model == 1) {
-      if (backward)
-        return fail(MSRC_ERR_UNSUPPORTED, "room %d: reverse mode does not support emission-time delays", s);
       for (int t = 0; t < S.n_tiers; ++t)
         if (S.tier_up[t] > 1)
           return fail(MSRC_ERR_UNSUPPORTED,
@@ -746,9 +742,18 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     const int64_t u_item = int64_t(S.n_mics) * S.n_blocks * S.n_tiles;
     const int64_t u_red = backward ? int64_t(S.n_mics) * S.n_groups * S.n_ranges : int64_t(S.n_mics) * S.n_out;
     const int64_t u_bl = bl_units;  // (mic, image) rows of FP64 knot delays of upsampled tiers
+    // reverse mode: (mic, image, record knot) units of the tiers whose delays
+    // are not linear in the knot positions (upsampled, emission-time)
+    int64_t u_opt = 0;
+    for (int t = 0; t < S.n_tiers; ++t) {
+      S.opt_units_first[t] = u_opt;
+      if (backward && (S.delay_model == 1 || S.tier_up[t] > 1))
+        u_opt += int64_t(S.n_mics) * S.tier_count[t] * (int64_t(S.tier_intervals[t]) + 1);
+    }
+    S.n_opt_units = u_opt;
     if (int64_t(S.n_mics) * S.n_blocks * S.n_tiles >= (int64_t(1) << 31))
       return fail(MSRC_ERR_UNSUPPORTED, "room %d: more than 2^31 work items", s);
-    const int64_t u[kUnitKinds] = {u_enum, u_knots, u_rec, u_z, u_item, u_red, u_bl, u_dense, S.n_images};
+    const int64_t u[kUnitKinds] = {u_enum, u_knots, u_rec, u_z, u_item, u_red, u_bl, u_dense, S.n_images, u_opt};
     for (int k = 0; k < kUnitKinds; ++k) {
       P.prefix[k][s + 1] = P.prefix[k][s] + u[k];
       P.totals[k] += u[k];
@@ -808,6 +813,8 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     P.off_ppart = off; off = align256(off + 8 * size_t(n) * kParamPartialsPerScene);
     P.off_bwt = off; off = align256(off + 32 * I);
     P.off_trange = off; off = align256(off + 8 * size_t(P.totals[4]));
+    P.off_otau = off; off = align256(off + 8 * size_t(P.totals[9]));
+    P.off_ograd = off; off = align256(off + 8 * size_t(P.totals[9]));
   }
   P.fwd_bytes = off;
   if (I > (size_t(1) << 31)) return fail(MSRC_ERR_UNSUPPORTED, "more than 2^31 images in one call");
@@ -858,6 +865,8 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
     a.p.ppart = reinterpret_cast<double*>(ws + P.off_ppart);
     a.p.bwt = reinterpret_cast<float4*>(ws + P.off_bwt);
     a.p.trange = reinterpret_cast<float2*>(ws + P.off_trange);
+    a.p.otau = reinterpret_cast<double*>(ws + P.off_otau);
+    a.p.ograd = reinterpret_cast<double*>(ws + P.off_ograd);
   }
   // device tables: coefficients of the powers of w = v / 2 (c_q 2^q, exact)
   for (int sg = 0; sg < kFarrowSegs; ++sg)
@@ -890,6 +899,7 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
     a.tab.bl_prefix = pre + 6 * n1;
     a.tab.dense_prefix = pre + 7 * n1;
     a.tab.img_prefix = pre + 8 * n1;
+    a.tab.opt_prefix = pre + 9 * n1;
   }
 }
 

@@ -62,6 +62,8 @@ constexpr size_t kDxSmem = size_t(kDxSlots) * (sizeof(float4) + sizeof(float)) +
                            size_t(2 * (kBwTile + 4) + 3 * kBwBlock) * sizeof(float4) +
                            size_t(kBwRecCap + kBwBlock) * sizeof(float);
 static_assert(kBwRecCap % 2 == 0, "16-byte alignment of the image records");
+// the gradient kernel's z window (powers 0..3 and 4..5) is free while records are built
+constexpr int64_t kGradScratchFloats = int64_t(kFarrowSegs) * kGradWcap * 6;
 static_assert(kBwBlock <= kBwThreads, "the record builders give every image at least one thread");
 static_assert(kGradSmem <= 232448 && kDxSmem <= 232448, "shared memory per CTA");
 
@@ -134,6 +136,40 @@ __device__ __forceinline__ void window_of(float tmin, float tmax, const ItemGeom
   *width = g.n_end - int(floorf(tmin)) + 2 - *m_lo + 1;
   if (tmin_out) *tmin_out = tmin;
   if (tmax_out) *tmax_out = tmax;
+}
+
+// Shared-memory scratch of the record builders in both reverse-mode kernels:
+// u_s, um_s (kBwTile + 4 float4 each), anc_s (3 kBwBlock float4) and phi_s
+// (kBwRecCap + kBwBlock floats), contiguous and in that order. The
+// band-limited builder takes the region from u_s on; the emission-time builder
+// takes u_s for the microphone path and its anchors (6 float4 per image) from
+// um_s on, across um_s and anc_s.
+constexpr int64_t kRecScratchFloats = 4 * (2 * (kBwTile + 4) + 3 * kBwBlock) + kBwRecCap + kBwBlock;
+static_assert(6 * kBwBlock <= (kBwTile + 4) + 3 * kBwBlock, "emission-time anchors within um_s and anc_s");
+static_assert(kBwTile + 1 <= kBwTile + 4, "microphone path of every knot of a tile (N >= 1) within u_s");
+
+__device__ __forceinline__ bool opt_tier(const SceneDev& S, int t) { return S.delay_model == 1 || S.tier_up[t] > 1; }
+
+// Records of one item in layout kLayout, by the builder of the item's tier:
+// emission-time delays, band-limited upsampling (scratch from u_s on, bl_cap
+// floats) or linear knots (d_s, nullable, receives the knot distances).
+// Returns the item's image count: 0 when the upsampler's scratch did not fit
+// (the builder then flags the error word and writes no record).
+template <int kLayout>
+__device__ int adjoint_records(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
+                               int4* img_s, float4* u_s, float4* um_s, float4* anc_s, float* phi_s,
+                               int64_t bl_cap, float* tmin, float* tmax, float* d_s = nullptr) {
+  if (S.delay_model == 1) {
+    item_records_ret<kBwThreads, kLayout>(a, S, g, rec_s, img_s, u_s, um_s, phi_s, tmin, tmax);
+    return g.cnt;
+  }
+  if (S.tier_up[g.t] > 1)
+    return item_records_bl<kBwThreads, kLayout>(a, S, g, rec_s, img_s, reinterpret_cast<float*>(u_s), bl_cap, tmin,
+                                                tmax)
+               ? g.cnt
+               : 0;
+  item_records<kBwThreads, kLayout>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, tmin, tmax, 1.0f, d_s);
+  return g.cnt;
 }
 
 // The gradient kernel's image loop for this thread's chunks, over image pairs
@@ -273,12 +309,16 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
       li = item - a.tab.item_prefix[s];
     }
     const SceneDev& S = scene_of(a, s);
-    const ItemGeom g = item_geometry(S, li, kBwTile);
+    ItemGeom g = item_geometry(S, li, kBwTile);
     const float fsc = S.fsc;
+    // upsampled and emission-time tiers: the knot gradients come from the
+    // per-(mic, image, knot) kernels; this item only adds the wall terms and
+    // the delay range (zero unit vectors)
+    const bool opt = opt_tier(S, g.t);
 
     float tmin, tmax;
-    item_records<kBwThreads, kRecAdjoint>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax, 1.0f,
-                                          dk_s);
+    g.cnt = adjoint_records<kRecAdjoint>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, kGradScratchFloats, &tmin,
+                                         &tmax, dk_s);
     // paired layouts of the image loop: unit vectors per (pair, knot) as
     // {x, x', y, y'} and {z, z'}, wall weights per pair as three float4 of
     // (w, w') pairs; an odd block's zero-gain copy gets zeros
@@ -288,7 +328,12 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     // unit vectors (sigma o Delta) / d of every image at every knot of the tile
     // (sigma o Delta_j = w + u - sigma o u_m with a moving array; d from the
     // record pass) (image-fastest thread mapping: one division per thread)
-    if (const int tpi = kBwThreads / g.cnt; threadIdx.x < tpi * g.cnt) {
+    if (opt) {
+      for (int i = threadIdx.x; i < cntp * g.nk; i += kBwThreads) {
+        uxy_s[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        uz_s[i] = make_float2(0.f, 0.f);
+      }
+    } else if (const int tpi = kBwThreads / g.cnt; threadIdx.x < tpi * g.cnt) {
       const int j0 = threadIdx.x / g.cnt;
       const int ib = threadIdx.x - j0 * g.cnt;
       const float4 A = anc_s[2 * ib];
@@ -644,6 +689,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
         dyv[c] = valid[c] ? __ldg(S.dy + int64_t(mic) * S.n_out + n) : 0.0f;
       }
       const bool single = (b1 - b0 == 1);  // a single block keeps its records over the passes
+      int cnt_b = 0;                        // images of the block whose records are built
       for (int p0 = 0; p0 < width; p0 += kDxWcap) {
         const int pass_lo = m_lo + p0;
         const int pw = min(kDxWcap, width - p0);
@@ -660,13 +706,14 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
           if (!single || p0 == 0) {
             float lo, hi;
             __syncthreads();  // the previous block's records are no longer read
-            item_records<kBwThreads>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &lo, &hi);
+            cnt_b = adjoint_records<kRecPlain>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, kRecScratchFloats,
+                                               &lo, &hi);
           }
           __syncthreads();  // records and the zeroed window are complete
           if (width <= kDxWcap)
-            dx_images<false>(wq_s, wp_s, rec_s, img_s, g.cnt, jc, rmj, rf, dyv, valid, unsigned(pw));
+            dx_images<false>(wq_s, wp_s, rec_s, img_s, cnt_b, jc, rmj, rf, dyv, valid, unsigned(pw));
           else
-            dx_images<true>(wq_s, wp_s, rec_s, img_s, g.cnt, jc, rmj, rf, dyv, valid, unsigned(pw));
+            dx_images<true>(wq_s, wp_s, rec_s, img_s, cnt_b, jc, rmj, rf, dyv, valid, unsigned(pw));
         }
         // dx[m'] += sum_{row, k} c[row][k] w[row][m' + k] for the outputs m' =
         // pass_lo - kL/2 + 1 + q, q in [0, pw + kL - 1); output q reads window
@@ -755,7 +802,10 @@ __global__ void __launch_bounds__(kKnotsPerCta * kKnotLanes) k_knot_final(const 
     while (t + 1 < S.n_tiers && local >= S.knot_units_first[t + 1]) ++t;
     j = int(local - S.knot_units_first[t]);
     const int N = S.tier_step[t];
-    if (S.tier_count[t] > 0) {
+    // upsampled and emission-time tiers: zero here (k_opt_bl_knots writes the
+    // upsampled tiers' knots; emission-time gradients go to the parameters
+    // directly)
+    if (S.tier_count[t] > 0 && !opt_tier(S, t)) {
       // samples weighting knot j: intervals j - 1 and j, n in [(j-1) N, (j+1) N)
       const int64_t s_lo = max(int64_t(j - 1) * N, int64_t(0));
       const int64_t s_hi = min(int64_t(j + 1) * N - 1, S.n_out - 1);
@@ -848,21 +898,84 @@ __device__ void add_source_jacobian(const SceneDev& S, double t, const double g[
   }
 }
 
-// Partial dL/dparams of one chunk of a scene's knots (all tiers, flattened):
-// every thread sums J(t_j)^T dL/ds(t_j) over a contiguous knot range into its
-// own shared column, then the columns are summed in thread order.
+// Source velocity ds/dt at time t (FP64 central difference; only the
+// emission-time chain rule's denominator uses it, where its error is divided
+// by c).
+__device__ void source_velocity(const SceneDev& S, double t, double v[3]) {
+  constexpr double h = 1e-6;
+  double p1[3], p0[3];
+  source_position(S, t + h, p1);
+  source_position(S, t - h, p0);
+  for (int d = 0; d < 3; ++d) v[d] = (p1[d] - p0[d]) / (2.0 * h);
+}
+
+// Unit (mic, image, record knot) of the upsampled / emission-time tiers of a
+// scene: tier, microphone, image (sorted position in the tier), knot.
+struct OptUnit {
+  int t, mic, img, k;
+};
+__device__ __forceinline__ OptUnit opt_unit(const SceneDev& S, int64_t local) {
+  int t = 0;
+  for (int q = 0; q < S.n_tiers; ++q)
+    if (opt_tier(S, q) && S.opt_units_first[q] <= local) t = q;
+  const int64_t r = local - S.opt_units_first[t];
+  const int nk = S.tier_intervals[t] + 1;
+  const int64_t row = r / nk;
+  OptUnit u;
+  u.t = t;
+  u.k = int(r - row * nk);
+  u.mic = int(row / S.tier_count[t]);
+  u.img = int(row - int64_t(u.mic) * S.tier_count[t]);
+  return u;
+}
+
+// Microphone position at time t (FP64): static, or carried by the array.
+__device__ __forceinline__ void mic_at(const SceneDev& S, int mic, double t, double m[3]) {
+  double ad[3] = {0.0, 0.0, 0.0};
+  if (S.arr_moving) array_displacement(S, t, ad);
+  for (int d = 0; d < 3; ++d) m[d] = S.mics[mic][d] + ad[d];
+}
+
+// Emission-time path of image `code` for the reception time t: the emission
+// time e = t - tau and the vector Delta = sigma o s(e) + 2 n L - m(t), with
+// c tau = |Delta| (tau in seconds, given).
+__device__ void emission_vector(const SceneDev& S, uint32_t code, const double m[3], double t, double tau,
+                                double sg[3], double D[3], double* e) {
+  int n[3], p[3];
+  unpack_image(code, n, p);
+  *e = t - tau;
+  double sp[3];
+  source_position(S, *e, sp);
+  for (int d = 0; d < 3; ++d) {
+    sg[d] = p[d] ? -1.0 : 1.0;
+    D[d] = sg[d] * sp[d] + 2.0 * n[d] * S.dims[d] - m[d];
+  }
+}
+
+// Partial dL/dparams of one chunk of a scene's units (flattened): every thread
+// sums J^T g over a contiguous unit range into its own shared column, then the
+// columns are summed in thread order. Units: the knots of every tier,
+// J(t_j)^T dL/ds(t_j) (t_j = (j - knot_shift) times the knot spacing); with
+// emission-time delays instead the (mic, image, knot) units: with
+// e = t_j - tau the emission time, u = Delta / d and sigma o u = dd/ds,
+//   dd/dparams = (sigma o u)^T J(e) / (1 + (sigma o u) . s'(e) / c)
+// (implicit differentiation of c tau = |sigma o s(t_j - tau) + 2 n L - m(t_j)|),
+// times dL/dd at the knot.
 __global__ void __launch_bounds__(kParamThreads) k_param_partial(const __grid_constant__ KernelArgs a) {
   const int s = blockIdx.x / kParamChunks, chunk = blockIdx.x % kParamChunks;
   const SceneDev& S = scene_of(a, s);
   extern __shared__ double rows[];  // [48][kParamThreads]
   for (int p = 0; p < 48; ++p) rows[p * kParamThreads + threadIdx.x] = 0.0;
   const int last = S.n_tiers - 1;
-  const int64_t total = S.knot_units_first[last] + S.tier_intervals[last] + 1;
+  const bool ret = S.delay_model == 1;
+  const int64_t total = ret ? S.n_opt_units
+                            : S.knot_units_first[last] +
+                                  (S.tier_up[last] > 1 ? int64_t(S.bl_knots[last]) : int64_t(S.tier_intervals[last]) + 1);
   const int64_t per_cta = (total + kParamChunks - 1) / kParamChunks;
   const int64_t per_thr = (per_cta + kParamThreads - 1) / kParamThreads;
   const int64_t lo = min(total, chunk * per_cta + threadIdx.x * per_thr);
   const int64_t hi = min(min(total, (chunk + 1) * per_cta), lo + per_thr);
-  if (S.dparams) {
+  if (S.dparams && !ret) {
     int t = 0;
     for (int64_t k = lo; k < hi; ++k) {
       while (t + 1 < S.n_tiers && k >= S.knot_units_first[t + 1]) ++t;
@@ -870,7 +983,25 @@ __global__ void __launch_bounds__(kParamThreads) k_param_partial(const __grid_co
       const int64_t j = k - S.knot_units_first[t];
       const double* gk = a.p.gk + 3 * (S.knot_base[t] + j);
       const double g[3] = {gk[0], gk[1], gk[2]};
-      add_source_jacobian(S, double(j * S.tier_step[t]) / S.fs, g, rows + threadIdx.x);
+      add_source_jacobian(S, double((j - S.knot_shift[t]) * S.tier_coarse[t]) / S.fs, g, rows + threadIdx.x);
+    }
+  } else if (S.dparams) {
+    const int64_t base = a.n_scenes > 1 ? a.tab.opt_prefix[s] : int64_t(0);
+    for (int64_t k = lo; k < hi; ++k) {
+      const OptUnit u = opt_unit(S, k);
+      const double gr = a.p.ograd[base + k];
+      if (gr == 0.0) continue;
+      const double tr = double(int64_t(u.k) * S.tier_step[u.t]) / S.fs;
+      double m[3], sg[3], D[3], e, v[3];
+      mic_at(S, u.mic, tr, m);
+      emission_vector(S, a.p.img_code[S.img_base + S.tier_first[u.t] + u.img], m, tr, a.p.otau[base + k] / S.fs, sg,
+                      D, &e);
+      const double d = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+      source_velocity(S, e, v);
+      const double su[3] = {sg[0] * D[0] / d, sg[1] * D[1] / d, sg[2] * D[2] / d};
+      const double f = gr / (1.0 + (su[0] * v[0] + su[1] * v[1] + su[2] * v[2]) / S.c);
+      const double g[3] = {f * su[0], f * su[1], f * su[2]};
+      add_source_jacobian(S, e, g, rows + threadIdx.x);
     }
   }
   __syncthreads();
@@ -878,6 +1009,199 @@ __global__ void __launch_bounds__(kParamThreads) k_param_partial(const __grid_co
     double acc = 0.0;
     for (int r = 0; r < kParamThreads; ++r) acc += rows[threadIdx.x * kParamThreads + r];
     a.p.ppart[(int64_t(s) * kParamChunks + chunk) * 48 + threadIdx.x] = acc;
+  }
+}
+
+// ------------------------------------------------- upsampled / emission-time tiers
+// Their delays are not linear in the knot positions, so their knot gradients
+// are formed per (mic, image, record knot) unit: k_opt_tau the FP64 delay at
+// every record knot, k_opt_grad dL/dd there (the samples of the two adjacent
+// intervals, from the degree-5 rows), then the chain rule: k_opt_bl_knots for
+// upsampled tiers (through the upsampler's weights to the knots, times the
+// unit vectors), k_param_partial for emission-time delays.
+
+// Delay tau (samples, FP64) at record knot k of unit u.
+//   upsampled tier: tau at virtual knot k = j0 U + p from the knots' delays,
+//   in the chord form of the synthesis (tau_j0 + Delta M_p + sum_i w_p[i] e_i,
+//   e_i the deviations from the chord through knots j0 and j0 + 1);
+//   emission-time delays: Newton's method on c tau = |Delta(t - tau)| with the
+//   path's velocity by central difference, from the reception-time distance.
+__global__ void k_opt_tau(const __grid_constant__ KernelArgs a) {
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= a.totals[9]) return;
+  int s = 0;
+  int64_t local = gid;
+  if (a.n_scenes > 1) {
+    s = find_scene(a.tab.opt_prefix, a.n_scenes, gid);
+    local = gid - a.tab.opt_prefix[s];
+  }
+  const SceneDev& S = scene_of(a, s);
+  const OptUnit u = opt_unit(S, local);
+  double tau;
+  if (S.delay_model == 1) {
+    const double tr = double(int64_t(u.k) * S.tier_step[u.t]) / S.fs;
+    const uint32_t code = a.p.img_code[S.img_base + S.tier_first[u.t] + u.img];
+    double m[3], sg[3], D[3], e;
+    mic_at(S, u.mic, tr, m);
+    emission_vector(S, code, m, tr, 0.0, sg, D, &e);
+    double ts = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]) / S.c;  // seconds
+    for (int it = 0; it < 40; ++it) {
+      emission_vector(S, code, m, tr, ts, sg, D, &e);
+      const double d = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+      double v[3];
+      source_velocity(S, e, v);
+      const double slope = S.c + (sg[0] * D[0] * v[0] + sg[1] * D[1] * v[1] + sg[2] * D[2] * v[2]) / d;
+      const double step = (S.c * ts - d) / slope;
+      ts -= step;
+      if (fabs(step) <= 1e-15 * ts) break;
+    }
+    tau = ts * S.fs;
+  } else {
+    const int U = S.tier_up[u.t], Q = S.up_q;
+    const int j0 = u.k / U, pp = u.k - j0 * U;
+    // the tier's knot table starts Q knots before t = 0
+    const float2* row = a.p.bl_tau + S.bl_tau_base[u.t] +
+                        (int64_t(u.mic) * S.tier_count[u.t] + u.img) * S.bl_knots[u.t] + Q;
+    const float* W = a.p.upw + S.upw_base[u.t] + pp * (2 * Q + 1);
+    auto tv = [&](int j) {
+      const float2 v = row[j];
+      return double(v.x) + double(v.y);
+    };
+    const double t0 = tv(j0), dl = tv(j0 + 1) - t0;
+    tau = t0 + dl * double(W[2 * Q]);
+    for (int i = 0; i < 2 * Q; ++i)
+      if (i != Q - 1 && i != Q) tau += double(W[i]) * (tv(j0 - Q + 1 + i) - t0 - double(i - Q + 1) * dl);
+  }
+  a.p.otau[gid] = tau;
+}
+
+// dL/dd at record knot k of unit u: sum over the samples n of intervals k - 1
+// and k of dL/dd_i(n) = -dy g (fs/c) (S de/dw + e / tau) times the linear
+// weight of knot k at n (the delay interpolated in FP64 from the FP64 knot
+// delays; e and de/dw from the degree-5 rows in global memory). One warp per
+// unit, lanes over samples, FP64 sum in a fixed order.
+__global__ void __launch_bounds__(256) k_opt_grad(const __grid_constant__ KernelArgs a) {
+  const int64_t gid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gid >= a.totals[9]) return;
+  int s = 0;
+  int64_t local = gid;
+  if (a.n_scenes > 1) {
+    s = find_scene(a.tab.opt_prefix, a.n_scenes, gid);
+    local = gid - a.tab.opt_prefix[s];
+  }
+  const SceneDev& S = scene_of(a, s);
+  const OptUnit u = opt_unit(S, local);
+  const int N = S.tier_step[u.t];
+  const double* kt = a.p.otau + (gid - u.k);  // the row's knot delays
+  const double G = double(a.p.img_gain[S.img_base + S.tier_first[u.t] + u.img]);
+  const float* dy = S.dy + int64_t(u.mic) * S.n_out;
+  const int64_t lo = max(int64_t(u.k - 1) * N, int64_t(0));
+  const int64_t hi = min(int64_t(u.k + 1) * N, S.n_out);
+  const float4* zq = a.p.zq + S.z_base;
+  const float2* zg = a.p.zg + S.z_base;
+  double acc = 0.0;
+  for (int64_t n = lo + lane; n < hi; n += 32) {
+    const int j = int(n / N);
+    const double r = double(n - int64_t(j) * N) / N;
+    const double tau = kt[j] + (kt[j + 1] - kt[j]) * r;
+    const double wk = (j == u.k) ? 1.0 - r : r;
+    const double pos = double(n) - tau;
+    const double m0 = floor(pos);
+    const double v = double(kFarrowSegs) * (pos - m0);
+    const int seg = min(int(v), kFarrowSegs - 1);
+    const float w = float(v - seg - 0.5);
+    const int64_t col = int64_t(m0) - S.z_m0;
+    if (col < 0 || col >= S.z_len) continue;  // outside the rows: x is zero there
+    float pe, pd;
+    horner_d5(zq[int64_t(seg) * S.z_len + col], zg[int64_t(seg) * S.z_len + col], w, &pe, &pd);
+    const double g = G / tau;  // gain beta / (4 pi d)
+    const double ad = -double(dy[n]) * double(S.fsc) * g * (double(kFarrowSegs) * pd + double(pe) / tau);
+    acc += wk * ad;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) a.p.ograd[gid] = acc;
+}
+
+// dL/ds(t_j) at knot j of an upsampled tier (one CTA per knot of the tier's
+// table, knots -Q .. J_c + Q): over every (mic, image), dL/dd at the knot,
+// sum_k w_eff(k, j) dL/dd(record knot k), times sigma o Delta / d at the knot.
+// The effective weights are the chord form's derivatives: w_p[i] off the chord's
+// two knots, M_p - sum' w_p[i] c_i for knot j0 + 1 and
+// 1 - M_p - sum' w_p[i] (1 - c_i) for knot j0 (c_i = i - Q + 1; sum' over i
+// other than the chord's knots). Fixed-order sums.
+constexpr int kBlThreads = 256;
+__global__ void __launch_bounds__(kBlThreads) k_opt_bl_knots(const __grid_constant__ KernelArgs a) {
+  __shared__ float weff[kMaxUpsample * 2 * kMaxUpHalfwidth];
+  __shared__ double part[3][kBlThreads];
+  const int64_t gid = blockIdx.x;
+  if (gid >= a.totals[1]) return;
+  int s = 0;
+  int64_t local = gid;
+  if (a.n_scenes > 1) {
+    s = find_scene(a.tab.knots_prefix, a.n_scenes, gid);
+    local = gid - a.tab.knots_prefix[s];
+  }
+  const SceneDev& S = scene_of(a, s);
+  int t = 0;
+  while (t + 1 < S.n_tiers && local >= S.knot_units_first[t + 1]) ++t;
+  if (S.tier_up[t] <= 1 || S.delay_model == 1) return;
+  const int jt = int(local - S.knot_units_first[t]);
+  const int U = S.tier_up[t], Q = S.up_q;
+  const int j = jt - Q;  // the knot's index (time j N_c / fs)
+  for (int pp = threadIdx.x; pp < U; pp += kBlThreads) {
+    const float* W = a.p.upw + S.upw_base[t] + pp * (2 * Q + 1);
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = 0; i < 2 * Q; ++i)
+      if (i != Q - 1 && i != Q) {
+        weff[pp * 2 * Q + i] = W[i];
+        s0 += double(W[i]);
+        s1 += double(W[i]) * double(i - Q + 1);
+      }
+    const double M = double(W[2 * Q]);
+    weff[pp * 2 * Q + Q] = float(M - s1);
+    weff[pp * 2 * Q + Q - 1] = float(1.0 - M - s0 + s1);
+  }
+  __syncthreads();
+  const int nk = S.tier_intervals[t] + 1;
+  const int k_lo = max((j - Q) * U, 0), k_hi = min((j + Q) * U - 1, nk - 1);
+  const int64_t rows = int64_t(S.n_mics) * S.tier_count[t];
+  const int64_t base = (a.n_scenes > 1 ? a.tab.opt_prefix[s] : int64_t(0)) + S.opt_units_first[t];
+  const double* sp = a.p.knot_pos + 3 * (S.knot_base[t] + jt);
+  const double* ap = a.p.arr_pos + 3 * (S.knot_base[t] + jt);
+  double gx = 0.0, gy = 0.0, gz = 0.0;
+  for (int64_t r = threadIdx.x; r < rows; r += kBlThreads) {
+    const double* gr = a.p.ograd + base + r * nk;
+    double cg = 0.0;
+    for (int k = k_lo; k <= k_hi; ++k) {
+      const int j0 = k / U;
+      cg += double(weff[(k - j0 * U) * 2 * Q + (j - j0 + Q - 1)]) * gr[k];
+    }
+    const int mic = int(r / S.tier_count[t]);
+    const int img = int(r - int64_t(mic) * S.tier_count[t]);
+    int n[3], p[3];
+    unpack_image(a.p.img_code[S.img_base + S.tier_first[t] + img], n, p);
+    double D[3], sg[3], dd = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      sg[d] = p[d] ? -1.0 : 1.0;
+      const double m = S.mics[mic][d] + (S.arr_moving ? ap[d] : 0.0);
+      D[d] = sg[d] * sp[d] + 2.0 * n[d] * S.dims[d] - m;
+      dd += D[d] * D[d];
+    }
+    const double f = cg / sqrt(dd);
+    gx += f * sg[0] * D[0];
+    gy += f * sg[1] * D[1];
+    gz += f * sg[2] * D[2];
+  }
+  part[0][threadIdx.x] = gx;
+  part[1][threadIdx.x] = gy;
+  part[2][threadIdx.x] = gz;
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double acc = 0.0;
+    for (int r = 0; r < kBlThreads; ++r) acc += part[threadIdx.x][r];
+    a.p.gk[3 * (S.knot_base[t] + jt) + threadIdx.x] = acc;
   }
 }
 
@@ -932,6 +1256,7 @@ cudaError_t persistent_launch(K kern, size_t smem, int64_t items, const KernelAr
 static const TileConfig kBwConfig = {kBwThreads, kBwChunks, kGradWcap, kBwRecCap, kBwBlock};
 const TileConfig& backward_tile_config() { return kBwConfig; }
 size_t backward_unit_cap() { return kBwUnitCap; }
+int64_t backward_bl_scratch_floats() { return kGradScratchFloats < kRecScratchFloats ? kGradScratchFloats : kRecScratchFloats; }
 int backward_group_images() { return kDxGroupImages; }
 
 cudaError_t launch_prefilter(const KernelArgs& a, cudaStream_t st, bool gradient_rows);
@@ -942,6 +1267,7 @@ cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
   // per device and kernel: shared-memory limit and persistent grid
   static PerDevice g_grad, g_dx16, g_dx32, g_dx64;
   if (a.totals[0] > 0) k_beta_table<<<unsigned((a.totals[0] + 255) / 256), 256, 0, st>>>(a);
+  if (a.totals[9] > 0) k_opt_tau<<<unsigned((a.totals[9] + 127) / 128), 128, 0, st>>>(a);
   e = persistent_launch(k_adj_grad, kGradSmem, a.totals[4], a, st, &g_grad);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.p.dxb, 0, sizeof(float) * size_t(a.p.dxb_floats), st);
@@ -952,8 +1278,10 @@ cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int T = 256;
   if (a.totals[2] > 0) k_dx_final<<<unsigned((a.totals[2] + T - 1) / T), T, 0, st>>>(a);
+  if (a.totals[9] > 0) k_opt_grad<<<unsigned((a.totals[9] * 32 + 255) / 256), 256, 0, st>>>(a);
   if (a.totals[1] > 0)
     k_knot_final<<<unsigned((a.totals[1] + kKnotsPerCta - 1) / kKnotsPerCta), kKnotsPerCta * kKnotLanes, 0, st>>>(a);
+  if (a.totals[6] > 0 && a.totals[1] > 0) k_opt_bl_knots<<<unsigned(a.totals[1]), kBlThreads, 0, st>>>(a);
   {
     constexpr size_t smem = 48 * kParamThreads * sizeof(double);
     static PerDevice attr;  // the shared-memory limit, once per device

@@ -25,59 +25,6 @@ __device__ __forceinline__ int locate(const KernelArgs& a, const int64_t* prefix
   return s;
 }
 
-// Point of a trajectory (FP64): line p0 + v t dir/|dir|, circle
-// centre + R (cos, sin, 0)(theta0 + v t / R), or clamped uniform cubic B-spline
-// by de Boor's algorithm on the knot vector {0,0,0,0, 1/m, ..., (m-1)/m, 1,1,1,1}
-// with u = clamp(t / duration, 0, 1).
-__device__ void trajectory_point(int kind, const double* p, int n_ctrl, double duration, double t,
-                                 double out[3]) {
-  if (kind == 0) {
-    const double inv = 1.0 / sqrt(p[3] * p[3] + p[4] * p[4] + p[5] * p[5]);
-    for (int d = 0; d < 3; ++d) out[d] = p[d] + p[6] * t * p[3 + d] * inv;
-  } else if (kind == 1) {
-    const double ang = p[5] + p[4] * t / p[3];
-    double sn, cs;
-    sincos(ang, &sn, &cs);
-    out[0] = p[0] + p[3] * cs;
-    out[1] = p[1] + p[3] * sn;
-    out[2] = p[2];
-  } else {
-    const int m = n_ctrl - 3;  // segments
-    double u = t / duration;
-    u = fmin(1.0, fmax(0.0, u));
-    int span = min(int(u * m), m - 1);  // segment index
-    // knot i of the clamped vector: clamp((i - 3) / m, 0, 1)
-    auto knot = [m](int i) { return fmin(1.0, fmax(0.0, double(i - 3) / double(m))); };
-    double dd[4][3];
-    for (int j = 0; j < 4; ++j)
-      for (int c = 0; c < 3; ++c) dd[j][c] = p[3 * (span + j) + c];
-    const int k = span + 3;
-    for (int r = 1; r <= 3; ++r)
-      for (int j = 3; j >= r; --j) {
-        const int i = j + k - 3;
-        const double den = knot(i + 4 - r) - knot(i);
-        const double al = den > 0.0 ? (u - knot(i)) / den : 0.0;
-        for (int c = 0; c < 3; ++c) dd[j][c] = (1.0 - al) * dd[j - 1][c] + al * dd[j][c];
-      }
-    for (int c = 0; c < 3; ++c) out[c] = dd[3][c];
-  }
-}
-
-// Source position s(t).
-__device__ void source_position(const SceneDev& S, double t, double out[3]) {
-  trajectory_point(S.traj_kind, S.traj, S.n_ctrl, S.duration, t, out);
-}
-
-// Displacement of the microphone array a(t) - a(0) (zero for a static array).
-__device__ void array_displacement(const SceneDev& S, double t, double out[3]) {
-  out[0] = out[1] = out[2] = 0.0;
-  if (!S.arr_moving) return;
-  double a0[3], at[3];
-  trajectory_point(S.arr_kind, S.arr_params, S.arr_n_ctrl, S.arr_duration, 0.0, a0);
-  trajectory_point(S.arr_kind, S.arr_params, S.arr_n_ctrl, S.arr_duration, t, at);
-  for (int d = 0; d < 3; ++d) out[d] = at[d] - a0[d];
-}
-
 __device__ __forceinline__ int tier_of(const SceneDev& S, int rho) {
   for (int t = 0; t < S.n_tiers; ++t)
     if (rho <= S.tier_max_rho[t]) return t;

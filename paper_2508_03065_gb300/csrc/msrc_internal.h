@@ -132,6 +132,11 @@ struct SceneDev {
   int64_t kslot_mic_stride;                // slots per microphone
   int32_t kcap[MSRC_MAX_TIERS];            // knot slots per (block, tile) item of tier t
   int64_t bpart_base;                      // first float of the per-(mic, block) beta partials
+  // reverse mode over tiers whose delays are not linear in the knot positions
+  // (band-limited upsampling, emission-time delays): one unit per
+  // (microphone, image, record knot), [mic][image][knot] from opt_units_first[t]
+  int64_t opt_units_first[MSRC_MAX_TIERS];
+  int64_t n_opt_units;
   float c_over_fs;                         // metres per sample of delay
   float fsc;                               // fs / c (samples of delay per metre), FP32
   double fs_over_c;                        // fs / c, FP64
@@ -159,6 +164,8 @@ struct LaunchTables {
   const int64_t* bl_prefix;      // knot delays of upsampled tiers
   const int64_t* dense_prefix;   // source path table entries (emission-time delays)
   const int64_t* img_prefix;     // images (lattice order, once per scene)
+  const int64_t* opt_prefix;     // reverse mode: (mic, image, record knot) units of the
+                                 // upsampled and emission-time tiers
 };
 // Image table units of the enumeration and sort: time groups x images. Sort
 // key: (scene's time group << kSortGroupShift) | (tier << 24) | distance (24 bits).
@@ -199,6 +206,8 @@ struct DevicePtrs {
   double* ppart;                 // trajectory-parameter partials (48 doubles per (scene, knot chunk))
   float4* bwt;                   // per image: dbeta_i/dbeta_w / (4 pi) for walls 0..3 | walls 4..5, gain, 0
   float2* trange;                // reverse mode: delay range (tmin, tmax) of every (mic, block, tile) item
+  double* otau;                  // reverse mode, upsampled / emission-time tiers: FP64 delay (samples)
+  double* ograd;                 //   and dL/dd at every (mic, image, record knot) unit
   // band-limited knot upsampling: per (scene, tier) a table of tier_up rows
   // of 2 up_q + 1 floats, row p = the normalised kernel weights of knots
   // j0 - up_q + 1 .. j0 + up_q at the virtual knot p / tier_up past knot j0,
@@ -214,13 +223,14 @@ struct DevicePtrs {
 };
 constexpr int kParamPartialsPerScene = 32 * 48;
 
-constexpr int kUnitKinds = 9;
+constexpr int kUnitKinds = 10;
 
 struct KernelArgs {
   SceneDev scene0;               // used when n_scenes == 1
   const SceneDev* scenes;        // used when n_scenes > 1
   int32_t n_scenes;
-  int64_t totals[kUnitKinds];    // total units per kernel kind (enum, knots, rec, z, item, red, bl, dense, img)
+  int64_t totals[kUnitKinds];    // total units per kernel kind (enum, knots, rec, z, item, red, bl, dense,
+                                 // img, opt)
   LaunchTables tab;
   DevicePtrs p;
   float farrow[kFarrowSegs][kFarrowCoef][kMaxTaps];  // coefficients c[s][q][k + L/2] of the powers of w
@@ -286,6 +296,9 @@ cudaError_t persistent_grid(PerDevice& cache, K kern, int threads, size_t smem, 
 cudaError_t launch_setup(const KernelArgs& a, cudaStream_t s);
 // Reverse-mode tile configuration (threads = tile samples, one per thread).
 const TileConfig& backward_tile_config();
+// Shared-memory floats both reverse-mode kernels give the band-limited record
+// builder's scratch.
+int64_t backward_bl_scratch_floats();
 cudaError_t launch_forward(const KernelArgs& a, int tile_config, cudaStream_t s,
                            cudaEvent_t* ev /* nullable: [after prefilter, after synthesis] */);
 size_t sort_temp_bytes(int64_t n_items, int end_bit);

@@ -244,12 +244,13 @@ def test_array_trajectory_validation():
 
 
 def test_band_limited_upsampling_planning():
-    """Band-limited tiers plan a forward call, refuse reverse mode, and check
-    the path's extension before t = 0 that their knots reach."""
+    """Band-limited tiers plan forward and reverse-mode calls (the reverse
+    mode adds the per-(mic, image, record knot) delay and gradient tables), and
+    check the path's extension before t = 0 that their knots reach."""
     lib = _lib.load()
     n = _lib.i64_array([16000])
     arr, p = _mics((2.5, 2.0, 1.2))
-    sizes = []
+    sizes, bsizes = [], []
     for tiers in ([(1, 16000.0), (2**31 - 1, 5.0)], [(1, 16000.0), (2**31 - 1, 5.0, 100)]):
         st, h = _create(tiers=tiers)
         assert st == _lib.OK
@@ -258,10 +259,12 @@ def test_band_limited_upsampling_planning():
         fwd, bwd = ctypes.c_size_t(), ctypes.c_size_t()
         assert lib.msrc_workspace_size(hs, 1, n, n, ctypes.byref(fwd), None) == _lib.OK
         sizes.append(fwd.value)
-        st = lib.msrc_workspace_size(hs, 1, n, n, None, ctypes.byref(bwd))
-        assert st == (_lib.OK if len(tiers[1]) == 2 else _lib.ERR_UNSUPPORTED)
+        assert lib.msrc_workspace_size(hs, 1, n, n, None, ctypes.byref(bwd)) == _lib.OK
+        bsizes.append(bwd.value)
         lib.msrc_destroy_room(h)
     assert sizes[1] > sizes[0]
+    # reverse mode: the upsampled tier's images x 1601 record knots x 2 doubles more
+    assert bsizes[1] > bsizes[0]
     # 2 m/s along (3, 2, 0) from x = 1 m: inside the room on [0, 1] s, but the
     # 5 Hz tier's kernel reaches 4 knots (0.8 s) before t = 0, where x < 0
     fast = _traj(params=(1.0, 1.0, 1.5, 3.0, 2.0, 0.0, 2.0))

@@ -105,6 +105,37 @@ def test_random_scene_dx_parity(i):
     assert err < TOL, (spec.name, err)
 
 
+def _has_option_tiers(spec) -> bool:
+    return spec.delay_model == 1 or any(len(t) == 3 and t[2] > 1 for t in spec.tiers)
+
+
+# the random scenes with upsampled tiers or emission-time delays
+OPTION_CASES = [i for i in range(N_CASES) if _has_option_tiers(random_spec(i))]
+
+
+@pytest.mark.parametrize("i", OPTION_CASES[:12])
+def test_random_option_scene_dx_parity(i):
+    # reverse mode on the forward generator's scenes that upsample a tier or
+    # take emission-time delays
+    spec = random_spec(i)
+    room = api.Room.from_spec(spec)
+    dy = np.random.default_rng(9200 + i).standard_normal((len(spec.mics), spec.n_out)).astype(np.float32)
+    x = torch.from_numpy(spec.x).cuda()
+    ws = api.Workspace()
+    dx = api.synthesize_backward([room], [x], [torch.from_numpy(dy).cuda()], want_params=False,
+                                 want_beta=False, workspace=ws)[0][0]
+    torch.cuda.synchronize()
+    assert api.workspace_errors(ws) == 0
+    dx = dx.cpu().numpy().astype(np.float64)
+    ref, env = np.zeros(spec.n_in), np.zeros(spec.n_in)
+    for m in range(len(spec.mics)):
+        r, e = oracle.adjoint_x_envelope(oracle_scene(spec, m), dy[m].astype(np.float64), spec.n_in, WRAP_DELTA)
+        ref += r
+        env += e
+    err = beyond_envelope(dx, ref, env)
+    assert err < TOL, (spec.name, err)
+
+
 def test_random_batch_equals_single_calls():
     # one batched launch over 8 heterogeneous random scenes (taps and window
     # shared, as a batch requires) equals the per-scene calls bitwise
