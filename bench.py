@@ -452,27 +452,15 @@ def run_batched(args, torch, api, W):
                    "call per scene on the same stream (same kernels and tile configuration)"}
 
 
-def run_backward(args, torch, api, W, n_scenes=16):
-    """The 16 differentiation scenes (6x5x3 m, order 8, 2 s at 16 kHz): one
-    batched forward and one batched backward (dx, trajectory and wall
-    gradients of 0.5 ||y - y*||^2)."""
-    pairs = [W.config4_scene(s) for s in range(n_scenes)]
-    rooms = [api.Room.from_spec(sp) for sp, _ in pairs]
-    xs = [torch.from_numpy(sp.x).cuda() for sp, _ in pairs]
-    tg = [torch.from_numpy(t).cuda() for _, t in pairs]
-    ws = api.Workspace("cuda")
-    work = sum(r.image_count()[0] * sp.n_in * r.n_mics for r, (sp, _) in zip(rooms, pairs))
+def _fwd_bwd_ms(torch, api, rooms, xs, tg, ws, reps=3):
+    """Mean device time (ms) of one batched forward and one batched backward
+    (dx, trajectory and wall gradients of 0.5 ||y - y*||^2), after 2 warm-up
+    steps."""
     stream = torch.cuda.current_stream()
-
-    def step():
-        ys = api.synthesize(rooms, xs, workspace=ws)
-        dys = [y - t[None] for y, t in zip(ys, tg)]
-        return api.synthesize_backward(rooms, xs, dys, workspace=ws)
-
     for _ in range(2):
-        step()
+        ys = api.synthesize(rooms, xs, workspace=ws)
+        api.synthesize_backward(rooms, xs, [y - t[None] for y, t in zip(ys, tg)], workspace=ws)
     torch.cuda.synchronize()
-    reps = 3
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     t_f = t_b = 0.0
     for _ in range(reps):
@@ -485,9 +473,38 @@ def run_backward(args, torch, api, W, n_scenes=16):
         torch.cuda.synchronize()
         t_f += e0.elapsed_time(e1) / reps
         t_b += e1.elapsed_time(e2) / reps
-    return {"scenes": n_scenes, "image_samples": work, "forward_ms": t_f, "backward_ms": t_b,
-            "forward_value": work / (t_f * 1e-3), "backward_value": work / (t_b * 1e-3), "unit": UNIT,
-            "grads": "dx (32000), 18 spline control-point coordinates, 6 wall coefficients per scene"}
+    return t_f, t_b
+
+
+def run_backward(args, torch, api, W, n_scenes=16):
+    """The 16 differentiation scenes (6x5x3 m, order 8, 2 s at 16 kHz): one
+    batched forward and one batched backward (dx, trajectory and wall
+    gradients of 0.5 ||y - y*||^2). The same scenes also with their last tier
+    on 200 Hz knots upsampled x8 (records every 10 samples) and with
+    emission-time delays."""
+    from dataclasses import replace
+
+    pairs = [W.config4_scene(s) for s in range(n_scenes)]
+    xs = [torch.from_numpy(sp.x).cuda() for sp, _ in pairs]
+    tg = [torch.from_numpy(t).cuda() for _, t in pairs]
+    ws = api.Workspace("cuda")
+    out = None
+    for name, f in (("linear", lambda sp: sp),
+                    ("upsampled", lambda sp: replace(sp, tiers=[(1, 16000.0), (W.RHO_INF, 200.0, 8)],
+                                                     up_halfwidth=4)),
+                    ("emission_time", lambda sp: replace(sp, delay_model=1))):
+        specs = [f(sp) for sp, _ in pairs]
+        rooms = [api.Room.from_spec(sp) for sp in specs]
+        work = sum(r.image_count()[0] * sp.n_in * r.n_mics for r, sp in zip(rooms, specs))
+        t_f, t_b = _fwd_bwd_ms(torch, api, rooms, xs, tg, ws)
+        rec = {"forward_ms": t_f, "backward_ms": t_b, "forward_value": work / (t_f * 1e-3),
+               "backward_value": work / (t_b * 1e-3)}
+        if out is None:
+            out = {"scenes": n_scenes, "image_samples": work, **rec, "unit": UNIT,
+                   "grads": "dx (32000), 18 spline control-point coordinates, 6 wall coefficients per scene"}
+        else:
+            out[name] = rec
+    return out
 
 
 def run_array(args, torch, api, W):

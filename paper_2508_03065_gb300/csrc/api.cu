@@ -473,7 +473,7 @@ struct Plan {
   int cfg = 0;                      // forward tile configuration
   int64_t dxb_floats = 0;
   size_t off_dxb = 0, off_kslot = 0, off_bpart = 0, off_gk = 0, off_ppart = 0, off_bwt = 0, off_trange = 0;
-  size_t off_otau = 0, off_ograd = 0;
+  size_t off_otau = 0, off_ograd = 0, off_cgrad = 0;
   int kL = 32;
   int taps = 32;
   // band-limited knot upsampling: weight tables (uploaded to off_upw)
@@ -815,6 +815,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     P.off_trange = off; off = align256(off + 8 * size_t(P.totals[4]));
     P.off_otau = off; off = align256(off + 8 * size_t(P.totals[9]));
     P.off_ograd = off; off = align256(off + 8 * size_t(P.totals[9]));
+    P.off_cgrad = off; off = align256(off + 4 * size_t(bl_acc));
   }
   P.fwd_bytes = off;
   if (I > (size_t(1) << 31)) return fail(MSRC_ERR_UNSUPPORTED, "more than 2^31 images in one call");
@@ -866,7 +867,8 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
     a.p.bwt = reinterpret_cast<float4*>(ws + P.off_bwt);
     a.p.trange = reinterpret_cast<float2*>(ws + P.off_trange);
     a.p.otau = reinterpret_cast<double*>(ws + P.off_otau);
-    a.p.ograd = reinterpret_cast<double*>(ws + P.off_ograd);
+    a.p.ograd = reinterpret_cast<float2*>(ws + P.off_ograd);
+    a.p.cgrad = reinterpret_cast<float*>(ws + P.off_cgrad);
   }
   // device tables: coefficients of the powers of w = v / 2 (c_q 2^q, exact)
   for (int sg = 0; sg < kFarrowSegs; ++sg)

@@ -151,25 +151,37 @@ static_assert(kBwTile + 1 <= kBwTile + 4, "microphone path of every knot of a ti
 __device__ __forceinline__ bool opt_tier(const SceneDev& S, int t) { return S.delay_model == 1 || S.tier_up[t] > 1; }
 
 // Records of one item in layout kLayout, by the builder of the item's tier:
-// emission-time delays, band-limited upsampling (scratch from u_s on, bl_cap
-// floats) or linear knots (d_s, nullable, receives the knot distances).
-// Returns the item's image count: 0 when the upsampler's scratch did not fit
-// (the builder then flags the error word and writes no record).
+// emission-time delays, band-limited upsampling (scratch from u_s on,
+// kRecScratchFloats floats) or linear knots (d_s, nullable, receives the knot
+// distances). Returns the item's image count: 0 when the upsampler's scratch
+// did not fit (the builder then flags the error word and writes no record).
+// For the two option builders, dfl_out (cnt floats, nullable) receives the
+// anchors D and *phi_out the relative knot delays phi (cnt x nk): the delay at
+// knot jf + jj of image ib is D[ib] + phi[ib * nk + jj].
 template <int kLayout>
 __device__ int adjoint_records(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
-                               int4* img_s, float4* u_s, float4* um_s, float4* anc_s, float* phi_s,
-                               int64_t bl_cap, float* tmin, float* tmax, float* d_s = nullptr) {
+                               int4* img_s, float4* u_s, float4* um_s, float4* anc_s, float* phi_s, float* tmin,
+                               float* tmax, float* d_s = nullptr, float* dfl_out = nullptr,
+                               const float** phi_out = nullptr) {
   if (S.delay_model == 1) {
-    item_records_ret<kBwThreads, kLayout>(a, S, g, rec_s, img_s, u_s, um_s, phi_s, tmin, tmax);
+    item_records_ret<kBwThreads, kLayout>(a, S, g, rec_s, img_s, u_s, um_s, phi_s, tmin, tmax, 1.0f, dfl_out);
+    if (phi_out) *phi_out = phi_s;
     return g.cnt;
   }
   if (S.tier_up[g.t] > 1)
-    return item_records_bl<kBwThreads, kLayout>(a, S, g, rec_s, img_s, reinterpret_cast<float*>(u_s), bl_cap, tmin,
-                                                tmax)
+    return item_records_bl<kBwThreads, kLayout>(a, S, g, rec_s, img_s, reinterpret_cast<float*>(u_s),
+                                                kRecScratchFloats, tmin, tmax, 1.0f, dfl_out, phi_out)
                ? g.cnt
                : 0;
   item_records<kBwThreads, kLayout>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, tmin, tmax, 1.0f, d_s);
   return g.cnt;
+}
+
+// First (mic, image, record knot) unit of tier t of scene s in the global
+// option-unit tables (otau, ograd), laid out [mic][knot][image] (J_t + 1
+// knots), so that consecutive images of one knot are adjacent.
+__device__ __forceinline__ int64_t opt_row0(const KernelArgs& a, const SceneDev& S, int s, int t) {
+  return (a.n_scenes > 1 ? a.tab.opt_prefix[s] : int64_t(0)) + S.opt_units_first[t];
 }
 
 // The gradient kernel's image loop for this thread's chunks, over image pairs
@@ -317,8 +329,26 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     const bool opt = opt_tier(S, g.t);
 
     float tmin, tmax;
-    g.cnt = adjoint_records<kRecAdjoint>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, kGradScratchFloats, &tmin,
-                                         &tmax, dk_s);
+    const float* kphi = nullptr;
+    g.cnt = adjoint_records<kRecAdjoint>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax, dk_s, dk_s,
+                                         &kphi);
+    if (opt && g.cnt > 0) {
+      // the knot delays D + phi of the item's images, each (mic, image, knot)
+      // written by exactly one item: the tile holding the knot's sample, the
+      // last tile for the knot past the output
+      const int nk = g.nk;
+      const bool last_tile = g.n_end == S.n_out - 1;
+      const int J1 = S.tier_intervals[g.t] + 1;
+      const int cnt_t = S.tier_count[g.t];
+      double* obase = a.p.otau + opt_row0(a, S, s, g.t) + int64_t(g.mic) * J1 * cnt_t + g.img0;
+      for (int i = threadIdx.x; i < g.cnt * nk; i += kBwThreads) {
+        const int jj = i / g.cnt, ib = i - jj * g.cnt;
+        const int k = g.jf + jj;
+        const int64_t kn = int64_t(k) * g.N;
+        if ((kn >= g.n0 && kn <= g.n_end) || (last_tile && kn > g.n_end))
+          obase[int64_t(k) * cnt_t + ib] = double(dk_s[ib]) + double(kphi[ib * nk + jj]);
+      }
+    }
     // paired layouts of the image loop: unit vectors per (pair, knot) as
     // {x, x', y, y'} and {z, z'}, wall weights per pair as three float4 of
     // (w, w') pairs; an odd block's zero-gain copy gets zeros
@@ -706,8 +736,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
           if (!single || p0 == 0) {
             float lo, hi;
             __syncthreads();  // the previous block's records are no longer read
-            cnt_b = adjoint_records<kRecPlain>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, kRecScratchFloats,
-                                               &lo, &hi);
+            cnt_b = adjoint_records<kRecPlain>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &lo, &hi);
           }
           __syncthreads();  // records and the zeroed window are complete
           if (width <= kDxWcap)
@@ -844,73 +873,115 @@ __global__ void __launch_bounds__(kKnotsPerCta * kKnotLanes) k_knot_final(const 
   }
 }
 
-// Adds J(t)^T g to every trajectory parameter, J = ds(t)/dparams (3 x 48):
-// row[p * kParamThreads] += sum_d J[d][p] g[d].
 constexpr int kParamThreads = 256;
-constexpr int kParamChunks = 32;  // CTAs per scene of the parameter reduction
+constexpr int kParamChunks = 128;  // CTAs per scene of the parameter reduction
 static_assert(kParamChunks * 48 == kParamPartialsPerScene, "parameter partials per scene");
 
-__device__ void add_source_jacobian(const SceneDev& S, double t, const double g[3], double* row) {
-  const double* q = S.traj;
-  constexpr int st = kParamThreads;
-  if (S.traj_kind == 0) {  // s = p0 + v t u, u = dir / |dir|
-    const double nrm = sqrt(q[3] * q[3] + q[4] * q[4] + q[5] * q[5]);
-    const double u[3] = {q[3] / nrm, q[4] / nrm, q[5] / nrm};
-    const double ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
-    const double f = q[6] * t / nrm;
-    for (int d = 0; d < 3; ++d) {
-      row[d * st] += g[d];
-      row[(3 + d) * st] += f * (g[d] - u[d] * ug);
-    }
-    row[6 * st] += t * ug;
-  } else if (S.traj_kind == 1) {  // s = c + R (cos th, sin th, 0), th = th0 + v t / R
-    const double R = q[3], v = q[4];
-    double sn, cs;
-    sincos(q[5] + v * t / R, &sn, &cs);
-    const double w = v * t / R;
-    for (int d = 0; d < 3; ++d) row[d * st] += g[d];
-    row[3 * st] += (cs + sn * w) * g[0] + (sn - cs * w) * g[1];
-    row[4 * st] += t * (cs * g[1] - sn * g[0]);
-    row[5 * st] += R * (cs * g[1] - sn * g[0]);
-  } else {  // clamped uniform cubic B-spline: s = sum_c N_c(u) P_c
-    const int m = S.n_ctrl - 3;
-    const double u = fmin(1.0, fmax(0.0, t / S.duration));
-    const int span = min(int(u * m), m - 1);
-    auto knot = [m](int i) { return fmin(1.0, fmax(0.0, double(i - 3) / double(m))); };
-    // the four non-zero basis functions on the span (triangular scheme)
-    const int K = span + 3;
-    double Nb[4], left[4], right[4];
-    Nb[0] = 1.0;
-    for (int jdeg = 1; jdeg <= 3; ++jdeg) {
-      left[jdeg] = u - knot(K + 1 - jdeg);
-      right[jdeg] = knot(K + jdeg) - u;
-      double saved = 0.0;
-      for (int rr = 0; rr < jdeg; ++rr) {
-        const double den = right[rr + 1] + left[jdeg - rr];
-        const double tmp = den != 0.0 ? Nb[rr] / den : 0.0;
-        Nb[rr] = saved + right[rr + 1] * tmp;
-        saved = left[jdeg - rr] * tmp;
-      }
-      Nb[jdeg] = saved;
-    }
-    for (int r = 0; r < 4; ++r)
-      for (int d = 0; d < 3; ++d) row[(3 * (span + r) + d) * st] += Nb[r] * g[d];
-  }
+// J(t)^T g for the trajectory parameters, J = ds(t)/dparams (3 x 48): its
+// non-zero terms form one block of consecutive parameters, v[i] for parameter
+// p0 + i (returned p0; jacobian_count terms: line 7, circle 6, spline 12, the
+// four control points of t's span). In the scalar T: FP64 for the knots, FP32
+// for the emission-time units (images x knots of them).
+__device__ __forceinline__ void sin_cos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ void sin_cos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ int jacobian_count(const SceneDev& S) {
+  return S.traj_kind == 0 ? 7 : (S.traj_kind == 1 ? 6 : 12);
 }
 
-// Source velocity ds/dt at time t (FP64 central difference; only the
-// emission-time chain rule's denominator uses it, where its error is divided
-// by c).
-__device__ void source_velocity(const SceneDev& S, double t, double v[3]) {
-  constexpr double h = 1e-6;
-  double p1[3], p0[3];
-  source_position(S, t + h, p1);
-  source_position(S, t - h, p0);
-  for (int d = 0; d < 3; ++d) v[d] = (p1[d] - p0[d]) / (2.0 * h);
+template <class T>
+__device__ int jacobian_terms(const SceneDev& S, T t, const T g[3], T v[12]) {
+  const double* q = S.traj;
+  if (S.traj_kind == 0) {  // s = p0 + v t u, u = dir / |dir|
+    const T nrm = sqrt(T(q[3]) * T(q[3]) + T(q[4]) * T(q[4]) + T(q[5]) * T(q[5]));
+    const T u[3] = {T(q[3]) / nrm, T(q[4]) / nrm, T(q[5]) / nrm};
+    const T ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
+    const T f = T(q[6]) * t / nrm;
+    for (int d = 0; d < 3; ++d) {
+      v[d] = g[d];
+      v[3 + d] = f * (g[d] - u[d] * ug);
+    }
+    v[6] = t * ug;
+    return 0;
+  }
+  if (S.traj_kind == 1) {  // s = c + R (cos th, sin th, 0), th = th0 + v t / R
+    const T R = T(q[3]), vel = T(q[4]);
+    T sn, cs;
+    sin_cos(T(q[5]) + vel * t / R, &sn, &cs);
+    const T w = vel * t / R;
+    for (int d = 0; d < 3; ++d) v[d] = g[d];
+    v[3] = (cs + sn * w) * g[0] + (sn - cs * w) * g[1];
+    v[4] = t * (cs * g[1] - sn * g[0]);
+    v[5] = R * (cs * g[1] - sn * g[0]);
+    return 0;
+  }
+  // clamped uniform cubic B-spline: s = sum_c N_c(u) P_c
+  const int m = S.n_ctrl - 3;
+  const T u = fmin(T(1), fmax(T(0), t / T(S.duration)));
+  const int span = min(int(u * T(m)), m - 1);
+  auto knot = [m](int i) { return fmin(T(1), fmax(T(0), T(i - 3) / T(m))); };
+  // the four non-zero basis functions on the span (triangular scheme)
+  const int K = span + 3;
+  T Nb[4], left[4], right[4];
+  Nb[0] = T(1);
+  for (int jdeg = 1; jdeg <= 3; ++jdeg) {
+    left[jdeg] = u - knot(K + 1 - jdeg);
+    right[jdeg] = knot(K + jdeg) - u;
+    T saved = T(0);
+    for (int rr = 0; rr < jdeg; ++rr) {
+      const T den = right[rr + 1] + left[jdeg - rr];
+      const T tmp = den != T(0) ? Nb[rr] / den : T(0);
+      Nb[rr] = saved + right[rr + 1] * tmp;
+      saved = left[jdeg - rr] * tmp;
+    }
+    Nb[jdeg] = saved;
+  }
+  for (int r = 0; r < 4; ++r)
+    for (int d = 0; d < 3; ++d) v[3 * r + d] = Nb[r] * g[d];
+  return 3 * span;
 }
+
+// Adds J(t)^T g to the thread's FP64 parameter column:
+// row[p * kParamThreads] += sum_d J[d][p] g[d].
+__device__ void add_source_jacobian(const SceneDev& S, double t, const double g[3], double* row) {
+  double v[12];
+  const int p0 = jacobian_terms<double>(S, t, g, v);
+  const int nt = jacobian_count(S);
+  for (int i = 0; i < nt; ++i) row[(p0 + i) * kParamThreads] += v[i];
+}
+
+// FP32 sums of J(e)^T g over consecutive emission-time units, added to the
+// FP64 column when the block of parameters changes (another spline span),
+// every kJacRun units and at the end.
+constexpr int kJacRun = 64;
+struct JacAcc {
+  float v[12];
+  int p0 = -1, n = 0;
+  __device__ void flush(const SceneDev& S, double* row) {
+    if (p0 >= 0) {
+      const int nt = jacobian_count(S);
+      for (int i = 0; i < nt; ++i) row[(p0 + i) * kParamThreads] += double(v[i]);
+    }
+    p0 = -1;
+    n = 0;
+  }
+  __device__ void add(const SceneDev& S, float t, const float g[3], double* row) {
+    float w[12];
+    const int q0 = jacobian_terms<float>(S, t, g, w);
+    if (q0 != p0 || n == kJacRun) {
+      flush(S, row);
+      p0 = q0;
+#pragma unroll
+      for (int i = 0; i < 12; ++i) v[i] = 0.0f;
+    }
+    ++n;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) v[i] += w[i];
+  }
+};
 
 // Unit (mic, image, record knot) of the upsampled / emission-time tiers of a
-// scene: tier, microphone, image (sorted position in the tier), knot.
+// scene: tier, microphone, image (sorted position in the tier), knot; units
+// are numbered [tier][mic][knot][image].
 struct OptUnit {
   int t, mic, img, k;
 };
@@ -919,48 +990,36 @@ __device__ __forceinline__ OptUnit opt_unit(const SceneDev& S, int64_t local) {
   for (int q = 0; q < S.n_tiers; ++q)
     if (opt_tier(S, q) && S.opt_units_first[q] <= local) t = q;
   const int64_t r = local - S.opt_units_first[t];
-  const int nk = S.tier_intervals[t] + 1;
-  const int64_t row = r / nk;
+  const int cnt = S.tier_count[t];
+  const int64_t per_mic = (int64_t(S.tier_intervals[t]) + 1) * cnt;
   OptUnit u;
   u.t = t;
-  u.k = int(r - row * nk);
-  u.mic = int(row / S.tier_count[t]);
-  u.img = int(row - int64_t(u.mic) * S.tier_count[t]);
+  if (r < (int64_t(1) << 31) && per_mic < (int64_t(1) << 31)) {  // 32-bit divisions
+    const unsigned r32 = unsigned(r), pm = unsigned(per_mic);
+    u.mic = int(r32 / pm);
+    const unsigned rem = r32 - unsigned(u.mic) * pm;
+    u.k = int(rem / unsigned(cnt));
+    u.img = int(rem - unsigned(u.k) * unsigned(cnt));
+    return u;
+  }
+  u.mic = int(r / per_mic);
+  const int64_t rem = r - u.mic * per_mic;
+  u.k = int(rem / cnt);
+  u.img = int(rem - int64_t(u.k) * cnt);
   return u;
 }
 
-// Microphone position at time t (FP64): static, or carried by the array.
-__device__ __forceinline__ void mic_at(const SceneDev& S, int mic, double t, double m[3]) {
-  double ad[3] = {0.0, 0.0, 0.0};
-  if (S.arr_moving) array_displacement(S, t, ad);
-  for (int d = 0; d < 3; ++d) m[d] = S.mics[mic][d] + ad[d];
-}
-
-// Emission-time path of image `code` for the reception time t: the emission
-// time e = t - tau and the vector Delta = sigma o s(e) + 2 n L - m(t), with
-// c tau = |Delta| (tau in seconds, given).
-__device__ void emission_vector(const SceneDev& S, uint32_t code, const double m[3], double t, double tau,
-                                double sg[3], double D[3], double* e) {
-  int n[3], p[3];
-  unpack_image(code, n, p);
-  *e = t - tau;
-  double sp[3];
-  source_position(S, *e, sp);
-  for (int d = 0; d < 3; ++d) {
-    sg[d] = p[d] ? -1.0 : 1.0;
-    D[d] = sg[d] * sp[d] + 2.0 * n[d] * S.dims[d] - m[d];
-  }
-}
-
 // Partial dL/dparams of one chunk of a scene's units (flattened): every thread
-// sums J^T g over a contiguous unit range into its own shared column, then the
-// columns are summed in thread order. Units: the knots of every tier,
+// sums J^T g over its units (a contiguous range of knots; every stride-th
+// emission-time unit) into its own shared column, then the columns are summed
+// in thread order. Units: the knots of every tier,
 // J(t_j)^T dL/ds(t_j) (t_j = (j - knot_shift) times the knot spacing); with
 // emission-time delays instead the (mic, image, knot) units: with
 // e = t_j - tau the emission time, u = Delta / d and sigma o u = dd/ds,
 //   dd/dparams = (sigma o u)^T J(e) / (1 + (sigma o u) . s'(e) / c)
 // (implicit differentiation of c tau = |sigma o s(t_j - tau) + 2 n L - m(t_j)|),
-// times dL/dd at the knot.
+// times dL/dd at the knot; s(e) and s'(e) from the source path table (linear
+// between its points), the rest in FP32.
 __global__ void __launch_bounds__(kParamThreads) k_param_partial(const __grid_constant__ KernelArgs a) {
   const int s = blockIdx.x / kParamChunks, chunk = blockIdx.x % kParamChunks;
   const SceneDev& S = scene_of(a, s);
@@ -986,23 +1045,50 @@ __global__ void __launch_bounds__(kParamThreads) k_param_partial(const __grid_co
       add_source_jacobian(S, double((j - S.knot_shift[t]) * S.tier_coarse[t]) / S.fs, g, rows + threadIdx.x);
     }
   } else if (S.dparams) {
+    // emission-time units: thread q of the scene's kParamChunks x kParamThreads
+    // takes units q, q + stride, ... (adjacent lanes, adjacent units: coalesced
+    // loads; a thread's successive units lie a few knots apart, so a spline
+    // span changes rarely along them)
     const int64_t base = a.n_scenes > 1 ? a.tab.opt_prefix[s] : int64_t(0);
-    for (int64_t k = lo; k < hi; ++k) {
+    const float4* HI = a.p.dense_hi + S.dense_base;
+    const float4* LO = a.p.dense_lo + S.dense_base;
+    const double xs = double(kDenseOver) * S.fs;  // path table points per second
+    const float c = float(S.c);
+    JacAcc acc;
+    const int64_t stride = int64_t(kParamChunks) * kParamThreads;
+    for (int64_t k = int64_t(chunk) * kParamThreads + threadIdx.x; k < total; k += stride) {
       const OptUnit u = opt_unit(S, k);
-      const double gr = a.p.ograd[base + k];
-      if (gr == 0.0) continue;
-      const double tr = double(int64_t(u.k) * S.tier_step[u.t]) / S.fs;
-      double m[3], sg[3], D[3], e, v[3];
-      mic_at(S, u.mic, tr, m);
-      emission_vector(S, a.p.img_code[S.img_base + S.tier_first[u.t] + u.img], m, tr, a.p.otau[base + k] / S.fs, sg,
-                      D, &e);
-      const double d = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
-      source_velocity(S, e, v);
-      const double su[3] = {sg[0] * D[0] / d, sg[1] * D[1] / d, sg[2] * D[2] / d};
-      const double f = gr / (1.0 + (su[0] * v[0] + su[1] * v[1] + su[2] * v[2]) / S.c);
-      const double g[3] = {f * su[0], f * su[1], f * su[2]};
-      add_source_jacobian(S, e, g, rows + threadIdx.x);
+      const int cnt = S.tier_count[u.t];
+      const float gr = a.p.ograd[base + k].x + (u.k > 0 ? a.p.ograd[base + k - cnt].y : 0.0f);
+      if (gr == 0.0f) continue;
+      const int64_t kn = int64_t(u.k) * S.tier_step[u.t];
+      const double e = double(kn) / S.fs - a.p.otau[base + k] / S.fs;  // emission time
+      const double x = e * xs - double(S.dense_k0);
+      const int64_t i = min(max(int64_t(floor(x)), int64_t(0)), S.n_dense - 2);
+      const float f = float(x - double(i));
+      const float4 h0 = HI[i], h1 = HI[i + 1], l0 = LO[i], l1 = LO[i + 1];
+      const float ds[3] = {(h1.x - h0.x) + (l1.x - l0.x), (h1.y - h0.y) + (l1.y - l0.y),
+                           (h1.z - h0.z) + (l1.z - l0.z)};
+      const double sp[3] = {double(h0.x) + double(l0.x) + double(f * ds[0]),
+                            double(h0.y) + double(l0.y) + double(f * ds[1]),
+                            double(h0.z) + double(l0.z) + double(f * ds[2])};
+      const double* ap = a.p.arr_pos + 3 * (S.knot_base[u.t] + u.k);
+      int n[3], p[3];
+      unpack_image(a.p.img_code[S.img_base + S.tier_first[u.t] + u.img], n, p);
+      float su[3], D[3];
+      for (int d = 0; d < 3; ++d) {
+        su[d] = p[d] ? -1.0f : 1.0f;
+        const double m = S.mics[u.mic][d] + (S.arr_moving ? ap[d] : 0.0);
+        D[d] = float(double(su[d]) * sp[d] + 2.0 * n[d] * S.dims[d] - m);
+      }
+      const float rd = rsqrtf(fmaf(D[0], D[0], fmaf(D[1], D[1], D[2] * D[2])));
+      for (int d = 0; d < 3; ++d) su[d] *= D[d] * rd;  // sigma o u
+      const float vs = float(xs) * (su[0] * ds[0] + su[1] * ds[1] + su[2] * ds[2]);  // (sigma o u) . s'(e)
+      const float fac = gr / (1.0f + vs / c);
+      const float g[3] = {fac * su[0], fac * su[1], fac * su[2]};
+      acc.add(S, float(e), g, rows + threadIdx.x);
     }
+    acc.flush(S, rows + threadIdx.x);
   }
   __syncthreads();
   if (threadIdx.x < 48) {
@@ -1014,19 +1100,21 @@ __global__ void __launch_bounds__(kParamThreads) k_param_partial(const __grid_co
 
 // ------------------------------------------------- upsampled / emission-time tiers
 // Their delays are not linear in the knot positions, so their knot gradients
-// are formed per (mic, image, record knot) unit: k_opt_tau the FP64 delay at
-// every record knot, k_opt_grad dL/dd there (the samples of the two adjacent
-// intervals, from the degree-5 rows), then the chain rule: k_opt_bl_knots for
-// upsampled tiers (through the upsampler's weights to the knots, times the
-// unit vectors), k_param_partial for emission-time delays.
+// are formed per (mic, image, record knot) unit. The gradient kernel stores
+// the FP32 knot delays of its records (otau); k_opt_grad sums dL/dd_i(n) over
+// every knot interval with the two knots' linear weights (ograd); the chain
+// rule then runs through the upsampler's weights to the knots and the unit
+// vectors there (k_opt_bl_rows, k_opt_bl_knots), or, for emission-time delays,
+// through the implicit emission time to the trajectory parameters
+// (k_param_partial).
 
-// Delay tau (samples, FP64) at record knot k of unit u.
-//   upsampled tier: tau at virtual knot k = j0 U + p from the knots' delays,
-//   in the chord form of the synthesis (tau_j0 + Delta M_p + sum_i w_p[i] e_i,
-//   e_i the deviations from the chord through knots j0 and j0 + 1);
-//   emission-time delays: Newton's method on c tau = |Delta(t - tau)| with the
-//   path's velocity by central difference, from the reception-time distance.
-__global__ void k_opt_tau(const __grid_constant__ KernelArgs a) {
+// Unit (row, interval j) of the option tiers: per sample n = j N + r of the
+// interval, dL/dd_i(n) = -dy g (fs/c) (S de/dw + e / tau) with e and de/dw from
+// the degree-5 rows in global memory and the delay linear between the knot
+// delays; stored: A = sum (1 - r/N) dL/dd_i(n) (to knot j) and
+// B = sum (r/N) dL/dd_i(n) (to knot j + 1). The read position is formed
+// relative to D = floor(tau_j) in FP32. Unit j = J (no interval) stores zeros.
+__global__ void __launch_bounds__(256) k_opt_grad(const __grid_constant__ KernelArgs a) {
   const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (gid >= a.totals[9]) return;
   int s = 0;
@@ -1037,103 +1125,120 @@ __global__ void k_opt_tau(const __grid_constant__ KernelArgs a) {
   }
   const SceneDev& S = scene_of(a, s);
   const OptUnit u = opt_unit(S, local);
-  double tau;
-  if (S.delay_model == 1) {
-    const double tr = double(int64_t(u.k) * S.tier_step[u.t]) / S.fs;
-    const uint32_t code = a.p.img_code[S.img_base + S.tier_first[u.t] + u.img];
-    double m[3], sg[3], D[3], e;
-    mic_at(S, u.mic, tr, m);
-    emission_vector(S, code, m, tr, 0.0, sg, D, &e);
-    double ts = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]) / S.c;  // seconds
-    for (int it = 0; it < 40; ++it) {
-      emission_vector(S, code, m, tr, ts, sg, D, &e);
-      const double d = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
-      double v[3];
-      source_velocity(S, e, v);
-      const double slope = S.c + (sg[0] * D[0] * v[0] + sg[1] * D[1] * v[1] + sg[2] * D[2] * v[2]) / d;
-      const double step = (S.c * ts - d) / slope;
-      ts -= step;
-      if (fabs(step) <= 1e-15 * ts) break;
+  const int N = S.tier_step[u.t];
+  const int j = u.k;
+  const int64_t n0 = int64_t(j) * N;
+  float A = 0.0f, B = 0.0f;
+  if (j < S.tier_intervals[u.t] && n0 < S.n_out) {
+    const double t0 = a.p.otau[gid], t1 = a.p.otau[gid + S.tier_count[u.t]];  // knots j and j + 1
+    const double D = floor(t0);
+    const float phi0 = float(t0 - D), dphi = float(t1 - t0);
+    const float Df = float(D);
+    const int64_t base = n0 - int64_t(D) - S.z_m0;  // z column of read position n - D at r = 0
+    const float G = a.p.img_gain[S.img_base + S.tier_first[u.t] + u.img];
+    const float* dy = S.dy + int64_t(u.mic) * S.n_out + n0;
+    const float4* zq = a.p.zq + S.z_base;
+    const float2* zg = a.p.zg + S.z_base;
+    const float invN = 1.0f / float(N);
+    const int nr = int(min(int64_t(N), S.n_out - n0));
+    for (int r = 0; r < nr; ++r) {
+      const float sr = float(r) * invN;
+      const float phi = fmaf(dphi, sr, phi0);
+      const float pr = float(r) - phi;  // read position n - tau relative to n0 - D
+      const float fl = floorf(pr);
+      const float v = float(kFarrowSegs) * (pr - fl);
+      const int seg = min(int(v), kFarrowSegs - 1);
+      const float w = v - float(seg) - 0.5f;
+      const int64_t col = base + int64_t(fl);
+      if (col < 0 || col >= S.z_len) continue;  // x is zero there
+      float pe, pd;
+      horner_d5(zq[int64_t(seg) * S.z_len + col], zg[int64_t(seg) * S.z_len + col], w, &pe, &pd);
+      const float tau = Df + phi;
+      const float rt = 1.0f / tau;
+      const float ad = -dy[r] * S.fsc * G * rt * fmaf(float(kFarrowSegs), pd, pe * rt);
+      A = fmaf(1.0f - sr, ad, A);
+      B = fmaf(sr, ad, B);
     }
-    tau = ts * S.fs;
-  } else {
-    const int U = S.tier_up[u.t], Q = S.up_q;
-    const int j0 = u.k / U, pp = u.k - j0 * U;
-    // the tier's knot table starts Q knots before t = 0
-    const float2* row = a.p.bl_tau + S.bl_tau_base[u.t] +
-                        (int64_t(u.mic) * S.tier_count[u.t] + u.img) * S.bl_knots[u.t] + Q;
-    const float* W = a.p.upw + S.upw_base[u.t] + pp * (2 * Q + 1);
-    auto tv = [&](int j) {
-      const float2 v = row[j];
-      return double(v.x) + double(v.y);
-    };
-    const double t0 = tv(j0), dl = tv(j0 + 1) - t0;
-    tau = t0 + dl * double(W[2 * Q]);
-    for (int i = 0; i < 2 * Q; ++i)
-      if (i != Q - 1 && i != Q) tau += double(W[i]) * (tv(j0 - Q + 1 + i) - t0 - double(i - Q + 1) * dl);
   }
-  a.p.otau[gid] = tau;
+  a.p.ograd[gid] = make_float2(A, B);
 }
 
-// dL/dd at record knot k of unit u: sum over the samples n of intervals k - 1
-// and k of dL/dd_i(n) = -dy g (fs/c) (S de/dw + e / tau) times the linear
-// weight of knot k at n (the delay interpolated in FP64 from the FP64 knot
-// delays; e and de/dw from the degree-5 rows in global memory). One warp per
-// unit, lanes over samples, FP64 sum in a fixed order.
-__global__ void __launch_bounds__(256) k_opt_grad(const __grid_constant__ KernelArgs a) {
-  const int64_t gid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (gid >= a.totals[9]) return;
+// dL/dd at every knot of an upsampled tier's table, per (mic, image) row: the
+// record knots' dL/dd (A_k + B_{k-1}) through the chord form's derivatives,
+// w_p[i] off the chord's two knots, M_p - sum' w_p[i] c_i for knot j0 + 1 and
+// 1 - M_p - sum' w_p[i] (1 - c_i) for knot j0 (c_i = i - Q + 1; sum' over i
+// other than the chord's knots). One thread per row walks its record knots in
+// order with 2Q running knot sums; stored knot-major (cgrad[knot][row]).
+__global__ void k_opt_bl_rows(const __grid_constant__ KernelArgs a) {
+  const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gid >= a.totals[6]) return;
   int s = 0;
   int64_t local = gid;
   if (a.n_scenes > 1) {
-    s = find_scene(a.tab.opt_prefix, a.n_scenes, gid);
-    local = gid - a.tab.opt_prefix[s];
+    s = find_scene(a.tab.bl_prefix, a.n_scenes, gid);
+    local = gid - a.tab.bl_prefix[s];
   }
   const SceneDev& S = scene_of(a, s);
-  const OptUnit u = opt_unit(S, local);
-  const int N = S.tier_step[u.t];
-  const double* kt = a.p.otau + (gid - u.k);  // the row's knot delays
-  const double G = double(a.p.img_gain[S.img_base + S.tier_first[u.t] + u.img]);
-  const float* dy = S.dy + int64_t(u.mic) * S.n_out;
-  const int64_t lo = max(int64_t(u.k - 1) * N, int64_t(0));
-  const int64_t hi = min(int64_t(u.k + 1) * N, S.n_out);
-  const float4* zq = a.p.zq + S.z_base;
-  const float2* zg = a.p.zg + S.z_base;
-  double acc = 0.0;
-  for (int64_t n = lo + lane; n < hi; n += 32) {
-    const int j = int(n / N);
-    const double r = double(n - int64_t(j) * N) / N;
-    const double tau = kt[j] + (kt[j + 1] - kt[j]) * r;
-    const double wk = (j == u.k) ? 1.0 - r : r;
-    const double pos = double(n) - tau;
-    const double m0 = floor(pos);
-    const double v = double(kFarrowSegs) * (pos - m0);
-    const int seg = min(int(v), kFarrowSegs - 1);
-    const float w = float(v - seg - 0.5);
-    const int64_t col = int64_t(m0) - S.z_m0;
-    if (col < 0 || col >= S.z_len) continue;  // outside the rows: x is zero there
-    float pe, pd;
-    horner_d5(zq[int64_t(seg) * S.z_len + col], zg[int64_t(seg) * S.z_len + col], w, &pe, &pd);
-    const double g = G / tau;  // gain beta / (4 pi d)
-    const double ad = -double(dy[n]) * double(S.fsc) * g * (double(kFarrowSegs) * pd + double(pe) / tau);
-    acc += wk * ad;
-  }
+  int t = -1;
+  for (int q = 0; q < S.n_tiers; ++q)
+    if (S.tier_up[q] > 1 && S.bl_units_first[q] <= local) t = q;
+  if (t < 0) return;
+  const int64_t row = local - S.bl_units_first[t];
+  const int64_t rows = int64_t(S.n_mics) * S.tier_count[t];
+  const int U = S.tier_up[t], Q = S.up_q, nkt = S.bl_knots[t];
+  const int J1 = S.tier_intervals[t] + 1;
+  const int cnt = S.tier_count[t];
+  const int mic = int(row / cnt);
+  // record knot k of this (mic, image) at gr[k * cnt]
+  const float2* gr = a.p.ograd + opt_row0(a, S, s, t) + int64_t(mic) * J1 * cnt + (row - int64_t(mic) * cnt);
+  float* cg = a.p.cgrad + S.bl_tau_base[t] + row;  // knot jt at cg[jt * rows]
+  constexpr int kW = 2 * kMaxUpHalfwidth;
+  float acc[kW];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) a.p.ograd[gid] = acc;
+  for (int i = 0; i < kW; ++i) acc[i] = 0.0f;
+  cg[0] = 0.0f;  // knot -Q: no record knot reaches it
+  int j0 = 0;    // acc[i] holds knot j0 - Q + 1 + i (table index j0 + 1 + i)
+  float prevB = 0.0f;
+  for (int k = 0; k < J1; ++k) {
+    const int jk = k / U;
+    for (; j0 < jk; ++j0) {  // knot j0 - Q + 1 is complete
+      cg[int64_t(j0 + 1) * rows] = acc[0];
+#pragma unroll
+      for (int i = 0; i + 1 < kW; ++i) acc[i] = acc[i + 1];
+      acc[kW - 1] = 0.0f;
+    }
+    const float2 ab = gr[int64_t(k) * cnt];
+    const float g = ab.x + prevB;
+    prevB = ab.y;
+    const float* W = a.p.upw + S.upw_base[t] + (k - j0 * U) * (2 * Q + 1);
+    float s0 = 0.0f, s1 = 0.0f;
+    for (int i = 0; i < 2 * Q; ++i)
+      if (i != Q - 1 && i != Q) {
+        const float wi = __ldg(W + i);
+        s0 += wi;
+        s1 = fmaf(wi, float(i - Q + 1), s1);
+      }
+    const float M = __ldg(W + 2 * Q);
+#pragma unroll
+    for (int i = 0; i < kW; ++i) {
+      if (i < 2 * Q) {
+        const float wi = (i == Q) ? M - s1 : (i == Q - 1) ? 1.0f - M - s0 + s1 : __ldg(W + i);
+        acc[i] = fmaf(wi, g, acc[i]);
+      }
+    }
+  }
+  // the last 2Q knots reached, then zeros to the end of the table
+#pragma unroll
+  for (int i = 0; i < kW; ++i)
+    if (i < 2 * Q && j0 + 1 + i < nkt) cg[int64_t(j0 + 1 + i) * rows] = acc[i];
+  for (int jt = j0 + 1 + 2 * Q; jt < nkt; ++jt) cg[int64_t(jt) * rows] = 0.0f;
 }
 
 // dL/ds(t_j) at knot j of an upsampled tier (one CTA per knot of the tier's
-// table, knots -Q .. J_c + Q): over every (mic, image), dL/dd at the knot,
-// sum_k w_eff(k, j) dL/dd(record knot k), times sigma o Delta / d at the knot.
-// The effective weights are the chord form's derivatives: w_p[i] off the chord's
-// two knots, M_p - sum' w_p[i] c_i for knot j0 + 1 and
-// 1 - M_p - sum' w_p[i] (1 - c_i) for knot j0 (c_i = i - Q + 1; sum' over i
-// other than the chord's knots). Fixed-order sums.
+// table): sum over (mic, image) of dL/dd there times sigma o Delta / d, in a
+// fixed order.
 constexpr int kBlThreads = 256;
 __global__ void __launch_bounds__(kBlThreads) k_opt_bl_knots(const __grid_constant__ KernelArgs a) {
-  __shared__ float weff[kMaxUpsample * 2 * kMaxUpHalfwidth];
   __shared__ double part[3][kBlThreads];
   const int64_t gid = blockIdx.x;
   if (gid >= a.totals[1]) return;
@@ -1148,51 +1253,28 @@ __global__ void __launch_bounds__(kBlThreads) k_opt_bl_knots(const __grid_consta
   while (t + 1 < S.n_tiers && local >= S.knot_units_first[t + 1]) ++t;
   if (S.tier_up[t] <= 1 || S.delay_model == 1) return;
   const int jt = int(local - S.knot_units_first[t]);
-  const int U = S.tier_up[t], Q = S.up_q;
-  const int j = jt - Q;  // the knot's index (time j N_c / fs)
-  for (int pp = threadIdx.x; pp < U; pp += kBlThreads) {
-    const float* W = a.p.upw + S.upw_base[t] + pp * (2 * Q + 1);
-    double s0 = 0.0, s1 = 0.0;
-    for (int i = 0; i < 2 * Q; ++i)
-      if (i != Q - 1 && i != Q) {
-        weff[pp * 2 * Q + i] = W[i];
-        s0 += double(W[i]);
-        s1 += double(W[i]) * double(i - Q + 1);
-      }
-    const double M = double(W[2 * Q]);
-    weff[pp * 2 * Q + Q] = float(M - s1);
-    weff[pp * 2 * Q + Q - 1] = float(1.0 - M - s0 + s1);
-  }
-  __syncthreads();
-  const int nk = S.tier_intervals[t] + 1;
-  const int k_lo = max((j - Q) * U, 0), k_hi = min((j + Q) * U - 1, nk - 1);
   const int64_t rows = int64_t(S.n_mics) * S.tier_count[t];
-  const int64_t base = (a.n_scenes > 1 ? a.tab.opt_prefix[s] : int64_t(0)) + S.opt_units_first[t];
+  const float* cg = a.p.cgrad + S.bl_tau_base[t] + int64_t(jt) * rows;
   const double* sp = a.p.knot_pos + 3 * (S.knot_base[t] + jt);
   const double* ap = a.p.arr_pos + 3 * (S.knot_base[t] + jt);
   double gx = 0.0, gy = 0.0, gz = 0.0;
   for (int64_t r = threadIdx.x; r < rows; r += kBlThreads) {
-    const double* gr = a.p.ograd + base + r * nk;
-    double cg = 0.0;
-    for (int k = k_lo; k <= k_hi; ++k) {
-      const int j0 = k / U;
-      cg += double(weff[(k - j0 * U) * 2 * Q + (j - j0 + Q - 1)]) * gr[k];
-    }
+    const float c = cg[r];
+    if (c == 0.0f) continue;
     const int mic = int(r / S.tier_count[t]);
     const int img = int(r - int64_t(mic) * S.tier_count[t]);
     int n[3], p[3];
     unpack_image(a.p.img_code[S.img_base + S.tier_first[t] + img], n, p);
-    double D[3], sg[3], dd = 0.0;
+    float D[3], sg[3];
     for (int d = 0; d < 3; ++d) {
-      sg[d] = p[d] ? -1.0 : 1.0;
+      sg[d] = p[d] ? -1.0f : 1.0f;
       const double m = S.mics[mic][d] + (S.arr_moving ? ap[d] : 0.0);
-      D[d] = sg[d] * sp[d] + 2.0 * n[d] * S.dims[d] - m;
-      dd += D[d] * D[d];
+      D[d] = float(double(sg[d]) * sp[d] + 2.0 * n[d] * S.dims[d] - m);
     }
-    const double f = cg / sqrt(dd);
-    gx += f * sg[0] * D[0];
-    gy += f * sg[1] * D[1];
-    gz += f * sg[2] * D[2];
+    const float f = c * rsqrtf(fmaf(D[0], D[0], fmaf(D[1], D[1], D[2] * D[2])));
+    gx += double(f * sg[0] * D[0]);
+    gy += double(f * sg[1] * D[1]);
+    gz += double(f * sg[2] * D[2]);
   }
   part[0][threadIdx.x] = gx;
   part[1][threadIdx.x] = gy;
@@ -1267,7 +1349,6 @@ cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
   // per device and kernel: shared-memory limit and persistent grid
   static PerDevice g_grad, g_dx16, g_dx32, g_dx64;
   if (a.totals[0] > 0) k_beta_table<<<unsigned((a.totals[0] + 255) / 256), 256, 0, st>>>(a);
-  if (a.totals[9] > 0) k_opt_tau<<<unsigned((a.totals[9] + 127) / 128), 128, 0, st>>>(a);
   e = persistent_launch(k_adj_grad, kGradSmem, a.totals[4], a, st, &g_grad);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.p.dxb, 0, sizeof(float) * size_t(a.p.dxb_floats), st);
@@ -1278,10 +1359,13 @@ cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int T = 256;
   if (a.totals[2] > 0) k_dx_final<<<unsigned((a.totals[2] + T - 1) / T), T, 0, st>>>(a);
-  if (a.totals[9] > 0) k_opt_grad<<<unsigned((a.totals[9] * 32 + 255) / 256), 256, 0, st>>>(a);
+  if (a.totals[9] > 0) k_opt_grad<<<unsigned((a.totals[9] + 255) / 256), 256, 0, st>>>(a);
   if (a.totals[1] > 0)
     k_knot_final<<<unsigned((a.totals[1] + kKnotsPerCta - 1) / kKnotsPerCta), kKnotsPerCta * kKnotLanes, 0, st>>>(a);
-  if (a.totals[6] > 0 && a.totals[1] > 0) k_opt_bl_knots<<<unsigned(a.totals[1]), kBlThreads, 0, st>>>(a);
+  if (a.totals[6] > 0 && a.totals[9] > 0) {
+    k_opt_bl_rows<<<unsigned((a.totals[6] + 127) / 128), 128, 0, st>>>(a);
+    k_opt_bl_knots<<<unsigned(a.totals[1]), kBlThreads, 0, st>>>(a);
+  }
   {
     constexpr size_t smem = 48 * kParamThreads * sizeof(double);
     static PerDevice attr;  // the shared-memory limit, once per device

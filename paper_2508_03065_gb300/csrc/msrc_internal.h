@@ -206,8 +206,12 @@ struct DevicePtrs {
   double* ppart;                 // trajectory-parameter partials (48 doubles per (scene, knot chunk))
   float4* bwt;                   // per image: dbeta_i/dbeta_w / (4 pi) for walls 0..3 | walls 4..5, gain, 0
   float2* trange;                // reverse mode: delay range (tmin, tmax) of every (mic, block, tile) item
-  double* otau;                  // reverse mode, upsampled / emission-time tiers: FP64 delay (samples)
-  double* ograd;                 //   and dL/dd at every (mic, image, record knot) unit
+  // reverse mode, upsampled / emission-time tiers, per (mic, image, record knot)
+  // unit: the knot delay (samples) of the gradient kernel's records, and the
+  // interval's dL/dd sums toward its two knots (A to knot k, B to knot k + 1)
+  double* otau;
+  float2* ograd;
+  float* cgrad;                  // upsampled tiers: dL/dd at the knots, [knot][mic x image] from bl_tau_base[t]
   // band-limited knot upsampling: per (scene, tier) a table of tier_up rows
   // of 2 up_q + 1 floats, row p = the normalised kernel weights of knots
   // j0 - up_q + 1 .. j0 + up_q at the virtual knot p / tier_up past knot j0,
@@ -221,7 +225,7 @@ struct DevicePtrs {
   float4* dense_hi;
   float4* dense_lo;
 };
-constexpr int kParamPartialsPerScene = 32 * 48;
+constexpr int kParamPartialsPerScene = 128 * 48;
 
 constexpr int kUnitKinds = 10;
 

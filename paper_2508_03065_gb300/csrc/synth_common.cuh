@@ -468,11 +468,14 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
 // floor(jf / U) is the image's anchor. Scratch `scr` (`cap` floats): D (cnt),
 // chord rows (cnt x nj x (2Q + 2)), phi (cnt x nk). If the item does not fit,
 // the error word gets kErrUpsampleScratch, no record is written and the result
-// is false (the caller then treats the block as empty).
+// is false (the caller then treats the block as empty). With dfl_out / phi_out
+// (nullable) the anchors D (cnt floats) are also stored at dfl_out and
+// *phi_out points at the relative delays phi[ib * nk + jj] in the scratch: the
+// delay at virtual knot jf + jj is D + phi.
 template <int kThreads, int kLayout = kRecPlain>
 __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                                 int4* img_s, float* scr, int64_t cap, float* tmin_out, float* tmax_out,
-                                float gscale = 1.0f) {
+                                float gscale = 1.0f, float* dfl_out = nullptr, const float** phi_out = nullptr) {
   const int U = S.tier_up[g.t];
   const int Q = S.up_q;
   const int nk = g.nk;
@@ -511,6 +514,7 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
     const float Dfl = df_floor(DF{an.x, an.y});  // the anchor, knot floor(jf / U)
     if (jr == 0) {
       dfl_s[ib] = Dfl;
+      if (dfl_out) dfl_out[ib] = Dfl;
       put_image_record<kLayout>(img_s, ib, g.cnt, g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib) * gscale);
     }
     const float2* tv = row + (j0_first + jr - Q + 1);  // knots j0 - Q + 1 .. j0 + Q
@@ -560,6 +564,7 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
   }
   __syncthreads();
   records_from_phi<kThreads, kLayout>(g, phi_s, rec_s);
+  if (phi_out) *phi_out = phi_s;
   *tmin_out = tmin;
   *tmax_out = tmax;
   return true;
@@ -586,6 +591,8 @@ __device__ bool item_records_bl(const KernelArgs& a, const SceneDev& S, const It
 //   differences of nearby positions are exact); the second step reads the
 //   table again only when its emission point lies in another segment.
 // Scratch: um_s (nk, moving array), an6 (6 x cnt float4), phi_s (cnt x nk).
+// The delay at knot jf + jj is D + phi_s[ib * nk + jj], D the image's anchor
+// (stored at dfl_out when it is not null).
 struct RetAnchor {
   float4 A, H, Lw, dA, Sg, E;
 };
@@ -634,7 +641,7 @@ __device__ __forceinline__ float ret_increment(const RetAnchor& r, const float4 
 template <int kThreads, int kLayout = kRecPlain>
 __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                                  int4* img_s, float4* um_s, float4* an6, float* phi_s, float* tmin_out,
-                                 float* tmax_out, float gscale = 1.0f) {
+                                 float* tmax_out, float gscale = 1.0f, float* dfl_out = nullptr) {
   const bool moving = S.arr_moving != 0;
   const int64_t kj = S.knot_base[g.t] + g.jf;
   const float4* ahl = a.p.arr_hl + 2 * kj;
@@ -771,6 +778,7 @@ __device__ void item_records_ret(const KernelArgs& a, const SceneDev& S, const I
     an6[6 * ib + 3] = make_float4(dsx, dsy, dsz, gsl / (1.0f + gsl));
     an6[6 * ib + 4] = make_float4(sg[0], sg[1], sg[2], __int_as_float(int(k)));
     an6[6 * ib + 5] = make_float4(eps, Dfl, r2, 0.0f);
+    if (dfl_out) dfl_out[ib] = Dfl;
     put_image_record<kLayout>(img_s, ib, g.cnt, g.jf * g.N - int(Dfl), Dfl, __ldg(gain + ib) * gscale);
   }
   __syncthreads();
