@@ -1019,7 +1019,8 @@ __device__ __forceinline__ OptUnit opt_unit(const SceneDev& S, int64_t local) {
 //   dd/dparams = (sigma o u)^T J(e) / (1 + (sigma o u) . s'(e) / c)
 // (implicit differentiation of c tau = |sigma o s(t_j - tau) + 2 n L - m(t_j)|),
 // times dL/dd at the knot; s(e) and s'(e) from the source path table (linear
-// between its points), the rest in FP32.
+// between its points), in FP32 after one FP64 difference for the emission time
+// (the unit vector to ~1e-6, the table fraction to ~1e-2 of a table step).
 __global__ void __launch_bounds__(kParamThreads) k_param_partial(const __grid_constant__ KernelArgs a) {
   const int s = blockIdx.x / kParamChunks, chunk = blockIdx.x % kParamChunks;
   const SceneDev& S = scene_of(a, s);
@@ -1052,8 +1053,11 @@ __global__ void __launch_bounds__(kParamThreads) k_param_partial(const __grid_co
     const int64_t base = a.n_scenes > 1 ? a.tab.opt_prefix[s] : int64_t(0);
     const float4* HI = a.p.dense_hi + S.dense_base;
     const float4* LO = a.p.dense_lo + S.dense_base;
-    const double xs = double(kDenseOver) * S.fs;  // path table points per second
-    const float c = float(S.c);
+    const float xs = float(kDenseOver) * float(S.fs);  // path table points per second
+    const float rc = float(1.0 / S.c);
+    const float rfs = float(1.0 / S.fs);
+    const float k0 = float(S.dense_k0);
+    const int64_t kmax = S.n_dense - 2;
     JacAcc acc;
     const int64_t stride = int64_t(kParamChunks) * kParamThreads;
     for (int64_t k = int64_t(chunk) * kParamThreads + threadIdx.x; k < total; k += stride) {
@@ -1061,32 +1065,31 @@ __global__ void __launch_bounds__(kParamThreads) k_param_partial(const __grid_co
       const int cnt = S.tier_count[u.t];
       const float gr = a.p.ograd[base + k].x + (u.k > 0 ? a.p.ograd[base + k - cnt].y : 0.0f);
       if (gr == 0.0f) continue;
-      const int64_t kn = int64_t(u.k) * S.tier_step[u.t];
-      const double e = double(kn) / S.fs - a.p.otau[base + k] / S.fs;  // emission time
-      const double x = e * xs - double(S.dense_k0);
-      const int64_t i = min(max(int64_t(floor(x)), int64_t(0)), S.n_dense - 2);
-      const float f = float(x - double(i));
+      // emission time e = (n_j - tau) / fs (samples: n_j - tau, one FP64 difference)
+      const float es = float(double(int64_t(u.k) * S.tier_step[u.t]) - a.p.otau[base + k]);
+      const float x = fmaf(float(kDenseOver), es, -k0);  // path table coordinate
+      const float xi = floorf(x);
+      const int64_t i = min(max(int64_t(xi), int64_t(0)), kmax);
+      const float f = x - float(i);
       const float4 h0 = HI[i], h1 = HI[i + 1], l0 = LO[i], l1 = LO[i + 1];
       const float ds[3] = {(h1.x - h0.x) + (l1.x - l0.x), (h1.y - h0.y) + (l1.y - l0.y),
                            (h1.z - h0.z) + (l1.z - l0.z)};
-      const double sp[3] = {double(h0.x) + double(l0.x) + double(f * ds[0]),
-                            double(h0.y) + double(l0.y) + double(f * ds[1]),
-                            double(h0.z) + double(l0.z) + double(f * ds[2])};
+      const float sp[3] = {fmaf(f, ds[0], h0.x + l0.x), fmaf(f, ds[1], h0.y + l0.y), fmaf(f, ds[2], h0.z + l0.z)};
       const double* ap = a.p.arr_pos + 3 * (S.knot_base[u.t] + u.k);
       int n[3], p[3];
       unpack_image(a.p.img_code[S.img_base + S.tier_first[u.t] + u.img], n, p);
       float su[3], D[3];
       for (int d = 0; d < 3; ++d) {
         su[d] = p[d] ? -1.0f : 1.0f;
-        const double m = S.mics[u.mic][d] + (S.arr_moving ? ap[d] : 0.0);
-        D[d] = float(double(su[d]) * sp[d] + 2.0 * n[d] * S.dims[d] - m);
+        const float m = float(S.mics[u.mic][d]) + (S.arr_moving ? float(ap[d]) : 0.0f);
+        D[d] = fmaf(su[d], sp[d], fmaf(float(2 * n[d]), float(S.dims[d]), -m));
       }
       const float rd = rsqrtf(fmaf(D[0], D[0], fmaf(D[1], D[1], D[2] * D[2])));
       for (int d = 0; d < 3; ++d) su[d] *= D[d] * rd;  // sigma o u
-      const float vs = float(xs) * (su[0] * ds[0] + su[1] * ds[1] + su[2] * ds[2]);  // (sigma o u) . s'(e)
-      const float fac = gr / (1.0f + vs / c);
+      const float vs = xs * (su[0] * ds[0] + su[1] * ds[1] + su[2] * ds[2]);  // (sigma o u) . s'(e)
+      const float fac = gr / fmaf(vs, rc, 1.0f);
       const float g[3] = {fac * su[0], fac * su[1], fac * su[2]};
-      acc.add(S, float(e), g, rows + threadIdx.x);
+      acc.add(S, es * rfs, g, rows + threadIdx.x);
     }
     acc.flush(S, rows + threadIdx.x);
   }
