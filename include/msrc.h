@@ -95,17 +95,19 @@ typedef struct {
                                 over 2 upsample_halfwidth knots, weights normalised to sum 1),
                                 then linear between virtual knots. Knots before t = 0 and after
                                 the end follow the trajectory's extension (line and circle
-                                continue, the spline clamps). Forward synthesis only. */
+                                continue, the spline clamps). Reverse mode differentiates
+                                through the interpolation (the weights' exact derivatives). */
   int32_t upsample_halfwidth;/* Q, half-width of that kernel in knots: 0 (= 4) or 1..8 */
   int32_t delay_model;       /* 0: an image's distance at a knot is taken at the reception time,
                                 d = |r_i(t) - m(t)| (Sec. II-A, Eq. 2 evaluated at the output time);
                                 1: emission-time (retarded) path length d = c tau with
                                 c tau = |r_i(t - tau) - m(t)|, the sound reaching the microphone
                                 at t having left the moving image at t - tau. Delay and gain
-                                follow from d in both models. Model 1 is forward only, needs
-                                linear knot interpolation (tier_upsample <= 1) and the path valid
+                                follow from d in both models. Model 1 needs linear knot
+                                interpolation (tier_upsample <= 1) and the path valid
                                 over [-(largest delay), end] (line and circle continue before
-                                t = 0, the spline clamps). */
+                                t = 0, the spline clamps); its reverse mode differentiates
+                                through the emission time (implicit derivative of the equation). */
 } msrc_room_desc;
 
 /* Source trajectory s(t) (Sec. II-C: a band-limited trajectory p(n)). */
@@ -259,8 +261,11 @@ msrc_status msrc_host_io_bytes(const msrc_room_t* rooms, int32_t n_rooms,
  *   dparams_dev[r] (48 doubles, device, nullable): dL/d traj.params (spline
  *                 control points; line p0 and speed; circle centre, radius and speed)
  *   dbeta_dev[r]  (6 doubles, device, nullable): dL/d beta per wall
- * Delays are recomputed from the trajectory, not stored. Reductions use a fixed
- * order, so results are bitwise reproducible. The rooms, signals and lengths must
+ * Delays are recomputed from the trajectory, not stored. Every tier kind is
+ * differentiated: linear knots, band-limited knots (through the upsampler's
+ * weights) and emission-time delays (through the implicit emission time,
+ * dd/dtheta = (sigma o u)^T J(e) / (1 + (sigma o u) . s'(e) / c)). Reductions
+ * use a fixed order, so results are bitwise reproducible. The rooms, signals and lengths must
  * be those of the forward call whose output dy refers to. The source speed must
  * stay below c/2 on the output range (1 ms grid), else MSRC_ERR_UNSUPPORTED:
  * the dx scatter relies on consecutive samples of one image reading different
