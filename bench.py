@@ -444,12 +444,45 @@ def run_batched(args, torch, api, W):
         e1.record(stream)
         stream.synchronize()
     t_single = e0.elapsed_time(e1) / reps
+    # the same comparison per quarter of the scenes by size (image-samples):
+    # where one scene fills the GPU batching has little to remove; the small
+    # scenes show the launch and tail overhead it does remove
+    sizes = [r.image_count()[0] * sp.n_in * r.n_mics for r, sp in zip(rooms, specs)]
+    order = sorted(range(len(specs)), key=lambda i: sizes[i])
+    by_size = []
+    q = max(1, len(order) // 4)
+    for k in range(0, len(order), q):
+        idx = order[k:k + q]
+        sub_r, sub_x, sub_y = [rooms[i] for i in idx], [xs[i] for i in idx], [ys[i] for i in idx]
+        b = api.Batch(sub_r, sub_x, stream=stream, tile_config=cfg)
+        w = b.work()
+        for _ in range(2):
+            b.run(True)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            b.run(True)
+        e1.record(stream)
+        stream.synchronize()
+        tb = e0.elapsed_time(e1) / reps
+        del b
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                for r, x, y in zip(sub_r, sub_x, sub_y):
+                    api.synthesize([r], [x], out=[y], workspace=ws, stream=stream, tile_config=cfg)
+            e1.record(stream)
+            stream.synchronize()
+        ts = e0.elapsed_time(e1) / reps
+        by_size.append({"scenes": len(idx), "image_samples_per_scene": [int(sizes[idx[0]]), int(sizes[idx[-1]])],
+                        "batched_ms": tb, "single_loop_ms": ts, "speedup": ts / tb})
     return {"scenes": len(specs), "image_samples": work, "tile_config": cfg, "batched_ms": t_batched,
             "single_loop_ms": t_single,
             "batched_value": work / (t_batched * 1e-3), "single_value": work / (t_single * 1e-3),
-            "speedup": t_single / t_batched, "unit": UNIT,
+            "speedup": t_single / t_batched, "by_size": by_size, "unit": UNIT,
             "how": "one persistent synthesis launch over all scenes, CUDA-graph replay, vs one msrc_synthesize "
-                   "call per scene on the same stream (same kernels and tile configuration)"}
+                   "call per scene on the same stream (same kernels and tile configuration); by_size: the "
+                   "same per quarter of the scenes sorted by image-samples"}
 
 
 def _fwd_bwd_ms(torch, api, rooms, xs, tg, ws, reps=3):

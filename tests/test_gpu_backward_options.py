@@ -104,11 +104,12 @@ def test_dot_product_identity(spec):
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
 
 
-def _cs_case(spec, ids):
+def _cs_case(spec, ids, n_out=None):
     sc = oracle_scene(spec)
     x = spec.x.astype(np.float64)
-    target = np.random.default_rng(3).standard_normal(spec.n_in) * 0.01
-    y_ref = oracle.synthesize(sc, x)
+    n_out = spec.n_in if n_out is None else n_out
+    target = np.random.default_rng(3).standard_normal(n_out) * 0.01
+    y_ref = oracle.synthesize(sc, x, n_out)
     _, dp, db = _bwd(spec, y_ref - target, want_dx=False)
     g_cs = oracle.loss_grad_cs(sc, x, target, ids + [48, 49, 50, 51, 52, 53])
     got = np.concatenate([dp[ids], db])
@@ -139,6 +140,16 @@ def test_upsampled_param_and_beta_gradients_match_complex_step(kw, Q, ids):
 ])
 def test_emission_time_param_and_beta_gradients_match_complex_step(kw, ids):
     _cs_case(_ret(kw), ids)
+
+
+@pytest.mark.parametrize("which", ["upsampled", "emission-time"])
+def test_gradients_with_a_shorter_output(which):
+    if which == "upsampled":
+        spec = _bl(dict(seed=44, K=2, seconds=0.04, traj_kind=W.SPLINE, tiers=[(1, 16000.0), (W.RHO_INF, 500.0, 8)]), 4)
+    else:
+        spec = _ret(dict(seed=45, K=2, seconds=0.04, traj_kind=W.CIRCLE))
+    ids = [0, 1, 4] if which == "upsampled" else [0, 1, 3, 4]
+    _cs_case(spec, ids, n_out=spec.n_in // 2 + 3)
 
 
 def test_emission_time_moving_array_gradients():
@@ -208,3 +219,26 @@ def test_batch_mixing_delay_kinds_equals_single_and_reproducible():
         single = api.synthesize_backward([rooms[i]], [xs[i]], [dys[i]])[0]
         for a, b, c in zip(batched[i], single, again[i]):
             assert torch.equal(a, b) and torch.equal(a, c), specs[i].name
+
+
+@pytest.mark.parametrize("which", ["upsampled", "emission-time"])
+@pytest.mark.parametrize("n_out_kind", ["shorter", "longer", "direct-path-only"])
+def test_output_lengths_and_free_field(which, n_out_kind):
+    # outputs shorter and longer than the input (the knots past the input's end,
+    # a last tile that is partly empty) and a scene of the direct path alone
+    # (order 0), against the oracle's transpose
+    kw = dict(BL[0][0]) if which == "upsampled" else dict(RET[0])
+    if n_out_kind == "direct-path-only":
+        kw["K"] = 0
+    spec = _bl(kw, BL[0][1]) if which == "upsampled" else _ret(kw)
+    n_out = {"shorter": spec.n_in // 2 + 1, "longer": spec.n_in + 700, "direct-path-only": spec.n_in}[n_out_kind]
+    room = api.Room.from_spec(spec)
+    x = torch.from_numpy(spec.x).cuda()
+    dy = np.random.default_rng(77).standard_normal((1, n_out))
+    ws = api.Workspace()
+    dx = api.synthesize_backward([room], [x], [torch.from_numpy(dy.astype(np.float32)).cuda()], want_params=False,
+                                 want_beta=False, workspace=ws)[0][0]
+    torch.cuda.synchronize()
+    assert api.workspace_errors(ws) == 0
+    ref = oracle.adjoint_x(oracle_scene(spec), dy[0], spec.n_in)
+    assert rel_l2(dx.cpu().numpy().astype(np.float64), ref) < 1e-5
