@@ -14,7 +14,10 @@ point).
   with Richardson extrapolation of the FP64 oracle on a sampled-output loss
   (<= 1e-4 relative);
 - a batch mixing linear, upsampled and emission-time scenes equals the
-  per-scene calls bitwise, and a repeated call is bitwise identical.
+  per-scene calls bitwise, and a repeated call is bitwise identical;
+- outputs shorter and longer than the input, the direct path alone, and six
+  small random scenes (trajectory kind, window, taps, tier layout, U, Q, array
+  motion) against the complex step.
 """
 from dataclasses import replace
 
@@ -242,3 +245,36 @@ def test_output_lengths_and_free_field(which, n_out_kind):
     assert api.workspace_errors(ws) == 0
     ref = oracle.adjoint_x(oracle_scene(spec), dy[0], spec.n_in)
     assert rel_l2(dx.cpu().numpy().astype(np.float64), ref) < 1e-5
+
+
+def _random_option_spec(i):
+    # a small random scene with band-limited tiers or emission-time delays:
+    # random trajectory kind, window, taps, tier layout (U, Q), microphones and
+    # array motion, for the complex-step comparison
+    rng = np.random.default_rng(9500 + i)
+    retarded = bool(i % 2)
+    fs = float(rng.choice([16000.0, 22050.0, 48000.0]))
+    kind = int(rng.choice([W.LINE, W.CIRCLE, W.SPLINE]))
+    tiers = []
+    for b in sorted(rng.choice(np.arange(0, 3), size=1, replace=False).tolist()) + [W.RHO_INF]:
+        if not retarded and (b == W.RHO_INF or rng.random() < 0.5):  # the last tier upsampled
+            U = int(rng.choice([2, 4, 8]))
+            M = int(rng.choice([2, 4, 6]))
+            tiers.append((b, fs / (U * M), U))
+        else:
+            tiers.append((b, fs / int(rng.choice([1, 4, 12, 32]))))
+    spec = W.small_scene(seed=600 + i, K=int(rng.integers(1, 3)), fs=fs, seconds=float(rng.uniform(0.02, 0.035)),
+                         traj_kind=kind, window=int(rng.choice([W.HANN, W.KAISER])),
+                         taps=int(rng.choice([16, 32])), tiers=tiers)
+    spec = replace(spec, delay_model=1 if retarded else 0, up_halfwidth=int(rng.choice([2, 4])))
+    if rng.random() < 0.4:
+        d = rng.standard_normal(3)
+        spec = replace(spec, arr_kind=W.LINE, arr_traj=[0.0, 0.0, 0.0] + list(d) + [0.3], arr_duration=spec.duration)
+    return spec
+
+
+@pytest.mark.parametrize("i", range(6))
+def test_random_option_scene_gradients_match_complex_step(i):
+    spec = _random_option_spec(i)
+    ids = {W.LINE: [0, 1, 2, 6], W.CIRCLE: [0, 1, 3, 4, 5], W.SPLINE: [0, 1, 4, 8]}[spec.traj_kind]
+    _cs_case(spec, ids)
