@@ -494,18 +494,19 @@ def _fwd_bwd_ms(torch, api, rooms, xs, tg, ws, reps=3):
         ys = api.synthesize(rooms, xs, workspace=ws)
         api.synthesize_backward(rooms, xs, [y - t[None] for y, t in zip(ys, tg)], workspace=ws)
     torch.cuda.synchronize()
-    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
     t_f = t_b = 0.0
     for _ in range(reps):
         e0.record(stream)
         ys = api.synthesize(rooms, xs, workspace=ws)
-        dys = [y - t[None] for y, t in zip(ys, tg)]
         e1.record(stream)
-        api.synthesize_backward(rooms, xs, dys, workspace=ws)
+        dys = [y - t[None] for y, t in zip(ys, tg)]  # the loss gradient: neither pass's work
         e2.record(stream)
+        api.synthesize_backward(rooms, xs, dys, workspace=ws)
+        e3.record(stream)
         torch.cuda.synchronize()
         t_f += e0.elapsed_time(e1) / reps
-        t_b += e1.elapsed_time(e2) / reps
+        t_b += e2.elapsed_time(e3) / reps
     return t_f, t_b
 
 

@@ -222,9 +222,9 @@ msrc_status msrc_synthesize(const msrc_room_t* rooms, int32_t n_rooms,
  * record capacity; msrc_tile_configs() lists how many exist):
  * MSRC_TILE_DEFAULT = the process default (msrc_set_tile_config, initially
  * MSRC_TILE_AUTO); MSRC_TILE_AUTO = chosen from the call's knot layout (tiles
- * of 1024 samples with room for many interval records when most images sit on
- * knots at most 24 samples apart, tiles of 768 samples with two CTAs per SM
- * otherwise); else 0 .. msrc_tile_configs() - 1. The _cfg entry points take it per call, so
+ * of 768 samples with two CTAs per SM; per-knot records, which hold twice as
+ * many images per block, when most images sit on knots at most 24 samples
+ * apart, interval records otherwise); else 0 .. msrc_tile_configs() - 1. The _cfg entry points take it per call, so
  * that workloads tuned differently (msrc_autotune) share a process without
  * overwriting each other's choice. The workspace size depends on it: size the
  * workspace with the configuration the call uses. An id out of range is

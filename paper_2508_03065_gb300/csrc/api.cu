@@ -64,10 +64,12 @@ uint32_t g_test_extra_tx = 0;  // msrc_test_stall_window_copies
 
 // MSRC_TILE_AUTO: the configuration measured fastest for the call's knot
 // layout. Knot spacings of at most 24 samples (1 kHz knots at 16 kHz) need
-// many interval records per image: tile configuration 10 (1024-sample tiles,
-// 10240 records) holds the most images per block. Sparser knots run in
-// configuration 11 (768-sample tiles, two CTAs per SM). The spacing that
-// counts is that of the tiers holding most of the call's images.
+// many records per image: tile configuration 14 (768-sample tiles, two CTAs
+// per SM, knot records: 162 images per block at 16-sample spacing) holds
+// enough images per block. Sparser knots run in configuration 11 (the same
+// tiles with interval records, which save a load and a multiply per image
+// pair and sample). The spacing that counts is that of the tiers holding most
+// of the call's images.
 int auto_config(const msrc_room_t* rooms, int n) {
   int64_t dense = 0, sparse = 0;
   for (int r = 0; r < n; ++r) {
@@ -78,7 +80,7 @@ int auto_config(const msrc_room_t* rooms, int n) {
       (N <= 24 ? dense : sparse) += R->tier_count[t] * int64_t(R->n_mics);
     }
   }
-  return dense > sparse ? 10 : 11;
+  return dense > sparse ? 14 : 11;
 }
 
 // The configuration a call runs in: its own, the process default, or the
@@ -593,9 +595,11 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
       // (the forward synthesis and the gradient kernel store them for image
       // pairs: an even count)
       const int rec_per_image = (T - 1) / N + 2;
-      if (2 * rec_per_image > tc.reccap)
+      // interval records: one float2 per image and interval (a pair takes two
+      // images' worth); knot records: one float2 per image pair and knot
+      if ((tc.knots ? rec_per_image : 2 * rec_per_image) > tc.reccap)
         return fail(MSRC_ERR_UNSUPPORTED, "tile configuration too small for knot spacing %d", N);
-      int B = std::max(1, std::min(tc.block, tc.reccap / rec_per_image));
+      int B = std::max(1, std::min(tc.block, (tc.knots ? 2 * tc.reccap : tc.reccap) / rec_per_image));
       if (backward) B = std::max(1, std::min(B, int(backward_unit_cap()) / (rec_per_image + 1)));
       if (B > 1) B &= ~1;
       int64_t n_knots = J + 1;

@@ -1338,7 +1338,7 @@ cudaError_t persistent_launch(K kern, size_t smem, int64_t items, const KernelAr
 
 }  // namespace
 
-static const TileConfig kBwConfig = {kBwThreads, kBwChunks, kGradWcap, kBwRecCap, kBwBlock};
+static const TileConfig kBwConfig = {kBwThreads, kBwChunks, kGradWcap, kBwRecCap, kBwBlock, 0};
 const TileConfig& backward_tile_config() { return kBwConfig; }
 size_t backward_unit_cap() { return kBwUnitCap; }
 int64_t backward_bl_scratch_floats() { return kGradScratchFloats < kRecScratchFloats ? kGradScratchFloats : kRecScratchFloats; }

@@ -131,21 +131,19 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 // acc + (beta_i / (4 pi d_i(n))) e_i(n) for one chunk sample of an image pair
 // (paired layout, see records_from_phi), read from the staged window (kStride
-// columns per segment). R = the pair's interval record, AB its gain terms, I4
-// its column byte offsets; rf2 = {r, r} with r the sample's offset in its knot
-// interval. The delay, its rounding, the local variable w, tau / G and the
-// accumulation run as float2 pairs (one instruction for both images); the
-// window offsets, the loads and the Farrow polynomial per image.
+// columns per segment). Y = the pair's Y(n) from its records (see
+// gather_pairs), AB its gain terms, I4 its column byte offsets. The rounding of
+// the delay, the local variable w, tau / G and the accumulation run as float2
+// pairs (one instruction for both images); the window offsets, the loads and
+// the Farrow polynomial per image.
 // kChecked: the window is processed in several column passes and only columns
 // inside this pass count; otherwise every read position lies inside the window
 // by construction and the index is only clamped to the window arrays.
 // Unchecked reads index the window by byte offset (split_offset's form): the
 // offset of the power-4 value, 4 times it for the powers 0..3.
 template <int kStride, bool kChecked>
-__device__ __forceinline__ float2 pair_sample(const float4* zq, const float4 R, const float4 AB,
-                                              const int2 I4, float2 rf2, unsigned rmc4, int rmj, unsigned wmax,
-                                              float2 acc) {
-  const float2 Y = __ffma2_rn(rf2, make_float2(R.z, R.w), make_float2(R.x, R.y));
+__device__ __forceinline__ float2 pair_sample(const float4* zq, const float2 Y, const float4 AB, const int2 I4,
+                                              unsigned rmc4, int rmj, unsigned wmax, float2 acc) {
   const float2 q = __fadd2_rn(Y, make_float2(kRound, kRound));
   const float2 t = __fadd2_rn(q, make_float2(-kRound, -kRound));
   const float2 w = __ffma2_rn(t, make_float2(-1.0f, -1.0f), Y);       // Y - round(Y), exact
@@ -177,47 +175,77 @@ __device__ __forceinline__ float2 pair_sample(const float4* zq, const float4 R, 
 // All image pairs of the block for this thread's kChunks samples; rmj[c] =
 // r - m_lo + jj N_t of chunk c (its interval jj = jc[c]). acc[c] holds the
 // sums over the even and the odd images of the block.
+// kKnots = false: interval records, Y = Psi + sigma r from one float4 per pair;
+// kKnots = true: knot records, Y = (1 - s) K_jj + s K_jj+1 from two float2 per
+// pair (s = r / N_t; half the record storage, one more load and multiply).
 // kOne: every chunk of this lane lies in one knot interval (warp-uniform), so
 // one record load per pair serves all chunks.
-template <int kStride, int kChunks, int kUnroll, bool kChecked, bool kOne>
-__device__ __forceinline__ void gather_pairs(const float4* zq, const float4* rec4,
-                                             const float4* ab_s, const int2* i4_s, int cntp, const int* jc,
-                                             const int* rmj, const float* rf, unsigned wmax, float2* acc) {
+template <int kStride, int kChunks, int kUnroll, bool kChecked, bool kOne, bool kKnots>
+__device__ __forceinline__ void gather_pairs(const float4* zq, const float2* rec, const float4* ab_s,
+                                             const int2* i4_s, int cntp, const int* jc, const int* rmj,
+                                             const float* rf, float invN, unsigned wmax, float2* acc) {
   unsigned rmc4[kChunks];
-  float2 rf2[kChunks];
-  const float4* row[kChunks];  // records of chunk c: row jc[c] of the interval-major table
+  float2 wa[kChunks], wb[kChunks];  // interval records: {r, r}; knot records: {1 - s, 1 - s}, {s, s}
+  const float2* row[kChunks];      // records of chunk c: row jc[c] of the interval- (knot-) major table
 #pragma unroll
   for (int c = 0; c < kChunks; ++c) {
     rmc4[c] = fold_rounding(rmj[c]) << 2;
-    rf2[c] = make_float2(rf[c], rf[c]);
-    row[c] = rec4 + jc[c] * cntp;
+    if (kKnots) {
+      const float sN = rf[c] * invN;
+      wa[c] = make_float2(1.0f - sN, 1.0f - sN);
+      wb[c] = make_float2(sN, sN);
+      row[c] = rec + jc[c] * cntp;
+    } else {
+      wa[c] = make_float2(rf[c], rf[c]);
+      row[c] = reinterpret_cast<const float2*>(reinterpret_cast<const float4*>(rec) + jc[c] * cntp);
+    }
   }
+  auto pair_y = [&](int c, int q, const float4 R0) {
+    if constexpr (kKnots) {
+      const float2 K0 = (kOne || c == 0) ? make_float2(R0.x, R0.y) : row[c][q];
+      const float2 K1 = (kOne || c == 0) ? make_float2(R0.z, R0.w) : row[c][q + cntp];
+      return __ffma2_rn(wb[c], K1, __fmul2_rn(wa[c], K0));
+    } else {
+      const float4 R = (kOne || c == 0) ? R0 : reinterpret_cast<const float4*>(row[c])[q];
+      return __ffma2_rn(wa[c], make_float2(R.z, R.w), make_float2(R.x, R.y));
+    }
+  };
+  auto first = [&](int q) {  // chunk 0's records of pair q (all chunks' with kOne)
+    if constexpr (kKnots) {
+      const float2 K0 = row[0][q], K1 = row[0][q + cntp];
+      return make_float4(K0.x, K0.y, K1.x, K1.y);
+    } else {
+      return reinterpret_cast<const float4*>(row[0])[q];
+    }
+  };
   int p = 0;
   for (; p + kUnroll <= cntp; p += kUnroll) {
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const float4 AB = ab_s[p + u];
       const int2 I4 = i4_s[p + u];
-      const float4 R0 = row[0][p + u];
+      const float4 R0 = first(p + u);
 #pragma unroll
       for (int c = 0; c < kChunks; ++c)
-        acc[c] = pair_sample<kStride, kChecked>(zq, (kOne || c == 0) ? R0 : row[c][p + u], AB, I4, rf2[c],
-                                                rmc4[c], rmj[c], wmax, acc[c]);
+        acc[c] = pair_sample<kStride, kChecked>(zq, pair_y(c, p + u, R0), AB, I4, rmc4[c], rmj[c], wmax, acc[c]);
     }
   }
   for (; p < cntp; ++p) {
     const float4 AB = ab_s[p];
     const int2 I4 = i4_s[p];
-    const float4 R0 = row[0][p];
+    const float4 R0 = first(p);
 #pragma unroll
     for (int c = 0; c < kChunks; ++c)
-      acc[c] = pair_sample<kStride, kChecked>(zq, (kOne || c == 0) ? R0 : row[c][p], AB, I4, rf2[c], rmc4[c],
-                                              rmj[c], wmax, acc[c]);
+      acc[c] = pair_sample<kStride, kChecked>(zq, pair_y(c, p, R0), AB, I4, rmc4[c], rmj[c], wmax, acc[c]);
   }
 }
 
-template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock, int kUnroll>
+template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock, int kUnroll, bool kKnots>
 __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(const __grid_constant__ KernelArgs a) {
+  constexpr int kLayout = kKnots ? kRecForwardKnots : kRecForward;
+  // relative knot delays of the block (cnt x nk floats): knot records hold twice
+  // as many image-knots as interval records hold image-intervals
+  constexpr int kPhiCap = (kKnots ? 2 * kRecCap : kRecCap) + kBlock;
   extern __shared__ __align__(16) float4 smem4[];
   float4* zq_s = smem4;                                                  // kFarrowSegs x kWcap
   float2* rec_s = reinterpret_cast<float2*>(zq_s + kFarrowSegs * kWcap);  // kRecCap interval records
@@ -227,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
   float4* u_s = smem4;
   float4* um_s = u_s + kThreads * kChunks + 4;                           // moving array
   float4* anc_s = um_s + kThreads * kChunks + 4;                         // 3 x kBlock
-  float* phi_s = reinterpret_cast<float*>(anc_s + 3 * kBlock);           // kRecCap + kBlock
+  float* phi_s = reinterpret_cast<float*>(anc_s + 3 * kBlock);           // kPhiCap
   // emission-time delays: u_s holds the array increments, then 6 x kBlock anchors, then phi
   float4* an6_s = um_s;
   float* phi_r = reinterpret_cast<float*>(an6_s + 6 * kBlock);
@@ -237,9 +265,8 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
   static_assert(kWcap % 4 == 0, "window columns in steps of 4 (the bulk copies' alignment of the rows)");
   static_assert(kBlock <= kThreads, "the record builders give every image at least one thread");
   constexpr int kTile = kThreads * kChunks;
-  static_assert(4 * (2 * (kTile + 4) + 3 * kBlock) + kRecCap + kBlock <= 4 * kFarrowSegs * kWcap,
-                "prologue scratch");
-  static_assert(4 * ((kTile + 4) + 6 * kBlock) + kRecCap + kBlock <= 4 * kFarrowSegs * kWcap,
+  static_assert(4 * (2 * (kTile + 4) + 3 * kBlock) + kPhiCap <= 4 * kFarrowSegs * kWcap, "prologue scratch");
+  static_assert(4 * ((kTile + 4) + 6 * kBlock) + kPhiCap <= 4 * kFarrowSegs * kWcap,
                 "prologue scratch (emission-time delays)");
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -266,14 +293,14 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
     float tmin, tmax;
     int cnt = g.cnt;
     if (S.delay_model == 1) {
-      item_records_ret<kThreads, kRecForward>(a, S, g, rec_s, img_s, u_s, an6_s, phi_r, &tmin, &tmax, gscale);
+      item_records_ret<kThreads, kLayout>(a, S, g, rec_s, img_s, u_s, an6_s, phi_r, &tmin, &tmax, gscale);
     } else if (S.tier_up[g.t] > 1) {
       // band-limited knot upsampling: its scratch takes the z window
-      if (!item_records_bl<kThreads, kRecForward>(a, S, g, rec_s, img_s, reinterpret_cast<float*>(smem4),
+      if (!item_records_bl<kThreads, kLayout>(a, S, g, rec_s, img_s, reinterpret_cast<float*>(smem4),
                                            int64_t(kFarrowSegs) * kWcap * 4, &tmin, &tmax, gscale))
         cnt = 0;
     } else {
-      item_records<kThreads, kRecForward>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax, gscale);
+      item_records<kThreads, kLayout>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax, gscale);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -319,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
     one = __all_sync(0xffffffffu, one);
     // paired record layout (see records_from_phi)
     const int cntp = pair_count(cnt);
-    const float4* rec4 = reinterpret_cast<const float4*>(rec_s);
+    const float invN = 1.0f / float(g.N);
     const float4* ab_s = reinterpret_cast<const float4*>(img_s);
     const int2* i4_s = reinterpret_cast<const int2*>(ab_s + cntp);
     const float4* zqg = a.p.zq + S.z_base;
@@ -362,14 +389,14 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       constexpr int kPairUnroll = kUnroll >= 2 ? kUnroll / 2 : 1;
       if (width <= kWcap) {
         if (one)
-          gather_pairs<kWcap, kChunks, kPairUnroll, false, true>(zq_s, rec4, ab_s, i4_s, cntp, jc, rmj, rf,
-                                                                 wmax, acc);
+          gather_pairs<kWcap, kChunks, kPairUnroll, false, true, kKnots>(zq_s, rec_s, ab_s, i4_s, cntp, jc, rmj, rf,
+                                                                         invN, wmax, acc);
         else
-          gather_pairs<kWcap, kChunks, kPairUnroll, false, false>(zq_s, rec4, ab_s, i4_s, cntp, jc, rmj, rf,
-                                                                  wmax, acc);
+          gather_pairs<kWcap, kChunks, kPairUnroll, false, false, kKnots>(zq_s, rec_s, ab_s, i4_s, cntp, jc, rmj,
+                                                                          rf, invN, wmax, acc);
       } else {
-        gather_pairs<kWcap, kChunks, kPairUnroll, true, false>(zq_s, rec4, ab_s, i4_s, cntp, jc, rmj, rf,
-                                                               wmax, acc);
+        gather_pairs<kWcap, kChunks, kPairUnroll, true, false, kKnots>(zq_s, rec_s, ab_s, i4_s, cntp, jc, rmj, rf,
+                                                                       invN, wmax, acc);
       }
     }
     float* out = a.p.part + S.part_base + (int64_t(g.mic) * S.n_blocks + g.blk) * S.n_out;
@@ -401,9 +428,9 @@ __global__ void k_reduce(const __grid_constant__ KernelArgs a) {
   S.y[int64_t(mic) * S.n_out + n] = acc;
 }
 
-template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock, int kUnroll>
+template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock, int kUnroll, bool kKnots>
 cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
-  auto kern = k_synth<kThreads, kChunks, kWcap, kRecCap, kBlock, kUnroll>;
+  auto kern = k_synth<kThreads, kChunks, kWcap, kRecCap, kBlock, kUnroll, kKnots>;
   const size_t smem = size_t(kFarrowSegs) * kWcap * sizeof(float4) + size_t(kRecCap) * sizeof(float2) +
                       size_t(kBlock) * sizeof(int4);
   static PerDevice setup;  // per device: shared-memory limit set, grid computed
@@ -421,22 +448,27 @@ cudaError_t run_synth(const KernelArgs& a, cudaStream_t st) {
 }  // namespace
 
 // Tile configurations of the synthesis launch (see TileConfig).
-#define MSRC_TILE_CONFIGS(X)             \
-  X(0, 512, 3, 3040, 4096, 256, 8)       \
-  X(1, 256, 2, 1440, 1664, 256, 4)       \
-  X(2, 384, 2, 2560, 3072, 256, 4)       \
-  X(3, 1024, 1, 3040, 4096, 256, 2)      \
-  X(4, 512, 2, 3040, 4096, 256, 8)       \
-  X(5, 512, 1, 3040, 4096, 256, 8)       \
-  X(6, 512, 3, 3040, 4096, 256, 4)       \
-  X(7, 512, 2, 3040, 4096, 256, 16)      \
-  X(8, 512, 3, 2240, 8192, 256, 8)       \
-  X(9, 512, 2, 2240, 8192, 256, 8)       \
-  X(10, 512, 2, 1920, 10240, 256, 8)     \
-  X(11, 256, 3, 1440, 2048, 256, 8)
+// Columns: id, threads, chunks, window columns, record capacity (float2),
+// images per block, pair unroll x 2, knot records.
+#define MSRC_TILE_CONFIGS(X)                \
+  X(0, 512, 3, 3040, 4096, 256, 8, 0)       \
+  X(1, 256, 2, 1440, 1664, 256, 4, 0)       \
+  X(2, 384, 2, 2560, 3072, 256, 4, 0)       \
+  X(3, 1024, 1, 3040, 4096, 256, 2, 0)      \
+  X(4, 512, 2, 3040, 4096, 256, 8, 0)       \
+  X(5, 512, 1, 3040, 4096, 256, 8, 0)       \
+  X(6, 512, 3, 3040, 4096, 256, 4, 0)       \
+  X(7, 512, 2, 3040, 4096, 256, 16, 0)      \
+  X(8, 512, 3, 2240, 8192, 256, 8, 0)       \
+  X(9, 512, 2, 2240, 8192, 256, 8, 0)       \
+  X(10, 512, 2, 1920, 10240, 256, 8, 0)     \
+  X(11, 256, 3, 1440, 2048, 256, 8, 0)      \
+  X(12, 256, 3, 1440, 2048, 256, 8, 1)      \
+  X(13, 512, 2, 1920, 8448, 256, 8, 1)      \
+  X(14, 256, 3, 1200, 4000, 256, 8, 1)
 
 static const TileConfig kConfigs[] = {
-#define MSRC_ROW(id, th, ch, wc, rc, bl, un) {th, ch, wc, rc, bl},
+#define MSRC_ROW(id, th, ch, wc, rc, bl, un, kn) {th, ch, wc, rc, bl, kn},
     MSRC_TILE_CONFIGS(MSRC_ROW)
 #undef MSRC_ROW
 };
@@ -472,8 +504,8 @@ cudaError_t launch_forward(const KernelArgs& a, int cfg, cudaStream_t st, cudaEv
   if (ev) cudaEventRecord(ev[0], st);
   cudaError_t e = cudaSuccess;
   switch (cfg) {
-#define MSRC_CASE(id, th, ch, wc, rc, bl, un) \
-  case id: e = run_synth<th, ch, wc, rc, bl, un>(a, st); break;
+#define MSRC_CASE(id, th, ch, wc, rc, bl, un, kn) \
+  case id: e = run_synth<th, ch, wc, rc, bl, un, kn != 0>(a, st); break;
     MSRC_TILE_CONFIGS(MSRC_CASE)
 #undef MSRC_CASE
     default: e = cudaErrorInvalidValue; break;

@@ -144,10 +144,11 @@ struct SceneDev {
 
 // Tile configuration of the synthesis launch: CTA threads, 32-sample chunks per
 // warp (tile = threads * chunks samples), shared z-window capacity (samples),
-// shared record capacity (one record per image and knot interval), maximum
-// images per block.
+// shared record capacity (float2 units: one per image and knot interval, or
+// with knot records one per image pair and knot), maximum images per block,
+// record format (0 interval records, 1 knot records).
 struct TileConfig {
-  int threads, chunks, wcap, reccap, block;
+  int threads, chunks, wcap, reccap, block, knots;
 };
 int tile_config_count();
 const TileConfig& tile_config(int cfg);

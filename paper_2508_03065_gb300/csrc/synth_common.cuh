@@ -262,8 +262,10 @@ __device__ __forceinline__ void anchor_df(const SceneDev& S, uint32_t code, cons
 }
 
 // Record layouts: one record per image (the reverse-mode dx kernel), or per
-// image pair for the forward synthesis and the gradient kernel.
-constexpr int kRecPlain = 0, kRecForward = 1, kRecAdjoint = 2;
+// image pair for the forward synthesis and the gradient kernel; the forward
+// synthesis also takes per-knot records (kRecForwardKnots, below), half the
+// size of interval records, for tiers whose knots are close together.
+constexpr int kRecPlain = 0, kRecForward = 1, kRecAdjoint = 2, kRecForwardKnots = 3;
 
 // Paired record layout of the forward synthesis (kRecForward): images 2p and 2p + 1
 // of a block share one 16-byte interval record per interval jj,
@@ -275,6 +277,10 @@ constexpr int kRecPlain = 0, kRecForward = 1, kRecAdjoint = 2;
 // an odd block's last pair carries a copy of its last image with zero gain
 // (a = 0, b = +inf), which reads in-bounds columns and adds nothing. Every
 // operand of the pair arithmetic is then one aligned 8-byte register pair.
+// Per-knot layout (kRecForwardKnots): per knot jj and pair p one float2
+//   kn[jj * cntp + p] = {K_2p, K_2p+1},  K = -S phi_jj - 1/2,
+// so that Y = (1 - s) K_jj + s K_jj+1 (s = r / N_t) for a sample of interval jj
+// (the same Y as Psi + sigma r); image records as for kRecForward.
 __device__ __forceinline__ int pair_count(int cnt) { return (cnt + 1) >> 1; }
 
 // Interval records of an item from the relative delays phi at its knots
@@ -286,6 +292,20 @@ __device__ __forceinline__ void records_from_phi(const ItemGeom& g, const float*
   const int nk = g.nk;
   const int nrec = nk - 1;
   const int cntp = pair_count(g.cnt);
+  if (kLayout == kRecForwardKnots) {  // one float2 per (knot, pair): K = -S phi - 1/2
+    const int tpk = kThreads / g.cnt;
+    if (threadIdx.x < tpk * g.cnt) {
+      const int j0 = threadIdx.x / g.cnt;
+      const int ib = threadIdx.x - j0 * g.cnt;
+      for (int jj = j0; jj < nk; jj += tpk) {
+        const float K = fmaf(-float(kFarrowSegs), phi_s[ib * nk + jj], -0.5f);
+        float* f = reinterpret_cast<float*>(rec_s + jj * cntp + (ib >> 1));
+        f[ib & 1] = K;
+        if ((ib & 1) == 0 && ib == g.cnt - 1) f[1] = K;  // odd block: the zero-gain copy
+      }
+    }
+    return;
+  }
   // image-fastest as in item_records: consecutive threads, consecutive records
   const int tpi = kThreads / g.cnt;
   if (threadIdx.x < tpi * g.cnt) {
@@ -350,7 +370,7 @@ __device__ __forceinline__ void put_image_record(int4* img_s, int ib, int cnt, i
                                    (ib >> 1));
   const int h = ib & 1;
   const float Dp = Dfl - 0.5f / kFarrowSegs;
-  if (kLayout == kRecForward) {
+  if (kLayout == kRecForward || kLayout == kRecForwardKnots) {
     const float inf = __int_as_float(0x7f800000);
     const bool live = gain > 0.0f;
     ab[h] = live ? -(1.0f / kFarrowSegs) / gain : 0.0f;

@@ -329,7 +329,7 @@ def test_device_farrow_table_against_oracle_taps(taps, window, beta):
     lib.msrc_destroy_room(h)
 
 
-@pytest.mark.parametrize("tiers,expect", [([(1, 16000.0), (2**31 - 1, 1000.0)], 10),   # most images on 16-sample knots
+@pytest.mark.parametrize("tiers,expect", [([(1, 16000.0), (2**31 - 1, 1000.0)], 14),   # most images on 16-sample knots
                                           ([(1, 16000.0), (2**31 - 1, 250.0)], 11)])   # sparse knots
 def test_automatic_tile_configuration(tiers, expect):
     # the default configuration follows the knot layout of the call's images
