@@ -364,6 +364,31 @@ void host_source(const msrc_traj_desc& T, double t, double out[3]) {
   }
 }
 
+// Power-basis cubics of the spline's segments: segment s is interpolated at
+// x = 0, 1/3, 2/3, 1 (host_source, de Boor) and the cubic through the four
+// points solved for (the segment is a cubic, so this is exact up to rounding:
+// about 1e-14 relative).
+void spline_segments(const msrc_traj_desc& T, double poly[MSRC_MAX_CTRL - 3][3][4]) {
+  const int m = T.n_ctrl - 3;
+  for (int sg = 0; sg < m; ++sg) {
+    double v[4][3];
+    for (int k = 0; k < 4; ++k) host_source(T, (sg + k / 3.0) / m * T.duration_s, v[k]);
+    for (int c = 0; c < 3; ++c) {
+      // Newton divided differences on the nodes 0, h, 2h, 3h (h = 1/3)
+      const double h = 1.0 / 3.0;
+      const double f0 = v[0][c], f1 = v[1][c], f2 = v[2][c], f3 = v[3][c];
+      const double d1 = (f1 - f0) / h, d2 = (f2 - f1) / h, d3 = (f3 - f2) / h;
+      const double e1 = (d2 - d1) / (2 * h), e2 = (d3 - d2) / (2 * h);
+      const double g = (e2 - e1) / (3 * h);
+      // p(x) = f0 + d1 x + e1 x (x - h) + g x (x - h)(x - 2h), in powers of x
+      poly[sg][c][0] = f0;
+      poly[sg][c][1] = d1 - e1 * h + g * 2 * h * h;
+      poly[sg][c][2] = e1 - 3 * g * h;
+      poly[sg][c][3] = g;
+    }
+  }
+}
+
 // Checks the source path and the microphones on a 1 ms grid over
 // [t_begin, t_end] (t_begin <= 0 <= t_end; band-limited knot upsampling
 // evaluates the path's extension before 0 and past its end): the source
@@ -539,6 +564,7 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
       for (int d = 0; d < 3; ++d) S.mics[m][d] = R->mics[m][d];
     std::memcpy(S.traj, R->traj.params, sizeof(S.traj));
     S.traj_kind = R->traj.kind;
+    if (R->traj.kind == 2) spline_segments(R->traj, S.traj_poly);
     S.n_ctrl = R->traj.n_ctrl;
     if (R->arr_moving) {
       S.arr_moving = 1;

@@ -58,6 +58,9 @@ struct SceneDev {
   double mics[MSRC_MAX_MICS][3];
   double traj[48];
   int32_t traj_kind, n_ctrl;
+  // spline source: per segment s the cubic in x = m t / duration - s (m
+  // segments), traj_poly[s][coordinate][power], for the FP64 knot positions
+  double traj_poly[MSRC_MAX_CTRL - 3][3][4];
   // microphone array motion: microphones at mics[m] + a(t) - a(0)
   double arr_params[48];
   double arr_duration;
@@ -246,6 +249,8 @@ struct KernelArgs {
   int32_t max_time_groups;       // largest time-group count of one scene
   uint32_t test_extra_tx;        // test hook: bytes a window staging expects beyond its copies (0)
 };
+// passed by value as a __grid_constant__ kernel parameter
+static_assert(sizeof(KernelArgs) <= 32000, "kernel parameter space");
 
 // Image code: n_d + 64 in 7 bits each, parity bits above.
 __host__ __device__ inline uint32_t pack_image(int nx, int ny, int nz, int pbits) {

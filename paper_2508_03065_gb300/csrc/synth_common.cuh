@@ -43,12 +43,13 @@ __device__ inline void trajectory_point(int kind, const double* p, int n_ctrl, d
     out[1] = p[1] + p[3] * sn;
     out[2] = p[2];
   } else {
+    // in units of the knot spacing: um = m u, knot i at clamp(i - 3, 0, m);
+    // de Boor's ratios (u - knot_i) / (knot_{i+4-r} - knot_i) then divide by
+    // an integer q = 1..3 (a multiplication by 1/q: one FP64 division per point)
     const int m = n_ctrl - 3;  // segments
-    double u = t / duration;
-    u = fmin(1.0, fmax(0.0, u));
-    int span = min(int(u * m), m - 1);  // segment index
-    // knot i of the clamped vector: clamp((i - 3) / m, 0, 1)
-    auto knot = [m](int i) { return fmin(1.0, fmax(0.0, double(i - 3) / double(m))); };
+    const double um = fmin(double(m), fmax(0.0, t * (double(m) / duration)));
+    const int span = min(int(um), m - 1);  // segment index
+    auto kk = [m](int i) { return min(max(i - 3, 0), m); };
     double dd[4][3];
     for (int j = 0; j < 4; ++j)
       for (int c = 0; c < 3; ++c) dd[j][c] = p[3 * (span + j) + c];
@@ -56,17 +57,29 @@ __device__ inline void trajectory_point(int kind, const double* p, int n_ctrl, d
     for (int r = 1; r <= 3; ++r)
       for (int j = 3; j >= r; --j) {
         const int i = j + k - 3;
-        const double den = knot(i + 4 - r) - knot(i);
-        const double al = den > 0.0 ? (u - knot(i)) / den : 0.0;
-        for (int c = 0; c < 3; ++c) dd[j][c] = (1.0 - al) * dd[j - 1][c] + al * dd[j][c];
+        const int q = kk(i + 4 - r) - kk(i);
+        const double rq = q == 1 ? 1.0 : (q == 2 ? 0.5 : (1.0 / 3.0));
+        const double al = q > 0 ? (um - double(kk(i))) * rq : 0.0;
+        for (int c = 0; c < 3; ++c) dd[j][c] = fma(al, dd[j][c] - dd[j - 1][c], dd[j - 1][c]);
       }
     for (int c = 0; c < 3; ++c) out[c] = dd[3][c];
   }
 }
 
-// Source position s(t).
+// Source position s(t); a spline by its segment's cubic (Horner).
 __device__ inline void source_position(const SceneDev& S, double t, double out[3]) {
-  trajectory_point(S.traj_kind, S.traj, S.n_ctrl, S.duration, t, out);
+  if (S.traj_kind != 2) {
+    trajectory_point(S.traj_kind, S.traj, S.n_ctrl, S.duration, t, out);
+    return;
+  }
+  const int m = S.n_ctrl - 3;
+  const double um = fmin(double(m), fmax(0.0, t * (double(m) / S.duration)));
+  const int sg = min(int(um), m - 1);
+  const double x = um - double(sg);
+  for (int c = 0; c < 3; ++c) {
+    const double* q = S.traj_poly[sg][c];
+    out[c] = fma(fma(fma(q[3], x, q[2]), x, q[1]), x, q[0]);
+  }
 }
 
 // Displacement of the microphone array a(t) - a(0) (zero for a static array).
