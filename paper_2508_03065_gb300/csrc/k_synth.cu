@@ -273,11 +273,15 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
   if (threadIdx.x == 0) mbar_init(&s_mbar, 1);
   unsigned phase = 0;  // of s_mbar, the same in every thread
 
+  if (threadIdx.x == 0) s_item = int(atomicAdd(a.p.counter, 1u));
   for (;;) {
-    if (threadIdx.x == 0) s_item = int(atomicAdd(a.p.counter, 1u));
     __syncthreads();
     const int64_t item = s_item;
     if (item >= a.totals[4]) break;
+    // the next item's index is requested now and stored after this item's
+    // gather, so that the atomic's round trip overlaps the work
+    unsigned next_item = 0;
+    if (threadIdx.x == 0) next_item = atomicAdd(a.p.counter, 1u);
     int s = 0;
     int64_t li = item;
     if (a.n_scenes > 1) {
@@ -405,7 +409,8 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       const int n = g.n0 + 32 * (warp * kChunks + c) + lane;
       if (valid[c]) out[n] = acc[c].x + acc[c].y;
     }
-    __syncthreads();  // shared memory and s_item are reused by the next item
+    __syncthreads();  // shared memory is reused by the next item
+    if (threadIdx.x == 0) s_item = int(next_item);
   }
 }
 
