@@ -210,8 +210,8 @@ __device__ __forceinline__ void grad_pairs(const float4* zq_s, const float2* zp_
                                            const float4* id_s, const int2* ii_s, const float4* uxy_s,
                                            const float2* uz_s, const float4* bwp_s, int cntp, int nk,
                                            const int* jc, const int* rmj, const float* rf, const float* sN,
-                                           const float* dyf, unsigned pw, float (&V)[kBwChunks][6],
-                                           float (&bacc)[6]) {
+                                           const float* dyf, unsigned pw, float2 (&V)[kBwChunks][6],
+                                           float2 (&bacc)[6]) {
   constexpr unsigned kCap = unsigned(kFarrowSegs * kGradWcap - 1);
   const float4* row[kBwChunks];
   unsigned rmc[kBwChunks];
@@ -266,21 +266,21 @@ __device__ __forceinline__ void grad_pairs(const float4* zq_s, const float2* zp_
       const float2 w0 = __ffma2_rn(w1, make_float2(-1.0f, -1.0f), ad);
       const float4 U0 = uxy_s[ub + jc[c]], U1 = uxy_s[ub + jc[c] + 1];
       const float2 Z0 = uz_s[ub + jc[c]], Z1 = uz_s[ub + jc[c] + 1];
-      V[c][0] = fmaf(w0.x, U0.x, fmaf(w0.y, U0.y, V[c][0]));
-      V[c][1] = fmaf(w0.x, U0.z, fmaf(w0.y, U0.w, V[c][1]));
-      V[c][2] = fmaf(w0.x, Z0.x, fmaf(w0.y, Z0.y, V[c][2]));
-      V[c][3] = fmaf(w1.x, U1.x, fmaf(w1.y, U1.y, V[c][3]));
-      V[c][4] = fmaf(w1.x, U1.z, fmaf(w1.y, U1.w, V[c][4]));
-      V[c][5] = fmaf(w1.x, Z1.x, fmaf(w1.y, Z1.y, V[c][5]));
+      V[c][0] = __ffma2_rn(w0, make_float2(U0.x, U0.y), V[c][0]);
+      V[c][1] = __ffma2_rn(w0, make_float2(U0.z, U0.w), V[c][1]);
+      V[c][2] = __ffma2_rn(w0, Z0, V[c][2]);
+      V[c][3] = __ffma2_rn(w1, make_float2(U1.x, U1.y), V[c][3]);
+      V[c][4] = __ffma2_rn(w1, make_float2(U1.z, U1.w), V[c][4]);
+      V[c][5] = __ffma2_rn(w1, Z1, V[c][5]);
     }
     // the wall weights depend on the image only: once per pair
     const float4 W0 = bwp_s[3 * p], W1 = bwp_s[3 * p + 1], W2 = bwp_s[3 * p + 2];
-    bacc[0] = fmaf(hsum.x, W0.x, fmaf(hsum.y, W0.y, bacc[0]));
-    bacc[1] = fmaf(hsum.x, W0.z, fmaf(hsum.y, W0.w, bacc[1]));
-    bacc[2] = fmaf(hsum.x, W1.x, fmaf(hsum.y, W1.y, bacc[2]));
-    bacc[3] = fmaf(hsum.x, W1.z, fmaf(hsum.y, W1.w, bacc[3]));
-    bacc[4] = fmaf(hsum.x, W2.x, fmaf(hsum.y, W2.y, bacc[4]));
-    bacc[5] = fmaf(hsum.x, W2.z, fmaf(hsum.y, W2.w, bacc[5]));
+    bacc[0] = __ffma2_rn(hsum, make_float2(W0.x, W0.y), bacc[0]);
+    bacc[1] = __ffma2_rn(hsum, make_float2(W0.z, W0.w), bacc[1]);
+    bacc[2] = __ffma2_rn(hsum, make_float2(W1.x, W1.y), bacc[2]);
+    bacc[3] = __ffma2_rn(hsum, make_float2(W1.z, W1.w), bacc[3]);
+    bacc[4] = __ffma2_rn(hsum, make_float2(W2.x, W2.y), bacc[4]);
+    bacc[5] = __ffma2_rn(hsum, make_float2(W2.z, W2.w), bacc[5]);
   }
 }
 
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
 
     int jc[kBwChunks], rr[kBwChunks];
     float rf[kBwChunks], sN[kBwChunks], dyf[kBwChunks];
-    float V[kBwChunks][6];
+    float2 V[kBwChunks][6];
 #pragma unroll
     for (int c = 0; c < kBwChunks; ++c) {
       const int n = g.n0 + 32 * (warp * kBwChunks + c) + lane;
@@ -437,9 +437,11 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
       sN[c] = rf[c] / float(g.N);
       dyf[c] = valid ? __ldg(S.dy + int64_t(g.mic) * S.n_out + n) * fsc : 0.0f;
 #pragma unroll
-      for (int k = 0; k < 6; ++k) V[c][k] = 0.0f;
+      for (int k = 0; k < 6; ++k) V[c][k] = make_float2(0.0f, 0.0f);
     }
-    float bacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float2 bacc[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) bacc[k] = make_float2(0.0f, 0.0f);
     const float4* zqg = a.p.zq + S.z_base;
     const float2* zpg = a.p.zg + S.z_base;
 
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     for (int c = 0; c < kBwChunks; ++c) {
       float vals[6];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) vals[k] = V[c][k];
+      for (int k = 0; k < 6; ++k) vals[k] = V[c][k].x + V[c][k].y;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
         const int kd = __shfl_up_sync(0xffffffffu, jc[c], d);
@@ -543,7 +545,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     // wall partials of the item (fixed-order block sum)
 #pragma unroll
     for (int w = 0; w < 6; ++w) {
-      float v = bacc[w];
+      float v = bacc[w].x + bacc[w].y;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane == 0) s_beta[warp][w] = v;
