@@ -43,13 +43,13 @@ FLOPS_PER_IMAGE_SAMPLE = 18
 # DRAM bytes (read + write) of one synthesis launch on this workload, from one
 # ncu capture of the full-size launch (35.77 MB read + 287.40 MB written, the
 # partial rows); None whenever the kernel changed since.
-K_SYNTH_TRAFFIC_BYTES = 35769088 + 287402752
+K_SYNTH_TRAFFIC_BYTES = 35280640 + 287459584
 # ncu figures of the same kernel (the full section set on the 1 s version of
 # this scene, --clock-control none; profiles/k_synth_order20_48k.md): FP32 pipe
 # utilisation beside the flop-count roofline below. None once the kernel changed.
-K_SYNTH_NCU = {"fma_pipe_active_pct": 49.6, "fmaheavy_pipe_active_pct": 49.8, "issue_active_pct": 69.1,
-               "thread_instructions_per_image_sample": 19.9, "shared_wavefronts_per_sm_cycle": 0.74,
-               "source": "ncu --set full on the 1 s scene, k_synth<256, 3, 1440, 2048, 256, 8>"}
+K_SYNTH_NCU = {"fma_pipe_active_pct": 50.0, "alu_pipe_active_pct": 39.2, "issue_active_pct": 69.6,
+               "thread_instructions_per_image_sample": 19.9, "shared_wavefronts_per_sm_cycle": 0.71,
+               "source": "ncu --set full on the 1 s scene, k_synth<256, 3, 1440, 2048, 256, 8, interval records>"}
 SM_COUNT = 152
 SMEM_BYTES_PER_CLK_PER_SM = 128
 FP32_LANES_PER_SM = 128
