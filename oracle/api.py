@@ -243,7 +243,8 @@ def knot_delay(scene: Scene, idx: int, t) -> np.ndarray:
 
 def knot_delay_cs(scene: Scene, idx: int, t, param_id: int, h: float = 1e-20) -> np.ndarray:
     """Complex-step derivative of knot_delay (s) with respect to one parameter
-    (ids < 48 index traj[], 48..53 the wall reflection coefficients)."""
+    (ids < 48 index traj[], 48..53 the wall reflection coefficients, 54..101
+    the array trajectory's arr_traj[])."""
     t = np.ascontiguousarray(np.atleast_1d(t), np.float64)
     out = np.zeros(t.size)
     sc = scene.to_c()
@@ -344,7 +345,8 @@ def loss(scene: Scene, x: np.ndarray, target: np.ndarray) -> float:
 
 def loss_grad_cs(scene: Scene, x: np.ndarray, target: np.ndarray, param_ids, h: float = 1e-20) -> np.ndarray:
     """Complex-step gradient of 0.5*||y - target||^2; ids < 48 index traj[],
-    48..53 index the wall reflection coefficients."""
+    48..53 index the wall reflection coefficients, 54..101 the array
+    trajectory's arr_traj[]."""
     x = np.ascontiguousarray(x, np.float64)
     target = np.ascontiguousarray(target, np.float64)
     ids = np.ascontiguousarray(np.atleast_1d(param_ids), np.int32)

@@ -155,6 +155,7 @@ template <class T>
 struct Params {
   T traj[48];
   T beta[6];
+  T arr[48];  // microphone-array trajectory (used when arr_kind >= 0)
 };
 
 template <class T>
@@ -162,6 +163,7 @@ Params<T> params_from(const OracleScene& S) {
   Params<T> P;
   for (int i = 0; i < 48; ++i) P.traj[i] = T(S.traj[i]);
   for (int i = 0; i < 6; ++i) P.beta[i] = T(S.beta[i]);
+  for (int i = 0; i < 48; ++i) P.arr[i] = T(S.arr_traj[i]);
   return P;
 }
 
@@ -195,67 +197,59 @@ std::vector<double> clamped_knots(int n_ctrl) {
   return kv;
 }
 
-// Source position s(t), Sec. II-C ("sample a segment of the band-limited
-// trajectory p(n)"). Parameter layout of traj[]:
+// Point of a trajectory of one of the source's kinds at time t, with real or
+// complex parameters p and a real or complex time t (the emission time of a
+// complex-step delay). Parameter layout:
 //   line:   p0[3], direction[3] (normalised here), speed v      -> p0 + v t dir
 //   circle: centre[3], radius R, speed v, start angle theta0    -> centre + R(cos, sin, 0)(theta0 + v t / R)
 //   spline: control points P_0..P_{n_ctrl-1} (3 each); u = clamp(t / T, 0, 1)
 template <class T, class TT>
-void source_position(const OracleScene& S, const Params<T>& P, TT t, T out[3]) {
-  // the time t is real, or complex (the emission time of a complex-step delay)
-  if (S.traj_kind == 0) {
-    T nrm = std::sqrt(P.traj[3] * P.traj[3] + P.traj[4] * P.traj[4] + P.traj[5] * P.traj[5]);
-    for (int d = 0; d < 3; ++d) out[d] = P.traj[d] + P.traj[6] * t * P.traj[3 + d] / nrm;
-  } else if (S.traj_kind == 1) {
-    T R = P.traj[3];
-    T ang = P.traj[5] + P.traj[4] * t / R;
-    out[0] = P.traj[0] + R * std::cos(ang);
-    out[1] = P.traj[1] + R * std::sin(ang);
-    out[2] = P.traj[2];
-  } else {
-    // u = clamp(t / T, 0, 1), by the real part (a clamped u is constant)
-    TT u = t / S.duration;
-    if (re(u) < 0.0) u = TT(0.0);
-    if (re(u) > 1.0) u = TT(1.0);
-    const std::vector<double> kv = clamped_knots(S.n_ctrl);
-    for (int d = 0; d < 3; ++d) out[d] = T(0.0);
-    for (int c = 0; c < S.n_ctrl; ++c) {
-      const TT B = bspline_basis(c, 3, u, kv);
-      for (int d = 0; d < 3; ++d) out[d] += B * P.traj[3 * c + d];
-    }
-  }
-}
-
-// Point of a trajectory of the source's kinds (line, circle, clamped cubic
-// B-spline) with real parameters, by the same formulas as source_position.
-void trajectory_point(int kind, const double* p, int n_ctrl, double duration, double t, double out[3]) {
+void trajectory_point_t(int kind, const T* p, int n_ctrl, double duration, TT t, T out[3]) {
   if (kind == 0) {
-    const double nrm = std::sqrt(p[3] * p[3] + p[4] * p[4] + p[5] * p[5]);
+    T nrm = std::sqrt(p[3] * p[3] + p[4] * p[4] + p[5] * p[5]);
     for (int d = 0; d < 3; ++d) out[d] = p[d] + p[6] * t * p[3 + d] / nrm;
   } else if (kind == 1) {
-    const double ang = p[5] + p[4] * t / p[3];
-    out[0] = p[0] + p[3] * std::cos(ang);
-    out[1] = p[1] + p[3] * std::sin(ang);
+    T R = p[3];
+    T ang = p[5] + p[4] * t / R;
+    out[0] = p[0] + R * std::cos(ang);
+    out[1] = p[1] + R * std::sin(ang);
     out[2] = p[2];
   } else {
-    double u = std::min(1.0, std::max(0.0, t / duration));
+    // u = clamp(t / T, 0, 1), by the real part (a clamped u is constant)
+    TT u = t / duration;
+    if (re(u) < 0.0) u = TT(0.0);
+    if (re(u) > 1.0) u = TT(1.0);
     const std::vector<double> kv = clamped_knots(n_ctrl);
-    for (int d = 0; d < 3; ++d) out[d] = 0.0;
+    for (int d = 0; d < 3; ++d) out[d] = T(0.0);
     for (int c = 0; c < n_ctrl; ++c) {
-      const double B = bspline_basis(c, 3, u, kv);
+      const TT B = bspline_basis(c, 3, u, kv);
       for (int d = 0; d < 3; ++d) out[d] += B * p[3 * c + d];
     }
   }
 }
 
+// Source position s(t), Sec. II-C ("sample a segment of the band-limited
+// trajectory p(n)"), with the trajectory parameters of P.
+template <class T, class TT>
+void source_position(const OracleScene& S, const Params<T>& P, TT t, T out[3]) {
+  trajectory_point_t(S.traj_kind, P.traj, S.n_ctrl, S.duration, t, out);
+}
+
+// Point of a trajectory with real parameters (the array motion and the
+// exported helpers).
+void trajectory_point(int kind, const double* p, int n_ctrl, double duration, double t, double out[3]) {
+  trajectory_point_t(kind, p, n_ctrl, duration, t, out);
+}
+
 // Microphone position at time t: static, or carried by the array motion a(t)
-// as mic + a(t) - a(0).
-void mic_position(const OracleScene& S, double t, double out[3]) {
-  for (int d = 0; d < 3; ++d) out[d] = S.mic[d];
+// as mic + a(t) - a(0), with the array trajectory parameters of P.
+template <class T>
+void mic_position(const OracleScene& S, const Params<T>& P, double t, T out[3]) {
+  for (int d = 0; d < 3; ++d) out[d] = T(S.mic[d]);
   if (S.arr_kind < 0) return;
-  double a0[3], at[3];
-  trajectory_point(S.arr_kind, S.arr_traj, S.arr_n_ctrl, S.arr_duration, 0.0, a0);
-  trajectory_point(S.arr_kind, S.arr_traj, S.arr_n_ctrl, S.arr_duration, t, at);
+  T a0[3], at[3];
+  trajectory_point_t(S.arr_kind, P.arr, S.arr_n_ctrl, S.arr_duration, 0.0, a0);
+  trajectory_point_t(S.arr_kind, P.arr, S.arr_n_ctrl, S.arr_duration, t, at);
   for (int d = 0; d < 3; ++d) out[d] += at[d] - a0[d];
 }
 
@@ -264,8 +258,8 @@ template <class T>
 T image_distance(const OracleScene& S, const Params<T>& P, const Image& im, double t) {
   T s[3];
   source_position(S, P, t, s);
-  double m[3];
-  mic_position(S, t, m);
+  T m[3];
+  mic_position(S, P, t, m);
   T acc = T(0.0);
   for (int d = 0; d < 3; ++d) {
     const double sigma = 1.0 - 2.0 * im.p[d];
@@ -291,8 +285,8 @@ T image_distance(const OracleScene& S, const Params<T>& P, const Image& im, doub
 // the difference between the slope and its central-difference estimate).
 template <class T>
 T retarded_delay(const OracleScene& S, const Params<T>& P, const Image& im, double t) {
-  double m[3];
-  mic_position(S, t, m);
+  T m[3];
+  mic_position(S, P, t, m);
   auto dist = [&](T te) {
     T s[3];
     source_position(S, P, te, s);
@@ -520,7 +514,8 @@ void oracle_knot_delay_cs(const OracleScene* S, long idx, const double* t, long 
   const std::vector<Image> imgs = enumerate_images(*S);
   Params<cplx> P = params_from<cplx>(*S);
   if (param_id < 48) P.traj[param_id] += cplx(0.0, h);
-  else P.beta[param_id - 48] += cplx(0.0, h);
+  else if (param_id < 54) P.beta[param_id - 48] += cplx(0.0, h);
+  else P.arr[param_id - 54] += cplx(0.0, h);
   for (long i = 0; i < n_t; ++i) out[i] = (knot_distance(*S, P, imgs[idx], t[i]) / S->c).imag() / h;
 }
 
@@ -690,7 +685,8 @@ double oracle_loss(const OracleScene* S, const double* x, long Ns, long n_out, c
 }
 
 // Complex-step derivatives of the loss: for each requested parameter q,
-// param_ids[q] < 48 selects traj[param_ids[q]], 48..53 selects beta[param_ids[q]-48];
+// param_ids[q] < 48 selects traj[param_ids[q]], 48..53 selects beta[param_ids[q]-48],
+// 54..101 selects the array trajectory's arr_traj[param_ids[q]-54];
 // grad[q] = Im(L(theta + i h e_q)) / h.
 void oracle_loss_grad_cs(const OracleScene* S, const double* x, long Ns, long n_out,
                          const double* target, const int32_t* param_ids, long n_params,
@@ -700,7 +696,8 @@ void oracle_loss_grad_cs(const OracleScene* S, const double* x, long Ns, long n_
     Params<cplx> P = params_from<cplx>(*S);
     const int id = param_ids[q];
     if (id < 48) P.traj[id] += cplx(0.0, h);
-    else P.beta[id - 48] += cplx(0.0, h);
+    else if (id < 54) P.beta[id - 48] += cplx(0.0, h);
+    else P.arr[id - 54] += cplx(0.0, h);
     double im_sum = 0.0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : im_sum)
     for (long n = 0; n < n_out; ++n) {

@@ -10,7 +10,11 @@ source's kinds. Pinned by:
   received 1 kHz sine is x(t - r(t)/c) / (4 pi r(t)) within the fractional-delay
   response error, with apparent frequency f0 (1 - v/c);
 - the pure-Python brute force (mirroring, de Boor) on a tiny room with a
-  circling array.
+  circling array;
+- derivatives with respect to the array trajectory: the complex step of a knot
+  delay against that of the explicit distance (a line array), and the
+  complex-step loss gradient against Richardson-extrapolated central
+  differences (circle and spline arrays, both delay models).
 """
 from dataclasses import replace
 
@@ -100,3 +104,62 @@ def test_brute_force_tiny_room_moving_array(arr_kind, arr_traj):
     y = oracle.synthesize(oracle_scene(spec), x)
     yb = np.array(brute.synthesize(spec, list(x), x.size))
     assert rel_l2(y, yb) < 1e-12
+
+
+@pytest.mark.parametrize("param", [54, 56, 57, 58, 60])
+def test_array_derivative_matches_closed_form(param):
+    """Complex-step derivative of a knot delay with respect to the array's line
+    parameters (ids 54.., arr_traj[]) against the complex-step derivative of the
+    explicit distance |r_i - (m + v t u)|, u = dir / |dir|, for the direct path
+    and mirrored images (reception-time delays; the array's offset a(0) cancels)."""
+    h = 1e-20
+    arr = [0.3, -0.2, 0.1, 0.6, 0.8, 0.1, 0.9]
+    sc = _scene(traj_kind=0, traj=[1.2, 1.1, 1.4, 1.0, 0.5, 0.0, 0.0], arr_kind=0, arr_traj=arr, arr_duration=1.0)
+    tab = oracle.enumerate_images(sc)
+    t = np.array([0.0, 0.2, 0.7])
+    src = np.array(sc.traj[:3])
+    for i in range(0, tab["tier"].size, 9):
+        got = oracle.knot_delay_cs(sc, i, t, param)
+        sg = np.array([1 - 2 * int(p) for p in tab["p"][i]])
+        r = sg * src + 2.0 * np.array([int(n) for n in tab["n"][i]]) * np.array(sc.dims)
+        q = np.array(arr, dtype=complex)
+        q[param - 54] += 1j * h
+        u = q[3:6] / np.sqrt(np.sum(q[3:6] ** 2))
+        want = []
+        for tk in t:
+            m = np.array(sc.mic) + q[6] * tk * u          # a(t) - a(0) = v t u (the p0 terms cancel)
+            want.append((np.sqrt(np.sum((r - m) ** 2)) / sc.c).imag / h)
+        want = np.array(want)
+        assert np.max(np.abs(got - want)) <= 1e-10 * max(np.max(np.abs(want)), 1e-12), (i, got, want)
+
+
+@pytest.mark.parametrize("delay_model,arr_kind,ids", [(0, W.CIRCLE, [54, 55, 57, 58, 59]),
+                                                      (0, W.SPLINE, [54, 58, 62, 65]),
+                                                      (1, W.LINE, [54, 57, 58, 60])])
+def test_array_loss_gradient_matches_richardson(delay_model, arr_kind, ids):
+    """Complex-step loss gradient with respect to the array trajectory's
+    parameters against central differences of the real loss with Richardson
+    extrapolation."""
+    spec = W.small_scene(seed=46, K=1, seconds=0.02, window=W.HANN, taps=16, traj_kind=W.SPLINE,
+                         tiers=[(0, 16000.0), (W.RHO_INF, 2000.0)])
+    arr = {W.LINE: [0.0, 0.0, 0.0, 0.3, 0.9, 0.2, 0.8],
+           W.CIRCLE: [0.0, 0.0, 0.0, 0.12, 0.6, 0.4],
+           W.SPLINE: [0.0, 0.0, 0.0, 0.05, 0.02, 0.0, 0.08, 0.07, 0.01, 0.1, 0.12, 0.03]}[arr_kind]
+    spec = replace(spec, delay_model=delay_model, arr_kind=arr_kind, arr_traj=arr, arr_duration=spec.duration,
+                   arr_n_ctrl=4 if arr_kind == W.SPLINE else 0)
+    sc = oracle_scene(spec)
+    x = spec.x.astype(np.float64)
+    target = np.random.default_rng(6).standard_normal(spec.n_in) * 0.01
+    g_cs = oracle.loss_grad_cs(sc, x, target, ids)
+
+    def loss_at(pid, dv):
+        a = list(sc.arr_traj)
+        a[pid - 54] += dv
+        return oracle.loss(replace(sc, arr_traj=a), x, target)
+
+    for q, pid in enumerate(ids):
+        hh = 1e-4
+        d1 = (loss_at(pid, hh) - loss_at(pid, -hh)) / (2 * hh)
+        d2 = (loss_at(pid, hh / 2) - loss_at(pid, -hh / 2)) / hh
+        fd = (4 * d2 - d1) / 3
+        assert abs(fd - g_cs[q]) <= 1e-6 * np.max(np.abs(g_cs)) + 1e-6 * abs(g_cs[q]), (pid, fd, g_cs[q])
