@@ -277,6 +277,26 @@ msrc_status msrc_synthesize_backward(const msrc_room_t* rooms, int32_t n_rooms,
                                      double* const* dbeta_dev,
                                      void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* msrc_synthesize_backward with one more output per room:
+ *   darray_dev[r] (48 doubles, device, nullable): dL/d of the microphone
+ *                 array's trajectory parameters (msrc_set_array_trajectory;
+ *                 the microphones sit at their positions plus a(t) - a(0)),
+ *                 laid out like those parameters; zeros for a room without
+ *                 array motion.
+ * The microphones' positions are inputs of Sec. II-A's distance; this is its
+ * derivative through the array motion: dd/dm = -Delta / d at the knot time
+ * (reception-time distances), through the upsampler's weights for band-limited
+ * tiers, and dd/dm = -u / (1 + (sigma o u) . s'(e) / c) for emission-time
+ * delays. Asking for it adds a second pass of the gradient kernel over the
+ * linear tiers. Same workspace (msrc_workspace_size) and other arguments as
+ * msrc_synthesize_backward, whose results it leaves unchanged. */
+msrc_status msrc_synthesize_backward_ex(const msrc_room_t* rooms, int32_t n_rooms,
+                                        const float* const* x_dev, const int64_t* n_in,
+                                        const float* const* dy_dev, const int64_t* n_out,
+                                        float* const* dx_dev, double* const* dparams_dev,
+                                        double* const* dbeta_dev, double* const* darray_dev,
+                                        void* workspace_dev, size_t workspace_bytes, void* stream);
+
 /* Batched synthesis with a reusable plan. msrc_batch_create plans the call
  * (scene descriptors, work queue of (scene, microphone, image block, output
  * tile) items, workspace layout) and uploads the descriptors into the

@@ -86,6 +86,9 @@ SIGNATURES = [
     ("msrc_synthesize_backward", _I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P), _I64P,
                                         ctypes.POINTER(_P), _I64P, ctypes.POINTER(_P),
                                         ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.c_size_t, _P]),
+    ("msrc_synthesize_backward_ex", _I32, [ctypes.POINTER(_P), _I32, ctypes.POINTER(_P), _I64P,
+                                           ctypes.POINTER(_P), _I64P, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                           ctypes.POINTER(_P), ctypes.POINTER(_P), _P, ctypes.c_size_t, _P]),
     ("msrc_workspace_errors", _I32, [_P, _P, ctypes.POINTER(ctypes.c_uint32)]),
     ("msrc_test_stall_window_copies", _I32, [ctypes.c_uint32]),
     ("msrc_measure_alu_peaks", _I32, [_P, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),

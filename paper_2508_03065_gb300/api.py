@@ -317,12 +317,15 @@ def profile_read():
 
 def synthesize_backward(rooms: Sequence[Room], xs: Sequence[torch.Tensor], dys: Sequence[torch.Tensor],
                         want_dx: bool = True, want_params: bool = True, want_beta: bool = True,
-                        workspace: Optional[Workspace] = None, stream: Optional[torch.cuda.Stream] = None):
+                        workspace: Optional[Workspace] = None, stream: Optional[torch.cuda.Stream] = None,
+                        want_array: bool = False):
     """Reverse mode of synthesize(): for upstream gradients dys[r] of shape
     (n_mics, n_out) returns, per room, (dx, dparams, dbeta): dL/dx (float32,
     n_in), dL/d trajectory parameters (float64, 48, laid out like the
     trajectory parameters) and dL/d wall reflection coefficients (float64, 6),
-    each None when not requested."""
+    each None when not requested. With want_array, a fourth entry: dL/d of the
+    microphone array's trajectory parameters (float64, 48; zeros for a room
+    without array motion)."""
     lib = _lib.load()
     xs = [x.contiguous() for x in xs]
     dys = [d.contiguous().float() for d in dys]
@@ -332,18 +335,20 @@ def synthesize_backward(rooms: Sequence[Room], xs: Sequence[torch.Tensor], dys: 
     dx = [torch.empty(n, dtype=torch.float32, device=dev) for n in n_in] if want_dx else None
     dp = [torch.zeros(48, dtype=torch.float64, device=dev) for _ in rooms] if want_params else None
     db = [torch.zeros(6, dtype=torch.float64, device=dev) for _ in rooms] if want_beta else None
+    da = [torch.zeros(48, dtype=torch.float64, device=dev) for _ in rooms] if want_array else None
     _, bwd = workspace_size(rooms, n_in, n_out, backward=True)
     ws = workspace or _workspace(dev)
     buf = ws.get(bwd)
     hs = _lib.ptr_array([r.handle.value for r in rooms])
     arr = lambda ts: _lib.ptr_array([t.data_ptr() for t in ts]) if ts is not None else None  # noqa: E731
-    _lib.check(lib.msrc_synthesize_backward(hs, len(rooms), arr(xs), _lib.i64_array(n_in), arr(dys),
-                                            _lib.i64_array(n_out), arr(dx), arr(dp), arr(db),
-                                            ctypes.c_void_p(buf.data_ptr()), buf.numel(),
-                                            _stream_handle(stream)))
+    _lib.check(lib.msrc_synthesize_backward_ex(hs, len(rooms), arr(xs), _lib.i64_array(n_in), arr(dys),
+                                               _lib.i64_array(n_out), arr(dx), arr(dp), arr(db), arr(da),
+                                               ctypes.c_void_p(buf.data_ptr()), buf.numel(),
+                                               _stream_handle(stream)))
     out = []
     for r in range(len(rooms)):
-        out.append((dx[r] if dx else None, dp[r] if dp else None, db[r] if db else None))
+        row = (dx[r] if dx else None, dp[r] if dp else None, db[r] if db else None)
+        out.append(row + (da[r],) if want_array else row)
     return out
 
 

@@ -500,7 +500,7 @@ struct Plan {
   int cfg = 0;                      // forward tile configuration
   int64_t dxb_floats = 0;
   size_t off_dxb = 0, off_kslot = 0, off_bpart = 0, off_gk = 0, off_ppart = 0, off_bwt = 0, off_trange = 0;
-  size_t off_otau = 0, off_ograd = 0, off_cgrad = 0;
+  size_t off_otau = 0, off_ograd = 0, off_cgrad = 0, off_kslot_arr = 0, off_garr = 0;
   int kL = 32;
   int taps = 32;
   // band-limited knot upsampling: weight tables (uploaded to off_upw)
@@ -840,6 +840,9 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     P.off_kslot = off; off = align256(off + 12 * size_t(kslot_acc));
     P.off_bpart = off; off = align256(off + 4 * size_t(bpart_acc));
     P.off_gk = off; off = align256(off + 24 * size_t(knot_acc));
+    // moving arrays: the second knot-slot set and knot gradients of dL/da
+    P.off_kslot_arr = off; off = align256(off + (any_moving ? 12 * size_t(kslot_acc) : 0));
+    P.off_garr = off; off = align256(off + (any_moving ? 24 * size_t(knot_acc) : 0));
     P.off_ppart = off; off = align256(off + 8 * size_t(n) * kParamPartialsPerScene);
     P.off_bwt = off; off = align256(off + 32 * I);
     P.off_trange = off; off = align256(off + 8 * size_t(P.totals[4]));
@@ -893,6 +896,8 @@ void fill_args(const Plan& P, const msrc_room_t* rooms, char* ws, KernelArgs& a)
     a.p.kslot = reinterpret_cast<float*>(ws + P.off_kslot);
     a.p.bpart = reinterpret_cast<float*>(ws + P.off_bpart);
     a.p.gk = reinterpret_cast<double*>(ws + P.off_gk);
+    a.p.kslot_arr = reinterpret_cast<float*>(ws + P.off_kslot_arr);
+    a.p.garr = reinterpret_cast<double*>(ws + P.off_garr);
     a.p.ppart = reinterpret_cast<double*>(ws + P.off_ppart);
     a.p.bwt = reinterpret_cast<float4*>(ws + P.off_bwt);
     a.p.trange = reinterpret_cast<float2*>(ws + P.off_trange);
@@ -1460,6 +1465,15 @@ msrc_status msrc_synthesize_backward(const msrc_room_t* rooms, int32_t n_rooms, 
                                      const int64_t* n_in, const float* const* dy_dev, const int64_t* n_out,
                                      float* const* dx_dev, double* const* dparams_dev,
                                      double* const* dbeta_dev, void* ws, size_t ws_bytes, void* stream) {
+  return msrc_synthesize_backward_ex(rooms, n_rooms, x_dev, n_in, dy_dev, n_out, dx_dev, dparams_dev, dbeta_dev,
+                                     nullptr, ws, ws_bytes, stream);
+}
+
+msrc_status msrc_synthesize_backward_ex(const msrc_room_t* rooms, int32_t n_rooms, const float* const* x_dev,
+                                        const int64_t* n_in, const float* const* dy_dev, const int64_t* n_out,
+                                        float* const* dx_dev, double* const* dparams_dev,
+                                        double* const* dbeta_dev, double* const* darray_dev, void* ws,
+                                        size_t ws_bytes, void* stream) {
   if (!x_dev || !dy_dev) return fail(MSRC_ERR_INVALID_ARG, "null signal pointer array");
   Plan P;
   msrc_status s = make_plan(rooms, n_rooms, n_in, n_out, P, true);
@@ -1473,6 +1487,8 @@ msrc_status msrc_synthesize_backward(const msrc_room_t* rooms, int32_t n_rooms, 
     P.scenes[r].dx = dx_dev ? dx_dev[r] : nullptr;
     P.scenes[r].dparams = dparams_dev ? dparams_dev[r] : nullptr;
     P.scenes[r].dbeta = dbeta_dev ? dbeta_dev[r] : nullptr;
+    // dL/d(array trajectory): computed for rooms with a moving array, zero otherwise
+    P.scenes[r].darray = (darray_dev && P.scenes[r].arr_moving) ? darray_dev[r] : nullptr;
   }
   char* w = static_cast<char*>(ws);
   KernelArgs* a = new (std::nothrow) KernelArgs;
@@ -1482,6 +1498,13 @@ msrc_status msrc_synthesize_backward(const msrc_room_t* rooms, int32_t n_rooms, 
   std::vector<char> blob;
   cudaError_t e = cudaMemsetAsync(w, 0, 256, st);
   if (e != cudaSuccess) { delete a; return cuda_fail(e, "workspace header clear"); }
+  for (int r = 0; r < n_rooms; ++r) {
+    if (P.scenes[r].darray) a->want_array = 1;
+    if (darray_dev && darray_dev[r] && !P.scenes[r].darray) {  // a still array: zero gradient
+      e = cudaMemsetAsync(darray_dev[r], 0, 48 * sizeof(double), st);
+      if (e != cudaSuccess) { delete a; return cuda_fail(e, "array gradient clear"); }
+    }
+  }
   s = upload_tables(P, w, st, blob);
   if (s != MSRC_OK) { delete a; return s; }
   e = launch_setup(*a, st);

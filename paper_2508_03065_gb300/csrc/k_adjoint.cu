@@ -285,6 +285,11 @@ __device__ __forceinline__ void grad_pairs(const float4* zq_s, const float2* zp_
 }
 
 // ------------------------------------------------------------------ gradients
+// kArray = false: the source-trajectory knot gradients, the wall terms and the
+// delay ranges (and the option tiers' knot delays). kArray = true: a second
+// pass over the linear tiers of the scenes asking for dL/d(array trajectory),
+// with the unit vectors of the microphone, dd/dm = -Delta / d, into kslot_arr.
+template <bool kArray>
 __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constant__ KernelArgs a) {
   extern __shared__ __align__(16) float4 sm[];
   float4* zq_s = sm;                                                    // kFarrowSegs x kGradWcap
@@ -327,12 +332,16 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     // per-(mic, image, knot) kernels; this item only adds the wall terms and
     // the delay range (zero unit vectors)
     const bool opt = opt_tier(S, g.t);
+    if (kArray && (opt || !S.darray || !S.arr_moving)) {
+      __syncthreads();  // s_item is read by every thread before the next item replaces it
+      continue;
+    }
 
     float tmin, tmax;
     const float* kphi = nullptr;
     g.cnt = adjoint_records<kRecAdjoint>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax, dk_s, dk_s,
                                          &kphi);
-    if (opt && g.cnt > 0) {
+    if (!kArray && opt && g.cnt > 0) {
       // the knot delays D + phi of the item's images, each (mic, image, knot)
       // written by exactly one item: the tile holding the knot's sample, the
       // last tile for the knot past the output
@@ -378,13 +387,15 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
           ey = sg.y * Um.y;
           ez = sg.z * Um.z;
         }
+        // the array pass: dd/dm = -Delta / d = -sigma o (sigma o Delta) / d
         const float inv = __fdividef(1.0f, d);
+        const float ix = kArray ? -sg.x * inv : inv, iy = kArray ? -sg.y * inv : inv, iz = kArray ? -sg.z * inv : inv;
         const int h = ib & 1;
         float* fxy = reinterpret_cast<float*>(uxy_s + (ib >> 1) * g.nk + jj);
         float* fz = reinterpret_cast<float*>(uz_s + (ib >> 1) * g.nk + jj);
-        fxy[h] = (A.x + U.x - ex) * inv;
-        fxy[2 + h] = (A.y + U.y - ey) * inv;
-        fz[h] = (A.z + U.z - ez) * inv;
+        fxy[h] = (A.x + U.x - ex) * ix;
+        fxy[2 + h] = (A.y + U.y - ey) * iy;
+        fz[h] = (A.z + U.z - ez) * iz;
         if (h == 0 && ib == g.cnt - 1) {
           fxy[1] = 0.0f;
           fxy[3] = 0.0f;
@@ -420,7 +431,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
       width += sh;
     }
     // the item's delay range, for the dx kernel's window
-    if (threadIdx.x == 0) a.p.trange[item] = make_float2(rmin, rmax);
+    if (!kArray && threadIdx.x == 0) a.p.trange[item] = make_float2(rmin, rmax);
 
     int jc[kBwChunks], rr[kBwChunks];
     float rf[kBwChunks], sN[kBwChunks], dyf[kBwChunks];
@@ -516,9 +527,9 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     }
     __syncthreads();
     {
-      float* slot = a.p.kslot + 3 * (S.kslot_first[g.t] + int64_t(g.mic) * S.kslot_mic_stride +
-                                     (int64_t(g.blk - S.block_first[g.t]) * S.n_tiles + (g.n0 / kBwTile)) *
-                                         S.kcap[g.t]);
+      float* slot = (kArray ? a.p.kslot_arr : a.p.kslot) +
+                    3 * (S.kslot_first[g.t] + int64_t(g.mic) * S.kslot_mic_stride +
+                         (int64_t(g.blk - S.block_first[g.t]) * S.n_tiles + (g.n0 / kBwTile)) * S.kcap[g.t]);
       constexpr int kChunksPerTile = kBwTile / 32;
       for (int jj = threadIdx.x; jj < g.nk; jj += kBwThreads) {
         float sx = 0.f, sy = 0.f, sz = 0.f;
@@ -551,7 +562,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
       if (lane == 0) s_beta[warp][w] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 6) {
+    if (!kArray && threadIdx.x < 6) {
       float v = 0.f;
       for (int w = 0; w < kBwThreads / 32; ++w) v += s_beta[w][threadIdx.x];
       a.p.bpart[S.bpart_base + li * 8 + threadIdx.x] = v;
@@ -816,6 +827,8 @@ __global__ void k_dx_final(const __grid_constant__ KernelArgs a) {
 // order), the 8 lane sums are added in lane order (bitwise reproducible).
 constexpr int kKnotsPerCta = 32;
 constexpr int kKnotLanes = 8;
+// kArray: the array pass's slots into dL/da(t_j) (garr).
+template <bool kArray>
 __global__ void __launch_bounds__(kKnotsPerCta * kKnotLanes) k_knot_final(const __grid_constant__ KernelArgs a) {
   __shared__ double part[kKnotLanes][kKnotsPerCta][3];
   const int kq = threadIdx.x % kKnotsPerCta, q = threadIdx.x / kKnotsPerCta;
@@ -836,7 +849,7 @@ __global__ void __launch_bounds__(kKnotsPerCta * kKnotLanes) k_knot_final(const 
     // upsampled and emission-time tiers: zero here (k_opt_bl_knots writes the
     // upsampled tiers' knots; emission-time gradients go to the parameters
     // directly)
-    if (S.tier_count[t] > 0 && !opt_tier(S, t)) {
+    if (S.tier_count[t] > 0 && !opt_tier(S, t) && (!kArray || S.darray)) {
       // samples weighting knot j: intervals j - 1 and j, n in [(j-1) N, (j+1) N)
       const int64_t s_lo = max(int64_t(j - 1) * N, int64_t(0));
       const int64_t s_hi = min(int64_t(j + 1) * N - 1, S.n_out - 1);
@@ -848,8 +861,9 @@ __global__ void __launch_bounds__(kKnotsPerCta * kKnotLanes) k_knot_final(const 
             const int n_end = int(min(int64_t(n0 + S.tile), S.n_out)) - 1;
             const int jf = n0 / N, nk = n_end / N - jf + 2;
             if (j < jf || j >= jf + nk) continue;
-            const float* slot = a.p.kslot + 3 * (S.kslot_first[t] + int64_t(mic) * S.kslot_mic_stride +
-                                                 (int64_t(b) * S.n_tiles + tile) * S.kcap[t] + (j - jf));
+            const float* slot = (kArray ? a.p.kslot_arr : a.p.kslot) +
+                                3 * (S.kslot_first[t] + int64_t(mic) * S.kslot_mic_stride +
+                                     (int64_t(b) * S.n_tiles + tile) * S.kcap[t] + (j - jf));
             gx += slot[0];
             gy += slot[1];
             gz += slot[2];
@@ -868,7 +882,7 @@ __global__ void __launch_bounds__(kKnotsPerCta * kKnotLanes) k_knot_final(const 
       sz += part[r][kq][2];
     }
     const SceneDev& S = scene_of(a, s);
-    double* out = a.p.gk + 3 * (S.knot_base[t] + j);
+    double* out = (kArray ? a.p.garr : a.p.gk) + 3 * (S.knot_base[t] + j);
     out[0] = sx;
     out[1] = sy;
     out[2] = sz;
@@ -886,14 +900,13 @@ static_assert(kParamChunks * 48 == kParamPartialsPerScene, "parameter partials p
 // for the emission-time units (images x knots of them).
 __device__ __forceinline__ void sin_cos(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ void sin_cos(float x, float* s, float* c) { sincosf(x, s, c); }
-__device__ __forceinline__ int jacobian_count(const SceneDev& S) {
-  return S.traj_kind == 0 ? 7 : (S.traj_kind == 1 ? 6 : 12);
-}
+__device__ __forceinline__ int jacobian_count(int kind) { return kind == 0 ? 7 : (kind == 1 ? 6 : 12); }
+__device__ __forceinline__ int jacobian_count(const SceneDev& S) { return jacobian_count(S.traj_kind); }
 
 template <class T>
-__device__ int jacobian_terms(const SceneDev& S, T t, const T g[3], T v[12]) {
-  const double* q = S.traj;
-  if (S.traj_kind == 0) {  // s = p0 + v t u, u = dir / |dir|
+__device__ int jacobian_terms(int kind, const double* q, int n_ctrl, double duration, T t, const T g[3],
+                              T v[12]) {
+  if (kind == 0) {  // s = p0 + v t u, u = dir / |dir|
     const T nrm = sqrt(T(q[3]) * T(q[3]) + T(q[4]) * T(q[4]) + T(q[5]) * T(q[5]));
     const T u[3] = {T(q[3]) / nrm, T(q[4]) / nrm, T(q[5]) / nrm};
     const T ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
@@ -905,7 +918,7 @@ __device__ int jacobian_terms(const SceneDev& S, T t, const T g[3], T v[12]) {
     v[6] = t * ug;
     return 0;
   }
-  if (S.traj_kind == 1) {  // s = c + R (cos th, sin th, 0), th = th0 + v t / R
+  if (kind == 1) {  // s = c + R (cos th, sin th, 0), th = th0 + v t / R
     const T R = T(q[3]), vel = T(q[4]);
     T sn, cs;
     sin_cos(T(q[5]) + vel * t / R, &sn, &cs);
@@ -917,8 +930,8 @@ __device__ int jacobian_terms(const SceneDev& S, T t, const T g[3], T v[12]) {
     return 0;
   }
   // clamped uniform cubic B-spline: s = sum_c N_c(u) P_c
-  const int m = S.n_ctrl - 3;
-  const T u = fmin(T(1), fmax(T(0), t / T(S.duration)));
+  const int m = n_ctrl - 3;
+  const T u = fmin(T(1), fmax(T(0), t / T(duration)));
   const int span = min(int(u * T(m)), m - 1);
   auto knot = [m](int i) { return fmin(T(1), fmax(T(0), T(i - 3) / T(m))); };
   // the four non-zero basis functions on the span (triangular scheme)
@@ -942,6 +955,12 @@ __device__ int jacobian_terms(const SceneDev& S, T t, const T g[3], T v[12]) {
   return 3 * span;
 }
 
+// The source trajectory's terms.
+template <class T>
+__device__ __forceinline__ int jacobian_terms(const SceneDev& S, T t, const T g[3], T v[12]) {
+  return jacobian_terms<T>(S.traj_kind, S.traj, S.n_ctrl, S.duration, t, g, v);
+}
+
 // Adds J(t)^T g to the thread's FP64 parameter column:
 // row[p * kParamThreads] += sum_d J[d][p] g[d].
 __device__ void add_source_jacobian(const SceneDev& S, double t, const double g[3], double* row) {
@@ -951,26 +970,30 @@ __device__ void add_source_jacobian(const SceneDev& S, double t, const double g[
   for (int i = 0; i < nt; ++i) row[(p0 + i) * kParamThreads] += v[i];
 }
 
-// FP32 sums of J(e)^T g over consecutive emission-time units, added to the
-// FP64 column when the block of parameters changes (another spline span),
-// every kJacRun units and at the end.
+// FP32 sums of J(t)^T g over consecutive emission-time units of one trajectory
+// (the source's or the array's), added to the FP64 column when the block of
+// parameters changes (another spline span), every kJacRun units and at the end.
 constexpr int kJacRun = 64;
 struct JacAcc {
+  int kind, n_ctrl;
+  const double* q;
+  double duration;
   float v[12];
   int p0 = -1, n = 0;
-  __device__ void flush(const SceneDev& S, double* row) {
+  __device__ JacAcc(int k, const double* params, int nc, double dur) : kind(k), n_ctrl(nc), q(params), duration(dur) {}
+  __device__ void flush(double* row) {
     if (p0 >= 0) {
-      const int nt = jacobian_count(S);
+      const int nt = jacobian_count(kind);
       for (int i = 0; i < nt; ++i) row[(p0 + i) * kParamThreads] += double(v[i]);
     }
     p0 = -1;
     n = 0;
   }
-  __device__ void add(const SceneDev& S, float t, const float g[3], double* row) {
+  __device__ void add(float t, const float g[3], double* row) {
     float w[12];
-    const int q0 = jacobian_terms<float>(S, t, g, w);
+    const int q0 = jacobian_terms<float>(kind, q, n_ctrl, duration, t, g, w);
     if (q0 != p0 || n == kJacRun) {
-      flush(S, row);
+      flush(row);
       p0 = q0;
 #pragma unroll
       for (int i = 0; i < 12; ++i) v[i] = 0.0f;
@@ -1060,7 +1083,7 @@ __global__ void __launch_bounds__(kParamThreads) k_param_partial(const __grid_co
     const float rfs = float(1.0 / S.fs);
     const float k0 = float(S.dense_k0);
     const int64_t kmax = S.n_dense - 2;
-    JacAcc acc;
+    JacAcc acc(S.traj_kind, S.traj, S.n_ctrl, S.duration);
     const int64_t stride = int64_t(kParamChunks) * kParamThreads;
     for (int64_t k = int64_t(chunk) * kParamThreads + threadIdx.x; k < total; k += stride) {
       const OptUnit u = opt_unit(S, k);
@@ -1091,9 +1114,9 @@ __global__ void __launch_bounds__(kParamThreads) k_param_partial(const __grid_co
       const float vs = xs * (su[0] * ds[0] + su[1] * ds[1] + su[2] * ds[2]);  // (sigma o u) . s'(e)
       const float fac = gr / fmaf(vs, rc, 1.0f);
       const float g[3] = {fac * su[0], fac * su[1], fac * su[2]};
-      acc.add(S, es * rfs, g, rows + threadIdx.x);
+      acc.add(es * rfs, g, rows + threadIdx.x);
     }
-    acc.flush(S, rows + threadIdx.x);
+    acc.flush(rows + threadIdx.x);
   }
   __syncthreads();
   if (threadIdx.x < 48) {
@@ -1241,10 +1264,11 @@ __global__ void k_opt_bl_rows(const __grid_constant__ KernelArgs a) {
 
 // dL/ds(t_j) at knot j of an upsampled tier (one CTA per knot of the tier's
 // table): sum over (mic, image) of dL/dd there times sigma o Delta / d, in a
-// fixed order.
+// fixed order; with a moving array whose gradient is asked for, also
+// dL/da(t_j): the same sum with -Delta / d.
 constexpr int kBlThreads = 256;
 __global__ void __launch_bounds__(kBlThreads) k_opt_bl_knots(const __grid_constant__ KernelArgs a) {
-  __shared__ double part[3][kBlThreads];
+  __shared__ double part[6][kBlThreads];
   const int64_t gid = blockIdx.x;
   if (gid >= a.totals[1]) return;
   int s = 0;
@@ -1262,7 +1286,8 @@ __global__ void __launch_bounds__(kBlThreads) k_opt_bl_knots(const __grid_consta
   const float* cg = a.p.cgrad + S.bl_tau_base[t] + int64_t(jt) * rows;
   const double* sp = a.p.knot_pos + 3 * (S.knot_base[t] + jt);
   const double* ap = a.p.arr_pos + 3 * (S.knot_base[t] + jt);
-  double gx = 0.0, gy = 0.0, gz = 0.0;
+  double gx = 0.0, gy = 0.0, gz = 0.0, hx = 0.0, hy = 0.0, hz = 0.0;
+  const bool arr = S.darray && S.arr_moving;
   for (int64_t r = threadIdx.x; r < rows; r += kBlThreads) {
     const float c = cg[r];
     if (c == 0.0f) continue;
@@ -1280,15 +1305,22 @@ __global__ void __launch_bounds__(kBlThreads) k_opt_bl_knots(const __grid_consta
     gx += double(f * sg[0] * D[0]);
     gy += double(f * sg[1] * D[1]);
     gz += double(f * sg[2] * D[2]);
+    hx -= double(f * D[0]);
+    hy -= double(f * D[1]);
+    hz -= double(f * D[2]);
   }
   part[0][threadIdx.x] = gx;
   part[1][threadIdx.x] = gy;
   part[2][threadIdx.x] = gz;
+  part[3][threadIdx.x] = hx;
+  part[4][threadIdx.x] = hy;
+  part[5][threadIdx.x] = hz;
   __syncthreads();
-  if (threadIdx.x < 3) {
+  if (threadIdx.x < (arr ? 6 : 3)) {
     double acc = 0.0;
     for (int r = 0; r < kBlThreads; ++r) acc += part[threadIdx.x][r];
-    a.p.gk[3 * (S.knot_base[t] + jt) + threadIdx.x] = acc;
+    if (threadIdx.x < 3) a.p.gk[3 * (S.knot_base[t] + jt) + threadIdx.x] = acc;
+    else a.p.garr[3 * (S.knot_base[t] + jt) + threadIdx.x - 3] = acc;
   }
 }
 
@@ -1299,6 +1331,113 @@ __global__ void k_param_final(const __grid_constant__ KernelArgs a) {
   double acc = 0.0;
   for (int c = 0; c < kParamChunks; ++c) acc += a.p.ppart[(int64_t(blockIdx.x) * kParamChunks + c) * 48 + threadIdx.x];
   S.dparams[threadIdx.x] = acc;
+}
+
+// Partial dL/d(array trajectory parameters) of one chunk of a scene's units,
+// arranged as k_param_partial. The microphones sit at m + a(t) - a(0), so
+// dL/dtheta_a = sum_j (J_a(t_j) - J_a(0))^T dL/da(t_j), dL/da summed over the
+// microphones. Units: the knots of every tier, dL/da(t_j) from garr; with
+// emission-time delays the (mic, knot, image) units, where at the reception
+// time t_j the implicit derivative of c tau = |sigma o s(t_j - tau) + 2 n L - m(t_j)|
+// gives dd/dm = -u / (1 + (sigma o u) . s'(e) / c), u = Delta / d.
+__global__ void __launch_bounds__(kParamThreads) k_arr_param_partial(const __grid_constant__ KernelArgs a) {
+  const int s = blockIdx.x / kParamChunks, chunk = blockIdx.x % kParamChunks;
+  const SceneDev& S = scene_of(a, s);
+  if (!S.darray || !S.arr_moving) return;
+  extern __shared__ double rows[];  // [48][kParamThreads]
+  for (int p = 0; p < 48; ++p) rows[p * kParamThreads + threadIdx.x] = 0.0;
+  double* row = rows + threadIdx.x;
+  const int last = S.n_tiers - 1;
+  const bool ret = S.delay_model == 1;
+  const int64_t total = ret ? S.n_opt_units
+                            : S.knot_units_first[last] +
+                                  (S.tier_up[last] > 1 ? int64_t(S.bl_knots[last]) : int64_t(S.tier_intervals[last]) + 1);
+  double gsum[3] = {0.0, 0.0, 0.0};  // for the -J_a(0) term
+  if (!ret) {
+    const int64_t per_cta = (total + kParamChunks - 1) / kParamChunks;
+    const int64_t per_thr = (per_cta + kParamThreads - 1) / kParamThreads;
+    const int64_t lo = min(total, chunk * per_cta + threadIdx.x * per_thr);
+    const int64_t hi = min(min(total, (chunk + 1) * per_cta), lo + per_thr);
+    int t = 0;
+    for (int64_t k = lo; k < hi; ++k) {
+      while (t + 1 < S.n_tiers && k >= S.knot_units_first[t + 1]) ++t;
+      if (S.tier_count[t] == 0) continue;
+      const int64_t j = k - S.knot_units_first[t];
+      const double* gk = a.p.garr + 3 * (S.knot_base[t] + j);
+      const double g[3] = {gk[0], gk[1], gk[2]};
+      double v[12];
+      const int p0 = jacobian_terms<double>(S.arr_kind, S.arr_params, S.arr_n_ctrl, S.arr_duration,
+                                            double((j - S.knot_shift[t]) * S.tier_coarse[t]) / S.fs, g, v);
+      const int nt = jacobian_count(S.arr_kind);
+      for (int i = 0; i < nt; ++i) row[(p0 + i) * kParamThreads] += v[i];
+      for (int d = 0; d < 3; ++d) gsum[d] += g[d];
+    }
+  } else {
+    const int64_t base = a.n_scenes > 1 ? a.tab.opt_prefix[s] : int64_t(0);
+    const float4* HI = a.p.dense_hi + S.dense_base;
+    const float4* LO = a.p.dense_lo + S.dense_base;
+    const float xs = float(kDenseOver) * float(S.fs);
+    const float rc = float(1.0 / S.c);
+    const float rfs = float(1.0 / S.fs);
+    const float k0 = float(S.dense_k0);
+    const int64_t kmax = S.n_dense - 2;
+    JacAcc acc(S.arr_kind, S.arr_params, S.arr_n_ctrl, S.arr_duration);
+    const int64_t stride = int64_t(kParamChunks) * kParamThreads;
+    for (int64_t k = int64_t(chunk) * kParamThreads + threadIdx.x; k < total; k += stride) {
+      const OptUnit u = opt_unit(S, k);
+      const int cnt = S.tier_count[u.t];
+      const float gr = a.p.ograd[base + k].x + (u.k > 0 ? a.p.ograd[base + k - cnt].y : 0.0f);
+      if (gr == 0.0f) continue;
+      const int64_t kn = int64_t(u.k) * S.tier_step[u.t];
+      const float es = float(double(kn) - a.p.otau[base + k]);  // emission time (samples)
+      const float x = fmaf(float(kDenseOver), es, -k0);
+      const int64_t i = min(max(int64_t(floorf(x)), int64_t(0)), kmax);
+      const float f = x - float(i);
+      const float4 h0 = HI[i], h1 = HI[i + 1], l0 = LO[i], l1 = LO[i + 1];
+      const float ds[3] = {(h1.x - h0.x) + (l1.x - l0.x), (h1.y - h0.y) + (l1.y - l0.y),
+                           (h1.z - h0.z) + (l1.z - l0.z)};
+      const float sp[3] = {fmaf(f, ds[0], h0.x + l0.x), fmaf(f, ds[1], h0.y + l0.y), fmaf(f, ds[2], h0.z + l0.z)};
+      const double* ap = a.p.arr_pos + 3 * (S.knot_base[u.t] + u.k);
+      int n[3], p[3];
+      unpack_image(a.p.img_code[S.img_base + S.tier_first[u.t] + u.img], n, p);
+      float sg[3], D[3];
+      for (int d = 0; d < 3; ++d) {
+        sg[d] = p[d] ? -1.0f : 1.0f;
+        const float m = float(S.mics[u.mic][d]) + float(ap[d]);
+        D[d] = fmaf(sg[d], sp[d], fmaf(float(2 * n[d]), float(S.dims[d]), -m));
+      }
+      const float rd = rsqrtf(fmaf(D[0], D[0], fmaf(D[1], D[1], D[2] * D[2])));
+      const float uv[3] = {D[0] * rd, D[1] * rd, D[2] * rd};
+      const float vs = xs * (sg[0] * uv[0] * ds[0] + sg[1] * uv[1] * ds[1] + sg[2] * uv[2] * ds[2]);
+      const float fac = -gr / fmaf(vs, rc, 1.0f);
+      const float g[3] = {fac * uv[0], fac * uv[1], fac * uv[2]};
+      acc.add(float(kn) * rfs, g, row);  // the microphone at the reception time
+      for (int d = 0; d < 3; ++d) gsum[d] += double(g[d]);
+    }
+    acc.flush(row);
+  }
+  {  // - J_a(0)^T sum_j dL/da(t_j)
+    const double g0[3] = {-gsum[0], -gsum[1], -gsum[2]};
+    double v[12];
+    const int p0 = jacobian_terms<double>(S.arr_kind, S.arr_params, S.arr_n_ctrl, S.arr_duration, 0.0, g0, v);
+    const int nt = jacobian_count(S.arr_kind);
+    for (int i = 0; i < nt; ++i) row[(p0 + i) * kParamThreads] += v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < 48) {
+    double acc = 0.0;
+    for (int r = 0; r < kParamThreads; ++r) acc += rows[threadIdx.x * kParamThreads + r];
+    a.p.ppart[(int64_t(s) * kParamChunks + chunk) * 48 + threadIdx.x] = acc;
+  }
+}
+
+// dL/d(array trajectory parameters): the chunk partials in chunk order.
+__global__ void k_arr_param_final(const __grid_constant__ KernelArgs a) {
+  const SceneDev& S = scene_of(a, blockIdx.x);
+  if (!S.darray || !S.arr_moving || threadIdx.x >= 48) return;
+  double acc = 0.0;
+  for (int c = 0; c < kParamChunks; ++c) acc += a.p.ppart[(int64_t(blockIdx.x) * kParamChunks + c) * 48 + threadIdx.x];
+  S.darray[threadIdx.x] = acc;
 }
 
 // dL/dbeta_w: sum of the item partials in item order (one CTA per scene).
@@ -1352,9 +1491,9 @@ cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
   cudaError_t e = launch_prefilter(a, st, true);
   if (e != cudaSuccess) return e;
   // per device and kernel: shared-memory limit and persistent grid
-  static PerDevice g_grad, g_dx16, g_dx32, g_dx64;
+  static PerDevice g_grad, g_grad_arr, g_dx16, g_dx32, g_dx64;
   if (a.totals[0] > 0) k_beta_table<<<unsigned((a.totals[0] + 255) / 256), 256, 0, st>>>(a);
-  e = persistent_launch(k_adj_grad, kGradSmem, a.totals[4], a, st, &g_grad);
+  e = persistent_launch(k_adj_grad<false>, kGradSmem, a.totals[4], a, st, &g_grad);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.p.dxb, 0, sizeof(float) * size_t(a.p.dxb_floats), st);
   if (e != cudaSuccess) return e;
@@ -1366,7 +1505,15 @@ cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
   if (a.totals[2] > 0) k_dx_final<<<unsigned((a.totals[2] + T - 1) / T), T, 0, st>>>(a);
   if (a.totals[9] > 0) k_opt_grad<<<unsigned((a.totals[9] + 255) / 256), 256, 0, st>>>(a);
   if (a.totals[1] > 0)
-    k_knot_final<<<unsigned((a.totals[1] + kKnotsPerCta - 1) / kKnotsPerCta), kKnotsPerCta * kKnotLanes, 0, st>>>(a);
+    k_knot_final<false><<<unsigned((a.totals[1] + kKnotsPerCta - 1) / kKnotsPerCta), kKnotsPerCta * kKnotLanes, 0,
+                          st>>>(a);
+  if (a.want_array) {  // the array pass over the linear tiers, then dL/da per knot
+    e = persistent_launch(k_adj_grad<true>, kGradSmem, a.totals[4], a, st, &g_grad_arr);
+    if (e != cudaSuccess) return e;
+    if (a.totals[1] > 0)
+      k_knot_final<true><<<unsigned((a.totals[1] + kKnotsPerCta - 1) / kKnotsPerCta), kKnotsPerCta * kKnotLanes, 0,
+                           st>>>(a);
+  }
   if (a.totals[6] > 0 && a.totals[9] > 0) {
     k_opt_bl_rows<<<unsigned((a.totals[6] + 127) / 128), 128, 0, st>>>(a);
     k_opt_bl_knots<<<unsigned(a.totals[1]), kBlThreads, 0, st>>>(a);
@@ -1382,6 +1529,8 @@ cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
         dev,
         [&](int* v) {
           ae = cudaFuncSetAttribute(k_param_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+          if (ae == cudaSuccess)
+            ae = cudaFuncSetAttribute(k_arr_param_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
           *v = 1;
           return ae == cudaSuccess ? 0 : 1;
         },
@@ -1389,6 +1538,10 @@ cudaError_t launch_backward_kernels(const KernelArgs& a, cudaStream_t st) {
     if (st_attr != 0) return ae != cudaSuccess ? ae : cudaErrorInvalidDevice;
     k_param_partial<<<unsigned(a.n_scenes * kParamChunks), kParamThreads, smem, st>>>(a);
     k_param_final<<<unsigned(a.n_scenes), 64, 0, st>>>(a);
+    if (a.want_array) {
+      k_arr_param_partial<<<unsigned(a.n_scenes * kParamChunks), kParamThreads, smem, st>>>(a);
+      k_arr_param_final<<<unsigned(a.n_scenes), 64, 0, st>>>(a);
+    }
   }
   k_beta_final<<<unsigned(a.n_scenes), kBetaThreads, 0, st>>>(a);
   return cudaGetLastError();

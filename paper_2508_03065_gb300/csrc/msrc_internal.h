@@ -124,6 +124,7 @@ struct SceneDev {
   float* dx;                               // [n_in] or null
   double* dparams;                         // [48] or null
   double* dbeta;                           // [6] or null
+  double* darray;                          // [48] or null: dL/d(array trajectory parameters)
   int64_t dxb_base;                        // first float of the per-(mic, block group) dx rows
   int32_t n_groups;                        // dx block groups over all tiers
   int32_t group_first[MSRC_MAX_TIERS];     // first group of tier t
@@ -207,6 +208,8 @@ struct DevicePtrs {
   float* kslot;                  // knot-gradient slots (3 floats each)
   float* bpart;                  // beta partials (8 floats per (scene, mic, block))
   double* gk;                    // dL/ds(t_j) per tier knot (3 doubles, indexed like knot_pos)
+  float* kslot_arr;              // moving arrays: knot slots of dL/da(t_j), like kslot
+  double* garr;                  // moving arrays: dL/da(t_j) per tier knot, like gk
   double* ppart;                 // trajectory-parameter partials (48 doubles per (scene, knot chunk))
   float4* bwt;                   // per image: dbeta_i/dbeta_w / (4 pi) for walls 0..3 | walls 4..5, gain, 0
   float2* trange;                // reverse mode: delay range (tmin, tmax) of every (mic, block, tile) item
@@ -248,6 +251,7 @@ struct KernelArgs {
   int64_t n_sort_groups;         // time groups over all scenes (the sort key's leading field)
   int32_t max_time_groups;       // largest time-group count of one scene
   uint32_t test_extra_tx;        // test hook: bytes a window staging expects beyond its copies (0)
+  int32_t want_array;            // reverse mode: some scene asks for dL/d(array trajectory)
 };
 // passed by value as a __grid_constant__ kernel parameter
 static_assert(sizeof(KernelArgs) <= 32000, "kernel parameter space");
