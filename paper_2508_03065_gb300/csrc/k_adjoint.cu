@@ -162,7 +162,8 @@ template <int kLayout>
 __device__ int adjoint_records(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                                int4* img_s, float4* u_s, float4* um_s, float4* anc_s, float* phi_s, float* tmin,
                                float* tmax, float* d_s = nullptr, float* dfl_out = nullptr,
-                               const float** phi_out = nullptr) {
+                               const float** phi_out = nullptr, float4* unit_xy = nullptr,
+                               float2* unit_z = nullptr, bool unit_array = false) {
   if (S.delay_model == 1) {
     item_records_ret<kBwThreads, kLayout>(a, S, g, rec_s, img_s, u_s, um_s, phi_s, tmin, tmax, 1.0f, dfl_out);
     if (phi_out) *phi_out = phi_s;
@@ -173,7 +174,8 @@ __device__ int adjoint_records(const KernelArgs& a, const SceneDev& S, const Ite
                                                 kRecScratchFloats, tmin, tmax, 1.0f, dfl_out, phi_out)
                ? g.cnt
                : 0;
-  item_records<kBwThreads, kLayout>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, tmin, tmax, 1.0f, d_s);
+  item_records<kBwThreads, kLayout>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, tmin, tmax, 1.0f, d_s, unit_xy,
+                                    unit_z, unit_array);
   return g.cnt;
 }
 
@@ -314,15 +316,22 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
   __shared__ int s_item;
   __shared__ float s_red[2][kBwThreads / 32];
   __shared__ float s_beta[kBwThreads / 32][6];
+  SceneCursor cursor;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
+  if (threadIdx.x == 0) s_item = int(atomicAdd(a.p.counter, 1u));
   for (;;) {
-    const int64_t item = next_item(a, &s_item);
+    __syncthreads();
+    const int64_t item = s_item;
     if (item >= a.totals[4]) break;
+    // the next item's index is requested now and published at this item's
+    // end, so that the atomic's round trip overlaps the work
+    unsigned next_item = 0;
+    if (threadIdx.x == 0) next_item = atomicAdd(a.p.counter, 1u);
     int s = 0;
     int64_t li = item;
     if (a.n_scenes > 1) {
-      s = find_scene(a.tab.item_prefix, a.n_scenes, item);
+      s = scene_at(a.tab.item_prefix, a.n_scenes, item, cursor);
       li = item - a.tab.item_prefix[s];
     }
     const SceneDev& S = scene_of(a, s);
@@ -334,13 +343,20 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     const bool opt = opt_tier(S, g.t);
     if (kArray && (opt || !S.darray || !S.arr_moving)) {
       __syncthreads();  // s_item is read by every thread before the next item replaces it
+      if (threadIdx.x == 0) s_item = int(next_item);
       continue;
     }
 
     float tmin, tmax;
     const float* kphi = nullptr;
-    g.cnt = adjoint_records<kRecAdjoint>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax, dk_s, dk_s,
-                                         &kphi);
+    // paired layouts of the image loop: unit vectors per (pair, knot) as
+    // {x, x', y, y'} and {z, z'} (written by the linear tiers' record pass;
+    // zeros for the option tiers), wall weights per pair as three float4 of
+    // (w, w') pairs; an odd block's zero-gain copy gets zeros
+    float4* uxy_s = unit_s;
+    float2* uz_s = reinterpret_cast<float2*>(uxy_s + pair_count(g.cnt) * g.nk);
+    g.cnt = adjoint_records<kRecAdjoint>(a, S, g, rec_s, img_s, u_s, um_s, anc_s, phi_s, &tmin, &tmax, nullptr, dk_s,
+                                         &kphi, uxy_s, uz_s, kArray);
     if (!kArray && opt && g.cnt > 0) {
       // the knot delays D + phi of the item's images, each (mic, image, knot)
       // written by exactly one item: the tile holding the knot's sample, the
@@ -358,49 +374,44 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
           obase[int64_t(k) * cnt_t + ib] = double(dk_s[ib]) + double(kphi[ib * nk + jj]);
       }
     }
-    // paired layouts of the image loop: unit vectors per (pair, knot) as
-    // {x, x', y, y'} and {z, z'}, wall weights per pair as three float4 of
-    // (w, w') pairs; an odd block's zero-gain copy gets zeros
+    int m_lo, width;
+    float rmin, rmax;
+    window_of<kBwThreads>(tmin, tmax, g, s_red, &m_lo, &width, &rmin, &rmax);
+    {  // window start congruent to the z rows' origin mod 4 (16-byte row segments)
+      const int sh = int(((int64_t(m_lo) - S.z_m0) % 4 + 4) % 4);
+      m_lo -= sh;
+      width += sh;
+    }
+    // the item's delay range, for the dx kernel's window
+    if (!kArray && threadIdx.x == 0) a.p.trange[item] = make_float2(rmin, rmax);
+    // the first pass's powers 4..5 start copying now: their rows (zp_s) lie
+    // above every prologue scratch array, so only powers 0..3 (zq_s) wait for
+    // the scratch to be dead
+    const float4* zqg = a.p.zq + S.z_base;
+    const float2* zpg = a.p.zg + S.z_base;
+    {
+      const int64_t lo_c = max(int64_t(m_lo), S.z_m0);
+      const int64_t hi_c = min(int64_t(m_lo) + min(kGradWcap, width), S.z_m0 + S.z_len);
+      const int cnt_c = int(hi_c > lo_c ? hi_c - lo_c : int64_t(0));
+      if (cnt_c > 0) {
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          const unsigned bq = unsigned(cnt_c) * 16u;
+          const unsigned bp = unsigned((cnt_c + 3) & ~3) * 8u;  // within the padded rows
+          mbar_expect_tx(&s_mbar, unsigned(kFarrowSegs) * (bq + bp) + a.test_extra_tx);
+          const int dst0 = int(lo_c - m_lo);
+          const int64_t src0 = lo_c - S.z_m0;
+          for (int sg = 0; sg < kFarrowSegs; ++sg)
+            bulk_g2s(zp_s + sg * kGradWcap + dst0, zpg + int64_t(sg) * S.z_len + src0, bp, &s_mbar);
+        }
+      }
+    }
     const int cntp = pair_count(g.cnt);
-    float4* uxy_s = unit_s;
-    float2* uz_s = reinterpret_cast<float2*>(uxy_s + cntp * g.nk);
-    // unit vectors (sigma o Delta) / d of every image at every knot of the tile
-    // (sigma o Delta_j = w + u - sigma o u_m with a moving array; d from the
-    // record pass) (image-fastest thread mapping: one division per thread)
     if (opt) {
       for (int i = threadIdx.x; i < cntp * g.nk; i += kBwThreads) {
         uxy_s[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         uz_s[i] = make_float2(0.f, 0.f);
-      }
-    } else if (const int tpi = kBwThreads / g.cnt; threadIdx.x < tpi * g.cnt) {
-      const int j0 = threadIdx.x / g.cnt;
-      const int ib = threadIdx.x - j0 * g.cnt;
-      const float4 A = anc_s[2 * ib];
-      const float4 sg = anc_s[2 * g.cnt + ib];
-      for (int jj = j0; jj < g.nk; jj += tpi) {
-        const float4 U = u_s[jj];
-        const float d = dk_s[ib * g.nk + jj];
-        float ex = 0.f, ey = 0.f, ez = 0.f;
-        if (S.arr_moving) {
-          const float4 Um = um_s[jj];
-          ex = sg.x * Um.x;
-          ey = sg.y * Um.y;
-          ez = sg.z * Um.z;
-        }
-        // the array pass: dd/dm = -Delta / d = -sigma o (sigma o Delta) / d
-        const float inv = __fdividef(1.0f, d);
-        const float ix = kArray ? -sg.x * inv : inv, iy = kArray ? -sg.y * inv : inv, iz = kArray ? -sg.z * inv : inv;
-        const int h = ib & 1;
-        float* fxy = reinterpret_cast<float*>(uxy_s + (ib >> 1) * g.nk + jj);
-        float* fz = reinterpret_cast<float*>(uz_s + (ib >> 1) * g.nk + jj);
-        fxy[h] = (A.x + U.x - ex) * ix;
-        fxy[2 + h] = (A.y + U.y - ey) * iy;
-        fz[h] = (A.z + U.z - ez) * iz;
-        if (h == 0 && ib == g.cnt - 1) {
-          fxy[1] = 0.0f;
-          fxy[3] = 0.0f;
-          fz[1] = 0.0f;
-        }
       }
     }
     // dbeta_i/dbeta_w / (4 pi) of the block's images, paired
@@ -422,16 +433,6 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
         }
       }
     }
-    int m_lo, width;
-    float rmin, rmax;
-    window_of<kBwThreads>(tmin, tmax, g, s_red, &m_lo, &width, &rmin, &rmax);
-    {  // window start congruent to the z rows' origin mod 4 (16-byte row segments)
-      const int sh = int(((int64_t(m_lo) - S.z_m0) % 4 + 4) % 4);
-      m_lo -= sh;
-      width += sh;
-    }
-    // the item's delay range, for the dx kernel's window
-    if (!kArray && threadIdx.x == 0) a.p.trange[item] = make_float2(rmin, rmax);
 
     int jc[kBwChunks], rr[kBwChunks];
     float rf[kBwChunks], sN[kBwChunks], dyf[kBwChunks];
@@ -453,8 +454,6 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
     float2 bacc[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) bacc[k] = make_float2(0.0f, 0.0f);
-    const float4* zqg = a.p.zq + S.z_base;
-    const float2* zpg = a.p.zg + S.z_base;
 
     for (int p0 = 0; p0 < width; p0 += kGradWcap) {
       const int pass_lo = m_lo + p0;
@@ -472,10 +471,11 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
         if (threadIdx.x == 0) {
           const unsigned bq = unsigned(cnt_c) * 16u;
           const unsigned bp = unsigned((cnt_c + 3) & ~3) * 8u;  // within the padded rows
-          mbar_expect_tx(&s_mbar, unsigned(kFarrowSegs) * (bq + bp) + a.test_extra_tx);
+          // the first pass's expected bytes and powers 4..5 were issued above
+          if (p0 > 0) mbar_expect_tx(&s_mbar, unsigned(kFarrowSegs) * (bq + bp) + a.test_extra_tx);
           for (int sg = 0; sg < kFarrowSegs; ++sg) {
             bulk_g2s(zq_s + sg * kGradWcap + dst0, zqg + int64_t(sg) * S.z_len + src0, bq, &s_mbar);
-            bulk_g2s(zp_s + sg * kGradWcap + dst0, zpg + int64_t(sg) * S.z_len + src0, bp, &s_mbar);
+            if (p0 > 0) bulk_g2s(zp_s + sg * kGradWcap + dst0, zpg + int64_t(sg) * S.z_len + src0, bp, &s_mbar);
           }
         }
         const bool ok = mbar_wait(&s_mbar, phase);
@@ -567,7 +567,8 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
       for (int w = 0; w < kBwThreads / 32; ++w) v += s_beta[w][threadIdx.x];
       a.p.bpart[S.bpart_base + li * 8 + threadIdx.x] = v;
     }
-    __syncthreads();
+    __syncthreads();  // shared memory is reused by the next item
+    if (threadIdx.x == 0) s_item = int(next_item);
   }
 }
 
@@ -674,6 +675,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
   float* phi_s = reinterpret_cast<float*>(anc_s + 3 * kBwBlock);          // kBwRecCap + kBwBlock
   __shared__ int s_item;
   __shared__ float s_red[2][kBwThreads / 32];
+  SceneCursor cursor;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // a gradient kernel that gave up on a wait left some delay ranges unwritten:
   // windows sized from them could be arbitrary, so nothing is scattered (the
@@ -686,7 +688,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
     int s = 0;
     int64_t li = item;
     if (a.n_scenes > 1) {
-      s = find_scene(a.tab.red_prefix, a.n_scenes, item);
+      s = scene_at(a.tab.red_prefix, a.n_scenes, item, cursor);
       li = item - a.tab.red_prefix[s];
     }
     const SceneDev& S = scene_of(a, s);

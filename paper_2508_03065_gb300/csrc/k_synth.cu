@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) mbar_init(&s_mbar, 1);
   unsigned phase = 0;  // of s_mbar, the same in every thread
+  SceneCursor cursor;  // the scene of the current item (batched calls)
 
   if (threadIdx.x == 0) s_item = int(atomicAdd(a.p.counter, 1u));
   for (;;) {
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
     int s = 0;
     int64_t li = item;
     if (a.n_scenes > 1) {
-      s = find_scene(a.tab.item_prefix, a.n_scenes, item);
+      s = scene_at(a.tab.item_prefix, a.n_scenes, item, cursor);
       li = item - a.tab.item_prefix[s];
     }
     const SceneDev& S = scene_of(a, s);

@@ -26,6 +26,29 @@ __device__ __forceinline__ int find_scene(const int64_t* prefix, int n, int64_t 
   return lo;
 }
 
+// Scene of the work items of a persistent CTA. Its items come from one
+// increasing counter, so the scene index only grows: the cursor keeps the
+// current scene's item range and advances by at most a few scenes before it
+// falls back to the binary search (one uncached global load per scene change
+// instead of a search per item).
+struct SceneCursor {
+  int s = 0;
+  int64_t lo = 0, hi = -1;
+};
+__device__ __forceinline__ int scene_at(const int64_t* prefix, int n, int64_t idx, SceneCursor& c) {
+  if (idx >= c.lo && idx < c.hi) return c.s;
+  int s = -1;
+  if (c.hi >= 0 && idx >= c.hi) {
+    for (int k = c.s + 1; k < n && k <= c.s + 4; ++k)
+      if (idx < prefix[k + 1]) { s = k; break; }
+  }
+  if (s < 0) s = find_scene(prefix, n, idx);
+  c.s = s;
+  c.lo = prefix[s];
+  c.hi = prefix[s + 1];
+  return s;
+}
+
 // Point of a trajectory (FP64): line p0 + v t dir/|dir|, circle
 // centre + R (cos, sin, 0)(theta0 + v t / R), or clamped uniform cubic B-spline
 // by de Boor's algorithm on the knot vector {0,0,0,0, 1/m, ..., (m-1)/m, 1,1,1,1}
@@ -406,10 +429,15 @@ __device__ __forceinline__ void put_image_record(int4* img_s, int ib, int cnt, i
   }
 }
 
+// With unit_xy / unit_z (nullable) the unit vectors of the reverse mode are
+// written as well, per image pair and knot {x, x', y, y'} and {z, z'}: the
+// source's (sigma o Delta) / d, or with unit_array the microphone's -Delta / d
+// (an odd block's zero-gain copy gets zeros).
 template <int kThreads, int kLayout = kRecPlain>
 __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemGeom& g, float2* rec_s,
                              int4* img_s, float4* u_s, float4* um_s, float4* anc_s, float* phi_s,
-                             float* tmin_out, float* tmax_out, float gscale = 1.0f, float* d_s = nullptr) {
+                             float* tmin_out, float* tmax_out, float gscale = 1.0f, float* d_s = nullptr,
+                             float4* unit_xy = nullptr, float2* unit_z = nullptr, bool unit_array = false) {
   // knot positions and array displacements as double-float pairs; increments
   // from the anchor knot jf: hi differences of nearby positions are exact
   const int64_t kj = S.knot_base[g.t] + g.jf;
@@ -471,12 +499,32 @@ __device__ void item_records(const KernelArgs& a, const SceneDev& S, const ItemG
     const float4 SG = anc_s[2 * g.cnt + ib];
     for (int jj = j0; jj < nk; jj += tpi) {
       float phi, d;
-      if (moving) knot_increment_moving(A, SG, u_s[jj], um_s[jj], fsc, A2.x, &phi, &d);
-      else knot_increment(A, u_s[jj], fsc, A2.x, &phi, &d);
+      const float4 U = u_s[jj];
+      const float4 Um = moving ? um_s[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (moving) knot_increment_moving(A, SG, U, Um, fsc, A2.x, &phi, &d);
+      else knot_increment(A, U, fsc, A2.x, &phi, &d);
       phi_s[ib * nk + jj] = phi;
       if (d_s) d_s[ib * nk + jj] = d;
       tmin = fminf(tmin, A2.y + phi);
       tmax = fmaxf(tmax, A2.y + phi);
+      if (unit_xy) {
+        // sigma o Delta_j = A + u - sigma o u_m; the microphone's -Delta / d
+        // is -sigma o (sigma o Delta) / d
+        const float inv = __fdividef(1.0f, d);
+        const float ix = unit_array ? -SG.x * inv : inv, iy = unit_array ? -SG.y * inv : inv,
+                    iz = unit_array ? -SG.z * inv : inv;
+        const int h = ib & 1;
+        float* fxy = reinterpret_cast<float*>(unit_xy + (ib >> 1) * nk + jj);
+        float* fz = reinterpret_cast<float*>(unit_z + (ib >> 1) * nk + jj);
+        fxy[h] = fmaf(-SG.x, Um.x, A.x + U.x) * ix;
+        fxy[2 + h] = fmaf(-SG.y, Um.y, A.y + U.y) * iy;
+        fz[h] = fmaf(-SG.z, Um.z, A.z + U.z) * iz;
+        if (h == 0 && ib == g.cnt - 1) {
+          fxy[1] = 0.0f;
+          fxy[3] = 0.0f;
+          fz[1] = 0.0f;
+        }
+      }
     }
   }
   __syncthreads();
