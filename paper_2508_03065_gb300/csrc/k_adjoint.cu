@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
   __shared__ int s_item;
   __shared__ float s_red[2][kBwThreads / 32];
   __shared__ float s_beta[kBwThreads / 32][6];
-  SceneCursor cursor;
+  SceneCursor cursor = fresh_cursor();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
   if (threadIdx.x == 0) s_item = int(atomicAdd(a.p.counter, 1u));
@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_dx(const __grid_constant_
   float* phi_s = reinterpret_cast<float*>(anc_s + 3 * kBwBlock);          // kBwRecCap + kBwBlock
   __shared__ int s_item;
   __shared__ float s_red[2][kBwThreads / 32];
-  SceneCursor cursor;
+  SceneCursor cursor = fresh_cursor();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // a gradient kernel that gave up on a wait left some delay ranges unwritten:
   // windows sized from them could be arbitrary, so nothing is scattered (the

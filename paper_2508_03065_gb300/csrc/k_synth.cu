@@ -272,9 +272,16 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) mbar_init(&s_mbar, 1);
   unsigned phase = 0;  // of s_mbar, the same in every thread
-  SceneCursor cursor;  // the scene of the current item (batched calls)
+  // batched calls: the scene of the current item (s_scene) and the scene
+  // cursor, kept in shared memory by thread 0 (no registers held over the loop)
+  __shared__ int s_scene;
+  __shared__ SceneCursor s_cursor;
 
-  if (threadIdx.x == 0) s_item = int(atomicAdd(a.p.counter, 1u));
+  if (threadIdx.x == 0) {
+    s_cursor = fresh_cursor();
+    s_item = int(atomicAdd(a.p.counter, 1u));
+    s_scene = (a.n_scenes > 1 && s_item < a.totals[4]) ? scene_at(a.tab.item_prefix, a.n_scenes, s_item, s_cursor) : 0;
+  }
   for (;;) {
     __syncthreads();
     const int64_t item = s_item;
@@ -283,12 +290,8 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
     // gather, so that the atomic's round trip overlaps the work
     unsigned next_item = 0;
     if (threadIdx.x == 0) next_item = atomicAdd(a.p.counter, 1u);
-    int s = 0;
-    int64_t li = item;
-    if (a.n_scenes > 1) {
-      s = scene_at(a.tab.item_prefix, a.n_scenes, item, cursor);
-      li = item - a.tab.item_prefix[s];
-    }
+    const int s = s_scene;
+    const int64_t li = a.n_scenes > 1 ? item - s_cursor.lo : item;
     const SceneDev& S = scene_of(a, s);
     const ItemGeom g = item_geometry(S, li, kTile);
 
@@ -411,7 +414,11 @@ __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(c
       if (valid[c]) out[n] = acc[c].x + acc[c].y;
     }
     __syncthreads();  // shared memory is reused by the next item
-    if (threadIdx.x == 0) s_item = int(next_item);
+    if (threadIdx.x == 0) {
+      s_item = int(next_item);
+      if (a.n_scenes > 1 && int64_t(next_item) < a.totals[4])
+        s_scene = scene_at(a.tab.item_prefix, a.n_scenes, int64_t(next_item), s_cursor);
+    }
   }
 }
 

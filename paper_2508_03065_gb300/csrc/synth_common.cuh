@@ -31,10 +31,17 @@ __device__ __forceinline__ int find_scene(const int64_t* prefix, int n, int64_t 
 // current scene's item range and advances by at most a few scenes before it
 // falls back to the binary search (one uncached global load per scene change
 // instead of a search per item).
-struct SceneCursor {
-  int s = 0;
-  int64_t lo = 0, hi = -1;
+struct SceneCursor {  // plain data: it also lives in shared memory
+  int s;
+  int64_t lo, hi;
 };
+__device__ __forceinline__ SceneCursor fresh_cursor() {
+  SceneCursor c;
+  c.s = 0;
+  c.lo = 0;
+  c.hi = -1;
+  return c;
+}
 __device__ __forceinline__ int scene_at(const int64_t* prefix, int n, int64_t idx, SceneCursor& c) {
   if (idx >= c.lo && idx < c.hi) return c.s;
   int s = -1;
