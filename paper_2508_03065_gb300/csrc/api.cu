@@ -674,12 +674,15 @@ msrc_status make_plan(const msrc_room_t* rooms, int n, const int64_t* n_in, cons
     S.n_blocks = blk;
     S.img_base = img_acc;
     S.master_base = master_acc;
-    // time groups: one per kTimeGroupSamples of output in forward mode; one
-    // (ordered at the middle of the trajectory) in reverse mode (band-limited
-    // tiers' knot-delay rows follow the first group's order, k_group0_pos)
+    // time groups: one per kTimeGroupSamples of output. Reverse mode keeps one
+    // (ordered at the middle of the trajectory) when a tier is band-limited or
+    // the delays are emission-time: the per-(mic, image, knot) tables of those
+    // tiers are indexed by the first group's image order.
     {
+      bool opt_tiers = R->d.delay_model == 1;
+      for (int t = 0; t < S.n_tiers; ++t) opt_tiers = opt_tiers || S.tier_up[t] > 1;
       const int tg = int(std::max<int64_t>(1, kTimeGroupSamples / T));
-      const bool grouped = !backward && S.n_tiles > tg;
+      const bool grouped = !(backward && opt_tiers) && S.n_tiles > tg;
       S.tile_group = grouped ? tg : S.n_tiles;
       S.n_time_groups = grouped ? (S.n_tiles + tg - 1) / tg : 1;
       S.sort_group0 = group_acc;

@@ -45,6 +45,7 @@ constexpr int kBwTile = kBwThreads * kBwChunks;
 constexpr int kBwRecCap = 3328;                 // records (image x interval)
 constexpr int kBwUnitCap = 3584;                // unit vectors (image x knot)
 constexpr int kBwBlock = 256;                   // images per block at most
+static_assert(kBwBlock <= kBwThreads, "the record builders give every image of a block its own thread");
 constexpr int kGradWcap = 1408;                 // shared z window of the gradient kernel
 constexpr int kDxWcap = 1760;                   // shared w window of the dx kernel
 constexpr int kSegCap = 33;                     // knot intervals touched by 32 consecutive samples
@@ -414,9 +415,10 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_adj_grad(const __grid_constan
         uz_s[i] = make_float2(0.f, 0.f);
       }
     }
-    // dbeta_i/dbeta_w / (4 pi) of the block's images, paired
+    // dbeta_i/dbeta_w / (4 pi) of the block's images (in the item's time
+    // group's order), paired
     {
-      const float4* bwt = a.p.bwt + 2 * (S.img_base + S.tier_first[g.t] + g.img0);
+      const float4* bwt = a.p.bwt + 2 * (S.img_base + g.img_off + S.tier_first[g.t] + g.img0);
       for (int i = threadIdx.x; i < 2 * cntp; i += kBwThreads) {
         const int ib = 2 * (i >> 1) + (i & 1);  // image of this thread: pair i / 2, member i % 2
         float wv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};

@@ -242,6 +242,7 @@ __device__ __forceinline__ void gather_pairs(const float4* zq, const float2* rec
 
 template <int kThreads, int kChunks, int kWcap, int kRecCap, int kBlock, int kUnroll, bool kKnots>
 __global__ void __launch_bounds__(kThreads, (kThreads <= 256 ? 2 : 1)) k_synth(const __grid_constant__ KernelArgs a) {
+  static_assert(kBlock <= kThreads, "the record builders give every image of a block its own thread");
   constexpr int kLayout = kKnots ? kRecForwardKnots : kRecForward;
   // relative knot delays of the block (cnt x nk floats): knot records hold twice
   // as many image-knots as interval records hold image-intervals

@@ -101,11 +101,12 @@ struct SceneDev {
   float fsc_hl[2];
   int64_t img_base;                        // first entry of this scene in the image table
   int64_t master_base;                     // first entry in the per-image (lattice order) tables
-  // time groups: the forward synthesis orders the images separately for every
-  // group of tile_group consecutive output tiles (by tier, then distance at the
-  // group's middle), so that the images of a block stay close in delay over the
-  // group's tiles; group g's table starts at img_base + g * n_images.
-  // Reverse mode and band-limited tiers use one group (tile_group >= n_tiles).
+  // time groups: the images are ordered separately for every group of
+  // tile_group consecutive output tiles (by tier, then distance at the group's
+  // middle), so that the images of a block stay close in delay over the
+  // group's tiles; group g's table starts at img_base + g * n_images. Reverse
+  // mode with a band-limited tier or emission-time delays uses one group
+  // (tile_group >= n_tiles).
   int32_t tile_group;                      // output tiles per time group
   int32_t n_time_groups;                   // time groups of the scene
   int64_t sort_group0;                     // the scene's first group in the sort key
