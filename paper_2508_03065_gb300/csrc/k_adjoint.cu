@@ -19,12 +19,12 @@
 //   loop. Per item: a warp-segmented scan folds the lanes' knot vectors into
 //   knot slots; the wall partials are reduced in a fixed order.
 // k_adj_dx: persistent over (scene, mic, block group, tile range) items, a
-//   group being consecutive image blocks of one tier (about 256 images), a
-//   range spanning more than the largest delay; walks the range's tiles in
-//   order, two output samples per thread. dy g w^q of every image of the group
-//   is scattered into one shared w window; within one image no two samples
-//   share a (segment, column) bin, so images are separated by a barrier and no
-//   atomics are used. Each tile's window is correlated once with the Farrow
+//   group being consecutive image blocks of one tier (about 256 images, at
+//   least two blocks), a range spanning more than the largest delay; walks
+//   the range's tiles in order, two output samples per thread. dy g w^q of
+//   every image of the group is scattered into one shared w window; within
+//   one image no two samples share a (segment, column) bin, so images are
+//   separated by a barrier and no atomics are used. Each tile's window is correlated once with the Farrow
 //   coefficients and added, in tile order, to the dx row of the range's parity
 //   (ranges two apart write disjoint columns). The window
 //   is the union of the blocks' delay ranges, which the gradient kernel stores
@@ -53,7 +53,7 @@ constexpr int kSegCap = 33;                     // knot intervals touched by 32 
 constexpr size_t kGradSmem = size_t(kFarrowSegs) * kGradWcap * (sizeof(float4) + sizeof(float2)) +
                              size_t(kBwRecCap) * sizeof(float2) + size_t(kBwBlock) * sizeof(int4) +
                              size_t(kBwUnitCap) * sizeof(float4) + size_t(2 * kBwBlock) * sizeof(float4);
-constexpr int kDxGroupImages = 256;             // images per dx item (block group), about
+constexpr int kDxGroupImages = 256;             // images per dx item (block group), about; >= 2 blocks
 constexpr int kDxSlots = kFarrowSegs * kDxWcap + 4;   // w window + a discard slot (+ 16-byte alignment)
 static_assert((kDxSlots * sizeof(float)) % 16 == 0 && (kBwRecCap * sizeof(float2)) % 16 == 0,
               "every shared array of the reverse-mode kernels starts on a 16-byte boundary");
