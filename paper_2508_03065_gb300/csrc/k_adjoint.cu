@@ -24,11 +24,12 @@
 //   the range's tiles in order, two output samples per thread. dy g w^q of
 //   every image of the group is scattered into one shared w window; within
 //   one image no two samples share a (segment, column) bin, so images are
-//   separated by a barrier and no atomics are used. Each tile's window is correlated once with the Farrow
-//   coefficients and added, in tile order, to the dx row of the range's parity
-//   (ranges two apart write disjoint columns). The window
-//   is the union of the blocks' delay ranges, which the gradient kernel stores
-//   per (mic, block, tile) item; wide windows run in several column passes.
+//   separated by a barrier and no atomics are used. Each tile's window is
+//   correlated once with the Farrow coefficients and added, in tile order, to
+//   the dx row of the range's parity (ranges two apart write disjoint
+//   columns). The window is the union of the blocks' delay ranges, which the
+//   gradient kernel stores per (mic, block, tile) item; wide windows run in
+//   several column passes.
 // k_dx_final / k_knot_final / k_param_partial + k_param_final / k_beta_final:
 // fixed-order sums.
 #include <cstdint>
