@@ -71,6 +71,17 @@ def test_dx_several_time_groups(kw):
     assert rel_l2(dx, ref) < 1e-5
 
 
+def test_dx_groups_of_two_full_blocks():
+    # a tier with knots every 96 samples holds 256 images per block, and the
+    # dx kernel's groups take two such blocks (one correlation for 512 images)
+    spec = W.small_scene(seed=77, K=6, seconds=0.1, window=W.HANN, taps=32,
+                         tiers=[(1, 16000.0), (W.RHO_INF, 16000.0 / 96)])
+    dy = np.random.default_rng(77).standard_normal(spec.n_in)
+    dx, _, _ = _bwd(spec, dy, want_params=False, want_beta=False)
+    ref = oracle.adjoint_x(oracle_scene(spec), dy, spec.n_in)
+    assert rel_l2(dx, ref) < 1e-5
+
+
 def test_param_and_beta_gradients_several_time_groups():
     spec = W.small_scene(seed=76, K=2, seconds=1.6, window=W.HANN, taps=16)
     sc = oracle_scene(spec)
