@@ -64,7 +64,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=320, help="output samples timed for the oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seconds", type=float, default=None,
-                    help="shorten the scene (profiling captures); the benchmark default is 4 s")
+                    help="shorten the scene, and with --only array the array scene's signal (profiling "
+                         "captures); the benchmark default is 4 s")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--delay-model", type=int, default=0, choices=[0, 1],
                     help="knot distances at the reception time (0, the benchmark) or emission-time path lengths (1)")
@@ -543,8 +544,11 @@ def run_backward(args, torch, api, W, n_scenes=16):
 
 def run_array(args, torch, api, W):
     """The array scene: 8-mic circular array, order 25 (177 208 images), 10 s at
-    48 kHz, 64 taps; forward and backward."""
+    48 kHz, 64 taps; forward and backward. With --seconds, the first seconds of
+    its signal on the same trajectory (profiling captures)."""
     spec = W.config5()
+    if args.seconds is not None:
+        spec = W.with_signal(spec, spec.x[:int(args.seconds * spec.fs)])
     room = api.Room.from_spec(spec)
     x = torch.from_numpy(spec.x).cuda()
     ws = api.Workspace("cuda")
